@@ -1,0 +1,295 @@
+"""FP64 CPU oracle of the Gaussian-plus-SDF hot path - TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of `bench.py`
+may import this package.  It shares no code with the CUDA path
+(`paper_2509_11574_b300`), which never imports it.
+
+The arithmetic lives in `tsdf.cpp` (fusion, ray-cast) and `splat.cpp`
+(projection, compositing Eq. 1-4 and the Table 7 "with sort" variant, L1 loss
+Eq. 6, adjoints, tile binning, Adam).  This module builds `liboracle.so` with
+g++ (FP64, `-ffp-contract=off`, OpenMP over independent pixels / voxels) and
+wraps it with ctypes on float64 numpy arrays.
+
+Parity status per function (what pins it, see tests/test_oracle_*.py):
+  fuse              - fronto-parallel plane closed form, weight / re-fusion invariants
+  raycast           - analytic plane / box (exact) and sphere (0.1 voxel) hits
+  project           - on-axis isotropic closed form, off-axis hand value, invariances
+  composite (OIT)   - 1- and 2-Gaussian hand blends, M = 0, eps limits, brute force,
+                      permutation invariance
+  composite (ALPHA) - 1-Gaussian blend, opaque limit, termination count by hand;
+                      the paper never writes this variant, so its formula is a reading
+  loss              - torch.nn.functional.l1_loss (FP64)
+  backward          - central finite differences (FP64) end to end, rotation
+                      invariance, single-Gaussian closed form
+  bin               - brute-force enumeration of tiles + Python sorted()
+  adam              - torch.optim.Adam (FP64)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRCS = [os.path.join(_HERE, f) for f in ("tsdf.cpp", "splat.cpp")]
+
+# projected record layout (FP64), mirrors the enum in splat.cpp
+R_MX, R_MY, R_D, R_SIG, R_CA, R_CB, R_CC, R_QMAX, R_R, R_G, R_B, R_EX, R_EY, R_VIS, \
+    R_S2XX, R_S2YY = range(16)
+R_N = 16
+# per-Gaussian 2D gradient layout
+G_MX, G_MY, G_CA, G_CB, G_CC, G_SIG, G_R, G_G, G_B, G_D = range(10)
+G_N = 10
+
+OIT, ALPHA = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to the sources (g++, FP64, OpenMP)."""
+    newest = max(os.path.getmtime(s) for s in _SRCS)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", _SO] + _SRCS
+        subprocess.check_call(cmd)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_SO)
+        _lib.orc_project.restype = ctypes.c_int
+        _lib.orc_loss.restype = ctypes.c_double
+        _lib.orc_bin.restype = ctypes.c_long
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"], "arrays passed to the oracle must be contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _cam(cam):
+    K = _f64([cam.fx, cam.fy, cam.cx, cam.cy])
+    return K, _f64(cam.R).reshape(9), _f64(cam.t).reshape(3)
+
+
+def _vol(spec):
+    dims = np.ascontiguousarray([spec.nx, spec.ny, spec.nz], dtype=np.int32)
+    geo = _f64([spec.voxel, *spec.origin, spec.trunc, spec.max_weight])
+    return dims, geo
+
+
+class Volume:
+    """FP64 TSDF in linear storage (x fastest): sdf, w, cw [nz][ny][nx], rgb [...][3].
+    Unobserved voxels: sdf = 1, w = 0, rgb = 0, cw = 0."""
+
+    def __init__(self, spec):
+        self.spec = spec
+        shape = (spec.nz, spec.ny, spec.nx)
+        self.sdf = np.ones(shape)
+        self.w = np.zeros(shape)
+        self.rgb = np.zeros(shape + (3,))
+        self.cw = np.zeros(shape)
+        self.amb = np.zeros(shape, dtype=np.int32)
+
+
+def fuse(vol: Volume, depth, rgb, cam) -> None:
+    """Sec. 3.2.1 SDF fusion of one frame into `vol` (in place)."""
+    dims, geo = _vol(vol.spec)
+    K, R, t = _cam(cam)
+    d = _f64(depth)
+    c = _f64(rgb)
+    lib().orc_fuse(_p(dims), _p(geo), _p(vol.sdf), _p(vol.w), _p(vol.rgb), _p(vol.cw),
+                   _p(vol.amb), _p(d), _p(c), ctypes.c_int(cam.width), ctypes.c_int(cam.height),
+                   _p(K), _p(R), _p(t))
+
+
+def raycast(spec, sdf, rgb, cam, near=0.2, far=0.0):
+    """Sec. 3.1 first pass.  Returns (C_t [3][H][W], D_t [H][W], vertex [H][W][3], amb)."""
+    dims, geo = _vol(spec)
+    K, R, t = _cam(cam)
+    H, W = cam.height, cam.width
+    out_rgb = np.zeros((3, H, W))
+    out_d = np.zeros((H, W))
+    out_v = np.zeros((H, W, 3))
+    amb = np.zeros((H, W), dtype=np.int32)
+    lib().orc_raycast(_p(dims), _p(geo), _p(_f64(sdf)), _p(_f64(rgb)), ctypes.c_int(W),
+                      ctypes.c_int(H), _p(K), _p(R), _p(t), ctypes.c_double(near),
+                      ctypes.c_double(far), _p(out_rgb), _p(out_d), _p(out_v), _p(amb))
+    return out_rgb, out_d, out_v, amb
+
+
+def project(g, cam, near=0.2):
+    """Projection of a GaussianSet into one view -> (rec [M][16] f64, amb [M])."""
+    M = g.M
+    arrs = [_f64(a) for a in g.arrays()]
+    K, R, t = _cam(cam)
+    rec = np.zeros((M, R_N))
+    amb = np.zeros(M, dtype=np.int32)
+    lib().orc_project(ctypes.c_int(M), *[_p(a) for a in arrs[:4]], _p(arrs[4]),
+                      ctypes.c_int(cam.width), ctypes.c_int(cam.height), _p(K), _p(R), _p(t),
+                      ctypes.c_double(near), _p(rec), _p(amb))
+    return rec, amb
+
+
+def composite(rec, Ct, Dt, eps, mode=OIT, f32=False, brute=False, window=None):
+    """Eq. 1-4 (mode OIT) or the Table 7 variant (mode ALPHA) for one view.
+    Returns dict C [3][H][W], D, W (= W_G), T (T_end), n (counted), amb."""
+    Ct = _f64(Ct)
+    Dt = _f64(Dt)
+    H, W = Dt.shape
+    x0, x1, y0, y1 = window if window is not None else (0, W - 1, 0, H - 1)
+    rec = _f64(rec)
+    out = dict(C=np.zeros((3, H, W)), D=np.zeros((H, W)), W=np.zeros((H, W)),
+               T=np.zeros((H, W)), n=np.zeros((H, W), np.int32), amb=np.zeros((H, W), np.int32))
+    lib().orc_composite(ctypes.c_int(rec.shape[0]), _p(rec), ctypes.c_int(W), ctypes.c_int(H),
+                        _p(Ct), _p(Dt), ctypes.c_double(eps), ctypes.c_int(mode),
+                        ctypes.c_int(int(f32)), ctypes.c_int(int(brute)), ctypes.c_int(x0),
+                        ctypes.c_int(x1), ctypes.c_int(y0), ctypes.c_int(y1), _p(out["C"]),
+                        _p(out["D"]), _p(out["W"]), _p(out["T"]), _p(out["n"]), _p(out["amb"]))
+    return out
+
+
+def loss(C, D, Ctgt, Dtgt, Dt, lambda_depth=0.0):
+    """Eq. 6 L1 loss -> (L, dL/dC* [3][H][W], dL/dD* [H][W], N_v, amb)."""
+    C, D, Ctgt, Dtgt, Dt = (_f64(a) for a in (C, D, Ctgt, Dtgt, Dt))
+    H, W = D.shape
+    dC = np.zeros((3, H, W))
+    dD = np.zeros((H, W))
+    nv = ctypes.c_long(0)
+    amb = np.zeros((H, W), np.int32)
+    L = lib().orc_loss(ctypes.c_int(W), ctypes.c_int(H), _p(C), _p(D), _p(Ctgt), _p(Dtgt),
+                       _p(Dt), ctypes.c_double(lambda_depth), _p(dC), _p(dD), ctypes.byref(nv),
+                       _p(amb))
+    return float(L), dC, dD, int(nv.value), amb
+
+
+def composite_backward(rec, Ct, Dt, eps, dC, dD, mode=OIT, f32=False):
+    """Adjoint of `composite` -> per-Gaussian 2D gradients [M][10]."""
+    rec = _f64(rec)
+    Ct, Dt, dC, dD = (_f64(a) for a in (Ct, Dt, dC, dD))
+    H, W = Dt.shape
+    g2 = np.zeros((rec.shape[0], G_N))
+    lib().orc_composite_backward(ctypes.c_int(rec.shape[0]), _p(rec), ctypes.c_int(W),
+                                 ctypes.c_int(H), _p(Ct), _p(Dt), ctypes.c_double(eps),
+                                 ctypes.c_int(mode), ctypes.c_int(int(f32)), _p(dC), _p(dD),
+                                 _p(g2))
+    return g2
+
+
+def project_backward(g, cam, g2, near=0.2):
+    """Adjoint of `project` -> dict of gradients (means, log_scales, quats,
+    opacity_logits, rgb), float64."""
+    M = g.M
+    arrs = [_f64(a) for a in g.arrays()]
+    K, R, t = _cam(cam)
+    out = dict(means=np.zeros((M, 3)), log_scales=np.zeros((M, 3)), quats=np.zeros((M, 4)),
+               opacity_logits=np.zeros(M), rgb=np.zeros((M, 3)))
+    lib().orc_project_backward(ctypes.c_int(M), *[_p(a) for a in arrs[:4]],
+                               ctypes.c_int(cam.width), ctypes.c_int(cam.height), _p(K), _p(R),
+                               _p(t), ctypes.c_double(near), _p(_f64(g2)), _p(out["means"]),
+                               _p(out["log_scales"]), _p(out["quats"]),
+                               _p(out["opacity_logits"]), _p(out["rgb"]))
+    return out
+
+
+def bin_records(rec32: np.ndarray, W: int, H: int, TW: int, TH: int, cap: int = 1 << 26):
+    """Tile binning of FP32 records [M][16] -> (keys u64 [P], vals u32 [P],
+    ranges u32 [tiles][2])."""
+    rec32 = np.ascontiguousarray(rec32, dtype=np.float32)
+    M = rec32.shape[0]
+    ntiles = ((W + TW - 1) // TW) * ((H + TH - 1) // TH)
+    cap = int(min(cap, max(1, _count_pairs(rec32, W, H, TW, TH))))
+    keys = np.zeros(cap, np.uint64)
+    vals = np.zeros(cap, np.uint32)
+    ranges = np.zeros((ntiles, 2), np.uint32)
+    P = lib().orc_bin(ctypes.c_int(M), _p(rec32), ctypes.c_int(W), ctypes.c_int(H),
+                      ctypes.c_int(TW), ctypes.c_int(TH), ctypes.c_long(cap), _p(keys), _p(vals),
+                      _p(ranges))
+    if P < 0:
+        raise RuntimeError("pair capacity exceeded")
+    return keys[:P].copy(), vals[:P].copy(), ranges
+
+
+def _count_pairs(rec32, W, H, TW, TH) -> int:
+    """Upper bound on the number of (tile, Gaussian) pairs (buffer sizing only)."""
+    ex, ey = rec32[:, 11].astype(np.float64), rec32[:, 12].astype(np.float64)
+    ok = (ex >= 0) & (ey >= 0)
+    mx, my = rec32[:, 0].astype(np.float64), rec32[:, 1].astype(np.float64)
+    x0 = np.clip(np.floor(mx - ex), 0, W - 1)
+    x1 = np.clip(np.ceil(mx + ex), 0, W - 1)
+    y0 = np.clip(np.floor(my - ey), 0, H - 1)
+    y1 = np.clip(np.ceil(my + ey), 0, H - 1)
+    n = (x1 // TW - x0 // TW + 1) * (y1 // TH - y0 // TH + 1)
+    return int(np.where(ok & np.isfinite(n), n, 0).sum())
+
+
+def adam(p, g, m, v, lr, b1=0.9, b2=0.999, eps=1e-15, step=1) -> None:
+    """In-place FP64 Adam step on flat contiguous float64 arrays."""
+    n = p.size
+    lib().orc_adam(ctypes.c_long(n), _p(p), _p(g), _p(m), _p(v), ctypes.c_double(lr),
+                   ctypes.c_double(b1), ctypes.c_double(b2), ctypes.c_double(eps),
+                   ctypes.c_int(step))
+
+
+# --------------------------------------------------------------------------
+# conversions and whole-view helpers
+# --------------------------------------------------------------------------
+EXT_REL = np.float32(1.0 + 2.0 ** -7)
+EXT_ABS = np.float32(2.0 ** -4)
+
+
+def records_f32(rec: np.ndarray) -> np.ndarray:
+    """FP32 records in the kernels' 16-float layout from FP64 oracle records:
+    (mx, my, d, sigma, a, b, c, qmax, r, g, b, ext_x, ext_y, 0, 0, 0) rounded to
+    float, with the conservative extent ext = sqrt(qmax * S2xx) * (1 + 2^-7) + 2^-4
+    evaluated in float, and ext = -1 for invisible Gaussians."""
+    M = rec.shape[0]
+    out = np.zeros((M, 16), np.float32)
+    for k_out, k_in in enumerate((R_MX, R_MY, R_D, R_SIG, R_CA, R_CB, R_CC, R_QMAX, R_R, R_G,
+                                  R_B)):
+        out[:, k_out] = rec[:, k_in].astype(np.float32)
+    q = out[:, 7]
+    with np.errstate(invalid="ignore"):
+        ex = np.sqrt(q * rec[:, R_S2XX].astype(np.float32)) * EXT_REL + EXT_ABS
+        ey = np.sqrt(q * rec[:, R_S2YY].astype(np.float32)) * EXT_REL + EXT_ABS
+    vis = rec[:, R_VIS] != 0
+    out[:, 11] = np.where(vis, ex, np.float32(-1))
+    out[:, 12] = np.where(vis, ey, np.float32(-1))
+    return out
+
+
+def rounded(rec: np.ndarray) -> np.ndarray:
+    """FP64 record array holding the FP32-rounded values (for f32 decisions)."""
+    r = rec.astype(np.float32).astype(np.float64)
+    r[:, R_VIS] = rec[:, R_VIS]
+    return r
+
+
+def render_loss_grads(g, cam, Ct, Dt, Ctgt, Dtgt, eps=0.01, lambda_depth=0.0, mode=OIT,
+                      f32=False, near=0.2):
+    """One view end to end: project -> composite -> loss -> adjoints.
+    f32=True takes the counting decisions in FP32 on FP32-rounded records."""
+    rec, pamb = project(g, cam, near)
+    rr = rounded(rec) if f32 else rec
+    out = composite(rr, Ct, Dt, eps, mode, f32)
+    L, dC, dD, nv, lamb = loss(out["C"], out["D"], Ctgt, Dtgt, Dt, lambda_depth)
+    g2 = composite_backward(rr, Ct, Dt, eps, dC, dD, mode, f32)
+    grads = project_backward(g, cam, g2, near)
+    return dict(L=L, rec=rec, proj_amb=pamb, out=out, dC=dC, dD=dD, n_valid=nv, loss_amb=lamb,
+                g2=g2, grads=grads)

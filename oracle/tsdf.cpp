@@ -1,0 +1,217 @@
+// Oracle (test infrastructure only): colourised TSDF fusion and SDF ray-cast in FP64.
+//
+// Plain, slow, obviously-correct restatement of the supporting steps of the
+// Gaussian-plus-SDF renderer:
+//   * fusion  - Sec. 3.2.1 "SDF fusion": each voxel keeps a truncated signed
+//               distance d(p) and a colour c(p) (Sec. 3.1), updated by the
+//               standard weighted running average (KinectFusion / InfiniTAM);
+//   * ray-cast - Sec. 3.1 first rendering pass: march every pixel's ray to the
+//               zero crossing V^g(u), C_t(u) = trilinear colour of the eight
+//               neighbouring voxels, D_t(u) = depth of V^g(u) in the camera.
+// Readings where the paper is silent (step rule, secant refinement, colour
+// weight, rounding of the projected pixel) are stated at each function.
+//
+// Storage here is linear, x fastest: idx = x + nx * (y + ny * z).  Only tests,
+// the package smoke check and the benchmark's CPU-baseline leg may call this.
+#include <cmath>
+#include <cstdint>
+#include <algorithm>
+
+namespace {
+
+struct Vol {
+  int nx, ny, nz;
+  double voxel, ox, oy, oz, trunc, wmax;
+  long idx(int x, int y, int z) const { return x + (long)nx * (y + (long)ny * z); }
+};
+
+Vol make_vol(const int* dims, const double* geo) {
+  Vol v;
+  v.nx = dims[0]; v.ny = dims[1]; v.nz = dims[2];
+  v.voxel = geo[0]; v.ox = geo[1]; v.oy = geo[2]; v.oz = geo[3];
+  v.trunc = geo[4]; v.wmax = geo[5];
+  return v;
+}
+
+// world -> camera: X_c = R^T (X_w - t), R camera->world row-major.
+inline void world_to_cam(const double* R, const double* t, const double* xw, double* xc) {
+  double d0 = xw[0] - t[0], d1 = xw[1] - t[1], d2 = xw[2] - t[2];
+  for (int i = 0; i < 3; ++i) xc[i] = R[0 * 3 + i] * d0 + R[1 * 3 + i] * d1 + R[2 * 3 + i] * d2;
+}
+
+// Trilinear interpolation of a per-voxel field at continuous voxel coordinate g
+// (voxel centres at integer g).  The 8-voxel stencil is clamped to the grid.
+double trilinear(const Vol& v, const double* f, int stride, int comp, const double* g) {
+  int i0[3];
+  double fr[3];
+  const int n[3] = {v.nx, v.ny, v.nz};
+  for (int k = 0; k < 3; ++k) {
+    double gk = g[k];
+    int i = (int)std::floor(gk);
+    if (i < 0) i = 0;
+    if (i > n[k] - 2) i = n[k] - 2;
+    i0[k] = i;
+    fr[k] = gk - i;
+  }
+  double acc = 0.0;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        double w = (dx ? fr[0] : 1.0 - fr[0]) * (dy ? fr[1] : 1.0 - fr[1]) *
+                   (dz ? fr[2] : 1.0 - fr[2]);
+        acc += w * f[v.idx(i0[0] + dx, i0[1] + dy, i0[2] + dz) * stride + comp];
+      }
+  return acc;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Colourised TSDF fusion of one RGB-D frame (Sec. 3.2.1, "standard SDF fusion").
+// For each voxel centre x_v = origin + (idx + 0.5) * voxel:
+//   x_c = R^T (x_v - t); skip unless z_c > 0;
+//   (u, v) = (fx x/z + cx, fy y/z + cy), nearest pixel = floor(u + 0.5), floor(v + 0.5);
+//   skip unless the pixel is inside the image and its depth D > 0;
+//   eta = D - z_c; skip if eta < -trunc;
+//   f = min(1, eta / trunc); sdf <- (w sdf + f) / (w + 1); w <- min(w + 1, wmax);
+//   if |eta| < trunc: rgb <- (cw rgb + C) / (cw + 1); cw <- min(cw + 1, wmax)
+// (the colour keeps its own weight cw, as InfiniTAM's coloured voxels do).
+// amb[v] |= 1 when a discrete decision of this update sits within a relative
+// 1e-6 of its threshold (pixel rounding, truncation tests), so a
+// single-precision implementation may legitimately take the other branch.
+void orc_fuse(const int* dims, const double* geo, double* sdf, double* w, double* rgb,
+              double* cw, int* amb, const double* depth, const double* img, int W, int H,
+              const double* K, const double* R, const double* t) {
+  const Vol v = make_vol(dims, geo);
+  const double fx = K[0], fy = K[1], cx = K[2], cy = K[3];
+  const long n = (long)v.nx * v.ny * v.nz;
+#pragma omp parallel for schedule(static)
+  for (long id = 0; id < n; ++id) {
+    int x = (int)(id % v.nx), y = (int)((id / v.nx) % v.ny), z = (int)(id / ((long)v.nx * v.ny));
+    double xw[3] = {v.ox + (x + 0.5) * v.voxel, v.oy + (y + 0.5) * v.voxel,
+                    v.oz + (z + 0.5) * v.voxel};
+    double xc[3];
+    world_to_cam(R, t, xw, xc);
+    if (!(xc[2] > 0.0)) continue;
+    double u = fx * xc[0] / xc[2] + cx, vv = fy * xc[1] / xc[2] + cy;
+    double fu = u + 0.5 - std::floor(u + 0.5), fv = vv + 0.5 - std::floor(vv + 0.5);
+    bool near_round = std::min(fu, 1.0 - fu) < 1e-6 * std::max(1.0, std::fabs(u)) ||
+                      std::min(fv, 1.0 - fv) < 1e-6 * std::max(1.0, std::fabs(vv));
+    double pu = std::floor(u + 0.5), pv = std::floor(vv + 0.5);
+    if (pu < 0 || pv < 0 || pu > W - 1 || pv > H - 1) {
+      if (amb && near_round) amb[id] |= 1;
+      continue;
+    }
+    long pix = (long)pv * W + (long)pu;
+    double D = depth[pix];
+    if (!(D > 0.0)) {
+      if (amb && near_round) amb[id] |= 1;
+      continue;
+    }
+    double eta = D - xc[2];
+    if (amb && (near_round || std::fabs(eta + v.trunc) < 1e-6 * v.trunc ||
+                std::fabs(std::fabs(eta) - v.trunc) < 1e-6 * v.trunc))
+      amb[id] |= 1;
+    if (eta < -v.trunc) continue;
+    double f = std::min(1.0, eta / v.trunc);
+    double w0 = w[id];
+    sdf[id] = (w0 * sdf[id] + f) / (w0 + 1.0);
+    w[id] = std::min(w0 + 1.0, v.wmax);
+    if (std::fabs(eta) < v.trunc) {
+      double c0 = cw[id];
+      for (int ch = 0; ch < 3; ++ch)
+        rgb[id * 3 + ch] = (c0 * rgb[id * 3 + ch] + img[(long)ch * W * H + pix]) / (c0 + 1.0);
+      cw[id] = std::min(c0 + 1.0, v.wmax);
+    }
+  }
+}
+
+// SDF ray-cast (Sec. 3.1 first pass; marching "as in InfiniTAM").
+// Ray of pixel (i, j): origin t, direction dir = normalize(R ((i-cx)/fx, (j-cy)/fy, 1)).
+// The march is confined to the box spanned by the voxel centres, starting at
+// max(near, box entry) and ending at min(far, box exit) (far <= 0: box exit).
+// f(s) = trilinear sdf at o + s dir.  Step = max(min(f, 1) * trunc, 0.5 voxel)
+// (a full truncation band while f == 1).  The first sample pair with
+// f_a > 0 >= f_b is a hit; secant refinement s* = s_a + (s_b - s_a) f_a / (f_a - f_b).
+// V^g = o + s* dir; D_t = camera z of V^g; C_t = trilinear of the 8 voxel colours.
+// No hit: D_t = 0, C_t = 0, vertex = 0.
+// amb[pix] = 1 when some sample had |f| < 1e-4 without being the final bracket,
+// or the bracket values were within 1e-4 of zero, or a sample sat within a
+// relative 1e-6 of the march end - decisions a single-precision march can take
+// differently.
+void orc_raycast(const int* dims, const double* geo, const double* sdf, const double* rgb,
+                 int W, int H, const double* K, const double* R, const double* t,
+                 double near_, double far_, double* out_rgb, double* out_depth,
+                 double* out_vertex, int* amb) {
+  const Vol v = make_vol(dims, geo);
+  const double fx = K[0], fy = K[1], cx = K[2], cy = K[3];
+  const double lo[3] = {v.ox + 0.5 * v.voxel, v.oy + 0.5 * v.voxel, v.oz + 0.5 * v.voxel};
+  const double hi[3] = {v.ox + (v.nx - 0.5) * v.voxel, v.oy + (v.ny - 0.5) * v.voxel,
+                        v.oz + (v.nz - 0.5) * v.voxel};
+  const long npx = (long)W * H;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long pix = 0; pix < npx; ++pix) {
+    const int i = (int)(pix % W), j = (int)(pix / W);
+    double dc[3] = {(i - cx) / fx, (j - cy) / fy, 1.0};
+    double dw[3];
+    for (int r = 0; r < 3; ++r) dw[r] = R[r * 3 + 0] * dc[0] + R[r * 3 + 1] * dc[1] + R[r * 3 + 2] * dc[2];
+    double nrm = std::sqrt(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
+    for (int r = 0; r < 3; ++r) dw[r] /= nrm;
+    double s_in = -INFINITY, s_out = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+      if (dw[k] != 0.0) {
+        double a = (lo[k] - t[k]) / dw[k], b = (hi[k] - t[k]) / dw[k];
+        s_in = std::max(s_in, std::min(a, b));
+        s_out = std::min(s_out, std::max(a, b));
+      } else if (t[k] < lo[k] || t[k] > hi[k]) {
+        s_in = INFINITY;
+      }
+    }
+    double s0 = std::max(near_, s_in);
+    double s1 = far_ > 0.0 ? std::min(far_, s_out) : s_out;
+    out_rgb[pix] = out_rgb[npx + pix] = out_rgb[2 * npx + pix] = 0.0;
+    out_depth[pix] = 0.0;
+    if (out_vertex) out_vertex[pix * 3] = out_vertex[pix * 3 + 1] = out_vertex[pix * 3 + 2] = 0.0;
+    if (amb) amb[pix] = 0;
+    if (!(s0 < s1)) continue;
+    auto sample = [&](double s) {
+      double g[3];
+      const double o3[3] = {v.ox, v.oy, v.oz};
+      for (int k = 0; k < 3; ++k) g[k] = (t[k] + s * dw[k] - o3[k]) / v.voxel - 0.5;
+      return trilinear(v, sdf, 1, 0, g);
+    };
+    double sa = s0, fa = sample(sa);
+    bool hit = false, ambig = false;
+    double sb = 0.0, fb = 0.0;
+    while (true) {
+      double step = std::max(std::min(fa, 1.0) * v.trunc, 0.5 * v.voxel);
+      sb = sa + step;
+      if (std::fabs(sb - s1) < 1e-6 * s1) ambig = true;
+      if (sb > s1) break;
+      fb = sample(sb);
+      if (fa > 0.0 && fb <= 0.0) {
+        hit = true;
+        if (std::fabs(fa) < 1e-4 || std::fabs(fb) < 1e-4) ambig = true;
+        break;
+      }
+      if (std::fabs(fb) < 1e-4) ambig = true;
+      sa = sb;
+      fa = fb;
+    }
+    if (amb) amb[pix] = ambig ? 1 : 0;
+    if (!hit) continue;
+    double ss = sa + (sb - sa) * fa / (fa - fb);
+    double V[3] = {t[0] + ss * dw[0], t[1] + ss * dw[1], t[2] + ss * dw[2]};
+    double xc[3];
+    world_to_cam(R, t, V, xc);
+    out_depth[pix] = xc[2];
+    double g[3] = {(V[0] - v.ox) / v.voxel - 0.5, (V[1] - v.oy) / v.voxel - 0.5,
+                   (V[2] - v.oz) / v.voxel - 0.5};
+    for (int ch = 0; ch < 3; ++ch) out_rgb[ch * npx + pix] = trilinear(v, rgb, 3, ch, g);
+    if (out_vertex)
+      for (int k = 0; k < 3; ++k) out_vertex[pix * 3 + k] = V[k];
+  }
+}
+
+}  // extern "C"

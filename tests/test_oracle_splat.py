@@ -1,0 +1,388 @@
+"""Pins of the oracle's projection, compositing (Eq. 1-4, Table 7 variant),
+loss (Eq. 6), adjoints, binning and Adam against closed forms, hand-computed
+blends, brute force, torch (FP64) and central finite differences."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from datagen import Camera, GaussianSet
+from datagen import workloads
+
+F = 100.0
+W_IMG, H_IMG = 48, 40
+
+
+def cam_axis(W=W_IMG, H=H_IMG, f=F):
+    return Camera(f, f, W / 2.0, H / 2.0, W, H, np.eye(3), np.zeros(3))
+
+
+def gset(means, scales, quats=None, logits=None, rgb=None):
+    means = np.atleast_2d(np.asarray(means, float))
+    M = means.shape[0]
+    ls = np.log(np.broadcast_to(np.asarray(scales, float), (M, 3))).copy()
+    q = np.tile([1.0, 0, 0, 0], (M, 1)) if quats is None else np.atleast_2d(np.asarray(quats, float))
+    lg = np.zeros(M) if logits is None else np.asarray(logits, float).reshape(M)
+    c = np.full((M, 3), 0.5) if rgb is None else np.atleast_2d(np.asarray(rgb, float))
+    return GaussianSet(means, ls, q, lg, c)
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + math.exp(-x))
+
+
+# ----------------------------------------------------------------- projection
+def test_project_on_axis_isotropic_closed_form():
+    s, z = 0.02, 1.3
+    rec, amb = oracle.project(gset([0, 0, z], s, logits=[0.7]), cam_axis())
+    r = rec[0]
+    var = (F * s / z) ** 2 + 0.3
+    assert r[oracle.R_VIS] == 1
+    np.testing.assert_allclose([r[oracle.R_MX], r[oracle.R_MY]], [W_IMG / 2, H_IMG / 2], atol=1e-12)
+    np.testing.assert_allclose(r[oracle.R_D], z, rtol=1e-15)
+    np.testing.assert_allclose([r[oracle.R_CA], r[oracle.R_CB], r[oracle.R_CC]],
+                               [1 / var, 0.0, 1 / var], rtol=1e-13, atol=1e-15)
+    sig = sigmoid(0.7)
+    np.testing.assert_allclose(r[oracle.R_SIG], sig, rtol=1e-15)
+    np.testing.assert_allclose(r[oracle.R_QMAX], 2 * math.log(255 * sig), rtol=1e-14)
+    np.testing.assert_allclose(r[oracle.R_EX], math.sqrt(2 * math.log(255 * sig) * var), rtol=1e-13)
+
+
+def test_project_off_axis_and_clamp_by_hand():
+    s, z = 0.01, 2.0
+    for x in (0.1, 0.4, -0.9):  # limit |x/z| <= 1.3 * 24 / 100 = 0.312
+        rec, _ = oracle.project(gset([x, 0.0, z], s), cam_axis())
+        lim = 1.3 * (W_IMG / (2 * F))
+        xp = max(-lim, min(lim, x / z)) * z
+        # J = [[F/z, 0, -F xp / z^2], [0, F/z, 0]], Sigma = s^2 I
+        sxx = s * s * (F * F / z ** 2 + (F * xp / z ** 2) ** 2) + 0.3
+        syy = s * s * F * F / z ** 2 + 0.3
+        np.testing.assert_allclose(rec[0, oracle.R_S2XX], sxx, rtol=1e-13)
+        np.testing.assert_allclose(rec[0, oracle.R_S2YY], syy, rtol=1e-13)
+        np.testing.assert_allclose(rec[0, oracle.R_MX], F * x / z + W_IMG / 2, rtol=1e-14)
+
+
+def test_project_rotation_about_optical_axis():
+    s1, s2, s3, z, th = 0.03, 0.01, 0.02, 1.5, 0.6
+    q = [math.cos(th / 2), 0, 0, math.sin(th / 2)]  # rotation by th about +z
+    rec, _ = oracle.project(gset([0, 0, z], [s1, s2, s3], quats=[q]), cam_axis())
+    R2 = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    S2 = (F / z) ** 2 * R2 @ np.diag([s1 * s1, s2 * s2]) @ R2.T + 0.3 * np.eye(2)
+    Ci = np.linalg.inv(S2)
+    r = rec[0]
+    np.testing.assert_allclose([r[oracle.R_CA], r[oracle.R_CB], r[oracle.R_CC]],
+                               [Ci[0, 0], Ci[0, 1], Ci[1, 1]], rtol=1e-12)
+    # quaternion scale does not matter
+    rec2, _ = oracle.project(gset([0, 0, z], [s1, s2, s3], quats=[np.array(q) * 3.7]), cam_axis())
+    np.testing.assert_allclose(rec2, rec, rtol=1e-13, atol=1e-15)
+
+
+def test_project_culling():
+    cam = cam_axis()
+    rec, _ = oracle.project(gset([[0, 0, 0.1], [0, 0, 1.0], [0, 0, 1.0], [50, 0, 1.0]], 0.01,
+                                 logits=[0, -6.0, 0, 0]), cam)
+    assert list(rec[:, oracle.R_VIS]) == [0, 0, 1, 0]  # near plane, sigma < 1/255, off image
+
+
+# ------------------------------------------------------------------ composite
+def flat_inputs(W=W_IMG, H=H_IMG, c=(0.2, 0.4, 0.6), d=2.0):
+    Ct = np.empty((3, H, W))
+    for k in range(3):
+        Ct[k] = c[k]
+    return Ct, np.full((H, W), d)
+
+
+def alpha_at(r, x, y):
+    dx, dy = x - r[oracle.R_MX], y - r[oracle.R_MY]
+    q = r[oracle.R_CA] * dx * dx + 2 * r[oracle.R_CB] * dx * dy + r[oracle.R_CC] * dy * dy
+    return r[oracle.R_SIG] * math.exp(-0.5 * q)
+
+
+def test_composite_single_gaussian_by_hand():
+    g = gset([0.01, -0.02, 1.2], 0.02, logits=[0.3], rgb=[[0.9, 0.1, 0.3]])
+    rec, _ = oracle.project(g, cam_axis())
+    Ct, Dt = flat_inputs()
+    out = oracle.composite(rec, Ct, Dt, eps=0.01)
+    for (x, y) in [(24, 20), (25, 18), (27, 21)]:
+        a = alpha_at(rec[0], x, y)
+        assert a >= 1 / 255
+        exp_c = (Ct[:, y, x] + a * np.array([0.9, 0.1, 0.3])) / (1 + a)
+        np.testing.assert_allclose(out["C"][:, y, x], exp_c, rtol=1e-14)
+        np.testing.assert_allclose(out["D"][y, x], (2.0 + a * 1.2) / (1 + a), rtol=1e-14)
+        np.testing.assert_allclose(out["W"][y, x], a, rtol=1e-14)
+    # far corner: outside the support, untouched
+    np.testing.assert_allclose(out["C"][:, 0, 0], Ct[:, 0, 0])
+    # depth culling: surface in front of the Gaussian (d >= D_t + eps)
+    out2 = oracle.composite(rec, Ct, np.full_like(Dt, 1.19), eps=0.01)
+    np.testing.assert_array_equal(out2["C"], Ct)
+    out3 = oracle.composite(rec, Ct, np.full_like(Dt, 1.19), eps=0.0101)
+    assert out3["W"][20, 24] > 0
+    # a pixel with no ray-cast hit (D_t = 0) never culls
+    out4 = oracle.composite(rec, Ct, np.zeros_like(Dt), eps=0.01)
+    assert out4["W"][20, 24] > 0
+
+
+def test_composite_two_gaussians_by_hand_and_ALPHA():
+    g = gset([[0.0, 0.0, 1.0], [0.004, 0.0, 1.5]], 0.03, logits=[0.5, -0.2],
+             rgb=[[1, 0, 0], [0, 0, 1]])
+    rec, _ = oracle.project(g, cam_axis())
+    Ct, Dt = flat_inputs()
+    x, y = 24, 20
+    a1, a2 = alpha_at(rec[0], x, y), alpha_at(rec[1], x, y)
+    out = oracle.composite(rec, Ct, Dt, eps=0.01, mode=oracle.OIT)
+    exp_c = (Ct[:, y, x] + a1 * np.array([1, 0, 0]) + a2 * np.array([0, 0, 1])) / (1 + a1 + a2)
+    np.testing.assert_allclose(out["C"][:, y, x], exp_c, rtol=1e-14)
+    out = oracle.composite(rec, Ct, Dt, eps=0.01, mode=oracle.ALPHA)
+    # front to back: Gaussian 0 (d = 1.0) then Gaussian 1 (d = 1.5)
+    T1 = 1 - a1
+    exp_c = a1 * np.array([1, 0, 0]) + a2 * T1 * np.array([0, 0, 1]) + T1 * (1 - a2) * Ct[:, y, x]
+    np.testing.assert_allclose(out["C"][:, y, x], exp_c, rtol=1e-14)
+    np.testing.assert_allclose(out["T"][y, x], T1 * (1 - a2), rtol=1e-14)
+    np.testing.assert_allclose(out["D"][y, x], a1 * 1.0 + a2 * T1 * 1.5 + T1 * (1 - a2) * 2.0,
+                               rtol=1e-14)
+
+
+def test_ALPHA_opaque_limit_and_termination_count():
+    # sigma -> 1 at the centre: alpha clamps to 0.99
+    g = gset([0, 0, 1.0], 0.03, logits=[40.0], rgb=[[0.3, 0.6, 0.9]])
+    rec, _ = oracle.project(g, cam_axis())
+    Ct, Dt = flat_inputs()
+    out = oracle.composite(rec, Ct, Dt, 0.01, mode=oracle.ALPHA)
+    np.testing.assert_allclose(out["C"][:, 20, 24], 0.99 * np.array([0.3, 0.6, 0.9]) +
+                               0.01 * Ct[:, 20, 24], rtol=1e-13)
+    # 20 identical Gaussians with alpha = 0.5 exactly at the pixel centre:
+    # T after k = 0.5^k; the 14th would give 0.5^14 < 1e-4, so 13 are counted.
+    M = 20
+    g = gset(np.tile([0, 0, 1.0], (M, 1)) + np.arange(M)[:, None] * [0, 0, 1e-3], 0.03,
+             logits=np.zeros(M))
+    rec, _ = oracle.project(g, cam_axis())
+    out = oracle.composite(rec, Ct, Dt, 0.01, mode=oracle.ALPHA)
+    assert out["n"][20, 24] == 13
+    np.testing.assert_allclose(out["T"][20, 24], 0.5 ** 13, rtol=1e-12)
+
+
+def test_composite_empty_set_and_eps_limits():
+    w = workloads.tiny(M=40)
+    f = w.frames[0]
+    cam = f.cam
+    rec, _ = oracle.project(w.gaussians.astype(np.float64), cam)
+    Ct = np.random.default_rng(0).uniform(size=(3, cam.height, cam.width))
+    Dt = f.depth.astype(np.float64)
+    out0 = oracle.composite(rec[:0], Ct, Dt, 0.01)
+    np.testing.assert_array_equal(out0["C"], Ct)
+    np.testing.assert_array_equal(out0["D"], Dt)
+    outm = oracle.composite(rec, Ct, np.where(Dt > 0, Dt, 1.0), -1e9)
+    np.testing.assert_array_equal(outm["C"], Ct)
+    # eps -> +inf: nothing is culled, equals D_t = 0 everywhere (no culling)
+    outp = oracle.composite(rec, Ct, np.where(Dt > 0, Dt, 1.0), 1e9)
+    outz = oracle.composite(rec, Ct, np.zeros_like(Dt), 0.01)
+    np.testing.assert_allclose(outp["C"], outz["C"], rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("mode", [oracle.OIT, oracle.ALPHA])
+@pytest.mark.parametrize("f32", [False, True])
+def test_composite_bbox_path_equals_brute_force(mode, f32):
+    w = workloads.tiny(M=64)
+    cam = w.frames[0].cam
+    rec, _ = oracle.project(w.gaussians.astype(np.float64), cam)
+    if f32:
+        rec = oracle.rounded(rec)
+    Ct = np.random.default_rng(1).uniform(size=(3, cam.height, cam.width))
+    Dt = w.frames[0].depth.astype(np.float64)
+    a = oracle.composite(rec, Ct, Dt, 0.01, mode, f32)
+    b = oracle.composite(rec, Ct, Dt, 0.01, mode, f32, brute=True)
+    assert a["n"].sum() > 100
+    for k in ("C", "D", "W", "T", "n"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_OIT_permutation_invariance():
+    w = workloads.tiny(M=64)
+    cam = w.frames[0].cam
+    g = w.gaussians.astype(np.float64)
+    perm = np.random.default_rng(3).permutation(g.M)
+    gp = GaussianSet(*(a[perm] for a in g.arrays()))
+    Ct = np.random.default_rng(1).uniform(size=(3, cam.height, cam.width))
+    Dt = w.frames[0].depth.astype(np.float64)
+    a = oracle.composite(oracle.project(g, cam)[0], Ct, Dt, 0.01)
+    b = oracle.composite(oracle.project(gp, cam)[0], Ct, Dt, 0.01)
+    np.testing.assert_allclose(a["C"], b["C"], rtol=1e-13)
+    np.testing.assert_allclose(a["W"], b["W"], rtol=1e-13)
+
+
+# ----------------------------------------------------------------------- loss
+def test_loss_matches_torch_l1():
+    rng = np.random.default_rng(5)
+    H, W = 12, 17
+    C, Ct_ = rng.uniform(size=(3, H, W)), rng.uniform(size=(3, H, W))
+    D, Dtg = rng.uniform(1, 2, size=(H, W)), rng.uniform(1, 2, size=(H, W))
+    Dtg[0, :5] = 0
+    Dt = rng.uniform(1, 2, size=(H, W))
+    Dt[3, 3:9] = 0
+    lam = 0.7
+    L, dC, dD, nv, _ = oracle.loss(C, D, Ct_, Dtg, Dt, lam)
+    valid = torch.from_numpy((Dtg > 0) & (Dt > 0))
+    tC = torch.tensor(C, requires_grad=True)
+    tD = torch.tensor(D, requires_grad=True)
+    ref = torch.nn.functional.l1_loss(tC[:, valid], torch.from_numpy(Ct_)[:, valid]) + \
+        lam * torch.nn.functional.l1_loss(tD[valid], torch.from_numpy(Dtg)[valid])
+    ref.backward()
+    assert nv == int(valid.sum())
+    np.testing.assert_allclose(L, ref.item(), rtol=1e-14)
+    np.testing.assert_allclose(dC, tC.grad.numpy(), rtol=1e-14, atol=1e-18)
+    np.testing.assert_allclose(dD, tD.grad.numpy(), rtol=1e-14, atol=1e-18)
+
+
+# ------------------------------------------------------------------ adjoints
+def test_single_gaussian_rgb_gradient_closed_form():
+    g = gset([0.0, 0.01, 1.2], 0.02, logits=[0.1], rgb=[[0.8, 0.2, 0.5]])
+    cam = cam_axis()
+    Ct, Dt = flat_inputs()
+    Ctgt = np.zeros_like(Ct)  # C* > target everywhere: sign = +1
+    r = oracle.render_loss_grads(g, cam, Ct, Dt, Ctgt, np.full_like(Dt, 2.0))
+    rec = r["rec"][0]
+    nv = r["n_valid"]
+    exp = 0.0
+    for y in range(H_IMG):
+        for x in range(W_IMG):
+            a = alpha_at(rec, x, y)
+            if a >= 1 / 255:
+                exp += a / (1 + a) / (3 * nv)
+    np.testing.assert_allclose(r["grads"]["rgb"][0], [exp] * 3, rtol=1e-13)
+
+
+def test_isotropic_rotation_gradient_is_zero():
+    w = workloads.tiny(M=20)
+    g = w.gaussians.astype(np.float64)
+    g.log_scales[:] = g.log_scales[:, :1]  # isotropic
+    f = w.frames[0]
+    Ct = np.random.default_rng(2).uniform(size=(3, f.cam.height, f.cam.width))
+    Dt = f.depth.astype(np.float64)
+    r = oracle.render_loss_grads(g, f.cam, Ct, Dt, f.rgb, f.depth, lambda_depth=1.0)
+    assert np.abs(r["grads"]["means"]).max() > 0
+    assert np.abs(r["grads"]["quats"]).max() < 1e-12 * np.abs(r["grads"]["means"]).max()
+
+
+def _fd_case(mode):
+    w = workloads.grad(M=600, width=64, height=48)
+    f = w.frames[0]
+    g = w.gaussians.astype(np.float64)
+    g.log_scales += 0.8  # larger footprints at this small resolution
+    rng = np.random.default_rng(4)
+    Ct = np.clip(f.rgb + rng.normal(0, 0.1, size=f.rgb.shape), 0, 1).astype(np.float64)
+    Dt = f.depth.astype(np.float64)
+    return w, f, g, Ct, Dt
+
+
+@pytest.mark.parametrize("mode", [oracle.OIT, oracle.ALPHA])
+def test_backward_matches_central_finite_differences(mode):
+    """Analytic adjoint vs central differences (h = 1e-5, FP64) on random
+    parameters whose +-h perturbation leaves every discrete decision (counted
+    sets, loss signs) unchanged."""
+    w, f, g, Ct, Dt = _fd_case(mode)
+    cam = f.cam
+    lam = 1.0
+    base = oracle.render_loss_grads(g, cam, Ct, Dt, f.rgb, f.depth, lambda_depth=lam, mode=mode)
+    rec0 = base["rec"]
+    names = ["means", "log_scales", "quats", "opacity_logits", "rgb"]
+    rng = np.random.default_rng(11)
+    vis = np.nonzero(rec0[:, oracle.R_VIS] > 0)[0]
+    h = 1e-5
+    checked, worst = 0, 0.0
+    attempts = 0
+    while checked < 60 and attempts < 400:
+        attempts += 1
+        i = int(rng.choice(vis))
+        name = names[rng.integers(0, 5)]
+        arr = getattr(g, name)
+        k = int(rng.integers(0, arr.shape[1])) if arr.ndim == 2 else None
+        Ls, sig = [], []
+        for sgn in (+1, -1):
+            gp = GaussianSet(*(a.copy() for a in g.arrays()))
+            a = getattr(gp, name)
+            if k is None:
+                a[i] += sgn * h
+            else:
+                a[i, k] += sgn * h
+            rec1, _ = oracle.project(GaussianSet(*(x[i:i + 1] for x in gp.arrays())), cam)
+            rec = rec0.copy()
+            rec[i] = rec1[0]
+            ext = max(rec0[i, oracle.R_EX], rec1[0, oracle.R_EX]) + 3
+            eyt = max(rec0[i, oracle.R_EY], rec1[0, oracle.R_EY]) + 3
+            mx, my = rec0[i, oracle.R_MX], rec0[i, oracle.R_MY]
+            win = (max(0, int(mx - ext)), min(cam.width - 1, int(mx + ext) + 1),
+                   max(0, int(my - eyt)), min(cam.height - 1, int(my + eyt) + 1))
+            o = oracle.composite(rec, Ct, Dt, w.eps_depth, mode, window=win)
+            C = base["out"]["C"].copy()
+            D = base["out"]["D"].copy()
+            n = base["out"]["n"].copy()
+            x0, x1, y0, y1 = win
+            C[:, y0:y1 + 1, x0:x1 + 1] = o["C"][:, y0:y1 + 1, x0:x1 + 1]
+            D[y0:y1 + 1, x0:x1 + 1] = o["D"][y0:y1 + 1, x0:x1 + 1]
+            n[y0:y1 + 1, x0:x1 + 1] = o["n"][y0:y1 + 1, x0:x1 + 1]
+            L, dC, dD, _, _ = oracle.loss(C, D, f.rgb, f.depth, Dt, lam)
+            Ls.append(L)
+            sig.append((n.tobytes(), np.sign(C - f.rgb).tobytes(), np.sign(D - f.depth).tobytes()))
+        ref_sig = (base["out"]["n"].tobytes(), np.sign(base["out"]["C"] - f.rgb).tobytes(),
+                   np.sign(base["out"]["D"] - f.depth).tobytes())
+        if sig[0] != ref_sig or sig[1] != ref_sig:
+            continue  # a discrete event changed inside [-h, h]
+        fd = (Ls[0] - Ls[1]) / (2 * h)
+        an = base["grads"][name][i] if k is None else base["grads"][name][i, k]
+        scale = max(abs(an), 1e-9)
+        err = abs(fd - an) / scale
+        if abs(an) > 1e-7:
+            worst = max(worst, err)
+            assert err < 1e-4, (name, i, k, fd, an)
+            checked += 1
+    assert checked >= 40, checked
+    print("fd checked", checked, "worst rel", worst)
+
+
+# ------------------------------------------------------------------- binning
+def test_bin_matches_brute_force_enumeration():
+    w = workloads.tiny(M=64)
+    cam = w.frames[0].cam
+    rec, _ = oracle.project(w.gaussians.astype(np.float64), cam)
+    r32 = oracle.records_f32(rec)
+    TW, TH = 16, 8
+    keys, vals, ranges = oracle.bin_records(r32, cam.width, cam.height, TW, TH)
+    ntx = -(-cam.width // TW)
+    exp = []
+    for i, r in enumerate(r32):
+        if r[11] < 0:
+            continue
+        xs = [px for px in range(cam.width) if np.float32(r[0] - r[11]) <= px <= np.float32(r[0] + r[11])]
+        ys = [py for py in range(cam.height) if np.float32(r[1] - r[12]) <= py <= np.float32(r[1] + r[12])]
+        if not xs or not ys:
+            continue
+        tiles = sorted({(py // TH) * ntx + px // TW for px in xs for py in ys})
+        dbits = int(np.float32(r[2]).view(np.uint32))
+        exp += [((t << 32) | dbits, i) for t in tiles]
+    exp.sort()
+    assert len(exp) == len(keys) > 50
+    np.testing.assert_array_equal(keys, np.array([e[0] for e in exp], np.uint64))
+    np.testing.assert_array_equal(vals, np.array([e[1] for e in exp], np.uint32))
+    for t in range(ranges.shape[0]):
+        sel = [k for k, e in enumerate(exp) if e[0] >> 32 == t]
+        if sel:
+            assert (ranges[t, 0], ranges[t, 1]) == (sel[0], sel[-1] + 1)
+
+
+# ---------------------------------------------------------------------- Adam
+def test_adam_matches_torch():
+    rng = np.random.default_rng(9)
+    n = 257
+    p0 = rng.normal(size=n)
+    grads = [rng.normal(size=n) for _ in range(5)]
+    lr = 1.6e-4
+    tp = torch.tensor(p0.copy(), requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=lr, betas=(0.9, 0.999), eps=1e-15)
+    p, m, v = p0.copy(), np.zeros(n), np.zeros(n)
+    for step, gr in enumerate(grads, 1):
+        tp.grad = torch.tensor(gr)
+        opt.step()
+        oracle.adam(p, gr, m, v, lr, 0.9, 0.999, 1e-15, step)
+    np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-14, atol=1e-16)
