@@ -1,0 +1,551 @@
+#!/usr/bin/env python
+"""Benchmark of the Gaussian-plus-SDF hot path on one or more B300s.
+
+Workload (synthetic stand-in for the paper's Kinect-class sequences): a
+2.56 m room with six walls and 20 random boxes / spheres, 30 RGB-D frames at
+640x480 (fx = fy = 560) along a smooth camera path, a dense 256^3 TSDF at
+1 cm, 100,000 Gaussians, 10 fwd+bwd+Adam iterations per frame.
+
+One step = one frame: fuse_frame + raycast_sdf + 10 x (render_forward with
+the fused L1 loss, render_backward, adam_step), all through the C ABI.  The
+timed form replays one CUDA graph per frame; the plain (uncaptured) form is
+timed beside it.  value = iterations / s over whole steps (fusion and ray-cast
+included); ms_per_step = ms per frame.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (its own scene seed): no data-path collective, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ITERS_PER_FRAME = 10
+N_FRAMES = 30
+M_GAUSS = 100_000
+METRIC = "fwd+bwd+Adam iterations/sec (640x480, 100k Gaussians)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--mode", default="oit", choices=["oit", "alpha"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--frames", type=int, default=N_FRAMES)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- workload
+def make_workload(rank: int, n_frames: int):
+    from datagen import workloads
+    return workloads.room(n_frames=n_frames, M=M_GAUSS, seed_scene=2 + 1000 * rank,
+                          seed_path=3 + 1000 * rank)
+
+
+class GpuPipeline:
+    """Device-resident state of one replica and the per-frame step."""
+
+    def __init__(self, w, tile, mode, device):
+        import torch
+        import paper_2509_11574_b300 as gps
+        self.gps, self.torch = gps, torch
+        self.w = w
+        self.dev = device
+        self.frames = [(torch.from_numpy(f.depth).to(device), torch.from_numpy(f.rgb).to(device))
+                       for f in w.frames]
+        self.cams = [f.cam for f in w.frames]
+        H, W = self.cams[0].height, self.cams[0].width
+        self.vol = gps.Tsdf(w.tsdf, device)
+        self.g0 = gps.Gaussians.from_numpy(w.gaussians, device)
+        self.g = gps.Gaussians(*[t.clone() for t in self.g0.tensors()])
+        self.grads = self.g.zeros_like()
+        self.opt = gps.Adam(self.g, device_step=True)
+        self.s = gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, near=w.near,
+                              blend_mode=gps.BLEND_ALPHA if mode == "alpha" else gps.BLEND_OIT,
+                              tile=tile, pair_capacity=64 * w.gaussians.M)
+        self.r = gps.Renderer(w.gaussians.M, self.cams[:1], self.s, device)
+        self.Ct = torch.zeros(3, H, W, device=device)
+        self.Dt = torch.zeros(H, W, device=device)
+        self.loss = torch.zeros(ITERS_PER_FRAME, device=device)
+        self.graphs = {}
+
+    def reset(self):
+        self.vol.reset()
+        for a, b in zip(self.g.tensors(), self.g0.tensors()):
+            a.copy_(b)
+        for t in self.grads.tensors() + self.opt.m.tensors() + self.opt.v.tensors():
+            t.zero_()
+        self.opt.device_step.zero_()
+
+    def view(self, k):
+        d, c = self.frames[k]
+        return self.gps.View(self.cams[k], self.Ct, self.Dt, c, d)
+
+    def step(self, k, stream=None, stage_events=None):
+        gps = self.gps
+        d, c = self.frames[k]
+        gps.fuse_frame(self.vol, d, c, self.cams[k], stream)
+        gps.raycast_sdf(self.vol, self.cams[k], self.w.near, 0.0, self.Ct, self.Dt, None, stream)
+        v = [self.view(k)]
+        for it in range(ITERS_PER_FRAME):
+            if stage_events is None:
+                gps.render_forward(self.g, v, self.s, self.r.ws, self.loss[it:it + 1], stream)
+                gps.render_backward(self.g, v, self.s, self.r.ws, self.grads, None, stream)
+                self.opt.step(self.grads, stream)
+            else:
+                self._staged_iteration(v, it, stage_events, stream)
+                e0 = self.torch.cuda.Event(enable_timing=True)
+                e1 = self.torch.cuda.Event(enable_timing=True)
+                e0.record()
+                self.opt.step(self.grads, stream)
+                e1.record()
+                stage_events.setdefault("adam", []).append((e0, e1))
+
+    def _staged_iteration(self, v, it, ev, stream):
+        import dataclasses
+        gps = self.gps
+        parts = [("project+bin", gps.STAGE_PROJECT | gps.STAGE_BIN, "f"),
+                 ("composite_fwd", gps.STAGE_COMPOSITE, "f"),
+                 ("composite_bwd", gps.STAGE_COMPOSITE_BWD, "b"),
+                 ("project_bwd", gps.STAGE_PROJECT_BWD, "b")]
+        for name, stg, kind in parts:
+            s = gps.GpsRenderSettings.from_buffer_copy(self.s)
+            s.stages = stg
+            e0 = self.torch.cuda.Event(enable_timing=True)
+            e1 = self.torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if kind == "f":
+                gps.render_forward(self.g, v, s, self.r.ws, self.loss[it:it + 1], stream)
+            else:
+                gps.render_backward(self.g, v, s, self.r.ws, self.grads, None, stream)
+            e1.record()
+            ev.setdefault(name, []).append((e0, e1))
+
+    def capture(self, k):
+        torch = self.torch
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step(k)  # warm the path once on the side stream
+        torch.cuda.current_stream().wait_stream(s)
+        with torch.cuda.graph(g):
+            self.step(k)
+        self.graphs[k] = g
+        return g
+
+
+def kernels_per_step(mode):
+    # fuse, raycast + per iteration: project, scan, emit, sort, composite, finalize,
+    # composite_bwd, project_bwd, adam, step counter
+    return 2 + ITERS_PER_FRAME * 10
+
+
+def count_evaluations(pipe, k):
+    """Untimed instrumented pass: Gaussian-pixel evaluations of one iteration."""
+    import numpy as np
+    gps, torch = pipe.gps, pipe.torch
+    s = gps.GpsRenderSettings.from_buffer_copy(pipe.s)
+    s.instrument = 1
+    v = [pipe.view(k)]
+    g = gps.Gaussians(*[t.clone() for t in pipe.g.tensors()])
+    grads = g.zeros_like()
+    gps.render_forward(g, v, s, pipe.r.ws, pipe.loss[:1])
+    gps.render_backward(g, v, s, pipe.r.ws, grads)
+    torch.cuda.synchronize()
+    L = pipe.r.layout(0)
+    raw = pipe.r.ws[L.view_scalars:L.view_scalars + 64].cpu().numpy()
+    sc = raw[:32].view(np.float32)
+    ctr = raw[32:64].view(np.uint64)
+    return {"pairs": float(sc[4]), "fwd_tested": int(ctr[0]), "fwd_counted": int(ctr[1]),
+            "bwd_tested": int(ctr[2]), "bwd_counted": int(ctr[3]), "n_valid": float(sc[3])}
+
+
+# FP32 operations per evaluation, counted from the kernels' arithmetic (an FMA = 2):
+# forward counted: dx, dy, q (7), exp argument + exp, alpha, 5 accumulations (10) = 22
+# backward counted: dx, q (7), exp (2), alpha, 4 colour/depth FMAs (8), dL/dalpha (8),
+#                   d sigma (2), v, 2 products, 5 moment FMAs (12) = 41
+FLOP_FWD, FLOP_BWD = 22, 41
+
+
+def fp32_peak_tflops(sm_count, mhz):
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import paper_2509_11574_b300 as gps
+    from paper_2509_11574_b300 import build
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    gps.lib()
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    t0 = time.time()
+    w = make_workload(rank, args.frames)
+    gen_s = time.time() - t0
+    pipe = GpuPipeline(w, tile, args.mode, dev)
+    nF = len(w.frames)
+    K, Wu = args.steps, args.warmup
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # capture one graph per frame (setup, untimed)
+    for k in range(min(nF, K + Wu)):
+        pipe.capture(k)
+    pipe.reset()
+    torch.cuda.synchronize()
+
+    def timed_loop(replay: bool):
+        times = []
+        for i in range(Wu + K):
+            k = i % nF
+            flush.zero_()  # write 256 MB > L2 between steps (untimed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if replay:
+                pipe.graphs[k].replay()
+            else:
+                pipe.step(k)
+            e1.record()
+            if i >= Wu:
+                times.append((e0, e1))
+        return times
+
+    # ---- headline: graph replay
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_id = vis.split(",")[local].strip() if vis else str(local)
+    clocks = ClockSampler(smi_id)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.time()
+    ev = timed_loop(True)
+    torch.cuda.synchronize()
+    wall = time.time() - wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    status = pipe.r.status()
+    losses = pipe.loss.cpu().numpy().tolist()
+
+    # ---- plain form (no graph), same process
+    pipe.reset()
+    torch.cuda.synchronize()
+    ev_plain = timed_loop(False)
+    torch.cuda.synchronize()
+    plain_ms = [a.elapsed_time(b) for a, b in ev_plain]
+
+    # ---- per-stage events over a timed run of the plain form (dominant kernel)
+    pipe.reset()
+    stage_ev = {}
+    for i in range(Wu + min(K, 10)):
+        pipe.step(i % nF, stage_events=stage_ev if i >= Wu else None)
+    torch.cuda.synchronize()
+    stage_ms = {n: statistics.mean(a.elapsed_time(b) for a, b in v) for n, v in stage_ev.items()}
+    counts = count_evaluations(pipe, (Wu + min(K, 10) - 1) % nF)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = [(torch.from_numpy(f.depth).pin_memory(), torch.from_numpy(f.rgb).pin_memory()) for f in w.frames]
+        loss_host = torch.zeros(ITERS_PER_FRAME, pin_memory=True)
+        pipe.reset()
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for i in range(Wu + K):
+            k = i % nF
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pipe.frames[k][0].copy_(host[k][0], non_blocking=True)
+            pipe.frames[k][1].copy_(host[k][1], non_blocking=True)
+            pipe.graphs[k].replay()
+            loss_host.copy_(pipe.loss, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            if i >= Wu:
+                e2e_ms.append(e0.elapsed_time(e1))
+        h2d = host[0][0].numel() * 4 + host[0][1].numel() * 4
+        e2e = {"value": ITERS_PER_FRAME * K / (sum(e2e_ms) / 1e3) * world, "unit": "iterations/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": ITERS_PER_FRAME * 4}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    props = torch.cuda.get_device_properties(dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    value = ITERS_PER_FRAME * K / total_s * world
+    # ---- roofline of the dominant kernel
+    dom = max(stage_ms, key=stage_ms.get)
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    peak_tf = fp32_peak_tflops(props.multi_processor_count, peaks.get("sm_max_mhz", 2032.0))
+    if dom == "composite_bwd":
+        flops = counts["bwd_counted"] * FLOP_BWD
+    elif dom == "composite_fwd":
+        flops = counts["fwd_counted"] * FLOP_FWD
+    else:
+        flops = None
+    achieved = flops / (stage_ms[dom] * 1e-3) / 1e12 if flops else None
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            ent = tj.get(dom)
+            if ent and ent.get("source_sha") == _source_sha(ent.get("source")):
+                traffic = ent.get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": (achieved / peak_tf) if achieved else None,
+                "traffic": traffic,
+                "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 x "
+                              f"{peaks.get('sm_max_mhz', 2032.0):.0f} MHz (max SM clock)",
+                "units": f"{counts['bwd_counted'] if dom == 'composite_bwd' else counts['fwd_counted']} "
+                         f"counted Gaussian-pixel evaluations x {FLOP_BWD if dom == 'composite_bwd' else FLOP_FWD} flop"}
+    # HBM fraction of the whole iteration against the algorithmic-bytes model
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    it_bytes = _iteration_bytes(w, counts)
+    it_ms = sum(stage_ms.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world, "steps": K,
+        "warmup": Wu, "ms_per_step": sum(step_ms) / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"room 2.56 m, {nF} frames 640x480, 256^3 TSDF at 1 cm, "
+                               f"{M_GAUSS} Gaussians, {ITERS_PER_FRAME} iterations/frame",
+                   "blend": args.mode, "tile": args.tile, "form": "CUDA graph per frame",
+                   "l2": "256 MB buffer written between steps (untimed)",
+                   "parallelism": f"{world} independent replicas"},
+        "ms_per_frame": sum(step_ms) / K,
+        "plain_ms_per_frame": sum(plain_ms) / K,
+        "graph_speedup_vs_plain": (sum(plain_ms) / sum(step_ms)),
+        "stage_ms": stage_ms,
+        "evaluations": counts,
+        "hbm_model": {"bytes_per_iteration": it_bytes, "peak_gbs": hbm,
+                      "frac_at_iteration_time": it_bytes / (it_ms * 1e-3) / 1e9 / hbm if it_ms else None},
+        "roofline": roofline,
+        "clocks": clk, "gpu_launches": kernels_per_step(args.mode) * K,
+        "status": status, "last_frame_losses": losses[-3:], "wall_s": wall,
+        "gen_s": gen_s, "gpu": props.name,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _source_sha(rel):
+    import hashlib
+    if not rel:
+        return None
+    p = os.path.join(ROOT, rel)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] if os.path.exists(p) else None
+
+
+def _iteration_bytes(w, counts):
+    """Algorithmic bytes of one iteration (model: per visible Gaussian 324 B,
+    Adam 392 B per Gaussian, 104 B per pixel, 36 B per (tile, Gaussian) pair)."""
+    M = w.gaussians.M
+    npx = w.frames[0].cam.width * w.frames[0].cam.height
+    return M * 324 + M * 392 + npx * 104 + counts["pairs"] * 36
+
+
+# ---------------------------------------------------------------- oracle arm
+def _oracle_iteration(w, frame, band, lam):
+    """The FP64 oracle on a horizontal band of rows of one frame: projection,
+    composite, loss and adjoints (band restricts the pixel work)."""
+    import numpy as np
+    import oracle
+    f = w.frames[frame]
+    H, W = f.cam.height, f.cam.width
+    vol = _oracle_iteration.vol
+    Ct, Dt = _oracle_iteration.sdf
+    g = w.gaussians.astype(np.float64)
+    rec, _ = oracle.project(g, f.cam, w.near)
+    y0, y1 = band
+    out = oracle.composite(rec, Ct, Dt, w.eps_depth, oracle.OIT, window=(0, W - 1, y0, y1))
+    Ctgt = np.zeros_like(f.rgb, dtype=np.float64)
+    Dtgt = np.zeros_like(f.depth, dtype=np.float64)
+    Ctgt[:, y0:y1 + 1] = f.rgb[:, y0:y1 + 1]
+    Dtgt[y0:y1 + 1] = f.depth[y0:y1 + 1]
+    L, dC, dD, nv, _ = oracle.loss(out["C"], out["D"], Ctgt, Dtgt, Dt, lam)
+    g2 = oracle.composite_backward(rec, Ct, Dt, w.eps_depth, dC, dD)
+    gr = oracle.project_backward(g, f.cam, g2, w.near)
+    p = np.concatenate([a.reshape(-1) for a in g.arrays()])
+    gg = np.concatenate([gr[k].reshape(-1) for k in ("means", "log_scales", "quats", "opacity_logits", "rgb")])
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    oracle.adam(p, gg, m, v, 1e-3)
+    return L
+
+
+def _oracle_setup(w):
+    import numpy as np
+    import oracle
+    f = w.frames[0]
+    vol = oracle.Volume(w.tsdf)
+    oracle.fuse(vol, f.depth, f.rgb, f.cam)
+    Ct, Dt, _, _ = oracle.raycast(w.tsdf, vol.sdf, vol.rgb, f.cam)
+    _oracle_iteration.vol = vol
+    _oracle_iteration.sdf = (Ct.astype(np.float32).astype(np.float64), Dt.astype(np.float32).astype(np.float64))
+
+
+BAND_ROWS = 60  # one eighth of the 480 rows per oracle sample
+
+
+def cpu_baseline(w):
+    """The oracle as it stands, on the host cores, on a bounded sample: one
+    iteration restricted to a band of 60 of the 480 rows (1/8 of the pixels;
+    projection and Adam over all 100k Gaussians)."""
+    import oracle
+    oracle.build()
+    _oracle_setup(w)
+    t0 = time.time()
+    _oracle_iteration(w, 0, (210, 210 + BAND_ROWS - 1), w.lambda_depth)
+    dt = time.time() - t0
+    frac = BAND_ROWS / w.frames[0].cam.height
+    return {"value": frac / dt, "unit": "iterations/s", "cores": _omp_threads(), "kind": "oracle",
+            "sample": f"one fwd+loss+bwd+Adam iteration of frame 0 restricted to rows 210-269 "
+                      f"(1/8 of 640x480; projection and Adam over all {w.gaussians.M} Gaussians), "
+                      f"scaled by 1/8 to iterations/s; took {dt:.1f} s"}
+
+
+def _omp_threads():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n and n.isdigit() else os.cpu_count()
+
+
+def run_reference(args, rank, world, local):
+    if rank != 0:
+        return
+    w = make_workload(0, args.frames)
+    import oracle
+    oracle.build()
+    _oracle_setup(w)
+    times = []
+    H = w.frames[0].cam.height
+    for i in range(args.warmup + args.steps):
+        y0 = (i * BAND_ROWS) % H
+        t0 = time.time()
+        _oracle_iteration(w, 0, (y0, y0 + BAND_ROWS - 1), w.lambda_depth)
+        if i >= args.warmup:
+            times.append(time.time() - t0)
+    frac = BAND_ROWS / H
+    value = frac * len(times) / sum(times)
+    cb = {"value": value, "unit": "iterations/s", "cores": _omp_threads(), "kind": "oracle",
+          "sample": f"each step: one iteration of frame 0 restricted to a {BAND_ROWS}-row band "
+                    f"(1/8 of the pixels), scaled by 1/8"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"room 2.56 m, 640x480, 256^3 TSDF at 1 cm, {M_GAUSS} Gaussians"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * gps.h - C ABI of the Gaussian-plus-SDF hot path (libgps.so, sm_103a).
+ *
+ * The library implements the per-frame Gaussian-overlay optimisation of
+ * Gaussian-plus-SDF reconstruction (arXiv 2509.11574): colourised TSDF fusion
+ * and SDF ray-casting (Sec. 3.1, Sec. 3.2.1) as supporting steps, then the
+ * hybrid render of Eq. 1-4 (or the sorted "with sort" variant of Table 7), the
+ * L1 loss (Eq. 6), its adjoint to every Gaussian parameter, and an Adam step
+ * with the learning rates of App. C.
+ *
+ * Conventions shared by every call
+ *   - All functions return int32_t status (GPS_OK = 0, negative on error) and
+ *     never throw.  On error `gps_last_error()` (thread-local) describes it.
+ *   - Device pointers are CUDA device addresses owned by the caller.  The
+ *     library allocates no device memory: scratch comes from a caller-provided
+ *     workspace sized by `gps_workspace_size`.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call only enqueues work on it and performs no host
+ *     synchronisation, so calls can be captured into a CUDA graph.
+ *     Errors discovered on the device (pair-buffer overflow, a bounded wait
+ *     that ran out) are recorded in the workspace status word and read with
+ *     `gps_query_status` after the stream has been synchronised.
+ *   - Camera frame: x right, y down, +z forward.  A pose is camera->world:
+ *     X_w = R X_c + t with R row-major, t the camera centre.  Pixel (i, j)
+ *     (column i, row j) has its centre at image coordinate (i, j):
+ *     u = fx x / z + cx.  Images are planar float32 [C][H][W]; depth is camera
+ *     z in metres, 0 = invalid / no surface.
+ *   - Gaussian parameters are float32 arrays: means [M][3], log_scales [M][3],
+ *     quats [M][4] (w, x, y, z; normalised inside), opacity_logits [M]
+ *     (sigma = sigmoid(logit)), rgb [M][3] (colour c_i used directly).
+ */
+#ifndef GPS_H_
+#define GPS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GPS_API __attribute__((visibility("default")))
+#else
+#define GPS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define GPS_OK 0
+#define GPS_ERR_INVALID_ARG (-1)         /* bad pointer, size or setting       */
+#define GPS_ERR_WORKSPACE_TOO_SMALL (-2) /* ws_bytes < gps_workspace_size()     */
+#define GPS_ERR_CAPACITY (-3)            /* more (tile, Gaussian) pairs than
+                                            pair_capacity; found on the device */
+#define GPS_ERR_CUDA (-4)                /* a CUDA launch / copy failed         */
+#define GPS_ERR_TIMEOUT (-5)             /* a bounded device wait gave up       */
+
+/* blend modes of the second rendering pass */
+#define GPS_BLEND_OIT 0   /* Eq. 1-4: order-independent, depth-culled, W_t = 1   */
+#define GPS_BLEND_ALPHA 1 /* Table 7 "with sort": front-to-back alpha over C_t  */
+
+/* storage precision of colour intermediates (transmittance, weights, loss,
+   gradients and Adam moments always accumulate in float32) */
+#define GPS_PREC_FP32 0
+#define GPS_PREC_FP16 1
+#define GPS_PREC_BF16 2
+
+/* stage mask (GpsRenderSettings.stages; 0 = all).  Tests use it to run one
+   stage on inputs they wrote into the workspace themselves. */
+#define GPS_STAGE_PROJECT 1        /* records from Gaussian parameters       */
+#define GPS_STAGE_BIN 2            /* tile lists from records                */
+#define GPS_STAGE_COMPOSITE 4      /* forward composite (+ fused loss)       */
+#define GPS_STAGE_COMPOSITE_BWD 8  /* per-Gaussian 2D gradients              */
+#define GPS_STAGE_PROJECT_BWD 16   /* 2D gradients -> parameter gradients    */
+
+/* ---------------------------------------------------------------- types */
+typedef struct GpsIntrinsics {
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} GpsIntrinsics;
+
+typedef struct GpsPose {
+  float R[9]; /* camera -> world rotation, row-major */
+  float t[3]; /* camera centre in world coordinates  */
+} GpsPose;
+
+/* Dense colourised TSDF (Sec. 3.1: every voxel stores d(p) and c(p)).
+ * nx, ny, nz must be positive multiples of 8.  Voxel (x, y, z) has its centre
+ * at origin + (x + 0.5, y + 0.5, z + 0.5) * voxel and is stored at the
+ * brick-major index
+ *     ((bz * (ny/8) + by) * (nx/8) + bx) * 512 + (z%8) * 64 + (y%8) * 8 + (x%8),
+ * (bx, by, bz) = (x/8, y/8, z/8), in three arrays:
+ *     sdf    float [n]    truncated signed distance / trunc, in [-1, 1]
+ *     weight float [n]    fusion weight (0 = never observed)
+ *     rgbw   float [n][4] colour (r, g, b) and its own weight.
+ * A fresh volume is sdf = 1, weight = 0, rgbw = 0 (caller-initialised). */
+typedef struct GpsTsdf {
+  int32_t nx, ny, nz;
+  float voxel;      /* edge length in metres           */
+  float origin[3];  /* world position of the grid corner */
+  float trunc;      /* truncation distance mu, metres  */
+  float max_weight; /* weight cap (e.g. 100)           */
+  float* sdf;
+  float* weight;
+  float* rgbw;
+} GpsTsdf;
+
+/* A Gaussian set, or a gradient / moment buffer of the same shape. */
+typedef struct GpsGaussians {
+  float* means;          /* [M][3] */
+  float* log_scales;     /* [M][3] */
+  float* quats;          /* [M][4] w, x, y, z */
+  float* opacity_logits; /* [M]    */
+  float* rgb;            /* [M][3] */
+  int32_t M;
+} GpsGaussians;
+
+/* One view of the second rendering pass.  Inputs are device images of this
+ * view's size; outputs are nullable device images written by render_forward. */
+typedef struct GpsView {
+  GpsIntrinsics K;
+  GpsPose T_wc;
+  const float* sdf_rgb;      /* C_t [3][H][W] from raycast_sdf (required)      */
+  const float* sdf_depth;    /* D_t [H][W]    from raycast_sdf (required)      */
+  const float* target_rgb;   /* C_k [3][H][W] observed colour; nullable        */
+  const float* target_depth; /* D_k [H][W]    observed depth; nullable         */
+  float* out_rgb;            /* C* [3][H][W]; nullable                          */
+  float* out_depth;          /* D* [H][W];    nullable                          */
+  float* out_weight;         /* W_G [H][W] (ALPHA: 1 - T_end); nullable         */
+  const float* grad_rgb;     /* dL/dC* [3][H][W] for render_backward; nullable  */
+  const float* grad_depth;   /* dL/dD* [H][W]   for render_backward; nullable  */
+} GpsView;
+
+typedef struct GpsRenderSettings {
+  float eps_depth;       /* epsilon of Eq. 1-2 (metres), e.g. 0.01            */
+  float lambda_depth;    /* weight of the depth L1 term (0 = colour only)      */
+  float near_plane;      /* Gaussians with camera z <= near are culled (0.2)  */
+  int32_t blend_mode;    /* GPS_BLEND_*                                        */
+  int32_t precision;     /* GPS_PREC_*                                         */
+  int32_t tile_w, tile_h;/* 0, 0 = 16 x 16; supported: 16x16, 16x8, 8x8, 32x8 */
+  int32_t deterministic; /* 1: fixed-order gradient reduction, no float atomics */
+  int32_t stages;        /* GPS_STAGE_* mask, 0 = all                          */
+  int32_t instrument;    /* 1: count Gaussian-pixel evaluations (slower; for
+                            measurement runs) into the view scalars           */
+  int64_t pair_capacity; /* (tile, Gaussian) pairs per view; 0 = 64 * M        */
+} GpsRenderSettings;
+
+/* Adam hyper-parameters; lr per group in the order means, log_scales, quats,
+ * opacity_logits, rgb (App. C: 1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3 * 0.28209479). */
+typedef struct GpsAdamHyper {
+  float lr[5];
+  float beta1, beta2, eps;
+} GpsAdamHyper;
+
+/* Byte offsets (from the workspace base) of the regions of view `v`.  The
+ * projected record of Gaussian i is 16 floats at records + 64 i:
+ *   mx, my, d, sigma, conic_a, conic_b, conic_c, qmax, r, g, b, ext_x, ext_y, 0, 0, 0
+ * with q = a dx^2 + 2 b dx dy + c dy^2, support {q <= qmax}, qmax =
+ * 2 ln(255 sigma), and a conservative half-extent ext (ext_x < 0: culled).
+ * Tile lists: keys u64 = bits(d) << 32 | index, sorted ascending inside each
+ * tile; ranges uint32 [tiles][2] = [start, end).  grad2d holds 12 floats per
+ * Gaussian: d/d(mx, my, conic_a, conic_b, conic_c, sigma, r, g, b, d), 0, 0. */
+typedef struct GpsWorkspaceLayout {
+  size_t total_bytes;
+  size_t status;        /* int32 status word (shared by all views)          */
+  size_t records;       /* float [M][16]                                    */
+  size_t tile_counts;   /* uint32 [tiles]                                   */
+  size_t tile_ranges;   /* uint32 [tiles][2]                                */
+  size_t pair_keys;     /* uint64 [pair_capacity]                           */
+  size_t pair_scratch;  /* uint64 [pair_capacity] (sort scratch)            */
+  size_t pix_state;     /* float [H*W][8] saved per-pixel forward state     */
+  size_t tile_partials; /* float [tiles][4] loss partial sums               */
+  size_t view_scalars;  /* float [8]: loss, colour sum, depth sum, N_valid,
+                           pairs; then uint64 [4] evaluation counters: forward
+                           tested, forward counted, backward tested, backward
+                           counted (instrument = 1)                           */
+  size_t grad2d;        /* float [M][12]                                    */
+  size_t pair_grads;    /* float [pair_capacity][12] (deterministic mode)   */
+  int32_t tiles_x, tiles_y, tile_w, tile_h;
+  int64_t pair_capacity;
+} GpsWorkspaceLayout;
+
+/* ---------------------------------------------------------------- calls */
+
+/* Last error message of the calling thread ("" if none). */
+GPS_API const char* gps_last_error(void);
+
+/* Library version string. */
+GPS_API const char* gps_version(void);
+
+/* Bytes of workspace needed by render_forward / render_backward for M Gaussians
+ * and these views (only K.width / K.height of each view are read).  The same
+ * workspace must be passed, unmodified between the two, to the forward and the
+ * backward of one iteration. */
+GPS_API int32_t gps_workspace_size(int32_t M, const GpsView* views, int32_t n_views,
+                           const GpsRenderSettings* settings, size_t* bytes);
+
+/* Region offsets of view `view` inside such a workspace (for inspection and tests). */
+GPS_API int32_t gps_workspace_layout(int32_t M, const GpsView* views, int32_t n_views,
+                             const GpsRenderSettings* settings, int32_t view,
+                             GpsWorkspaceLayout* out);
+
+/* Copy the workspace status word to *status (synchronises `stream`).
+ * Returns GPS_OK if the copy succeeded; *status holds the device-side code. */
+GPS_API int32_t gps_query_status(const void* ws, size_t ws_bytes, int32_t* status, void* stream);
+
+/* Fuse one RGB-D frame into the TSDF (Sec. 3.2.1 "SDF fusion", KinectFusion /
+ * InfiniTAM rule).  For every voxel centre with camera depth z > 0 projecting
+ * to the nearest pixel floor(u + 0.5), floor(v + 0.5) inside the image with
+ * depth D > 0: eta = D - z; if eta >= -trunc, sdf <- (w sdf + min(1, eta/trunc))
+ * / (w + 1), w <- min(w + 1, max_weight); if |eta| < trunc the colour is
+ * averaged with its own weight likewise.  depth [H][W], rgb [3][H][W] are
+ * device images of size K.  In-place on vol. */
+GPS_API int32_t fuse_frame(GpsTsdf* vol, const float* depth, const float* rgb, const GpsIntrinsics* K,
+                   const GpsPose* T_wc, void* stream);
+
+/* Ray-cast the TSDF (Sec. 3.1 first pass).  Per pixel, march the ray from
+ * max(near, entry into the voxel-centre box) to min(far, exit) (far <= 0: exit)
+ * with step max(min(f, 1) trunc, voxel / 2) on the trilinear sdf f; at the first
+ * f_a > 0 >= f_b refine by the secant; D_t = camera z of the hit V^g, C_t = the
+ * trilinear colour of the 8 neighbouring voxels.  No hit: 0.  Outputs:
+ * out_rgb [3][H][W], out_depth [H][W], out_vertex [H][W][3] world (nullable). */
+GPS_API int32_t raycast_sdf(const GpsTsdf* vol, const GpsIntrinsics* K, const GpsPose* T_wc,
+                    float near_plane, float far_plane, float* out_rgb, float* out_depth,
+                    float* out_vertex, void* stream);
+
+/* Second rendering pass and blend (Eq. 1-4, or Table 7's sorted variant) for
+ * n_views views, and, when every view has target_rgb and target_depth, the
+ * fused L1 loss (Eq. 6) written to *loss (device float, nullable):
+ *   L = sum_v [ sum |C* - C_k| / (3 N_v) + lambda_depth sum |D* - D_k| / N_v ]
+ * over pixels with D_k > 0 and D_t > 0 (N_v of them).  Writes the views'
+ * non-null outputs and the state render_backward needs into the workspace. */
+GPS_API int32_t render_forward(const GpsGaussians* gaussians, const GpsView* views, int32_t n_views,
+                       const GpsRenderSettings* settings, void* ws, size_t ws_bytes,
+                       float* loss, void* stream);
+
+/* Adjoint of render_forward: accumulates (+=) dL/d(parameters) into `grads`.
+ * Upstream gradients: each view's grad_rgb / grad_depth if given, else the
+ * derivative of the fused L1 loss (sign(C* - C_k) / (3 N_v), ...) scaled by
+ * *dloss (device float; NULL = 1).  Needs the workspace of the matching
+ * forward call with the same arguments. */
+GPS_API int32_t render_backward(const GpsGaussians* gaussians, const GpsView* views, int32_t n_views,
+                        const GpsRenderSettings* settings, void* ws, size_t ws_bytes,
+                        const float* dloss, GpsGaussians* grads, void* stream);
+
+/* Adam step (App. C learning rates, torch.optim.Adam semantics) on all five
+ * groups; grads are zeroed in the same pass.  step is the 1-based step number;
+ * if step <= 0 the step number is read from *device_step (int32, device),
+ * incremented first, so a captured graph can replay it. */
+GPS_API int32_t adam_step(GpsGaussians* params, GpsGaussians* grads, GpsGaussians* m, GpsGaussians* v,
+                  const GpsAdamHyper* hyper, int32_t step, int32_t* device_step, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPS_H_ */

@@ -149,19 +149,23 @@ def project(g, cam, near=0.2):
 
 def composite(rec, Ct, Dt, eps, mode=OIT, f32=False, brute=False, window=None):
     """Eq. 1-4 (mode OIT) or the Table 7 variant (mode ALPHA) for one view.
-    Returns dict C [3][H][W], D, W (= W_G), T (T_end), n (counted), amb."""
+    Returns dict C [3][H][W], D, W (= W_G), T (T_end), n (counted), amb, and
+    margin: per pixel, the smallest relative distance of a counting decision
+    (alpha vs 1/255, d vs D_t + eps) to its threshold."""
     Ct = _f64(Ct)
     Dt = _f64(Dt)
     H, W = Dt.shape
     x0, x1, y0, y1 = window if window is not None else (0, W - 1, 0, H - 1)
     rec = _f64(rec)
     out = dict(C=np.zeros((3, H, W)), D=np.zeros((H, W)), W=np.zeros((H, W)),
-               T=np.zeros((H, W)), n=np.zeros((H, W), np.int32), amb=np.zeros((H, W), np.int32))
+               T=np.zeros((H, W)), n=np.zeros((H, W), np.int32), amb=np.zeros((H, W), np.int32),
+               margin=np.full((H, W), np.inf))
     lib().orc_composite(ctypes.c_int(rec.shape[0]), _p(rec), ctypes.c_int(W), ctypes.c_int(H),
                         _p(Ct), _p(Dt), ctypes.c_double(eps), ctypes.c_int(mode),
                         ctypes.c_int(int(f32)), ctypes.c_int(int(brute)), ctypes.c_int(x0),
                         ctypes.c_int(x1), ctypes.c_int(y0), ctypes.c_int(y1), _p(out["C"]),
-                        _p(out["D"]), _p(out["W"]), _p(out["T"]), _p(out["n"]), _p(out["amb"]))
+                        _p(out["D"]), _p(out["W"]), _p(out["T"]), _p(out["n"]), _p(out["amb"]),
+                        _p(out["margin"]))
     return out
 
 

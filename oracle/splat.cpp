@@ -268,7 +268,7 @@ int orc_project(int M, const double* means, const double* log_scales, const doub
 void orc_composite(int M, const double* rec, int W, int H, const double* Ct, const double* Dt,
                    double eps, int mode, int f32, int brute, int x0, int x1, int y0, int y1,
                    double* out_C, double* out_D, double* out_W, double* out_T, int* out_n,
-                   int* amb) {
+                   int* amb, double* margin) {
   Lists L = build_lists(M, rec, W, H, brute, x0, x1, y0, y1);
   const long npx = (long)W * H;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -279,6 +279,22 @@ void orc_composite(int M, const double* rec, int W, int H, const double* Ct, con
     double C[3] = {0, 0, 0}, Z = 0, Wg = 0, T = 1.0;
     int n = 0;
     bool a = false;
+    if (margin) {
+      // smallest relative distance of a counting decision to its threshold
+      // (alpha vs 1/255, d vs D_t + eps) over this pixel's candidates
+      double mg = INFINITY;
+      const double thr = Dt[pix] > 0.0 ? Dt[pix] + eps : INFINITY;
+      for (int i : L.cand[pix]) {
+        const double* r = rec + (size_t)i * R_N;
+        double dx = x - r[R_MX], dy = y - r[R_MY];
+        double q = r[R_CA] * dx * dx + 2.0 * r[R_CB] * dx * dy + r[R_CC] * dy * dy;
+        double al = r[R_SIG] * std::exp(-0.5 * q);
+        mg = std::min(mg, std::fabs(al * 255.0 - 1.0));
+        if (std::isfinite(thr) && al * 255.0 >= 1.0 - 1e-3)
+          mg = std::min(mg, std::fabs(r[R_D] - thr) / thr);
+      }
+      margin[pix] = mg;
+    }
     for (const Item& it : its) {
       const double* r = rec + (size_t)it.id * R_N;
       double al = it.alpha;
@@ -371,10 +387,11 @@ void orc_composite_backward(int M, const double* rec, int W, int H, const double
   const long npx = (long)W * H;
   for (long pix = 0; pix < npx; ++pix) {
     int x = (int)(pix % W), y = (int)(pix / W);
-    std::vector<Item> its = counted(L.cand[pix], rec, x, y, Dt[pix], eps, f32);
-    if (its.empty()) continue;
     const double g[3] = {dC[pix], dC[npx + pix], dC[2 * npx + pix]};
     const double gD = dD[pix];
+    if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0 && gD == 0.0) continue;  // contributes nothing
+    std::vector<Item> its = counted(L.cand[pix], rec, x, y, Dt[pix], eps, f32);
+    if (its.empty()) continue;
     const double Ctp[3] = {Ct[pix], Ct[npx + pix], Ct[2 * npx + pix]};
     const size_t n = its.size();
     std::vector<double> a(n), T(n), dLda(n), dLdd(n);

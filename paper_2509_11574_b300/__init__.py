@@ -1,0 +1,461 @@
+"""Python binding of libgps.so (the Gaussian-plus-SDF hot path on sm_103a).
+
+Argument marshalling only: every step runs in the CUDA kernels behind the C ABI
+declared in include/gps.h.  PyTorch supplies device memory and streams.  There
+is no CPU fallback: importing works anywhere, but every call needs the built
+library and a CUDA device and raises otherwise.
+
+Layers:
+  * ctypes mirrors of the C structs and `lib()` (the loaded library);
+  * thin wrappers with the C names (`fuse_frame`, `raycast_sdf`,
+    `render_forward`, `render_backward`, `adam_step`, `gps_workspace_size`, ...);
+  * convenience holders: `Tsdf`, `Gaussians`, `Renderer`, `Adam`, and the
+    autograd functions `RenderImages` / `RenderLoss`.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import List, Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgps.so")
+
+GPS_OK = 0
+GPS_ERR_INVALID_ARG = -1
+GPS_ERR_WORKSPACE_TOO_SMALL = -2
+GPS_ERR_CAPACITY = -3
+GPS_ERR_CUDA = -4
+GPS_ERR_TIMEOUT = -5
+BLEND_OIT, BLEND_ALPHA = 0, 1
+PREC_FP32, PREC_FP16, PREC_BF16 = 0, 1, 2
+STAGE_PROJECT, STAGE_BIN, STAGE_COMPOSITE, STAGE_COMPOSITE_BWD, STAGE_PROJECT_BWD = 1, 2, 4, 8, 16
+
+# learning rates of App. C; the RGB colour plays the role of the degree-0 SH
+# coefficient, whose value is scaled by the SH basis constant 0.28209479
+LR_APP_C = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3 * 0.28209479177387814)
+
+c_float, c_int32, c_int64, c_size_t, c_void_p = (ctypes.c_float, ctypes.c_int32, ctypes.c_int64,
+                                                 ctypes.c_size_t, ctypes.c_void_p)
+P_float = ctypes.POINTER(ctypes.c_float)
+
+
+class GpsIntrinsics(ctypes.Structure):
+    _fields_ = [("fx", c_float), ("fy", c_float), ("cx", c_float), ("cy", c_float),
+                ("width", c_int32), ("height", c_int32)]
+
+
+class GpsPose(ctypes.Structure):
+    _fields_ = [("R", c_float * 9), ("t", c_float * 3)]
+
+
+class GpsTsdf(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("voxel", c_float),
+                ("origin", c_float * 3), ("trunc", c_float), ("max_weight", c_float),
+                ("sdf", c_void_p), ("weight", c_void_p), ("rgbw", c_void_p)]
+
+
+class GpsGaussians(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p),
+                ("opacity_logits", c_void_p), ("rgb", c_void_p), ("M", c_int32)]
+
+
+class GpsView(ctypes.Structure):
+    _fields_ = [("K", GpsIntrinsics), ("T_wc", GpsPose), ("sdf_rgb", c_void_p),
+                ("sdf_depth", c_void_p), ("target_rgb", c_void_p), ("target_depth", c_void_p),
+                ("out_rgb", c_void_p), ("out_depth", c_void_p), ("out_weight", c_void_p),
+                ("grad_rgb", c_void_p), ("grad_depth", c_void_p)]
+
+
+class GpsRenderSettings(ctypes.Structure):
+    _fields_ = [("eps_depth", c_float), ("lambda_depth", c_float), ("near_plane", c_float),
+                ("blend_mode", c_int32), ("precision", c_int32), ("tile_w", c_int32),
+                ("tile_h", c_int32), ("deterministic", c_int32), ("stages", c_int32),
+                ("instrument", c_int32), ("pair_capacity", c_int64)]
+
+
+class GpsAdamHyper(ctypes.Structure):
+    _fields_ = [("lr", c_float * 5), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
+
+
+class GpsWorkspaceLayout(ctypes.Structure):
+    _fields_ = [("total_bytes", c_size_t), ("status", c_size_t), ("records", c_size_t),
+                ("tile_counts", c_size_t), ("tile_ranges", c_size_t), ("pair_keys", c_size_t),
+                ("pair_scratch", c_size_t), ("pix_state", c_size_t), ("tile_partials", c_size_t),
+                ("view_scalars", c_size_t), ("grad2d", c_size_t), ("pair_grads", c_size_t),
+                ("tiles_x", c_int32), ("tiles_y", c_int32), ("tile_w", c_int32),
+                ("tile_h", c_int32), ("pair_capacity", c_int64)]
+
+
+EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspace_layout",
+            "gps_query_status", "fuse_frame", "raycast_sdf", "render_forward", "render_backward",
+            "adam_step")
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+class GpsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libgps error {code}: {msg}")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libgps.so.  Raises if the library has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2509_11574_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        L.gps_last_error.restype = ctypes.c_char_p
+        L.gps_version.restype = ctypes.c_char_p
+        for n in EXPORTED[2:]:
+            getattr(L, n).restype = c_int32
+        L.gps_workspace_size.argtypes = [c_int32, ctypes.POINTER(GpsView), c_int32,
+                                         ctypes.POINTER(GpsRenderSettings), ctypes.POINTER(c_size_t)]
+        L.gps_workspace_layout.argtypes = [c_int32, ctypes.POINTER(GpsView), c_int32,
+                                           ctypes.POINTER(GpsRenderSettings), c_int32,
+                                           ctypes.POINTER(GpsWorkspaceLayout)]
+        L.gps_query_status.argtypes = [c_void_p, c_size_t, ctypes.POINTER(c_int32), c_void_p]
+        L.fuse_frame.argtypes = [ctypes.POINTER(GpsTsdf), c_void_p, c_void_p,
+                                 ctypes.POINTER(GpsIntrinsics), ctypes.POINTER(GpsPose), c_void_p]
+        L.raycast_sdf.argtypes = [ctypes.POINTER(GpsTsdf), ctypes.POINTER(GpsIntrinsics),
+                                  ctypes.POINTER(GpsPose), c_float, c_float, c_void_p, c_void_p,
+                                  c_void_p, c_void_p]
+        L.render_forward.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsView), c_int32,
+                                     ctypes.POINTER(GpsRenderSettings), c_void_p, c_size_t,
+                                     c_void_p, c_void_p]
+        L.render_backward.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsView),
+                                      c_int32, ctypes.POINTER(GpsRenderSettings), c_void_p,
+                                      c_size_t, c_void_p, ctypes.POINTER(GpsGaussians), c_void_p]
+        L.adam_step.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsGaussians),
+                                ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsGaussians),
+                                ctypes.POINTER(GpsAdamHyper), c_int32, c_void_p, c_void_p]
+        _lib = L
+    return _lib
+
+
+def _check(code: int) -> None:
+    if code != GPS_OK:
+        raise GpsError(code, lib().gps_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libgps takes CUDA tensors only")
+    if not t.is_contiguous():
+        raise ValueError("libgps takes contiguous tensors only")
+    return c_void_p(t.data_ptr())
+
+
+def _stream(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- structs
+def intrinsics(cam) -> GpsIntrinsics:
+    return GpsIntrinsics(float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
+                         int(cam.width), int(cam.height))
+
+
+def pose(cam) -> GpsPose:
+    R = [float(x) for x in torch.as_tensor(cam.R, dtype=torch.float64).reshape(9)]
+    t = [float(x) for x in torch.as_tensor(cam.t, dtype=torch.float64).reshape(3)]
+    return GpsPose((c_float * 9)(*R), (c_float * 3)(*t))
+
+
+@dataclasses.dataclass
+class Gaussians:
+    """Gaussian parameters (or same-shaped gradients / moments) on the device."""
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logits: torch.Tensor
+    rgb: torch.Tensor
+
+    @property
+    def M(self) -> int:
+        return int(self.means.shape[0])
+
+    def tensors(self) -> List[torch.Tensor]:
+        return [self.means, self.log_scales, self.quats, self.opacity_logits, self.rgb]
+
+    def c(self) -> GpsGaussians:
+        return GpsGaussians(*[_ptr(t) for t in self.tensors()], self.M)
+
+    @staticmethod
+    def from_numpy(gs, device="cuda") -> "Gaussians":
+        return Gaussians(*[torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+                           for a in gs.arrays()])
+
+    def zeros_like(self) -> "Gaussians":
+        return Gaussians(*[torch.zeros_like(t) for t in self.tensors()])
+
+    def flat(self) -> torch.Tensor:
+        return torch.cat([t.reshape(-1) for t in self.tensors()])
+
+
+def brick_to_linear(a: torch.Tensor, nx: int, ny: int, nz: int) -> torch.Tensor:
+    """Reorder a brick-major voxel array (see GpsTsdf) to [nz][ny][nx](...) (x fastest)."""
+    tail = a.shape[1:]
+    b = a.reshape(nz // 8, ny // 8, nx // 8, 8, 8, 8, *tail)
+    perm = (0, 3, 1, 4, 2, 5) + tuple(range(6, 6 + len(tail)))
+    return b.permute(*perm).reshape(nz, ny, nx, *tail)
+
+
+def linear_to_brick(a: torch.Tensor) -> torch.Tensor:
+    """Inverse of brick_to_linear: [nz][ny][nx](...) -> brick-major [n](...)."""
+    nz, ny, nx = a.shape[:3]
+    tail = a.shape[3:]
+    b = a.reshape(nz // 8, 8, ny // 8, 8, nx // 8, 8, *tail)
+    perm = (0, 2, 4, 1, 3, 5) + tuple(range(6, 6 + len(tail)))
+    return b.permute(*perm).reshape(nz * ny * nx, *tail).contiguous()
+
+
+class Tsdf:
+    """Dense colourised TSDF on the device (brick-major, see include/gps.h)."""
+
+    def __init__(self, spec, device="cuda"):
+        self.spec = spec
+        n = spec.nx * spec.ny * spec.nz
+        self.sdf = torch.ones(n, dtype=torch.float32, device=device)
+        self.weight = torch.zeros(n, dtype=torch.float32, device=device)
+        self.rgbw = torch.zeros(n, 4, dtype=torch.float32, device=device)
+
+    def reset(self):
+        self.sdf.fill_(1.0)
+        self.weight.zero_()
+        self.rgbw.zero_()
+
+    def c(self) -> GpsTsdf:
+        s = self.spec
+        return GpsTsdf(s.nx, s.ny, s.nz, float(s.voxel), (c_float * 3)(*map(float, s.origin)),
+                       float(s.trunc), float(s.max_weight), _ptr(self.sdf), _ptr(self.weight),
+                       _ptr(self.rgbw))
+
+    def linear(self):
+        s = self.spec
+        return (brick_to_linear(self.sdf, s.nx, s.ny, s.nz),
+                brick_to_linear(self.weight, s.nx, s.ny, s.nz),
+                brick_to_linear(self.rgbw, s.nx, s.ny, s.nz))
+
+
+def settings(eps_depth=0.01, lambda_depth=0.0, near=0.2, blend_mode=BLEND_OIT,
+             precision=PREC_FP32, tile=(16, 16), deterministic=False, stages=0,
+             pair_capacity=0, instrument=False) -> GpsRenderSettings:
+    return GpsRenderSettings(eps_depth, lambda_depth, near, blend_mode, precision, tile[0], tile[1],
+                             int(deterministic), stages, int(instrument), pair_capacity)
+
+
+@dataclasses.dataclass
+class View:
+    """One view of the second rendering pass (device images)."""
+    cam: object
+    sdf_rgb: torch.Tensor
+    sdf_depth: torch.Tensor
+    target_rgb: Optional[torch.Tensor] = None
+    target_depth: Optional[torch.Tensor] = None
+    out_rgb: Optional[torch.Tensor] = None
+    out_depth: Optional[torch.Tensor] = None
+    out_weight: Optional[torch.Tensor] = None
+    grad_rgb: Optional[torch.Tensor] = None
+    grad_depth: Optional[torch.Tensor] = None
+
+    def c(self) -> GpsView:
+        return GpsView(intrinsics(self.cam), pose(self.cam), _ptr(self.sdf_rgb),
+                       _ptr(self.sdf_depth), _ptr(self.target_rgb), _ptr(self.target_depth),
+                       _ptr(self.out_rgb), _ptr(self.out_depth), _ptr(self.out_weight),
+                       _ptr(self.grad_rgb), _ptr(self.grad_depth))
+
+
+def _views(views: Sequence[View]):
+    arr = (GpsView * len(views))(*[v.c() for v in views])
+    return arr
+
+
+def _size_views(cams) -> ctypes.Array:
+    return (GpsView * len(cams))(*[GpsView(intrinsics(c), pose(c)) for c in cams])
+
+
+# ---------------------------------------------------------------- C names
+def gps_version() -> str:
+    return lib().gps_version().decode()
+
+
+def gps_workspace_size(M: int, cams, s: GpsRenderSettings) -> int:
+    n = c_size_t(0)
+    v = _size_views(cams)
+    _check(lib().gps_workspace_size(M, v, len(cams), ctypes.byref(s), ctypes.byref(n)))
+    return int(n.value)
+
+
+def gps_workspace_layout(M: int, cams, s: GpsRenderSettings, view: int) -> GpsWorkspaceLayout:
+    out = GpsWorkspaceLayout()
+    v = _size_views(cams)
+    _check(lib().gps_workspace_layout(M, v, len(cams), ctypes.byref(s), view, ctypes.byref(out)))
+    return out
+
+
+def gps_query_status(ws: torch.Tensor, stream=None) -> int:
+    st = c_int32(0)
+    _check(lib().gps_query_status(_ptr(ws), ws.numel(), ctypes.byref(st), _stream(stream)))
+    return int(st.value)
+
+
+def fuse_frame(vol: Tsdf, depth: torch.Tensor, rgb: torch.Tensor, cam, stream=None) -> None:
+    K, P = intrinsics(cam), pose(cam)
+    t = vol.c()
+    _check(lib().fuse_frame(ctypes.byref(t), _ptr(depth), _ptr(rgb), ctypes.byref(K),
+                            ctypes.byref(P), _stream(stream)))
+
+
+def raycast_sdf(vol: Tsdf, cam, near=0.2, far=0.0, out_rgb=None, out_depth=None,
+                out_vertex=None, stream=None):
+    H, W = cam.height, cam.width
+    dev = vol.sdf.device
+    out_rgb = out_rgb if out_rgb is not None else torch.empty(3, H, W, device=dev)
+    out_depth = out_depth if out_depth is not None else torch.empty(H, W, device=dev)
+    K, P = intrinsics(cam), pose(cam)
+    t = vol.c()
+    _check(lib().raycast_sdf(ctypes.byref(t), ctypes.byref(K), ctypes.byref(P), near, far,
+                             _ptr(out_rgb), _ptr(out_depth), _ptr(out_vertex), _stream(stream)))
+    return out_rgb, out_depth
+
+
+def render_forward(g: Gaussians, views: Sequence[View], s: GpsRenderSettings, ws: torch.Tensor,
+                   loss: Optional[torch.Tensor] = None, stream=None) -> None:
+    gc = g.c()
+    va = _views(views)
+    _check(lib().render_forward(ctypes.byref(gc), va, len(views), ctypes.byref(s), _ptr(ws),
+                                ws.numel(), _ptr(loss), _stream(stream)))
+
+
+def render_backward(g: Gaussians, views: Sequence[View], s: GpsRenderSettings, ws: torch.Tensor,
+                    grads: Gaussians, dloss: Optional[torch.Tensor] = None, stream=None) -> None:
+    gc, gr = g.c(), grads.c()
+    va = _views(views)
+    _check(lib().render_backward(ctypes.byref(gc), va, len(views), ctypes.byref(s), _ptr(ws),
+                                 ws.numel(), _ptr(dloss), ctypes.byref(gr), _stream(stream)))
+
+
+def adam_step(params: Gaussians, grads: Gaussians, m: Gaussians, v: Gaussians, lr=LR_APP_C,
+              beta1=0.9, beta2=0.999, eps=1e-15, step: int = 1,
+              device_step: Optional[torch.Tensor] = None, stream=None) -> None:
+    h = GpsAdamHyper((c_float * 5)(*lr), beta1, beta2, eps)
+    pc, gc, mc, vc = params.c(), grads.c(), m.c(), v.c()
+    _check(lib().adam_step(ctypes.byref(pc), ctypes.byref(gc), ctypes.byref(mc), ctypes.byref(vc),
+                           ctypes.byref(h), step, _ptr(device_step), _stream(stream)))
+
+
+# ---------------------------------------------------------------- holders
+class Renderer:
+    """Owns the workspace of render_forward / render_backward for fixed sizes."""
+
+    def __init__(self, M: int, cams, s: Optional[GpsRenderSettings] = None, device="cuda"):
+        self.s = s if s is not None else settings()
+        self.cams = list(cams)
+        self.M = M
+        nbytes = gps_workspace_size(M, self.cams, self.s)
+        self.ws = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+
+    def layout(self, view: int = 0) -> GpsWorkspaceLayout:
+        return gps_workspace_layout(self.M, self.cams, self.s, view)
+
+    def region(self, view: int, name: str, dtype, count: int) -> torch.Tensor:
+        L = self.layout(view)
+        off = getattr(L, name)
+        esz = torch.empty((), dtype=dtype).element_size()
+        return self.ws[off:off + count * esz].view(dtype)
+
+    def forward(self, g: Gaussians, views: Sequence[View], loss=None, stream=None):
+        render_forward(g, views, self.s, self.ws, loss, stream)
+
+    def backward(self, g: Gaussians, views: Sequence[View], grads: Gaussians, dloss=None,
+                 stream=None):
+        render_backward(g, views, self.s, self.ws, grads, dloss, stream)
+
+    def status(self, stream=None) -> int:
+        return gps_query_status(self.ws, stream)
+
+
+class Adam:
+    """Adam state (FP32 moments) for a Gaussian set; step() calls adam_step."""
+
+    def __init__(self, params: Gaussians, lr=LR_APP_C, betas=(0.9, 0.999), eps=1e-15,
+                 device_step: bool = False):
+        self.params = params
+        self.m = params.zeros_like()
+        self.v = params.zeros_like()
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self.t = 0
+        self.device_step = (torch.zeros(1, dtype=torch.int32, device=params.means.device)
+                            if device_step else None)
+
+    def step(self, grads: Gaussians, stream=None):
+        if self.device_step is not None:
+            adam_step(self.params, grads, self.m, self.v, self.lr, *self.betas, self.eps, 0,
+                      self.device_step, stream)
+        else:
+            self.t += 1
+            adam_step(self.params, grads, self.m, self.v, self.lr, *self.betas, self.eps, self.t,
+                      None, stream)
+
+
+class RenderImages(torch.autograd.Function):
+    """C*, D*, W_G of one view as differentiable outputs of the five parameter
+    tensors; the backward calls render_backward with dL/dC*, dL/dD*."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, view: View, means, log_scales, quats, logits, rgb):
+        g = Gaussians(means.detach(), log_scales.detach(), quats.detach(), logits.detach(),
+                      rgb.detach())
+        H, W = view.cam.height, view.cam.width
+        dev = means.device
+        out = dataclasses.replace(view, target_rgb=None, target_depth=None,
+                                  out_rgb=torch.empty(3, H, W, device=dev),
+                                  out_depth=torch.empty(H, W, device=dev),
+                                  out_weight=torch.empty(H, W, device=dev))
+        renderer.forward(g, [out])
+        ctx.renderer, ctx.view, ctx.g = renderer, out, g
+        ctx.mark_non_differentiable(out.out_weight)
+        return out.out_rgb, out.out_depth, out.out_weight
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_depth, d_weight):
+        g = ctx.g
+        grads = g.zeros_like()
+        v = dataclasses.replace(ctx.view,
+                                grad_rgb=(d_rgb.contiguous() if d_rgb is not None
+                                          else torch.zeros_like(ctx.view.out_rgb)),
+                                grad_depth=(d_depth.contiguous() if d_depth is not None
+                                            else torch.zeros_like(ctx.view.out_depth)))
+        ctx.renderer.backward(g, [v], grads)
+        return (None, None, *grads.tensors())
+
+
+class RenderLoss(torch.autograd.Function):
+    """Fused colour (+ depth) L1 loss of Eq. 6 over views with targets."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, views: Sequence[View], means, log_scales, quats, logits,
+                rgb):
+        g = Gaussians(means.detach(), log_scales.detach(), quats.detach(), logits.detach(),
+                      rgb.detach())
+        loss = torch.zeros(1, device=means.device)
+        renderer.forward(g, views, loss)
+        ctx.renderer, ctx.views, ctx.g = renderer, views, g
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, dloss):
+        g = ctx.g
+        grads = g.zeros_like()
+        ctx.renderer.backward(g, ctx.views, grads, dloss.reshape(1).contiguous().float())
+        return (None, None, *grads.tensors())

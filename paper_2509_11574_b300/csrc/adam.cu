@@ -1,0 +1,121 @@
+// Adam over the five parameter groups (App. C learning rates), torch.optim.Adam
+// semantics, FP32 moments.  One launch covers all groups; each thread updates
+// four consecutive floats with 16-byte loads where the group allows it.  The
+// gradient is zeroed in the same pass (its write replaces the zero_grad pass).
+//   m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2
+//   p <- p - (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+#include <cuda_runtime.h>
+
+#include "gps_common.cuh"
+
+namespace gps {
+
+struct AdamGroup {
+  float* p;
+  float* g;
+  float* m;
+  float* v;
+  long long n;
+  float lr;
+  int vec4;  // all four pointers 16-byte aligned
+};
+
+struct AdamArgs {
+  AdamGroup grp[5];
+  long long first_block[6];  // block offsets per group
+  float b1, b2, eps;
+  int step;
+  int* device_step;
+};
+
+__global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
+  __shared__ float s_bc[2];
+  if (threadIdx.x == 0) {
+    int t = a.step;
+    if (t <= 0) t = *a.device_step + 1;  // the counter is advanced by adam_step_advance
+    s_bc[0] = (float)(1.0 - pow((double)a.b1, (double)t));
+    s_bc[1] = (float)sqrt(1.0 - pow((double)a.b2, (double)t));
+  }
+  __syncthreads();
+  const long long blk = blockIdx.x;
+  int gidx = 0;
+#pragma unroll
+  for (int k = 1; k < 5; ++k)
+    if (blk >= a.first_block[k]) gidx = k;
+  const AdamGroup& G = a.grp[gidx];
+  const long long base = ((blk - a.first_block[gidx]) * 256 + threadIdx.x) * 4;
+  if (base >= G.n) return;
+  const float bc1 = s_bc[0], sbc2 = s_bc[1];
+  const float step_size = G.lr / bc1;
+  const float b1 = a.b1, b2 = a.b2, eps = a.eps;
+  if (G.vec4 && base + 4 <= G.n) {
+    float4 p = *reinterpret_cast<float4*>(G.p + base);
+    const float4 g = *reinterpret_cast<float4*>(G.g + base);
+    float4 m = *reinterpret_cast<float4*>(G.m + base);
+    float4 v = *reinterpret_cast<float4*>(G.v + base);
+#define GPS_ADAM1(c)                                           \
+  m.c = b1 * m.c + (1.0f - b1) * g.c;                          \
+  v.c = b2 * v.c + (1.0f - b2) * g.c * g.c;                    \
+  p.c = p.c - step_size * m.c / (sqrtf(v.c) / sbc2 + eps);
+    GPS_ADAM1(x) GPS_ADAM1(y) GPS_ADAM1(z) GPS_ADAM1(w)
+#undef GPS_ADAM1
+    *reinterpret_cast<float4*>(G.p + base) = p;
+    *reinterpret_cast<float4*>(G.m + base) = m;
+    *reinterpret_cast<float4*>(G.v + base) = v;
+    *reinterpret_cast<float4*>(G.g + base) = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    for (long long k = base; k < min(base + 4, G.n); ++k) {
+      const float g = G.g[k];
+      const float m = b1 * G.m[k] + (1.0f - b1) * g;
+      const float v = b2 * G.v[k] + (1.0f - b2) * g * g;
+      G.m[k] = m;
+      G.v[k] = v;
+      G.p[k] = G.p[k] - step_size * m / (sqrtf(v) / sbc2 + eps);
+      G.g[k] = 0.0f;
+    }
+  }
+}
+
+__global__ void adam_step_advance_kernel(int* device_step) { *device_step += 1; }
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+cudaError_t launch_adam(const GpsGaussians& P, const GpsGaussians& Gr, const GpsGaussians& Mo,
+                        const GpsGaussians& Vo, const GpsAdamHyper& h, int step, int* device_step,
+                        cudaStream_t st) {
+  AdamArgs a{};
+  float* const pp[5] = {P.means, P.log_scales, P.quats, P.opacity_logits, P.rgb};
+  float* const gg[5] = {Gr.means, Gr.log_scales, Gr.quats, Gr.opacity_logits, Gr.rgb};
+  float* const mm[5] = {Mo.means, Mo.log_scales, Mo.quats, Mo.opacity_logits, Mo.rgb};
+  float* const vv[5] = {Vo.means, Vo.log_scales, Vo.quats, Vo.opacity_logits, Vo.rgb};
+  const int width[5] = {3, 3, 4, 1, 3};
+  long long blocks = 0;
+  for (int k = 0; k < 5; ++k) {
+    AdamGroup& G = a.grp[k];
+    G.p = pp[k];
+    G.g = gg[k];
+    G.m = mm[k];
+    G.v = vv[k];
+    G.n = (long long)P.M * width[k];
+    G.lr = h.lr[k];
+    G.vec4 = aligned16(G.p) && aligned16(G.g) && aligned16(G.m) && aligned16(G.v);
+    a.first_block[k] = blocks;
+    blocks += (G.n + 1023) / 1024;
+  }
+  a.first_block[5] = blocks;
+  a.b1 = h.beta1;
+  a.b2 = h.beta2;
+  a.eps = h.eps;
+  a.step = step;
+  a.device_step = device_step;
+  if (blocks == 0) return cudaSuccess;
+  adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && step <= 0) {
+    adam_step_advance_kernel<<<1, 1, 0, st>>>(device_step);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace gps

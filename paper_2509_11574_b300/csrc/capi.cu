@@ -1,0 +1,362 @@
+// extern "C" entry points of libgps: argument checks, workspace layout and
+// the order of kernel launches.  No call synchronises the stream except
+// gps_query_status.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "gps_common.cuh"
+
+namespace gps {
+cudaError_t launch_fuse(const GpsTsdf&, const float*, const float*, const Cam&, cudaStream_t);
+cudaError_t launch_raycast(const GpsTsdf&, const Cam&, float, float, float*, float*, float*,
+                           cudaStream_t);
+cudaError_t launch_project(const GpsGaussians&, const Cam&, float, float4*, uint32_t*, int, int,
+                           int, cudaStream_t);
+cudaError_t launch_count_tiles(const float4*, int, int, int, uint32_t*, int, int, int,
+                               cudaStream_t);
+cudaError_t launch_project_backward(const GpsGaussians&, const Cam&, float, const float4*,
+                                    const GpsGaussians&, cudaStream_t);
+cudaError_t launch_scan_tiles(uint32_t*, uint2*, int, long long, float*, int*, cudaStream_t);
+cudaError_t launch_emit_pairs(const float4*, int, int, int, const uint2*, uint32_t*,
+                              unsigned long long*, int, int, int, cudaStream_t);
+cudaError_t launch_sort_tiles(const uint2*, int, unsigned long long*, unsigned long long*,
+                              cudaStream_t);
+cudaError_t launch_composite_fwd(const ViewDev&, float, int, int, int, cudaStream_t);
+cudaError_t launch_composite_bwd(const ViewDev&, float, float, const float*, int, int, int, int,
+                                 cudaStream_t);
+cudaError_t launch_finalize_loss(const ViewDev&, float, float*, int, cudaStream_t);
+cudaError_t launch_gather_pair_grads(const ViewDev&, int, cudaStream_t);
+cudaError_t launch_adam(const GpsGaussians&, const GpsGaussians&, const GpsGaussians&,
+                        const GpsGaussians&, const GpsAdamHyper&, int, int*, cudaStream_t);
+}  // namespace gps
+
+using namespace gps;
+
+namespace {
+
+thread_local std::string g_err;
+
+int32_t fail(int32_t code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int32_t fail(int32_t code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int32_t cuda_fail(cudaError_t e, const char* where) {
+  return fail(GPS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+struct TileCfg {
+  int tw, th;
+};
+
+bool tile_cfg(const GpsRenderSettings* s, TileCfg& c) {
+  c.tw = s->tile_w;
+  c.th = s->tile_h;
+  if (c.tw == 0 && c.th == 0) {
+    c.tw = 16;
+    c.th = 16;
+  }
+  return (c.tw == 16 && c.th == 16) || (c.tw == 16 && c.th == 8) || (c.tw == 8 && c.th == 8) ||
+         (c.tw == 32 && c.th == 8);
+}
+
+long long pair_cap(const GpsRenderSettings* s, int M) {
+  return s->pair_capacity > 0 ? s->pair_capacity : 64LL * (M > 0 ? M : 1);
+}
+
+// Workspace: [status 256 B] then per view, in order, its regions.
+int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRenderSettings* s,
+               int32_t want, GpsWorkspaceLayout* out, size_t* total) {
+  if (M < 0 || n_views <= 0 || !views || !s) return fail(GPS_ERR_INVALID_ARG, "bad layout arguments");
+  TileCfg tc;
+  if (!tile_cfg(s, tc)) return fail(GPS_ERR_INVALID_ARG, "unsupported tile size %dx%d", s->tile_w, s->tile_h);
+  const long long cap = pair_cap(s, M);
+  if (cap <= 0 || cap > 0xFFFFFFF0LL) return fail(GPS_ERR_INVALID_ARG, "pair_capacity out of range");
+  size_t off = 256;
+  for (int v = 0; v < n_views; ++v) {
+    const int W = views[v].K.width, H = views[v].K.height;
+    if (W <= 0 || H <= 0) return fail(GPS_ERR_INVALID_ARG, "view %d has size %dx%d", v, W, H);
+    const int tx = (W + tc.tw - 1) / tc.tw, ty = (H + tc.th - 1) / tc.th;
+    const size_t ntiles = (size_t)tx * ty, npx = (size_t)W * H;
+    GpsWorkspaceLayout L{};
+    L.status = 0;
+    L.records = off; off = align256(off + (size_t)M * 64);
+    L.tile_counts = off; off = align256(off + ntiles * 4);
+    L.tile_ranges = off; off = align256(off + ntiles * 8);
+    L.pair_keys = off; off = align256(off + (size_t)cap * 8);
+    L.pair_scratch = off; off = align256(off + (size_t)cap * 8);
+    L.pix_state = off; off = align256(off + npx * 32);
+    L.tile_partials = off; off = align256(off + ntiles * 16);
+    L.view_scalars = off; off = align256(off + 64);
+    L.grad2d = off; off = align256(off + (size_t)M * 48);
+    L.pair_grads = off;
+    off = align256(off + (s->deterministic ? (size_t)cap * 48 : 0));
+    L.tiles_x = tx;
+    L.tiles_y = ty;
+    L.tile_w = tc.tw;
+    L.tile_h = tc.th;
+    L.pair_capacity = cap;
+    if (v == want && out) *out = L;
+  }
+  if (out) out->total_bytes = off;
+  if (total) *total = off;
+  return GPS_OK;
+}
+
+Cam make_cam(const GpsIntrinsics& K, const GpsPose& P) {
+  Cam c;
+  c.fx = K.fx; c.fy = K.fy; c.cx = K.cx; c.cy = K.cy;
+  c.W = K.width; c.H = K.height;
+  for (int k = 0; k < 9; ++k) c.R[k] = P.R[k];
+  for (int k = 0; k < 3; ++k) c.t[k] = P.t[k];
+  return c;
+}
+
+bool finite_cam(const GpsIntrinsics& K, const GpsPose& P) {
+  bool ok = std::isfinite(K.fx) && std::isfinite(K.fy) && std::isfinite(K.cx) &&
+            std::isfinite(K.cy) && K.fx > 0 && K.fy > 0 && K.width > 0 && K.height > 0;
+  for (int k = 0; k < 9; ++k) ok = ok && std::isfinite(P.R[k]);
+  for (int k = 0; k < 3; ++k) ok = ok && std::isfinite(P.t[k]);
+  return ok;
+}
+
+int32_t check_gaussians(const GpsGaussians* g, const char* what) {
+  if (!g) return fail(GPS_ERR_INVALID_ARG, "%s is NULL", what);
+  if (g->M < 0) return fail(GPS_ERR_INVALID_ARG, "%s.M < 0", what);
+  if (g->M == 0) return GPS_OK;
+  if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->rgb)
+    return fail(GPS_ERR_INVALID_ARG, "%s has a NULL array", what);
+  if (!aligned(g->means, 4) || !aligned(g->log_scales, 4) || !aligned(g->quats, 16) ||
+      !aligned(g->opacity_logits, 4) || !aligned(g->rgb, 4))
+    return fail(GPS_ERR_INVALID_ARG, "%s arrays must be 4-byte aligned (quats 16-byte)", what);
+  return GPS_OK;
+}
+
+ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L) {
+  ViewDev v{};
+  v.cam = make_cam(vw.K, vw.T_wc);
+  v.Ct = vw.sdf_rgb;
+  v.Dt = vw.sdf_depth;
+  v.Ctgt = vw.target_rgb;
+  v.Dtgt = vw.target_depth;
+  v.out_rgb = vw.out_rgb;
+  v.out_depth = vw.out_depth;
+  v.out_weight = vw.out_weight;
+  v.g_rgb = vw.grad_rgb;
+  v.g_depth = vw.grad_depth;
+  v.rec = reinterpret_cast<float4*>(ws + L.records);
+  v.tile_counts = reinterpret_cast<uint32_t*>(ws + L.tile_counts);
+  v.tile_cursor = v.tile_counts;
+  v.tile_ranges = reinterpret_cast<uint2*>(ws + L.tile_ranges);
+  v.keys = reinterpret_cast<unsigned long long*>(ws + L.pair_keys);
+  v.keys_tmp = reinterpret_cast<unsigned long long*>(ws + L.pair_scratch);
+  const size_t npx = (size_t)vw.K.width * vw.K.height;
+  v.pix_a = reinterpret_cast<float4*>(ws + L.pix_state);
+  v.pix_b = v.pix_a + npx;
+  v.tile_partials = reinterpret_cast<float4*>(ws + L.tile_partials);
+  v.scalars = reinterpret_cast<float*>(ws + L.view_scalars);
+  v.grad2d = reinterpret_cast<float4*>(ws + L.grad2d);
+  v.pair_grads = reinterpret_cast<float4*>(ws + L.pair_grads);
+  v.tiles_x = L.tiles_x;
+  v.tiles_y = L.tiles_y;
+  v.tw = L.tile_w;
+  v.th = L.tile_h;
+  v.cap = L.pair_capacity;
+  return v;
+}
+
+int32_t check_render_args(const GpsGaussians* g, const GpsView* views, int32_t n_views,
+                          const GpsRenderSettings* s, void* ws, size_t ws_bytes) {
+  if (int32_t e = check_gaussians(g, "gaussians")) return e;
+  if (!views || n_views <= 0) return fail(GPS_ERR_INVALID_ARG, "no views");
+  if (!s) return fail(GPS_ERR_INVALID_ARG, "settings is NULL");
+  if (!std::isfinite(s->eps_depth) || !std::isfinite(s->lambda_depth) || !std::isfinite(s->near_plane))
+    return fail(GPS_ERR_INVALID_ARG, "non-finite settings");
+  if (s->blend_mode != GPS_BLEND_OIT && s->blend_mode != GPS_BLEND_ALPHA)
+    return fail(GPS_ERR_INVALID_ARG, "unknown blend_mode %d", s->blend_mode);
+  if (s->precision != GPS_PREC_FP32 && s->precision != GPS_PREC_FP16 && s->precision != GPS_PREC_BF16)
+    return fail(GPS_ERR_INVALID_ARG, "unknown precision %d", s->precision);
+  if (!ws || !aligned(ws, 256)) return fail(GPS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  for (int v = 0; v < n_views; ++v) {
+    if (!finite_cam(views[v].K, views[v].T_wc))
+      return fail(GPS_ERR_INVALID_ARG, "view %d: bad intrinsics or pose", v);
+    if (!views[v].sdf_rgb || !views[v].sdf_depth)
+      return fail(GPS_ERR_INVALID_ARG, "view %d: sdf_rgb / sdf_depth are required", v);
+  }
+  size_t need = 0;
+  if (int32_t e = layout(g->M, views, n_views, s, -1, nullptr, &need)) return e;
+  if (ws_bytes < need)
+    return fail(GPS_ERR_WORKSPACE_TOO_SMALL, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+  return GPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gps_last_error(void) { return g_err.c_str(); }
+
+const char* gps_version(void) { return "gps-b300 0.1 (sm_103a)"; }
+
+int32_t gps_workspace_size(int32_t M, const GpsView* views, int32_t n_views,
+                           const GpsRenderSettings* settings, size_t* bytes) {
+  if (!bytes) return fail(GPS_ERR_INVALID_ARG, "bytes is NULL");
+  return layout(M, views, n_views, settings, -1, nullptr, bytes);
+}
+
+int32_t gps_workspace_layout(int32_t M, const GpsView* views, int32_t n_views,
+                             const GpsRenderSettings* settings, int32_t view,
+                             GpsWorkspaceLayout* out) {
+  if (!out || view < 0 || view >= n_views) return fail(GPS_ERR_INVALID_ARG, "bad view / out");
+  return layout(M, views, n_views, settings, view, out, nullptr);
+}
+
+int32_t gps_query_status(const void* ws, size_t ws_bytes, int32_t* status, void* stream) {
+  if (!ws || !status || ws_bytes < 256) return fail(GPS_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(status, ws, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "gps_query_status");
+  return GPS_OK;
+}
+
+int32_t fuse_frame(GpsTsdf* vol, const float* depth, const float* rgb, const GpsIntrinsics* K,
+                   const GpsPose* T_wc, void* stream) {
+  if (!vol || !depth || !rgb || !K || !T_wc) return fail(GPS_ERR_INVALID_ARG, "NULL argument");
+  if (vol->nx <= 0 || vol->ny <= 0 || vol->nz <= 0 || vol->nx % 8 || vol->ny % 8 || vol->nz % 8)
+    return fail(GPS_ERR_INVALID_ARG, "volume dims must be positive multiples of 8");
+  if (!vol->sdf || !vol->weight || !vol->rgbw || !aligned(vol->rgbw, 16))
+    return fail(GPS_ERR_INVALID_ARG, "volume arrays missing or rgbw not 16-byte aligned");
+  if (!(vol->voxel > 0) || !(vol->trunc > 0) || !(vol->max_weight > 0))
+    return fail(GPS_ERR_INVALID_ARG, "voxel, trunc and max_weight must be positive");
+  if (!finite_cam(*K, *T_wc)) return fail(GPS_ERR_INVALID_ARG, "bad intrinsics or pose");
+  cudaError_t e = launch_fuse(*vol, depth, rgb, make_cam(*K, *T_wc), static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GPS_OK : cuda_fail(e, "fuse_frame");
+}
+
+int32_t raycast_sdf(const GpsTsdf* vol, const GpsIntrinsics* K, const GpsPose* T_wc,
+                    float near_plane, float far_plane, float* out_rgb, float* out_depth,
+                    float* out_vertex, void* stream) {
+  if (!vol || !K || !T_wc || !out_rgb || !out_depth) return fail(GPS_ERR_INVALID_ARG, "NULL argument");
+  if (vol->nx < 8 || vol->ny < 8 || vol->nz < 8 || vol->nx % 8 || vol->ny % 8 || vol->nz % 8)
+    return fail(GPS_ERR_INVALID_ARG, "volume dims must be positive multiples of 8");
+  if (!vol->sdf || !vol->rgbw || !aligned(vol->rgbw, 16))
+    return fail(GPS_ERR_INVALID_ARG, "volume arrays missing or rgbw not 16-byte aligned");
+  if (!(vol->voxel > 0) || !(vol->trunc > 0) || !std::isfinite(near_plane) || !std::isfinite(far_plane))
+    return fail(GPS_ERR_INVALID_ARG, "bad voxel / trunc / near / far");
+  if (!finite_cam(*K, *T_wc)) return fail(GPS_ERR_INVALID_ARG, "bad intrinsics or pose");
+  cudaError_t e = launch_raycast(*vol, make_cam(*K, *T_wc), near_plane, far_plane, out_rgb,
+                                 out_depth, out_vertex, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GPS_OK : cuda_fail(e, "raycast_sdf");
+}
+
+int32_t render_forward(const GpsGaussians* g, const GpsView* views, int32_t n_views,
+                       const GpsRenderSettings* s, void* ws, size_t ws_bytes, float* loss,
+                       void* stream) {
+  if (int32_t e = check_render_args(g, views, n_views, s, ws, ws_bytes)) return e;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int stages = s->stages ? s->stages : 0x1f;
+  bool has_tgt = true;
+  for (int v = 0; v < n_views; ++v) has_tgt = has_tgt && views[v].target_rgb && views[v].target_depth;
+  char* base = static_cast<char*>(ws);
+  int* status = reinterpret_cast<int*>(base);
+  cudaError_t e = cudaSuccess;
+  if (stages & GPS_STAGE_PROJECT) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  for (int vi = 0; vi < n_views && e == cudaSuccess; ++vi) {
+    GpsWorkspaceLayout L;
+    layout(g->M, views, n_views, s, vi, &L, nullptr);
+    ViewDev v = make_view(views[vi], base, L);
+    const int ntiles = v.tiles_x * v.tiles_y;
+    if (stages & GPS_STAGE_PROJECT) {
+      e = cudaMemsetAsync(v.tile_counts, 0, (size_t)ntiles * 4, st);
+      if (e == cudaSuccess && g->M > 0)
+        e = launch_project(*g, v.cam, s->near_plane, v.rec, v.tile_counts, v.tiles_x, v.tw, v.th, st);
+    } else if (stages & GPS_STAGE_BIN) {
+      e = cudaMemsetAsync(v.tile_counts, 0, (size_t)ntiles * 4, st);
+      if (e == cudaSuccess && g->M > 0)
+        e = launch_count_tiles(v.rec, g->M, v.cam.W, v.cam.H, v.tile_counts, v.tiles_x, v.tw, v.th, st);
+    }
+    if (e == cudaSuccess && (stages & GPS_STAGE_BIN)) {
+      e = launch_scan_tiles(v.tile_counts, v.tile_ranges, ntiles, v.cap, v.scalars, status, st);
+      if (e == cudaSuccess && g->M > 0)
+        e = launch_emit_pairs(v.rec, g->M, v.cam.W, v.cam.H, v.tile_ranges, v.tile_cursor, v.keys,
+                              v.tiles_x, v.tw, v.th, st);
+      if (e == cudaSuccess) e = launch_sort_tiles(v.tile_ranges, ntiles, v.keys, v.keys_tmp, st);
+    }
+    if (e == cudaSuccess && (stages & GPS_STAGE_COMPOSITE)) {
+      if (s->instrument) e = cudaMemsetAsync(v.scalars + 8, 0, 32, st);
+      if (e == cudaSuccess)
+        e = launch_composite_fwd(v, s->eps_depth, s->blend_mode, has_tgt ? 1 : 0,
+                                 s->instrument ? 1 : 0, st);
+      if (e == cudaSuccess && has_tgt)
+        e = launch_finalize_loss(v, s->lambda_depth, loss, vi == 0 ? 1 : 0, st);
+    }
+  }
+  if (e == cudaSuccess && !has_tgt && loss) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+  return e == cudaSuccess ? GPS_OK : cuda_fail(e, "render_forward");
+}
+
+int32_t render_backward(const GpsGaussians* g, const GpsView* views, int32_t n_views,
+                        const GpsRenderSettings* s, void* ws, size_t ws_bytes, const float* dloss,
+                        GpsGaussians* grads, void* stream) {
+  if (int32_t e = check_render_args(g, views, n_views, s, ws, ws_bytes)) return e;
+  if (int32_t e = check_gaussians(grads, "grads")) return e;
+  if (grads->M != g->M) return fail(GPS_ERR_INVALID_ARG, "grads.M != gaussians.M");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int stages = s->stages ? s->stages : 0x1f;
+  char* base = static_cast<char*>(ws);
+  cudaError_t e = cudaSuccess;
+  for (int vi = 0; vi < n_views && e == cudaSuccess; ++vi) {
+    const GpsView& vw = views[vi];
+    const bool explicit_grads = vw.grad_rgb || vw.grad_depth;
+    const bool fused = !explicit_grads;
+    if (fused && (!vw.target_rgb || !vw.target_depth))
+      return fail(GPS_ERR_INVALID_ARG, "view %d: no upstream gradients and no targets", vi);
+    GpsWorkspaceLayout L;
+    layout(g->M, views, n_views, s, vi, &L, nullptr);
+    ViewDev v = make_view(vw, base, L);
+    if (stages & GPS_STAGE_COMPOSITE_BWD) {
+      if (!s->deterministic) e = cudaMemsetAsync(v.grad2d, 0, (size_t)g->M * 48, st);
+      if (e == cudaSuccess)
+        e = launch_composite_bwd(v, s->eps_depth, s->lambda_depth, dloss, s->blend_mode,
+                                 fused ? 1 : 0, s->deterministic ? 1 : 0, s->instrument ? 1 : 0, st);
+      if (e == cudaSuccess && s->deterministic && g->M > 0) e = launch_gather_pair_grads(v, g->M, st);
+    }
+    if (e == cudaSuccess && (stages & GPS_STAGE_PROJECT_BWD) && g->M > 0)
+      e = launch_project_backward(*g, v.cam, s->near_plane, v.grad2d, *grads, st);
+  }
+  return e == cudaSuccess ? GPS_OK : cuda_fail(e, "render_backward");
+}
+
+int32_t adam_step(GpsGaussians* params, GpsGaussians* grads, GpsGaussians* m, GpsGaussians* v,
+                  const GpsAdamHyper* hyper, int32_t step, int32_t* device_step, void* stream) {
+  if (int32_t e = check_gaussians(params, "params")) return e;
+  if (int32_t e = check_gaussians(grads, "grads")) return e;
+  if (int32_t e = check_gaussians(m, "m")) return e;
+  if (int32_t e = check_gaussians(v, "v")) return e;
+  if (grads->M != params->M || m->M != params->M || v->M != params->M)
+    return fail(GPS_ERR_INVALID_ARG, "group sizes differ");
+  if (!hyper) return fail(GPS_ERR_INVALID_ARG, "hyper is NULL");
+  if (step <= 0 && !device_step) return fail(GPS_ERR_INVALID_ARG, "step <= 0 needs device_step");
+  if (!(hyper->beta1 >= 0 && hyper->beta1 < 1 && hyper->beta2 >= 0 && hyper->beta2 < 1 && hyper->eps >= 0))
+    return fail(GPS_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+  cudaError_t e = launch_adam(*params, *grads, *m, *v, *hyper, step, device_step,
+                              static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GPS_OK : cuda_fail(e, "adam_step");
+}
+
+}  // extern "C"

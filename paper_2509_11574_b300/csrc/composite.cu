@@ -1,0 +1,662 @@
+// Second rendering pass, hybrid blend, fused L1 loss and their adjoints.
+//
+// Forward (Eq. 1-4; Table 7 variant): one CTA per tile, one thread per pixel.
+// Each tile's Gaussian list is sorted by depth, so the list is cut once at the
+// first Gaussian at or behind max over the tile of D_t + eps (every pixel would
+// cull it and all that follow), and each warp leaves a staged batch as soon as
+// the next Gaussian is at or behind its own pixels' maximum threshold.  Batches
+// of records are staged in shared memory and read as broadcasts.
+//
+// Backward, order-independent mode: the adjoint of Eq. 4 needs only per-pixel
+// final values (N = 1 + W_G, C*, D*), not the order of the Gaussians, so the
+// CTA transposes the work: each lane owns one Gaussian of the tile list and
+// walks the tile's pixels (staged in shared memory, read as broadcasts),
+// accumulating its 10 gradient terms privately - no shuffles.  One vector
+// atomic per (tile, Gaussian) pair, or a plain store into the pair's slot in
+// deterministic mode.
+//
+// Backward, alpha mode: per-pixel reverse walk of the list with the
+// transmittance recomputed by division from the stored T_end, warp-shuffle
+// reduction of each Gaussian's terms, then one shared-memory partial per warp.
+#include <cuda_runtime.h>
+
+#include "gps_common.cuh"
+
+namespace gps {
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_min_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_max_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Instrumented runs: evaluation counters in the view scalars (uint64 after 8 floats).
+__device__ __forceinline__ void add_counters(const ViewDev& v, int slot, unsigned tested,
+                                             unsigned counted) {
+  unsigned long long a = tested, b = counted;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    unsigned long long* c = reinterpret_cast<unsigned long long*>(v.scalars + 8);
+    atomicAdd(c + slot, a);
+    atomicAdd(c + slot + 1, b);
+  }
+}
+
+// First position in [lo, hi) whose depth bits are >= bits(thr); thr > 0.
+__device__ __forceinline__ uint32_t depth_cut(const unsigned long long* __restrict__ keys,
+                                              uint32_t lo, uint32_t hi, float thr) {
+  if (!(thr > 0.0f)) return lo;
+  const uint32_t tb = __float_as_uint(thr);
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if ((uint32_t)(keys[mid] >> 32) < tb) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int NT>
+__device__ __forceinline__ float block_max(float v, float* s_tmp) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) s_tmp[w] = v;
+  __syncthreads();
+  float r = s_tmp[0];
+#pragma unroll
+  for (int k = 1; k < NT / 32; ++k) r = fmaxf(r, s_tmp[k]);
+  return r;
+}
+
+// ------------------------------------------------------------------ forward
+template <int TW, int TH, int MODE, bool INSTR>
+__global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(ViewDev v, float eps, int has_tgt) {
+  constexpr int NT = TW * TH;
+  constexpr int ROWS_PER_WARP = 32 / TW;
+  __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
+  __shared__ float s_tmp[NT / 32 * 3];
+  const int W = v.cam.W, H = v.cam.H;
+  const int tile = blockIdx.x;
+  const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
+  const bool inside = px < W && py < H;
+  const long long npx = (long long)W * H, pix = (long long)py * W + px;
+  float ct0 = 0.f, ct1 = 0.f, ct2 = 0.f, dt = 0.f;
+  if (inside) {
+    ct0 = __ldg(v.Ct + pix);
+    ct1 = __ldg(v.Ct + npx + pix);
+    ct2 = __ldg(v.Ct + 2 * npx + pix);
+    dt = __ldg(v.Dt + pix);
+  }
+  const float thr = inside ? depth_threshold(dt, eps) : -INFINITY;
+  const float wthr = warp_max(thr);
+  const float bthr = block_max<NT>(thr, s_tmp);
+  const uint2 r = v.tile_ranges[tile];
+  const uint32_t end = depth_cut(v.keys, r.x, r.y, bthr);
+  const float wy0 = (float)(ty * TH + warp * ROWS_PER_WARP);
+  const float wy1 = wy0 + (float)(ROWS_PER_WARP - 1);
+  const float fpx = (float)px, fpy = (float)py;
+  float cr = 0.f, cg = 0.f, cb = 0.f, wsum = 0.f, zsum = 0.f, T = 1.0f;
+  uint32_t last = r.x;
+  bool done = !inside;
+  unsigned n_tested = 0, n_counted = 0;
+  for (uint32_t b = r.x; b < end; b += NT) {
+    __syncthreads();
+    if (MODE == GPS_BLEND_ALPHA) {
+      if (__syncthreads_and(done)) break;
+    }
+    const uint32_t k = b + tid;
+    if (k < end) {
+      const uint32_t gi = (uint32_t)v.keys[k];
+      const float4* rr = v.rec + 4 * (size_t)gi;
+      float4 A = rr[0], B = rr[1], C = rr[2];
+      const float ey = rr[3].x;
+      B.y = 2.0f * B.y;  // 2 b, exact
+      C.w = ey;
+      s_a[tid] = A;
+      s_b[tid] = B;
+      s_c[tid] = C;
+    }
+    __syncthreads();
+    const int nb = (int)min((uint32_t)NT, end - b);
+    for (int j = 0; j < nb; ++j) {
+      const float4 A = s_a[j];
+      if (A.z >= wthr) break;  // sorted by depth: the rest is culled for the whole warp
+      const float4 C = s_c[j];
+      if (A.y + C.w < wy0 || A.y - C.w > wy1) continue;  // misses this warp's rows
+      const float4 B = s_b[j];
+      const float q = quad_form(B.x, B.y, B.z, __fsub_rn(fpx, A.x), __fsub_rn(fpy, A.y));
+      if (INSTR) n_tested += inside;
+      if (q <= B.w && A.z < thr) {
+        if (INSTR) ++n_counted;
+        const float al = A.w * __expf(-0.5f * q);
+        if (MODE == GPS_BLEND_OIT) {
+          cr += al * C.x;
+          cg += al * C.y;
+          cb += al * C.z;
+          wsum += al;
+          zsum += al * A.z;
+        } else if (!done) {
+          const float a = fminf(al, kAlphaMax);
+          const float test = T * (1.0f - a);
+          if (test < kTMin) {
+            done = true;
+          } else {
+            const float aT = a * T;
+            cr += C.x * aT;
+            cg += C.y * aT;
+            cb += C.z * aT;
+            zsum += A.z * aT;
+            T = test;
+            last = b + j + 1;
+          }
+        }
+      }
+    }
+  }
+  if (INSTR) add_counters(v, 0, n_tested, n_counted);
+  float o0, o1, o2, od, ow;
+  if (MODE == GPS_BLEND_OIT) {
+    const float iN = 1.0f / (1.0f + wsum);
+    o0 = (ct0 + cr) * iN;
+    o1 = (ct1 + cg) * iN;
+    o2 = (ct2 + cb) * iN;
+    od = (dt + zsum) * iN;
+    ow = wsum;
+  } else {
+    o0 = cr + T * ct0;
+    o1 = cg + T * ct1;
+    o2 = cb + T * ct2;
+    od = zsum + T * dt;
+    ow = 1.0f - T;
+  }
+  if (inside) {
+    v.pix_a[pix] = make_float4(o0, o1, o2, od);
+    v.pix_b[pix] = make_float4(MODE == GPS_BLEND_OIT ? wsum : T, __uint_as_float(last), 0.f, 0.f);
+    if (v.out_rgb) {
+      v.out_rgb[pix] = o0;
+      v.out_rgb[npx + pix] = o1;
+      v.out_rgb[2 * npx + pix] = o2;
+    }
+    if (v.out_depth) v.out_depth[pix] = od;
+    if (v.out_weight) v.out_weight[pix] = ow;
+  }
+  if (has_tgt) {
+    float lr = 0.f, ld = 0.f, nv = 0.f;
+    if (inside) {
+      const float dk = __ldg(v.Dtgt + pix);
+      if (dk > 0.0f && dt > 0.0f) {
+        lr = fabsf(o0 - __ldg(v.Ctgt + pix)) + fabsf(o1 - __ldg(v.Ctgt + npx + pix)) +
+             fabsf(o2 - __ldg(v.Ctgt + 2 * npx + pix));
+        ld = fabsf(od - dk);
+        nv = 1.0f;
+      }
+    }
+    lr = warp_sum(lr);
+    ld = warp_sum(ld);
+    nv = warp_sum(nv);
+    __syncthreads();
+    if (lane == 0) {
+      s_tmp[warp * 3 + 0] = lr;
+      s_tmp[warp * 3 + 1] = ld;
+      s_tmp[warp * 3 + 2] = nv;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float a = 0.f, b = 0.f, c = 0.f;
+      for (int k = 0; k < NT / 32; ++k) {
+        a += s_tmp[k * 3];
+        b += s_tmp[k * 3 + 1];
+        c += s_tmp[k * 3 + 2];
+      }
+      v.tile_partials[tile] = make_float4(a, b, c, 0.f);
+    }
+  }
+}
+
+// Per-view loss from the tile partial sums, summed in a fixed order (FP64).
+// scalars: [0] view loss, [1] sum |C* - C|, [2] sum |D* - D|, [3] N_valid.
+// The total over views is accumulated into *loss (view 0 overwrites).
+__global__ void __launch_bounds__(256) finalize_loss_kernel(const float4* __restrict__ partials,
+                                                            int ntiles, float lambda_depth,
+                                                            float* scalars, float* loss, int first) {
+  __shared__ double s[3][256];
+  double a = 0, b = 0, c = 0;
+  for (int k = threadIdx.x; k < ntiles; k += 256) {
+    const float4 p = partials[k];
+    a += p.x;
+    b += p.y;
+    c += p.z;
+  }
+  s[0][threadIdx.x] = a;
+  s[1][threadIdx.x] = b;
+  s[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + o];
+      s[1][threadIdx.x] += s[1][threadIdx.x + o];
+      s[2][threadIdx.x] += s[2][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double n = s[2][0];
+    const double L = n > 0 ? s[0][0] / (3.0 * n) + (double)lambda_depth * s[1][0] / n : 0.0;
+    scalars[0] = (float)L;
+    scalars[1] = (float)s[0][0];
+    scalars[2] = (float)s[1][0];
+    scalars[3] = (float)n;
+    if (loss) *loss = first ? (float)L : *loss + (float)L;
+  }
+}
+
+// Upstream gradient of one pixel (already scaled).
+__device__ __forceinline__ void upstream(const ViewDev& v, long long pix, long long npx,
+                                         const float4& st, float dt, int fused, float lambda,
+                                         float scale, float& g0, float& g1, float& g2,
+                                         float& gD) {
+  if (fused) {
+    const float dk = __ldg(v.Dtgt + pix);
+    if (dk > 0.0f && dt > 0.0f) {
+      const float s3 = scale * (1.0f / 3.0f);
+      const float r0 = st.x - __ldg(v.Ctgt + pix), r1 = st.y - __ldg(v.Ctgt + npx + pix);
+      const float r2 = st.z - __ldg(v.Ctgt + 2 * npx + pix), rd = st.w - dk;
+      g0 = r0 > 0.f ? s3 : (r0 < 0.f ? -s3 : 0.f);
+      g1 = r1 > 0.f ? s3 : (r1 < 0.f ? -s3 : 0.f);
+      g2 = r2 > 0.f ? s3 : (r2 < 0.f ? -s3 : 0.f);
+      const float sl = lambda * scale;
+      gD = rd > 0.f ? sl : (rd < 0.f ? -sl : 0.f);
+    } else {
+      g0 = g1 = g2 = gD = 0.f;
+    }
+  } else {
+    g0 = v.g_rgb ? __ldg(v.g_rgb + pix) : 0.f;
+    g1 = v.g_rgb ? __ldg(v.g_rgb + npx + pix) : 0.f;
+    g2 = v.g_rgb ? __ldg(v.g_rgb + 2 * npx + pix) : 0.f;
+    gD = v.g_depth ? __ldg(v.g_depth + pix) : 0.f;
+  }
+}
+
+__device__ __forceinline__ float loss_scale(const ViewDev& v, int fused, const float* dloss) {
+  if (!fused) return 1.0f;
+  const float nv = v.scalars[3];
+  return (nv > 0.f ? 1.0f / nv : 0.f) * (dloss ? *dloss : 1.0f);
+}
+
+__device__ __forceinline__ void store_grad2d(const ViewDev& v, int deterministic, uint32_t k,
+                                             uint32_t gi, const float (&g)[10]) {
+  const float4 a = make_float4(g[0], g[1], g[2], g[3]);
+  const float4 b = make_float4(g[4], g[5], g[6], g[7]);
+  const float4 c = make_float4(g[8], g[9], 0.f, 0.f);
+  if (deterministic) {
+    float4* o = v.pair_grads + 3 * (size_t)k;
+    o[0] = a;
+    o[1] = b;
+    o[2] = c;
+  } else {
+    float4* o = v.grad2d + 3 * (size_t)gi;
+    atomicAdd(o, a);
+    atomicAdd(o + 1, b);
+    atomicAdd(reinterpret_cast<float2*>(o + 2), make_float2(c.x, c.y));
+  }
+}
+
+// ------------------------------------------------------- backward, OIT mode
+template <int TW, int TH, bool INSTR>
+__global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, float eps,
+                                                                   float lambda, const float* dloss,
+                                                                   int fused, int deterministic) {
+  constexpr int NT = TW * TH;
+  __shared__ float4 s_h[NT];
+  __shared__ float2 s_s[NT];
+  __shared__ float s_tmp[NT / 32];
+  const int W = v.cam.W, H = v.cam.H;
+  const int tile = blockIdx.x;
+  const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
+  const int tid = threadIdx.x;
+  const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
+  const bool inside = px < W && py < H;
+  const long long npx = (long long)W * H, pix = (long long)py * W + px;
+  const float scale = loss_scale(v, fused, dloss);
+  float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+  float sv = 0.f, thr = -INFINITY;
+  if (inside) {
+    const float4 st = v.pix_a[pix];
+    const float iN = 1.0f / (1.0f + v.pix_b[pix].x);
+    const float dt = __ldg(v.Dt + pix);
+    float g0, g1, g2, gD;
+    upstream(v, pix, npx, st, dt, fused, lambda, scale, g0, g1, g2, gD);
+    h = make_float4(g0 * iN, g1 * iN, g2 * iN, gD * iN);
+    sv = (g0 * st.x + g1 * st.y + g2 * st.z + gD * st.w) * iN;
+    if (g0 != 0.f || g1 != 0.f || g2 != 0.f || gD != 0.f) thr = depth_threshold(dt, eps);
+  }
+  s_h[tid] = h;
+  s_s[tid] = make_float2(sv, thr);
+  const float bthr = block_max<NT>(thr, s_tmp);
+  const uint2 r = v.tile_ranges[tile];
+  const uint32_t end = depth_cut(v.keys, r.x, r.y, bthr);
+  const int tx0 = tx * TW, ty0 = ty * TH;
+  unsigned n_tested = 0, n_counted = 0;
+  for (uint32_t b = r.x; b < end; b += NT) {
+    const uint32_t k = b + tid;
+    const bool has = k < end;
+    uint32_t gi = 0;
+    float mx = 0.f, my = 0.f, d = 0.f, sig = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, qmax = -1.f;
+    float cr = 0.f, cg = 0.f, cbl = 0.f;
+    int lx0 = TW, lx1 = -1, ly0 = TH, ly1 = -1;
+    if (has) {
+      gi = (uint32_t)v.keys[k];
+      const float4* rr = v.rec + 4 * (size_t)gi;
+      const float4 A = rr[0], B = rr[1], C = rr[2];
+      const float ey = rr[3].x;
+      mx = A.x; my = A.y; d = A.z; sig = A.w;
+      ca = B.x; cb = B.y; cc = B.z; qmax = B.w;
+      cr = C.x; cg = C.y; cbl = C.z;
+      int x0, x1, y0, y1;
+      if (record_rect(mx, my, C.w, ey, W, H, x0, x1, y0, y1)) {
+        lx0 = max(x0 - tx0, 0);
+        lx1 = min(x1 - tx0, TW - 1);
+        ly0 = max(y0 - ty0, 0);
+        ly1 = min(y1 - ty0, TH - 1);
+      }
+    }
+    // loop over the union of this warp's rectangles (warp-uniform bounds)
+    const int ux0 = warp_min_i(lx0), ux1 = warp_max_i(lx1);
+    const int uy0 = warp_min_i(ly0), uy1 = warp_max_i(ly1);
+    const float b2 = 2.0f * cb;
+    float dcr = 0.f, dcg = 0.f, dcb = 0.f, dd = 0.f, dsig = 0.f;
+    float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+    for (int yy = uy0; yy <= uy1; ++yy) {
+      const float dy = __fsub_rn((float)(ty0 + yy), my);
+      for (int xx = ux0; xx <= ux1; ++xx) {
+        const int p = yy * TW + xx;
+        const float2 ss = s_s[p];
+        const float dx = __fsub_rn((float)(tx0 + xx), mx);
+        const float q = quad_form(ca, b2, cc, dx, dy);
+        if (INSTR) n_tested += has && xx >= lx0 && xx <= lx1 && yy >= ly0 && yy <= ly1;
+        if (q <= qmax && d < ss.y) {
+          if (INSTR) ++n_counted;
+          const float4 hh = s_h[p];
+          const float G = __expf(-0.5f * q);
+          const float al = sig * G;
+          dcr += al * hh.x;
+          dcg += al * hh.y;
+          dcb += al * hh.z;
+          dd += al * hh.w;
+          const float dLda = hh.x * cr + hh.y * cg + hh.z * cbl + hh.w * d - ss.x;
+          dsig += G * dLda;
+          const float vv = dLda * al;
+          const float tx_ = vv * dx, ty_ = vv * dy;
+          sx += tx_;
+          sy += ty_;
+          sxx += tx_ * dx;
+          sxy += tx_ * dy;
+          syy += ty_ * dy;
+        }
+      }
+    }
+    if (has) {
+      const float g[10] = {ca * sx + cb * sy, cb * sx + cc * sy, -0.5f * sxx, -sxy, -0.5f * syy,
+                           dsig, dcr, dcg, dcb, dd};
+      store_grad2d(v, deterministic, k, gi, g);
+    }
+  }
+  if (INSTR) add_counters(v, 2, n_tested, n_counted);
+  if (deterministic) {
+    // pairs behind the depth cut contribute nothing; give their slots zeros
+    for (uint32_t k = end + tid; k < r.y; k += NT) {
+      float4* o = v.pair_grads + 3 * (size_t)k;
+      o[0] = o[1] = o[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// ----------------------------------------------------- backward, alpha mode
+constexpr int kAlphaBatch = 32;
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(ViewDev v, float eps,
+                                                                     float lambda,
+                                                                     const float* dloss, int fused,
+                                                                     int deterministic) {
+  constexpr int NT = TW * TH;
+  constexpr int NW = NT / 32;
+  __shared__ float4 s_a[kAlphaBatch], s_b[kAlphaBatch], s_c[kAlphaBatch];
+  __shared__ float s_part[NW][kAlphaBatch][10];
+  __shared__ float s_tmp[NW];
+  __shared__ uint32_t s_gi[kAlphaBatch];
+  const int W = v.cam.W, H = v.cam.H;
+  const int tile = blockIdx.x;
+  const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
+  const bool inside = px < W && py < H;
+  const long long npx = (long long)W * H, pix = (long long)py * W + px;
+  const float scale = loss_scale(v, fused, dloss);
+  const uint2 r = v.tile_ranges[tile];
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, T = 1.f, thr = -INFINITY;
+  float S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
+  uint32_t mylast = r.x;
+  if (inside) {
+    const float4 st = v.pix_a[pix];
+    const float4 sb = v.pix_b[pix];
+    const float dt = __ldg(v.Dt + pix);
+    upstream(v, pix, npx, st, dt, fused, lambda, scale, g0, g1, g2, gD);
+    T = sb.x;
+    mylast = min(max(__float_as_uint(sb.y), r.x), r.y);  // stays inside this tile's list
+    thr = depth_threshold(dt, eps);
+    S0 = T * __ldg(v.Ct + pix);
+    S1 = T * __ldg(v.Ct + npx + pix);
+    S2 = T * __ldg(v.Ct + 2 * npx + pix);
+    SD = T * dt;
+    if (g0 == 0.f && g1 == 0.f && g2 == 0.f && gD == 0.f) mylast = r.x;
+  }
+  const float fpx = (float)px, fpy = (float)py;
+  const float maxlast = block_max<NT>((float)(mylast - r.x), s_tmp);
+  const uint32_t top = r.x + (uint32_t)maxlast;
+  for (uint32_t hi = top; hi > r.x; hi = hi > r.x + kAlphaBatch ? hi - kAlphaBatch : r.x) {
+    const uint32_t lo = hi > r.x + kAlphaBatch ? hi - kAlphaBatch : r.x;
+    const int nb = (int)(hi - lo);
+    __syncthreads();
+    if (tid < nb) {
+      const uint32_t gi = (uint32_t)v.keys[lo + tid];
+      const float4* rr = v.rec + 4 * (size_t)gi;
+      float4 B = rr[1];
+      B.y = 2.0f * B.y;
+      s_a[tid] = rr[0];
+      s_b[tid] = B;
+      s_c[tid] = rr[2];
+      s_gi[tid] = gi;
+    }
+    __syncthreads();
+    for (int j = nb - 1; j >= 0; --j) {
+      const uint32_t k = lo + j;
+      float gv[10];
+#pragma unroll
+      for (int c = 0; c < 10; ++c) gv[c] = 0.f;
+      bool contrib = false;
+      if (k < mylast) {
+        const float4 A = s_a[j], B = s_b[j], C = s_c[j];
+        const float dx = __fsub_rn(fpx, A.x), dy = __fsub_rn(fpy, A.y);
+        const float q = quad_form(B.x, B.y, B.z, dx, dy);
+        if (q <= B.w && A.z < thr) {
+          const float G = __expf(-0.5f * q);
+          const float raw = A.w * G;
+          const bool clamped = raw > kAlphaMax;
+          const float a = fminf(raw, kAlphaMax);
+          const float ia = 1.0f / (1.0f - a);
+          const float Tj = T * ia;
+          const float aT = a * Tj;
+          gv[6] = g0 * aT;
+          gv[7] = g1 * aT;
+          gv[8] = g2 * aT;
+          gv[9] = gD * aT;
+          const float dLda = g0 * (C.x * Tj - S0 * ia) + g1 * (C.y * Tj - S1 * ia) +
+                             g2 * (C.z * Tj - S2 * ia) + gD * (A.z * Tj - SD * ia);
+          S0 += C.x * aT;
+          S1 += C.y * aT;
+          S2 += C.z * aT;
+          SD += A.z * aT;
+          T = Tj;
+          if (!clamped) {
+            const float vv = dLda * a;
+            const float cb = 0.5f * B.y;
+            gv[0] = vv * (B.x * dx + cb * dy);
+            gv[1] = vv * (cb * dx + B.z * dy);
+            gv[2] = -0.5f * vv * dx * dx;
+            gv[3] = -vv * dx * dy;
+            gv[4] = -0.5f * vv * dy * dy;
+            gv[5] = dLda * G;
+          }
+          contrib = true;
+        }
+      }
+      if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+        for (int c = 0; c < 10; ++c) gv[c] = warp_sum(gv[c]);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 10; ++c) s_part[warp][j][c] = gv[c];
+      }
+    }
+    __syncthreads();
+    // fixed-order sum over warps, then one write per (tile, Gaussian) pair
+    if (tid < nb) {
+      float g[10];
+#pragma unroll
+      for (int c = 0; c < 10; ++c) {
+        float acc = 0.f;
+        for (int w = 0; w < NW; ++w) acc += s_part[w][tid][c];
+        g[c] = acc;
+      }
+      store_grad2d(v, deterministic, lo + tid, s_gi[tid], g);
+    }
+  }
+  if (deterministic) {
+    for (uint32_t k = top + tid; k < r.y; k += NT) {
+      float4* o = v.pair_grads + 3 * (size_t)k;
+      o[0] = o[1] = o[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// Deterministic mode: per Gaussian, sum its pair slots in row-major tile order.
+__global__ void __launch_bounds__(256) gather_pair_grads_kernel(ViewDev v, int M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const float4 A = v.rec[4 * (size_t)i], C = v.rec[4 * (size_t)i + 2], E = v.rec[4 * (size_t)i + 3];
+  float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
+  int x0, x1, y0, y1;
+  if (record_rect(A.x, A.y, C.w, E.x, v.cam.W, v.cam.H, x0, x1, y0, y1)) {
+    const unsigned long long key = key_of(A.z, (uint32_t)i);
+    for (int ty = y0 / v.th; ty <= y1 / v.th; ++ty)
+      for (int tx = x0 / v.tw; tx <= x1 / v.tw; ++tx) {
+        const uint2 r = v.tile_ranges[ty * v.tiles_x + tx];
+        uint32_t lo = r.x, hi = r.y;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (v.keys[mid] < key) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < r.y && v.keys[lo] == key) {
+          const float4* p = v.pair_grads + 3 * (size_t)lo;
+          const float4 a = p[0], b = p[1], c = p[2];
+          s0.x += a.x; s0.y += a.y; s0.z += a.z; s0.w += a.w;
+          s1.x += b.x; s1.y += b.y; s1.z += b.z; s1.w += b.w;
+          s2.x += c.x; s2.y += c.y;
+        }
+      }
+  }
+  float4* o = v.grad2d + 3 * (size_t)i;
+  o[0] = s0;
+  o[1] = s1;
+  o[2] = s2;
+}
+
+// ------------------------------------------------------------------ launchers
+template <int TW, int TH>
+static cudaError_t fwd_tw(const ViewDev& v, float eps, int mode, int has_tgt, int instr,
+                          cudaStream_t st) {
+  const int ntiles = v.tiles_x * v.tiles_y;
+  if (mode == GPS_BLEND_OIT) {
+    if (instr)
+      composite_fwd_kernel<TW, TH, GPS_BLEND_OIT, true><<<ntiles, TW * TH, 0, st>>>(v, eps, has_tgt);
+    else
+      composite_fwd_kernel<TW, TH, GPS_BLEND_OIT, false><<<ntiles, TW * TH, 0, st>>>(v, eps, has_tgt);
+  } else {
+    if (instr)
+      composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, true><<<ntiles, TW * TH, 0, st>>>(v, eps, has_tgt);
+    else
+      composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, false><<<ntiles, TW * TH, 0, st>>>(v, eps, has_tgt);
+  }
+  return cudaGetLastError();
+}
+
+template <int TW, int TH>
+static cudaError_t bwd_tw(const ViewDev& v, float eps, float lambda, const float* dloss, int mode,
+                          int fused, int det, int instr, cudaStream_t st) {
+  const int ntiles = v.tiles_x * v.tiles_y;
+  if (mode == GPS_BLEND_OIT) {
+    if (instr)
+      composite_bwd_oit_kernel<TW, TH, true><<<ntiles, TW * TH, 0, st>>>(v, eps, lambda, dloss, fused, det);
+    else
+      composite_bwd_oit_kernel<TW, TH, false><<<ntiles, TW * TH, 0, st>>>(v, eps, lambda, dloss, fused, det);
+  } else
+    composite_bwd_alpha_kernel<TW, TH><<<ntiles, TW * TH, 0, st>>>(v, eps, lambda, dloss, fused,
+                                                                   det);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_composite_fwd(const ViewDev& v, float eps, int mode, int has_tgt, int instr,
+                                 cudaStream_t st) {
+  if (v.tw == 16 && v.th == 16) return fwd_tw<16, 16>(v, eps, mode, has_tgt, instr, st);
+  if (v.tw == 16 && v.th == 8) return fwd_tw<16, 8>(v, eps, mode, has_tgt, instr, st);
+  if (v.tw == 8 && v.th == 8) return fwd_tw<8, 8>(v, eps, mode, has_tgt, instr, st);
+  if (v.tw == 32 && v.th == 8) return fwd_tw<32, 8>(v, eps, mode, has_tgt, instr, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_composite_bwd(const ViewDev& v, float eps, float lambda, const float* dloss,
+                                 int mode, int fused, int det, int instr, cudaStream_t st) {
+  if (v.tw == 16 && v.th == 16) return bwd_tw<16, 16>(v, eps, lambda, dloss, mode, fused, det, instr, st);
+  if (v.tw == 16 && v.th == 8) return bwd_tw<16, 8>(v, eps, lambda, dloss, mode, fused, det, instr, st);
+  if (v.tw == 8 && v.th == 8) return bwd_tw<8, 8>(v, eps, lambda, dloss, mode, fused, det, instr, st);
+  if (v.tw == 32 && v.th == 8) return bwd_tw<32, 8>(v, eps, lambda, dloss, mode, fused, det, instr, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_finalize_loss(const ViewDev& v, float lambda, float* loss, int first,
+                                 cudaStream_t st) {
+  finalize_loss_kernel<<<1, 256, 0, st>>>(v.tile_partials, v.tiles_x * v.tiles_y, lambda, v.scalars,
+                                          loss, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_pair_grads(const ViewDev& v, int M, cudaStream_t st) {
+  gather_pair_grads_kernel<<<(M + 255) / 256, 256, 0, st>>>(v, M);
+  return cudaGetLastError();
+}
+
+}  // namespace gps

@@ -1,0 +1,92 @@
+// Shared device helpers of libgps (sm_103a).  Internal header.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gps.h"
+
+namespace gps {
+
+constexpr int kRecFloats = 16;    // projected record, see GpsWorkspaceLayout
+constexpr int kGrad2d = 12;       // per-Gaussian 2D gradient slots
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kExtRel = 1.0f + 0.0078125f;  // 1 + 2^-7: conservative extent
+constexpr float kExtAbs = 0.0625f;             // 2^-4 px
+constexpr float kAlphaMax = 0.99f;             // Table 7 variant (3DGS clamp)
+constexpr float kTMin = 1e-4f;                 // Table 7 variant termination
+
+// grad2d slot names
+enum { G_MX = 0, G_MY, G_CA, G_CB, G_CC, G_SIG, G_R, G_G, G_B, G_D };
+
+struct Cam {
+  float fx, fy, cx, cy;
+  int W, H;
+  float R[9];  // camera -> world
+  float t[3];
+};
+
+// Per-view device-side description (passed by value to kernels).
+struct ViewDev {
+  Cam cam;
+  const float* Ct;    // [3][H][W]
+  const float* Dt;    // [H][W]
+  const float* Ctgt;  // nullable
+  const float* Dtgt;  // nullable
+  float* out_rgb;
+  float* out_depth;
+  float* out_weight;
+  const float* g_rgb;    // nullable
+  const float* g_depth;  // nullable
+  // workspace regions
+  float4* rec;           // [M][4] float4
+  uint32_t* tile_counts;
+  uint2* tile_ranges;
+  uint32_t* tile_cursor;  // shares the tile_counts region after the scan
+  unsigned long long* keys;
+  unsigned long long* keys_tmp;
+  float4* pix_a;  // [npx] (C*.rgb, D*)
+  float4* pix_b;  // [npx] (W_G | T_end, n_last, -, -)
+  float4* tile_partials;  // [tiles] (sum|dC|, sum|dD|, n_valid, -)
+  float* scalars;         // [8]
+  float4* grad2d;         // [M][3] float4
+  float4* pair_grads;     // [cap][3] float4
+  int tiles_x, tiles_y, tw, th;
+  long long cap;
+};
+
+// Pixel rectangle of a record, clipped to the image: [x0, x1] x [y0, y1].
+// Float arithmetic spelled out so that the oracle can reproduce it bit for bit.
+__device__ __forceinline__ bool record_rect(float mx, float my, float ex, float ey, int W, int H,
+                                            int& x0, int& x1, int& y0, int& y1) {
+  if (!(ex >= 0.0f) || !(ey >= 0.0f)) return false;
+  const float lx = __fsub_rn(mx, ex), hx = __fadd_rn(mx, ex);
+  const float ly = __fsub_rn(my, ey), hy = __fadd_rn(my, ey);
+  if (!(hx >= 0.0f) || !(lx <= (float)(W - 1)) || !(hy >= 0.0f) || !(ly <= (float)(H - 1)))
+    return false;
+  x0 = max(0, (int)ceilf(fmaxf(lx, -1.0f)));
+  x1 = min(W - 1, (int)floorf(fminf(hx, (float)W)));
+  y0 = max(0, (int)ceilf(fmaxf(ly, -1.0f)));
+  y1 = min(H - 1, (int)floorf(fminf(hy, (float)H)));
+  return x0 <= x1 && y0 <= y1;
+}
+
+// q = dx (a dx + 2b dy) + (c dy) dy with explicit roundings (identical on the
+// oracle's FP32 decision path).  b2 = 2 b.
+__device__ __forceinline__ float quad_form(float a, float b2, float c, float dx, float dy) {
+  const float s2 = __fmaf_rn(a, dx, __fmul_rn(b2, dy));
+  const float s3 = __fmul_rn(__fmul_rn(c, dy), dy);
+  return __fmaf_rn(dx, s2, s3);
+}
+
+__device__ __forceinline__ float depth_threshold(float Dt, float eps) {
+  return Dt > 0.0f ? __fadd_rn(Dt, eps) : __int_as_float(0x7f800000);
+}
+
+__device__ __forceinline__ unsigned long long key_of(float d, uint32_t idx) {
+  return ((unsigned long long)__float_as_uint(d) << 32) | idx;
+}
+
+// status word helpers
+__device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+}  // namespace gps

@@ -1,0 +1,133 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function include/gps.h declares, the ctypes mirrors match the C struct
+layouts, and argument validation rejects bad calls before any launch."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2509_11574_b300 as gps
+from paper_2509_11574_b300 import build as gbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gps.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    gbuild.build()
+    return gps.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return re.findall(r"GPS_API\s+[\w\s\*]+?\b(\w+)\s*\(", src)
+
+
+def test_header_declares_the_five_calls():
+    names = declared_functions()
+    for n in ("fuse_frame", "raycast_sdf", "render_forward", "render_backward", "adam_step"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", gps.LIB_PATH]).decode()
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    for n in declared_functions():
+        assert n in exported, n
+        assert hasattr(L, n)
+    assert set(gps.EXPORTED) == set(declared_functions())
+
+
+def test_struct_layouts_match_header(tmp_path):
+    structs = ["GpsIntrinsics", "GpsPose", "GpsTsdf", "GpsGaussians", "GpsView",
+               "GpsRenderSettings", "GpsAdamHyper", "GpsWorkspaceLayout"]
+    prog = tmp_path / "sz.c"
+    body = "".join(f'  printf("{s} %zu\\n", sizeof({s}));\n' for s in structs)
+    body += '  printf("off_pair_capacity %zu\\n", offsetof(GpsRenderSettings, pair_capacity));\n'
+    body += '  printf("off_grad_depth %zu\\n", offsetof(GpsView, grad_depth));\n'
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gps.h"\nint main(){\n'
+                    + body + "  return 0;\n}\n")
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
+    sizes = dict(ln.split() for ln in subprocess.check_output([str(exe)]).decode().splitlines())
+    for s in structs:
+        assert int(sizes[s]) == ctypes.sizeof(getattr(gps, s)), s
+    assert int(sizes["off_pair_capacity"]) == gps.GpsRenderSettings.pair_capacity.offset
+    assert int(sizes["off_grad_depth"]) == gps.GpsView.grad_depth.offset
+
+
+class _Cam:
+    def __init__(self, W, H):
+        self.fx = self.fy = 100.0
+        self.cx, self.cy = W / 2, H / 2
+        self.width, self.height = W, H
+        self.R = [1, 0, 0, 0, 1, 0, 0, 0, 1]
+        self.t = [0, 0, 0]
+
+
+def test_workspace_size_and_layout_host_only(L):
+    s = gps.settings()
+    cams = [_Cam(160, 120), _Cam(77, 33)]
+    n = gps.gps_workspace_size(2000, cams, s)
+    assert n > 0 and n % 256 == 0
+    L0 = gps.gps_workspace_layout(2000, cams, s, 0)
+    L1 = gps.gps_workspace_layout(2000, cams, s, 1)
+    assert L0.tiles_x == 10 and L0.tiles_y == 8 and L1.tiles_x == 5 and L1.tiles_y == 3
+    assert L0.records < L0.pair_keys < L0.grad2d < L1.records
+    for off in (L0.records, L0.pair_keys, L0.pix_state, L1.grad2d):
+        assert off % 256 == 0
+    assert L0.pair_capacity == 64 * 2000
+    s2 = gps.settings(deterministic=True)
+    assert gps.gps_workspace_size(2000, cams, s2) > n
+    with pytest.raises(gps.GpsError) as e:
+        gps.gps_workspace_size(2000, cams, gps.settings(tile=(12, 12)))
+    assert e.value.code == gps.GPS_ERR_INVALID_ARG
+    with pytest.raises(gps.GpsError):
+        gps.gps_workspace_size(2000, [_Cam(0, 10)], s)
+
+
+def test_invalid_arguments_fail_before_launch(L):
+    K = gps.GpsIntrinsics(100.0, 100.0, 10.0, 10.0, 20, 20)
+    P = gps.GpsPose((ctypes.c_float * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1), (ctypes.c_float * 3)(0, 0, 0))
+    vol = gps.GpsTsdf(12, 8, 8, 0.01, (ctypes.c_float * 3)(0, 0, 0), 0.03, 100.0, None, None, None)
+    assert L.fuse_frame(ctypes.byref(vol), None, None, ctypes.byref(K), ctypes.byref(P), None) \
+        == gps.GPS_ERR_INVALID_ARG
+    assert b"NULL" in L.gps_last_error()
+    fake = ctypes.c_void_p(4096)
+    assert L.fuse_frame(ctypes.byref(vol), fake, fake, ctypes.byref(K), ctypes.byref(P), None) \
+        == gps.GPS_ERR_INVALID_ARG  # nx = 12 is not a multiple of 8
+    g = gps.GpsGaussians(None, None, None, None, None, 10)
+    v = (gps.GpsView * 1)(gps.GpsView(K, P))
+    s = gps.settings()
+    assert L.render_forward(ctypes.byref(g), v, 1, ctypes.byref(s), fake, 1 << 20, None, None) \
+        == gps.GPS_ERR_INVALID_ARG
+    gz = gps.GpsGaussians(None, None, None, None, None, 0)
+    # sdf images missing
+    assert L.render_forward(ctypes.byref(gz), v, 1, ctypes.byref(s), fake, 1 << 20, None, None) \
+        == gps.GPS_ERR_INVALID_ARG
+    v[0].sdf_rgb = fake
+    v[0].sdf_depth = fake
+    # workspace too small
+    assert L.render_forward(ctypes.byref(gz), v, 1, ctypes.byref(s), fake, 256, None, None) \
+        == gps.GPS_ERR_WORKSPACE_TOO_SMALL
+    bad = gps.settings(blend_mode=7)
+    assert L.render_forward(ctypes.byref(gz), v, 1, ctypes.byref(bad), fake, 1 << 30, None, None) \
+        == gps.GPS_ERR_INVALID_ARG
+    h = gps.GpsAdamHyper((ctypes.c_float * 5)(*gps.LR_APP_C), 0.9, 0.999, 1e-15)
+    assert L.adam_step(ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(gz),
+                       ctypes.byref(h), 0, None, None) == gps.GPS_ERR_INVALID_ARG
+
+
+def test_layout_helpers_roundtrip():
+    import torch
+    a = torch.arange(16 * 8 * 24 * 3, dtype=torch.float32).reshape(16, 8, 24, 3)  # nz, ny, nx
+    b = gps.linear_to_brick(a)
+    assert b.shape == (16 * 8 * 24, 3)
+    # voxel (x=9, y=3, z=10): brick (1, 0, 1), local (1, 3, 2)
+    nbx, nby = 3, 1
+    idx = ((1 * nby + 0) * nbx + 1) * 512 + 2 * 64 + 3 * 8 + 1
+    assert torch.equal(b[idx], a[10, 3, 9])
+    assert torch.equal(gps.brick_to_linear(b, 24, 8, 16), a)

@@ -1,0 +1,345 @@
+"""CUDA path vs the FP64 oracle, through the C ABI.
+
+Stage by stage (each stage fed identical inputs, written into the workspace
+where needed) and end to end.  Tolerances (derived in the design doc from FP32
+arithmetic): images 1e-4 absolute, depth 1e-4 relative, gradients per tensor
+||g - o||_inf <= 1e-4 ||o||_inf and 1e-4 relative elementwise where
+|o| > 1e-3 ||o||_inf; binning and sort order bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2509_11574_b300 as gps
+from datagen import GaussianSet, workloads
+
+from helpers import assert_grads_close, cuda, oracle_sdf_images, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2509_11574_b300 import build
+    build.build()
+    gps.lib()
+
+
+# ------------------------------------------------------------------ TSDF
+@pytest.mark.parametrize("name", ["tiny", "small"])
+def test_fuse_matches_oracle(name):
+    w = workload(name)
+    vol_o = oracle.Volume(w.tsdf)
+    vol_g = gps.Tsdf(w.tsdf)
+    for _ in range(2):  # fuse the same frame twice: running average and weights
+        f = w.frames[0]
+        oracle.fuse(vol_o, f.depth, f.rgb, f.cam)
+        gps.fuse_frame(vol_g, cuda(f.depth), cuda(f.rgb), f.cam)
+    torch.cuda.synchronize()
+    sdf, wt, rgbw = (t.cpu().numpy() for t in vol_g.linear())
+    ok = vol_o.amb == 0
+    assert ok.mean() > 0.99
+    assert (vol_o.w > 0).sum() > 1000
+    np.testing.assert_array_equal(wt[ok], vol_o.w[ok])
+    np.testing.assert_allclose(sdf[ok], vol_o.sdf[ok], atol=2e-6)
+    np.testing.assert_allclose(rgbw[..., :3][ok], vol_o.rgb[ok], atol=2e-6)
+    np.testing.assert_array_equal(rgbw[..., 3][ok], vol_o.cw[ok])
+
+
+@pytest.mark.parametrize("name", ["tiny", "small"])
+def test_raycast_matches_oracle(name):
+    w = workload(name)
+    vol_o = oracle.Volume(w.tsdf)
+    f = w.frames[0]
+    oracle.fuse(vol_o, f.depth, f.rgb, f.cam)
+    # both sides ray-cast the same float32 volume
+    sdf32 = vol_o.sdf.astype(np.float32)
+    rgb32 = vol_o.rgb.astype(np.float32)
+    Ct, Dt, V, amb = oracle.raycast(w.tsdf, sdf32, rgb32, f.cam)
+    vg = gps.Tsdf(w.tsdf)
+    vg.sdf.copy_(gps.linear_to_brick(torch.from_numpy(sdf32)).cuda())
+    rgbw = np.concatenate([rgb32, np.ones(rgb32.shape[:3] + (1,), np.float32)], -1)
+    vg.rgbw.copy_(gps.linear_to_brick(torch.from_numpy(rgbw)).cuda())
+    c, d = gps.raycast_sdf(vg, f.cam)
+    c, d = c.cpu().numpy(), d.cpu().numpy()
+    ok = amb == 0
+    assert ok.mean() > 0.98, ok.mean()
+    np.testing.assert_array_equal(d[ok] > 0, Dt[ok] > 0)
+    hit = ok & (Dt > 0)
+    assert hit.sum() > 100
+    np.testing.assert_allclose(d[hit], Dt[hit], rtol=1e-4)
+    np.testing.assert_allclose(c[:, hit], Ct[:, hit], atol=1e-4)
+
+
+# ------------------------------------------------------------ projection
+def _renderer(w, cams, **kw):
+    s = gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, near=w.near, **kw)
+    return gps.Renderer(w.gaussians.M, cams, s)
+
+
+def _records(r: gps.Renderer, view=0):
+    return r.region(view, "records", torch.float32, r.M * 16).view(r.M, 16).cpu().numpy()
+
+
+def test_projection_matches_oracle():
+    w = workload("grad")
+    f = w.frames[0]
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    rec_o, amb = oracle.project(w.gaussians.astype(np.float64), f.cam)
+    r = _renderer(w, [f.cam], stages=gps.STAGE_PROJECT)
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    v = gps.View(f.cam, cuda(Ct), cuda(Dt))
+    r.forward(g, [v])
+    rec_g = _records(r)
+    vis_o = rec_o[:, oracle.R_VIS] > 0
+    vis_g = rec_g[:, 11] >= 0
+    ok = amb == 0
+    # the kernel's conservative extent may keep a Gaussian whose exact support
+    # misses the image; it then has no counted pixels
+    assert np.all(vis_g[ok & vis_o])
+    both = vis_o & vis_g & ok
+    assert both.sum() > 1000
+    pairs = [(0, oracle.R_MX), (1, oracle.R_MY), (2, oracle.R_D), (3, oracle.R_SIG),
+             (4, oracle.R_CA), (5, oracle.R_CB), (6, oracle.R_CC), (7, oracle.R_QMAX),
+             (8, oracle.R_R), (9, oracle.R_G), (10, oracle.R_B)]
+    for kg, ko in pairs:
+        a, b = rec_g[both, kg].astype(np.float64), rec_o[both, ko]
+        scale = np.maximum(np.abs(b), 1e-3 * np.abs(b).max())
+        if kg == 5:  # off-diagonal conic: relative to the diagonal
+            scale = np.maximum(scale, 1e-3 * np.sqrt(rec_o[both, oracle.R_CA] * rec_o[both, oracle.R_CC]))
+        err = np.abs(a - b) / scale
+        assert err.max() < 2e-4, (kg, err.max())
+
+
+# --------------------------------------------------------------- binning
+@pytest.mark.parametrize("tile", [(16, 16), (16, 8), (8, 8), (32, 8)])
+def test_binning_bit_exact(tile):
+    """Identical FP32 records in, identical sorted (tile, depth, index) lists out."""
+    w = workload("small", M=3000, width=150, height=100)  # ragged tiles
+    f = w.frames[0]
+    rec_o, _ = oracle.project(w.gaussians.astype(np.float64), f.cam)
+    r32 = oracle.records_f32(rec_o)
+    keys_o, vals_o, ranges_o = oracle.bin_records(r32, f.cam.width, f.cam.height, *tile)
+    r = _renderer(w, [f.cam], stages=gps.STAGE_BIN, tile=tile)
+    r.region(0, "records", torch.float32, r.M * 16).copy_(torch.from_numpy(r32.reshape(-1)).cuda())
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    Ct, Dt = np.zeros((3, f.cam.height, f.cam.width), np.float32), np.zeros((f.cam.height, f.cam.width), np.float32)
+    r.forward(g, [gps.View(f.cam, cuda(Ct), cuda(Dt))])
+    L = r.layout(0)
+    nt = L.tiles_x * L.tiles_y
+    ranges = r.region(0, "tile_ranges", torch.int32, nt * 2).view(nt, 2).cpu().numpy().astype(np.uint32)
+    P = int(ranges[:, 1].max())
+    keys = r.region(0, "pair_keys", torch.int64, P).cpu().numpy().view(np.uint64)
+    assert P == len(keys_o) > 1000
+    # identical per-tile segments (an empty tile's start is immaterial)
+    np.testing.assert_array_equal(ranges[:, 1] - ranges[:, 0], ranges_o[:, 1] - ranges_o[:, 0])
+    ne = ranges_o[:, 1] > ranges_o[:, 0]
+    np.testing.assert_array_equal(ranges[ne], ranges_o[ne])
+    # device key = bits(d) << 32 | index inside each tile; oracle key = tile << 32 | bits(d)
+    np.testing.assert_array_equal(keys >> np.uint64(32), keys_o & np.uint64(0xffffffff))
+    np.testing.assert_array_equal((keys & np.uint64(0xffffffff)).astype(np.uint32), vals_o)
+    assert r.status() == gps.GPS_OK
+
+
+def test_binning_capacity_overflow_is_reported():
+    w = workload("tiny")
+    f = w.frames[0]
+    r = _renderer(w, [f.cam], pair_capacity=8)
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    r.forward(g, [gps.View(f.cam, cuda(Ct), cuda(Dt))])
+    assert r.status() == gps.GPS_ERR_CAPACITY
+
+
+# ---------------------------------------------- composite, staged inputs
+def _staged(w, mode, tile=(16, 16)):
+    f = w.frames[0]
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    rec_o, _ = oracle.project(w.gaussians.astype(np.float64), f.cam)
+    r32 = oracle.records_f32(rec_o)
+    rr = oracle.rounded(rec_o)  # FP64 copies of the FP32 values (decisions in FP32)
+    r = _renderer(w, [f.cam], blend_mode=mode, tile=tile,
+                  stages=gps.STAGE_BIN | gps.STAGE_COMPOSITE | gps.STAGE_COMPOSITE_BWD)
+    r.region(0, "records", torch.float32, r.M * 16).copy_(torch.from_numpy(r32.reshape(-1)).cuda())
+    return f, Ct, Dt, rr, r
+
+
+@pytest.mark.parametrize("mode", [gps.BLEND_OIT, gps.BLEND_ALPHA])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_composite_forward_and_backward_staged(mode, tile):
+    """Same FP32 records and images on both sides: identical counting
+    decisions, so images match to FP32 accumulation error and the 2D
+    gradients to 1e-4."""
+    w = workload("small", M=3000, width=150, height=100)
+    f, Ct, Dt, rr, r = _staged(w, mode, tile)
+    H, W = f.cam.height, f.cam.width
+    out = oracle.composite(rr, Ct, Dt, w.eps_depth, mode, f32=True)
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    v = gps.View(f.cam, cuda(Ct), cuda(Dt), out_rgb=torch.empty(3, H, W, device="cuda"),
+                 out_depth=torch.empty(H, W, device="cuda"),
+                 out_weight=torch.empty(H, W, device="cuda"))
+    r.forward(g, [v])
+    ok = out["amb"] == 0
+    assert ok.mean() > 0.999
+    np.testing.assert_allclose(v.out_rgb.cpu().numpy()[:, ok], out["C"][:, ok], atol=1e-5)
+    np.testing.assert_allclose(v.out_depth.cpu().numpy()[ok], out["D"][ok], rtol=1e-5)
+    np.testing.assert_allclose(v.out_weight.cpu().numpy()[ok], out["W"][ok], rtol=1e-5, atol=1e-6)
+    # backward with explicit upstream gradients (random signs, like an L1 loss)
+    rng = np.random.default_rng(0)
+    dC = (rng.choice([-1.0, 1.0], size=(3, H, W)) / (3 * H * W)).astype(np.float32)
+    dD = (rng.choice([-1.0, 1.0], size=(H, W)) / (H * W)).astype(np.float32)
+    g2_o = oracle.composite_backward(rr, Ct, Dt, w.eps_depth, dC, dD, mode, f32=True)
+    v.grad_rgb, v.grad_depth = cuda(dC), cuda(dD)
+    grads = g.zeros_like()
+    r.backward(g, [v], grads)
+    g2 = r.region(0, "grad2d", torch.float32, r.M * 12).view(r.M, 12).cpu().numpy()[:, :10]
+    excl = None
+    if mode == gps.BLEND_ALPHA:  # Gaussians seen at pixels with a clamp/termination tie
+        amb_px = out["amb"] != 0
+        excl = np.zeros(r.M, bool)
+        ys, xs = np.nonzero(amb_px)
+        for i in range(r.M):
+            if rr[i, oracle.R_VIS] and len(xs):
+                ex, ey = rr[i, oracle.R_EX] + 1, rr[i, oracle.R_EY] + 1
+                excl[i] = np.any((np.abs(xs - rr[i, oracle.R_MX]) <= ex) & (np.abs(ys - rr[i, oracle.R_MY]) <= ey))
+    names = ["mx", "my", "ca", "cb", "cc", "sig", "r", "g", "b", "d"]
+    assert_grads_close({n: g2[:, k] for k, n in enumerate(names)},
+                       {n: g2_o[:, k] for k, n in enumerate(names)}, exclude=excl,
+                       label=f"grad2d mode={mode}")
+
+
+def test_projection_backward_staged():
+    """Identical 2D gradients in: the parameter gradients of the projection adjoint."""
+    w = workload("grad")
+    f = w.frames[0]
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    g64 = w.gaussians.astype(np.float64)
+    rng = np.random.default_rng(3)
+    g2 = rng.normal(size=(w.gaussians.M, 10)).astype(np.float32)
+    ref = oracle.project_backward(g64, f.cam, g2.astype(np.float64))
+    rec_o, amb = oracle.project(g64, f.cam)
+    r = _renderer(w, [f.cam], stages=gps.STAGE_PROJECT_BWD)
+    g2pad = np.zeros((w.gaussians.M, 12), np.float32)
+    g2pad[:, :10] = g2
+    r.region(0, "grad2d", torch.float32, r.M * 12).copy_(torch.from_numpy(g2pad.reshape(-1)).cuda())
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    v = gps.View(f.cam, cuda(Ct), cuda(Dt), grad_rgb=cuda(np.zeros_like(Ct)))
+    grads = g.zeros_like()
+    r.backward(g, [v], grads)
+    got = {k: t.cpu().numpy() for k, t in zip(ref.keys(), grads.tensors())}
+    vis = (rec_o[:, oracle.R_VIS] > 0) & (amb == 0)
+    for k in ref:
+        ref[k] = np.where(vis.reshape((-1,) + (1,) * (ref[k].ndim - 1)), ref[k], 0)
+        got[k] = np.where(vis.reshape((-1,) + (1,) * (got[k].ndim - 1)), got[k], 0)
+    # the adjoint of a projection with cond(Sigma_2D) up to ~1e4 in FP32
+    assert_grads_close(got, ref, norm_tol=1e-4, elem_tol=1e-3, label="project_backward")
+
+
+# ---------------------------------------------------------- end to end
+@pytest.mark.parametrize("mode", [gps.BLEND_OIT, gps.BLEND_ALPHA])
+def test_end_to_end_small(mode):
+    """Full pipeline (projection, binning, composite, fused loss, backward) on
+    the 160x120 sphere+box frame with 2,000 Gaussians vs the FP64 oracle."""
+    w = workload("small")
+    _end_to_end(w, mode, lam=0.0)
+
+
+def test_end_to_end_grad_config():
+    """320x240 view, 20,000 Gaussians, colour + depth L1."""
+    w = workload("grad")
+    _end_to_end(w, gps.BLEND_OIT, lam=1.0)
+
+
+def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False):
+    f = w.frames[0]
+    H, W = f.cam.height, f.cam.width
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    ref = oracle.render_loss_grads(w.gaussians.astype(np.float64), f.cam, Ct, Dt, f.rgb, f.depth,
+                                   eps=w.eps_depth, lambda_depth=lam, mode=mode)
+    s = gps.settings(eps_depth=w.eps_depth, lambda_depth=lam, blend_mode=mode, tile=tile,
+                     deterministic=deterministic)
+    r = gps.Renderer(w.gaussians.M, [f.cam], s)
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    v = gps.View(f.cam, cuda(Ct), cuda(Dt), cuda(f.rgb), cuda(f.depth),
+                 out_rgb=torch.empty(3, H, W, device="cuda"), out_depth=torch.empty(H, W, device="cuda"))
+    loss = torch.zeros(1, device="cuda")
+    r.forward(g, [v], loss)
+    grads = g.zeros_like()
+    r.backward(g, [v], grads)
+    assert r.status() == gps.GPS_OK
+    margin = ref["out"]["margin"]
+    ok = (margin > 1e-4) & (ref["out"]["amb"] == 0)
+    frac = 1.0 - ok.mean()
+    assert frac < 0.02, frac
+    np.testing.assert_allclose(v.out_rgb.cpu().numpy()[:, ok], ref["out"]["C"][:, ok], atol=1e-4)
+    np.testing.assert_allclose(v.out_depth.cpu().numpy()[ok], ref["out"]["D"][ok], rtol=1e-4)
+    np.testing.assert_allclose(loss.item(), ref["L"], rtol=1e-4)
+    got = {k: t.cpu().numpy() for k, t in zip(ref["grads"].keys(), grads.tensors())}
+    # elementwise test skips Gaussians touching a pixel where some counting
+    # decision sits within 1e-4 of its threshold (FP32 and FP64 may differ)
+    rec = ref["rec"]
+    bad_px = ~ok
+    ys, xs = np.nonzero(bad_px)
+    excl = np.zeros(w.gaussians.M, bool)
+    for i in np.nonzero(rec[:, oracle.R_VIS] > 0)[0]:
+        ex, ey = rec[i, oracle.R_EX] + 1, rec[i, oracle.R_EY] + 1
+        excl[i] = np.any((np.abs(xs - rec[i, oracle.R_MX]) <= ex) & (np.abs(ys - rec[i, oracle.R_MY]) <= ey))
+    excl |= ref["proj_amb"] != 0
+    worst = assert_grads_close(got, ref["grads"], exclude=excl, elem_tol=1e-3, label="e2e")
+    print("excluded pixels", frac, "excluded Gaussians", excl.mean(), worst)
+
+
+def test_deterministic_mode_is_bitwise_reproducible_and_matches():
+    w = workload("small")
+    f = w.frames[0]
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    outs = []
+    for det in (True, True, False):
+        s = gps.settings(eps_depth=w.eps_depth, deterministic=det)
+        r = gps.Renderer(w.gaussians.M, [f.cam], s)
+        g = gps.Gaussians.from_numpy(w.gaussians)
+        v = gps.View(f.cam, cuda(Ct), cuda(Dt), cuda(f.rgb), cuda(f.depth))
+        loss = torch.zeros(1, device="cuda")
+        r.forward(g, [v], loss)
+        grads = g.zeros_like()
+        r.backward(g, [v], grads)
+        outs.append(grads.flat().cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_allclose(outs[0], outs[2], atol=1e-6 * np.abs(outs[2]).max())
+
+
+# ------------------------------------------------------------------ Adam
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(0)
+    M = 1001  # odd sizes exercise the scalar tails
+    gs = GaussianSet(rng.normal(size=(M, 3)), rng.normal(size=(M, 3)), rng.normal(size=(M, 4)),
+                     rng.normal(size=M), rng.uniform(size=(M, 3))).astype(np.float32)
+    p = gps.Gaussians.from_numpy(gs)
+    opt = gps.Adam(p)
+    ref = [a.astype(np.float64).copy() for a in gs.arrays()]
+    m = [np.zeros_like(a) for a in ref]
+    vv = [np.zeros_like(a) for a in ref]
+    for step in range(1, 4):
+        gr = [rng.normal(size=a.shape).astype(np.float32) for a in ref]
+        grads = gps.Gaussians(*[torch.from_numpy(x).cuda() for x in gr])
+        opt.step(grads)
+        for k in range(5):
+            oracle.adam(ref[k].reshape(-1), gr[k].astype(np.float64).reshape(-1), m[k].reshape(-1),
+                        vv[k].reshape(-1), gps.LR_APP_C[k], 0.9, 0.999, 1e-15, step)
+        assert float(grads.flat().abs().max()) == 0.0  # zeroed in the same pass
+    for k, t in enumerate(p.tensors()):
+        np.testing.assert_allclose(t.cpu().numpy(), ref[k], rtol=1e-6, atol=1e-6 * gps.LR_APP_C[k])
+
+
+def test_adam_device_step_counter_matches_host_steps():
+    rng = np.random.default_rng(1)
+    gs = GaussianSet(*(rng.normal(size=s) for s in ((64, 3), (64, 3), (64, 4), (64,), (64, 3)))).astype(np.float32)
+    pa, pb = gps.Gaussians.from_numpy(gs), gps.Gaussians.from_numpy(gs)
+    oa, ob = gps.Adam(pa), gps.Adam(pb, device_step=True)
+    for _ in range(3):
+        gr = [torch.from_numpy(rng.normal(size=a.shape).astype(np.float32)).cuda() for a in gs.arrays()]
+        oa.step(gps.Gaussians(*[x.clone() for x in gr]))
+        ob.step(gps.Gaussians(*[x.clone() for x in gr]))
+    assert int(ob.device_step.item()) == 3
+    for a, b in zip(pa.tensors(), pb.tensors()):
+        assert torch.equal(a, b)
