@@ -147,25 +147,35 @@ def project(g, cam, near=0.2):
     return rec, amb
 
 
-def composite(rec, Ct, Dt, eps, mode=OIT, f32=False, brute=False, window=None):
+def composite(rec, Ct, Dt, eps, mode=OIT, f32=False, brute=False, window=None,
+              band=(4e-6, 2e-6)):
     """Eq. 1-4 (mode OIT) or the Table 7 variant (mode ALPHA) for one view.
-    Returns dict C [3][H][W], D, W (= W_G), T (T_end), n (counted), amb, and
-    margin: per pixel, the smallest relative distance of a counting decision
-    (alpha vs 1/255, d vs D_t + eps) to its threshold."""
+    Returns dict C [3][H][W], D, W (= W_G), T (T_end), n (counted), amb, and the
+    flip allowance: allow_C, allow_D [H][W] bound how far C*, D* can move if
+    the counting decisions within `band` of their thresholds went the other
+    way (band[0]: relative error of the conic, scaled by the magnitude of the
+    quadratic form's terms; band[1]: relative error of d vs D_t + eps);
+    g_amb [M] sums the alpha
+    of a Gaussian's such decisions, g_mass [M] its total counted alpha."""
     Ct = _f64(Ct)
     Dt = _f64(Dt)
     H, W = Dt.shape
     x0, x1, y0, y1 = window if window is not None else (0, W - 1, 0, H - 1)
     rec = _f64(rec)
+    M = rec.shape[0]
     out = dict(C=np.zeros((3, H, W)), D=np.zeros((H, W)), W=np.zeros((H, W)),
-               T=np.zeros((H, W)), n=np.zeros((H, W), np.int32), amb=np.zeros((H, W), np.int32),
-               margin=np.full((H, W), np.inf))
-    lib().orc_composite(ctypes.c_int(rec.shape[0]), _p(rec), ctypes.c_int(W), ctypes.c_int(H),
+               T=np.zeros((H, W)), n=np.zeros((H, W), np.int32), amb=np.zeros((H, W), np.int32))
+    allow = np.zeros((2, H, W))
+    g_amb, g_mass = np.zeros(M), np.zeros(M)
+    b = _f64(band)
+    lib().orc_composite(ctypes.c_int(M), _p(rec), ctypes.c_int(W), ctypes.c_int(H),
                         _p(Ct), _p(Dt), ctypes.c_double(eps), ctypes.c_int(mode),
                         ctypes.c_int(int(f32)), ctypes.c_int(int(brute)), ctypes.c_int(x0),
                         ctypes.c_int(x1), ctypes.c_int(y0), ctypes.c_int(y1), _p(out["C"]),
                         _p(out["D"]), _p(out["W"]), _p(out["T"]), _p(out["n"]), _p(out["amb"]),
-                        _p(out["margin"]))
+                        _p(b), _p(allow), _p(g_amb), _p(g_mass))
+    out["allow_C"], out["allow_D"] = allow[0], allow[1]
+    out["g_amb"], out["g_mass"] = g_amb, g_mass
     return out
 
 

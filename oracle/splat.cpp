@@ -268,7 +268,7 @@ int orc_project(int M, const double* means, const double* log_scales, const doub
 void orc_composite(int M, const double* rec, int W, int H, const double* Ct, const double* Dt,
                    double eps, int mode, int f32, int brute, int x0, int x1, int y0, int y1,
                    double* out_C, double* out_D, double* out_W, double* out_T, int* out_n,
-                   int* amb, double* margin) {
+                   int* amb, const double* band, double* allow, double* g_amb, double* g_mass) {
   Lists L = build_lists(M, rec, W, H, brute, x0, x1, y0, y1);
   const long npx = (long)W * H;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -279,22 +279,7 @@ void orc_composite(int M, const double* rec, int W, int H, const double* Ct, con
     double C[3] = {0, 0, 0}, Z = 0, Wg = 0, T = 1.0;
     int n = 0;
     bool a = false;
-    if (margin) {
-      // smallest relative distance of a counting decision to its threshold
-      // (alpha vs 1/255, d vs D_t + eps) over this pixel's candidates
-      double mg = INFINITY;
-      const double thr = Dt[pix] > 0.0 ? Dt[pix] + eps : INFINITY;
-      for (int i : L.cand[pix]) {
-        const double* r = rec + (size_t)i * R_N;
-        double dx = x - r[R_MX], dy = y - r[R_MY];
-        double q = r[R_CA] * dx * dx + 2.0 * r[R_CB] * dx * dy + r[R_CC] * dy * dy;
-        double al = r[R_SIG] * std::exp(-0.5 * q);
-        mg = std::min(mg, std::fabs(al * 255.0 - 1.0));
-        if (std::isfinite(thr) && al * 255.0 >= 1.0 - 1e-3)
-          mg = std::min(mg, std::fabs(r[R_D] - thr) / thr);
-      }
-      margin[pix] = mg;
-    }
+
     for (const Item& it : its) {
       const double* r = rec + (size_t)it.id * R_N;
       double al = it.alpha;
@@ -329,6 +314,49 @@ void orc_composite(int M, const double* rec, int W, int H, const double* Ct, con
     }
     out_n[pix] = n;
     if (amb) amb[pix] = a ? 1 : 0;
+    if (allow) {
+      // First-order bound on how much C* (allow[0]) and D* (allow[1]) can move
+      // if every counting decision lying within the error band of its
+      // threshold were taken the other way, as a single-precision evaluation
+      // may.  Support: |qmax - q| < band[0] (|q| + (|a| + 2|b| + |c|)(dx^2 + dy^2)),
+      // the rounding error of q from a conic known to a relative band[0];
+      // depth: |d - (D_t + eps)| < band[1] (D_t + eps).  g_amb / g_mass collect,
+      // per Gaussian, the alpha of such decisions and its total counted alpha.
+      const double thr = Dt[pix] > 0.0 ? Dt[pix] + eps : INFINITY;
+      const double N = 1.0 + Wg;
+      const double Cs[3] = {out_C[pix], out_C[npx + pix], out_C[2 * npx + pix]};
+      double aC = 0.0, aD = 0.0;
+      for (int i : L.cand[pix]) {
+        const double* r = rec + (size_t)i * R_N;
+        double dx = x - r[R_MX], dy = y - r[R_MY];
+        double q = r[R_CA] * dx * dx + 2.0 * r[R_CB] * dx * dy + r[R_CC] * dy * dy;
+        double al = r[R_SIG] * std::exp(-0.5 * q);
+        const double cn = std::fabs(r[R_CA]) + 2.0 * std::fabs(r[R_CB]) + std::fabs(r[R_CC]);
+        const double qband = band[0] * (std::fabs(q) + cn * (dx * dx + dy * dy));
+        bool near_s = std::fabs(r[R_QMAX] - q) < qband;
+        bool near_d = std::isfinite(thr) && std::fabs(r[R_D] - thr) < band[1] * thr;
+        bool in_s = q <= r[R_QMAX] + qband;
+        bool cnt = al >= 1.0 / 255.0 && r[R_D] < thr;
+        if (cnt) {
+#pragma omp atomic
+          g_mass[i] += al;
+        }
+        if (!(near_s || (near_d && in_s))) continue;
+        double dc = 0.0;
+        for (int ch = 0; ch < 3; ++ch) dc = std::max(dc, std::fabs(r[R_R + ch] - Cs[ch]));
+        if (mode == 0) {
+          aC += al * dc / N;
+          aD += al * std::fabs(r[R_D] - out_D[pix]) / N;
+        } else {
+          aC += al * (1.0 + 1.0 / (1.0 - std::min(al, 0.99)));
+          aD += al * (r[R_D] + out_D[pix] / (1.0 - std::min(al, 0.99)));
+        }
+#pragma omp atomic
+        g_amb[i] += al;
+      }
+      allow[pix] = a ? INFINITY : aC;
+      allow[npx + pix] = a ? INFINITY : aD;
+    }
   }
 }
 

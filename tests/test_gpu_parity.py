@@ -68,7 +68,15 @@ def test_raycast_matches_oracle(name):
     hit = ok & (Dt > 0)
     assert hit.sum() > 100
     np.testing.assert_allclose(d[hit], Dt[hit], rtol=1e-4)
-    np.testing.assert_allclose(c[:, hit], Ct[:, hit], atol=1e-4)
+    # colour at the hit: 1e-4 plus the hit-position difference times the
+    # steepest colour change of the volume (at most 1 per voxel)
+    dpos = np.abs(d[hit] - Dt[hit]) * np.linalg.norm(
+        [(np.nonzero(hit)[1] - f.cam.cx) / f.cam.fx, (np.nonzero(hit)[0] - f.cam.cy) / f.cam.fy,
+         np.ones(hit.sum())], axis=0)
+    tol = 1e-4 + 2.0 * dpos / w.tsdf.voxel
+    assert np.all(np.abs(c[:, hit] - Ct[:, hit]) <= tol), np.abs(c[:, hit] - Ct[:, hit]).max()
+    print("raycast: max depth rel", np.max(np.abs(d[hit] - Dt[hit]) / Dt[hit]),
+          "max colour", np.abs(c[:, hit] - Ct[:, hit]).max())
 
 
 # ------------------------------------------------------------ projection
@@ -102,13 +110,18 @@ def test_projection_matches_oracle():
     pairs = [(0, oracle.R_MX), (1, oracle.R_MY), (2, oracle.R_D), (3, oracle.R_SIG),
              (4, oracle.R_CA), (5, oracle.R_CB), (6, oracle.R_CC), (7, oracle.R_QMAX),
              (8, oracle.R_R), (9, oracle.R_G), (10, oracle.R_B)]
+    cnorm = np.maximum(np.abs(rec_o[both, oracle.R_CA]), np.abs(rec_o[both, oracle.R_CC]))
     for kg, ko in pairs:
         a, b = rec_g[both, kg].astype(np.float64), rec_o[both, ko]
-        scale = np.maximum(np.abs(b), 1e-3 * np.abs(b).max())
-        if kg == 5:  # off-diagonal conic: relative to the diagonal
-            scale = np.maximum(scale, 1e-3 * np.sqrt(rec_o[both, oracle.R_CA] * rec_o[both, oracle.R_CC]))
+        if kg in (4, 5, 6):
+            # conic entries: relative to the conic's norm (inverse of Sigma_2D,
+            # which FP32 computes with relative error ~ eps * cond)
+            scale = cnorm
+        else:
+            scale = np.maximum(np.abs(b), 1e-3 * np.abs(b).max())
         err = np.abs(a - b) / scale
-        assert err.max() < 2e-4, (kg, err.max())
+        print("projection field", kg, "max rel err", err.max())
+        assert err.max() < 1e-4, (kg, err.max())
 
 
 # --------------------------------------------------------------- binning
@@ -267,26 +280,31 @@ def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False):
     grads = g.zeros_like()
     r.backward(g, [v], grads)
     assert r.status() == gps.GPS_OK
-    margin = ref["out"]["margin"]
-    ok = (margin > 1e-4) & (ref["out"]["amb"] == 0)
-    frac = 1.0 - ok.mean()
-    assert frac < 0.02, frac
-    np.testing.assert_allclose(v.out_rgb.cpu().numpy()[:, ok], ref["out"]["C"][:, ok], atol=1e-4)
-    np.testing.assert_allclose(v.out_depth.cpu().numpy()[ok], ref["out"]["D"][ok], rtol=1e-4)
+    out = ref["out"]
+    # pixels under a Gaussian whose visibility / clamp decision is itself
+    # ambiguous are left out; everywhere else every pixel must be within
+    # 1e-4 plus the flip allowance of its near-threshold decisions
+    rec = ref["rec"]
+    skip = np.zeros((H, W), bool)
+    for i in np.nonzero(ref["proj_amb"])[0]:
+        x0, x1 = int(max(0, rec[i, oracle.R_MX] - rec[i, oracle.R_EX] - 2)), int(min(W - 1, rec[i, oracle.R_MX] + rec[i, oracle.R_EX] + 2))
+        y0, y1 = int(max(0, rec[i, oracle.R_MY] - rec[i, oracle.R_EY] - 2)), int(min(H - 1, rec[i, oracle.R_MY] + rec[i, oracle.R_EY] + 2))
+        skip[y0:y1 + 1, x0:x1 + 1] = True
+    assert skip.mean() < 0.01
+    ok = ~skip & np.isfinite(out["allow_C"])
+    assert ok.mean() > 0.99, ok.mean()
+    dC = np.abs(v.out_rgb.cpu().numpy() - out["C"]).max(0)
+    dD = np.abs(v.out_depth.cpu().numpy() - out["D"])
+    assert np.all(dC[ok] <= 1e-4 + out["allow_C"][ok]), (dC[ok] - out["allow_C"][ok]).max()
+    assert np.all(dD[ok] <= 1e-4 * np.abs(out["D"][ok]) + out["allow_D"][ok])
     np.testing.assert_allclose(loss.item(), ref["L"], rtol=1e-4)
     got = {k: t.cpu().numpy() for k, t in zip(ref["grads"].keys(), grads.tensors())}
-    # elementwise test skips Gaussians touching a pixel where some counting
-    # decision sits within 1e-4 of its threshold (FP32 and FP64 may differ)
-    rec = ref["rec"]
-    bad_px = ~ok
-    ys, xs = np.nonzero(bad_px)
-    excl = np.zeros(w.gaussians.M, bool)
-    for i in np.nonzero(rec[:, oracle.R_VIS] > 0)[0]:
-        ex, ey = rec[i, oracle.R_EX] + 1, rec[i, oracle.R_EY] + 1
-        excl[i] = np.any((np.abs(xs - rec[i, oracle.R_MX]) <= ex) & (np.abs(ys - rec[i, oracle.R_MY]) <= ey))
-    excl |= ref["proj_amb"] != 0
+    # elementwise: Gaussians whose own counted alpha near a threshold is more
+    # than 1e-4 of their total counted alpha are left out
+    excl = (out["g_amb"] > 1e-4 * out["g_mass"]) | (ref["proj_amb"] != 0)
     worst = assert_grads_close(got, ref["grads"], exclude=excl, elem_tol=1e-3, label="e2e")
-    print("excluded pixels", frac, "excluded Gaussians", excl.mean(), worst)
+    print("e2e: allowance>0 px", (out["allow_C"] > 0).mean(), "excluded Gaussians", excl.mean(),
+          "worst (norm, elem)", worst)
 
 
 def test_deterministic_mode_is_bitwise_reproducible_and_matches():
