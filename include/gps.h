@@ -49,8 +49,9 @@ extern "C" {
 #define GPS_OK 0
 #define GPS_ERR_INVALID_ARG (-1)         /* bad pointer, size or setting       */
 #define GPS_ERR_WORKSPACE_TOO_SMALL (-2) /* ws_bytes < gps_workspace_size()     */
-#define GPS_ERR_CAPACITY (-3)            /* more (tile, Gaussian) pairs than
-                                            pair_capacity; found on the device */
+#define GPS_ERR_CAPACITY (-3)            /* more (super-tile, Gaussian) entries
+                                            than pair_capacity; found on the
+                                            device */
 #define GPS_ERR_CUDA (-4)                /* a CUDA launch / copy failed         */
 #define GPS_ERR_TIMEOUT (-5)             /* a bounded device wait gave up       */
 
@@ -141,7 +142,7 @@ typedef struct GpsRenderSettings {
   int32_t stages;        /* GPS_STAGE_* mask, 0 = all                          */
   int32_t instrument;    /* 1: count Gaussian-pixel evaluations (slower; for
                             measurement runs) into the view scalars           */
-  int64_t pair_capacity; /* (tile, Gaussian) pairs per view; 0 = 64 * M        */
+  int64_t pair_capacity; /* (super-tile, Gaussian) entries per view; 0 = 16 * M */
 } GpsRenderSettings;
 
 /* Adam hyper-parameters; lr per group in the order means, log_scales, quats,
@@ -156,26 +157,33 @@ typedef struct GpsAdamHyper {
  *   mx, my, d, sigma, conic_a, conic_b, conic_c, qmax, r, g, b, ext_x, ext_y, 0, 0, 0
  * with q = a dx^2 + 2 b dx dy + c dy^2, support {q <= qmax}, qmax =
  * 2 ln(255 sigma), and a conservative half-extent ext (ext_x < 0: culled).
- * Tile lists: keys u64 = bits(d) << 32 | index, sorted ascending inside each
- * tile; ranges uint32 [tiles][2] = [start, end).  grad2d holds 12 floats per
- * Gaussian: d/d(mx, my, conic_a, conic_b, conic_c, sigma, r, g, b, d), 0, 0. */
+ * Binning first buckets Gaussians into 32 x 32-pixel super-tiles, then splits
+ * each super-tile's sorted segment into its tiles.  Tile lists: keys u64 =
+ * bits(d) << 32 | index, sorted ascending; tile t's list is pair_keys[
+ * tile_ranges[t][0] .. tile_ranges[t][1]) (lists are not contiguous).
+ * grad2d holds 12 floats per Gaussian: d/d(mx, my, conic_a, conic_b, conic_c,
+ * sigma, r, g, b, d), 0, 0. */
 typedef struct GpsWorkspaceLayout {
   size_t total_bytes;
-  size_t status;        /* int32 status word (shared by all views)          */
-  size_t records;       /* float [M][16]                                    */
-  size_t tile_counts;   /* uint32 [tiles]                                   */
-  size_t tile_ranges;   /* uint32 [tiles][2]                                */
-  size_t pair_keys;     /* uint64 [pair_capacity]                           */
-  size_t pair_scratch;  /* uint64 [pair_capacity] (sort scratch)            */
-  size_t pix_state;     /* float [H*W][8] saved per-pixel forward state     */
-  size_t tile_partials; /* float [tiles][4] loss partial sums               */
+  size_t status;        /* int32 status word (shared by all views)            */
+  size_t records;       /* float [M][16]                                      */
+  size_t super_counts;  /* uint32 [super_tiles]                               */
+  size_t block_base;    /* uint32 [ceil(M/256)][super_tiles]                  */
+  size_t super_ranges;  /* uint32 [super_tiles][2]                            */
+  size_t super_keys;    /* uint64 [pair_capacity] super-tile segments         */
+  size_t super_scratch; /* uint64 [pair_capacity] (sort scratch)              */
+  size_t tile_ranges;   /* uint32 [tiles][2]                                  */
+  size_t pair_keys;     /* uint64 [tiles per super-tile * pair_capacity]      */
+  size_t pix_state;     /* float [H*W][8] saved per-pixel forward state       */
+  size_t tile_partials; /* float [tiles][4] loss partial sums                 */
   size_t view_scalars;  /* float [8]: loss, colour sum, depth sum, N_valid,
-                           pairs; then uint64 [4] evaluation counters: forward
-                           tested, forward counted, backward tested, backward
-                           counted (instrument = 1)                           */
-  size_t grad2d;        /* float [M][12]                                    */
-  size_t pair_grads;    /* float [pair_capacity][12] (deterministic mode)   */
-  int32_t tiles_x, tiles_y, tile_w, tile_h;
+                           super-tile entries; then uint64 [4] evaluation
+                           counters: forward tested, forward counted, backward
+                           tested, backward counted (instrument = 1)          */
+  size_t grad2d;        /* float [M][12]                                      */
+  size_t pair_grads;    /* float [tiles per super-tile * pair_capacity][12]
+                           (deterministic mode)                               */
+  int32_t tiles_x, tiles_y, tile_w, tile_h, super_x, super_y;
   int64_t pair_capacity;
 } GpsWorkspaceLayout;
 

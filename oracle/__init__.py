@@ -148,7 +148,7 @@ def project(g, cam, near=0.2):
 
 
 def composite(rec, Ct, Dt, eps, mode=OIT, f32=False, brute=False, window=None,
-              band=(4e-6, 2e-6)):
+              band=(4e-6, 2e-6), flip=None):
     """Eq. 1-4 (mode OIT) or the Table 7 variant (mode ALPHA) for one view.
     Returns dict C [3][H][W], D, W (= W_G), T (T_end), n (counted), amb, and the
     flip allowance: allow_C, allow_D [H][W] bound how far C*, D* can move if
@@ -156,7 +156,8 @@ def composite(rec, Ct, Dt, eps, mode=OIT, f32=False, brute=False, window=None,
     way (band[0]: relative error of the conic, scaled by the magnitude of the
     quadratic form's terms; band[1]: relative error of d vs D_t + eps);
     g_amb [M] sums the alpha
-    of a Gaussian's such decisions, g_mass [M] its total counted alpha."""
+    of a Gaussian's such decisions, g_mass [M] its total counted alpha.
+    flip (diagnostic): take every decision within that band the other way."""
     Ct = _f64(Ct)
     Dt = _f64(Dt)
     H, W = Dt.shape
@@ -173,7 +174,8 @@ def composite(rec, Ct, Dt, eps, mode=OIT, f32=False, brute=False, window=None,
                         ctypes.c_int(int(f32)), ctypes.c_int(int(brute)), ctypes.c_int(x0),
                         ctypes.c_int(x1), ctypes.c_int(y0), ctypes.c_int(y1), _p(out["C"]),
                         _p(out["D"]), _p(out["W"]), _p(out["T"]), _p(out["n"]), _p(out["amb"]),
-                        _p(b), _p(allow), _p(g_amb), _p(g_mass))
+                        _p(b), _p(allow), _p(g_amb), _p(g_mass),
+                        _p(_f64(flip)) if flip is not None else None)
     out["allow_C"], out["allow_D"] = allow[0], allow[1]
     out["g_amb"], out["g_mass"] = g_amb, g_mass
     return out
@@ -193,7 +195,7 @@ def loss(C, D, Ctgt, Dtgt, Dt, lambda_depth=0.0):
     return float(L), dC, dD, int(nv.value), amb
 
 
-def composite_backward(rec, Ct, Dt, eps, dC, dD, mode=OIT, f32=False):
+def composite_backward(rec, Ct, Dt, eps, dC, dD, mode=OIT, f32=False, flip=None):
     """Adjoint of `composite` -> per-Gaussian 2D gradients [M][10]."""
     rec = _f64(rec)
     Ct, Dt, dC, dD = (_f64(a) for a in (Ct, Dt, dC, dD))
@@ -202,7 +204,7 @@ def composite_backward(rec, Ct, Dt, eps, dC, dD, mode=OIT, f32=False):
     lib().orc_composite_backward(ctypes.c_int(rec.shape[0]), _p(rec), ctypes.c_int(W),
                                  ctypes.c_int(H), _p(Ct), _p(Dt), ctypes.c_double(eps),
                                  ctypes.c_int(mode), ctypes.c_int(int(f32)), _p(dC), _p(dD),
-                                 _p(g2))
+                                 _p(g2), _p(_f64(flip)) if flip is not None else None)
     return g2
 
 
@@ -296,14 +298,15 @@ def rounded(rec: np.ndarray) -> np.ndarray:
 
 
 def render_loss_grads(g, cam, Ct, Dt, Ctgt, Dtgt, eps=0.01, lambda_depth=0.0, mode=OIT,
-                      f32=False, near=0.2):
+                      f32=False, near=0.2, flip=None):
     """One view end to end: project -> composite -> loss -> adjoints.
-    f32=True takes the counting decisions in FP32 on FP32-rounded records."""
+    f32=True takes the counting decisions in FP32 on FP32-rounded records;
+    flip (diagnostic) inverts the decisions inside that error band."""
     rec, pamb = project(g, cam, near)
     rr = rounded(rec) if f32 else rec
-    out = composite(rr, Ct, Dt, eps, mode, f32)
+    out = composite(rr, Ct, Dt, eps, mode, f32, flip=flip)
     L, dC, dD, nv, lamb = loss(out["C"], out["D"], Ctgt, Dtgt, Dt, lambda_depth)
-    g2 = composite_backward(rr, Ct, Dt, eps, dC, dD, mode, f32)
+    g2 = composite_backward(rr, Ct, Dt, eps, dC, dD, mode, f32, flip=flip)
     grads = project_backward(g, cam, g2, near)
     return dict(L=L, rec=rec, proj_amb=pamb, out=out, dC=dC, dD=dD, n_valid=nv, loss_amb=lamb,
                 g2=g2, grads=grads)

@@ -179,8 +179,12 @@ Lists build_lists(int M, const double* rec, int W, int H, int brute, int x0, int
 // The Gaussians counted at pixel (x, y), sorted front to back by (d, index).
 // f32 != 0: decisions in FP32 from the record's float values (see support_f32);
 // otherwise alpha >= 1/255 and d < D_t + eps in FP64.
+// flip (diagnostic only, nullable): decisions lying within the error band of
+// their threshold (flip[0]: conic, flip[1]: depth; see the allowance in
+// orc_composite) are taken the other way, giving the result a single-precision
+// evaluation reaches when it decides each of them differently.
 std::vector<Item> counted(const std::vector<int>& cand, const double* rec, int x, int y,
-                          double Dt, double eps, int f32) {
+                          double Dt, double eps, int f32, const double* flip = nullptr) {
   std::vector<Item> out;
   for (int i : cand) {
     const double* r = rec + (size_t)i * R_N;
@@ -189,6 +193,16 @@ std::vector<Item> counted(const std::vector<int>& cand, const double* rec, int x
     double G = std::exp(-0.5 * q);
     double alpha = r[R_SIG] * G;
     bool keep;
+    if (flip) {
+      const double thr = Dt > 0.0 ? Dt + eps : INFINITY;
+      const double cn = std::fabs(r[R_CA]) + 2.0 * std::fabs(r[R_CB]) + std::fabs(r[R_CC]);
+      const double qband = flip[0] * (std::fabs(q) + cn * (dx * dx + dy * dy));
+      const bool in_s = q <= r[R_QMAX], near_s = std::fabs(r[R_QMAX] - q) < qband;
+      const bool in_d = r[R_D] < thr, near_d = std::isfinite(thr) && std::fabs(r[R_D] - thr) < flip[1] * thr;
+      keep = (in_s != near_s) && (in_d != near_d);
+      if (keep) out.push_back({i, alpha, G, dx, dy});
+      continue;
+    }
     if (f32) {
       float thr = Dt > 0.0 ? (float)Dt + (float)eps : INFINITY;
       keep = support_f32((float)r[R_MX], (float)r[R_MY], (float)r[R_CA], (float)r[R_CB],
@@ -268,14 +282,15 @@ int orc_project(int M, const double* means, const double* log_scales, const doub
 void orc_composite(int M, const double* rec, int W, int H, const double* Ct, const double* Dt,
                    double eps, int mode, int f32, int brute, int x0, int x1, int y0, int y1,
                    double* out_C, double* out_D, double* out_W, double* out_T, int* out_n,
-                   int* amb, const double* band, double* allow, double* g_amb, double* g_mass) {
+                   int* amb, const double* band, double* allow, double* g_amb, double* g_mass,
+                   const double* flip) {
   Lists L = build_lists(M, rec, W, H, brute, x0, x1, y0, y1);
   const long npx = (long)W * H;
 #pragma omp parallel for schedule(dynamic, 16)
   for (long pix = 0; pix < npx; ++pix) {
     int x = (int)(pix % W), y = (int)(pix / W);
     if (x < x0 || x > x1 || y < y0 || y > y1) continue;
-    std::vector<Item> its = counted(L.cand[pix], rec, x, y, Dt[pix], eps, f32);
+    std::vector<Item> its = counted(L.cand[pix], rec, x, y, Dt[pix], eps, f32, flip);
     double C[3] = {0, 0, 0}, Z = 0, Wg = 0, T = 1.0;
     int n = 0;
     bool a = false;
@@ -315,7 +330,7 @@ void orc_composite(int M, const double* rec, int W, int H, const double* Ct, con
     out_n[pix] = n;
     if (amb) amb[pix] = a ? 1 : 0;
     if (allow) {
-      // First-order bound on how much C* (allow[0]) and D* (allow[1]) can move
+      // Bound on how much C* (allow[0]) and D* (allow[1]) can move
       // if every counting decision lying within the error band of its
       // threshold were taken the other way, as a single-precision evaluation
       // may.  Support: |qmax - q| < band[0] (|q| + (|a| + 2|b| + |c|)(dx^2 + dy^2)),
@@ -345,8 +360,10 @@ void orc_composite(int M, const double* rec, int W, int H, const double* Ct, con
         double dc = 0.0;
         for (int ch = 0; ch < 3; ++ch) dc = std::max(dc, std::fabs(r[R_R + ch] - Cs[ch]));
         if (mode == 0) {
-          aC += al * dc / N;
-          aD += al * std::fabs(r[R_D] - out_D[pix]) / N;
+          // exact change of (C_t + C_G) / N when alpha leaves (N - alpha) or joins (N + alpha)
+          const double Nm = std::max(N - al, 1.0);
+          aC += al * dc / Nm;
+          aD += al * std::fabs(r[R_D] - out_D[pix]) / Nm;
         } else {
           aC += al * (1.0 + 1.0 / (1.0 - std::min(al, 0.99)));
           aD += al * (r[R_D] + out_D[pix] / (1.0 - std::min(al, 0.99)));
@@ -409,7 +426,7 @@ double orc_loss(int W, int H, const double* C, const double* D, const double* Ct
 // Mode 1: dC*/dc_i = a_i T_i,  dC*/da_i = c_i T_i - (sum_{j>i} c_j a_j T_j + T_end C_t) / (1 - a_i).
 void orc_composite_backward(int M, const double* rec, int W, int H, const double* Ct,
                             const double* Dt, double eps, int mode, int f32, const double* dC,
-                            const double* dD, double* g2) {
+                            const double* dD, double* g2, const double* flip) {
   Lists L = build_lists(M, rec, W, H, 0, 0, W - 1, 0, H - 1);
   std::memset(g2, 0, sizeof(double) * (size_t)M * G_N);
   const long npx = (long)W * H;
@@ -418,7 +435,7 @@ void orc_composite_backward(int M, const double* rec, int W, int H, const double
     const double g[3] = {dC[pix], dC[npx + pix], dC[2 * npx + pix]};
     const double gD = dD[pix];
     if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0 && gD == 0.0) continue;  // contributes nothing
-    std::vector<Item> its = counted(L.cand[pix], rec, x, y, Dt[pix], eps, f32);
+    std::vector<Item> its = counted(L.cand[pix], rec, x, y, Dt[pix], eps, f32, flip);
     if (its.empty()) continue;
     const double Ctp[3] = {Ct[pix], Ct[npx + pix], Ct[2 * npx + pix]};
     const size_t n = its.size();

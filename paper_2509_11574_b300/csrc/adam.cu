@@ -6,6 +6,8 @@
 //   p <- p - (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps)
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "gps_common.cuh"
 
 namespace gps {
@@ -24,19 +26,18 @@ struct AdamArgs {
   AdamGroup grp[5];
   long long first_block[6];  // block offsets per group
   float b1, b2, eps;
-  int step;
-  int* device_step;
+  float bc1, sbc2;  // 1 - b1^t and sqrt(1 - b2^t) when the step is known on the host
+  int* device_step; // else: step t = *device_step + 1
 };
 
 __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
-  __shared__ float s_bc[2];
-  if (threadIdx.x == 0) {
-    int t = a.step;
-    if (t <= 0) t = *a.device_step + 1;  // the counter is advanced by adam_step_advance
-    s_bc[0] = (float)(1.0 - pow((double)a.b1, (double)t));
-    s_bc[1] = (float)sqrt(1.0 - pow((double)a.b2, (double)t));
+  float bc1 = a.bc1, sbc2 = a.sbc2;
+  if (a.device_step) {
+    // 1 - b^t = -expm1(t ln b), with ln b = log1p(b - 1): accurate for b near 1
+    const float t = (float)(*a.device_step + 1);
+    bc1 = -expm1f(t * log1pf(a.b1 - 1.0f));
+    sbc2 = sqrtf(-expm1f(t * log1pf(a.b2 - 1.0f)));
   }
-  __syncthreads();
   const long long blk = blockIdx.x;
   int gidx = 0;
 #pragma unroll
@@ -45,7 +46,6 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   const AdamGroup& G = a.grp[gidx];
   const long long base = ((blk - a.first_block[gidx]) * 256 + threadIdx.x) * 4;
   if (base >= G.n) return;
-  const float bc1 = s_bc[0], sbc2 = s_bc[1];
   const float step_size = G.lr / bc1;
   const float b1 = a.b1, b2 = a.b2, eps = a.eps;
   if (G.vec4 && base + 4 <= G.n) {
@@ -106,8 +106,13 @@ cudaError_t launch_adam(const GpsGaussians& P, const GpsGaussians& Gr, const Gps
   a.b1 = h.beta1;
   a.b2 = h.beta2;
   a.eps = h.eps;
-  a.step = step;
-  a.device_step = device_step;
+  if (step > 0) {
+    a.bc1 = (float)(1.0 - std::pow((double)h.beta1, (double)step));
+    a.sbc2 = (float)std::sqrt(1.0 - std::pow((double)h.beta2, (double)step));
+    a.device_step = nullptr;
+  } else {
+    a.device_step = device_step;
+  }
   if (blocks == 0) return cudaSuccess;
   adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();

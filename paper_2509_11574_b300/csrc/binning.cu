@@ -1,11 +1,19 @@
-// Tile binning with a sort on (tile, depth) keys.
+// Tile binning: per-tile Gaussian lists sorted by (depth, index).
 //
-// The sort is split the way its key is: the tile id is the most significant
-// digit and is placed by a counting sort (per-tile counts from the projection,
-// an exclusive scan, then one atomic cursor per tile), and each tile's segment
-// is then sorted by the 64-bit key bits(depth) << 32 | index in shared memory.
-// The result equals a stable sort of (tile << 32 | bits(depth)) keys with ties
-// broken by Gaussian index, whatever order the emission atomics ran in.
+// The sort key is (tile, bits(depth), index).  Its most significant part is
+// placed in two levels:
+//   1. super-tiles of 32 x 32 px: every block of the projection histograms its
+//      Gaussians' super-tile rectangles in shared memory and reserves one range
+//      per (block, super-tile) with a single global atomic; after a scan over
+//      super-tiles, the emission writes bits(d) << 32 | index into those ranges
+//      (the rank inside a block comes from a shared-memory atomic).  No
+//      per-(Gaussian, tile) global atomic and no contended counter chain.
+//   2. one CTA per super-tile sorts its segment by the 64-bit key (8 keys per
+//      thread in registers with a sorting network, then merge-path rounds in
+//      shared memory) and splits it, in order, into the lists of its tiles
+//      (rectangle overlap, the same test as the oracle's binning).
+// The result equals a stable sort of (tile << 32 | bits(d)) keys with ties in
+// index order, independent of the order the atomics ran in.
 #include <cuda_runtime.h>
 
 #include "gps_common.cuh"
@@ -14,48 +22,77 @@ namespace gps {
 
 constexpr int kScanThreads = 1024;
 
-// Exclusive scan of the per-tile counts -> [start, end) ranges, clipped to the
-// pair capacity (overflow raises GPS_ERR_CAPACITY and truncates the lists).
-// Resets the counts to zero so that the emission can reuse them as cursors.
-// Writes the total pair count to scalars[4].
-__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(uint32_t* __restrict__ counts,
+// -------------------------------------------------- super-tile histograms
+__device__ __forceinline__ bool super_rect(float mx, float my, float ex, float ey, int W, int H,
+                                           int& sx0, int& sx1, int& sy0, int& sy1) {
+  int x0, x1, y0, y1;
+  if (!record_rect(mx, my, ex, ey, W, H, x0, x1, y0, y1)) return false;
+  sx0 = x0 >> kSuperShift;
+  sx1 = x1 >> kSuperShift;
+  sy0 = y0 >> kSuperShift;
+  sy1 = y1 >> kSuperShift;
+  return true;
+}
+
+// Histogram of caller-provided records (binning stage run on its own; the
+// projection kernel fuses the same histogram).
+__global__ void __launch_bounds__(256) bin_histogram_kernel(const float4* __restrict__ rec, int M,
+                                                            int W, int H, int sup_x, int nsup,
+                                                            uint32_t* __restrict__ sup_count,
+                                                            uint32_t* __restrict__ block_base) {
+  extern __shared__ uint32_t s_hist[];
+  for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_hist[s] = 0;
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) {
+    const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
+    int sx0, sx1, sy0, sy1;
+    if (super_rect(a.x, a.y, c.w, e.x, W, H, sx0, sx1, sy0, sy1))
+      for (int sy = sy0; sy <= sy1; ++sy)
+        for (int sx = sx0; sx <= sx1; ++sx) atomicAdd(s_hist + sy * sup_x + sx, 1u);
+  }
+  reserve_block_ranges(s_hist, nsup, sup_count, block_base);
+}
+
+// Exclusive scan of the super-tile counts -> [start, end) (clipped to the
+// capacity; overflow raises GPS_ERR_CAPACITY).  Resets the counts for the next
+// call.  scalars[4] = number of (super-tile, Gaussian) entries.
+__global__ void __launch_bounds__(kScanThreads) scan_super_kernel(uint32_t* __restrict__ counts,
                                                                   uint2* __restrict__ ranges,
-                                                                  int ntiles, long long cap,
+                                                                  int n, long long cap,
                                                                   float* scalars, int* status) {
   __shared__ unsigned long long warp_sums[kScanThreads / 32];
   const int tid = threadIdx.x;
-  const int per = (ntiles + kScanThreads - 1) / kScanThreads;
-  const int b = tid * per, e = min(ntiles, b + per);
+  const int per = (n + kScanThreads - 1) / kScanThreads;
+  const int b = tid * per, e = min(n, b + per);
   unsigned long long local = 0;
   for (int k = b; k < e; ++k) local += counts[k];
-  // block exclusive scan of `local`
   unsigned long long incl = local;
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long n = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += n;
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
   }
   if (lane == 31) warp_sums[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    unsigned long long v = lane < kScanThreads / 32 ? warp_sums[lane] : 0ull;
+    unsigned long long v = warp_sums[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long n = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += n;
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
     }
-    warp_sums[lane] = v;  // inclusive over warps
+    warp_sums[lane] = v;
   }
   __syncthreads();
   unsigned long long run = incl - local + (warp > 0 ? warp_sums[warp - 1] : 0ull);
   for (int k = b; k < e; ++k) {
     const unsigned long long c = counts[k];
-    const unsigned long long s = run, t = run + c;
-    ranges[k] = make_uint2((uint32_t)min(s, (unsigned long long)cap),
-                           (uint32_t)min(t, (unsigned long long)cap));
+    ranges[k] = make_uint2((uint32_t)min(run, (unsigned long long)cap),
+                           (uint32_t)min(run + c, (unsigned long long)cap));
     counts[k] = 0u;
-    run = t;
+    run += c;
   }
   if (tid == kScanThreads - 1) {
     scalars[4] = (float)run;
@@ -63,132 +100,263 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(uint32_t* __re
   }
 }
 
-// One thread per Gaussian: append bits(d) << 32 | i to every tile its rectangle touches.
-__global__ void __launch_bounds__(256) emit_pairs_kernel(const float4* __restrict__ rec, int M,
-                                                         int W, int H,
-                                                         const uint2* __restrict__ ranges,
-                                                         uint32_t* __restrict__ cursor,
-                                                         unsigned long long* __restrict__ keys,
-                                                         int tiles_x, int tw, int th) {
+// Emission into the reserved ranges; same block partition as the histogram.
+__global__ void __launch_bounds__(256) emit_super_kernel(const float4* __restrict__ rec, int M,
+                                                         int W, int H, int sup_x, int nsup,
+                                                         const uint2* __restrict__ sup_ranges,
+                                                         const uint32_t* __restrict__ block_base,
+                                                         unsigned long long* __restrict__ keys) {
+  extern __shared__ uint32_t s_rank[];
+  for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_rank[s] = 0;
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
-  int x0, x1, y0, y1;
-  if (!record_rect(a.x, a.y, c.w, e.x, W, H, x0, x1, y0, y1)) return;
+  int sx0, sx1, sy0, sy1;
+  if (!super_rect(a.x, a.y, c.w, e.x, W, H, sx0, sx1, sy0, sy1)) return;
   const unsigned long long key = key_of(a.z, (uint32_t)i);
-  for (int ty = y0 / th; ty <= y1 / th; ++ty)
-    for (int tx = x0 / tw; tx <= x1 / tw; ++tx) {
-      const int t = ty * tiles_x + tx;
-      const uint2 r = ranges[t];
-      const uint32_t pos = r.x + atomicAdd(cursor + t, 1u);
+  const uint32_t* bb = block_base + (size_t)blockIdx.x * nsup;
+  for (int sy = sy0; sy <= sy1; ++sy)
+    for (int sx = sx0; sx <= sx1; ++sx) {
+      const int s = sy * sup_x + sx;
+      const uint2 r = sup_ranges[s];
+      const uint32_t pos = r.x + bb[s] + atomicAdd(s_rank + s, 1u);
       if (pos < r.y) keys[pos] = key;
     }
 }
 
-// ---------------------------------------------------------------- per-tile sort
-constexpr int kSortThreads = 512;
-constexpr int kSortCap = 4096;  // keys sorted in shared memory in one piece
+// ------------------------------------------------------ per-super-tile sort
+constexpr int kSortThreads = 256;
+constexpr int kPerThread = 8;
+constexpr int kSortCap = kSortThreads * kPerThread * 2;  // keys sorted in shared memory
 
-__device__ __forceinline__ void bitonic_smem(unsigned long long* s, int n2, int tid, int nt) {
-  for (int k = 2; k <= n2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < n2; i += nt) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const unsigned long long a = s[i], b = s[ixj];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            s[i] = b;
-            s[ixj] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
+__device__ __forceinline__ void cswap(unsigned long long& a, unsigned long long& b) {
+  const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
+  a = lo;
+  b = hi;
 }
 
-// Merge sorted runs A[0, na) and B[0, nb) into out[0, na + nb); each thread
-// produces a contiguous slice found by a merge-path search.
-__device__ void merge_runs(const unsigned long long* A, int na, const unsigned long long* B, int nb,
-                           unsigned long long* out, int tid, int nt) {
-  const int total = na + nb;
-  const int per = (total + nt - 1) / nt;
-  const int d0 = min(total, tid * per), d1 = min(total, d0 + per);
-  if (d0 >= d1) return;
-  // find i (from A) with i + j = d0 and A[i-1] <= B[j], B[j-1] < A[i]
+// Batcher odd-even merge sort network for 8 keys in registers.
+__device__ __forceinline__ void sort8(unsigned long long (&k)[8]) {
+  cswap(k[0], k[1]); cswap(k[2], k[3]); cswap(k[4], k[5]); cswap(k[6], k[7]);
+  cswap(k[0], k[2]); cswap(k[1], k[3]); cswap(k[4], k[6]); cswap(k[5], k[7]);
+  cswap(k[1], k[2]); cswap(k[5], k[6]);
+  cswap(k[0], k[4]); cswap(k[1], k[5]); cswap(k[2], k[6]); cswap(k[3], k[7]);
+  cswap(k[2], k[4]); cswap(k[3], k[5]);
+  cswap(k[1], k[2]); cswap(k[3], k[4]); cswap(k[5], k[6]);
+}
+
+// Output slice [d0, d0 + cnt) of the merge of sorted runs A[0, na), B[0, nb)
+// (keys are distinct: the index sits in the low bits).
+__device__ __forceinline__ void merge_slice(const unsigned long long* A, int na,
+                                            const unsigned long long* B, int nb, int d0, int cnt,
+                                            unsigned long long* out) {
   int lo = max(0, d0 - nb), hi = min(d0, na);
   while (lo < hi) {
-    const int i = (lo + hi) >> 1, j = d0 - i;
-    if (A[i] < B[j - 1]) lo = i + 1;  // keys are distinct (index in the low bits)
-    else hi = i;
+    const int mid = (lo + hi) >> 1;
+    if (A[mid] < B[d0 - mid - 1]) lo = mid + 1;
+    else hi = mid;
   }
   int i = lo, j = d0 - lo;
-  for (int d = d0; d < d1; ++d) {
-    if (j >= nb || (i < na && A[i] < B[j])) out[d] = A[i++];
-    else out[d] = B[j++];
+  for (int d = 0; d < cnt; ++d) {
+    const bool takeA = j >= nb || (i < na && A[i] < B[j]);
+    out[d] = takeA ? A[i++] : B[j++];
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) sort_tiles_kernel(const uint2* __restrict__ ranges,
-                                                                 unsigned long long* __restrict__ keys,
-                                                                 unsigned long long* __restrict__ tmp) {
-  __shared__ unsigned long long s[kSortCap];
-  const uint2 r = ranges[blockIdx.x];
-  const int n = (int)(r.y - r.x);
-  if (n <= 1) return;
-  unsigned long long* seg = keys + r.x;
-  unsigned long long* seg_tmp = tmp + r.x;
+// Sorts seg[0, n) (n <= kSortCap/2 for the buffer pair) using buf0/buf1 of
+// kSortCap/2 keys each; returns the buffer that holds the result.
+__device__ unsigned long long* block_merge_sort(const unsigned long long* __restrict__ seg, int n,
+                                                unsigned long long* buf0, unsigned long long* buf1) {
   const int tid = threadIdx.x;
-  // 1) sort chunks of kSortCap in shared memory
-  const int nchunks = (n + kSortCap - 1) / kSortCap;
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const int base = ch * kSortCap, len = min(kSortCap, n - base);
-    int n2 = 1;
-    while (n2 < len) n2 <<= 1;
-    for (int i = tid; i < n2; i += kSortThreads) s[i] = i < len ? seg[base + i] : ~0ull;
-    __syncthreads();
-    bitonic_smem(s, n2, tid, kSortThreads);
-    for (int i = tid; i < len; i += kSortThreads) seg[base + i] = s[i];
-    __syncthreads();
+  const int n8 = (n + 7) & ~7;
+  for (int t = tid; t * kPerThread < n8; t += kSortThreads) {
+    unsigned long long k[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = t * kPerThread + q;
+      k[q] = idx < n ? seg[idx] : ~0ull;
+    }
+    sort8(k);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf0[t * kPerThread + q] = k[q];
   }
-  if (nchunks == 1) return;
-  // 2) pairwise merges of sorted runs, ping-ponging through the scratch buffer
-  unsigned long long* src = seg;
-  unsigned long long* dst = seg_tmp;
-  for (int w = kSortCap; w < n; w <<= 1) {
-    for (int b = 0; b < n; b += 2 * w) {
-      const int na = min(w, n - b), nb = max(0, min(w, n - b - w));
-      merge_runs(src + b, na, src + b + na, nb, dst + b, tid, kSortThreads);
+  __syncthreads();
+  unsigned long long* src = buf0;
+  unsigned long long* dst = buf1;
+  for (int w = 8; w < n8; w <<= 1) {
+    for (int t = tid; t * kPerThread < n8; t += kSortThreads) {
+      const int d = t * kPerThread;
+      const int p = d / (2 * w), base = p * 2 * w;
+      const int na = min(w, n8 - base), nb = max(0, min(w, n8 - base - w));
+      merge_slice(src + base, na, src + base + na, nb, d - base, kPerThread, dst + d);
     }
     __syncthreads();
-    unsigned long long* t = src;
+    unsigned long long* tmp = src;
     src = dst;
-    dst = t;
+    dst = tmp;
   }
-  if (src != seg) {
-    for (int i = tid; i < n; i += kSortThreads) seg[i] = src[i];
+  return src;
+}
+
+// Chunked sort for segments larger than the shared buffers: sort chunks in
+// shared memory, then merge runs pairwise through the global scratch buffer.
+__device__ unsigned long long* large_sort(unsigned long long* seg, unsigned long long* seg_tmp,
+                                          int n, unsigned long long* buf0,
+                                          unsigned long long* buf1) {
+  constexpr int C = kSortCap / 2;
+  const int tid = threadIdx.x;
+  for (int base = 0; base < n; base += C) {
+    const int len = min(C, n - base);
+    unsigned long long* r = block_merge_sort(seg + base, len, buf0, buf1);
+    for (int i = tid; i < len; i += kSortThreads) seg[base + i] = r[i];
+    __syncthreads();
+  }
+  unsigned long long* src = seg;
+  unsigned long long* dst = seg_tmp;
+  for (int w = C; w < n; w <<= 1) {
+    const int per = 8;
+    for (int t = tid; t * per < n; t += kSortThreads) {
+      const int d = t * per;
+      const int p = d / (2 * w), base = p * 2 * w;
+      const int na = min(w, n - base), nb = max(0, min(w, n - base - w));
+      merge_slice(src + base, na, src + base + na, nb, d - base, min(per, n - d), dst + d);
+    }
+    __syncthreads();
+    unsigned long long* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  return src;
+}
+
+// One CTA per super-tile: sort its segment, then split it in order into the
+// lists of its tiles.  Tile l of super-tile s owns tile_keys[L * start_s +
+// l * n_s ...] (a list is never longer than its super-tile's segment).
+template <int TW, int TH>
+__global__ void __launch_bounds__(kSortThreads) sort_split_kernel(
+    const uint2* __restrict__ sup_ranges, unsigned long long* __restrict__ sup_keys,
+    unsigned long long* __restrict__ sup_tmp, const float4* __restrict__ rec, int W, int H,
+    int sup_x, int tiles_x, int tiles_y, unsigned long long* __restrict__ tile_keys,
+    uint2* __restrict__ tile_ranges) {
+  constexpr int LX = kSuperPx / TW, LY = kSuperPx / TH, L = LX * LY;
+  constexpr int NW = kSortThreads / 32;
+  __shared__ unsigned long long buf[kSortCap];
+  __shared__ uint32_t s_cnt[L][NW];
+  __shared__ uint32_t s_run[L];
+  const int s = blockIdx.x;
+  const int sx = s % sup_x, sy = s / sup_x;
+  const uint2 r = sup_ranges[s];
+  const int n = (int)(r.y - r.x);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // tiles of this super-tile that exist in the image
+  const int tx0 = sx * LX, ty0 = sy * LY;
+  if (tid < L) s_run[tid] = 0;
+  const unsigned long long* sorted = nullptr;
+  if (n > 0) {
+    if (n <= kSortCap / 2)
+      sorted = block_merge_sort(sup_keys + r.x, n, buf, buf + kSortCap / 2);
+    else
+      sorted = large_sort(sup_keys + r.x, sup_tmp + r.x, n, buf, buf + kSortCap / 2);
+  }
+  __syncthreads();
+  const size_t region = (size_t)L * r.x;
+  for (int c0 = 0; c0 < n; c0 += kSortThreads) {
+    const int k = c0 + tid;
+    uint32_t bits = 0;
+    unsigned long long key = 0;
+    if (k < n) {
+      key = sorted[k];
+      const uint32_t gi = (uint32_t)key;
+      const float4 a = rec[4 * (size_t)gi], c = rec[4 * (size_t)gi + 2], e = rec[4 * (size_t)gi + 3];
+      int x0, x1, y0, y1;
+      if (record_rect(a.x, a.y, c.w, e.x, W, H, x0, x1, y0, y1)) {
+        const int ax = max(x0 / TW, tx0), bx = min(x1 / TW, tx0 + LX - 1);
+        const int ay = max(y0 / TH, ty0), by = min(y1 / TH, ty0 + LY - 1);
+        for (int ty = ay; ty <= by; ++ty)
+          for (int tx = ax; tx <= bx; ++tx) bits |= 1u << ((ty - ty0) * LX + (tx - tx0));
+      }
+    }
+    uint32_t mine[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      const uint32_t b = __ballot_sync(0xffffffffu, (bits >> l) & 1u);
+      mine[l] = __popc(b & ((1u << lane) - 1u));
+      if (lane == 0) s_cnt[l][warp] = __popc(b);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      if ((bits >> l) & 1u) {
+        uint32_t off = s_run[l];
+        for (int w2 = 0; w2 < warp; ++w2) off += s_cnt[l][w2];
+        tile_keys[region + (size_t)l * n + off + mine[l]] = key;
+      }
+    }
+    __syncthreads();
+    if (tid < L) {
+      uint32_t tot = 0;
+      for (int w2 = 0; w2 < NW; ++w2) tot += s_cnt[tid][w2];
+      s_run[tid] += tot;
+    }
+    __syncthreads();
+  }
+  if (tid < L) {
+    const int tx = tx0 + tid % LX, ty = ty0 + tid / LX;
+    if (tx < tiles_x && ty < tiles_y) {
+      const uint32_t start = (uint32_t)(region + (size_t)tid * n);
+      tile_ranges[ty * tiles_x + tx] = make_uint2(start, start + s_run[tid]);
+    }
   }
 }
 
-cudaError_t launch_scan_tiles(uint32_t* counts, uint2* ranges, int ntiles, long long cap,
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_bin_histogram(const float4* rec, int M, int W, int H, int sup_x, int nsup,
+                                 uint32_t* sup_count, uint32_t* block_base, cudaStream_t st) {
+  bin_histogram_kernel<<<(M + 255) / 256, 256, nsup * sizeof(uint32_t), st>>>(
+      rec, M, W, H, sup_x, nsup, sup_count, block_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_super(uint32_t* counts, uint2* ranges, int n, long long cap,
                               float* scalars, int* status, cudaStream_t st) {
-  scan_tiles_kernel<<<1, kScanThreads, 0, st>>>(counts, ranges, ntiles, cap, scalars, status);
+  scan_super_kernel<<<1, kScanThreads, 0, st>>>(counts, ranges, n, cap, scalars, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit_pairs(const float4* rec, int M, int W, int H, const uint2* ranges,
-                              uint32_t* cursor, unsigned long long* keys, int tiles_x, int tw,
-                              int th, cudaStream_t st) {
-  emit_pairs_kernel<<<(M + 255) / 256, 256, 0, st>>>(rec, M, W, H, ranges, cursor, keys, tiles_x,
-                                                      tw, th);
+cudaError_t launch_emit_super(const float4* rec, int M, int W, int H, int sup_x, int nsup,
+                              const uint2* sup_ranges, const uint32_t* block_base,
+                              unsigned long long* keys, cudaStream_t st) {
+  emit_super_kernel<<<(M + 255) / 256, 256, nsup * sizeof(uint32_t), st>>>(
+      rec, M, W, H, sup_x, nsup, sup_ranges, block_base, keys);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_tiles(const uint2* ranges, int ntiles, unsigned long long* keys,
-                              unsigned long long* tmp, cudaStream_t st) {
-  sort_tiles_kernel<<<ntiles, kSortThreads, 0, st>>>(ranges, keys, tmp);
+template <int TW, int TH>
+static cudaError_t split_tw(const uint2* sup_ranges, int nsup, unsigned long long* sup_keys,
+                            unsigned long long* sup_tmp, const float4* rec, int W, int H,
+                            int sup_x, int tiles_x, int tiles_y, unsigned long long* tile_keys,
+                            uint2* tile_ranges, cudaStream_t st) {
+  sort_split_kernel<TW, TH><<<nsup, kSortThreads, 0, st>>>(
+      sup_ranges, sup_keys, sup_tmp, rec, W, H, sup_x, tiles_x, tiles_y, tile_keys, tile_ranges);
   return cudaGetLastError();
+}
+
+cudaError_t launch_sort_split(int tw, int th, const uint2* sup_ranges, int nsup,
+                              unsigned long long* sup_keys, unsigned long long* sup_tmp,
+                              const float4* rec, int W, int H, int sup_x, int tiles_x,
+                              int tiles_y, unsigned long long* tile_keys, uint2* tile_ranges,
+                              cudaStream_t st) {
+#define GPS_SPLIT(a, b)                                                                      \
+  if (tw == a && th == b)                                                                    \
+    return split_tw<a, b>(sup_ranges, nsup, sup_keys, sup_tmp, rec, W, H, sup_x, tiles_x,    \
+                          tiles_y, tile_keys, tile_ranges, st);
+  GPS_SPLIT(16, 16)
+  GPS_SPLIT(16, 8)
+  GPS_SPLIT(8, 8)
+  GPS_SPLIT(32, 8)
+#undef GPS_SPLIT
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace gps

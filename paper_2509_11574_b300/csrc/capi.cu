@@ -15,16 +15,17 @@ namespace gps {
 cudaError_t launch_fuse(const GpsTsdf&, const float*, const float*, const Cam&, cudaStream_t);
 cudaError_t launch_raycast(const GpsTsdf&, const Cam&, float, float, float*, float*, float*,
                            cudaStream_t);
-cudaError_t launch_project(const GpsGaussians&, const Cam&, float, float4*, uint32_t*, int, int,
-                           int, cudaStream_t);
-cudaError_t launch_count_tiles(const float4*, int, int, int, uint32_t*, int, int, int,
-                               cudaStream_t);
+cudaError_t launch_project(const GpsGaussians&, const Cam&, float, float4*, int, int, uint32_t*,
+                           uint32_t*, cudaStream_t);
 cudaError_t launch_project_backward(const GpsGaussians&, const Cam&, float, const float4*,
                                     const GpsGaussians&, cudaStream_t);
-cudaError_t launch_scan_tiles(uint32_t*, uint2*, int, long long, float*, int*, cudaStream_t);
-cudaError_t launch_emit_pairs(const float4*, int, int, int, const uint2*, uint32_t*,
-                              unsigned long long*, int, int, int, cudaStream_t);
-cudaError_t launch_sort_tiles(const uint2*, int, unsigned long long*, unsigned long long*,
+cudaError_t launch_bin_histogram(const float4*, int, int, int, int, int, uint32_t*, uint32_t*,
+                                 cudaStream_t);
+cudaError_t launch_scan_super(uint32_t*, uint2*, int, long long, float*, int*, cudaStream_t);
+cudaError_t launch_emit_super(const float4*, int, int, int, int, int, const uint2*, const uint32_t*,
+                              unsigned long long*, cudaStream_t);
+cudaError_t launch_sort_split(int, int, const uint2*, int, unsigned long long*, unsigned long long*,
+                              const float4*, int, int, int, int, int, unsigned long long*, uint2*,
                               cudaStream_t);
 cudaError_t launch_composite_fwd(const ViewDev&, float, int, int, int, cudaStream_t);
 cudaError_t launch_composite_bwd(const ViewDev&, float, float, const float*, int, int, int, int,
@@ -75,8 +76,10 @@ bool tile_cfg(const GpsRenderSettings* s, TileCfg& c) {
 }
 
 long long pair_cap(const GpsRenderSettings* s, int M) {
-  return s->pair_capacity > 0 ? s->pair_capacity : 64LL * (M > 0 ? M : 1);
+  return s->pair_capacity > 0 ? s->pair_capacity : 16LL * (M > 0 ? M : 1);
 }
+
+constexpr int kSuperMax = 16384;  // super-tile histogram lives in shared memory
 
 // Workspace: [status 256 B] then per view, in order, its regions.
 int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRenderSettings* s,
@@ -85,30 +88,41 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
   TileCfg tc;
   if (!tile_cfg(s, tc)) return fail(GPS_ERR_INVALID_ARG, "unsupported tile size %dx%d", s->tile_w, s->tile_h);
   const long long cap = pair_cap(s, M);
-  if (cap <= 0 || cap > 0xFFFFFFF0LL) return fail(GPS_ERR_INVALID_ARG, "pair_capacity out of range");
+  const int per_super = (kSuperPx / tc.tw) * (kSuperPx / tc.th);
+  if (cap <= 0 || cap * per_super > 0xFFFFFFF0LL)
+    return fail(GPS_ERR_INVALID_ARG, "pair_capacity out of range");
+  const size_t nblocks = ((size_t)M + 255) / 256;
   size_t off = 256;
   for (int v = 0; v < n_views; ++v) {
     const int W = views[v].K.width, H = views[v].K.height;
     if (W <= 0 || H <= 0) return fail(GPS_ERR_INVALID_ARG, "view %d has size %dx%d", v, W, H);
     const int tx = (W + tc.tw - 1) / tc.tw, ty = (H + tc.th - 1) / tc.th;
-    const size_t ntiles = (size_t)tx * ty, npx = (size_t)W * H;
+    const int sx = (W + kSuperPx - 1) / kSuperPx, sy = (H + kSuperPx - 1) / kSuperPx;
+    if ((long long)sx * sy > kSuperMax)
+      return fail(GPS_ERR_INVALID_ARG, "view %d: image too large (%d super-tiles)", v, sx * sy);
+    const size_t ntiles = (size_t)tx * ty, npx = (size_t)W * H, nsup = (size_t)sx * sy;
     GpsWorkspaceLayout L{};
     L.status = 0;
     L.records = off; off = align256(off + (size_t)M * 64);
-    L.tile_counts = off; off = align256(off + ntiles * 4);
+    L.super_counts = off; off = align256(off + nsup * 4);
+    L.block_base = off; off = align256(off + nblocks * nsup * 4);
+    L.super_ranges = off; off = align256(off + nsup * 8);
+    L.super_keys = off; off = align256(off + (size_t)cap * 8);
+    L.super_scratch = off; off = align256(off + (size_t)cap * 8);
     L.tile_ranges = off; off = align256(off + ntiles * 8);
-    L.pair_keys = off; off = align256(off + (size_t)cap * 8);
-    L.pair_scratch = off; off = align256(off + (size_t)cap * 8);
+    L.pair_keys = off; off = align256(off + (size_t)cap * per_super * 8);
     L.pix_state = off; off = align256(off + npx * 32);
     L.tile_partials = off; off = align256(off + ntiles * 16);
     L.view_scalars = off; off = align256(off + 64);
     L.grad2d = off; off = align256(off + (size_t)M * 48);
     L.pair_grads = off;
-    off = align256(off + (s->deterministic ? (size_t)cap * 48 : 0));
+    off = align256(off + (s->deterministic ? (size_t)cap * per_super * 48 : 0));
     L.tiles_x = tx;
     L.tiles_y = ty;
     L.tile_w = tc.tw;
     L.tile_h = tc.th;
+    L.super_x = sx;
+    L.super_y = sy;
     L.pair_capacity = cap;
     if (v == want && out) *out = L;
   }
@@ -159,11 +173,13 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L) {
   v.g_rgb = vw.grad_rgb;
   v.g_depth = vw.grad_depth;
   v.rec = reinterpret_cast<float4*>(ws + L.records);
-  v.tile_counts = reinterpret_cast<uint32_t*>(ws + L.tile_counts);
-  v.tile_cursor = v.tile_counts;
+  v.sup_count = reinterpret_cast<uint32_t*>(ws + L.super_counts);
+  v.block_base = reinterpret_cast<uint32_t*>(ws + L.block_base);
+  v.sup_ranges = reinterpret_cast<uint2*>(ws + L.super_ranges);
+  v.sup_keys = reinterpret_cast<unsigned long long*>(ws + L.super_keys);
+  v.sup_tmp = reinterpret_cast<unsigned long long*>(ws + L.super_scratch);
   v.tile_ranges = reinterpret_cast<uint2*>(ws + L.tile_ranges);
   v.keys = reinterpret_cast<unsigned long long*>(ws + L.pair_keys);
-  v.keys_tmp = reinterpret_cast<unsigned long long*>(ws + L.pair_scratch);
   const size_t npx = (size_t)vw.K.width * vw.K.height;
   v.pix_a = reinterpret_cast<float4*>(ws + L.pix_state);
   v.pix_b = v.pix_a + npx;
@@ -175,6 +191,8 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L) {
   v.tiles_y = L.tiles_y;
   v.tw = L.tile_w;
   v.th = L.tile_h;
+  v.sup_x = L.super_x;
+  v.sup_y = L.super_y;
   v.cap = L.pair_capacity;
   return v;
 }
@@ -280,22 +298,27 @@ int32_t render_forward(const GpsGaussians* g, const GpsView* views, int32_t n_vi
     GpsWorkspaceLayout L;
     layout(g->M, views, n_views, s, vi, &L, nullptr);
     ViewDev v = make_view(views[vi], base, L);
-    const int ntiles = v.tiles_x * v.tiles_y;
+    const int nsup = v.sup_x * v.sup_y;
     if (stages & GPS_STAGE_PROJECT) {
-      e = cudaMemsetAsync(v.tile_counts, 0, (size_t)ntiles * 4, st);
+      e = cudaMemsetAsync(v.sup_count, 0, (size_t)nsup * 4, st);
       if (e == cudaSuccess && g->M > 0)
-        e = launch_project(*g, v.cam, s->near_plane, v.rec, v.tile_counts, v.tiles_x, v.tw, v.th, st);
+        e = launch_project(*g, v.cam, s->near_plane, v.rec, v.sup_x, nsup, v.sup_count,
+                           v.block_base, st);
     } else if (stages & GPS_STAGE_BIN) {
-      e = cudaMemsetAsync(v.tile_counts, 0, (size_t)ntiles * 4, st);
+      e = cudaMemsetAsync(v.sup_count, 0, (size_t)nsup * 4, st);
       if (e == cudaSuccess && g->M > 0)
-        e = launch_count_tiles(v.rec, g->M, v.cam.W, v.cam.H, v.tile_counts, v.tiles_x, v.tw, v.th, st);
+        e = launch_bin_histogram(v.rec, g->M, v.cam.W, v.cam.H, v.sup_x, nsup, v.sup_count,
+                                 v.block_base, st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_BIN)) {
-      e = launch_scan_tiles(v.tile_counts, v.tile_ranges, ntiles, v.cap, v.scalars, status, st);
+      e = launch_scan_super(v.sup_count, v.sup_ranges, nsup, v.cap, v.scalars, status, st);
       if (e == cudaSuccess && g->M > 0)
-        e = launch_emit_pairs(v.rec, g->M, v.cam.W, v.cam.H, v.tile_ranges, v.tile_cursor, v.keys,
-                              v.tiles_x, v.tw, v.th, st);
-      if (e == cudaSuccess) e = launch_sort_tiles(v.tile_ranges, ntiles, v.keys, v.keys_tmp, st);
+        e = launch_emit_super(v.rec, g->M, v.cam.W, v.cam.H, v.sup_x, nsup, v.sup_ranges,
+                              v.block_base, v.sup_keys, st);
+      if (e == cudaSuccess)
+        e = launch_sort_split(v.tw, v.th, v.sup_ranges, nsup, v.sup_keys, v.sup_tmp, v.rec,
+                              v.cam.W, v.cam.H, v.sup_x, v.tiles_x, v.tiles_y, v.keys,
+                              v.tile_ranges, st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_COMPOSITE)) {
       if (s->instrument) e = cudaMemsetAsync(v.scalars + 8, 0, 32, st);

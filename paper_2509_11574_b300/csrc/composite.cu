@@ -88,17 +88,31 @@ __device__ __forceinline__ float block_max(float v, float* s_tmp) {
 }
 
 // ------------------------------------------------------------------ forward
+// Warp w covers the 8 x 4 pixel block (w % (TW/8), w / (TW/8)) of the tile.
+template <int TW>
+__device__ __forceinline__ void warp_block(int warp, int lane, int& ox, int& oy, int& lx, int& ly) {
+  constexpr int BX = TW / 8;
+  ox = (warp % BX) * 8;
+  oy = (warp / BX) * 4;
+  lx = ox + (lane & 7);
+  ly = oy + (lane >> 3);
+}
+
 template <int TW, int TH, int MODE, bool INSTR>
 __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(ViewDev v, float eps, int has_tgt) {
   constexpr int NT = TW * TH;
-  constexpr int ROWS_PER_WARP = 32 / TW;
+  constexpr int NW = NT / 32;
   __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
-  __shared__ float s_tmp[NT / 32 * 3];
+  __shared__ float2 s_e[NT];
+  __shared__ uint8_t s_list[NW][NT];
+  __shared__ float s_tmp[NW * 3];
   const int W = v.cam.W, H = v.cam.H;
   const int tile = blockIdx.x;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
+  int ox, oy, lx, ly;
+  warp_block<TW>(warp, lane, ox, oy, lx, ly);
+  const int px = tx * TW + lx, py = ty * TH + ly;
   const bool inside = px < W && py < H;
   const long long npx = (long long)W * H, pix = (long long)py * W + px;
   float ct0 = 0.f, ct1 = 0.f, ct2 = 0.f, dt = 0.f;
@@ -113,43 +127,67 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(ViewDev v, float 
   const float bthr = block_max<NT>(thr, s_tmp);
   const uint2 r = v.tile_ranges[tile];
   const uint32_t end = depth_cut(v.keys, r.x, r.y, bthr);
-  const float wy0 = (float)(ty * TH + warp * ROWS_PER_WARP);
-  const float wy1 = wy0 + (float)(ROWS_PER_WARP - 1);
+  // this warp's pixel block, in image coordinates
+  const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
+  const float by0 = (float)(ty * TH + oy), by1 = by0 + 3.0f;
   const float fpx = (float)px, fpy = (float)py;
   float cr = 0.f, cg = 0.f, cb = 0.f, wsum = 0.f, zsum = 0.f, T = 1.0f;
   uint32_t last = r.x;
   bool done = !inside;
+  bool wdone = wthr == -INFINITY;  // warp-uniform: nothing left for this warp
   unsigned n_tested = 0, n_counted = 0;
   for (uint32_t b = r.x; b < end; b += NT) {
     __syncthreads();
-    if (MODE == GPS_BLEND_ALPHA) {
-      if (__syncthreads_and(done)) break;
-    }
+    if (__syncthreads_and(MODE == GPS_BLEND_ALPHA ? (done || wdone) : wdone)) break;
     const uint32_t k = b + tid;
     if (k < end) {
       const uint32_t gi = (uint32_t)v.keys[k];
       const float4* rr = v.rec + 4 * (size_t)gi;
-      float4 A = rr[0], B = rr[1], C = rr[2];
-      const float ey = rr[3].x;
+      float4 A = rr[0], B = rr[1];
+      const float4 C = rr[2];
+      A.w = logf(A.w);   // ln sigma: alpha = exp(ln sigma - q / 2)
       B.y = 2.0f * B.y;  // 2 b, exact
-      C.w = ey;
       s_a[tid] = A;
       s_b[tid] = B;
       s_c[tid] = C;
+      s_e[tid] = make_float2(C.w, rr[3].x);
     }
     __syncthreads();
     const int nb = (int)min((uint32_t)NT, end - b);
-    for (int j = 0; j < nb; ++j) {
-      const float4 A = s_a[j];
-      if (A.z >= wthr) break;  // sorted by depth: the rest is culled for the whole warp
-      const float4 C = s_c[j];
-      if (A.y + C.w < wy0 || A.y - C.w > wy1) continue;  // misses this warp's rows
-      const float4 B = s_b[j];
+    // warp-parallel culling of the batch against this warp's block, in depth
+    // order, stopping at the first Gaussian at or behind the warp's threshold
+    int cnt = 0;
+    if (!wdone) {
+      for (int j0 = 0; j0 < nb; j0 += 32) {
+        const int j = j0 + lane;
+        bool stop = false, ok = false;
+        if (j < nb) {
+          const float4 A = s_a[j];
+          const float2 E = s_e[j];
+          stop = A.z >= wthr;
+          ok = A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 && A.y - E.y <= by1;
+        }
+        const unsigned sb = __ballot_sync(0xffffffffu, stop);
+        unsigned ob = __ballot_sync(0xffffffffu, ok);
+        if (sb) ob &= (sb & (0u - sb)) - 1u;  // keep the entries before the first stop
+        if ((ob >> lane) & 1u) s_list[warp][cnt + __popc(ob & ((1u << lane) - 1u))] = (uint8_t)j;
+        cnt += __popc(ob);
+        if (sb) {
+          wdone = true;
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    for (int t = 0; t < cnt; ++t) {
+      const int j = s_list[warp][t];
+      const float4 A = s_a[j], B = s_b[j];
       const float q = quad_form(B.x, B.y, B.z, __fsub_rn(fpx, A.x), __fsub_rn(fpy, A.y));
       if (INSTR) n_tested += inside;
       if (q <= B.w && A.z < thr) {
         if (INSTR) ++n_counted;
-        const float al = A.w * __expf(-0.5f * q);
+        const float al = __expf(fmaf(q, -0.5f, A.w));
+        const float4 C = s_c[j];
         if (MODE == GPS_BLEND_OIT) {
           cr += al * C.x;
           cg += al * C.y;
@@ -223,13 +261,13 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(ViewDev v, float 
     }
     __syncthreads();
     if (tid == 0) {
-      float a = 0.f, b = 0.f, c = 0.f;
-      for (int k = 0; k < NT / 32; ++k) {
+      float a = 0.f, bsum = 0.f, c = 0.f;
+      for (int k = 0; k < NW; ++k) {
         a += s_tmp[k * 3];
-        b += s_tmp[k * 3 + 1];
+        bsum += s_tmp[k * 3 + 1];
         c += s_tmp[k * 3 + 2];
       }
-      v.tile_partials[tile] = make_float4(a, b, c, 0.f);
+      v.tile_partials[tile] = make_float4(a, bsum, c, 0.f);
     }
   }
 }
@@ -323,19 +361,36 @@ __device__ __forceinline__ void store_grad2d(const ViewDev& v, int deterministic
 }
 
 // ------------------------------------------------------- backward, OIT mode
+constexpr int kBwdBatch = 64;  // list entries staged per round of the OIT backward
+
+// OIT backward: warp w owns the same 8 x 4 pixel block as in the forward.  Per
+// staged batch, each warp compacts the Gaussians whose rectangle overlaps its
+// block (depth order, cut at the block's threshold); lanes take one Gaussian
+// each and walk the block's pixels (shared-memory broadcasts), accumulating
+// 10 moments privately.  Per-warp partials are summed over warps in a fixed
+// order and turned into the 2D gradient of the (tile, Gaussian) pair.
 template <int TW, int TH, bool INSTR>
 __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, float eps,
                                                                    float lambda, const float* dloss,
                                                                    int fused, int deterministic) {
   constexpr int NT = TW * TH;
+  constexpr int NW = NT / 32;
+  constexpr int NB = kBwdBatch;
   __shared__ float4 s_h[NT];
   __shared__ float2 s_s[NT];
-  __shared__ float s_tmp[NT / 32];
+  __shared__ float4 s_a[NB], s_b[NB], s_c[NB];
+  __shared__ float2 s_e[NB];
+  __shared__ float s_part[NW][NB][10];
+  __shared__ unsigned long long s_mask[NW];
+  __shared__ uint8_t s_list[NW][NB];
+  __shared__ float s_tmp[NW];
   const int W = v.cam.W, H = v.cam.H;
   const int tile = blockIdx.x;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
-  const int tid = threadIdx.x;
-  const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int ox, oy, lx, ly;
+  warp_block<TW>(warp, lane, ox, oy, lx, ly);
+  const int px = tx * TW + lx, py = ty * TH + ly;
   const bool inside = px < W && py < H;
   const long long npx = (long long)W * H, pix = (long long)py * W + px;
   const float scale = loss_scale(v, fused, dloss);
@@ -353,73 +408,137 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, fl
   }
   s_h[tid] = h;
   s_s[tid] = make_float2(sv, thr);
+  const float wthr = warp_max(thr);
   const float bthr = block_max<NT>(thr, s_tmp);
   const uint2 r = v.tile_ranges[tile];
   const uint32_t end = depth_cut(v.keys, r.x, r.y, bthr);
-  const int tx0 = tx * TW, ty0 = ty * TH;
+  const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
+  const float by0 = (float)(ty * TH + oy), by1 = by0 + 3.0f;
+  const int blk = warp * 32;  // this warp's pixels in s_h / s_s
+  bool wdone = wthr == -INFINITY;
   unsigned n_tested = 0, n_counted = 0;
-  for (uint32_t b = r.x; b < end; b += NT) {
-    const uint32_t k = b + tid;
-    const bool has = k < end;
-    uint32_t gi = 0;
-    float mx = 0.f, my = 0.f, d = 0.f, sig = 0.f, ca = 0.f, cb = 0.f, cc = 0.f, qmax = -1.f;
-    float cr = 0.f, cg = 0.f, cbl = 0.f;
-    int lx0 = TW, lx1 = -1, ly0 = TH, ly1 = -1;
-    if (has) {
-      gi = (uint32_t)v.keys[k];
+  for (uint32_t b = r.x; b < end; b += NB) {
+    __syncthreads();
+    if (__syncthreads_and(wdone)) break;
+    if (tid < NB && b + tid < end) {
+      const uint32_t gi = (uint32_t)v.keys[b + tid];
       const float4* rr = v.rec + 4 * (size_t)gi;
-      const float4 A = rr[0], B = rr[1], C = rr[2];
-      const float ey = rr[3].x;
-      mx = A.x; my = A.y; d = A.z; sig = A.w;
-      ca = B.x; cb = B.y; cc = B.z; qmax = B.w;
-      cr = C.x; cg = C.y; cbl = C.z;
-      int x0, x1, y0, y1;
-      if (record_rect(mx, my, C.w, ey, W, H, x0, x1, y0, y1)) {
-        lx0 = max(x0 - tx0, 0);
-        lx1 = min(x1 - tx0, TW - 1);
-        ly0 = max(y0 - ty0, 0);
-        ly1 = min(y1 - ty0, TH - 1);
-      }
+      float4 B = rr[1];
+      const float4 C = rr[2];
+      B.y = 2.0f * B.y;
+      s_a[tid] = rr[0];
+      s_b[tid] = B;
+      s_c[tid] = C;
+      s_e[tid] = make_float2(C.w, rr[3].x);
     }
-    // loop over the union of this warp's rectangles (warp-uniform bounds)
-    const int ux0 = warp_min_i(lx0), ux1 = warp_max_i(lx1);
-    const int uy0 = warp_min_i(ly0), uy1 = warp_max_i(ly1);
-    const float b2 = 2.0f * cb;
-    float dcr = 0.f, dcg = 0.f, dcb = 0.f, dd = 0.f, dsig = 0.f;
-    float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-    for (int yy = uy0; yy <= uy1; ++yy) {
-      const float dy = __fsub_rn((float)(ty0 + yy), my);
-      for (int xx = ux0; xx <= ux1; ++xx) {
-        const int p = yy * TW + xx;
-        const float2 ss = s_s[p];
-        const float dx = __fsub_rn((float)(tx0 + xx), mx);
-        const float q = quad_form(ca, b2, cc, dx, dy);
-        if (INSTR) n_tested += has && xx >= lx0 && xx <= lx1 && yy >= ly0 && yy <= ly1;
-        if (q <= qmax && d < ss.y) {
-          if (INSTR) ++n_counted;
-          const float4 hh = s_h[p];
-          const float G = __expf(-0.5f * q);
-          const float al = sig * G;
-          dcr += al * hh.x;
-          dcg += al * hh.y;
-          dcb += al * hh.z;
-          dd += al * hh.w;
-          const float dLda = hh.x * cr + hh.y * cg + hh.z * cbl + hh.w * d - ss.x;
-          dsig += G * dLda;
-          const float vv = dLda * al;
-          const float tx_ = vv * dx, ty_ = vv * dy;
-          sx += tx_;
-          sy += ty_;
-          sxx += tx_ * dx;
-          sxy += tx_ * dy;
-          syy += ty_ * dy;
+    __syncthreads();
+    const int nb = (int)min((uint32_t)NB, end - b);
+    int cnt = 0;
+    unsigned long long mask = 0;
+    if (!wdone) {
+      for (int j0 = 0; j0 < nb; j0 += 32) {
+        const int j = j0 + lane;
+        bool stop = false, ok = false;
+        if (j < nb) {
+          const float4 A = s_a[j];
+          const float2 E = s_e[j];
+          stop = A.z >= wthr;
+          ok = A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 && A.y - E.y <= by1;
+        }
+        const unsigned sb = __ballot_sync(0xffffffffu, stop);
+        unsigned ob = __ballot_sync(0xffffffffu, ok);
+        if (sb) ob &= (sb & (0u - sb)) - 1u;
+        if ((ob >> lane) & 1u) s_list[warp][cnt + __popc(ob & ((1u << lane) - 1u))] = (uint8_t)j;
+        cnt += __popc(ob);
+        mask |= (unsigned long long)ob << j0;
+        if (sb) {
+          wdone = true;
+          break;
         }
       }
     }
-    if (has) {
-      const float g[10] = {ca * sx + cb * sy, cb * sx + cc * sy, -0.5f * sxx, -sxy, -0.5f * syy,
-                           dsig, dcr, dcg, dcb, dd};
-      store_grad2d(v, deterministic, k, gi, g);
+    if (lane == 0) s_mask[warp] = mask;
+    __syncwarp();
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+      const int t = c0 + lane;
+      const bool has = t < cnt;
+      const int j = has ? s_list[warp][t] : 0;
+      float mx = 0.f, my = 0.f, d = 0.f, lns = 0.f, ca = 0.f, b2 = 0.f, cc = 0.f, qmax = -1.f;
+      float cr = 0.f, cg = 0.f, cbl = 0.f;
+      int kx0 = 8, kx1 = -1, ky0 = 4, ky1 = -1;
+      if (has) {
+        const float4 A = s_a[j], B = s_b[j], C = s_c[j];
+        const float2 E = s_e[j];
+        mx = A.x; my = A.y; d = A.z; lns = logf(A.w);
+        ca = B.x; b2 = B.y; cc = B.z; qmax = B.w;
+        cr = C.x; cg = C.y; cbl = C.z;
+        // this Gaussian's rectangle inside the block (block-local pixel indices)
+        kx0 = max(0, (int)ceilf(mx - E.x - bx0));
+        kx1 = min(7, (int)floorf(mx + E.x - bx0));
+        ky0 = max(0, (int)ceilf(my - E.y - by0));
+        ky1 = min(3, (int)floorf(my + E.y - by0));
+      }
+      const int ux0 = warp_min_i(kx0), ux1 = warp_max_i(kx1);
+      const int uy0 = warp_min_i(ky0), uy1 = warp_max_i(ky1);
+      float dcr = 0.f, dcg = 0.f, dcb = 0.f, dd = 0.f, sa = 0.f;
+      float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+      for (int ky = uy0; ky <= uy1; ++ky) {
+        const float dy = __fsub_rn(by0 + (float)ky, my);
+        for (int kx = ux0; kx <= ux1; ++kx) {
+          const int p = blk + ky * 8 + kx;
+          const float2 ss = s_s[p];
+          const float dx = __fsub_rn(bx0 + (float)kx, mx);
+          const float q = quad_form(ca, b2, cc, dx, dy);
+          if (INSTR) n_tested += has && kx >= kx0 && kx <= kx1 && ky >= ky0 && ky <= ky1;
+          if (q <= qmax && d < ss.y) {
+            if (INSTR) ++n_counted;
+            const float4 hh = s_h[p];
+            const float al = __expf(fmaf(q, -0.5f, lns));
+            dcr += al * hh.x;
+            dcg += al * hh.y;
+            dcb += al * hh.z;
+            dd += al * hh.w;
+            const float dLda =
+                fmaf(hh.x, cr, fmaf(hh.y, cg, fmaf(hh.z, cbl, fmaf(hh.w, d, -ss.x))));
+            const float vv = dLda * al;
+            sa += vv;
+            const float tx_ = vv * dx, ty_ = vv * dy;
+            sx += tx_;
+            sy += ty_;
+            sxx += tx_ * dx;
+            sxy += tx_ * dy;
+            syy += ty_ * dy;
+          }
+        }
+      }
+      if (has) {
+        float* o = s_part[warp][j];
+        o[0] = dcr; o[1] = dcg; o[2] = dcb; o[3] = dd; o[4] = sa;
+        o[5] = sx; o[6] = sy; o[7] = sxx; o[8] = sxy; o[9] = syy;
+      }
+    }
+    __syncthreads();
+    // fixed-order sum over warps, one gradient per (tile, Gaussian) pair
+    for (int t = tid; t < nb; t += NT) {
+      float m[10];
+#pragma unroll
+      for (int c = 0; c < 10; ++c) m[c] = 0.f;
+      bool any = false;
+      for (int w2 = 0; w2 < NW; ++w2) {
+        if ((s_mask[w2] >> t) & 1ull) {
+          any = true;
+#pragma unroll
+          for (int c = 0; c < 10; ++c) m[c] += s_part[w2][t][c];
+        }
+      }
+      if (any || deterministic) {
+        const float4 A = s_a[t], B = s_b[t];
+        const float ca = B.x, cb = 0.5f * B.y, cc = B.z;
+        // dL/dsigma = sum dL/dalpha * G = (sum dL/dalpha * alpha) / sigma
+        const float g[10] = {ca * m[5] + cb * m[6], cb * m[5] + cc * m[6], -0.5f * m[7], -m[8],
+                             -0.5f * m[9], m[4] / A.w, m[0], m[1], m[2], m[3]};
+        store_grad2d(v, deterministic, b + t, (uint32_t)v.keys[b + t], g);
+      }
     }
   }
   if (INSTR) add_counters(v, 2, n_tested, n_counted);

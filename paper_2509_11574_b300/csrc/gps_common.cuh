@@ -14,6 +14,8 @@ constexpr float kExtRel = 1.0f + 0.0078125f;  // 1 + 2^-7: conservative extent
 constexpr float kExtAbs = 0.0625f;             // 2^-4 px
 constexpr float kAlphaMax = 0.99f;             // Table 7 variant (3DGS clamp)
 constexpr float kTMin = 1e-4f;                 // Table 7 variant termination
+constexpr int kSuperPx = 32;                   // super-tile edge (pixels) of the binning
+constexpr int kSuperShift = 5;
 
 // grad2d slot names
 enum { G_MX = 0, G_MY, G_CA, G_CB, G_CC, G_SIG, G_R, G_G, G_B, G_D };
@@ -39,11 +41,13 @@ struct ViewDev {
   const float* g_depth;  // nullable
   // workspace regions
   float4* rec;           // [M][4] float4
-  uint32_t* tile_counts;
-  uint2* tile_ranges;
-  uint32_t* tile_cursor;  // shares the tile_counts region after the scan
-  unsigned long long* keys;
-  unsigned long long* keys_tmp;
+  uint32_t* sup_count;   // [nsup]
+  uint32_t* block_base;  // [ceil(M/256)][nsup]
+  uint2* sup_ranges;     // [nsup]
+  unsigned long long* sup_keys;
+  unsigned long long* sup_tmp;
+  uint2* tile_ranges;    // [tiles]
+  unsigned long long* keys;  // tile lists
   float4* pix_a;  // [npx] (C*.rgb, D*)
   float4* pix_b;  // [npx] (W_G | T_end, n_last, -, -)
   float4* tile_partials;  // [tiles] (sum|dC|, sum|dD|, n_valid, -)
@@ -51,6 +55,7 @@ struct ViewDev {
   float4* grad2d;         // [M][3] float4
   float4* pair_grads;     // [cap][3] float4
   int tiles_x, tiles_y, tw, th;
+  int sup_x, sup_y;
   long long cap;
 };
 
@@ -84,6 +89,22 @@ __device__ __forceinline__ float depth_threshold(float Dt, float eps) {
 
 __device__ __forceinline__ unsigned long long key_of(float d, uint32_t idx) {
   return ((unsigned long long)__float_as_uint(d) << 32) | idx;
+}
+
+// Binning: after every thread of the block has added its Gaussians' super-tiles
+// to the shared histogram s_hist, reserve one range per nonzero super-tile with
+// one global atomic; the block's base inside super-tile s goes to
+// block_base[block][s].
+__device__ __forceinline__ void reserve_block_ranges(uint32_t* s_hist, int nsup,
+                                                     uint32_t* __restrict__ sup_count,
+                                                     uint32_t* __restrict__ block_base) {
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsup; s += blockDim.x) {
+    const uint32_t h = s_hist[s];
+    uint32_t base = 0;
+    if (h) base = atomicAdd(sup_count + s, h);
+    block_base[(size_t)blockIdx.x * nsup + s] = base;
+  }
 }
 
 // status word helpers

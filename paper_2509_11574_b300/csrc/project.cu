@@ -1,7 +1,7 @@
 // Projection of 3D Gaussians to 2D conics (Sec. 3.1, "following 3DGS") and its
 // adjoint.  One thread per Gaussian; parameters are read once (56 B) and one
-// 64-byte record is written.  The forward also counts, per tile, how many
-// Gaussians' conservative rectangles touch it (first half of the binning).
+// 64-byte record is written.  The forward also builds its block's histogram of
+// super-tiles touched and reserves the block's ranges (first half of the binning).
 #include <cuda_runtime.h>
 
 #include "gps_common.cuh"
@@ -99,46 +99,39 @@ __device__ __forceinline__ void project_gaussian(const Params& P, int i, const C
   o.vis = isfinite(o.mx) && isfinite(o.my) && isfinite(o.ca) && isfinite(o.cb) && isfinite(o.cc);
 }
 
-// K3: records + per-tile counts.  tile_counts must be zero on entry.
+// K3: records, plus the block's super-tile histogram and range reservation
+// (first half of the binning).  sup_count must be zero on entry.
 __global__ void __launch_bounds__(256) project_kernel(Params P, int M, Cam cam, float near_,
-                                                      float4* __restrict__ rec,
-                                                      uint32_t* __restrict__ tile_counts,
-                                                      int tiles_x, int tw, int th) {
+                                                      float4* __restrict__ rec, int sup_x,
+                                                      int nsup, uint32_t* __restrict__ sup_count,
+                                                      uint32_t* __restrict__ block_base) {
+  extern __shared__ uint32_t s_hist[];
+  for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_hist[s] = 0;
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  ProjState o;
-  project_gaussian(P, i, cam, near_, o);
-  float4* r = rec + 4 * (size_t)i;
-  if (!o.vis) {
-    r[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    r[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    r[2] = make_float4(0.f, 0.f, 0.f, -1.0f);
-    r[3] = make_float4(-1.0f, 0.f, 0.f, 0.f);
-    return;
+  if (i < M) {
+    ProjState o;
+    project_gaussian(P, i, cam, near_, o);
+    float4* r = rec + 4 * (size_t)i;
+    if (!o.vis) {
+      r[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+      r[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      r[2] = make_float4(0.f, 0.f, 0.f, -1.0f);
+      r[3] = make_float4(-1.0f, 0.f, 0.f, 0.f);
+    } else {
+      const float* col = P.rgb + 3 * (size_t)i;
+      r[0] = make_float4(o.mx, o.my, o.tc[2], o.sig);
+      r[1] = make_float4(o.ca, o.cb, o.cc, o.qmax);
+      r[2] = make_float4(col[0], col[1], col[2], o.ex);
+      r[3] = make_float4(o.ey, 0.f, 0.f, 0.f);
+      int x0, x1, y0, y1;
+      record_rect(o.mx, o.my, o.ex, o.ey, cam.W, cam.H, x0, x1, y0, y1);
+      for (int sy = y0 >> kSuperShift; sy <= (y1 >> kSuperShift); ++sy)
+        for (int sx = x0 >> kSuperShift; sx <= (x1 >> kSuperShift); ++sx)
+          atomicAdd(s_hist + sy * sup_x + sx, 1u);
+    }
   }
-  const float* col = P.rgb + 3 * (size_t)i;
-  r[0] = make_float4(o.mx, o.my, o.tc[2], o.sig);
-  r[1] = make_float4(o.ca, o.cb, o.cc, o.qmax);
-  r[2] = make_float4(col[0], col[1], col[2], o.ex);
-  r[3] = make_float4(o.ey, 0.f, 0.f, 0.f);
-  int x0, x1, y0, y1;
-  record_rect(o.mx, o.my, o.ex, o.ey, cam.W, cam.H, x0, x1, y0, y1);
-  for (int ty = y0 / th; ty <= y1 / th; ++ty)
-    for (int tx = x0 / tw; tx <= x1 / tw; ++tx) atomicAdd(tile_counts + ty * tiles_x + tx, 1u);
-}
-
-// Per-tile counts from caller-provided records (binning stage run on its own).
-__global__ void __launch_bounds__(256) count_tiles_kernel(const float4* __restrict__ rec, int M,
-                                                          int W, int H,
-                                                          uint32_t* __restrict__ tile_counts,
-                                                          int tiles_x, int tw, int th) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
-  int x0, x1, y0, y1;
-  if (!record_rect(a.x, a.y, c.w, e.x, W, H, x0, x1, y0, y1)) return;
-  for (int ty = y0 / th; ty <= y1 / th; ++ty)
-    for (int tx = x0 / tw; tx <= x1 / tw; ++tx) atomicAdd(tile_counts + ty * tiles_x + tx, 1u);
+  reserve_block_ranges(s_hist, nsup, sup_count, block_base);
 }
 
 // K8: adjoint of the projection.  g2 holds this view's per-Gaussian 2D
@@ -248,16 +241,11 @@ __global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, 
 }
 
 cudaError_t launch_project(const GpsGaussians& g, const Cam& cam, float near_, float4* rec,
-                           uint32_t* tile_counts, int tiles_x, int tw, int th, cudaStream_t st) {
+                           int sup_x, int nsup, uint32_t* sup_count, uint32_t* block_base,
+                           cudaStream_t st) {
   Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb};
-  project_kernel<<<(g.M + 255) / 256, 256, 0, st>>>(P, g.M, cam, near_, rec, tile_counts, tiles_x,
-                                                     tw, th);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_count_tiles(const float4* rec, int M, int W, int H, uint32_t* tile_counts,
-                               int tiles_x, int tw, int th, cudaStream_t st) {
-  count_tiles_kernel<<<(M + 255) / 256, 256, 0, st>>>(rec, M, W, H, tile_counts, tiles_x, tw, th);
+  project_kernel<<<(g.M + 255) / 256, 256, nsup * sizeof(uint32_t), st>>>(
+      P, g.M, cam, near_, rec, sup_x, nsup, sup_count, block_base);
   return cudaGetLastError();
 }
 

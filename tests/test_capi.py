@@ -76,10 +76,11 @@ def test_workspace_size_and_layout_host_only(L):
     L0 = gps.gps_workspace_layout(2000, cams, s, 0)
     L1 = gps.gps_workspace_layout(2000, cams, s, 1)
     assert L0.tiles_x == 10 and L0.tiles_y == 8 and L1.tiles_x == 5 and L1.tiles_y == 3
-    assert L0.records < L0.pair_keys < L0.grad2d < L1.records
-    for off in (L0.records, L0.pair_keys, L0.pix_state, L1.grad2d):
+    assert L0.records < L0.super_keys < L0.pair_keys < L0.grad2d < L1.records
+    for off in (L0.records, L0.block_base, L0.pair_keys, L0.pix_state, L1.grad2d):
         assert off % 256 == 0
-    assert L0.pair_capacity == 64 * 2000
+    assert L0.pair_capacity == 16 * 2000
+    assert (L0.super_x, L0.super_y, L1.super_x, L1.super_y) == (5, 4, 3, 2)
     s2 = gps.settings(deterministic=True)
     assert gps.gps_workspace_size(2000, cams, s2) > n
     with pytest.raises(gps.GpsError) as e:
