@@ -257,6 +257,34 @@ GPS_API int32_t render_backward(const GpsGaussians* gaussians, const GpsView* vi
 GPS_API int32_t adam_step(GpsGaussians* params, GpsGaussians* grads, GpsGaussians* m, GpsGaussians* v,
                   const GpsAdamHyper* hyper, int32_t step, int32_t* device_step, void* stream);
 
+/* Size of the static device array behind render_forward_noalloc: 64 MiB,
+ * held by every GPU that loads this library until the process exits. */
+#define GPS_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* render_forward without a caller-provided workspace.  The paper has no
+ * counterpart: this entry point exists for callers that may not call
+ * cudaMalloc - for example code running inside a host application that owns
+ * every device allocation (a plug-in), or a real-time loop whose device memory
+ * is fixed at start-up.  It runs the full forward (settings.stages is ignored)
+ * on a file-scope static device array of GPS_NOALLOC_SCRATCH_BYTES and
+ * allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ *   - Arguments, outputs (views' out_* images, *loss) and errors are those of
+ *     render_forward; a problem whose workspace (gps_workspace_size) exceeds
+ *     GPS_NOALLOC_SCRATCH_BYTES is rejected with GPS_ERR_WORKSPACE_TOO_SMALL
+ *     before anything is launched.
+ *   - The first call on each device performs a one-time set-up with that
+ *     device current (it looks up the array's device address with
+ *     cudaGetSymbolAddress); make that first call before any stream capture
+ *     begins.
+ *   - Every call on a device shares the one array, and the array keeps the
+ *     last call's contents (so render_backward cannot be paired with it):
+ *     calls whose work overlaps on the GPU - on different streams or from
+ *     different threads - race with each other and must be serialised by the
+ *     caller. */
+GPS_API int32_t render_forward_noalloc(const GpsGaussians* gaussians, const GpsView* views,
+                                       int32_t n_views, const GpsRenderSettings* settings,
+                                       float* loss, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,7 +94,8 @@ class GpsWorkspaceLayout(ctypes.Structure):
 
 EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspace_layout",
             "gps_query_status", "fuse_frame", "raycast_sdf", "render_forward", "render_backward",
-            "adam_step")
+            "adam_step", "render_forward_noalloc")
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib: Optional[ctypes.CDLL] = None
 
@@ -137,6 +138,10 @@ def lib() -> ctypes.CDLL:
         L.adam_step.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsGaussians),
                                 ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsGaussians),
                                 ctypes.POINTER(GpsAdamHyper), c_int32, c_void_p, c_void_p]
+        L.render_forward_noalloc.argtypes = [ctypes.POINTER(GpsGaussians),
+                                             ctypes.POINTER(GpsView), c_int32,
+                                             ctypes.POINTER(GpsRenderSettings), c_void_p,
+                                             c_void_p]
         _lib = L
     return _lib
 
@@ -337,6 +342,15 @@ def render_forward(g: Gaussians, views: Sequence[View], s: GpsRenderSettings, ws
     va = _views(views)
     _check(lib().render_forward(ctypes.byref(gc), va, len(views), ctypes.byref(s), _ptr(ws),
                                 ws.numel(), _ptr(loss), _stream(stream)))
+
+
+def render_forward_noalloc(g: Gaussians, views: Sequence[View], s: GpsRenderSettings,
+                           loss: Optional[torch.Tensor] = None, stream=None) -> None:
+    """render_forward on the library's static device scratch (no workspace)."""
+    gc = g.c()
+    va = _views(views)
+    _check(lib().render_forward_noalloc(ctypes.byref(gc), va, len(views), ctypes.byref(s),
+                                        _ptr(loss), _stream(stream)))
 
 
 def render_backward(g: Gaussians, views: Sequence[View], s: GpsRenderSettings, ws: torch.Tensor,

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgps.so")
-SOURCES = ["tsdf.cu", "project.cu", "binning.cu", "composite.cu", "adam.cu", "capi.cu"]
+SOURCES = ["tsdf.cu", "project.cu", "binning.cu", "composite.cu", "adam.cu", "capi.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -224,6 +224,10 @@ int32_t check_render_args(const GpsGaussians* g, const GpsView* views, int32_t n
 
 }  // namespace
 
+namespace gps {
+void set_error(const char* msg) { g_err = msg; }
+}  // namespace gps
+
 extern "C" {
 
 const char* gps_last_error(void) { return g_err.c_str(); }
