@@ -157,8 +157,10 @@ typedef struct GpsAdamHyper {
  *   mx, my, d, sigma, conic_a, conic_b, conic_c, qmax, r, g, b, ext_x, ext_y, 0, 0, 0
  * with q = a dx^2 + 2 b dx dy + c dy^2, support {q <= qmax}, qmax =
  * 2 ln(255 sigma), and a conservative half-extent ext (ext_x < 0: culled).
- * Binning first buckets Gaussians into 32 x 32-pixel super-tiles, then splits
- * each super-tile's sorted segment into its tiles.  Tile lists: keys u64 =
+ * Binning first buckets Gaussians into super-tiles of super_px x super_px
+ * pixels, sorts each segment, then splits it into its tiles (when a tile is a
+ * whole super-tile its list is the segment itself: tile_ranges ==
+ * super_ranges and pair_keys == super_keys).  Tile lists: keys u64 =
  * bits(d) << 32 | index, sorted ascending; tile t's list is pair_keys[
  * tile_ranges[t][0] .. tile_ranges[t][1]) (lists are not contiguous).
  * grad2d holds 12 floats per Gaussian: d/d(mx, my, conic_a, conic_b, conic_c,
@@ -172,6 +174,8 @@ typedef struct GpsWorkspaceLayout {
   size_t super_ranges;  /* uint32 [super_tiles][2]                            */
   size_t super_keys;    /* uint64 [pair_capacity] super-tile segments         */
   size_t super_scratch; /* uint64 [pair_capacity] (sort scratch)              */
+  size_t super_rects;   /* uint64 [pair_capacity] pixel rectangle of each
+                           sorted entry: x0, x1, y0, y1 as 4 x uint16          */
   size_t tile_ranges;   /* uint32 [tiles][2]                                  */
   size_t pair_keys;     /* uint64 [tiles per super-tile * pair_capacity]      */
   size_t pix_state;     /* float [H*W][8] saved per-pixel forward state       */
@@ -184,6 +188,8 @@ typedef struct GpsWorkspaceLayout {
   size_t pair_grads;    /* float [tiles per super-tile * pair_capacity][12]
                            (deterministic mode)                               */
   int32_t tiles_x, tiles_y, tile_w, tile_h, super_x, super_y;
+  int32_t super_px;     /* super-tile edge in pixels (16, or 32 for 32-px-wide tiles) */
+  int32_t reserved;
   int64_t pair_capacity;
 } GpsWorkspaceLayout;
 

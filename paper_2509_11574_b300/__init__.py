@@ -84,12 +84,13 @@ class GpsAdamHyper(ctypes.Structure):
 class GpsWorkspaceLayout(ctypes.Structure):
     _fields_ = [("total_bytes", c_size_t), ("status", c_size_t), ("records", c_size_t),
                 ("super_counts", c_size_t), ("block_base", c_size_t), ("super_ranges", c_size_t),
-                ("super_keys", c_size_t), ("super_scratch", c_size_t), ("tile_ranges", c_size_t),
+                ("super_keys", c_size_t), ("super_scratch", c_size_t), ("super_rects", c_size_t),
+                ("tile_ranges", c_size_t),
                 ("pair_keys", c_size_t), ("pix_state", c_size_t), ("tile_partials", c_size_t),
                 ("view_scalars", c_size_t), ("grad2d", c_size_t), ("pair_grads", c_size_t),
                 ("tiles_x", c_int32), ("tiles_y", c_int32), ("tile_w", c_int32),
                 ("tile_h", c_int32), ("super_x", c_int32), ("super_y", c_int32),
-                ("pair_capacity", c_int64)]
+                ("super_px", c_int32), ("reserved", c_int32), ("pair_capacity", c_int64)]
 
 
 EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspace_layout",

@@ -2,7 +2,8 @@
 //
 // The sort key is (tile, bits(depth), index).  Its most significant part is
 // placed in two levels:
-//   1. super-tiles of 32 x 32 px: every block of the projection histograms its
+//   1. super-tiles (16 x 16 px, or 32 x 32 px for 32-px-wide tiles): every
+//      block of the projection histograms its
 //      Gaussians' super-tile rectangles in shared memory and reserves one range
 //      per (block, super-tile) with a single global atomic; after a scan over
 //      super-tiles, the emission writes bits(d) << 32 | index into those ranges
@@ -10,8 +11,9 @@
 //      per-(Gaussian, tile) global atomic and no contended counter chain.
 //   2. one CTA per super-tile sorts its segment by the 64-bit key (8 keys per
 //      thread in registers with a sorting network, then merge-path rounds in
-//      shared memory) and splits it, in order, into the lists of its tiles
-//      (rectangle overlap, the same test as the oracle's binning).
+//      shared memory) and stores each entry's pixel rectangle beside it;
+//   3. one CTA per tile filters its super-tile's sorted segment, in order, by
+//      rectangle overlap (the same test as the oracle's binning).
 // The result equals a stable sort of (tile << 32 | bits(d)) keys with ties in
 // index order, independent of the order the atomics ran in.
 #include <cuda_runtime.h>
@@ -24,20 +26,20 @@ constexpr int kScanThreads = 1024;
 
 // -------------------------------------------------- super-tile histograms
 __device__ __forceinline__ bool super_rect(float mx, float my, float ex, float ey, int W, int H,
-                                           int& sx0, int& sx1, int& sy0, int& sy1) {
+                                           int sh, int& sx0, int& sx1, int& sy0, int& sy1) {
   int x0, x1, y0, y1;
   if (!record_rect(mx, my, ex, ey, W, H, x0, x1, y0, y1)) return false;
-  sx0 = x0 >> kSuperShift;
-  sx1 = x1 >> kSuperShift;
-  sy0 = y0 >> kSuperShift;
-  sy1 = y1 >> kSuperShift;
+  sx0 = x0 >> sh;
+  sx1 = x1 >> sh;
+  sy0 = y0 >> sh;
+  sy1 = y1 >> sh;
   return true;
 }
 
 // Histogram of caller-provided records (binning stage run on its own; the
 // projection kernel fuses the same histogram).
 __global__ void __launch_bounds__(256) bin_histogram_kernel(const float4* __restrict__ rec, int M,
-                                                            int W, int H, int sup_x, int nsup,
+                                                            int W, int H, int sh, int sup_x, int nsup,
                                                             uint32_t* __restrict__ sup_count,
                                                             uint32_t* __restrict__ block_base) {
   extern __shared__ uint32_t s_hist[];
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(256) bin_histogram_kernel(const float4* __rest
   if (i < M) {
     const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
     int sx0, sx1, sy0, sy1;
-    if (super_rect(a.x, a.y, c.w, e.x, W, H, sx0, sx1, sy0, sy1))
+    if (super_rect(a.x, a.y, c.w, e.x, W, H, sh, sx0, sx1, sy0, sy1))
       for (int sy = sy0; sy <= sy1; ++sy)
         for (int sx = sx0; sx <= sx1; ++sx) atomicAdd(s_hist + sy * sup_x + sx, 1u);
   }
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_super_kernel(uint32_t* __re
 
 // Emission into the reserved ranges; same block partition as the histogram.
 __global__ void __launch_bounds__(256) emit_super_kernel(const float4* __restrict__ rec, int M,
-                                                         int W, int H, int sup_x, int nsup,
+                                                         int W, int H, int sh, int sup_x, int nsup,
                                                          const uint2* __restrict__ sup_ranges,
                                                          const uint32_t* __restrict__ block_base,
                                                          unsigned long long* __restrict__ keys) {
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(256) emit_super_kernel(const float4* __restric
   if (i >= M) return;
   const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
   int sx0, sx1, sy0, sy1;
-  if (!super_rect(a.x, a.y, c.w, e.x, W, H, sx0, sx1, sy0, sy1)) return;
+  if (!super_rect(a.x, a.y, c.w, e.x, W, H, sh, sx0, sx1, sy0, sy1)) return;
   const unsigned long long key = key_of(a.z, (uint32_t)i);
   const uint32_t* bb = block_base + (size_t)blockIdx.x * nsup;
   for (int sy = sy0; sy <= sy1; ++sy)
@@ -230,91 +232,87 @@ __device__ unsigned long long* large_sort(unsigned long long* seg, unsigned long
   return src;
 }
 
-// One CTA per super-tile: sort its segment, then split it in order into the
-// lists of its tiles.  Tile l of super-tile s owns tile_keys[L * start_s +
-// l * n_s ...] (a list is never longer than its super-tile's segment).
-template <int TW, int TH>
-__global__ void __launch_bounds__(kSortThreads) sort_split_kernel(
+__device__ __forceinline__ unsigned long long pack_rect(int x0, int x1, int y0, int y1) {
+  return (unsigned long long)(uint16_t)x0 | ((unsigned long long)(uint16_t)x1 << 16) |
+         ((unsigned long long)(uint16_t)y0 << 32) | ((unsigned long long)(uint16_t)y1 << 48);
+}
+
+// One CTA per super-tile: sort its segment in place and write, beside each
+// sorted key, its Gaussian's pixel rectangle (x0, x1, y0, y1 as 4 x u16).
+__global__ void __launch_bounds__(kSortThreads) sort_super_kernel(
     const uint2* __restrict__ sup_ranges, unsigned long long* __restrict__ sup_keys,
-    unsigned long long* __restrict__ sup_tmp, const float4* __restrict__ rec, int W, int H,
-    int sup_x, int tiles_x, int tiles_y, unsigned long long* __restrict__ tile_keys,
-    uint2* __restrict__ tile_ranges) {
-  constexpr int LX = kSuperPx / TW, LY = kSuperPx / TH, L = LX * LY;
-  constexpr int NW = kSortThreads / 32;
+    unsigned long long* __restrict__ sup_tmp, unsigned long long* __restrict__ sup_rect,
+    const float4* __restrict__ rec, int W, int H) {
   __shared__ unsigned long long buf[kSortCap];
-  __shared__ uint32_t s_cnt[L][NW];
-  __shared__ uint32_t s_run[L];
-  const int s = blockIdx.x;
-  const int sx = s % sup_x, sy = s / sup_x;
-  const uint2 r = sup_ranges[s];
+  const uint2 r = sup_ranges[blockIdx.x];
   const int n = (int)(r.y - r.x);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // tiles of this super-tile that exist in the image
-  const int tx0 = sx * LX, ty0 = sy * LY;
-  if (tid < L) s_run[tid] = 0;
-  const unsigned long long* sorted = nullptr;
-  if (n > 0) {
-    if (n <= kSortCap / 2)
-      sorted = block_merge_sort(sup_keys + r.x, n, buf, buf + kSortCap / 2);
-    else
-      sorted = large_sort(sup_keys + r.x, sup_tmp + r.x, n, buf, buf + kSortCap / 2);
-  }
+  if (n <= 0) return;
+  const unsigned long long* sorted;
+  if (n <= kSortCap / 2)
+    sorted = block_merge_sort(sup_keys + r.x, n, buf, buf + kSortCap / 2);
+  else
+    sorted = large_sort(sup_keys + r.x, sup_tmp + r.x, n, buf, buf + kSortCap / 2);
   __syncthreads();
-  const size_t region = (size_t)L * r.x;
-  for (int c0 = 0; c0 < n; c0 += kSortThreads) {
-    const int k = c0 + tid;
-    uint32_t bits = 0;
-    unsigned long long key = 0;
-    if (k < n) {
-      key = sorted[k];
-      const uint32_t gi = (uint32_t)key;
-      const float4 a = rec[4 * (size_t)gi], c = rec[4 * (size_t)gi + 2], e = rec[4 * (size_t)gi + 3];
-      int x0, x1, y0, y1;
-      if (record_rect(a.x, a.y, c.w, e.x, W, H, x0, x1, y0, y1)) {
-        const int ax = max(x0 / TW, tx0), bx = min(x1 / TW, tx0 + LX - 1);
-        const int ay = max(y0 / TH, ty0), by = min(y1 / TH, ty0 + LY - 1);
-        for (int ty = ay; ty <= by; ++ty)
-          for (int tx = ax; tx <= bx; ++tx) bits |= 1u << ((ty - ty0) * LX + (tx - tx0));
-      }
-    }
-    uint32_t mine[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-      const uint32_t b = __ballot_sync(0xffffffffu, (bits >> l) & 1u);
-      mine[l] = __popc(b & ((1u << lane) - 1u));
-      if (lane == 0) s_cnt[l][warp] = __popc(b);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-      if ((bits >> l) & 1u) {
-        uint32_t off = s_run[l];
-        for (int w2 = 0; w2 < warp; ++w2) off += s_cnt[l][w2];
-        tile_keys[region + (size_t)l * n + off + mine[l]] = key;
-      }
-    }
-    __syncthreads();
-    if (tid < L) {
-      uint32_t tot = 0;
-      for (int w2 = 0; w2 < NW; ++w2) tot += s_cnt[tid][w2];
-      s_run[tid] += tot;
-    }
-    __syncthreads();
-  }
-  if (tid < L) {
-    const int tx = tx0 + tid % LX, ty = ty0 + tid / LX;
-    if (tx < tiles_x && ty < tiles_y) {
-      const uint32_t start = (uint32_t)(region + (size_t)tid * n);
-      tile_ranges[ty * tiles_x + tx] = make_uint2(start, start + s_run[tid]);
-    }
+  for (int k = threadIdx.x; k < n; k += kSortThreads) {
+    const unsigned long long key = sorted[k];
+    const uint32_t gi = (uint32_t)key;
+    const float4 a = rec[4 * (size_t)gi], c = rec[4 * (size_t)gi + 2], e = rec[4 * (size_t)gi + 3];
+    int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+    record_rect(a.x, a.y, c.w, e.x, W, H, x0, x1, y0, y1);
+    sup_rect[r.x + k] = pack_rect(x0, x1, y0, y1);
+    if (sorted != sup_keys + r.x) sup_keys[r.x + k] = key;
   }
 }
 
+// One CTA per tile: the tile's list is its super-tile's sorted segment
+// filtered, in order, by rectangle overlap.  Tile l of super-tile s owns
+// tile_keys[L * start_s + l * n_s ...] (never longer than the segment).
+template <int TW, int TH>
+__global__ void __launch_bounds__(128) split_tiles_kernel(
+    const uint2* __restrict__ sup_ranges, const unsigned long long* __restrict__ sup_keys,
+    const unsigned long long* __restrict__ sup_rect, int sh, int sup_x, int tiles_x,
+    unsigned long long* __restrict__ tile_keys, uint2* __restrict__ tile_ranges) {
+  const int sp = 1 << sh, LX = sp / TW, LY = sp / TH, L = LX * LY;
+  __shared__ uint32_t s_cnt[4];
+  const int t = blockIdx.x;
+  const int tx = t % tiles_x, ty = t / tiles_x;
+  const int x0 = tx * TW, x1 = x0 + TW - 1, y0 = ty * TH, y1 = y0 + TH - 1;
+  const int s = (y0 >> sh) * sup_x + (x0 >> sh);
+  const int l = ((y0 & (sp - 1)) / TH) * LX + (x0 & (sp - 1)) / TW;
+  const uint2 r = sup_ranges[s];
+  const int n = (int)(r.y - r.x);
+  const size_t base = (size_t)L * r.x + (size_t)l * n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t run = 0;
+  for (int c0 = 0; c0 < n; c0 += 128) {
+    const int k = c0 + tid;
+    bool mem = false;
+    unsigned long long key = 0;
+    if (k < n) {
+      const unsigned long long pr = sup_rect[r.x + k];
+      const int rx0 = (int)(pr & 0xFFFF), rx1 = (int)((pr >> 16) & 0xFFFF);
+      const int ry0 = (int)((pr >> 32) & 0xFFFF), ry1 = (int)(pr >> 48);
+      mem = rx0 <= x1 && rx1 >= x0 && ry0 <= y1 && ry1 >= y0;
+      if (mem) key = sup_keys[r.x + k];
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, mem);
+    if (lane == 0) s_cnt[warp] = __popc(b);
+    __syncthreads();
+    uint32_t off = run;
+    for (int w2 = 0; w2 < warp; ++w2) off += s_cnt[w2];
+    if (mem) tile_keys[base + off + __popc(b & ((1u << lane) - 1u))] = key;
+    run += s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3];
+    __syncthreads();
+  }
+  if (tid == 0) tile_ranges[t] = make_uint2((uint32_t)base, (uint32_t)(base + run));
+}
+
 // ------------------------------------------------------------------ launchers
-cudaError_t launch_bin_histogram(const float4* rec, int M, int W, int H, int sup_x, int nsup,
-                                 uint32_t* sup_count, uint32_t* block_base, cudaStream_t st) {
+cudaError_t launch_bin_histogram(const float4* rec, int M, int W, int H, int sh, int sup_x,
+                                 int nsup, uint32_t* sup_count, uint32_t* block_base,
+                                 cudaStream_t st) {
   bin_histogram_kernel<<<(M + 255) / 256, 256, nsup * sizeof(uint32_t), st>>>(
-      rec, M, W, H, sup_x, nsup, sup_count, block_base);
+      rec, M, W, H, sh, sup_x, nsup, sup_count, block_base);
   return cudaGetLastError();
 }
 
@@ -324,33 +322,34 @@ cudaError_t launch_scan_super(uint32_t* counts, uint2* ranges, int n, long long 
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit_super(const float4* rec, int M, int W, int H, int sup_x, int nsup,
+cudaError_t launch_emit_super(const float4* rec, int M, int W, int H, int sh, int sup_x, int nsup,
                               const uint2* sup_ranges, const uint32_t* block_base,
                               unsigned long long* keys, cudaStream_t st) {
   emit_super_kernel<<<(M + 255) / 256, 256, nsup * sizeof(uint32_t), st>>>(
-      rec, M, W, H, sup_x, nsup, sup_ranges, block_base, keys);
+      rec, M, W, H, sh, sup_x, nsup, sup_ranges, block_base, keys);
   return cudaGetLastError();
 }
 
-template <int TW, int TH>
-static cudaError_t split_tw(const uint2* sup_ranges, int nsup, unsigned long long* sup_keys,
-                            unsigned long long* sup_tmp, const float4* rec, int W, int H,
-                            int sup_x, int tiles_x, int tiles_y, unsigned long long* tile_keys,
-                            uint2* tile_ranges, cudaStream_t st) {
-  sort_split_kernel<TW, TH><<<nsup, kSortThreads, 0, st>>>(
-      sup_ranges, sup_keys, sup_tmp, rec, W, H, sup_x, tiles_x, tiles_y, tile_keys, tile_ranges);
+cudaError_t launch_sort_super(const uint2* sup_ranges, int nsup, unsigned long long* sup_keys,
+                              unsigned long long* sup_tmp, unsigned long long* sup_rect,
+                              const float4* rec, int W, int H, cudaStream_t st) {
+  sort_super_kernel<<<nsup, kSortThreads, 0, st>>>(sup_ranges, sup_keys, sup_tmp, sup_rect, rec, W,
+                                                   H);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_split(int tw, int th, const uint2* sup_ranges, int nsup,
-                              unsigned long long* sup_keys, unsigned long long* sup_tmp,
-                              const float4* rec, int W, int H, int sup_x, int tiles_x,
-                              int tiles_y, unsigned long long* tile_keys, uint2* tile_ranges,
-                              cudaStream_t st) {
-#define GPS_SPLIT(a, b)                                                                      \
-  if (tw == a && th == b)                                                                    \
-    return split_tw<a, b>(sup_ranges, nsup, sup_keys, sup_tmp, rec, W, H, sup_x, tiles_x,    \
-                          tiles_y, tile_keys, tile_ranges, st);
+cudaError_t launch_split_tiles(int tw, int th, const uint2* sup_ranges,
+                               const unsigned long long* sup_keys,
+                               const unsigned long long* sup_rect, int sh, int sup_x, int tiles_x,
+                               int tiles_y, unsigned long long* tile_keys, uint2* tile_ranges,
+                               cudaStream_t st) {
+  const int nt = tiles_x * tiles_y;
+#define GPS_SPLIT(a, b)                                                                       \
+  if (tw == a && th == b) {                                                                   \
+    split_tiles_kernel<a, b><<<nt, 128, 0, st>>>(sup_ranges, sup_keys, sup_rect, sh, sup_x,   \
+                                                  tiles_x, tile_keys, tile_ranges);           \
+    return cudaGetLastError();                                                                \
+  }
   GPS_SPLIT(16, 16)
   GPS_SPLIT(16, 8)
   GPS_SPLIT(8, 8)

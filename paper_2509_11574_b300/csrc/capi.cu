@@ -15,18 +15,20 @@ namespace gps {
 cudaError_t launch_fuse(const GpsTsdf&, const float*, const float*, const Cam&, cudaStream_t);
 cudaError_t launch_raycast(const GpsTsdf&, const Cam&, float, float, float*, float*, float*,
                            cudaStream_t);
-cudaError_t launch_project(const GpsGaussians&, const Cam&, float, float4*, int, int, uint32_t*,
-                           uint32_t*, cudaStream_t);
+cudaError_t launch_project(const GpsGaussians&, const Cam&, float, float4*, int, int, int,
+                           uint32_t*, uint32_t*, cudaStream_t);
 cudaError_t launch_project_backward(const GpsGaussians&, const Cam&, float, const float4*,
                                     const GpsGaussians&, cudaStream_t);
-cudaError_t launch_bin_histogram(const float4*, int, int, int, int, int, uint32_t*, uint32_t*,
-                                 cudaStream_t);
+cudaError_t launch_bin_histogram(const float4*, int, int, int, int, int, int, uint32_t*,
+                                 uint32_t*, cudaStream_t);
 cudaError_t launch_scan_super(uint32_t*, uint2*, int, long long, float*, int*, cudaStream_t);
-cudaError_t launch_emit_super(const float4*, int, int, int, int, int, const uint2*, const uint32_t*,
-                              unsigned long long*, cudaStream_t);
-cudaError_t launch_sort_split(int, int, const uint2*, int, unsigned long long*, unsigned long long*,
-                              const float4*, int, int, int, int, int, unsigned long long*, uint2*,
-                              cudaStream_t);
+cudaError_t launch_emit_super(const float4*, int, int, int, int, int, int, const uint2*,
+                              const uint32_t*, unsigned long long*, cudaStream_t);
+cudaError_t launch_sort_super(const uint2*, int, unsigned long long*, unsigned long long*,
+                              unsigned long long*, const float4*, int, int, cudaStream_t);
+cudaError_t launch_split_tiles(int, int, const uint2*, const unsigned long long*,
+                               const unsigned long long*, int, int, int, int, unsigned long long*,
+                               uint2*, cudaStream_t);
 cudaError_t launch_composite_fwd(const ViewDev&, float, int, int, int, cudaStream_t);
 cudaError_t launch_composite_bwd(const ViewDev&, float, float, const float*, int, int, int, int,
                                  cudaStream_t);
@@ -88,7 +90,8 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
   TileCfg tc;
   if (!tile_cfg(s, tc)) return fail(GPS_ERR_INVALID_ARG, "unsupported tile size %dx%d", s->tile_w, s->tile_h);
   const long long cap = pair_cap(s, M);
-  const int per_super = (kSuperPx / tc.tw) * (kSuperPx / tc.th);
+  const int sh = super_shift_for(tc.tw), sp = 1 << sh;
+  const int per_super = (sp / tc.tw) * (sp / tc.th);
   if (cap <= 0 || cap * per_super > 0xFFFFFFF0LL)
     return fail(GPS_ERR_INVALID_ARG, "pair_capacity out of range");
   const size_t nblocks = ((size_t)M + 255) / 256;
@@ -97,7 +100,7 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     const int W = views[v].K.width, H = views[v].K.height;
     if (W <= 0 || H <= 0) return fail(GPS_ERR_INVALID_ARG, "view %d has size %dx%d", v, W, H);
     const int tx = (W + tc.tw - 1) / tc.tw, ty = (H + tc.th - 1) / tc.th;
-    const int sx = (W + kSuperPx - 1) / kSuperPx, sy = (H + kSuperPx - 1) / kSuperPx;
+    const int sx = (W + sp - 1) / sp, sy = (H + sp - 1) / sp;
     if ((long long)sx * sy > kSuperMax)
       return fail(GPS_ERR_INVALID_ARG, "view %d: image too large (%d super-tiles)", v, sx * sy);
     const size_t ntiles = (size_t)tx * ty, npx = (size_t)W * H, nsup = (size_t)sx * sy;
@@ -109,8 +112,16 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     L.super_ranges = off; off = align256(off + nsup * 8);
     L.super_keys = off; off = align256(off + (size_t)cap * 8);
     L.super_scratch = off; off = align256(off + (size_t)cap * 8);
-    L.tile_ranges = off; off = align256(off + ntiles * 8);
-    L.pair_keys = off; off = align256(off + (size_t)cap * per_super * 8);
+    L.super_rects = off; off = align256(off + (size_t)cap * 8);
+    // with one tile per super-tile the tile lists are the sorted segments
+    // themselves: tile ranges and pair keys alias the super-tile regions
+    if (per_super == 1) {
+      L.tile_ranges = L.super_ranges;
+      L.pair_keys = L.super_keys;
+    } else {
+      L.tile_ranges = off; off = align256(off + ntiles * 8);
+      L.pair_keys = off; off = align256(off + (size_t)cap * per_super * 8);
+    }
     L.pix_state = off; off = align256(off + npx * 32);
     L.tile_partials = off; off = align256(off + ntiles * 16);
     L.view_scalars = off; off = align256(off + 64);
@@ -123,6 +134,7 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     L.tile_h = tc.th;
     L.super_x = sx;
     L.super_y = sy;
+    L.super_px = sp;
     L.pair_capacity = cap;
     if (v == want && out) *out = L;
   }
@@ -178,6 +190,7 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L) {
   v.sup_ranges = reinterpret_cast<uint2*>(ws + L.super_ranges);
   v.sup_keys = reinterpret_cast<unsigned long long*>(ws + L.super_keys);
   v.sup_tmp = reinterpret_cast<unsigned long long*>(ws + L.super_scratch);
+  v.sup_rect = reinterpret_cast<unsigned long long*>(ws + L.super_rects);
   v.tile_ranges = reinterpret_cast<uint2*>(ws + L.tile_ranges);
   v.keys = reinterpret_cast<unsigned long long*>(ws + L.pair_keys);
   const size_t npx = (size_t)vw.K.width * vw.K.height;
@@ -193,6 +206,7 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L) {
   v.th = L.tile_h;
   v.sup_x = L.super_x;
   v.sup_y = L.super_y;
+  v.sup_shift = L.super_px == 32 ? 5 : 4;
   v.cap = L.pair_capacity;
   return v;
 }
@@ -306,23 +320,25 @@ int32_t render_forward(const GpsGaussians* g, const GpsView* views, int32_t n_vi
     if (stages & GPS_STAGE_PROJECT) {
       e = cudaMemsetAsync(v.sup_count, 0, (size_t)nsup * 4, st);
       if (e == cudaSuccess && g->M > 0)
-        e = launch_project(*g, v.cam, s->near_plane, v.rec, v.sup_x, nsup, v.sup_count,
-                           v.block_base, st);
+        e = launch_project(*g, v.cam, s->near_plane, v.rec, v.sup_shift, v.sup_x, nsup,
+                           v.sup_count, v.block_base, st);
     } else if (stages & GPS_STAGE_BIN) {
       e = cudaMemsetAsync(v.sup_count, 0, (size_t)nsup * 4, st);
       if (e == cudaSuccess && g->M > 0)
-        e = launch_bin_histogram(v.rec, g->M, v.cam.W, v.cam.H, v.sup_x, nsup, v.sup_count,
-                                 v.block_base, st);
+        e = launch_bin_histogram(v.rec, g->M, v.cam.W, v.cam.H, v.sup_shift, v.sup_x, nsup,
+                                 v.sup_count, v.block_base, st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_BIN)) {
       e = launch_scan_super(v.sup_count, v.sup_ranges, nsup, v.cap, v.scalars, status, st);
       if (e == cudaSuccess && g->M > 0)
-        e = launch_emit_super(v.rec, g->M, v.cam.W, v.cam.H, v.sup_x, nsup, v.sup_ranges,
-                              v.block_base, v.sup_keys, st);
+        e = launch_emit_super(v.rec, g->M, v.cam.W, v.cam.H, v.sup_shift, v.sup_x, nsup,
+                              v.sup_ranges, v.block_base, v.sup_keys, st);
       if (e == cudaSuccess)
-        e = launch_sort_split(v.tw, v.th, v.sup_ranges, nsup, v.sup_keys, v.sup_tmp, v.rec,
-                              v.cam.W, v.cam.H, v.sup_x, v.tiles_x, v.tiles_y, v.keys,
-                              v.tile_ranges, st);
+        e = launch_sort_super(v.sup_ranges, nsup, v.sup_keys, v.sup_tmp, v.sup_rect, v.rec,
+                              v.cam.W, v.cam.H, st);
+      if (e == cudaSuccess && v.tile_ranges != v.sup_ranges)
+        e = launch_split_tiles(v.tw, v.th, v.sup_ranges, v.sup_keys, v.sup_rect, v.sup_shift,
+                               v.sup_x, v.tiles_x, v.tiles_y, v.keys, v.tile_ranges, st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_COMPOSITE)) {
       if (s->instrument) e = cudaMemsetAsync(v.scalars + 8, 0, 32, st);

@@ -87,6 +87,31 @@ __device__ __forceinline__ float block_max(float v, float* s_tmp) {
   return r;
 }
 
+// Does the support {q <= qmax} of a Gaussian centred at (mx, my) meet the
+// rectangle [x0, x1] x [y0, y1]?  The minimum of the convex quadratic q over
+// the rectangle is 0 if the centre lies inside, else it lies on an edge, at
+// the stationary point of the edge's 1D quadratic clamped to the edge.
+// Conservative (relative 1e-2 and absolute 1e-2 slack over FP32 rounding):
+// used only to skip work, never to decide whether a pixel counts.
+__device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float a, float b, float c,
+                                                   float qmax, float x0, float x1, float y0,
+                                                   float y1) {
+  const float lx = x0 - mx, hx = x1 - mx, ly = y0 - my, hy = y1 - my;
+  if (lx <= 0.f && hx >= 0.f && ly <= 0.f && hy >= 0.f) return true;
+  float qmin = INFINITY;
+  const float ic = 1.0f / c, ia = 1.0f / a;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float dx = e ? hx : lx;
+    const float dy = fminf(fmaxf(-b * dx * ic, ly), hy);
+    qmin = fminf(qmin, a * dx * dx + 2.0f * b * dx * dy + c * dy * dy);
+    const float ey = e ? hy : ly;
+    const float ex = fminf(fmaxf(-b * ey * ia, lx), hx);
+    qmin = fminf(qmin, a * ex * ex + 2.0f * b * ex * ey + c * ey * ey);
+  }
+  return qmin <= qmax * 1.01f + 0.01f;
+}
+
 // ------------------------------------------------------------------ forward
 // Warp w covers the 8 x 4 pixel block (w % (TW/8), w / (TW/8)) of the tile.
 template <int TW>
@@ -166,6 +191,10 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(ViewDev v, float 
           const float2 E = s_e[j];
           stop = A.z >= wthr;
           ok = A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 && A.y - E.y <= by1;
+          if (ok) {
+            const float4 B = s_b[j];
+            ok = ellipse_meets_rect(A.x, A.y, B.x, 0.5f * B.y, B.z, B.w, bx0, bx1, by0, by1);
+          }
         }
         const unsigned sb = __ballot_sync(0xffffffffu, stop);
         unsigned ob = __ballot_sync(0xffffffffu, ok);
@@ -272,40 +301,44 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(ViewDev v, float 
   }
 }
 
-// Per-view loss from the tile partial sums, summed in a fixed order (FP64).
+// Per-view loss from the tile partial sums, summed in a fixed order: each
+// thread adds a strided subset, then a fixed shuffle tree and warp order.
 // scalars: [0] view loss, [1] sum |C* - C|, [2] sum |D* - D|, [3] N_valid.
 // The total over views is accumulated into *loss (view 0 overwrites).
 __global__ void __launch_bounds__(256) finalize_loss_kernel(const float4* __restrict__ partials,
                                                             int ntiles, float lambda_depth,
                                                             float* scalars, float* loss, int first) {
-  __shared__ double s[3][256];
-  double a = 0, b = 0, c = 0;
+  __shared__ float s[3][8];
+  float a = 0.f, b = 0.f, c = 0.f;
   for (int k = threadIdx.x; k < ntiles; k += 256) {
     const float4 p = partials[k];
     a += p.x;
     b += p.y;
     c += p.z;
   }
-  s[0][threadIdx.x] = a;
-  s[1][threadIdx.x] = b;
-  s[2][threadIdx.x] = c;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      s[0][threadIdx.x] += s[0][threadIdx.x + o];
-      s[1][threadIdx.x] += s[1][threadIdx.x + o];
-      s[2][threadIdx.x] += s[2][threadIdx.x + o];
-    }
-    __syncthreads();
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s[0][w] = a;
+    s[1][w] = b;
+    s[2][w] = c;
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const double n = s[2][0];
-    const double L = n > 0 ? s[0][0] / (3.0 * n) + (double)lambda_depth * s[1][0] / n : 0.0;
-    scalars[0] = (float)L;
-    scalars[1] = (float)s[0][0];
-    scalars[2] = (float)s[1][0];
-    scalars[3] = (float)n;
-    if (loss) *loss = first ? (float)L : *loss + (float)L;
+    float sa = 0.f, sb = 0.f, n = 0.f;
+    for (int k = 0; k < 8; ++k) {
+      sa += s[0][k];
+      sb += s[1][k];
+      n += s[2][k];
+    }
+    const float L = n > 0.f ? sa / (3.0f * n) + lambda_depth * sb / n : 0.0f;
+    scalars[0] = L;
+    scalars[1] = sa;
+    scalars[2] = sb;
+    scalars[3] = n;
+    if (loss) *loss = first ? L : *loss + L;
   }
 }
 
@@ -361,7 +394,12 @@ __device__ __forceinline__ void store_grad2d(const ViewDev& v, int deterministic
 }
 
 // ------------------------------------------------------- backward, OIT mode
-constexpr int kBwdBatch = 64;  // list entries staged per round of the OIT backward
+// list entries staged per round of the OIT backward (per-warp partials of
+// NW x NB x 10 floats stay within 20 KB of shared memory)
+template <int NT>
+struct BwdBatch {
+  static constexpr int value = NT >= 256 ? 64 : (NT >= 128 ? 128 : 64);
+};
 
 // OIT backward: warp w owns the same 8 x 4 pixel block as in the forward.  Per
 // staged batch, each warp compacts the Gaussians whose rectangle overlaps its
@@ -375,13 +413,14 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, fl
                                                                    int fused, int deterministic) {
   constexpr int NT = TW * TH;
   constexpr int NW = NT / 32;
-  constexpr int NB = kBwdBatch;
+  constexpr int NB = BwdBatch<NT>::value;
+  constexpr int NMW = NB / 32;  // mask words per warp
   __shared__ float4 s_h[NT];
   __shared__ float2 s_s[NT];
   __shared__ float4 s_a[NB], s_b[NB], s_c[NB];
   __shared__ float2 s_e[NB];
   __shared__ float s_part[NW][NB][10];
-  __shared__ unsigned long long s_mask[NW];
+  __shared__ uint32_t s_mask[NW][NMW];
   __shared__ uint8_t s_list[NW][NB];
   __shared__ float s_tmp[NW];
   const int W = v.cam.W, H = v.cam.H;
@@ -434,7 +473,8 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, fl
     __syncthreads();
     const int nb = (int)min((uint32_t)NB, end - b);
     int cnt = 0;
-    unsigned long long mask = 0;
+    if (lane < NMW) s_mask[warp][lane] = 0u;
+    __syncwarp();
     if (!wdone) {
       for (int j0 = 0; j0 < nb; j0 += 32) {
         const int j = j0 + lane;
@@ -444,20 +484,23 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, fl
           const float2 E = s_e[j];
           stop = A.z >= wthr;
           ok = A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 && A.y - E.y <= by1;
+          if (ok) {
+            const float4 B = s_b[j];
+            ok = ellipse_meets_rect(A.x, A.y, B.x, 0.5f * B.y, B.z, B.w, bx0, bx1, by0, by1);
+          }
         }
         const unsigned sb = __ballot_sync(0xffffffffu, stop);
         unsigned ob = __ballot_sync(0xffffffffu, ok);
         if (sb) ob &= (sb & (0u - sb)) - 1u;
         if ((ob >> lane) & 1u) s_list[warp][cnt + __popc(ob & ((1u << lane) - 1u))] = (uint8_t)j;
         cnt += __popc(ob);
-        mask |= (unsigned long long)ob << j0;
+        if (lane == 0) s_mask[warp][j0 >> 5] = ob;
         if (sb) {
           wdone = true;
           break;
         }
       }
     }
-    if (lane == 0) s_mask[warp] = mask;
     __syncwarp();
     for (int c0 = 0; c0 < cnt; c0 += 32) {
       const int t = c0 + lane;
@@ -484,11 +527,15 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, fl
       float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
       for (int ky = uy0; ky <= uy1; ++ky) {
         const float dy = __fsub_rn(by0 + (float)ky, my);
-        for (int kx = ux0; kx <= ux1; ++kx) {
+        // the dy terms of quad_form, hoisted out of the row (same roundings)
+        const float t1 = __fmul_rn(b2, dy);
+        const float s3 = __fmul_rn(__fmul_rn(cc, dy), dy);
+        float fx = bx0 + (float)ux0;
+        for (int kx = ux0; kx <= ux1; ++kx, fx += 1.0f) {
           const int p = blk + ky * 8 + kx;
           const float2 ss = s_s[p];
-          const float dx = __fsub_rn(bx0 + (float)kx, mx);
-          const float q = quad_form(ca, b2, cc, dx, dy);
+          const float dx = __fsub_rn(fx, mx);
+          const float q = __fmaf_rn(dx, __fmaf_rn(ca, dx, t1), s3);
           if (INSTR) n_tested += has && kx >= kx0 && kx <= kx1 && ky >= ky0 && ky <= ky1;
           if (q <= qmax && d < ss.y) {
             if (INSTR) ++n_counted;
@@ -525,7 +572,7 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, fl
       for (int c = 0; c < 10; ++c) m[c] = 0.f;
       bool any = false;
       for (int w2 = 0; w2 < NW; ++w2) {
-        if ((s_mask[w2] >> t) & 1ull) {
+        if ((s_mask[w2][t >> 5] >> (t & 31)) & 1u) {
           any = true;
 #pragma unroll
           for (int c = 0; c < 10; ++c) m[c] += s_part[w2][t][c];

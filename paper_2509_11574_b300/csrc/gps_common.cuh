@@ -14,8 +14,9 @@ constexpr float kExtRel = 1.0f + 0.0078125f;  // 1 + 2^-7: conservative extent
 constexpr float kExtAbs = 0.0625f;             // 2^-4 px
 constexpr float kAlphaMax = 0.99f;             // Table 7 variant (3DGS clamp)
 constexpr float kTMin = 1e-4f;                 // Table 7 variant termination
-constexpr int kSuperPx = 32;                   // super-tile edge (pixels) of the binning
-constexpr int kSuperShift = 5;
+// Binning super-tiles are 16 x 16 px (32 x 32 px for 32-px-wide tiles):
+// log2 of their edge for a tile width.
+__host__ __device__ constexpr int super_shift_for(int tw) { return tw > 16 ? 5 : 4; }
 
 // grad2d slot names
 enum { G_MX = 0, G_MY, G_CA, G_CB, G_CC, G_SIG, G_R, G_G, G_B, G_D };
@@ -46,6 +47,7 @@ struct ViewDev {
   uint2* sup_ranges;     // [nsup]
   unsigned long long* sup_keys;
   unsigned long long* sup_tmp;
+  unsigned long long* sup_rect;  // pixel rectangle of each sorted entry (4 x u16)
   uint2* tile_ranges;    // [tiles]
   unsigned long long* keys;  // tile lists
   float4* pix_a;  // [npx] (C*.rgb, D*)
@@ -55,7 +57,7 @@ struct ViewDev {
   float4* grad2d;         // [M][3] float4
   float4* pair_grads;     // [cap][3] float4
   int tiles_x, tiles_y, tw, th;
-  int sup_x, sup_y;
+  int sup_x, sup_y, sup_shift;
   long long cap;
 };
 

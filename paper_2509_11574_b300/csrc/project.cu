@@ -102,7 +102,7 @@ __device__ __forceinline__ void project_gaussian(const Params& P, int i, const C
 // K3: records, plus the block's super-tile histogram and range reservation
 // (first half of the binning).  sup_count must be zero on entry.
 __global__ void __launch_bounds__(256) project_kernel(Params P, int M, Cam cam, float near_,
-                                                      float4* __restrict__ rec, int sup_x,
+                                                      float4* __restrict__ rec, int sh, int sup_x,
                                                       int nsup, uint32_t* __restrict__ sup_count,
                                                       uint32_t* __restrict__ block_base) {
   extern __shared__ uint32_t s_hist[];
@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(256) project_kernel(Params P, int M, Cam cam, 
       r[3] = make_float4(o.ey, 0.f, 0.f, 0.f);
       int x0, x1, y0, y1;
       record_rect(o.mx, o.my, o.ex, o.ey, cam.W, cam.H, x0, x1, y0, y1);
-      for (int sy = y0 >> kSuperShift; sy <= (y1 >> kSuperShift); ++sy)
-        for (int sx = x0 >> kSuperShift; sx <= (x1 >> kSuperShift); ++sx)
+      for (int sy = y0 >> sh; sy <= (y1 >> sh); ++sy)
+        for (int sx = x0 >> sh; sx <= (x1 >> sh); ++sx)
           atomicAdd(s_hist + sy * sup_x + sx, 1u);
     }
   }
@@ -241,11 +241,11 @@ __global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, 
 }
 
 cudaError_t launch_project(const GpsGaussians& g, const Cam& cam, float near_, float4* rec,
-                           int sup_x, int nsup, uint32_t* sup_count, uint32_t* block_base,
+                           int sh, int sup_x, int nsup, uint32_t* sup_count, uint32_t* block_base,
                            cudaStream_t st) {
   Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb};
   project_kernel<<<(g.M + 255) / 256, 256, nsup * sizeof(uint32_t), st>>>(
-      P, g.M, cam, near_, rec, sup_x, nsup, sup_count, block_base);
+      P, g.M, cam, near_, rec, sh, sup_x, nsup, sup_count, block_base);
   return cudaGetLastError();
 }
 

@@ -76,11 +76,18 @@ def test_workspace_size_and_layout_host_only(L):
     L0 = gps.gps_workspace_layout(2000, cams, s, 0)
     L1 = gps.gps_workspace_layout(2000, cams, s, 1)
     assert L0.tiles_x == 10 and L0.tiles_y == 8 and L1.tiles_x == 5 and L1.tiles_y == 3
-    assert L0.records < L0.super_keys < L0.pair_keys < L0.grad2d < L1.records
+    # 16 x 16 tiles are whole 16-px super-tiles: the tile lists are the segments
+    assert L0.records < L0.super_keys == L0.pair_keys < L0.grad2d < L1.records
+    assert L0.tile_ranges == L0.super_ranges
     for off in (L0.records, L0.block_base, L0.pair_keys, L0.pix_state, L1.grad2d):
         assert off % 256 == 0
     assert L0.pair_capacity == 16 * 2000
-    assert (L0.super_x, L0.super_y, L1.super_x, L1.super_y) == (5, 4, 3, 2)
+    assert (L0.super_px, L0.super_x, L0.super_y, L1.super_x, L1.super_y) == (16, 10, 8, 5, 3)
+    L8 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(16, 8)), 0)
+    assert L8.super_keys < L8.pair_keys and L8.super_ranges < L8.tile_ranges
+    assert L8.tiles_y == 15
+    L32 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(32, 8)), 0)
+    assert L32.super_px == 32 and (L32.super_x, L32.super_y) == (5, 4)
     s2 = gps.settings(deterministic=True)
     assert gps.gps_workspace_size(2000, cams, s2) > n
     with pytest.raises(gps.GpsError) as e:
