@@ -241,10 +241,12 @@ class GpuPipeline:
         return g
 
 
-def kernels_per_step(mode):
-    # fuse, raycast + per iteration: project, scan, emit, sort, composite, finalize,
+def kernels_per_step(mode, tile):
+    # fuse, raycast + per iteration: project, scan, emit, sort, [split into tiles
+    # unless a tile is a whole 16-px super-tile], composite, finalize,
     # composite_bwd, project_bwd, adam, step counter
-    return 2 + ITERS_PER_FRAME * 10
+    split = 0 if tuple(tile) == (16, 16) else 1
+    return 2 + ITERS_PER_FRAME * (10 + split)
 
 
 def count_evaluations(pipe, k):
@@ -460,7 +462,7 @@ def run_ours(args, rank, world, local):
         "hbm_model": {"bytes_per_iteration": it_bytes, "peak_gbs": hbm,
                       "frac_at_iteration_time": it_bytes / (it_ms * 1e-3) / 1e9 / hbm if it_ms else None},
         "roofline": roofline,
-        "clocks": clk, "gpu_launches": kernels_per_step(args.mode) * K,
+        "clocks": clk, "gpu_launches": kernels_per_step(args.mode, tile) * K,
         "status": status, "last_frame_losses": losses[-3:], "wall_s": wall,
         "gen_s": gen_s, "gpu": props.name,
     }
