@@ -37,33 +37,39 @@ __device__ __forceinline__ bool super_rect(float mx, float my, float ex, float e
 }
 
 // Histogram of caller-provided records (binning stage run on its own; the
-// projection kernel fuses the same histogram).
-__global__ void __launch_bounds__(256) bin_histogram_kernel(const float4* __restrict__ rec, int M,
-                                                            int W, int H, int sh, int sup_x, int nsup,
-                                                            uint32_t* __restrict__ sup_count,
-                                                            uint32_t* __restrict__ block_base) {
+// projection kernel fuses the same histogram).  Block row blockIdx.y: view.
+__global__ void __launch_bounds__(256) bin_histogram_kernel(int M,
+                                                            const __grid_constant__ ViewBatch vb) {
   extern __shared__ uint32_t s_hist[];
+  const ViewDev& v = vb.v[blockIdx.y];
+  const int nsup = v.sup_x * v.sup_y;
   for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_hist[s] = 0;
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < M) {
+    const float4* rec = v.rec;
     const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
     int sx0, sx1, sy0, sy1;
-    if (super_rect(a.x, a.y, c.w, e.x, W, H, sh, sx0, sx1, sy0, sy1))
+    if (super_rect(a.x, a.y, c.w, e.x, v.cam.W, v.cam.H, v.sup_shift, sx0, sx1, sy0, sy1))
       for (int sy = sy0; sy <= sy1; ++sy)
-        for (int sx = sx0; sx <= sx1; ++sx) atomicAdd(s_hist + sy * sup_x + sx, 1u);
+        for (int sx = sx0; sx <= sx1; ++sx) atomicAdd(s_hist + sy * v.sup_x + sx, 1u);
   }
-  reserve_block_ranges(s_hist, nsup, sup_count, block_base);
+  reserve_block_ranges(s_hist, nsup, v.sup_count, v.block_base);
 }
 
 // Exclusive scan of the super-tile counts -> [start, end) (clipped to the
 // capacity; overflow raises GPS_ERR_CAPACITY).  Resets the counts for the next
-// call.  scalars[4] = number of (super-tile, Gaussian) entries.
-__global__ void __launch_bounds__(kScanThreads) scan_super_kernel(uint32_t* __restrict__ counts,
-                                                                  uint2* __restrict__ ranges,
-                                                                  int n, long long cap,
-                                                                  float* scalars, int* status) {
+// call.  scalars[4] = number of (super-tile, Gaussian) entries.  One block
+// per view of the batch.
+__global__ void __launch_bounds__(kScanThreads) scan_super_kernel(const __grid_constant__ ViewBatch vb,
+                                                                  int* status) {
   __shared__ unsigned long long warp_sums[kScanThreads / 32];
+  const ViewDev& v = vb.v[blockIdx.x];
+  uint32_t* __restrict__ counts = v.sup_count;
+  uint2* __restrict__ ranges = v.sup_ranges;
+  const int n = v.sup_x * v.sup_y;
+  const long long cap = v.cap;
+  float* scalars = v.scalars;
   const int tid = threadIdx.x;
   const int per = (n + kScanThreads - 1) / kScanThreads;
   const int b = tid * per, e = min(n, b + per);
@@ -103,12 +109,15 @@ __global__ void __launch_bounds__(kScanThreads) scan_super_kernel(uint32_t* __re
 }
 
 // Emission into the reserved ranges; same block partition as the histogram.
-__global__ void __launch_bounds__(256) emit_super_kernel(const float4* __restrict__ rec, int M,
-                                                         int W, int H, int sh, int sup_x, int nsup,
-                                                         const uint2* __restrict__ sup_ranges,
-                                                         const uint32_t* __restrict__ block_base,
-                                                         unsigned long long* __restrict__ keys) {
+__global__ void __launch_bounds__(256) emit_super_kernel(int M, const __grid_constant__ ViewBatch vb) {
   extern __shared__ uint32_t s_rank[];
+  const ViewDev& v = vb.v[blockIdx.y];
+  const float4* __restrict__ rec = v.rec;
+  const int W = v.cam.W, H = v.cam.H, sh = v.sup_shift, sup_x = v.sup_x;
+  const int nsup = v.sup_x * v.sup_y;
+  const uint2* __restrict__ sup_ranges = v.sup_ranges;
+  const uint32_t* __restrict__ block_base = v.block_base;
+  unsigned long long* __restrict__ keys = v.sup_keys;
   for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_rank[s] = 0;
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -237,21 +246,24 @@ __device__ __forceinline__ unsigned long long pack_rect(int x0, int x1, int y0, 
          ((unsigned long long)(uint16_t)y0 << 32) | ((unsigned long long)(uint16_t)y1 << 48);
 }
 
-// One CTA per super-tile: sort its segment in place and write, beside each
-// sorted key, its Gaussian's pixel rectangle (x0, x1, y0, y1 as 4 x u16).
-__global__ void __launch_bounds__(kSortThreads) sort_super_kernel(
-    const uint2* __restrict__ sup_ranges, unsigned long long* __restrict__ sup_keys,
-    unsigned long long* __restrict__ sup_tmp, unsigned long long* __restrict__ sup_rect,
-    const float4* __restrict__ rec, int W, int H) {
+// One CTA per (view, super-tile): sort its segment in place and write, beside
+// each sorted key, its Gaussian's pixel rectangle (x0, x1, y0, y1 as 4 x u16).
+__global__ void __launch_bounds__(kSortThreads) sort_super_kernel(const __grid_constant__ ViewBatch vb) {
   __shared__ unsigned long long buf[kSortCap];
-  const uint2 r = sup_ranges[blockIdx.x];
+  const int slot = batch_slot(vb.sup_start, vb.n, blockIdx.x);
+  const ViewDev& v = vb.v[vb.order[slot]];
+  unsigned long long* __restrict__ sup_keys = v.sup_keys;
+  unsigned long long* __restrict__ sup_rect = v.sup_rect;
+  const float4* __restrict__ rec = v.rec;
+  const int W = v.cam.W, H = v.cam.H;
+  const uint2 r = v.sup_ranges[blockIdx.x - vb.sup_start[slot]];
   const int n = (int)(r.y - r.x);
   if (n <= 0) return;
   const unsigned long long* sorted;
   if (n <= kSortCap / 2)
     sorted = block_merge_sort(sup_keys + r.x, n, buf, buf + kSortCap / 2);
   else
-    sorted = large_sort(sup_keys + r.x, sup_tmp + r.x, n, buf, buf + kSortCap / 2);
+    sorted = large_sort(sup_keys + r.x, v.sup_tmp + r.x, n, buf, buf + kSortCap / 2);
   __syncthreads();
   for (int k = threadIdx.x; k < n; k += kSortThreads) {
     const unsigned long long key = sorted[k];
@@ -264,17 +276,22 @@ __global__ void __launch_bounds__(kSortThreads) sort_super_kernel(
   }
 }
 
-// One CTA per tile: the tile's list is its super-tile's sorted segment
+// One CTA per (view, tile): the tile's list is its super-tile's sorted segment
 // filtered, in order, by rectangle overlap.  Tile l of super-tile s owns
 // tile_keys[L * start_s + l * n_s ...] (never longer than the segment).
 template <int TW, int TH>
-__global__ void __launch_bounds__(128) split_tiles_kernel(
-    const uint2* __restrict__ sup_ranges, const unsigned long long* __restrict__ sup_keys,
-    const unsigned long long* __restrict__ sup_rect, int sh, int sup_x, int tiles_x,
-    unsigned long long* __restrict__ tile_keys, uint2* __restrict__ tile_ranges) {
+__global__ void __launch_bounds__(128) split_tiles_kernel(const __grid_constant__ ViewBatch vb) {
+  const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
+  const ViewDev& v = vb.v[vb.order[slot]];
+  const uint2* __restrict__ sup_ranges = v.sup_ranges;
+  const unsigned long long* __restrict__ sup_keys = v.sup_keys;
+  const unsigned long long* __restrict__ sup_rect = v.sup_rect;
+  unsigned long long* __restrict__ tile_keys = v.keys;
+  uint2* __restrict__ tile_ranges = v.tile_ranges;
+  const int sh = v.sup_shift, sup_x = v.sup_x, tiles_x = v.tiles_x;
   const int sp = 1 << sh, LX = sp / TW, LY = sp / TH, L = LX * LY;
   __shared__ uint32_t s_cnt[4];
-  const int t = blockIdx.x;
+  const int t = blockIdx.x - vb.tile_start[slot];
   const int tx = t % tiles_x, ty = t / tiles_x;
   const int x0 = tx * TW, x1 = x0 + TW - 1, y0 = ty * TH, y1 = y0 + TH - 1;
   const int s = (y0 >> sh) * sup_x + (x0 >> sh);
@@ -308,47 +325,45 @@ __global__ void __launch_bounds__(128) split_tiles_kernel(
 }
 
 // ------------------------------------------------------------------ launchers
-cudaError_t launch_bin_histogram(const float4* rec, int M, int W, int H, int sh, int sup_x,
-                                 int nsup, uint32_t* sup_count, uint32_t* block_base,
-                                 cudaStream_t st) {
-  bin_histogram_kernel<<<(M + 255) / 256, 256, nsup * sizeof(uint32_t), st>>>(
-      rec, M, W, H, sh, sup_x, nsup, sup_count, block_base);
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_bin_histogram(int M, const ViewBatch& vb, int max_nsup, cudaStream_t st) {
+  const size_t smem = (size_t)max_nsup * sizeof(uint32_t);
+  if (cudaError_t e = allow_smem(bin_histogram_kernel, smem)) return e;
+  bin_histogram_kernel<<<dim3((M + 255) / 256, vb.n), 256, smem, st>>>(M, vb);
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan_super(uint32_t* counts, uint2* ranges, int n, long long cap,
-                              float* scalars, int* status, cudaStream_t st) {
-  scan_super_kernel<<<1, kScanThreads, 0, st>>>(counts, ranges, n, cap, scalars, status);
+cudaError_t launch_scan_super(const ViewBatch& vb, int* status, cudaStream_t st) {
+  scan_super_kernel<<<vb.n, kScanThreads, 0, st>>>(vb, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit_super(const float4* rec, int M, int W, int H, int sh, int sup_x, int nsup,
-                              const uint2* sup_ranges, const uint32_t* block_base,
-                              unsigned long long* keys, cudaStream_t st) {
-  emit_super_kernel<<<(M + 255) / 256, 256, nsup * sizeof(uint32_t), st>>>(
-      rec, M, W, H, sh, sup_x, nsup, sup_ranges, block_base, keys);
+cudaError_t launch_emit_super(int M, const ViewBatch& vb, int max_nsup, cudaStream_t st) {
+  const size_t smem = (size_t)max_nsup * sizeof(uint32_t);
+  if (cudaError_t e = allow_smem(emit_super_kernel, smem)) return e;
+  emit_super_kernel<<<dim3((M + 255) / 256, vb.n), 256, smem, st>>>(M, vb);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_super(const uint2* sup_ranges, int nsup, unsigned long long* sup_keys,
-                              unsigned long long* sup_tmp, unsigned long long* sup_rect,
-                              const float4* rec, int W, int H, cudaStream_t st) {
-  sort_super_kernel<<<nsup, kSortThreads, 0, st>>>(sup_ranges, sup_keys, sup_tmp, sup_rect, rec, W,
-                                                   H);
+cudaError_t launch_sort_super(const ViewBatch& vb, cudaStream_t st) {
+  const int items = vb.sup_start[vb.n];
+  if (items <= 0) return cudaSuccess;
+  sort_super_kernel<<<items, kSortThreads, 0, st>>>(vb);
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_tiles(int tw, int th, const uint2* sup_ranges,
-                               const unsigned long long* sup_keys,
-                               const unsigned long long* sup_rect, int sh, int sup_x, int tiles_x,
-                               int tiles_y, unsigned long long* tile_keys, uint2* tile_ranges,
-                               cudaStream_t st) {
-  const int nt = tiles_x * tiles_y;
-#define GPS_SPLIT(a, b)                                                                       \
-  if (tw == a && th == b) {                                                                   \
-    split_tiles_kernel<a, b><<<nt, 128, 0, st>>>(sup_ranges, sup_keys, sup_rect, sh, sup_x,   \
-                                                  tiles_x, tile_keys, tile_ranges);           \
-    return cudaGetLastError();                                                                \
+cudaError_t launch_split_tiles(int tw, int th, const ViewBatch& vb, cudaStream_t st) {
+  const int items = vb.tile_start[vb.n];
+  if (items <= 0) return cudaSuccess;
+#define GPS_SPLIT(a, b)                                   \
+  if (tw == a && th == b) {                               \
+    split_tiles_kernel<a, b><<<items, 128, 0, st>>>(vb);  \
+    return cudaGetLastError();                            \
   }
   GPS_SPLIT(16, 16)
   GPS_SPLIT(16, 8)

@@ -3,6 +3,7 @@
 // gps_query_status.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -15,25 +16,19 @@ namespace gps {
 cudaError_t launch_fuse(const GpsTsdf&, const float*, const float*, const Cam&, cudaStream_t);
 cudaError_t launch_raycast(const GpsTsdf&, const Cam&, float, float, float*, float*, float*,
                            cudaStream_t);
-cudaError_t launch_project(const GpsGaussians&, const Cam&, float, float4*, int, int, int,
-                           uint32_t*, uint32_t*, cudaStream_t);
-cudaError_t launch_project_backward(const GpsGaussians&, const Cam&, float, const float4*,
+cudaError_t launch_project(const GpsGaussians&, float, const ViewBatch&, int, cudaStream_t);
+cudaError_t launch_project_backward(const GpsGaussians&, float, const ViewBatch&,
                                     const GpsGaussians&, cudaStream_t);
-cudaError_t launch_bin_histogram(const float4*, int, int, int, int, int, int, uint32_t*,
-                                 uint32_t*, cudaStream_t);
-cudaError_t launch_scan_super(uint32_t*, uint2*, int, long long, float*, int*, cudaStream_t);
-cudaError_t launch_emit_super(const float4*, int, int, int, int, int, int, const uint2*,
-                              const uint32_t*, unsigned long long*, cudaStream_t);
-cudaError_t launch_sort_super(const uint2*, int, unsigned long long*, unsigned long long*,
-                              unsigned long long*, const float4*, int, int, cudaStream_t);
-cudaError_t launch_split_tiles(int, int, const uint2*, const unsigned long long*,
-                               const unsigned long long*, int, int, int, int, unsigned long long*,
-                               uint2*, cudaStream_t);
-cudaError_t launch_composite_fwd(const ViewDev&, float, int, int, int, cudaStream_t);
-cudaError_t launch_composite_bwd(const ViewDev&, float, float, const float*, int, int, int, int,
-                                 cudaStream_t);
-cudaError_t launch_finalize_loss(const ViewDev&, float, float*, int, cudaStream_t);
-cudaError_t launch_gather_pair_grads(const ViewDev&, int, cudaStream_t);
+cudaError_t launch_bin_histogram(int, const ViewBatch&, int, cudaStream_t);
+cudaError_t launch_scan_super(const ViewBatch&, int*, cudaStream_t);
+cudaError_t launch_emit_super(int, const ViewBatch&, int, cudaStream_t);
+cudaError_t launch_sort_super(const ViewBatch&, cudaStream_t);
+cudaError_t launch_split_tiles(int, int, const ViewBatch&, cudaStream_t);
+cudaError_t launch_composite_fwd(const ViewBatch&, int, int, float, int, int, int, cudaStream_t);
+cudaError_t launch_composite_bwd(const ViewBatch&, int, int, float, float, const float*, int, int,
+                                 int, cudaStream_t);
+cudaError_t launch_finalize_loss(const ViewBatch&, float, float*, int, cudaStream_t);
+cudaError_t launch_gather_pair_grads(const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_adam(const GpsGaussians&, const GpsGaussians&, const GpsGaussians&,
                         const GpsGaussians&, const GpsAdamHyper&, int, int*, cudaStream_t);
 }  // namespace gps
@@ -184,6 +179,7 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L) {
   v.out_weight = vw.out_weight;
   v.g_rgb = vw.grad_rgb;
   v.g_depth = vw.grad_depth;
+  v.fused = (vw.grad_rgb || vw.grad_depth) ? 0 : 1;
   v.rec = reinterpret_cast<float4*>(ws + L.records);
   v.sup_count = reinterpret_cast<uint32_t*>(ws + L.super_counts);
   v.block_base = reinterpret_cast<uint32_t*>(ws + L.block_base);
@@ -209,6 +205,30 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L) {
   v.sup_shift = L.super_px == 32 ? 5 : 4;
   v.cap = L.pair_capacity;
   return v;
+}
+
+// Views [b0, b0 + kMaxBatch) of a call as one batch: device descriptors,
+// work items ordered largest view first, and the largest super-tile count.
+void make_batch(int M, const GpsView* views, int32_t n_views, const GpsRenderSettings* s,
+                char* base, int b0, ViewBatch& vb, int& max_nsup) {
+  std::memset(&vb, 0, sizeof(vb));
+  vb.n = std::min(kMaxBatch, n_views - b0);
+  max_nsup = 0;
+  int tiles[kMaxBatch];
+  for (int j = 0; j < vb.n; ++j) {
+    GpsWorkspaceLayout L;
+    layout(M, views, n_views, s, b0 + j, &L, nullptr);
+    vb.v[j] = make_view(views[b0 + j], base, L);
+    max_nsup = std::max(max_nsup, vb.v[j].sup_x * vb.v[j].sup_y);
+    tiles[j] = vb.v[j].tiles_x * vb.v[j].tiles_y;
+    vb.order[j] = j;
+  }
+  std::stable_sort(vb.order, vb.order + vb.n, [&](int a, int b) { return tiles[a] > tiles[b]; });
+  for (int k = 0; k < vb.n; ++k) {
+    const ViewDev& v = vb.v[vb.order[k]];
+    vb.tile_start[k + 1] = vb.tile_start[k] + v.tiles_x * v.tiles_y;
+    vb.sup_start[k + 1] = vb.sup_start[k] + v.sup_x * v.sup_y;
+  }
 }
 
 int32_t check_render_args(const GpsGaussians* g, const GpsView* views, int32_t n_views,
@@ -312,41 +332,35 @@ int32_t render_forward(const GpsGaussians* g, const GpsView* views, int32_t n_vi
   int* status = reinterpret_cast<int*>(base);
   cudaError_t e = cudaSuccess;
   if (stages & GPS_STAGE_PROJECT) e = cudaMemsetAsync(status, 0, sizeof(int), st);
-  for (int vi = 0; vi < n_views && e == cudaSuccess; ++vi) {
-    GpsWorkspaceLayout L;
-    layout(g->M, views, n_views, s, vi, &L, nullptr);
-    ViewDev v = make_view(views[vi], base, L);
-    const int nsup = v.sup_x * v.sup_y;
-    if (stages & GPS_STAGE_PROJECT) {
-      e = cudaMemsetAsync(v.sup_count, 0, (size_t)nsup * 4, st);
+  // one launch per stage for up to kMaxBatch views
+  for (int b0 = 0; b0 < n_views && e == cudaSuccess; b0 += kMaxBatch) {
+    ViewBatch vb;
+    int max_nsup = 0;
+    make_batch(g->M, views, n_views, s, base, b0, vb, max_nsup);
+    const ViewDev& v0 = vb.v[0];
+    if (stages & (GPS_STAGE_PROJECT | GPS_STAGE_BIN)) {
+      for (int j = 0; j < vb.n && e == cudaSuccess; ++j)
+        e = cudaMemsetAsync(vb.v[j].sup_count, 0, (size_t)vb.v[j].sup_x * vb.v[j].sup_y * 4, st);
       if (e == cudaSuccess && g->M > 0)
-        e = launch_project(*g, v.cam, s->near_plane, v.rec, v.sup_shift, v.sup_x, nsup,
-                           v.sup_count, v.block_base, st);
-    } else if (stages & GPS_STAGE_BIN) {
-      e = cudaMemsetAsync(v.sup_count, 0, (size_t)nsup * 4, st);
-      if (e == cudaSuccess && g->M > 0)
-        e = launch_bin_histogram(v.rec, g->M, v.cam.W, v.cam.H, v.sup_shift, v.sup_x, nsup,
-                                 v.sup_count, v.block_base, st);
+        e = (stages & GPS_STAGE_PROJECT) ? launch_project(*g, s->near_plane, vb, max_nsup, st)
+                                         : launch_bin_histogram(g->M, vb, max_nsup, st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_BIN)) {
-      e = launch_scan_super(v.sup_count, v.sup_ranges, nsup, v.cap, v.scalars, status, st);
-      if (e == cudaSuccess && g->M > 0)
-        e = launch_emit_super(v.rec, g->M, v.cam.W, v.cam.H, v.sup_shift, v.sup_x, nsup,
-                              v.sup_ranges, v.block_base, v.sup_keys, st);
-      if (e == cudaSuccess)
-        e = launch_sort_super(v.sup_ranges, nsup, v.sup_keys, v.sup_tmp, v.sup_rect, v.rec,
-                              v.cam.W, v.cam.H, st);
-      if (e == cudaSuccess && v.tile_ranges != v.sup_ranges)
-        e = launch_split_tiles(v.tw, v.th, v.sup_ranges, v.sup_keys, v.sup_rect, v.sup_shift,
-                               v.sup_x, v.tiles_x, v.tiles_y, v.keys, v.tile_ranges, st);
+      e = launch_scan_super(vb, status, st);
+      if (e == cudaSuccess && g->M > 0) e = launch_emit_super(g->M, vb, max_nsup, st);
+      if (e == cudaSuccess) e = launch_sort_super(vb, st);
+      // tiles that are whole super-tiles read the sorted segments directly
+      if (e == cudaSuccess && v0.tile_ranges != v0.sup_ranges)
+        e = launch_split_tiles(v0.tw, v0.th, vb, st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_COMPOSITE)) {
-      if (s->instrument) e = cudaMemsetAsync(v.scalars + 8, 0, 32, st);
+      for (int j = 0; j < vb.n && e == cudaSuccess && s->instrument; ++j)
+        e = cudaMemsetAsync(vb.v[j].scalars + 8, 0, 32, st);
       if (e == cudaSuccess)
-        e = launch_composite_fwd(v, s->eps_depth, s->blend_mode, has_tgt ? 1 : 0,
+        e = launch_composite_fwd(vb, v0.tw, v0.th, s->eps_depth, s->blend_mode, has_tgt ? 1 : 0,
                                  s->instrument ? 1 : 0, st);
       if (e == cudaSuccess && has_tgt)
-        e = launch_finalize_loss(v, s->lambda_depth, loss, vi == 0 ? 1 : 0, st);
+        e = launch_finalize_loss(vb, s->lambda_depth, loss, b0 == 0 ? 1 : 0, st);
     }
   }
   if (e == cudaSuccess && !has_tgt && loss) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
@@ -359,28 +373,29 @@ int32_t render_backward(const GpsGaussians* g, const GpsView* views, int32_t n_v
   if (int32_t e = check_render_args(g, views, n_views, s, ws, ws_bytes)) return e;
   if (int32_t e = check_gaussians(grads, "grads")) return e;
   if (grads->M != g->M) return fail(GPS_ERR_INVALID_ARG, "grads.M != gaussians.M");
+  for (int vi = 0; vi < n_views; ++vi) {
+    const GpsView& vw = views[vi];
+    if (!vw.grad_rgb && !vw.grad_depth && (!vw.target_rgb || !vw.target_depth))
+      return fail(GPS_ERR_INVALID_ARG, "view %d: no upstream gradients and no targets", vi);
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int stages = s->stages ? s->stages : 0x1f;
   char* base = static_cast<char*>(ws);
   cudaError_t e = cudaSuccess;
-  for (int vi = 0; vi < n_views && e == cudaSuccess; ++vi) {
-    const GpsView& vw = views[vi];
-    const bool explicit_grads = vw.grad_rgb || vw.grad_depth;
-    const bool fused = !explicit_grads;
-    if (fused && (!vw.target_rgb || !vw.target_depth))
-      return fail(GPS_ERR_INVALID_ARG, "view %d: no upstream gradients and no targets", vi);
-    GpsWorkspaceLayout L;
-    layout(g->M, views, n_views, s, vi, &L, nullptr);
-    ViewDev v = make_view(vw, base, L);
+  for (int b0 = 0; b0 < n_views && e == cudaSuccess; b0 += kMaxBatch) {
+    ViewBatch vb;
+    int max_nsup = 0;
+    make_batch(g->M, views, n_views, s, base, b0, vb, max_nsup);
     if (stages & GPS_STAGE_COMPOSITE_BWD) {
-      if (!s->deterministic) e = cudaMemsetAsync(v.grad2d, 0, (size_t)g->M * 48, st);
+      for (int j = 0; j < vb.n && e == cudaSuccess && !s->deterministic; ++j)
+        e = cudaMemsetAsync(vb.v[j].grad2d, 0, (size_t)g->M * 48, st);
       if (e == cudaSuccess)
-        e = launch_composite_bwd(v, s->eps_depth, s->lambda_depth, dloss, s->blend_mode,
-                                 fused ? 1 : 0, s->deterministic ? 1 : 0, s->instrument ? 1 : 0, st);
-      if (e == cudaSuccess && s->deterministic && g->M > 0) e = launch_gather_pair_grads(v, g->M, st);
+        e = launch_composite_bwd(vb, vb.v[0].tw, vb.v[0].th, s->eps_depth, s->lambda_depth, dloss,
+                                 s->blend_mode, s->deterministic ? 1 : 0, s->instrument ? 1 : 0, st);
+      if (e == cudaSuccess && s->deterministic && g->M > 0) e = launch_gather_pair_grads(vb, g->M, st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_PROJECT_BWD) && g->M > 0)
-      e = launch_project_backward(*g, v.cam, s->near_plane, v.grad2d, *grads, st);
+      e = launch_project_backward(*g, s->near_plane, vb, *grads, st);
   }
   return e == cudaSuccess ? GPS_OK : cuda_fail(e, "render_backward");
 }

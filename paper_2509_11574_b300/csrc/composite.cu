@@ -124,15 +124,18 @@ __device__ __forceinline__ void warp_block(int warp, int lane, int& ox, int& oy,
 }
 
 template <int TW, int TH, int MODE, bool INSTR>
-__global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(ViewDev v, float eps, int has_tgt) {
+__global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_constant__ ViewBatch vb,
+                                                              float eps, int has_tgt) {
   constexpr int NT = TW * TH;
   constexpr int NW = NT / 32;
   __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
   __shared__ float2 s_e[NT];
   __shared__ uint8_t s_list[NW][NT];
   __shared__ float s_tmp[NW * 3];
+  const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
+  const ViewDev& v = vb.v[vb.order[slot]];
+  const int tile = blockIdx.x - vb.tile_start[slot];
   const int W = v.cam.W, H = v.cam.H;
-  const int tile = blockIdx.x;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int ox, oy, lx, ly;
@@ -304,42 +307,50 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(ViewDev v, float 
 // Per-view loss from the tile partial sums, summed in a fixed order: each
 // thread adds a strided subset, then a fixed shuffle tree and warp order.
 // scalars: [0] view loss, [1] sum |C* - C|, [2] sum |D* - D|, [3] N_valid.
-// The total over views is accumulated into *loss (view 0 overwrites).
-__global__ void __launch_bounds__(256) finalize_loss_kernel(const float4* __restrict__ partials,
-                                                            int ntiles, float lambda_depth,
-                                                            float* scalars, float* loss, int first) {
+// The views' losses are summed in view order into *loss (overwritten when
+// `first`, else added).
+__global__ void __launch_bounds__(256) finalize_loss_kernel(const __grid_constant__ ViewBatch vb,
+                                                            float lambda_depth, float* loss,
+                                                            int first) {
   __shared__ float s[3][8];
-  float a = 0.f, b = 0.f, c = 0.f;
-  for (int k = threadIdx.x; k < ntiles; k += 256) {
-    const float4 p = partials[k];
-    a += p.x;
-    b += p.y;
-    c += p.z;
-  }
-  a = warp_sum(a);
-  b = warp_sum(b);
-  c = warp_sum(c);
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    s[0][w] = a;
-    s[1][w] = b;
-    s[2][w] = c;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float sa = 0.f, sb = 0.f, n = 0.f;
-    for (int k = 0; k < 8; ++k) {
-      sa += s[0][k];
-      sb += s[1][k];
-      n += s[2][k];
+  float total = 0.f;
+  for (int k = 0; k < vb.n; ++k) {
+    const ViewDev& v = vb.v[k];
+    const int ntiles = v.tiles_x * v.tiles_y;
+    float a = 0.f, b = 0.f, c = 0.f;
+    for (int t = threadIdx.x; t < ntiles; t += 256) {
+      const float4 p = v.tile_partials[t];
+      a += p.x;
+      b += p.y;
+      c += p.z;
     }
-    const float L = n > 0.f ? sa / (3.0f * n) + lambda_depth * sb / n : 0.0f;
-    scalars[0] = L;
-    scalars[1] = sa;
-    scalars[2] = sb;
-    scalars[3] = n;
-    if (loss) *loss = first ? L : *loss + L;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      s[0][w] = a;
+      s[1][w] = b;
+      s[2][w] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float sa = 0.f, sb = 0.f, n = 0.f;
+      for (int q = 0; q < 8; ++q) {
+        sa += s[0][q];
+        sb += s[1][q];
+        n += s[2][q];
+      }
+      const float L = n > 0.f ? sa / (3.0f * n) + lambda_depth * sb / n : 0.0f;
+      v.scalars[0] = L;
+      v.scalars[1] = sa;
+      v.scalars[2] = sb;
+      v.scalars[3] = n;
+      total = k == 0 ? L : total + L;
+    }
   }
+  if (threadIdx.x == 0 && loss) *loss = first ? total : *loss + total;
 }
 
 // Upstream gradient of one pixel (already scaled).
@@ -408,9 +419,10 @@ struct BwdBatch {
 // 10 moments privately.  Per-warp partials are summed over warps in a fixed
 // order and turned into the 2D gradient of the (tile, Gaussian) pair.
 template <int TW, int TH, bool INSTR>
-__global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, float eps,
-                                                                   float lambda, const float* dloss,
-                                                                   int fused, int deterministic) {
+__global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_constant__ ViewBatch vb,
+                                                                   float eps, float lambda,
+                                                                   const float* dloss,
+                                                                   int deterministic) {
   constexpr int NT = TW * TH;
   constexpr int NW = NT / 32;
   constexpr int NB = BwdBatch<NT>::value;
@@ -423,8 +435,11 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, fl
   __shared__ uint32_t s_mask[NW][NMW];
   __shared__ uint8_t s_list[NW][NB];
   __shared__ float s_tmp[NW];
+  const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
+  const ViewDev& v = vb.v[vb.order[slot]];
+  const int tile = blockIdx.x - vb.tile_start[slot];
+  const int fused = v.fused;
   const int W = v.cam.W, H = v.cam.H;
-  const int tile = blockIdx.x;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int ox, oy, lx, ly;
@@ -602,9 +617,9 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(ViewDev v, fl
 constexpr int kAlphaBatch = 32;
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(ViewDev v, float eps,
-                                                                     float lambda,
-                                                                     const float* dloss, int fused,
+__global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __grid_constant__ ViewBatch vb,
+                                                                     float eps, float lambda,
+                                                                     const float* dloss,
                                                                      int deterministic) {
   constexpr int NT = TW * TH;
   constexpr int NW = NT / 32;
@@ -612,8 +627,11 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(ViewDev v, 
   __shared__ float s_part[NW][kAlphaBatch][10];
   __shared__ float s_tmp[NW];
   __shared__ uint32_t s_gi[kAlphaBatch];
+  const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
+  const ViewDev& v = vb.v[vb.order[slot]];
+  const int tile = blockIdx.x - vb.tile_start[slot];
+  const int fused = v.fused;
   const int W = v.cam.W, H = v.cam.H;
-  const int tile = blockIdx.x;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
@@ -729,7 +747,10 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(ViewDev v, 
 }
 
 // Deterministic mode: per Gaussian, sum its pair slots in row-major tile order.
-__global__ void __launch_bounds__(256) gather_pair_grads_kernel(ViewDev v, int M) {
+// Block row blockIdx.y: view.
+__global__ void __launch_bounds__(256) gather_pair_grads_kernel(const __grid_constant__ ViewBatch vb,
+                                                                int M) {
+  const ViewDev& v = vb.v[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const float4 A = v.rec[4 * (size_t)i], C = v.rec[4 * (size_t)i + 2], E = v.rec[4 * (size_t)i + 3];
@@ -763,65 +784,65 @@ __global__ void __launch_bounds__(256) gather_pair_grads_kernel(ViewDev v, int M
 
 // ------------------------------------------------------------------ launchers
 template <int TW, int TH>
-static cudaError_t fwd_tw(const ViewDev& v, float eps, int mode, int has_tgt, int instr,
+static cudaError_t fwd_tw(const ViewBatch& vb, float eps, int mode, int has_tgt, int instr,
                           cudaStream_t st) {
-  const int ntiles = v.tiles_x * v.tiles_y;
+  const int items = vb.tile_start[vb.n];
+  if (items <= 0) return cudaSuccess;
   if (mode == GPS_BLEND_OIT) {
     if (instr)
-      composite_fwd_kernel<TW, TH, GPS_BLEND_OIT, true><<<ntiles, TW * TH, 0, st>>>(v, eps, has_tgt);
+      composite_fwd_kernel<TW, TH, GPS_BLEND_OIT, true><<<items, TW * TH, 0, st>>>(vb, eps, has_tgt);
     else
-      composite_fwd_kernel<TW, TH, GPS_BLEND_OIT, false><<<ntiles, TW * TH, 0, st>>>(v, eps, has_tgt);
+      composite_fwd_kernel<TW, TH, GPS_BLEND_OIT, false><<<items, TW * TH, 0, st>>>(vb, eps, has_tgt);
   } else {
     if (instr)
-      composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, true><<<ntiles, TW * TH, 0, st>>>(v, eps, has_tgt);
+      composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, true><<<items, TW * TH, 0, st>>>(vb, eps, has_tgt);
     else
-      composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, false><<<ntiles, TW * TH, 0, st>>>(v, eps, has_tgt);
+      composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, false><<<items, TW * TH, 0, st>>>(vb, eps, has_tgt);
   }
   return cudaGetLastError();
 }
 
 template <int TW, int TH>
-static cudaError_t bwd_tw(const ViewDev& v, float eps, float lambda, const float* dloss, int mode,
-                          int fused, int det, int instr, cudaStream_t st) {
-  const int ntiles = v.tiles_x * v.tiles_y;
+static cudaError_t bwd_tw(const ViewBatch& vb, float eps, float lambda, const float* dloss, int mode,
+                          int det, int instr, cudaStream_t st) {
+  const int items = vb.tile_start[vb.n];
+  if (items <= 0) return cudaSuccess;
   if (mode == GPS_BLEND_OIT) {
     if (instr)
-      composite_bwd_oit_kernel<TW, TH, true><<<ntiles, TW * TH, 0, st>>>(v, eps, lambda, dloss, fused, det);
+      composite_bwd_oit_kernel<TW, TH, true><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss, det);
     else
-      composite_bwd_oit_kernel<TW, TH, false><<<ntiles, TW * TH, 0, st>>>(v, eps, lambda, dloss, fused, det);
+      composite_bwd_oit_kernel<TW, TH, false><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss, det);
   } else
-    composite_bwd_alpha_kernel<TW, TH><<<ntiles, TW * TH, 0, st>>>(v, eps, lambda, dloss, fused,
-                                                                   det);
+    composite_bwd_alpha_kernel<TW, TH><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss, det);
   return cudaGetLastError();
 }
 
-cudaError_t launch_composite_fwd(const ViewDev& v, float eps, int mode, int has_tgt, int instr,
-                                 cudaStream_t st) {
-  if (v.tw == 16 && v.th == 16) return fwd_tw<16, 16>(v, eps, mode, has_tgt, instr, st);
-  if (v.tw == 16 && v.th == 8) return fwd_tw<16, 8>(v, eps, mode, has_tgt, instr, st);
-  if (v.tw == 8 && v.th == 8) return fwd_tw<8, 8>(v, eps, mode, has_tgt, instr, st);
-  if (v.tw == 32 && v.th == 8) return fwd_tw<32, 8>(v, eps, mode, has_tgt, instr, st);
+cudaError_t launch_composite_fwd(const ViewBatch& vb, int tw, int th, float eps, int mode,
+                                 int has_tgt, int instr, cudaStream_t st) {
+  if (tw == 16 && th == 16) return fwd_tw<16, 16>(vb, eps, mode, has_tgt, instr, st);
+  if (tw == 16 && th == 8) return fwd_tw<16, 8>(vb, eps, mode, has_tgt, instr, st);
+  if (tw == 8 && th == 8) return fwd_tw<8, 8>(vb, eps, mode, has_tgt, instr, st);
+  if (tw == 32 && th == 8) return fwd_tw<32, 8>(vb, eps, mode, has_tgt, instr, st);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_composite_bwd(const ViewDev& v, float eps, float lambda, const float* dloss,
-                                 int mode, int fused, int det, int instr, cudaStream_t st) {
-  if (v.tw == 16 && v.th == 16) return bwd_tw<16, 16>(v, eps, lambda, dloss, mode, fused, det, instr, st);
-  if (v.tw == 16 && v.th == 8) return bwd_tw<16, 8>(v, eps, lambda, dloss, mode, fused, det, instr, st);
-  if (v.tw == 8 && v.th == 8) return bwd_tw<8, 8>(v, eps, lambda, dloss, mode, fused, det, instr, st);
-  if (v.tw == 32 && v.th == 8) return bwd_tw<32, 8>(v, eps, lambda, dloss, mode, fused, det, instr, st);
+cudaError_t launch_composite_bwd(const ViewBatch& vb, int tw, int th, float eps, float lambda,
+                                 const float* dloss, int mode, int det, int instr, cudaStream_t st) {
+  if (tw == 16 && th == 16) return bwd_tw<16, 16>(vb, eps, lambda, dloss, mode, det, instr, st);
+  if (tw == 16 && th == 8) return bwd_tw<16, 8>(vb, eps, lambda, dloss, mode, det, instr, st);
+  if (tw == 8 && th == 8) return bwd_tw<8, 8>(vb, eps, lambda, dloss, mode, det, instr, st);
+  if (tw == 32 && th == 8) return bwd_tw<32, 8>(vb, eps, lambda, dloss, mode, det, instr, st);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_finalize_loss(const ViewDev& v, float lambda, float* loss, int first,
+cudaError_t launch_finalize_loss(const ViewBatch& vb, float lambda, float* loss, int first,
                                  cudaStream_t st) {
-  finalize_loss_kernel<<<1, 256, 0, st>>>(v.tile_partials, v.tiles_x * v.tiles_y, lambda, v.scalars,
-                                          loss, first);
+  finalize_loss_kernel<<<1, 256, 0, st>>>(vb, lambda, loss, first);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_pair_grads(const ViewDev& v, int M, cudaStream_t st) {
-  gather_pair_grads_kernel<<<(M + 255) / 256, 256, 0, st>>>(v, M);
+cudaError_t launch_gather_pair_grads(const ViewBatch& vb, int M, cudaStream_t st) {
+  gather_pair_grads_kernel<<<dim3((M + 255) / 256, vb.n), 256, 0, st>>>(vb, M);
   return cudaGetLastError();
 }
 

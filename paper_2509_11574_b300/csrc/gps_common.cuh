@@ -58,8 +58,31 @@ struct ViewDev {
   float4* pair_grads;     // [cap][3] float4
   int tiles_x, tiles_y, tw, th;
   int sup_x, sup_y, sup_shift;
+  int fused;  // backward: upstream gradients from the fused L1 loss (1) or g_rgb/g_depth (0)
   long long cap;
 };
+
+// Views rendered by one launch per stage.  Work items of the per-tile and
+// per-super-tile kernels are numbered view after view in `order` (largest
+// views first, so that the small views' tiles fill the tail of the grid);
+// view order[k] owns items [tile_start[k], tile_start[k + 1]).  Passed to the
+// kernels by value as a __grid_constant__ parameter (about 2.6 KB).
+constexpr int kMaxBatch = 8;
+struct ViewBatch {
+  int n;
+  int order[kMaxBatch];
+  int tile_start[kMaxBatch + 1];
+  int sup_start[kMaxBatch + 1];
+  ViewDev v[kMaxBatch];
+};
+
+// Position k in `order` of the view owning work item `item` (n <= kMaxBatch).
+__device__ __forceinline__ int batch_slot(const int* start, int n, int item) {
+  int k = 0;
+#pragma unroll 1
+  while (k + 1 < n && item >= start[k + 1]) ++k;
+  return k;
+}
 
 // Pixel rectangle of a record, clipped to the image: [x0, x1] x [y0, y1].
 // Float arithmetic spelled out so that the oracle can reproduce it bit for bit.

@@ -100,19 +100,21 @@ __device__ __forceinline__ void project_gaussian(const Params& P, int i, const C
 }
 
 // K3: records, plus the block's super-tile histogram and range reservation
-// (first half of the binning).  sup_count must be zero on entry.
-__global__ void __launch_bounds__(256) project_kernel(Params P, int M, Cam cam, float near_,
-                                                      float4* __restrict__ rec, int sh, int sup_x,
-                                                      int nsup, uint32_t* __restrict__ sup_count,
-                                                      uint32_t* __restrict__ block_base) {
+// (first half of the binning).  Block row blockIdx.y projects for view
+// blockIdx.y of the batch.  sup_count must be zero on entry.
+__global__ void __launch_bounds__(256) project_kernel(Params P, int M, float near_,
+                                                      const __grid_constant__ ViewBatch vb) {
   extern __shared__ uint32_t s_hist[];
+  const ViewDev& v = vb.v[blockIdx.y];
+  const int sh = v.sup_shift, sup_x = v.sup_x, nsup = v.sup_x * v.sup_y;
   for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_hist[s] = 0;
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < M) {
+    const Cam cam = v.cam;
     ProjState o;
     project_gaussian(P, i, cam, near_, o);
-    float4* r = rec + 4 * (size_t)i;
+    float4* r = v.rec + 4 * (size_t)i;
     if (!o.vis) {
       r[0] = make_float4(0.f, 0.f, 0.f, 0.f);
       r[1] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -131,27 +133,26 @@ __global__ void __launch_bounds__(256) project_kernel(Params P, int M, Cam cam, 
           atomicAdd(s_hist + sy * sup_x + sx, 1u);
     }
   }
-  reserve_block_ranges(s_hist, nsup, sup_count, block_base);
+  reserve_block_ranges(s_hist, nsup, v.sup_count, v.block_base);
 }
 
-// K8: adjoint of the projection.  g2 holds this view's per-Gaussian 2D
-// gradients (already scaled); the parameter gradients are accumulated (+=).
-__global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, Cam cam,
-                                                               float near_,
-                                                               const float4* __restrict__ g2,
-                                                               GpsGaussians grads) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  ProjState o;
-  project_gaussian(P, i, cam, near_, o);
-  if (!o.vis) return;
-  const float4 ga = g2[3 * (size_t)i], gb = g2[3 * (size_t)i + 1], gc = g2[3 * (size_t)i + 2];
+// Parameter gradients of one Gaussian, summed over the views of a batch.
+struct ParamGrad {
+  float mean[3], ls[3], q[4], logit, rgb[3];
+};
+
+// K8 for one view: the adjoint of the projection of Gaussian i,
+// given its 2D gradient (d/d(mx, my, conic_a, conic_b, conic_c, sigma, r, g,
+// b, d), already scaled) and the forward state o of the same view; the
+// result is added to `acc`.
+__device__ __forceinline__ void project_adjoint(const ProjState& o, const Cam& cam, float4 ga,
+                                                float4 gb, float4 gc, ParamGrad& acc) {
   const float g_mx = ga.x, g_my = ga.y, g_ca = ga.z, g_cb = ga.w, g_cc = gb.x, g_sig = gb.y;
   const float g_r = gb.z, g_g = gb.w, g_b = gc.x, g_d = gc.y;
-  grads.rgb[3 * (size_t)i + 0] += g_r;
-  grads.rgb[3 * (size_t)i + 1] += g_g;
-  grads.rgb[3 * (size_t)i + 2] += g_b;
-  grads.opacity_logits[i] += g_sig * o.sig * (1.0f - o.sig);
+  acc.rgb[0] += g_r;
+  acc.rgb[1] += g_g;
+  acc.rgb[2] += g_b;
+  acc.logit += g_sig * o.sig * (1.0f - o.sig);
   // conic = inverse(Sigma2): dS2 = -C Gs C, Gs = [[g_ca, g_cb/2], [g_cb/2, g_cc]]
   const float C00 = o.ca, C01 = o.cb, C11 = o.cc;
   const float G00 = g_ca, G01 = 0.5f * g_cb, G11 = g_cc;
@@ -204,13 +205,12 @@ __global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, 
   dtx += g_mx * cam.fx * itz;
   dty += g_my * cam.fy * itz;
   dtz += -g_mx * cam.fx * o.tc[0] * itz2 - g_my * cam.fy * o.tc[1] * itz2 + g_d;
-  float* dm = grads.means + 3 * (size_t)i;
 #pragma unroll
-  for (int r = 0; r < 3; ++r) dm[r] += cam.R[r * 3 + 0] * dtx + cam.R[r * 3 + 1] * dty + cam.R[r * 3 + 2] * dtz;
+  for (int r = 0; r < 3; ++r)
+    acc.mean[r] += cam.R[r * 3 + 0] * dtx + cam.R[r * 3 + 1] * dty + cam.R[r * 3 + 2] * dtz;
   // Sigma = Mg Mg^T, Mg = Rg diag(s): dMg = 2 dSigma Mg; dRg = dMg diag(s); ds_b = sum_a dMg[a][b] Rg[a][b]
   const float* Rg = o.Rg;
   float dRg[9];
-  float* dl = grads.log_scales + 3 * (size_t)i;
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
     float ds = 0.f;
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, 
       dRg[a * 3 + b] = dMg * o.s[b];
       ds += dMg * Rg[a * 3 + b];
     }
-    dl[b] += ds * o.s[b];
+    acc.ls[b] += ds * o.s[b];
   }
   const float w = o.qn[0], x = o.qn[1], y = o.qn[2], z = o.qn[3];
   float dqn[4];
@@ -235,24 +235,62 @@ __global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, 
            dRg[4] * (-4 * z) + dRg[5] * (2 * y) + dRg[6] * (2 * x) + dRg[7] * (2 * y);
   const float dot = w * dqn[0] + x * dqn[1] + y * dqn[2] + z * dqn[3];
   const float iqn = 1.0f / o.qnorm;
-  float* dq = grads.quats + 4 * (size_t)i;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) dq[k] += (dqn[k] - o.qn[k] * dot) * iqn;
+  for (int k = 0; k < 4; ++k) acc.q[k] += (dqn[k] - o.qn[k] * dot) * iqn;
 }
 
-cudaError_t launch_project(const GpsGaussians& g, const Cam& cam, float near_, float4* rec,
-                           int sh, int sup_x, int nsup, uint32_t* sup_count, uint32_t* block_base,
+// K8: adjoint of the projection, summed over the batch's views in view order
+// and accumulated (+=) into the parameter gradients once per Gaussian.
+__global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, float near_,
+                                                               const __grid_constant__ ViewBatch vb,
+                                                               GpsGaussians grads) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  ParamGrad a{};
+  bool any = false;
+  for (int k = 0; k < vb.n; ++k) {
+    const Cam cam = vb.v[k].cam;
+    ProjState o;
+    project_gaussian(P, i, cam, near_, o);
+    if (!o.vis) continue;
+    const float4* g2 = vb.v[k].grad2d + 3 * (size_t)i;
+    project_adjoint(o, cam, g2[0], g2[1], g2[2], a);
+    any = true;
+  }
+  if (!any) return;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    grads.means[3 * (size_t)i + r] += a.mean[r];
+    grads.log_scales[3 * (size_t)i + r] += a.ls[r];
+    grads.rgb[3 * (size_t)i + r] += a.rgb[r];
+  }
+  float4* dq = reinterpret_cast<float4*>(grads.quats) + i;
+  float4 q = *dq;
+  q.x += a.q[0];
+  q.y += a.q[1];
+  q.z += a.q[2];
+  q.w += a.q[3];
+  *dq = q;
+  grads.opacity_logits[i] += a.logit;
+}
+
+cudaError_t launch_project(const GpsGaussians& g, float near_, const ViewBatch& vb, int max_nsup,
                            cudaStream_t st) {
   Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb};
-  project_kernel<<<(g.M + 255) / 256, 256, nsup * sizeof(uint32_t), st>>>(
-      P, g.M, cam, near_, rec, sh, sup_x, nsup, sup_count, block_base);
+  const size_t smem = (size_t)max_nsup * sizeof(uint32_t);
+  if (smem > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  project_kernel<<<dim3((g.M + 255) / 256, vb.n), 256, smem, st>>>(P, g.M, near_, vb);
   return cudaGetLastError();
 }
 
-cudaError_t launch_project_backward(const GpsGaussians& g, const Cam& cam, float near_,
-                                    const float4* g2, const GpsGaussians& grads, cudaStream_t st) {
+cudaError_t launch_project_backward(const GpsGaussians& g, float near_, const ViewBatch& vb,
+                                    const GpsGaussians& grads, cudaStream_t st) {
   Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb};
-  project_backward_kernel<<<(g.M + 255) / 256, 256, 0, st>>>(P, g.M, cam, near_, g2, grads);
+  project_backward_kernel<<<(g.M + 255) / 256, 256, 0, st>>>(P, g.M, near_, vb, grads);
   return cudaGetLastError();
 }
 
