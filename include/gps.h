@@ -59,8 +59,11 @@ extern "C" {
 #define GPS_BLEND_OIT 0   /* Eq. 1-4: order-independent, depth-culled, W_t = 1   */
 #define GPS_BLEND_ALPHA 1 /* Table 7 "with sort": front-to-back alpha over C_t  */
 
-/* storage precision of colour intermediates (transmittance, weights, loss,
-   gradients and Adam moments always accumulate in float32) */
+/* storage type of the colour images: C_t (GpsView.sdf_rgb, raycast_sdf's
+   out_rgb), the observed colour C_k (target_rgb) and C* (out_rgb) are float,
+   IEEE binary16 or bfloat16 [3][H][W].  Values are converted to float on load
+   and rounded to nearest-even on store; depth images, weights, the saved
+   per-pixel state, the loss, all gradients and Adam moments stay float32. */
 #define GPS_PREC_FP32 0
 #define GPS_PREC_FP16 1
 #define GPS_PREC_BF16 2
@@ -120,11 +123,15 @@ typedef struct GpsGaussians {
 typedef struct GpsView {
   GpsIntrinsics K;
   GpsPose T_wc;
-  const float* sdf_rgb;      /* C_t [3][H][W] from raycast_sdf (required)      */
+  const void* sdf_rgb;       /* C_t [3][H][W] from raycast_sdf (required);
+                                element type per settings.precision            */
   const float* sdf_depth;    /* D_t [H][W]    from raycast_sdf (required)      */
-  const float* target_rgb;   /* C_k [3][H][W] observed colour; nullable        */
+  const void* target_rgb;    /* C_k [3][H][W] observed colour; nullable;
+                                element type per settings.precision            */
   const float* target_depth; /* D_k [H][W]    observed depth; nullable         */
-  float* out_rgb;            /* C* [3][H][W]; nullable                          */
+  void* out_rgb;             /* C* [3][H][W]; nullable; element type per
+                                settings.precision (the loss uses C* before
+                                this rounding)                                 */
   float* out_depth;          /* D* [H][W];    nullable                          */
   float* out_weight;         /* W_G [H][W] (ALPHA: 1 - T_end); nullable         */
   const float* grad_rgb;     /* dL/dC* [3][H][W] for render_backward; nullable  */
@@ -136,7 +143,7 @@ typedef struct GpsRenderSettings {
   float lambda_depth;    /* weight of the depth L1 term (0 = colour only)      */
   float near_plane;      /* Gaussians with camera z <= near are culled (0.2)  */
   int32_t blend_mode;    /* GPS_BLEND_*                                        */
-  int32_t precision;     /* GPS_PREC_*                                         */
+  int32_t precision;     /* GPS_PREC_*: element type of the colour images      */
   int32_t tile_w, tile_h;/* 0, 0 = 16 x 16; supported: 16x16, 16x8, 8x8, 32x8 */
   int32_t deterministic; /* 1: fixed-order gradient reduction, no float atomics */
   int32_t stages;        /* GPS_STAGE_* mask, 0 = all                          */
@@ -232,10 +239,12 @@ GPS_API int32_t fuse_frame(GpsTsdf* vol, const float* depth, const float* rgb, c
  * with step max(min(f, 1) trunc, voxel / 2) on the trilinear sdf f; at the first
  * f_a > 0 >= f_b refine by the secant; D_t = camera z of the hit V^g, C_t = the
  * trilinear colour of the 8 neighbouring voxels.  No hit: 0.  Outputs:
- * out_rgb [3][H][W], out_depth [H][W], out_vertex [H][W][3] world (nullable). */
+ * out_rgb [3][H][W] of element type rgb_precision (GPS_PREC_*, rounded to
+ * nearest-even from the float result), out_depth [H][W], out_vertex [H][W][3]
+ * world (nullable). */
 GPS_API int32_t raycast_sdf(const GpsTsdf* vol, const GpsIntrinsics* K, const GpsPose* T_wc,
-                    float near_plane, float far_plane, float* out_rgb, float* out_depth,
-                    float* out_vertex, void* stream);
+                    float near_plane, float far_plane, void* out_rgb, int32_t rgb_precision,
+                    float* out_depth, float* out_vertex, void* stream);
 
 /* Second rendering pass and blend (Eq. 1-4, or Table 7's sorted variant) for
  * n_views views, and, when every view has target_rgb and target_depth, the

@@ -23,6 +23,7 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                       invariance, single-Gaussian closed form
   bin               - brute-force enumeration of tiles + Python sorted()
   adam              - torch.optim.Adam (FP64)
+  quantise          - torch's float16 / bfloat16 casts, tie-to-even hand values
 """
 from __future__ import annotations
 
@@ -46,6 +47,8 @@ G_MX, G_MY, G_CA, G_CB, G_CC, G_SIG, G_R, G_G, G_B, G_D = range(10)
 G_N = 10
 
 OIT, ALPHA = 0, 1
+# storage types of the colour images (the values of the C-ABI's GPS_PREC_*)
+FP32, FP16, BF16 = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -310,3 +313,22 @@ def render_loss_grads(g, cam, Ct, Dt, Ctgt, Dtgt, eps=0.01, lambda_depth=0.0, mo
     grads = project_backward(g, cam, g2, near)
     return dict(L=L, rec=rec, proj_amb=pamb, out=out, dC=dC, dD=dD, n_valid=nv, loss_amb=lamb,
                 g2=g2, grads=grads)
+
+
+def quantise(x, precision: int) -> np.ndarray:
+    """Colour values as stored in the given type, returned as float64: binary32
+    rounding first (the images are float), then IEEE binary16 (numpy's cast
+    rounds to nearest, ties to even) or bfloat16 (the upper half of the
+    binary32 pattern after rounding the lower 16 bits to nearest, ties to
+    even: add 0x7FFF plus the lowest kept bit, then truncate)."""
+    a = np.ascontiguousarray(np.asarray(x, np.float64).astype(np.float32))
+    if precision == FP32:
+        return a.astype(np.float64)
+    if precision == FP16:
+        return a.astype(np.float16).astype(np.float64)
+    if precision == BF16:
+        bits = a.view(np.uint32).astype(np.uint64)
+        keep = (bits >> np.uint64(16)) & np.uint64(1)
+        r = ((bits + np.uint64(0x7FFF) + keep) >> np.uint64(16)) << np.uint64(16)
+        return r.astype(np.uint32).view(np.float32).astype(np.float64)
+    raise ValueError(f"unknown precision {precision}")

@@ -32,6 +32,7 @@ GPS_ERR_CUDA = -4
 GPS_ERR_TIMEOUT = -5
 BLEND_OIT, BLEND_ALPHA = 0, 1
 PREC_FP32, PREC_FP16, PREC_BF16 = 0, 1, 2
+PREC_DTYPE = {PREC_FP32: torch.float32, PREC_FP16: torch.float16, PREC_BF16: torch.bfloat16}
 STAGE_PROJECT, STAGE_BIN, STAGE_COMPOSITE, STAGE_COMPOSITE_BWD, STAGE_PROJECT_BWD = 1, 2, 4, 8, 16
 
 # learning rates of App. C; the RGB colour plays the role of the degree-0 SH
@@ -128,8 +129,8 @@ def lib() -> ctypes.CDLL:
         L.fuse_frame.argtypes = [ctypes.POINTER(GpsTsdf), c_void_p, c_void_p,
                                  ctypes.POINTER(GpsIntrinsics), ctypes.POINTER(GpsPose), c_void_p]
         L.raycast_sdf.argtypes = [ctypes.POINTER(GpsTsdf), ctypes.POINTER(GpsIntrinsics),
-                                  ctypes.POINTER(GpsPose), c_float, c_float, c_void_p, c_void_p,
-                                  c_void_p, c_void_p]
+                                  ctypes.POINTER(GpsPose), c_float, c_float, c_void_p, c_int32,
+                                  c_void_p, c_void_p, c_void_p]
         L.render_forward.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsView), c_int32,
                                      ctypes.POINTER(GpsRenderSettings), c_void_p, c_size_t,
                                      c_void_p, c_void_p]
@@ -283,9 +284,24 @@ class View:
                        _ptr(self.grad_rgb), _ptr(self.grad_depth))
 
 
-def _views(views: Sequence[View]):
+def _views(views: Sequence[View], s: Optional[GpsRenderSettings] = None):
+    if s is not None:
+        want = PREC_DTYPE[s.precision]
+        for k, v in enumerate(views):
+            for name in ("sdf_rgb", "target_rgb", "out_rgb"):
+                t = getattr(v, name)
+                if t is not None and t.dtype != want:
+                    raise ValueError(f"view {k}: {name} is {t.dtype}, settings.precision "
+                                     f"stores colour as {want}")
     arr = (GpsView * len(views))(*[v.c() for v in views])
     return arr
+
+
+def _precision_of(t: torch.Tensor) -> int:
+    for p, dt in PREC_DTYPE.items():
+        if t.dtype == dt:
+            return p
+    raise ValueError(f"colour images are float32, float16 or bfloat16, not {t.dtype}")
 
 
 def _size_views(cams) -> ctypes.Array:
@@ -325,22 +341,27 @@ def fuse_frame(vol: Tsdf, depth: torch.Tensor, rgb: torch.Tensor, cam, stream=No
 
 
 def raycast_sdf(vol: Tsdf, cam, near=0.2, far=0.0, out_rgb=None, out_depth=None,
-                out_vertex=None, stream=None):
+                out_vertex=None, stream=None, precision=PREC_FP32):
+    """C_t, D_t (and the world vertex map) of `cam`.  C_t's element type is
+    that of out_rgb when given, else the one `precision` names."""
     H, W = cam.height, cam.width
     dev = vol.sdf.device
-    out_rgb = out_rgb if out_rgb is not None else torch.empty(3, H, W, device=dev)
+    if out_rgb is None:
+        out_rgb = torch.empty(3, H, W, device=dev, dtype=PREC_DTYPE[precision])
+    prec = _precision_of(out_rgb)
     out_depth = out_depth if out_depth is not None else torch.empty(H, W, device=dev)
     K, P = intrinsics(cam), pose(cam)
     t = vol.c()
     _check(lib().raycast_sdf(ctypes.byref(t), ctypes.byref(K), ctypes.byref(P), near, far,
-                             _ptr(out_rgb), _ptr(out_depth), _ptr(out_vertex), _stream(stream)))
+                             _ptr(out_rgb), prec, _ptr(out_depth), _ptr(out_vertex),
+                             _stream(stream)))
     return out_rgb, out_depth
 
 
 def render_forward(g: Gaussians, views: Sequence[View], s: GpsRenderSettings, ws: torch.Tensor,
                    loss: Optional[torch.Tensor] = None, stream=None) -> None:
     gc = g.c()
-    va = _views(views)
+    va = _views(views, s)
     _check(lib().render_forward(ctypes.byref(gc), va, len(views), ctypes.byref(s), _ptr(ws),
                                 ws.numel(), _ptr(loss), _stream(stream)))
 
@@ -349,7 +370,7 @@ def render_forward_noalloc(g: Gaussians, views: Sequence[View], s: GpsRenderSett
                            loss: Optional[torch.Tensor] = None, stream=None) -> None:
     """render_forward on the library's static device scratch (no workspace)."""
     gc = g.c()
-    va = _views(views)
+    va = _views(views, s)
     _check(lib().render_forward_noalloc(ctypes.byref(gc), va, len(views), ctypes.byref(s),
                                         _ptr(loss), _stream(stream)))
 
@@ -357,7 +378,7 @@ def render_forward_noalloc(g: Gaussians, views: Sequence[View], s: GpsRenderSett
 def render_backward(g: Gaussians, views: Sequence[View], s: GpsRenderSettings, ws: torch.Tensor,
                     grads: Gaussians, dloss: Optional[torch.Tensor] = None, stream=None) -> None:
     gc, gr = g.c(), grads.c()
-    va = _views(views)
+    va = _views(views, s)
     _check(lib().render_backward(ctypes.byref(gc), va, len(views), ctypes.byref(s), _ptr(ws),
                                  ws.numel(), _ptr(dloss), ctypes.byref(gr), _stream(stream)))
 

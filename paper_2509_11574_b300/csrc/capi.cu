@@ -14,7 +14,7 @@
 
 namespace gps {
 cudaError_t launch_fuse(const GpsTsdf&, const float*, const float*, const Cam&, cudaStream_t);
-cudaError_t launch_raycast(const GpsTsdf&, const Cam&, float, float, float*, float*, float*,
+cudaError_t launch_raycast(const GpsTsdf&, const Cam&, float, float, void*, int, float*, float*,
                            cudaStream_t);
 cudaError_t launch_project(const GpsGaussians&, float, const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_project_backward(const GpsGaussians&, float, const ViewBatch&,
@@ -167,7 +167,7 @@ int32_t check_gaussians(const GpsGaussians* g, const char* what) {
   return GPS_OK;
 }
 
-ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L) {
+ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int prec) {
   ViewDev v{};
   v.cam = make_cam(vw.K, vw.T_wc);
   v.Ct = vw.sdf_rgb;
@@ -180,6 +180,7 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L) {
   v.g_rgb = vw.grad_rgb;
   v.g_depth = vw.grad_depth;
   v.fused = (vw.grad_rgb || vw.grad_depth) ? 0 : 1;
+  v.prec = prec;
   v.rec = reinterpret_cast<float4*>(ws + L.records);
   v.sup_count = reinterpret_cast<uint32_t*>(ws + L.super_counts);
   v.block_base = reinterpret_cast<uint32_t*>(ws + L.block_base);
@@ -218,7 +219,7 @@ void make_batch(int M, const GpsView* views, int32_t n_views, const GpsRenderSet
   for (int j = 0; j < vb.n; ++j) {
     GpsWorkspaceLayout L;
     layout(M, views, n_views, s, b0 + j, &L, nullptr);
-    vb.v[j] = make_view(views[b0 + j], base, L);
+    vb.v[j] = make_view(views[b0 + j], base, L, s->precision);
     max_nsup = std::max(max_nsup, vb.v[j].sup_x * vb.v[j].sup_y);
     tiles[j] = vb.v[j].tiles_x * vb.v[j].tiles_y;
     vb.order[j] = j;
@@ -305,9 +306,11 @@ int32_t fuse_frame(GpsTsdf* vol, const float* depth, const float* rgb, const Gps
 }
 
 int32_t raycast_sdf(const GpsTsdf* vol, const GpsIntrinsics* K, const GpsPose* T_wc,
-                    float near_plane, float far_plane, float* out_rgb, float* out_depth,
-                    float* out_vertex, void* stream) {
+                    float near_plane, float far_plane, void* out_rgb, int32_t rgb_precision,
+                    float* out_depth, float* out_vertex, void* stream) {
   if (!vol || !K || !T_wc || !out_rgb || !out_depth) return fail(GPS_ERR_INVALID_ARG, "NULL argument");
+  if (rgb_precision != GPS_PREC_FP32 && rgb_precision != GPS_PREC_FP16 && rgb_precision != GPS_PREC_BF16)
+    return fail(GPS_ERR_INVALID_ARG, "unknown rgb precision %d", rgb_precision);
   if (vol->nx < 8 || vol->ny < 8 || vol->nz < 8 || vol->nx % 8 || vol->ny % 8 || vol->nz % 8)
     return fail(GPS_ERR_INVALID_ARG, "volume dims must be positive multiples of 8");
   if (!vol->sdf || !vol->rgbw || !aligned(vol->rgbw, 16))
@@ -316,7 +319,8 @@ int32_t raycast_sdf(const GpsTsdf* vol, const GpsIntrinsics* K, const GpsPose* T
     return fail(GPS_ERR_INVALID_ARG, "bad voxel / trunc / near / far");
   if (!finite_cam(*K, *T_wc)) return fail(GPS_ERR_INVALID_ARG, "bad intrinsics or pose");
   cudaError_t e = launch_raycast(*vol, make_cam(*K, *T_wc), near_plane, far_plane, out_rgb,
-                                 out_depth, out_vertex, static_cast<cudaStream_t>(stream));
+                                 rgb_precision, out_depth, out_vertex,
+                                 static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GPS_OK : cuda_fail(e, "raycast_sdf");
 }
 

@@ -145,9 +145,9 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
   const long long npx = (long long)W * H, pix = (long long)py * W + px;
   float ct0 = 0.f, ct1 = 0.f, ct2 = 0.f, dt = 0.f;
   if (inside) {
-    ct0 = __ldg(v.Ct + pix);
-    ct1 = __ldg(v.Ct + npx + pix);
-    ct2 = __ldg(v.Ct + 2 * npx + pix);
+    ct0 = ld_col(v.Ct, pix, v.prec);
+    ct1 = ld_col(v.Ct, npx + pix, v.prec);
+    ct2 = ld_col(v.Ct, 2 * npx + pix, v.prec);
     dt = __ldg(v.Dt + pix);
   }
   const float thr = inside ? depth_threshold(dt, eps) : -INFINITY;
@@ -264,9 +264,9 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
     v.pix_a[pix] = make_float4(o0, o1, o2, od);
     v.pix_b[pix] = make_float4(MODE == GPS_BLEND_OIT ? wsum : T, __uint_as_float(last), 0.f, 0.f);
     if (v.out_rgb) {
-      v.out_rgb[pix] = o0;
-      v.out_rgb[npx + pix] = o1;
-      v.out_rgb[2 * npx + pix] = o2;
+      st_col(v.out_rgb, pix, v.prec, o0);
+      st_col(v.out_rgb, npx + pix, v.prec, o1);
+      st_col(v.out_rgb, 2 * npx + pix, v.prec, o2);
     }
     if (v.out_depth) v.out_depth[pix] = od;
     if (v.out_weight) v.out_weight[pix] = ow;
@@ -276,8 +276,8 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
     if (inside) {
       const float dk = __ldg(v.Dtgt + pix);
       if (dk > 0.0f && dt > 0.0f) {
-        lr = fabsf(o0 - __ldg(v.Ctgt + pix)) + fabsf(o1 - __ldg(v.Ctgt + npx + pix)) +
-             fabsf(o2 - __ldg(v.Ctgt + 2 * npx + pix));
+        lr = fabsf(o0 - ld_col(v.Ctgt, pix, v.prec)) + fabsf(o1 - ld_col(v.Ctgt, npx + pix, v.prec)) +
+             fabsf(o2 - ld_col(v.Ctgt, 2 * npx + pix, v.prec));
         ld = fabsf(od - dk);
         nv = 1.0f;
       }
@@ -362,8 +362,9 @@ __device__ __forceinline__ void upstream(const ViewDev& v, long long pix, long l
     const float dk = __ldg(v.Dtgt + pix);
     if (dk > 0.0f && dt > 0.0f) {
       const float s3 = scale * (1.0f / 3.0f);
-      const float r0 = st.x - __ldg(v.Ctgt + pix), r1 = st.y - __ldg(v.Ctgt + npx + pix);
-      const float r2 = st.z - __ldg(v.Ctgt + 2 * npx + pix), rd = st.w - dk;
+      const float r0 = st.x - ld_col(v.Ctgt, pix, v.prec);
+      const float r1 = st.y - ld_col(v.Ctgt, npx + pix, v.prec);
+      const float r2 = st.z - ld_col(v.Ctgt, 2 * npx + pix, v.prec), rd = st.w - dk;
       g0 = r0 > 0.f ? s3 : (r0 < 0.f ? -s3 : 0.f);
       g1 = r1 > 0.f ? s3 : (r1 < 0.f ? -s3 : 0.f);
       g2 = r2 > 0.f ? s3 : (r2 < 0.f ? -s3 : 0.f);
@@ -650,9 +651,9 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
     T = sb.x;
     mylast = min(max(__float_as_uint(sb.y), r.x), r.y);  // stays inside this tile's list
     thr = depth_threshold(dt, eps);
-    S0 = T * __ldg(v.Ct + pix);
-    S1 = T * __ldg(v.Ct + npx + pix);
-    S2 = T * __ldg(v.Ct + 2 * npx + pix);
+    S0 = T * ld_col(v.Ct, pix, v.prec);
+    S1 = T * ld_col(v.Ct, npx + pix, v.prec);
+    S2 = T * ld_col(v.Ct, 2 * npx + pix, v.prec);
     SD = T * dt;
     if (g0 == 0.f && g1 == 0.f && g2 == 0.f && gD == 0.f) mylast = r.x;
   }

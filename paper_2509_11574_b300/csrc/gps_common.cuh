@@ -1,6 +1,8 @@
 // Shared device helpers of libgps (sm_103a).  Internal header.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/gps.h"
@@ -31,11 +33,11 @@ struct Cam {
 // Per-view device-side description (passed by value to kernels).
 struct ViewDev {
   Cam cam;
-  const float* Ct;    // [3][H][W]
+  const void* Ct;     // [3][H][W], element type per `prec`
   const float* Dt;    // [H][W]
-  const float* Ctgt;  // nullable
+  const void* Ctgt;   // nullable, element type per `prec`
   const float* Dtgt;  // nullable
-  float* out_rgb;
+  void* out_rgb;      // nullable, element type per `prec`
   float* out_depth;
   float* out_weight;
   const float* g_rgb;    // nullable
@@ -59,6 +61,7 @@ struct ViewDev {
   int tiles_x, tiles_y, tw, th;
   int sup_x, sup_y, sup_shift;
   int fused;  // backward: upstream gradients from the fused L1 loss (1) or g_rgb/g_depth (0)
+  int prec;   // GPS_PREC_* storage type of the colour images Ct, Ctgt, out_rgb
   long long cap;
 };
 
@@ -82,6 +85,20 @@ __device__ __forceinline__ int batch_slot(const int* start, int n, int item) {
 #pragma unroll 1
   while (k + 1 < n && item >= start[k + 1]) ++k;
   return k;
+}
+
+// Colour images are stored as float, IEEE binary16 or bfloat16 (GPS_PREC_*);
+// every value is converted to float on load and rounded to nearest-even on
+// store.
+__device__ __forceinline__ float ld_col(const void* p, long long i, int prec) {
+  if (prec == GPS_PREC_FP16) return __half2float(static_cast<const __half*>(p)[i]);
+  if (prec == GPS_PREC_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+  return __ldg(static_cast<const float*>(p) + i);
+}
+__device__ __forceinline__ void st_col(void* p, long long i, int prec, float x) {
+  if (prec == GPS_PREC_FP16) static_cast<__half*>(p)[i] = __float2half_rn(x);
+  else if (prec == GPS_PREC_BF16) static_cast<__nv_bfloat16*>(p)[i] = __float2bfloat16_rn(x);
+  else static_cast<float*>(p)[i] = x;
 }
 
 // Pixel rectangle of a record, clipped to the image: [x0, x1] x [y0, y1].

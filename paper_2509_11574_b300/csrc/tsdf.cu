@@ -113,7 +113,7 @@ __device__ __forceinline__ float3 sample_rgb(const VolDev& v, float gx, float gy
 }
 
 __global__ void __launch_bounds__(256) raycast_kernel(VolDev v, Cam cam, float near_, float far_,
-                                                      float* __restrict__ out_rgb,
+                                                      void* __restrict__ out_rgb, int rgb_prec,
                                                       float* __restrict__ out_depth,
                                                       float* __restrict__ out_vertex) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -182,9 +182,9 @@ __global__ void __launch_bounds__(256) raycast_kernel(VolDev v, Cam cam, float n
     }
   }
   out_depth[pix] = depth;
-  out_rgb[pix] = col.x;
-  out_rgb[npx + pix] = col.y;
-  out_rgb[2 * npx + pix] = col.z;
+  st_col(out_rgb, pix, rgb_prec, col.x);
+  st_col(out_rgb, npx + pix, rgb_prec, col.y);
+  st_col(out_rgb, 2 * npx + pix, rgb_prec, col.z);
   if (out_vertex) {
     out_vertex[pix * 3 + 0] = V[0];
     out_vertex[pix * 3 + 1] = V[1];
@@ -202,12 +202,12 @@ cudaError_t launch_fuse(const GpsTsdf& t, const float* depth, const float* rgb, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_raycast(const GpsTsdf& t, const Cam& cam, float near_, float far_, float* rgb,
-                           float* depth, float* vertex, cudaStream_t st) {
+cudaError_t launch_raycast(const GpsTsdf& t, const Cam& cam, float near_, float far_, void* rgb,
+                           int rgb_prec, float* depth, float* vertex, cudaStream_t st) {
   VolDev v{t.nx, t.ny, t.nz, t.voxel, t.origin[0], t.origin[1], t.origin[2], t.trunc,
            t.max_weight, t.sdf, t.weight, reinterpret_cast<float4*>(t.rgbw)};
   dim3 grid((cam.W + 15) / 16, (cam.H + 15) / 16);
-  raycast_kernel<<<grid, 256, 0, st>>>(v, cam, near_, far_, rgb, depth, vertex);
+  raycast_kernel<<<grid, 256, 0, st>>>(v, cam, near_, far_, rgb, rgb_prec, depth, vertex);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,17 @@ def test_fuse_matches_oracle(name):
 
 @pytest.mark.parametrize("name", ["tiny", "small"])
 def test_raycast_matches_oracle(name):
+    _raycast_vs_oracle(name, gps.PREC_FP32)
+
+
+@pytest.mark.parametrize("prec", [gps.PREC_FP16, gps.PREC_BF16])
+def test_raycast_reduced_precision_colour(prec):
+    """C_t stored as binary16 / bfloat16: the same tolerance plus half an ulp
+    of the stored type."""
+    _raycast_vs_oracle("small", prec)
+
+
+def _raycast_vs_oracle(name, prec):
     w = workload(name)
     vol_o = oracle.Volume(w.tsdf)
     f = w.frames[0]
@@ -63,8 +74,9 @@ def test_raycast_matches_oracle(name):
     vg.sdf.copy_(gps.linear_to_brick(torch.from_numpy(sdf32)).cuda())
     rgbw = np.concatenate([rgb32, np.ones(rgb32.shape[:3] + (1,), np.float32)], -1)
     vg.rgbw.copy_(gps.linear_to_brick(torch.from_numpy(rgbw)).cuda())
-    c, d = gps.raycast_sdf(vg, f.cam)
-    c, d = c.cpu().numpy(), d.cpu().numpy()
+    c, d = gps.raycast_sdf(vg, f.cam, precision=prec)
+    assert c.dtype == gps.PREC_DTYPE[prec]
+    c, d = c.float().cpu().numpy(), d.cpu().numpy()
     ok = amb == 0
     assert ok.mean() > 0.98, ok.mean()
     np.testing.assert_array_equal(d[ok] > 0, Dt[ok] > 0)
@@ -77,9 +89,15 @@ def test_raycast_matches_oracle(name):
         [(np.nonzero(hit)[1] - f.cam.cx) / f.cam.fx, (np.nonzero(hit)[0] - f.cam.cy) / f.cam.fy,
          np.ones(hit.sum())], axis=0)
     tol = 1e-4 + 2.0 * dpos / w.tsdf.voxel
+    tol = tol + _HALF_ULP[prec] * (np.abs(Ct[:, hit]) + tol)
     assert np.all(np.abs(c[:, hit] - Ct[:, hit]) <= tol), np.abs(c[:, hit] - Ct[:, hit]).max()
     print("raycast: max depth rel", np.max(np.abs(d[hit] - Dt[hit]) / Dt[hit]),
           "max colour", np.abs(c[:, hit] - Ct[:, hit]).max())
+
+
+# relative half-ulp of the colour storage types (round to nearest, normal
+# numbers): 2^-24 float32, 2^-11 binary16, 2^-8 bfloat16
+_HALF_ULP = {gps.PREC_FP32: 0.0, gps.PREC_FP16: 2.0 ** -11, gps.PREC_BF16: 2.0 ** -8}
 
 
 # ------------------------------------------------------------ projection
@@ -267,18 +285,33 @@ def test_end_to_end_grad_config():
     _end_to_end(w, gps.BLEND_OIT, lam=1.0)
 
 
-def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False):
+@pytest.mark.parametrize("prec", [gps.PREC_FP16, gps.PREC_BF16])
+@pytest.mark.parametrize("mode", [gps.BLEND_OIT, gps.BLEND_ALPHA])
+def test_end_to_end_reduced_precision_colour(mode, prec):
+    """C_t, C_k and C* stored as binary16 / bfloat16.  The oracle takes the
+    same rounded C_t and C_k, so the only new difference is the rounding of
+    the stored C* (half an ulp); loss and gradients keep their tolerances."""
+    w = workload("small")
+    _end_to_end(w, mode, lam=1.0, prec=prec)
+
+
+def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False, prec=gps.PREC_FP32):
     f = w.frames[0]
     H, W = f.cam.height, f.cam.width
     Ct, Dt, _, _ = oracle_sdf_images(w)
-    ref = oracle.render_loss_grads(w.gaussians.astype(np.float64), f.cam, Ct, Dt, f.rgb, f.depth,
+    # colour images as stored (oracle.quantise: float32 for PREC_FP32)
+    Ct = oracle.quantise(Ct, prec).astype(np.float32)
+    Ctgt = oracle.quantise(f.rgb, prec).astype(np.float32)
+    ref = oracle.render_loss_grads(w.gaussians.astype(np.float64), f.cam, Ct, Dt, Ctgt, f.depth,
                                    eps=w.eps_depth, lambda_depth=lam, mode=mode)
     s = gps.settings(eps_depth=w.eps_depth, lambda_depth=lam, blend_mode=mode, tile=tile,
-                     deterministic=deterministic)
+                     deterministic=deterministic, precision=prec)
     r = gps.Renderer(w.gaussians.M, [f.cam], s)
     g = gps.Gaussians.from_numpy(w.gaussians)
-    v = gps.View(f.cam, cuda(Ct), cuda(Dt), cuda(f.rgb), cuda(f.depth),
-                 out_rgb=torch.empty(3, H, W, device="cuda"), out_depth=torch.empty(H, W, device="cuda"))
+    cdt = gps.PREC_DTYPE[prec]
+    v = gps.View(f.cam, cuda(Ct).to(cdt), cuda(Dt), cuda(Ctgt).to(cdt), cuda(f.depth),
+                 out_rgb=torch.empty(3, H, W, device="cuda", dtype=cdt),
+                 out_depth=torch.empty(H, W, device="cuda"))
     loss = torch.zeros(1, device="cuda")
     r.forward(g, [v], loss)
     grads = g.zeros_like()
@@ -297,16 +330,19 @@ def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False):
     assert skip.mean() < 0.01
     ok = ~skip & np.isfinite(out["allow_C"])
     assert ok.mean() > 0.99, ok.mean()
-    dC = np.abs(v.out_rgb.cpu().numpy() - out["C"]).max(0)
+    # stored C*: FP32 error and flip allowance, plus half an ulp of the storage type
+    tolC = 1e-4 + out["allow_C"]
+    tolC = tolC + _HALF_ULP[prec] * (np.abs(out["C"]).max(0) + tolC)
+    dC = np.abs(v.out_rgb.float().cpu().numpy() - out["C"]).max(0)
     dD = np.abs(v.out_depth.cpu().numpy() - out["D"])
-    assert np.all(dC[ok] <= 1e-4 + out["allow_C"][ok]), (dC[ok] - out["allow_C"][ok]).max()
+    assert np.all(dC[ok] <= tolC[ok]), (dC[ok] - tolC[ok]).max()
     assert np.all(dD[ok] <= 1e-4 * np.abs(out["D"][ok]) + out["allow_D"][ok])
     np.testing.assert_allclose(loss.item(), ref["L"], rtol=1e-4)
     got = {k: t.cpu().numpy() for k, t in zip(ref["grads"].keys(), grads.tensors())}
     # A counting decision within the FP32 error band of its threshold may go
     # either way: the oracle evaluated with every such decision inverted
     # bounds how far the gradients can move (single flips per pixel).
-    alt = oracle.render_loss_grads(w.gaussians.astype(np.float64), f.cam, Ct, Dt, f.rgb, f.depth,
+    alt = oracle.render_loss_grads(w.gaussians.astype(np.float64), f.cam, Ct, Dt, Ctgt, f.depth,
                                    eps=w.eps_depth, lambda_depth=lam, mode=mode,
                                    flip=(4e-6, 2e-6))
     # Gaussians whose own near-threshold alpha is more than 1e-4 of their
@@ -316,7 +352,7 @@ def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False):
     # gradient then moves by at most twice those pixels' absolute
     # contributions, which the oracle's own adjoint gives exactly
     valid = (f.depth > 0) & (Dt > 0)
-    ambC = (np.abs(out["C"] - f.rgb) < 2e-5) & valid[None]
+    ambC = (np.abs(out["C"] - Ctgt) < 2e-5) & valid[None]
     ambD = (np.abs(out["D"] - f.depth) < 2e-5 * np.abs(f.depth)) & valid
     ga = sign_flip_allowance(w.gaussians.astype(np.float64), f.cam, rec, Ct, Dt, w.eps_depth, mode,
                              ambC, ambD if lam else np.zeros_like(ambD), ref["n_valid"], lam)

@@ -386,3 +386,27 @@ def test_adam_matches_torch():
         opt.step()
         oracle.adam(p, gr, m, v, lr, 0.9, 0.999, 1e-15, step)
     np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-14, atol=1e-16)
+
+
+def test_quantise_matches_torch_casts_and_ties_to_even():
+    """Storage rounding of the colour images: torch's own float16 / bfloat16
+    casts on random values, plus tie cases worked by hand."""
+    import torch
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.uniform(0, 1, 20000), rng.normal(0, 3, 20000),
+                        [0.0, 1.0, 65504.0, 1e-7, -2.5]])
+    x32 = torch.from_numpy(x.astype(np.float32))
+    np.testing.assert_array_equal(oracle.quantise(x, oracle.FP16),
+                                  x32.to(torch.float16).double().numpy())
+    np.testing.assert_array_equal(oracle.quantise(x, oracle.BF16),
+                                  x32.to(torch.bfloat16).double().numpy())
+    np.testing.assert_array_equal(oracle.quantise(x, oracle.FP32), x.astype(np.float32))
+    # bfloat16 keeps 7 fraction bits: 1 + 2^-8 is a tie between 1 and 1 + 2^-7
+    # (odd), so it goes to 1; 1 + 3 * 2^-8 ties between 1 + 2^-7 (odd) and
+    # 1 + 2^-6 (even)
+    assert oracle.quantise([1 + 2 ** -8], oracle.BF16)[0] == 1.0
+    assert oracle.quantise([1 + 3 * 2 ** -8], oracle.BF16)[0] == 1 + 2 ** -6
+    assert oracle.quantise([1 + 2 ** -8 + 2 ** -20], oracle.BF16)[0] == 1 + 2 ** -7
+    # binary16 keeps 10: 1 + 2^-11 ties to 1, 1 + 3 * 2^-11 to 1 + 2^-9
+    assert oracle.quantise([1 + 2 ** -11], oracle.FP16)[0] == 1.0
+    assert oracle.quantise([1 + 3 * 2 ** -11], oracle.FP16)[0] == 1 + 2 ** -9
