@@ -35,7 +35,10 @@ sys.path.insert(0, ROOT)
 ITERS_PER_FRAME = 10
 N_FRAMES = 30
 M_GAUSS = 100_000
+N_FRAMES_LARGE = 20
+M_GAUSS_LARGE = 1_000_000
 METRIC = "fwd+bwd+Adam iterations/sec (640x480, 100k Gaussians)"
+METRIC_LARGE = "fwd+bwd+Adam iterations/sec (1280x720, 1M Gaussians)"
 
 
 def parse():
@@ -44,14 +47,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tile", default="16x8")
+    ap.add_argument("--tile", default="16x8",
+                    help="tile shape WxH, or 'auto' for the autotuner's choice on the first frame")
     ap.add_argument("--mode", default="oit", choices=["oit", "alpha"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--frames", type=int, default=N_FRAMES)
-    ap.add_argument("--workload", default="room", choices=["room", "multiview"],
-                    help="multiview: 8 mixed-resolution views of one scene, 300k Gaussians; "
-                         "one call per iteration for all views vs one call per view")
+    ap.add_argument("--frames", type=int, default=None,
+                    help=f"frames of the sequence (room: {N_FRAMES}, large: {N_FRAMES_LARGE})")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="storage type of the colour images C_t, C_k, C*")
+    ap.add_argument("--workload", default="room", choices=["room", "large", "multiview"],
+                    help="room: 640x480, 100k Gaussians (the headline); large: 1280x720, "
+                         "5.12 m room, 512^3 TSDF, 1M Gaussians; multiview: 8 mixed-resolution "
+                         "views of one scene, 300k Gaussians, one call for all views vs one per view")
     ap.add_argument("--profile", action="store_true",
                     help="short plain run (3 frames) for ncu captures; prints no JSON line")
     return ap.parse_args()
@@ -145,23 +153,47 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- workload
-def make_workload(rank: int, n_frames: int):
+def make_workload(rank: int, args):
     from datagen import workloads
-    return workloads.room(n_frames=n_frames, M=M_GAUSS, seed_scene=2 + 1000 * rank,
+    if args.workload == "large":
+        return workloads.room(n_frames=args.frames or N_FRAMES_LARGE, M=M_GAUSS_LARGE, width=1280,
+                              height=720, size=5.12, n_vox=512, seed_scene=2 + 1000 * rank,
+                              seed_path=3 + 1000 * rank)
+    return workloads.room(n_frames=args.frames or N_FRAMES, M=M_GAUSS, seed_scene=2 + 1000 * rank,
                           seed_path=3 + 1000 * rank)
+
+
+def workload_config(args, w):
+    """The `config` object of both arms' JSON lines."""
+    c0 = w.frames[0].cam
+    s = w.tsdf
+    return {"workload": f"room {s.nx * s.voxel:.2f} m, {len(w.frames)} frames {c0.width}x{c0.height}, "
+                        f"{s.nx}^3 TSDF at {100 * s.voxel:.0f} cm, {w.gaussians.M} Gaussians, "
+                        f"{ITERS_PER_FRAME} iterations/frame",
+            "blend": args.mode, "tile": args.tile, "colour_storage": args.precision,
+            "form": "CUDA graph per frame", "l2": "256 MB buffer written between steps (untimed)"}
+
+
+PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 
 class GpuPipeline:
     """Device-resident state of one replica and the per-frame step."""
 
-    def __init__(self, w, tile, mode, device):
+    def __init__(self, w, tile, mode, device, precision="fp32"):
         import torch
         import paper_2509_11574_b300 as gps
         self.gps, self.torch = gps, torch
         self.w = w
         self.dev = device
-        self.frames = [(torch.from_numpy(f.depth).to(device), torch.from_numpy(f.rgb).to(device))
-                       for f in w.frames]
+        prec = PRECISIONS[precision]
+        self.cdt = gps.PREC_DTYPE[prec]
+        # per frame: depth, colour (float, fused into the TSDF), colour target C_k
+        # in the storage type (the same tensor when that is float)
+        self.frames = []
+        for f in w.frames:
+            d, c = torch.from_numpy(f.depth).to(device), torch.from_numpy(f.rgb).to(device)
+            self.frames.append((d, c, c if prec == 0 else c.to(self.cdt)))
         self.cams = [f.cam for f in w.frames]
         H, W = self.cams[0].height, self.cams[0].width
         self.vol = gps.Tsdf(w.tsdf, device)
@@ -171,9 +203,9 @@ class GpuPipeline:
         self.opt = gps.Adam(self.g, device_step=True)
         self.s = gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, near=w.near,
                               blend_mode=gps.BLEND_ALPHA if mode == "alpha" else gps.BLEND_OIT,
-                              tile=tile, pair_capacity=64 * w.gaussians.M)
+                              tile=tile, pair_capacity=64 * w.gaussians.M, precision=prec)
         self.r = gps.Renderer(w.gaussians.M, self.cams[:1], self.s, device)
-        self.Ct = torch.zeros(3, H, W, device=device)
+        self.Ct = torch.zeros(3, H, W, device=device, dtype=self.cdt)
         self.Dt = torch.zeros(H, W, device=device)
         self.loss = torch.zeros(ITERS_PER_FRAME, device=device)
         self.graphs = {}
@@ -186,13 +218,25 @@ class GpuPipeline:
             t.zero_()
         self.opt.device_step.zero_()
 
+    def autotune(self):
+        """Tile shape from gps_autotune_tiles on frame 0 (fused and ray-cast
+        first); the device state is reset afterwards."""
+        d, c, _ = self.frames[0]
+        self.gps.fuse_frame(self.vol, d, c, self.cams[0])
+        self.gps.raycast_sdf(self.vol, self.cams[0], self.w.near, 0.0, self.Ct, self.Dt, None)
+        best, times = self.r.autotune(self.g, [self.view(0)], repeats=3)
+        self.s = self.r.s
+        self.reset()
+        return {"chosen": f"{best[0]}x{best[1]}",
+                "ms_fwd_bwd": {f"{a}x{b}": t for (a, b), t in times.items()}}
+
     def view(self, k):
-        d, c = self.frames[k]
-        return self.gps.View(self.cams[k], self.Ct, self.Dt, c, d)
+        d, _, ck = self.frames[k]
+        return self.gps.View(self.cams[k], self.Ct, self.Dt, ck, d)
 
     def step(self, k, stream=None, stage_events=None):
         gps = self.gps
-        d, c = self.frames[k]
+        d, c, _ = self.frames[k]
         gps.fuse_frame(self.vol, d, c, self.cams[k], stream)
         gps.raycast_sdf(self.vol, self.cams[k], self.w.near, 0.0, self.Ct, self.Dt, None, stream)
         v = [self.view(k)]
@@ -298,11 +342,16 @@ def run_ours(args, rank, world, local):
     if world > 1:
         dist.barrier()
     gps.lib()
-    tile = tuple(int(x) for x in args.tile.split("x"))
+    tile = (16, 8) if args.tile == "auto" else tuple(int(x) for x in args.tile.split("x"))
     t0 = time.time()
-    w = make_workload(rank, args.frames)
+    w = make_workload(rank, args)
     gen_s = time.time() - t0
-    pipe = GpuPipeline(w, tile, args.mode, dev)
+    pipe = GpuPipeline(w, tile, args.mode, dev, args.precision)
+    tuned = None
+    if args.tile == "auto":
+        tuned = pipe.autotune()
+        tile = (pipe.s.tile_w, pipe.s.tile_h)
+        args.tile = f"{tile[0]}x{tile[1]} (autotuned)"
     nF = len(w.frames)
     if args.profile:
         for k in range(3):
@@ -381,7 +430,14 @@ def run_ours(args, rank, world, local):
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        host = [(torch.from_numpy(f.depth).pin_memory(), torch.from_numpy(f.rgb).pin_memory()) for f in w.frames]
+        # host inputs per frame: depth, colour (float) and, for reduced colour
+        # storage, the colour target already in the storage type
+        host = []
+        for k, f in enumerate(w.frames):
+            hk = [torch.from_numpy(f.depth).pin_memory(), torch.from_numpy(f.rgb).pin_memory()]
+            if pipe.frames[k][2] is not pipe.frames[k][1]:
+                hk.append(pipe.frames[k][2].cpu().pin_memory())
+            host.append(hk)
         loss_host = torch.zeros(ITERS_PER_FRAME, pin_memory=True)
         pipe.reset()
         torch.cuda.synchronize()
@@ -392,15 +448,15 @@ def run_ours(args, rank, world, local):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            pipe.frames[k][0].copy_(host[k][0], non_blocking=True)
-            pipe.frames[k][1].copy_(host[k][1], non_blocking=True)
+            for dst, src in zip(pipe.frames[k], host[k]):
+                dst.copy_(src, non_blocking=True)
             pipe.graphs[k].replay()
             loss_host.copy_(pipe.loss, non_blocking=True)
             e1.record()
             e1.synchronize()
             if i >= Wu:
                 e2e_ms.append(e0.elapsed_time(e1))
-        h2d = host[0][0].numel() * 4 + host[0][1].numel() * 4
+        h2d = sum(t.numel() * t.element_size() for t in host[0])
         e2e = {"value": ITERS_PER_FRAME * K / (sum(e2e_ms) / 1e3) * world, "unit": "iterations/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": ITERS_PER_FRAME * 4}
 
@@ -449,19 +505,17 @@ def run_ours(args, rank, world, local):
     it_bytes = _iteration_bytes(w, counts)
     it_ms = sum(stage_ms.values())
     line = {
-        "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world, "steps": K,
+        "metric": METRIC_LARGE if args.workload == "large" else METRIC, "value": value,
+        "unit": "iterations/s", "n_gpus": world, "steps": K,
         "warmup": Wu, "ms_per_step": sum(step_ms) / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"room 2.56 m, {nF} frames 640x480, 256^3 TSDF at 1 cm, "
-                               f"{M_GAUSS} Gaussians, {ITERS_PER_FRAME} iterations/frame",
-                   "blend": args.mode, "tile": args.tile, "form": "CUDA graph per frame",
-                   "l2": "256 MB buffer written between steps (untimed)",
-                   "parallelism": f"{world} independent replicas"},
+        "config": dict(workload_config(args, w), parallelism=f"{world} independent replicas"),
         "ms_per_frame": sum(step_ms) / K,
         "plain_ms_per_frame": sum(plain_ms) / K,
         "graph_speedup_vs_plain": (sum(plain_ms) / sum(step_ms)),
         "stage_ms": stage_ms,
         "evaluations": counts,
+        "autotune": tuned,
         "hbm_model": {"bytes_per_iteration": it_bytes, "peak_gbs": hbm,
                       "frac_at_iteration_time": it_bytes / (it_ms * 1e-3) / 1e9 / hbm if it_ms else None},
         "roofline": roofline,
@@ -503,7 +557,6 @@ def _oracle_iteration(w, frame, band, lam):
     import oracle
     f = w.frames[frame]
     H, W = f.cam.height, f.cam.width
-    vol = _oracle_iteration.vol
     Ct, Dt = _oracle_iteration.sdf
     g = w.gaussians.astype(np.float64)
     rec, _ = oracle.project(g, f.cam, w.near)
@@ -528,31 +581,42 @@ def _oracle_setup(w):
     import numpy as np
     import oracle
     f = w.frames[0]
-    vol = oracle.Volume(w.tsdf)
-    oracle.fuse(vol, f.depth, f.rgb, f.cam)
-    Ct, Dt, _, _ = oracle.raycast(w.tsdf, vol.sdf, vol.rgb, f.cam)
-    _oracle_iteration.vol = vol
+    s = w.tsdf
+    if s.nx * s.ny * s.nz <= 64 ** 3 * 64:
+        vol = oracle.Volume(w.tsdf)
+        oracle.fuse(vol, f.depth, f.rgb, f.cam)
+        Ct, Dt, _, _ = oracle.raycast(w.tsdf, vol.sdf, vol.rgb, f.cam)
+        _oracle_iteration.sdf_note = "C_t, D_t from the oracle's fusion + ray-cast of frame 0"
+    else:
+        # a 512^3 FP64 volume (6.4 GB) is out of a bounded sample's reach: the
+        # frame's own colour and depth stand in for the ray-cast images
+        Ct, Dt = f.rgb, f.depth
+        _oracle_iteration.sdf_note = "frame 0's colour and depth standing in for C_t, D_t"
     _oracle_iteration.sdf = (Ct.astype(np.float32).astype(np.float64), Dt.astype(np.float32).astype(np.float64))
 
 
-BAND_ROWS = 60  # one eighth of the 480 rows per oracle sample
+BAND_ROWS = 60  # one eighth of the 480 rows per sample of the reference arm
 
 
 def cpu_baseline(w):
     """The oracle as it stands, on the host cores, on a bounded sample: one
-    iteration restricted to a band of 60 of the 480 rows (1/8 of the pixels;
-    projection and Adam over all 100k Gaussians)."""
+    whole iteration of frame 0 at 640x480 (about 15 s on 16 cores); at
+    1280x720 with 1M Gaussians a band of 1/8 of the rows."""
     import oracle
     oracle.build()
     _oracle_setup(w)
+    H = w.frames[0].cam.height
+    rows = H if w.gaussians.M <= 200_000 else H // 8
+    y0 = (H - rows) // 2
     t0 = time.time()
-    _oracle_iteration(w, 0, (210, 210 + BAND_ROWS - 1), w.lambda_depth)
+    _oracle_iteration(w, 0, (y0, y0 + rows - 1), w.lambda_depth)
     dt = time.time() - t0
-    frac = BAND_ROWS / w.frames[0].cam.height
+    frac = rows / H
     return {"value": frac / dt, "unit": "iterations/s", "cores": _omp_threads(), "kind": "oracle",
-            "sample": f"one fwd+loss+bwd+Adam iteration of frame 0 restricted to rows 210-269 "
-                      f"(1/8 of 640x480; projection and Adam over all {w.gaussians.M} Gaussians), "
-                      f"scaled by 1/8 to iterations/s; took {dt:.1f} s"}
+            "sample": f"one fwd+loss+bwd+Adam iteration of frame 0 over rows {y0}-{y0 + rows - 1} "
+                      f"of {H} (projection and Adam over all {w.gaussians.M} Gaussians; "
+                      f"{_oracle_iteration.sdf_note}), scaled by {rows}/{H} to iterations/s; "
+                      f"took {dt:.1f} s"}
 
 
 def _omp_threads():
@@ -585,7 +649,7 @@ def run_multiview(args, rank, world, local):
     if world > 1:
         dist.barrier()
     gps.lib()
-    tile = tuple(int(x) for x in args.tile.split("x"))
+    tile = (16, 8) if args.tile == "auto" else tuple(int(x) for x in args.tile.split("x"))
     w = workloads.multiview(M=MV_GAUSS)
     cams = [f.cam for f in w.frames]
     vol = gps.Tsdf(w.tsdf, dev)
@@ -606,6 +670,13 @@ def run_multiview(args, rank, world, local):
     grads = g.zeros_like()
     opt = gps.Adam(g, device_step=True)
     rb = gps.Renderer(MV_GAUSS, cams, s, dev)
+    tuned = None
+    if args.tile == "auto":
+        best, times = rb.autotune(g, views, repeats=2)
+        s = rb.s
+        tuned = {"chosen": f"{best[0]}x{best[1]}",
+                 "ms_fwd_bwd": {f"{a}x{b}": t for (a, b), t in times.items()}}
+        args.tile = f"{best[0]}x{best[1]} (autotuned)"
     rs = [gps.Renderer(MV_GAUSS, [c], s, dev) for c in cams]
     loss = torch.zeros(len(cams), device=dev)
 
@@ -683,6 +754,7 @@ def run_multiview(args, rank, world, local):
                    "blend": args.mode, "tile": args.tile, "form": "CUDA graph",
                    "l2": "256 MB buffer written between steps (untimed)"},
         "timings_ms": res,
+        "autotune": tuned,
         "batched_speedup_vs_sequential": {
             "graph": res["sequential_graph_ms"] / res["batched_graph_ms"],
             "plain": res["sequential_plain_ms"] / res["batched_plain_ms"]},
@@ -695,7 +767,7 @@ def run_multiview(args, rank, world, local):
 def run_reference(args, rank, world, local):
     if rank != 0:
         return
-    w = make_workload(0, args.frames)
+    w = make_workload(0, args)
     import oracle
     oracle.build()
     _oracle_setup(w)
@@ -712,11 +784,12 @@ def run_reference(args, rank, world, local):
     cb = {"value": value, "unit": "iterations/s", "cores": _omp_threads(), "kind": "oracle",
           "sample": f"each step: one iteration of frame 0 restricted to a {BAND_ROWS}-row band "
                     f"(1/8 of the pixels), scaled by 1/8"}
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s",
+    line = {"impl": "reference", "metric": METRIC_LARGE if args.workload == "large" else METRIC,
+            "value": value, "unit": "iterations/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"room 2.56 m, 640x480, 256^3 TSDF at 1 cm, {M_GAUSS} Gaussians"},
+            "config": dict(workload_config(args, w), parallelism=f"{world} independent replicas"),
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}

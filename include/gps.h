@@ -144,7 +144,8 @@ typedef struct GpsRenderSettings {
   float near_plane;      /* Gaussians with camera z <= near are culled (0.2)  */
   int32_t blend_mode;    /* GPS_BLEND_*                                        */
   int32_t precision;     /* GPS_PREC_*: element type of the colour images      */
-  int32_t tile_w, tile_h;/* 0, 0 = 16 x 16; supported: 16x16, 16x8, 8x8, 32x8 */
+  int32_t tile_w, tile_h;/* pixels per tile; 0, 0 = 16 x 8; supported: 16x16,
+                            16x8, 8x8, 32x8 (gps_autotune_tiles picks one)   */
   int32_t deterministic; /* 1: fixed-order gradient reduction, no float atomics */
   int32_t stages;        /* GPS_STAGE_* mask, 0 = all                          */
   int32_t instrument;    /* 1: count Gaussian-pixel evaluations (slower; for
@@ -271,6 +272,32 @@ GPS_API int32_t render_backward(const GpsGaussians* gaussians, const GpsView* vi
  * incremented first, so a captured graph can replay it. */
 GPS_API int32_t adam_step(GpsGaussians* params, GpsGaussians* grads, GpsGaussians* m, GpsGaussians* v,
                   const GpsAdamHyper* hyper, int32_t step, int32_t* device_step, void* stream);
+
+/* Number of tile shapes gps_autotune_tiles tries, in this order:
+ * 16x16, 16x8, 8x8, 32x8 (pixels; the binning split and both composite kernels
+ * run one thread per tile pixel, so this also picks their CTA shape). */
+#define GPS_AUTOTUNE_SHAPES 4
+
+/* Tile-shape autotuner (the paper has no counterpart).  For every shape above
+ * whose workspace (gps_workspace_size) fits in ws_bytes, runs render_forward +
+ * render_backward on the caller's own Gaussians and views once untimed, then
+ * `repeats` times timed with CUDA events on `stream`, and returns the fastest
+ * in *best_tile_w, *best_tile_h; times_ms[GPS_AUTOTUNE_SHAPES] (nullable)
+ * receives each shape's mean milliseconds per forward + backward, -1 for a
+ * shape that was skipped (workspace too small, or the pair capacity
+ * overflowed).  settings supplies everything but the tile (stages and
+ * instrument are ignored).  The backward accumulates into scratch_grads (same
+ * shape as the Gaussians), which the caller discards; the views' outputs
+ * are overwritten.  Synchronises `stream` after every shape: call it before
+ * capturing graphs, then pass the chosen shape in GpsRenderSettings (and size
+ * the workspace for it).  Errors: GPS_ERR_INVALID_ARG for NULL arguments,
+ * render_forward's and render_backward's own errors, GPS_ERR_WORKSPACE_TOO_SMALL
+ * when no shape could run. */
+GPS_API int32_t gps_autotune_tiles(const GpsGaussians* gaussians, const GpsView* views,
+                                   int32_t n_views, const GpsRenderSettings* settings, void* ws,
+                                   size_t ws_bytes, GpsGaussians* scratch_grads, int32_t repeats,
+                                   int32_t* best_tile_w, int32_t* best_tile_h, float* times_ms,
+                                   void* stream);
 
 /* Size of the static device array behind render_forward_noalloc: 64 MiB,
  * held by every GPU that loads this library until the process exits. */

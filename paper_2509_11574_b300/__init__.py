@@ -96,7 +96,8 @@ class GpsWorkspaceLayout(ctypes.Structure):
 
 EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspace_layout",
             "gps_query_status", "fuse_frame", "raycast_sdf", "render_forward", "render_backward",
-            "adam_step", "render_forward_noalloc")
+            "adam_step", "render_forward_noalloc", "gps_autotune_tiles")
+AUTOTUNE_SHAPES = ((16, 16), (16, 8), (8, 8), (32, 8))  # the order of GPS_AUTOTUNE_SHAPES
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib: Optional[ctypes.CDLL] = None
@@ -137,6 +138,11 @@ def lib() -> ctypes.CDLL:
         L.render_backward.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsView),
                                       c_int32, ctypes.POINTER(GpsRenderSettings), c_void_p,
                                       c_size_t, c_void_p, ctypes.POINTER(GpsGaussians), c_void_p]
+        L.gps_autotune_tiles.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsView),
+                                         c_int32, ctypes.POINTER(GpsRenderSettings), c_void_p,
+                                         c_size_t, ctypes.POINTER(GpsGaussians), c_int32,
+                                         ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                         ctypes.POINTER(c_float), c_void_p]
         L.adam_step.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsGaussians),
                                 ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsGaussians),
                                 ctypes.POINTER(GpsAdamHyper), c_int32, c_void_p, c_void_p]
@@ -383,6 +389,22 @@ def render_backward(g: Gaussians, views: Sequence[View], s: GpsRenderSettings, w
                                  ws.numel(), _ptr(dloss), ctypes.byref(gr), _stream(stream)))
 
 
+def gps_autotune_tiles(g: Gaussians, views: Sequence[View], s: GpsRenderSettings,
+                       ws: torch.Tensor, scratch_grads: Gaussians, repeats: int = 3,
+                       stream=None):
+    """Fastest tile shape for these Gaussians and views: ((tile_w, tile_h),
+    {shape: ms per forward + backward, or None where skipped})."""
+    gc, sg = g.c(), scratch_grads.c()
+    va = _views(views, s)
+    tw, th = c_int32(0), c_int32(0)
+    times = (c_float * len(AUTOTUNE_SHAPES))()
+    _check(lib().gps_autotune_tiles(ctypes.byref(gc), va, len(views), ctypes.byref(s), _ptr(ws),
+                                    ws.numel(), ctypes.byref(sg), repeats, ctypes.byref(tw),
+                                    ctypes.byref(th), times, _stream(stream)))
+    return (tw.value, th.value), {shp: (t if t >= 0 else None)
+                                  for shp, t in zip(AUTOTUNE_SHAPES, times)}
+
+
 def adam_step(params: Gaussians, grads: Gaussians, m: Gaussians, v: Gaussians, lr=LR_APP_C,
               beta1=0.9, beta2=0.999, eps=1e-15, step: int = 1,
               device_step: Optional[torch.Tensor] = None, stream=None) -> None:
@@ -421,6 +443,23 @@ class Renderer:
 
     def status(self, stream=None) -> int:
         return gps_query_status(self.ws, stream)
+
+    def autotune(self, g: Gaussians, views: Sequence[View], repeats: int = 3, stream=None):
+        """Time every tile shape on these Gaussians and views, switch to the
+        fastest and size the workspace for it.  Returns gps_autotune_tiles'
+        result.  Synchronises; call before capturing graphs."""
+        need = 0
+        for tw, th in AUTOTUNE_SHAPES:
+            s = GpsRenderSettings.from_buffer_copy(self.s)
+            s.tile_w, s.tile_h = tw, th
+            need = max(need, gps_workspace_size(self.M, self.cams, s))
+        dev = self.ws.device
+        self.ws = torch.zeros(need, dtype=torch.uint8, device=dev)
+        best, times = gps_autotune_tiles(g, views, self.s, self.ws, g.zeros_like(), repeats, stream)
+        self.s.tile_w, self.s.tile_h = best
+        self.ws = torch.zeros(gps_workspace_size(self.M, self.cams, self.s), dtype=torch.uint8,
+                              device=dev)
+        return best, times
 
 
 class Adam:

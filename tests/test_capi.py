@@ -124,6 +124,17 @@ def test_invalid_arguments_fail_before_launch(L):
     bad = gps.settings(blend_mode=7)
     assert L.render_forward(ctypes.byref(gz), v, 1, ctypes.byref(bad), fake, 1 << 30, None, None) \
         == gps.GPS_ERR_INVALID_ARG
+    vol8 = gps.GpsTsdf(8, 8, 8, 0.01, (ctypes.c_float * 3)(0, 0, 0), 0.03, 100.0, fake, fake, fake)
+    assert L.raycast_sdf(ctypes.byref(vol8), ctypes.byref(K), ctypes.byref(P), 0.2, 0.0, fake, 9,
+                         fake, None, None) == gps.GPS_ERR_INVALID_ARG
+    assert b"precision" in L.gps_last_error()
+    tw, th = ctypes.c_int32(0), ctypes.c_int32(0)
+    assert L.gps_autotune_tiles(ctypes.byref(gz), v, 1, ctypes.byref(s), fake, 1 << 20, None, 3,
+                                ctypes.byref(tw), ctypes.byref(th), None, None) \
+        == gps.GPS_ERR_INVALID_ARG
+    assert L.gps_autotune_tiles(ctypes.byref(gz), v, 1, ctypes.byref(s), fake, 1 << 20,
+                                ctypes.byref(gz), 0, ctypes.byref(tw), ctypes.byref(th), None,
+                                None) == gps.GPS_ERR_INVALID_ARG
     h = gps.GpsAdamHyper((ctypes.c_float * 5)(*gps.LR_APP_C), 0.9, 0.999, 1e-15)
     assert L.adam_step(ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(gz),
                        ctypes.byref(h), 0, None, None) == gps.GPS_ERR_INVALID_ARG

@@ -424,3 +424,40 @@ def test_adam_device_step_counter_matches_host_steps():
     # the device path computes the bias corrections in FP32 (expm1 / log1p)
     for a, b in zip(pa.tensors(), pb.tensors()):
         torch.testing.assert_close(a, b, rtol=1e-6, atol=1e-7)
+
+
+# ------------------------------------------------------------- autotuner
+def test_autotuner_picks_a_shape_that_renders_identically():
+    """gps_autotune_tiles times every tile shape on the caller's data; the
+    forward images do not depend on the tile shape (each pixel counts the same
+    Gaussians in the same depth order), and the gradients only through the
+    order of the per-tile partial sums."""
+    w = workload("small")
+    f = w.frames[0]
+    H, W = f.cam.height, f.cam.width
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    res = {}
+    for tune in (False, True):
+        s = gps.settings(eps_depth=w.eps_depth, tile=(16, 16))
+        r = gps.Renderer(g.M, [f.cam], s)
+        v = gps.View(f.cam, cuda(Ct), cuda(Dt), cuda(f.rgb), cuda(f.depth),
+                     out_rgb=torch.empty(3, H, W, device="cuda"))
+        if tune:
+            best, times = r.autotune(g, [v], repeats=2)
+            assert best in gps.AUTOTUNE_SHAPES
+            ran = {k: t for k, t in times.items() if t is not None}
+            assert len(ran) == len(gps.AUTOTUNE_SHAPES) and all(t > 0 for t in ran.values())
+            assert times[best] == min(ran.values())
+            assert (r.s.tile_w, r.s.tile_h) == best
+            assert r.ws.numel() == gps.gps_workspace_size(g.M, [f.cam], r.s)
+        loss = torch.zeros(1, device="cuda")
+        r.forward(g, [v], loss)
+        grads = g.zeros_like()
+        r.backward(g, [v], grads)
+        assert r.status() == gps.GPS_OK
+        res[tune] = (v.out_rgb.cpu().numpy(), loss.item(), grads.flat().cpu().numpy())
+    np.testing.assert_array_equal(res[True][0], res[False][0])
+    np.testing.assert_allclose(res[True][1], res[False][1], rtol=1e-6)  # per-tile partial sums
+    np.testing.assert_allclose(res[True][2], res[False][2], rtol=1e-5,
+                               atol=1e-6 * np.abs(res[False][2]).max())
