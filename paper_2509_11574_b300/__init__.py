@@ -487,7 +487,9 @@ class Adam:
 
 class RenderImages(torch.autograd.Function):
     """C*, D*, W_G of one view as differentiable outputs of the five parameter
-    tensors; the backward calls render_backward with dL/dC*, dL/dD*."""
+    tensors; the backward calls render_backward with dL/dC*, dL/dD*.  The
+    renderer's workspace holds this forward's state until the backward: one
+    forward in flight per renderer."""
 
     @staticmethod
     def forward(ctx, renderer: Renderer, view: View, means, log_scales, quats, logits, rgb):
@@ -495,8 +497,9 @@ class RenderImages(torch.autograd.Function):
                       rgb.detach())
         H, W = view.cam.height, view.cam.width
         dev = means.device
+        cdt = PREC_DTYPE[renderer.s.precision]
         out = dataclasses.replace(view, target_rgb=None, target_depth=None,
-                                  out_rgb=torch.empty(3, H, W, device=dev),
+                                  out_rgb=torch.empty(3, H, W, device=dev, dtype=cdt),
                                   out_depth=torch.empty(H, W, device=dev),
                                   out_weight=torch.empty(H, W, device=dev))
         renderer.forward(g, [out])
@@ -508,9 +511,10 @@ class RenderImages(torch.autograd.Function):
     def backward(ctx, d_rgb, d_depth, d_weight):
         g = ctx.g
         grads = g.zeros_like()
+        # upstream gradients are float32 whatever the colour storage type
         v = dataclasses.replace(ctx.view,
-                                grad_rgb=(d_rgb.contiguous() if d_rgb is not None
-                                          else torch.zeros_like(ctx.view.out_rgb)),
+                                grad_rgb=(d_rgb.float().contiguous() if d_rgb is not None
+                                          else torch.zeros_like(ctx.view.out_depth).expand(3, -1, -1).contiguous()),
                                 grad_depth=(d_depth.contiguous() if d_depth is not None
                                             else torch.zeros_like(ctx.view.out_depth)))
         ctx.renderer.backward(g, [v], grads)
