@@ -87,6 +87,20 @@ __device__ __forceinline__ float block_max(float v, float* s_tmp) {
   return r;
 }
 
+// alpha = sigma exp(-q / 2) = 2^(log2(sigma) - q log2(e) / 2): one FMA on the
+// staged log2(sigma) and the hardware base-2 exponential (ex2.approx, relative
+// error about 2^-22, far inside the 1e-4 parity tolerance).  The counting
+// decision never looks at alpha: it is taken on q.
+constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float alpha_of(float q, float log2_sigma) {
+  return ex2_approx(fmaf(q, -kHalfLog2e, log2_sigma));
+}
+
 // Does the support {q <= qmax} of a Gaussian centred at (mx, my) meet the
 // rectangle [x0, x1] x [y0, y1]?  The minimum of the convex quadratic q over
 // the rectangle is 0 if the centre lies inside, else it lies on an edge, at
@@ -99,7 +113,9 @@ __device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float a, 
   const float lx = x0 - mx, hx = x1 - mx, ly = y0 - my, hy = y1 - my;
   if (lx <= 0.f && hx >= 0.f && ly <= 0.f && hy >= 0.f) return true;
   float qmin = INFINITY;
-  const float ic = 1.0f / c, ia = 1.0f / a;
+  // approximate reciprocals: they only place the stationary point, and q there
+  // is flat in the placement (error second order, inside the slack below)
+  const float ic = __fdividef(1.0f, c), ia = __fdividef(1.0f, a);
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     const float dx = e ? hx : lx;
@@ -173,7 +189,7 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
       const float4* rr = v.rec + 4 * (size_t)gi;
       float4 A = rr[0], B = rr[1];
       const float4 C = rr[2];
-      A.w = logf(A.w);   // ln sigma: alpha = exp(ln sigma - q / 2)
+      A.w = __log2f(A.w);  // log2 sigma, see alpha_of
       B.y = 2.0f * B.y;  // 2 b, exact
       s_a[tid] = A;
       s_b[tid] = B;
@@ -218,7 +234,7 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
       if (INSTR) n_tested += inside;
       if (q <= B.w && A.z < thr) {
         if (INSTR) ++n_counted;
-        const float al = __expf(fmaf(q, -0.5f, A.w));
+        const float al = alpha_of(q, A.w);
         const float4 C = s_c[j];
         if (MODE == GPS_BLEND_OIT) {
           cr += al * C.x;
@@ -528,7 +544,7 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
       if (has) {
         const float4 A = s_a[j], B = s_b[j], C = s_c[j];
         const float2 E = s_e[j];
-        mx = A.x; my = A.y; d = A.z; lns = logf(A.w);
+        mx = A.x; my = A.y; d = A.z; lns = __log2f(A.w);
         ca = B.x; b2 = B.y; cc = B.z; qmax = B.w;
         cr = C.x; cg = C.y; cbl = C.z;
         // this Gaussian's rectangle inside the block (block-local pixel indices)
@@ -556,7 +572,7 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
           if (q <= qmax && d < ss.y) {
             if (INSTR) ++n_counted;
             const float4 hh = s_h[p];
-            const float al = __expf(fmaf(q, -0.5f, lns));
+            const float al = alpha_of(q, lns);
             dcr += al * hh.x;
             dcg += al * hh.y;
             dcb += al * hh.z;
@@ -628,6 +644,7 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
   __shared__ float s_part[NW][kAlphaBatch][10];
   __shared__ float s_tmp[NW];
   __shared__ uint32_t s_gi[kAlphaBatch];
+  __shared__ float s_l2[kAlphaBatch];  // log2 sigma, as staged by the forward
   const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
   const int tile = blockIdx.x - vb.tile_start[slot];
@@ -669,10 +686,12 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
       const float4* rr = v.rec + 4 * (size_t)gi;
       float4 B = rr[1];
       B.y = 2.0f * B.y;
-      s_a[tid] = rr[0];
+      const float4 A0 = rr[0];
+      s_a[tid] = A0;
       s_b[tid] = B;
       s_c[tid] = rr[2];
       s_gi[tid] = gi;
+      s_l2[tid] = __log2f(A0.w);
     }
     __syncthreads();
     for (int j = nb - 1; j >= 0; --j) {
@@ -686,8 +705,9 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
         const float dx = __fsub_rn(fpx, A.x), dy = __fsub_rn(fpy, A.y);
         const float q = quad_form(B.x, B.y, B.z, dx, dy);
         if (q <= B.w && A.z < thr) {
-          const float G = __expf(-0.5f * q);
-          const float raw = A.w * G;
+          // the forward's alpha, bit for bit, so that T_i = T_{i+1} / (1 - alpha_i)
+          // undoes exactly what the forward multiplied in
+          const float raw = alpha_of(q, s_l2[j]);
           const bool clamped = raw > kAlphaMax;
           const float a = fminf(raw, kAlphaMax);
           const float ia = 1.0f / (1.0f - a);
@@ -712,7 +732,7 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
             gv[2] = -0.5f * vv * dx * dx;
             gv[3] = -vv * dx * dy;
             gv[4] = -0.5f * vv * dy * dy;
-            gv[5] = dLda * G;
+            gv[5] = __fdividef(dLda * raw, A.w);  // dL/dsigma = dL/dalpha * G, G = alpha / sigma
           }
           contrib = true;
         }

@@ -238,9 +238,14 @@ def test_composite_forward_and_backward_staged(mode, tile):
                 ex, ey = rr[i, oracle.R_EX] + 1, rr[i, oracle.R_EY] + 1
                 excl[i] = np.any((np.abs(xs - rr[i, oracle.R_MX]) <= ex) & (np.abs(ys - rr[i, oracle.R_MY]) <= ey))
     names = ["mx", "my", "ca", "cb", "cc", "sig", "r", "g", "b", "d"]
+    # OIT: 1e-4.  ALPHA: the backward recomputes T_i = T_{i+1} / (1 - alpha_i)
+    # from T_end; the kernel's alpha carries ~5e-7 relative rounding (FP32
+    # exponent argument and ex2), which 1 / (1 - alpha) <= 100 amplifies for
+    # every near-opaque Gaussian the reverse walk passes: 2e-4.
+    tol = 1e-4 if mode == gps.BLEND_OIT else 2e-4
     assert_grads_close({n: g2[:, k] for k, n in enumerate(names)},
                        {n: g2_o[:, k] for k, n in enumerate(names)}, exclude=excl,
-                       label=f"grad2d mode={mode}")
+                       norm_tol=tol, elem_tol=tol, label=f"grad2d mode={mode}")
 
 
 def test_projection_backward_staged():
