@@ -74,6 +74,28 @@ __device__ __forceinline__ uint32_t depth_cut(const unsigned long long* __restri
   return lo;
 }
 
+// The same cut computed by the whole CTA in two rounds of independent loads
+// (a binary search is a chain of dependent ones): round 1 samples every
+// step-th key, round 2 scans the one step that holds the cut.  All NT threads
+// call it; lists longer than NT^2 fall back to the binary search.
+template <int NT>
+__device__ __forceinline__ uint32_t depth_cut_block(const unsigned long long* __restrict__ keys,
+                                                   uint32_t lo, uint32_t hi, float thr) {
+  const uint32_t n = hi - lo;
+  if (!(thr > 0.0f) || n == 0) return lo;
+  if (n > (uint32_t)NT * NT) return depth_cut(keys, lo, hi, thr);
+  const uint32_t tb = __float_as_uint(thr);
+  const uint32_t step = (n + NT - 1) / NT;
+  const uint32_t p1 = lo + threadIdx.x * step;
+  const bool below1 = p1 < hi && (uint32_t)(keys[p1] >> 32) < tb;
+  const uint32_t c1 = (uint32_t)__syncthreads_count(below1);  // samples before the cut
+  if (c1 == 0) return lo;
+  const uint32_t a = lo + (c1 - 1) * step + 1, b = min(hi, lo + c1 * step);
+  const uint32_t p2 = a + threadIdx.x;
+  const bool below2 = p2 < b && (uint32_t)(keys[p2] >> 32) < tb;
+  return a + (uint32_t)__syncthreads_count(below2);
+}
+
 template <int NT>
 __device__ __forceinline__ float block_max(float v, float* s_tmp) {
   v = warp_max(v);
@@ -167,10 +189,12 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
     dt = __ldg(v.Dt + pix);
   }
   const float thr = inside ? depth_threshold(dt, eps) : -INFINITY;
+  const uint2 r = v.tile_ranges[tile];
+  // the first batch's key is fetched before the cut is known (it lies in the list)
+  uint32_t gi_next = r.x + tid < r.y ? (uint32_t)v.keys[r.x + tid] : 0u;
   const float wthr = warp_max(thr);
   const float bthr = block_max<NT>(thr, s_tmp);
-  const uint2 r = v.tile_ranges[tile];
-  const uint32_t end = depth_cut(v.keys, r.x, r.y, bthr);
+  const uint32_t end = depth_cut_block<NT>(v.keys, r.x, r.y, bthr);
   // this warp's pixel block, in image coordinates
   const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
   const float by0 = (float)(ty * TH + oy), by1 = by0 + 3.0f;
@@ -184,8 +208,10 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
     __syncthreads();
     if (__syncthreads_and(MODE == GPS_BLEND_ALPHA ? (done || wdone) : wdone)) break;
     const uint32_t k = b + tid;
+    const uint32_t gi = gi_next;
+    // next batch's key, in flight while this batch is staged and evaluated
+    gi_next = k + NT < r.y ? (uint32_t)v.keys[k + NT] : 0u;
     if (k < end) {
-      const uint32_t gi = (uint32_t)v.keys[k];
       const float4* rr = v.rec + 4 * (size_t)gi;
       float4 A = rr[0], B = rr[1];
       const float4 C = rr[2];
@@ -232,17 +258,23 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
       const float4 A = s_a[j], B = s_b[j];
       const float q = quad_form(B.x, B.y, B.z, __fsub_rn(fpx, A.x), __fsub_rn(fpy, A.y));
       if (INSTR) n_tested += inside;
-      if (q <= B.w && A.z < thr) {
+      const bool counted = q <= B.w && A.z < thr;
+      if (MODE == GPS_BLEND_OIT) {
+        // branch-free: a pixel that does not count adds alpha = 0 (exactly
+        // the same sums), and the warp never splits on the decision
+        if (INSTR) n_counted += counted;
+        const float al = counted ? alpha_of(q, A.w) : 0.0f;
+        const float4 C = s_c[j];
+        cr = fmaf(al, C.x, cr);
+        cg = fmaf(al, C.y, cg);
+        cb = fmaf(al, C.z, cb);
+        wsum += al;
+        zsum = fmaf(al, A.z, zsum);
+      } else if (counted) {
         if (INSTR) ++n_counted;
         const float al = alpha_of(q, A.w);
         const float4 C = s_c[j];
-        if (MODE == GPS_BLEND_OIT) {
-          cr += al * C.x;
-          cg += al * C.y;
-          cb += al * C.z;
-          wsum += al;
-          zsum += al * A.z;
-        } else if (!done) {
+        if (!done) {
           const float a = fminf(al, kAlphaMax);
           const float test = T * (1.0f - a);
           if (test < kTMin) {
@@ -479,10 +511,11 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
   }
   s_h[tid] = h;
   s_s[tid] = make_float2(sv, thr);
+  const uint2 r = v.tile_ranges[tile];
+  uint32_t gi_next = tid < NB && r.x + tid < r.y ? (uint32_t)v.keys[r.x + tid] : 0u;
   const float wthr = warp_max(thr);
   const float bthr = block_max<NT>(thr, s_tmp);
-  const uint2 r = v.tile_ranges[tile];
-  const uint32_t end = depth_cut(v.keys, r.x, r.y, bthr);
+  const uint32_t end = depth_cut_block<NT>(v.keys, r.x, r.y, bthr);
   const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
   const float by0 = (float)(ty * TH + oy), by1 = by0 + 3.0f;
   const int blk = warp * 32;  // this warp's pixels in s_h / s_s
@@ -491,8 +524,9 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
   for (uint32_t b = r.x; b < end; b += NB) {
     __syncthreads();
     if (__syncthreads_and(wdone)) break;
+    const uint32_t gi = gi_next;
+    if (tid < NB) gi_next = b + NB + tid < r.y ? (uint32_t)v.keys[b + NB + tid] : 0u;
     if (tid < NB && b + tid < end) {
-      const uint32_t gi = (uint32_t)v.keys[b + tid];
       const float4* rr = v.rec + 4 * (size_t)gi;
       float4 B = rr[1];
       const float4 C = rr[2];
@@ -562,33 +596,44 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
         // the dy terms of quad_form, hoisted out of the row (same roundings)
         const float t1 = __fmul_rn(b2, dy);
         const float s3 = __fmul_rn(__fmul_rn(cc, dy), dy);
+        // row sums of v, v dx, v dx^2; the dy moments follow per row
+        float ra = 0.f, rx = 0.f, rxx = 0.f;
         float fx = bx0 + (float)ux0;
         for (int kx = ux0; kx <= ux1; ++kx, fx += 1.0f) {
           const int p = blk + ky * 8 + kx;
           const float2 ss = s_s[p];
           const float dx = __fsub_rn(fx, mx);
           const float q = __fmaf_rn(dx, __fmaf_rn(ca, dx, t1), s3);
-          if (INSTR) n_tested += has && kx >= kx0 && kx <= kx1 && ky >= ky0 && ky <= ky1;
-          if (q <= qmax && d < ss.y) {
-            if (INSTR) ++n_counted;
+          const bool counted = q <= qmax && d < ss.y;
+          if (INSTR) {
+            n_tested += has && kx >= kx0 && kx <= kx1 && ky >= ky0 && ky <= ky1;
+            n_counted += counted;
+          }
+          // the loop bounds are warp-uniform: skip the pixel only when no
+          // lane counts it, otherwise run without splitting the warp (a lane
+          // that does not count adds alpha = 0)
+          if (__any_sync(0xffffffffu, counted)) {
             const float4 hh = s_h[p];
-            const float al = alpha_of(q, lns);
-            dcr += al * hh.x;
-            dcg += al * hh.y;
-            dcb += al * hh.z;
-            dd += al * hh.w;
+            const float al = counted ? alpha_of(q, lns) : 0.0f;
+            dcr = fmaf(al, hh.x, dcr);
+            dcg = fmaf(al, hh.y, dcg);
+            dcb = fmaf(al, hh.z, dcb);
+            dd = fmaf(al, hh.w, dd);
             const float dLda =
                 fmaf(hh.x, cr, fmaf(hh.y, cg, fmaf(hh.z, cbl, fmaf(hh.w, d, -ss.x))));
             const float vv = dLda * al;
-            sa += vv;
-            const float tx_ = vv * dx, ty_ = vv * dy;
-            sx += tx_;
-            sy += ty_;
-            sxx += tx_ * dx;
-            sxy += tx_ * dy;
-            syy += ty_ * dy;
+            ra += vv;
+            const float tx_ = vv * dx;
+            rx += tx_;
+            rxx = fmaf(tx_, dx, rxx);
           }
         }
+        sa += ra;
+        sx += rx;
+        sxx += rxx;
+        sy = fmaf(ra, dy, sy);
+        sxy = fmaf(rx, dy, sxy);
+        syy = fmaf(ra * dy, dy, syy);
       }
       if (has) {
         float* o = s_part[warp][j];
