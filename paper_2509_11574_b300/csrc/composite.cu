@@ -574,59 +574,58 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
       const int j = has ? s_list[warp][t] : 0;
       float mx = 0.f, my = 0.f, d = 0.f, lns = 0.f, ca = 0.f, b2 = 0.f, cc = 0.f, qmax = -1.f;
       float cr = 0.f, cg = 0.f, cbl = 0.f;
-      int kx0 = 8, kx1 = -1, ky0 = 4, ky1 = -1;
+      int kx0 = 8, kx1 = -1, ky0 = 4, ky1 = -1;  // own rectangle (instrumented runs)
       if (has) {
         const float4 A = s_a[j], B = s_b[j], C = s_c[j];
-        const float2 E = s_e[j];
         mx = A.x; my = A.y; d = A.z; lns = __log2f(A.w);
         ca = B.x; b2 = B.y; cc = B.z; qmax = B.w;
         cr = C.x; cg = C.y; cbl = C.z;
-        // this Gaussian's rectangle inside the block (block-local pixel indices)
-        kx0 = max(0, (int)ceilf(mx - E.x - bx0));
-        kx1 = min(7, (int)floorf(mx + E.x - bx0));
-        ky0 = max(0, (int)ceilf(my - E.y - by0));
-        ky1 = min(3, (int)floorf(my + E.y - by0));
+        if (INSTR) {
+          const float2 E = s_e[j];
+          kx0 = max(0, (int)ceilf(mx - E.x - bx0));
+          kx1 = min(7, (int)floorf(mx + E.x - bx0));
+          ky0 = max(0, (int)ceilf(my - E.y - by0));
+          ky1 = min(3, (int)floorf(my + E.y - by0));
+        }
       }
-      const int ux0 = warp_min_i(kx0), ux1 = warp_max_i(kx1);
-      const int uy0 = warp_min_i(ky0), uy1 = warp_max_i(ky1);
+      // every lane walks all 32 pixels of the block, unrolled and branch-free:
+      // a pixel outside a Gaussian's support fails q <= qmax and adds alpha = 0
+      // (cheaper than bounding each group's loop by the union of its
+      // Gaussians' rectangles)
       float dcr = 0.f, dcg = 0.f, dcb = 0.f, dd = 0.f, sa = 0.f;
       float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-      for (int ky = uy0; ky <= uy1; ++ky) {
+#pragma unroll 2
+      for (int ky = 0; ky < 4; ++ky) {
         const float dy = __fsub_rn(by0 + (float)ky, my);
         // the dy terms of quad_form, hoisted out of the row (same roundings)
         const float t1 = __fmul_rn(b2, dy);
         const float s3 = __fmul_rn(__fmul_rn(cc, dy), dy);
         // row sums of v, v dx, v dx^2; the dy moments follow per row
         float ra = 0.f, rx = 0.f, rxx = 0.f;
-        float fx = bx0 + (float)ux0;
-        for (int kx = ux0; kx <= ux1; ++kx, fx += 1.0f) {
+#pragma unroll
+        for (int kx = 0; kx < 8; ++kx) {
           const int p = blk + ky * 8 + kx;
           const float2 ss = s_s[p];
-          const float dx = __fsub_rn(fx, mx);
+          const float dx = __fsub_rn(bx0 + (float)kx, mx);
           const float q = __fmaf_rn(dx, __fmaf_rn(ca, dx, t1), s3);
           const bool counted = q <= qmax && d < ss.y;
           if (INSTR) {
             n_tested += has && kx >= kx0 && kx <= kx1 && ky >= ky0 && ky <= ky1;
             n_counted += counted;
           }
-          // the loop bounds are warp-uniform: skip the pixel only when no
-          // lane counts it, otherwise run without splitting the warp (a lane
-          // that does not count adds alpha = 0)
-          if (__any_sync(0xffffffffu, counted)) {
-            const float4 hh = s_h[p];
-            const float al = counted ? alpha_of(q, lns) : 0.0f;
-            dcr = fmaf(al, hh.x, dcr);
-            dcg = fmaf(al, hh.y, dcg);
-            dcb = fmaf(al, hh.z, dcb);
-            dd = fmaf(al, hh.w, dd);
-            const float dLda =
-                fmaf(hh.x, cr, fmaf(hh.y, cg, fmaf(hh.z, cbl, fmaf(hh.w, d, -ss.x))));
-            const float vv = dLda * al;
-            ra += vv;
-            const float tx_ = vv * dx;
-            rx += tx_;
-            rxx = fmaf(tx_, dx, rxx);
-          }
+          const float4 hh = s_h[p];
+          const float al = counted ? alpha_of(q, lns) : 0.0f;
+          dcr = fmaf(al, hh.x, dcr);
+          dcg = fmaf(al, hh.y, dcg);
+          dcb = fmaf(al, hh.z, dcb);
+          dd = fmaf(al, hh.w, dd);
+          const float dLda =
+              fmaf(hh.x, cr, fmaf(hh.y, cg, fmaf(hh.z, cbl, fmaf(hh.w, d, -ss.x))));
+          const float vv = dLda * al;
+          ra += vv;
+          const float tx_ = vv * dx;
+          rx += tx_;
+          rxx = fmaf(tx_, dx, rxx);
         }
         sa += ra;
         sx += rx;
