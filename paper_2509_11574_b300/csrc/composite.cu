@@ -352,6 +352,191 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
   }
 }
 
+// OIT forward with two pixels per lane: warp w covers the 8 x 8 pixel block
+// (w % (TW/8), w / (TW/8)) of the tile, lane l the pixels (l % 8, l / 8) and
+// (l % 8, l / 8 + 4) of it.  Each staged record is read once for both pixels,
+// which share dx.  Otherwise as composite_fwd_kernel (same decisions, same
+// per-pixel summation order, so the same images bit for bit).
+template <int TW, int TH, bool INSTR>
+__global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
+    const __grid_constant__ ViewBatch vb, float eps, int has_tgt) {
+  constexpr int NTT = TW * TH / 2;  // threads
+  constexpr int NW = NTT / 32;
+  constexpr int NB = 2 * NTT;       // staged entries per batch
+  constexpr int BX = TW / 8;
+  __shared__ float4 s_a[NB], s_b[NB], s_c[NB];
+  __shared__ float2 s_e[NB];
+  __shared__ uint8_t s_list[NW][NB];
+  __shared__ float s_tmp[NW * 3];
+  const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
+  const ViewDev& v = vb.v[vb.order[slot]];
+  const int tile = blockIdx.x - vb.tile_start[slot];
+  const int W = v.cam.W, H = v.cam.H;
+  const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ox = (warp % BX) * 8, oy = (warp / BX) * 8;
+  const int px = tx * TW + ox + (lane & 7);
+  const int py0 = ty * TH + oy + (lane >> 3), py1 = py0 + 4;
+  const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
+  const long long npx = (long long)W * H;
+  const long long pix0 = (long long)py0 * W + px, pix1 = (long long)py1 * W + px;
+  float ct[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, dt[2] = {0.f, 0.f};
+  if (in0) {
+    for (int c = 0; c < 3; ++c) ct[0][c] = ld_col(v.Ct, c * npx + pix0, v.prec);
+    dt[0] = __ldg(v.Dt + pix0);
+  }
+  if (in1) {
+    for (int c = 0; c < 3; ++c) ct[1][c] = ld_col(v.Ct, c * npx + pix1, v.prec);
+    dt[1] = __ldg(v.Dt + pix1);
+  }
+  const float thr0 = in0 ? depth_threshold(dt[0], eps) : -INFINITY;
+  const float thr1 = in1 ? depth_threshold(dt[1], eps) : -INFINITY;
+  const uint2 r = v.tile_ranges[tile];
+  uint32_t gi_next0 = r.x + tid < r.y ? (uint32_t)v.keys[r.x + tid] : 0u;
+  uint32_t gi_next1 = r.x + NTT + tid < r.y ? (uint32_t)v.keys[r.x + NTT + tid] : 0u;
+  const float wthr = warp_max(fmaxf(thr0, thr1));
+  const float bthr = block_max<NTT>(fmaxf(thr0, thr1), s_tmp);
+  const uint32_t end = depth_cut_block<NTT>(v.keys, r.x, r.y, bthr);
+  const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
+  const float by0 = (float)(ty * TH + oy), by1 = by0 + 7.0f;
+  const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
+  float acc[2][5] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};  // r, g, b, W_G, Z
+  bool wdone = wthr == -INFINITY;
+  unsigned n_tested = 0, n_counted = 0;
+  for (uint32_t b = r.x; b < end; b += NB) {
+    __syncthreads();
+    if (__syncthreads_and(wdone)) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t k = b + h * NTT + tid;
+      const uint32_t gi = h ? gi_next1 : gi_next0;
+      const uint32_t kn = k + NB;
+      const uint32_t nxt = kn < r.y ? (uint32_t)v.keys[kn] : 0u;
+      if (h) gi_next1 = nxt; else gi_next0 = nxt;
+      if (k < end) {
+        const float4* rr = v.rec + 4 * (size_t)gi;
+        float4 A = rr[0], B = rr[1];
+        const float4 C = rr[2];
+        A.w = __log2f(A.w);  // log2 sigma, see alpha_of
+        B.y = 2.0f * B.y;    // 2 b, exact
+        const int e = h * NTT + tid;
+        s_a[e] = A;
+        s_b[e] = B;
+        s_c[e] = C;
+        s_e[e] = make_float2(C.w, rr[3].x);
+      }
+    }
+    __syncthreads();
+    const int nb = (int)min((uint32_t)NB, end - b);
+    int cnt = 0;
+    if (!wdone) {
+      for (int j0 = 0; j0 < nb; j0 += 32) {
+        const int j = j0 + lane;
+        bool stop = false, ok = false;
+        if (j < nb) {
+          const float4 A = s_a[j];
+          const float2 E = s_e[j];
+          stop = A.z >= wthr;
+          ok = A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 && A.y - E.y <= by1;
+          if (ok) {
+            const float4 B = s_b[j];
+            ok = ellipse_meets_rect(A.x, A.y, B.x, 0.5f * B.y, B.z, B.w, bx0, bx1, by0, by1);
+          }
+        }
+        const unsigned sb = __ballot_sync(0xffffffffu, stop);
+        unsigned ob = __ballot_sync(0xffffffffu, ok);
+        if (sb) ob &= (sb & (0u - sb)) - 1u;  // keep the entries before the first stop
+        if ((ob >> lane) & 1u) s_list[warp][cnt + __popc(ob & ((1u << lane) - 1u))] = (uint8_t)j;
+        cnt += __popc(ob);
+        if (sb) {
+          wdone = true;
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    for (int t = 0; t < cnt; ++t) {
+      const int j = s_list[warp][t];
+      const float4 A = s_a[j], B = s_b[j];
+      const float4 C = s_c[j];
+      const float dx = __fsub_rn(fpx, A.x);
+      const float q0 = quad_form(B.x, B.y, B.z, dx, __fsub_rn(fpy0, A.y));
+      const float q1 = quad_form(B.x, B.y, B.z, dx, __fsub_rn(fpy1, A.y));
+      const bool c0 = q0 <= B.w && A.z < thr0, c1 = q1 <= B.w && A.z < thr1;
+      if (INSTR) {
+        n_tested += in0 + in1;
+        n_counted += c0 + c1;
+      }
+      const float a0 = c0 ? alpha_of(q0, A.w) : 0.0f;
+      const float a1 = c1 ? alpha_of(q1, A.w) : 0.0f;
+      acc[0][0] = fmaf(a0, C.x, acc[0][0]);
+      acc[0][1] = fmaf(a0, C.y, acc[0][1]);
+      acc[0][2] = fmaf(a0, C.z, acc[0][2]);
+      acc[0][3] += a0;
+      acc[0][4] = fmaf(a0, A.z, acc[0][4]);
+      acc[1][0] = fmaf(a1, C.x, acc[1][0]);
+      acc[1][1] = fmaf(a1, C.y, acc[1][1]);
+      acc[1][2] = fmaf(a1, C.z, acc[1][2]);
+      acc[1][3] += a1;
+      acc[1][4] = fmaf(a1, A.z, acc[1][4]);
+    }
+  }
+  if (INSTR) add_counters(v, 0, n_tested, n_counted);
+  float lr = 0.f, ld = 0.f, nv = 0.f;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const bool in = h ? in1 : in0;
+    const long long pix = h ? pix1 : pix0;
+    const float iN = 1.0f / (1.0f + acc[h][3]);
+    const float o0 = (ct[h][0] + acc[h][0]) * iN;
+    const float o1 = (ct[h][1] + acc[h][1]) * iN;
+    const float o2 = (ct[h][2] + acc[h][2]) * iN;
+    const float od = (dt[h] + acc[h][4]) * iN;
+    if (in) {
+      v.pix_a[pix] = make_float4(o0, o1, o2, od);
+      v.pix_b[pix] = make_float4(acc[h][3], __uint_as_float(r.x), 0.f, 0.f);
+      if (v.out_rgb) {
+        st_col(v.out_rgb, pix, v.prec, o0);
+        st_col(v.out_rgb, npx + pix, v.prec, o1);
+        st_col(v.out_rgb, 2 * npx + pix, v.prec, o2);
+      }
+      if (v.out_depth) v.out_depth[pix] = od;
+      if (v.out_weight) v.out_weight[pix] = acc[h][3];
+      if (has_tgt) {
+        const float dk = __ldg(v.Dtgt + pix);
+        if (dk > 0.0f && dt[h] > 0.0f) {
+          lr += fabsf(o0 - ld_col(v.Ctgt, pix, v.prec)) +
+                fabsf(o1 - ld_col(v.Ctgt, npx + pix, v.prec)) +
+                fabsf(o2 - ld_col(v.Ctgt, 2 * npx + pix, v.prec));
+          ld += fabsf(od - dk);
+          nv += 1.0f;
+        }
+      }
+    }
+  }
+  if (has_tgt) {
+    lr = warp_sum(lr);
+    ld = warp_sum(ld);
+    nv = warp_sum(nv);
+    __syncthreads();
+    if (lane == 0) {
+      s_tmp[warp * 3 + 0] = lr;
+      s_tmp[warp * 3 + 1] = ld;
+      s_tmp[warp * 3 + 2] = nv;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float a = 0.f, bsum = 0.f, c = 0.f;
+      for (int k = 0; k < NW; ++k) {
+        a += s_tmp[k * 3];
+        bsum += s_tmp[k * 3 + 1];
+        c += s_tmp[k * 3 + 2];
+      }
+      v.tile_partials[tile] = make_float4(a, bsum, c, 0.f);
+    }
+  }
+}
+
 // Per-view loss from the tile partial sums, summed in a fixed order: each
 // thread adds a strided subset, then a fixed shuffle tree and warp order.
 // scalars: [0] view loss, [1] sum |C* - C|, [2] sum |D* - D|, [3] N_valid.
@@ -855,9 +1040,9 @@ static cudaError_t fwd_tw(const ViewBatch& vb, float eps, int mode, int has_tgt,
   if (items <= 0) return cudaSuccess;
   if (mode == GPS_BLEND_OIT) {
     if (instr)
-      composite_fwd_kernel<TW, TH, GPS_BLEND_OIT, true><<<items, TW * TH, 0, st>>>(vb, eps, has_tgt);
+      composite_fwd_oit2_kernel<TW, TH, true><<<items, TW * TH / 2, 0, st>>>(vb, eps, has_tgt);
     else
-      composite_fwd_kernel<TW, TH, GPS_BLEND_OIT, false><<<items, TW * TH, 0, st>>>(vb, eps, has_tgt);
+      composite_fwd_oit2_kernel<TW, TH, false><<<items, TW * TH / 2, 0, st>>>(vb, eps, has_tgt);
   } else {
     if (instr)
       composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, true><<<items, TW * TH, 0, st>>>(vb, eps, has_tgt);
