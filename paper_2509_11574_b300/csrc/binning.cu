@@ -137,9 +137,7 @@ __global__ void __launch_bounds__(256) emit_super_kernel(int M, const __grid_con
 }
 
 // ------------------------------------------------------ per-super-tile sort
-constexpr int kSortThreads = 256;
 constexpr int kPerThread = 8;
-constexpr int kSortCap = kSortThreads * kPerThread * 2;  // keys sorted in shared memory
 
 __device__ __forceinline__ void cswap(unsigned long long& a, unsigned long long& b) {
   const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
@@ -157,50 +155,64 @@ __device__ __forceinline__ void sort8(unsigned long long (&k)[8]) {
   cswap(k[1], k[2]); cswap(k[3], k[4]); cswap(k[5], k[6]);
 }
 
-// Output slice [d0, d0 + cnt) of the merge of sorted runs A[0, na), B[0, nb)
-// (keys are distinct: the index sits in the low bits).
-__device__ __forceinline__ void merge_slice(const unsigned long long* A, int na,
-                                            const unsigned long long* B, int nb, int d0, int cnt,
-                                            unsigned long long* out) {
+// Shared-memory position of key i: one 8-byte pad after every 8 keys, so the
+// runs of 8 keys that neighbouring threads own start 72 bytes apart and their
+// 64-bit accesses fall in different banks (unpadded they would collide 16-way).
+__device__ __forceinline__ int spad(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int spad_size(int n) { return n + n / 8; }
+
+// Output slice [d0, d0 + cnt) of the merge of the sorted runs at positions
+// [a0, a0 + na) and [b0, b0 + nb) of `src` (P: padded shared-memory layout or
+// plain global memory), written from position o0 of `dst`.  Keys are distinct
+// (the index sits in the low bits).
+template <bool P>
+__device__ __forceinline__ void merge_slice(const unsigned long long* src, int a0, int na, int b0,
+                                            int nb, int d0, int cnt, unsigned long long* dst,
+                                            int o0) {
+  auto at = [&](int i) { return P ? src[spad(i)] : src[i]; };
   int lo = max(0, d0 - nb), hi = min(d0, na);
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (A[mid] < B[d0 - mid - 1]) lo = mid + 1;
+    if (at(a0 + mid) < at(b0 + d0 - mid - 1)) lo = mid + 1;
     else hi = mid;
   }
   int i = lo, j = d0 - lo;
   for (int d = 0; d < cnt; ++d) {
-    const bool takeA = j >= nb || (i < na && A[i] < B[j]);
-    out[d] = takeA ? A[i++] : B[j++];
+    const bool takeA = j >= nb || (i < na && at(a0 + i) < at(b0 + j));
+    const unsigned long long k = takeA ? at(a0 + i++) : at(b0 + j++);
+    if (P) dst[spad(o0 + d)] = k;
+    else dst[o0 + d] = k;
   }
 }
 
-// Sorts seg[0, n) (n <= kSortCap/2 for the buffer pair) using buf0/buf1 of
-// kSortCap/2 keys each; returns the buffer that holds the result.
+// Sorts seg[0, n) (n <= C = T * kPerThread) with T threads in the padded
+// shared buffers buf0 / buf1 (spad_size(C) keys each); returns the buffer that
+// holds the sorted keys (padded layout).
+template <int T>
 __device__ unsigned long long* block_merge_sort(const unsigned long long* __restrict__ seg, int n,
                                                 unsigned long long* buf0, unsigned long long* buf1) {
   const int tid = threadIdx.x;
   const int n8 = (n + 7) & ~7;
-  for (int t = tid; t * kPerThread < n8; t += kSortThreads) {
+  // coalesced load, then each thread sorts its 8 keys in registers
+  for (int i = tid; i < n8; i += T) buf1[spad(i)] = i < n ? seg[i] : ~0ull;
+  __syncthreads();
+  for (int t = tid; t * kPerThread < n8; t += T) {
     unsigned long long k[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int idx = t * kPerThread + q;
-      k[q] = idx < n ? seg[idx] : ~0ull;
-    }
+    for (int q = 0; q < 8; ++q) k[q] = buf1[spad(t * kPerThread + q)];
     sort8(k);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) buf0[t * kPerThread + q] = k[q];
+    for (int q = 0; q < 8; ++q) buf0[spad(t * kPerThread + q)] = k[q];
   }
   __syncthreads();
   unsigned long long* src = buf0;
   unsigned long long* dst = buf1;
   for (int w = 8; w < n8; w <<= 1) {
-    for (int t = tid; t * kPerThread < n8; t += kSortThreads) {
+    for (int t = tid; t * kPerThread < n8; t += T) {
       const int d = t * kPerThread;
       const int p = d / (2 * w), base = p * 2 * w;
       const int na = min(w, n8 - base), nb = max(0, min(w, n8 - base - w));
-      merge_slice(src + base, na, src + base + na, nb, d - base, kPerThread, dst + d);
+      merge_slice<true>(src, base, na, base + na, nb, d - base, kPerThread, dst, d);
     }
     __syncthreads();
     unsigned long long* tmp = src;
@@ -210,28 +222,30 @@ __device__ unsigned long long* block_merge_sort(const unsigned long long* __rest
   return src;
 }
 
-// Chunked sort for segments larger than the shared buffers: sort chunks in
-// shared memory, then merge runs pairwise through the global scratch buffer.
+// Chunked sort for segments larger than the shared buffers: sort chunks of C
+// keys in shared memory, then merge runs pairwise through the global scratch.
+// Returns the global buffer (seg or seg_tmp) that holds the result.
+template <int T>
 __device__ unsigned long long* large_sort(unsigned long long* seg, unsigned long long* seg_tmp,
                                           int n, unsigned long long* buf0,
                                           unsigned long long* buf1) {
-  constexpr int C = kSortCap / 2;
+  constexpr int C = T * kPerThread;
   const int tid = threadIdx.x;
   for (int base = 0; base < n; base += C) {
     const int len = min(C, n - base);
-    unsigned long long* r = block_merge_sort(seg + base, len, buf0, buf1);
-    for (int i = tid; i < len; i += kSortThreads) seg[base + i] = r[i];
+    unsigned long long* r = block_merge_sort<T>(seg + base, len, buf0, buf1);
+    for (int i = tid; i < len; i += T) seg[base + i] = r[spad(i)];
     __syncthreads();
   }
   unsigned long long* src = seg;
   unsigned long long* dst = seg_tmp;
   for (int w = C; w < n; w <<= 1) {
     const int per = 8;
-    for (int t = tid; t * per < n; t += kSortThreads) {
+    for (int t = tid; t * per < n; t += T) {
       const int d = t * per;
       const int p = d / (2 * w), base = p * 2 * w;
       const int na = min(w, n - base), nb = max(0, min(w, n - base - w));
-      merge_slice(src + base, na, src + base + na, nb, d - base, min(per, n - d), dst + d);
+      merge_slice<false>(src, base, na, base + na, nb, d - base, min(per, n - d), dst, d);
     }
     __syncthreads();
     unsigned long long* tmp = src;
@@ -246,10 +260,14 @@ __device__ __forceinline__ unsigned long long pack_rect(int x0, int x1, int y0, 
          ((unsigned long long)(uint16_t)y0 << 32) | ((unsigned long long)(uint16_t)y1 << 48);
 }
 
-// One CTA per (view, super-tile): sort its segment in place and write, beside
-// each sorted key, its Gaussian's pixel rectangle (x0, x1, y0, y1 as 4 x u16).
-__global__ void __launch_bounds__(kSortThreads) sort_super_kernel(const __grid_constant__ ViewBatch vb) {
-  __shared__ unsigned long long buf[kSortCap];
+// One CTA of T threads per (view, super-tile): sort its segment in place and
+// write, beside each sorted key, its Gaussian's pixel rectangle (x0, x1, y0,
+// y1 as 4 x u16).  T = 128 for 16-px super-tiles (about 600 keys each at
+// 640 x 480 with 100k Gaussians), 256 for 32-px ones.
+template <int T>
+__global__ void __launch_bounds__(T) sort_super_kernel(const __grid_constant__ ViewBatch vb) {
+  constexpr int C = T * kPerThread;
+  __shared__ unsigned long long buf[2 * spad_size(C)];
   const int slot = batch_slot(vb.sup_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
   unsigned long long* __restrict__ sup_keys = v.sup_keys;
@@ -260,19 +278,22 @@ __global__ void __launch_bounds__(kSortThreads) sort_super_kernel(const __grid_c
   const int n = (int)(r.y - r.x);
   if (n <= 0) return;
   const unsigned long long* sorted;
-  if (n <= kSortCap / 2)
-    sorted = block_merge_sort(sup_keys + r.x, n, buf, buf + kSortCap / 2);
-  else
-    sorted = large_sort(sup_keys + r.x, v.sup_tmp + r.x, n, buf, buf + kSortCap / 2);
+  bool padded = true;
+  if (n <= C) {
+    sorted = block_merge_sort<T>(sup_keys + r.x, n, buf, buf + spad_size(C));
+  } else {
+    sorted = large_sort<T>(sup_keys + r.x, v.sup_tmp + r.x, n, buf, buf + spad_size(C));
+    padded = false;
+  }
   __syncthreads();
-  for (int k = threadIdx.x; k < n; k += kSortThreads) {
-    const unsigned long long key = sorted[k];
+  for (int k = threadIdx.x; k < n; k += T) {
+    const unsigned long long key = padded ? sorted[spad(k)] : sorted[k];
     const uint32_t gi = (uint32_t)key;
     const float4 a = rec[4 * (size_t)gi], c = rec[4 * (size_t)gi + 2], e = rec[4 * (size_t)gi + 3];
     int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
     record_rect(a.x, a.y, c.w, e.x, W, H, x0, x1, y0, y1);
     sup_rect[r.x + k] = pack_rect(x0, x1, y0, y1);
-    if (sorted != sup_keys + r.x) sup_keys[r.x + k] = key;
+    if (padded || sorted != sup_keys + r.x) sup_keys[r.x + k] = key;
   }
 }
 
@@ -353,7 +374,8 @@ cudaError_t launch_emit_super(int M, const ViewBatch& vb, int max_nsup, cudaStre
 cudaError_t launch_sort_super(const ViewBatch& vb, cudaStream_t st) {
   const int items = vb.sup_start[vb.n];
   if (items <= 0) return cudaSuccess;
-  sort_super_kernel<<<items, kSortThreads, 0, st>>>(vb);
+  if (vb.v[0].sup_shift > 4) sort_super_kernel<256><<<items, 256, 0, st>>>(vb);
+  else sort_super_kernel<128><<<items, 128, 0, st>>>(vb);
   return cudaGetLastError();
 }
 
