@@ -56,6 +56,9 @@ def parse():
                     help=f"frames of the sequence (room: {N_FRAMES}, large: {N_FRAMES_LARGE})")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="storage type of the colour images C_t, C_k, C*")
+    ap.add_argument("--schedule", default="tiles", choices=["tiles", "per-gaussian"],
+                    help="per-gaussian: the paper's sort-free form (unsorted tile lists, "
+                         "one warp per Gaussian in the backward; OIT only)")
     ap.add_argument("--workload", default="room", choices=["room", "large", "multiview"],
                     help="room: 640x480, 100k Gaussians (the headline); large: 1280x720, "
                          "5.12 m room, 512^3 TSDF, 1M Gaussians; multiview: 8 mixed-resolution "
@@ -171,6 +174,7 @@ def workload_config(args, w):
                         f"{s.nx}^3 TSDF at {100 * s.voxel:.0f} cm, {w.gaussians.M} Gaussians, "
                         f"{ITERS_PER_FRAME} iterations/frame",
             "blend": args.mode, "tile": args.tile, "colour_storage": args.precision,
+            "schedule": args.schedule,
             "form": "CUDA graph per frame", "l2": "256 MB buffer written between steps (untimed)"}
 
 
@@ -180,7 +184,7 @@ PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 class GpuPipeline:
     """Device-resident state of one replica and the per-frame step."""
 
-    def __init__(self, w, tile, mode, device, precision="fp32"):
+    def __init__(self, w, tile, mode, device, precision="fp32", schedule="tiles"):
         import torch
         import paper_2509_11574_b300 as gps
         self.gps, self.torch = gps, torch
@@ -203,7 +207,8 @@ class GpuPipeline:
         self.opt = gps.Adam(self.g, device_step=True)
         self.s = gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, near=w.near,
                               blend_mode=gps.BLEND_ALPHA if mode == "alpha" else gps.BLEND_OIT,
-                              tile=tile, pair_capacity=64 * w.gaussians.M, precision=prec)
+                              tile=tile, pair_capacity=64 * w.gaussians.M, precision=prec,
+                              schedule=1 if schedule == "per-gaussian" else 0)
         self.r = gps.Renderer(w.gaussians.M, self.cams[:1], self.s, device)
         self.Ct = torch.zeros(3, H, W, device=device, dtype=self.cdt)
         self.Dt = torch.zeros(H, W, device=device)
@@ -288,12 +293,14 @@ class GpuPipeline:
         return g
 
 
-def kernels_per_step(mode, tile):
+def kernels_per_step(mode, tile, schedule="tiles"):
     # fuse, raycast + per iteration: project, scan, emit, sort, [split into tiles
     # unless a tile is a whole 16-px super-tile], composite, finalize,
-    # composite_bwd, project_bwd, adam, step counter
+    # composite_bwd [per-Gaussian schedule: pixel terms + per-Gaussian], project_bwd,
+    # adam, step counter
     split = 0 if tuple(tile) == (16, 16) else 1
-    return 2 + ITERS_PER_FRAME * (10 + split)
+    pg = 1 if schedule == "per-gaussian" else 0
+    return 2 + ITERS_PER_FRAME * (10 + split + pg)
 
 
 def count_evaluations(pipe, k):
@@ -346,7 +353,7 @@ def run_ours(args, rank, world, local):
     t0 = time.time()
     w = make_workload(rank, args)
     gen_s = time.time() - t0
-    pipe = GpuPipeline(w, tile, args.mode, dev, args.precision)
+    pipe = GpuPipeline(w, tile, args.mode, dev, args.precision, args.schedule)
     tuned = None
     if args.tile == "auto":
         tuned = pipe.autotune()
@@ -519,7 +526,7 @@ def run_ours(args, rank, world, local):
         "hbm_model": {"bytes_per_iteration": it_bytes, "peak_gbs": hbm,
                       "frac_at_iteration_time": it_bytes / (it_ms * 1e-3) / 1e9 / hbm if it_ms else None},
         "roofline": roofline,
-        "clocks": clk, "gpu_launches": kernels_per_step(args.mode, tile) * K,
+        "clocks": clk, "gpu_launches": kernels_per_step(args.mode, tile, args.schedule) * K,
         "status": status, "last_frame_losses": losses[-3:], "wall_s": wall,
         "gen_s": gen_s, "gpu": props.name,
     }

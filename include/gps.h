@@ -68,6 +68,14 @@ extern "C" {
 #define GPS_PREC_FP16 1
 #define GPS_PREC_BF16 2
 
+/* work schedule of the second pass (GpsRenderSettings.schedule) */
+#define GPS_SCHEDULE_TILES 0        /* depth-sorted tile lists; tile-parallel backward      */
+#define GPS_SCHEDULE_PER_GAUSSIAN 1 /* OIT only, the paper's sort-free form (Sec. 3.1,
+                                       App. B): unsorted tile lists for the forward (no
+                                       depth cut), and a backward with one warp per
+                                       Gaussian walking its pixel rectangle in groups of
+                                       32 pixels; no atomics, deterministic            */
+
 /* stage mask (GpsRenderSettings.stages; 0 = all).  Tests use it to run one
    stage on inputs they wrote into the workspace themselves. */
 #define GPS_STAGE_PROJECT 1        /* records from Gaussian parameters       */
@@ -150,6 +158,7 @@ typedef struct GpsRenderSettings {
   int32_t stages;        /* GPS_STAGE_* mask, 0 = all                          */
   int32_t instrument;    /* 1: count Gaussian-pixel evaluations (slower; for
                             measurement runs) into the view scalars           */
+  int32_t schedule;      /* GPS_SCHEDULE_*                                     */
   int64_t pair_capacity; /* (super-tile, Gaussian) entries per view; 0 = 16 * M */
 } GpsRenderSettings;
 
@@ -195,6 +204,10 @@ typedef struct GpsWorkspaceLayout {
   size_t grad2d;        /* float [M][12]                                      */
   size_t pair_grads;    /* float [tiles per super-tile * pair_capacity][12]
                            (deterministic mode)                               */
+  size_t pix_grad;      /* float [H*W][8] per-pixel upstream terms of the
+                           per-Gaussian backward (GPS_SCHEDULE_PER_GAUSSIAN):
+                           dL/dC* / N, dL/dD* / N, sum dL/d(C*, D*) (C*, D*) / N,
+                           D_t + eps (or -inf if the pixel has no gradient)   */
   int32_t tiles_x, tiles_y, tile_w, tile_h, super_x, super_y;
   int32_t super_px;     /* super-tile edge in pixels (16, or 32 for 32-px-wide tiles) */
   int32_t reserved;

@@ -32,6 +32,7 @@ GPS_ERR_CUDA = -4
 GPS_ERR_TIMEOUT = -5
 BLEND_OIT, BLEND_ALPHA = 0, 1
 PREC_FP32, PREC_FP16, PREC_BF16 = 0, 1, 2
+SCHEDULE_TILES, SCHEDULE_PER_GAUSSIAN = 0, 1
 PREC_DTYPE = {PREC_FP32: torch.float32, PREC_FP16: torch.float16, PREC_BF16: torch.bfloat16}
 STAGE_PROJECT, STAGE_BIN, STAGE_COMPOSITE, STAGE_COMPOSITE_BWD, STAGE_PROJECT_BWD = 1, 2, 4, 8, 16
 
@@ -75,7 +76,7 @@ class GpsRenderSettings(ctypes.Structure):
     _fields_ = [("eps_depth", c_float), ("lambda_depth", c_float), ("near_plane", c_float),
                 ("blend_mode", c_int32), ("precision", c_int32), ("tile_w", c_int32),
                 ("tile_h", c_int32), ("deterministic", c_int32), ("stages", c_int32),
-                ("instrument", c_int32), ("pair_capacity", c_int64)]
+                ("instrument", c_int32), ("schedule", c_int32), ("pair_capacity", c_int64)]
 
 
 class GpsAdamHyper(ctypes.Structure):
@@ -89,6 +90,7 @@ class GpsWorkspaceLayout(ctypes.Structure):
                 ("tile_ranges", c_size_t),
                 ("pair_keys", c_size_t), ("pix_state", c_size_t), ("tile_partials", c_size_t),
                 ("view_scalars", c_size_t), ("grad2d", c_size_t), ("pair_grads", c_size_t),
+                ("pix_grad", c_size_t),
                 ("tiles_x", c_int32), ("tiles_y", c_int32), ("tile_w", c_int32),
                 ("tile_h", c_int32), ("super_x", c_int32), ("super_y", c_int32),
                 ("super_px", c_int32), ("reserved", c_int32), ("pair_capacity", c_int64)]
@@ -264,9 +266,9 @@ class Tsdf:
 
 def settings(eps_depth=0.01, lambda_depth=0.0, near=0.2, blend_mode=BLEND_OIT,
              precision=PREC_FP32, tile=(16, 16), deterministic=False, stages=0,
-             pair_capacity=0, instrument=False) -> GpsRenderSettings:
+             pair_capacity=0, instrument=False, schedule=0) -> GpsRenderSettings:
     return GpsRenderSettings(eps_depth, lambda_depth, near, blend_mode, precision, tile[0], tile[1],
-                             int(deterministic), stages, int(instrument), pair_capacity)
+                             int(deterministic), stages, int(instrument), schedule, pair_capacity)
 
 
 @dataclasses.dataclass

@@ -260,11 +260,11 @@ __device__ __forceinline__ unsigned long long pack_rect(int x0, int x1, int y0, 
          ((unsigned long long)(uint16_t)y0 << 32) | ((unsigned long long)(uint16_t)y1 << 48);
 }
 
-// One CTA of T threads per (view, super-tile): sort its segment in place and
-// write, beside each sorted key, its Gaussian's pixel rectangle (x0, x1, y0,
-// y1 as 4 x u16).  T = 128 for 16-px super-tiles (about 600 keys each at
+// One CTA of T threads per (view, super-tile): sort its segment in place (SORT)
+// and write, beside each key, its Gaussian's pixel rectangle (x0, x1, y0, y1
+// as 4 x u16).  T = 128 for 16-px super-tiles (about 600 keys each at
 // 640 x 480 with 100k Gaussians), 256 for 32-px ones.
-template <int T>
+template <int T, bool SORT>
 __global__ void __launch_bounds__(T) sort_super_kernel(const __grid_constant__ ViewBatch vb) {
   constexpr int C = T * kPerThread;
   __shared__ unsigned long long buf[2 * spad_size(C)];
@@ -277,13 +277,15 @@ __global__ void __launch_bounds__(T) sort_super_kernel(const __grid_constant__ V
   const uint2 r = v.sup_ranges[blockIdx.x - vb.sup_start[slot]];
   const int n = (int)(r.y - r.x);
   if (n <= 0) return;
-  const unsigned long long* sorted;
-  bool padded = true;
-  if (n <= C) {
+  const unsigned long long* sorted = sup_keys + r.x;
+  bool padded = false;
+  if (!SORT) {
+    // emission order kept: rectangles only
+  } else if (n <= C) {
+    padded = true;
     sorted = block_merge_sort<T>(sup_keys + r.x, n, buf, buf + spad_size(C));
   } else {
     sorted = large_sort<T>(sup_keys + r.x, v.sup_tmp + r.x, n, buf, buf + spad_size(C));
-    padded = false;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < n; k += T) {
@@ -371,11 +373,12 @@ cudaError_t launch_emit_super(int M, const ViewBatch& vb, int max_nsup, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_super(const ViewBatch& vb, cudaStream_t st) {
+cudaError_t launch_sort_super(const ViewBatch& vb, int sort, cudaStream_t st) {
   const int items = vb.sup_start[vb.n];
   if (items <= 0) return cudaSuccess;
-  if (vb.v[0].sup_shift > 4) sort_super_kernel<256><<<items, 256, 0, st>>>(vb);
-  else sort_super_kernel<128><<<items, 128, 0, st>>>(vb);
+  if (!sort) sort_super_kernel<128, false><<<items, 128, 0, st>>>(vb);
+  else if (vb.v[0].sup_shift > 4) sort_super_kernel<256, true><<<items, 256, 0, st>>>(vb);
+  else sort_super_kernel<128, true><<<items, 128, 0, st>>>(vb);
   return cudaGetLastError();
 }
 

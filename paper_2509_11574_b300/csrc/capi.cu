@@ -22,9 +22,11 @@ cudaError_t launch_project_backward(const GpsGaussians&, float, const ViewBatch&
 cudaError_t launch_bin_histogram(int, const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_scan_super(const ViewBatch&, int*, cudaStream_t);
 cudaError_t launch_emit_super(int, const ViewBatch&, int, cudaStream_t);
-cudaError_t launch_sort_super(const ViewBatch&, cudaStream_t);
+cudaError_t launch_sort_super(const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_split_tiles(int, int, const ViewBatch&, cudaStream_t);
-cudaError_t launch_composite_fwd(const ViewBatch&, int, int, float, int, int, int, cudaStream_t);
+cudaError_t launch_composite_fwd(const ViewBatch&, int, int, float, int, int, int, int, cudaStream_t);
+cudaError_t launch_composite_bwd_per_gaussian(const ViewBatch&, int, float, float, const float*,
+                                              int, cudaStream_t);
 cudaError_t launch_composite_bwd(const ViewBatch&, int, int, float, float, const float*, int, int,
                                  int, cudaStream_t);
 cudaError_t launch_finalize_loss(const ViewBatch&, float, float*, int, cudaStream_t);
@@ -123,6 +125,8 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     L.grad2d = off; off = align256(off + (size_t)M * 48);
     L.pair_grads = off;
     off = align256(off + (s->deterministic ? (size_t)cap * per_super * 48 : 0));
+    L.pix_grad = off;
+    off = align256(off + (s->schedule == GPS_SCHEDULE_PER_GAUSSIAN ? npx * 32 : 0));
     L.tiles_x = tx;
     L.tiles_y = ty;
     L.tile_w = tc.tw;
@@ -197,6 +201,7 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int 
   v.scalars = reinterpret_cast<float*>(ws + L.view_scalars);
   v.grad2d = reinterpret_cast<float4*>(ws + L.grad2d);
   v.pair_grads = reinterpret_cast<float4*>(ws + L.pair_grads);
+  v.pix_g = reinterpret_cast<float4*>(ws + L.pix_grad);
   v.tiles_x = L.tiles_x;
   v.tiles_y = L.tiles_y;
   v.tw = L.tile_w;
@@ -243,6 +248,10 @@ int32_t check_render_args(const GpsGaussians* g, const GpsView* views, int32_t n
     return fail(GPS_ERR_INVALID_ARG, "unknown blend_mode %d", s->blend_mode);
   if (s->precision != GPS_PREC_FP32 && s->precision != GPS_PREC_FP16 && s->precision != GPS_PREC_BF16)
     return fail(GPS_ERR_INVALID_ARG, "unknown precision %d", s->precision);
+  if (s->schedule != GPS_SCHEDULE_TILES && s->schedule != GPS_SCHEDULE_PER_GAUSSIAN)
+    return fail(GPS_ERR_INVALID_ARG, "unknown schedule %d", s->schedule);
+  if (s->schedule == GPS_SCHEDULE_PER_GAUSSIAN && s->blend_mode != GPS_BLEND_OIT)
+    return fail(GPS_ERR_INVALID_ARG, "the per-Gaussian schedule is order-independent (OIT) only");
   if (!ws || !aligned(ws, 256)) return fail(GPS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   for (int v = 0; v < n_views; ++v) {
     if (!finite_cam(views[v].K, views[v].T_wc))
@@ -352,7 +361,8 @@ int32_t render_forward(const GpsGaussians* g, const GpsView* views, int32_t n_vi
     if (e == cudaSuccess && (stages & GPS_STAGE_BIN)) {
       e = launch_scan_super(vb, status, st);
       if (e == cudaSuccess && g->M > 0) e = launch_emit_super(g->M, vb, max_nsup, st);
-      if (e == cudaSuccess) e = launch_sort_super(vb, st);
+      // the per-Gaussian schedule keeps the lists in emission order (rectangles only)
+      if (e == cudaSuccess) e = launch_sort_super(vb, s->schedule == GPS_SCHEDULE_TILES, st);
       // tiles that are whole super-tiles read the sorted segments directly
       if (e == cudaSuccess && v0.tile_ranges != v0.sup_ranges)
         e = launch_split_tiles(v0.tw, v0.th, vb, st);
@@ -362,7 +372,7 @@ int32_t render_forward(const GpsGaussians* g, const GpsView* views, int32_t n_vi
         e = cudaMemsetAsync(vb.v[j].scalars + 8, 0, 32, st);
       if (e == cudaSuccess)
         e = launch_composite_fwd(vb, v0.tw, v0.th, s->eps_depth, s->blend_mode, has_tgt ? 1 : 0,
-                                 s->instrument ? 1 : 0, st);
+                                 s->instrument ? 1 : 0, s->schedule == GPS_SCHEDULE_TILES, st);
       if (e == cudaSuccess && has_tgt)
         e = launch_finalize_loss(vb, s->lambda_depth, loss, b0 == 0 ? 1 : 0, st);
     }
@@ -390,7 +400,10 @@ int32_t render_backward(const GpsGaussians* g, const GpsView* views, int32_t n_v
     ViewBatch vb;
     int max_nsup = 0;
     make_batch(g->M, views, n_views, s, base, b0, vb, max_nsup);
-    if (stages & GPS_STAGE_COMPOSITE_BWD) {
+    if ((stages & GPS_STAGE_COMPOSITE_BWD) && s->schedule == GPS_SCHEDULE_PER_GAUSSIAN) {
+      e = launch_composite_bwd_per_gaussian(vb, g->M, s->eps_depth, s->lambda_depth, dloss,
+                                            s->instrument ? 1 : 0, st);
+    } else if (stages & GPS_STAGE_COMPOSITE_BWD) {
       for (int j = 0; j < vb.n && e == cudaSuccess && !s->deterministic; ++j)
         e = cudaMemsetAsync(vb.v[j].grad2d, 0, (size_t)g->M * 48, st);
       if (e == cudaSuccess)

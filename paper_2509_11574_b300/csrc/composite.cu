@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
 // per-pixel summation order, so the same images bit for bit).
 template <int TW, int TH, bool INSTR>
 __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
-    const __grid_constant__ ViewBatch vb, float eps, int has_tgt) {
+    const __grid_constant__ ViewBatch vb, float eps, int has_tgt, int sorted) {
   constexpr int NTT = TW * TH / 2;  // threads
   constexpr int NW = NTT / 32;
   constexpr int NB = 2 * NTT;       // staged entries per batch
@@ -396,7 +396,9 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
   uint32_t gi_next1 = r.x + NTT + tid < r.y ? (uint32_t)v.keys[r.x + NTT + tid] : 0u;
   const float wthr = warp_max(fmaxf(thr0, thr1));
   const float bthr = block_max<NTT>(fmaxf(thr0, thr1), s_tmp);
-  const uint32_t end = depth_cut_block<NTT>(v.keys, r.x, r.y, bthr);
+  // sorted lists end at the first Gaussian behind every pixel of the tile; an
+  // unsorted list (per-Gaussian schedule) is walked to its end
+  const uint32_t end = sorted ? depth_cut_block<NTT>(v.keys, r.x, r.y, bthr) : r.y;
   const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
   const float by0 = (float)(ty * TH + oy), by1 = by0 + 7.0f;
   const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
         if (j < nb) {
           const float4 A = s_a[j];
           const float2 E = s_e[j];
-          stop = A.z >= wthr;
+          stop = sorted && A.z >= wthr;
           ok = A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 && A.y - E.y <= by1;
           if (ok) {
             const float4 B = s_b[j];
@@ -1032,17 +1034,126 @@ __global__ void __launch_bounds__(256) gather_pair_grads_kernel(const __grid_con
   o[2] = s2;
 }
 
+// ------------------------------------------- backward, per-Gaussian schedule
+// The paper's sort-free backward (Sec. 3.1, App. B): threads work per
+// Gaussian, over the pixels its support can reach, and accumulate its
+// gradient privately, so no atomics are needed.  Here one warp takes one
+// (view, Gaussian) and walks the Gaussian's pixel rectangle in groups of 32
+// pixels (every lane runs the same number of iterations whatever the
+// Gaussian's size: the fixed-size groups of App. B), then reduces its 10
+// moments with shuffles in a fixed order and writes the 2D gradient once.
+//
+// Per pixel it needs dL/dC* / N, dL/dD* / N, sum dL/d(C*, D*) (C*, D*) / N and
+// the depth threshold (-inf for pixels without gradient), precomputed here:
+__global__ void __launch_bounds__(256) bwd_pixel_terms_kernel(const __grid_constant__ ViewBatch vb,
+                                                              float eps, float lambda,
+                                                              const float* dloss) {
+  const ViewDev& v = vb.v[blockIdx.y];
+  const int W = v.cam.W, H = v.cam.H;
+  const long long npx = (long long)W * H;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npx) return;
+  const float scale = loss_scale(v, v.fused, dloss);
+  const float4 st = v.pix_a[pix];
+  const float iN = 1.0f / (1.0f + v.pix_b[pix].x);
+  const float dt = __ldg(v.Dt + pix);
+  float g0, g1, g2, gD;
+  upstream(v, pix, npx, st, dt, v.fused, lambda, scale, g0, g1, g2, gD);
+  const float sv = (g0 * st.x + g1 * st.y + g2 * st.z + gD * st.w) * iN;
+  const bool any = g0 != 0.f || g1 != 0.f || g2 != 0.f || gD != 0.f;
+  v.pix_g[2 * pix] = make_float4(g0 * iN, g1 * iN, g2 * iN, gD * iN);
+  v.pix_g[2 * pix + 1] = make_float4(sv, any ? depth_threshold(dt, eps) : -INFINITY, 0.f, 0.f);
+}
+
+template <bool INSTR>
+__global__ void __launch_bounds__(256) composite_bwd_per_gaussian_kernel(
+    const __grid_constant__ ViewBatch vb, int M) {
+  const ViewDev& v = vb.v[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gi = blockIdx.x * 8 + warp;
+  if (gi >= M) return;  // warp-uniform
+  const float4* rr = v.rec + 4 * (size_t)gi;
+  const float4 A = rr[0], B = rr[1], C = rr[2], E = rr[3];
+  float4* o = v.grad2d + 3 * (size_t)gi;
+  int x0, x1, y0, y1;
+  if (!record_rect(A.x, A.y, C.w, E.x, v.cam.W, v.cam.H, x0, x1, y0, y1)) {
+    if (lane == 0) o[0] = o[1] = o[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const int W = v.cam.W, w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+  const float inv_w = 1.0f / (float)w;
+  const float mx = A.x, my = A.y, d = A.z, lns = __log2f(A.w);
+  const float ca = B.x, b2 = 2.0f * B.y, cc = B.z, qmax = B.w;
+  float m[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  unsigned n_tested = 0, n_counted = 0;
+  for (int p = lane; p < n; p += 32) {
+    // pixel p of the rectangle, row-major (a float quotient, corrected)
+    int ky = __float2int_rd(((float)p + 0.5f) * inv_w);
+    int kx = p - ky * w;
+    if (kx < 0) { --ky; kx += w; }
+    if (kx >= w) { ++ky; kx -= w; }
+    const int x = x0 + kx, y = y0 + ky;
+    const long long pix = (long long)y * W + x;
+    const float4 hh = v.pix_g[2 * pix];
+    const float2 ss = *reinterpret_cast<const float2*>(v.pix_g + 2 * pix + 1);
+    const float dx = __fsub_rn((float)x, mx), dy = __fsub_rn((float)y, my);
+    const float q = quad_form(ca, b2, cc, dx, dy);
+    const bool counted = q <= qmax && d < ss.y;
+    if (INSTR) {
+      ++n_tested;
+      n_counted += counted;
+    }
+    const float al = counted ? alpha_of(q, lns) : 0.0f;
+    m[0] = fmaf(al, hh.x, m[0]);
+    m[1] = fmaf(al, hh.y, m[1]);
+    m[2] = fmaf(al, hh.z, m[2]);
+    m[3] = fmaf(al, hh.w, m[3]);
+    const float dLda = fmaf(hh.x, C.x, fmaf(hh.y, C.y, fmaf(hh.z, C.z, fmaf(hh.w, d, -ss.x))));
+    const float vv = dLda * al;
+    m[4] += vv;
+    const float tx = vv * dx, ty = vv * dy;
+    m[5] += tx;
+    m[6] += ty;
+    m[7] = fmaf(tx, dx, m[7]);
+    m[8] = fmaf(tx, dy, m[8]);
+    m[9] = fmaf(ty, dy, m[9]);
+  }
+  if (INSTR) add_counters(v, 2, n_tested, n_counted);
+#pragma unroll
+  for (int c = 0; c < 10; ++c) m[c] = warp_sum(m[c]);
+  if (lane == 0) {
+    const float cb = B.y;
+    o[0] = make_float4(ca * m[5] + cb * m[6], cb * m[5] + cc * m[6], -0.5f * m[7], -m[8]);
+    o[1] = make_float4(-0.5f * m[9], m[4] / A.w, m[0], m[1]);
+    o[2] = make_float4(m[2], m[3], 0.f, 0.f);
+  }
+}
+
+cudaError_t launch_composite_bwd_per_gaussian(const ViewBatch& vb, int M, float eps, float lambda,
+                                              const float* dloss, int instr, cudaStream_t st) {
+  int max_px = 0;
+  for (int k = 0; k < vb.n; ++k) max_px = max(max_px, vb.v[k].cam.W * vb.v[k].cam.H);
+  bwd_pixel_terms_kernel<<<dim3((max_px + 255) / 256, vb.n), 256, 0, st>>>(vb, eps, lambda, dloss);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || M <= 0) return e;
+  if (instr)
+    composite_bwd_per_gaussian_kernel<true><<<dim3((M + 7) / 8, vb.n), 256, 0, st>>>(vb, M);
+  else
+    composite_bwd_per_gaussian_kernel<false><<<dim3((M + 7) / 8, vb.n), 256, 0, st>>>(vb, M);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 template <int TW, int TH>
 static cudaError_t fwd_tw(const ViewBatch& vb, float eps, int mode, int has_tgt, int instr,
-                          cudaStream_t st) {
+                          int sorted, cudaStream_t st) {
   const int items = vb.tile_start[vb.n];
   if (items <= 0) return cudaSuccess;
   if (mode == GPS_BLEND_OIT) {
     if (instr)
-      composite_fwd_oit2_kernel<TW, TH, true><<<items, TW * TH / 2, 0, st>>>(vb, eps, has_tgt);
+      composite_fwd_oit2_kernel<TW, TH, true><<<items, TW * TH / 2, 0, st>>>(vb, eps, has_tgt, sorted);
     else
-      composite_fwd_oit2_kernel<TW, TH, false><<<items, TW * TH / 2, 0, st>>>(vb, eps, has_tgt);
+      composite_fwd_oit2_kernel<TW, TH, false><<<items, TW * TH / 2, 0, st>>>(vb, eps, has_tgt, sorted);
   } else {
     if (instr)
       composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, true><<<items, TW * TH, 0, st>>>(vb, eps, has_tgt);
@@ -1068,11 +1179,11 @@ static cudaError_t bwd_tw(const ViewBatch& vb, float eps, float lambda, const fl
 }
 
 cudaError_t launch_composite_fwd(const ViewBatch& vb, int tw, int th, float eps, int mode,
-                                 int has_tgt, int instr, cudaStream_t st) {
-  if (tw == 16 && th == 16) return fwd_tw<16, 16>(vb, eps, mode, has_tgt, instr, st);
-  if (tw == 16 && th == 8) return fwd_tw<16, 8>(vb, eps, mode, has_tgt, instr, st);
-  if (tw == 8 && th == 8) return fwd_tw<8, 8>(vb, eps, mode, has_tgt, instr, st);
-  if (tw == 32 && th == 8) return fwd_tw<32, 8>(vb, eps, mode, has_tgt, instr, st);
+                                 int has_tgt, int instr, int sorted, cudaStream_t st) {
+  if (tw == 16 && th == 16) return fwd_tw<16, 16>(vb, eps, mode, has_tgt, instr, sorted, st);
+  if (tw == 16 && th == 8) return fwd_tw<16, 8>(vb, eps, mode, has_tgt, instr, sorted, st);
+  if (tw == 8 && th == 8) return fwd_tw<8, 8>(vb, eps, mode, has_tgt, instr, sorted, st);
+  if (tw == 32 && th == 8) return fwd_tw<32, 8>(vb, eps, mode, has_tgt, instr, sorted, st);
   return cudaErrorInvalidValue;
 }
 

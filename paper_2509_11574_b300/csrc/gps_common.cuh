@@ -58,6 +58,7 @@ struct ViewDev {
   float* scalars;         // [8]
   float4* grad2d;         // [M][3] float4
   float4* pair_grads;     // [cap][3] float4
+  float4* pix_g;          // [npx][2] per-Gaussian backward: (h), (sv, thr, -, -)
   int tiles_x, tiles_y, tw, th;
   int sup_x, sup_y, sup_shift;
   int fused;  // backward: upstream gradients from the fused L1 loss (1) or g_rgb/g_depth (0)

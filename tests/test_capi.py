@@ -48,6 +48,7 @@ def test_struct_layouts_match_header(tmp_path):
     body = "".join(f'  printf("{s} %zu\\n", sizeof({s}));\n' for s in structs)
     body += '  printf("off_pair_capacity %zu\\n", offsetof(GpsRenderSettings, pair_capacity));\n'
     body += '  printf("off_grad_depth %zu\\n", offsetof(GpsView, grad_depth));\n'
+    body += '  printf("off_schedule %zu\\n", offsetof(GpsRenderSettings, schedule));\n'
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gps.h"\nint main(){\n'
                     + body + "  return 0;\n}\n")
     exe = tmp_path / "sz"
@@ -56,6 +57,7 @@ def test_struct_layouts_match_header(tmp_path):
     for s in structs:
         assert int(sizes[s]) == ctypes.sizeof(getattr(gps, s)), s
     assert int(sizes["off_pair_capacity"]) == gps.GpsRenderSettings.pair_capacity.offset
+    assert int(sizes["off_schedule"]) == gps.GpsRenderSettings.schedule.offset
     assert int(sizes["off_grad_depth"]) == gps.GpsView.grad_depth.offset
 
 
@@ -121,6 +123,10 @@ def test_invalid_arguments_fail_before_launch(L):
     # workspace too small
     assert L.render_forward(ctypes.byref(gz), v, 1, ctypes.byref(s), fake, 256, None, None) \
         == gps.GPS_ERR_WORKSPACE_TOO_SMALL
+    pg_alpha = gps.settings(blend_mode=gps.BLEND_ALPHA, schedule=gps.SCHEDULE_PER_GAUSSIAN)
+    assert L.render_forward(ctypes.byref(gz), v, 1, ctypes.byref(pg_alpha), fake, 1 << 30, None,
+                            None) == gps.GPS_ERR_INVALID_ARG
+    assert b"order-independent" in L.gps_last_error()
     bad = gps.settings(blend_mode=7)
     assert L.render_forward(ctypes.byref(gz), v, 1, ctypes.byref(bad), fake, 1 << 30, None, None) \
         == gps.GPS_ERR_INVALID_ARG

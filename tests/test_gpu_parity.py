@@ -466,3 +466,80 @@ def test_autotuner_picks_a_shape_that_renders_identically():
     np.testing.assert_allclose(res[True][1], res[False][1], rtol=1e-6)  # per-tile partial sums
     np.testing.assert_allclose(res[True][2], res[False][2], rtol=1e-5,
                                atol=1e-6 * np.abs(res[False][2]).max())
+
+
+# --------------------------------------------- per-Gaussian (paper) schedule
+def test_per_gaussian_schedule_staged_vs_oracle():
+    """The sort-free schedule of Sec. 3.1 / App. B on identical FP32 records:
+    forward over unsorted tile lists (order-independent sums, FP32 rounding of
+    another order) and the one-warp-per-Gaussian backward, against the oracle."""
+    w = workload("small", M=3000, width=150, height=100)
+    f = w.frames[0]
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    rec_o, _ = oracle.project(w.gaussians.astype(np.float64), f.cam)
+    r32 = oracle.records_f32(rec_o)
+    rr = oracle.rounded(rec_o)
+    r = _renderer(w, [f.cam], schedule=gps.SCHEDULE_PER_GAUSSIAN, tile=(16, 8),
+                  stages=gps.STAGE_BIN | gps.STAGE_COMPOSITE | gps.STAGE_COMPOSITE_BWD)
+    r.region(0, "records", torch.float32, r.M * 16).copy_(torch.from_numpy(r32.reshape(-1)).cuda())
+    H, W = f.cam.height, f.cam.width
+    out = oracle.composite(rr, Ct, Dt, w.eps_depth, gps.BLEND_OIT, f32=True)
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    v = gps.View(f.cam, cuda(Ct), cuda(Dt), out_rgb=torch.empty(3, H, W, device="cuda"),
+                 out_depth=torch.empty(H, W, device="cuda"),
+                 out_weight=torch.empty(H, W, device="cuda"))
+    r.forward(g, [v])
+    ok = out["amb"] == 0
+    assert ok.mean() > 0.999
+    np.testing.assert_allclose(v.out_rgb.cpu().numpy()[:, ok], out["C"][:, ok], atol=1e-5)
+    np.testing.assert_allclose(v.out_depth.cpu().numpy()[ok], out["D"][ok], rtol=1e-5)
+    np.testing.assert_allclose(v.out_weight.cpu().numpy()[ok], out["W"][ok], rtol=1e-5, atol=1e-6)
+    rng = np.random.default_rng(0)
+    dC = (rng.choice([-1.0, 1.0], size=(3, H, W)) / (3 * H * W)).astype(np.float32)
+    dD = (rng.choice([-1.0, 1.0], size=(H, W)) / (H * W)).astype(np.float32)
+    g2_o = oracle.composite_backward(rr, Ct, Dt, w.eps_depth, dC, dD, gps.BLEND_OIT, f32=True)
+    v.grad_rgb, v.grad_depth = cuda(dC), cuda(dD)
+    r.backward(g, [v], g.zeros_like())
+    assert r.status() == gps.GPS_OK
+    g2 = r.region(0, "grad2d", torch.float32, r.M * 12).view(r.M, 12).cpu().numpy()[:, :10]
+    names = ["mx", "my", "ca", "cb", "cc", "sig", "r", "g", "b", "d"]
+    assert_grads_close({n: g2[:, k] for k, n in enumerate(names)},
+                       {n: g2_o[:, k] for k, n in enumerate(names)}, label="grad2d per-Gaussian")
+
+
+@pytest.mark.parametrize("name", ["small", "grad"])
+def test_per_gaussian_schedule_matches_tile_schedule(name):
+    """End to end with the fused loss: both schedules give the same images (up to
+    FP32 rounding of the summation order), loss and gradients; the per-Gaussian
+    backward has no atomics, so for one forward state it is bitwise
+    reproducible (the unsorted forward itself sums in emission order)."""
+    w = workload(name)
+    f = w.frames[0]
+    H, W = f.cam.height, f.cam.width
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    res = []
+    for sched in (gps.SCHEDULE_TILES, gps.SCHEDULE_PER_GAUSSIAN):
+        s = gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, tile=(16, 8),
+                         schedule=sched)
+        r = gps.Renderer(w.gaussians.M, [f.cam], s)
+        g = gps.Gaussians.from_numpy(w.gaussians)
+        v = gps.View(f.cam, cuda(Ct), cuda(Dt), cuda(f.rgb), cuda(f.depth),
+                     out_rgb=torch.empty(3, H, W, device="cuda"))
+        loss = torch.zeros(1, device="cuda")
+        r.forward(g, [v], loss)
+        grads = g.zeros_like()
+        r.backward(g, [v], grads)
+        res.append((v.out_rgb.cpu().numpy(), loss.item(), grads.flat().cpu().numpy()))
+        if sched == gps.SCHEDULE_PER_GAUSSIAN:  # the same forward state again
+            again = g.zeros_like()
+            r.backward(g, [v], again)
+            np.testing.assert_array_equal(again.flat().cpu().numpy(), res[-1][2])
+        assert r.status() == gps.GPS_OK
+    (c0, l0, g0), (c1, l1, g1) = res
+    np.testing.assert_allclose(c1, c0, atol=2e-6)
+    np.testing.assert_allclose(l1, l0, rtol=1e-5)
+    # a residual within FP32 rounding of zero can flip its L1 sign between the
+    # two summation orders; everything else agrees to accumulation rounding
+    scale = np.abs(g0).max()
+    close = np.abs(g1 - g0) <= 1e-4 * scale + 1e-4 * np.abs(g0)
+    assert close.mean() > 0.999, close.mean()
