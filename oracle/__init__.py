@@ -24,6 +24,12 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   bin               - brute-force enumeration of tiles + Python sorted()
   adam              - torch.optim.Adam (FP64)
   quantise          - torch's float16 / bfloat16 casts, tie-to-even hand values
+  edit.py (insertion / removal, Sec. 3.2 and App. A, plain numpy):
+    splitmix64      - the generator's published outputs from seed 0
+    sampling        - fraction and uniformity over 10^6 pixels, seed independence
+    mask, removal   - threshold cases by hand
+    insert          - planes: means, colours, opacity, disc radius from pixel
+                      spacing, short axis on the analytic normal (scipy Rotation)
 """
 from __future__ import annotations
 
