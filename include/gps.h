@@ -312,6 +312,65 @@ GPS_API int32_t gps_autotune_tiles(const GpsGaussians* gaussians, const GpsView*
                                    int32_t* best_tile_w, int32_t* best_tile_h, float* times_ms,
                                    void* stream);
 
+/* ------------------------------------------ Gaussian insertion and removal */
+
+/* Thresholds of Sec. 3.2 (defaults in brackets are the paper's). */
+typedef struct GpsEditSettings {
+  float delta_c;          /* insertion: mean |C* - C_k| over the channels above [0.05] */
+  float delta_w;          /* insertion: Gaussian weight W_G below [4]             */
+  float sample_fraction;  /* insertion: share of the mask pixels sampled [0.25]   */
+  int32_t radius;         /* insertion: half-size of the neighbour window used for
+                             the disc radius, pixels [3]; at most 16           */
+  uint64_t seed;          /* insertion: SplitMix64 seed of the sampling draw      */
+  float delta_sigma;      /* removal: opacity below [0.005]                       */
+  float delta_smax;       /* removal: largest scale above [0.1] (metres)          */
+  float delta_smin;       /* removal: largest scale below [0.003]                 */
+  int32_t precision;      /* GPS_PREC_* of rendered_rgb and target_rgb            */
+} GpsEditSettings;
+
+/* Scratch bytes insert_gaussians / remove_gaussians need for `capacity`
+ * Gaussians and width x height images (caller-allocated, 256-byte aligned). */
+GPS_API int32_t gps_edit_scratch_size(int32_t capacity, int32_t width, int32_t height,
+                                      size_t* bytes);
+
+/* Gaussian insertion (Sec. 3.2 "Gaussian insertion", App. A) for one frame.
+ * The mask holds the pixels the ray-cast hit (sdf_depth > 0) whose colour
+ * error, taken in float32 as (|e_r| + |e_g|) + |e_b| > float(3 delta_c) with
+ * e = C* - C_k, is above delta_c and whose Gaussian weight is below delta_w.
+ * A pixel p (row-major) is sampled when it is in the mask and the top 24 bits
+ * of the (p + 1)-th output of SplitMix64 seeded with `seed` are below
+ * sample_fraction * 2^24.  Each sampled pixel u, in pixel order, appends one
+ * Gaussian at index M, M + 1, ... (up to `capacity`): mean = vertex(u),
+ * rgb = C_k(u), opacity logit 0 (sigma = 0.5), a flat disc with scales
+ * (s1, s1, 0.1 s1), s1 = min(0.1, sqrt of the mean squared distance from
+ * vertex(u) to the (at most) three nearest vertices of mask pixels within
+ * `radius` pixels; none: depth(u) / fx), whose short axis is the vertex-map
+ * normal at u turned to face the camera.  The new rows of m, v and grads
+ * (each nullable) are zeroed.
+ *   gaussians: arrays of `capacity` rows, gaussians->M = the current count.
+ *   vertex [H][W][3] world points from raycast_sdf; sdf_depth, weight [H][W]
+ *   float; rendered_rgb (C*) and target_rgb (C_k) [3][H][W] of type
+ *   s->precision; all device memory of the size K gives.
+ *   *count (device int32) receives the new count min(M + sampled, capacity).
+ * Enqueued on `stream`, no synchronisation; errors: GPS_ERR_INVALID_ARG,
+ * GPS_ERR_WORKSPACE_TOO_SMALL (scratch), GPS_ERR_CUDA. */
+GPS_API int32_t insert_gaussians(GpsGaussians* gaussians, int32_t capacity, GpsGaussians* m,
+                                 GpsGaussians* v, GpsGaussians* grads, const GpsIntrinsics* K,
+                                 const GpsPose* T_wc, const float* vertex, const float* sdf_depth,
+                                 const void* rendered_rgb, const float* weight,
+                                 const void* target_rgb, const GpsEditSettings* s, void* scratch,
+                                 size_t scratch_bytes, int32_t* count, void* stream);
+
+/* Gaussian removal (Sec. 3.2 "Gaussian removal"): deletes the Gaussians of
+ * [0, gaussians->M) with opacity logit < float(ln(delta_sigma / (1 - delta_sigma)))
+ * or largest log-scale > float(ln delta_smax) or < float(ln delta_smin), and
+ * compacts the rest to [0, kept) in their order, together with the same rows
+ * of m, v and grads (nullable; rows [kept, M) of those are zeroed).  *count
+ * (device int32) receives kept.  Enqueued on `stream`; errors as above. */
+GPS_API int32_t remove_gaussians(GpsGaussians* gaussians, GpsGaussians* m, GpsGaussians* v,
+                                 GpsGaussians* grads, const GpsEditSettings* s, void* scratch,
+                                 size_t scratch_bytes, int32_t* count, void* stream);
+
 /* Size of the static device array behind render_forward_noalloc: 64 MiB,
  * held by every GPU that loads this library until the process exits. */
 #define GPS_NOALLOC_SCRATCH_BYTES (64u << 20)

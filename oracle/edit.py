@@ -32,8 +32,9 @@ Readings of points the paper leaves open (listed with the other readings):
 - The normal is the cross product of the vertex map's horizontal and vertical
   differences (central where both neighbours are hits, one-sided otherwise;
   no usable neighbour on an axis: the reversed viewing ray), turned to face
-  the camera.  The disc's short axis (local z) is rotated onto it by the
-  quaternion (1 + n_z, -n_y, n_x, 0), normalised; n = -z uses (0, 1, 0, 0).
+  the camera.  The disc's short axis (local z) is rotated onto its line by
+  the quaternion (1 + n_z, -n_y, n_x, 0), normalised, with n's sign chosen so
+  that n_z >= 0 (a disc is the same Gaussian either way).
 - The removal tests are taken on the stored parameters against constants:
   logit < ln(delta_sigma / (1 - delta_sigma)), max log-scale > ln(delta_smax),
   max log-scale < ln(delta_smin), each constant rounded to float32.
@@ -103,11 +104,14 @@ def _normal(V, hit, y, x, cam_center):
 
 
 def quat_z_to(n) -> np.ndarray:
-    """Unit quaternion (w, x, y, z) rotating the local z axis onto unit n."""
-    w = 1.0 + n[2]
-    if w < 1e-6:
-        return np.array([0.0, 1.0, 0.0, 0.0])
-    q = np.array([w, -n[1], n[0], 0.0])
+    """Unit quaternion (w, x, y, z) rotating the local z axis onto the line of
+    unit n.  A disc's covariance does not change when its short axis flips, so
+    the axis is taken as the one of +-n with non-negative z: then
+    w = 1 + |n_z| >= 1 and the quaternion (1 + n_z, -n_y, n_x, 0) is well
+    conditioned (near n = -z it would cancel)."""
+    if n[2] < 0:
+        n = -np.asarray(n)
+    q = np.array([1.0 + n[2], -n[1], n[0], 0.0])
     return q / np.linalg.norm(q)
 
 

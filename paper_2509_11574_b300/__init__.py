@@ -79,6 +79,20 @@ class GpsRenderSettings(ctypes.Structure):
                 ("instrument", c_int32), ("schedule", c_int32), ("pair_capacity", c_int64)]
 
 
+class GpsEditSettings(ctypes.Structure):
+    _fields_ = [("delta_c", c_float), ("delta_w", c_float), ("sample_fraction", c_float),
+                ("radius", c_int32), ("seed", ctypes.c_uint64), ("delta_sigma", c_float),
+                ("delta_smax", c_float), ("delta_smin", c_float), ("precision", c_int32)]
+
+
+def edit_settings(delta_c=0.05, delta_w=4.0, sample_fraction=0.25, radius=3, seed=0,
+                  delta_sigma=0.005, delta_smax=0.1, delta_smin=0.003,
+                  precision=0) -> "GpsEditSettings":
+    """Sec. 3.2 thresholds (the defaults are the paper's)."""
+    return GpsEditSettings(delta_c, delta_w, sample_fraction, radius, seed, delta_sigma, delta_smax,
+                           delta_smin, precision)
+
+
 class GpsAdamHyper(ctypes.Structure):
     _fields_ = [("lr", c_float * 5), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
 
@@ -98,7 +112,8 @@ class GpsWorkspaceLayout(ctypes.Structure):
 
 EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspace_layout",
             "gps_query_status", "fuse_frame", "raycast_sdf", "render_forward", "render_backward",
-            "adam_step", "render_forward_noalloc", "gps_autotune_tiles")
+            "adam_step", "render_forward_noalloc", "gps_autotune_tiles",
+            "gps_edit_scratch_size", "insert_gaussians", "remove_gaussians")
 AUTOTUNE_SHAPES = ((16, 16), (16, 8), (8, 8), (32, 8))  # the order of GPS_AUTOTUNE_SHAPES
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -145,6 +160,14 @@ def lib() -> ctypes.CDLL:
                                          c_size_t, ctypes.POINTER(GpsGaussians), c_int32,
                                          ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
                                          ctypes.POINTER(c_float), c_void_p]
+        P_G = ctypes.POINTER(GpsGaussians)
+        L.gps_edit_scratch_size.argtypes = [c_int32, c_int32, c_int32, ctypes.POINTER(c_size_t)]
+        L.insert_gaussians.argtypes = [P_G, c_int32, P_G, P_G, P_G, ctypes.POINTER(GpsIntrinsics),
+                                       ctypes.POINTER(GpsPose), c_void_p, c_void_p, c_void_p,
+                                       c_void_p, c_void_p, ctypes.POINTER(GpsEditSettings),
+                                       c_void_p, c_size_t, c_void_p, c_void_p]
+        L.remove_gaussians.argtypes = [P_G, P_G, P_G, P_G, ctypes.POINTER(GpsEditSettings),
+                                       c_void_p, c_size_t, c_void_p, c_void_p]
         L.adam_step.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsGaussians),
                                 ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsGaussians),
                                 ctypes.POINTER(GpsAdamHyper), c_int32, c_void_p, c_void_p]
@@ -405,6 +428,49 @@ def gps_autotune_tiles(g: Gaussians, views: Sequence[View], s: GpsRenderSettings
                                     ctypes.byref(th), times, _stream(stream)))
     return (tw.value, th.value), {shp: (t if t >= 0 else None)
                                   for shp, t in zip(AUTOTUNE_SHAPES, times)}
+
+
+def gps_edit_scratch_size(capacity: int, width: int, height: int) -> int:
+    n = c_size_t(0)
+    _check(lib().gps_edit_scratch_size(capacity, width, height, ctypes.byref(n)))
+    return int(n.value)
+
+
+def _gs(z: Optional["Gaussians"], M: Optional[int] = None):
+    if z is None:
+        return None
+    c = z.c()
+    if M is not None:
+        c.M = M
+    return ctypes.byref(c)
+
+
+def insert_gaussians(g: "Gaussians", M: int, m: Optional["Gaussians"], v: Optional["Gaussians"],
+                     grads: Optional["Gaussians"], cam, vertex: torch.Tensor, sdf_depth: torch.Tensor,
+                     rendered_rgb: torch.Tensor, weight: torch.Tensor, target_rgb: torch.Tensor,
+                     s: GpsEditSettings, scratch: torch.Tensor, count: torch.Tensor,
+                     stream=None) -> None:
+    """Appends new Gaussians after the first M rows of g (its rows are the
+    capacity); the new count lands in count[0] (device int32)."""
+    K, P = intrinsics(cam), pose(cam)
+    gc = g.c()
+    gc.M = M
+    _check(lib().insert_gaussians(ctypes.byref(gc), g.M, _gs(m, M), _gs(v, M), _gs(grads, M),
+                                  ctypes.byref(K), ctypes.byref(P), _ptr(vertex), _ptr(sdf_depth),
+                                  _ptr(rendered_rgb), _ptr(weight), _ptr(target_rgb),
+                                  ctypes.byref(s), _ptr(scratch), scratch.numel(), _ptr(count),
+                                  _stream(stream)))
+
+
+def remove_gaussians(g: "Gaussians", M: int, m: Optional["Gaussians"], v: Optional["Gaussians"],
+                     grads: Optional["Gaussians"], s: GpsEditSettings, scratch: torch.Tensor,
+                     count: torch.Tensor, stream=None) -> None:
+    """Compacts the first M rows of g (and m, v, grads); kept count -> count[0]."""
+    gc = g.c()
+    gc.M = M
+    _check(lib().remove_gaussians(ctypes.byref(gc), _gs(m, M), _gs(v, M), _gs(grads, M),
+                                  ctypes.byref(s), _ptr(scratch), scratch.numel(), _ptr(count),
+                                  _stream(stream)))
 
 
 def adam_step(params: Gaussians, grads: Gaussians, m: Gaussians, v: Gaussians, lr=LR_APP_C,

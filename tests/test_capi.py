@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(L):
 
 def test_struct_layouts_match_header(tmp_path):
     structs = ["GpsIntrinsics", "GpsPose", "GpsTsdf", "GpsGaussians", "GpsView",
-               "GpsRenderSettings", "GpsAdamHyper", "GpsWorkspaceLayout"]
+               "GpsRenderSettings", "GpsAdamHyper", "GpsWorkspaceLayout", "GpsEditSettings"]
     prog = tmp_path / "sz.c"
     body = "".join(f'  printf("{s} %zu\\n", sizeof({s}));\n' for s in structs)
     body += '  printf("off_pair_capacity %zu\\n", offsetof(GpsRenderSettings, pair_capacity));\n'
@@ -141,6 +141,16 @@ def test_invalid_arguments_fail_before_launch(L):
     assert L.gps_autotune_tiles(ctypes.byref(gz), v, 1, ctypes.byref(s), fake, 1 << 20,
                                 ctypes.byref(gz), 0, ctypes.byref(tw), ctypes.byref(th), None,
                                 None) == gps.GPS_ERR_INVALID_ARG
+    es = gps.edit_settings()
+    cnt = ctypes.c_void_p(512)
+    assert L.insert_gaussians(ctypes.byref(gz), 10, None, None, None, ctypes.byref(K),
+                              ctypes.byref(P), None, fake, fake, fake, fake, ctypes.byref(es),
+                              fake, 1 << 20, cnt, None) == gps.GPS_ERR_INVALID_ARG
+    assert L.remove_gaussians(ctypes.byref(gz), None, None, None, ctypes.byref(es), None, 0, cnt,
+                              None) == gps.GPS_ERR_INVALID_ARG
+    n = ctypes.c_size_t(0)
+    assert L.gps_edit_scratch_size(1000, 640, 480, ctypes.byref(n)) == gps.GPS_OK
+    assert n.value >= 1000 * 56 + 2 * 640 * 480
     h = gps.GpsAdamHyper((ctypes.c_float * 5)(*gps.LR_APP_C), 0.9, 0.999, 1e-15)
     assert L.adam_step(ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(gz),
                        ctypes.byref(h), 0, None, None) == gps.GPS_ERR_INVALID_ARG
