@@ -294,13 +294,11 @@ class GpuPipeline:
 
 
 def kernels_per_step(mode, tile, schedule="tiles"):
-    # fuse, raycast + per iteration: project, scan, emit, sort, [split into tiles
-    # unless a tile is a whole 16-px super-tile], composite, finalize,
-    # composite_bwd [per-Gaussian schedule: pixel terms + per-Gaussian], project_bwd,
-    # adam, step counter
-    split = 0 if tuple(tile) == (16, 16) else 1
+    # fuse, raycast + per iteration: project, scan, emit, sort + split, composite,
+    # finalize, composite_bwd [per-Gaussian schedule: pixel terms + per-Gaussian],
+    # project_bwd, adam, step counter
     pg = 1 if schedule == "per-gaussian" else 0
-    return 2 + ITERS_PER_FRAME * (10 + split + pg)
+    return 2 + ITERS_PER_FRAME * (10 + pg)
 
 
 def count_evaluations(pipe, k):

@@ -191,8 +191,6 @@ typedef struct GpsWorkspaceLayout {
   size_t super_ranges;  /* uint32 [super_tiles][2]                            */
   size_t super_keys;    /* uint64 [pair_capacity] super-tile segments         */
   size_t super_scratch; /* uint64 [pair_capacity] (sort scratch)              */
-  size_t super_rects;   /* uint64 [pair_capacity] pixel rectangle of each
-                           sorted entry: x0, x1, y0, y1 as 4 x uint16          */
   size_t tile_ranges;   /* uint32 [tiles][2]                                  */
   size_t pair_keys;     /* uint64 [tiles per super-tile * pair_capacity]      */
   size_t pix_state;     /* float [H*W][8] saved per-pixel forward state       */

@@ -100,7 +100,7 @@ class GpsAdamHyper(ctypes.Structure):
 class GpsWorkspaceLayout(ctypes.Structure):
     _fields_ = [("total_bytes", c_size_t), ("status", c_size_t), ("records", c_size_t),
                 ("super_counts", c_size_t), ("block_base", c_size_t), ("super_ranges", c_size_t),
-                ("super_keys", c_size_t), ("super_scratch", c_size_t), ("super_rects", c_size_t),
+                ("super_keys", c_size_t), ("super_scratch", c_size_t),
                 ("tile_ranges", c_size_t),
                 ("pair_keys", c_size_t), ("pix_state", c_size_t), ("tile_partials", c_size_t),
                 ("view_scalars", c_size_t), ("grad2d", c_size_t), ("pair_grads", c_size_t),

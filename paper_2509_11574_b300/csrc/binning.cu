@@ -11,9 +11,9 @@
 //      per-(Gaussian, tile) global atomic and no contended counter chain.
 //   2. one CTA per super-tile sorts its segment by the 64-bit key (8 keys per
 //      thread in registers with a sorting network, then merge-path rounds in
-//      shared memory) and stores each entry's pixel rectangle beside it;
-//   3. one CTA per tile filters its super-tile's sorted segment, in order, by
-//      rectangle overlap (the same test as the oracle's binning).
+//      shared memory) and splits it, in order, into its tiles' lists by
+//      rectangle overlap (the same test as the oracle's binning); a tile that
+//      is a whole super-tile reads the sorted segment itself.
 // The result equals a stable sort of (tile << 32 | bits(d)) keys with ties in
 // index order, independent of the order the atomics ran in.
 #include <cuda_runtime.h>
@@ -255,32 +255,46 @@ __device__ unsigned long long* large_sort(unsigned long long* seg, unsigned long
   return src;
 }
 
-__device__ __forceinline__ unsigned long long pack_rect(int x0, int x1, int y0, int y1) {
-  return (unsigned long long)(uint16_t)x0 | ((unsigned long long)(uint16_t)x1 << 16) |
-         ((unsigned long long)(uint16_t)y0 << 32) | ((unsigned long long)(uint16_t)y1 << 48);
-}
-
-// One CTA of T threads per (view, super-tile): sort its segment in place (SORT)
-// and write, beside each key, its Gaussian's pixel rectangle (x0, x1, y0, y1
-// as 4 x u16).  T = 128 for 16-px super-tiles (about 600 keys each at
-// 640 x 480 with 100k Gaussians), 256 for 32-px ones.
-template <int T, bool SORT>
-__global__ void __launch_bounds__(T) sort_super_kernel(const __grid_constant__ ViewBatch vb) {
+// One CTA of T threads per (view, super-tile) of L = (sp / TW) x (sp / TH)
+// tiles: sort the segment (SORT; the per-Gaussian schedule keeps emission
+// order), then split it, in order, into its tiles' lists by rectangle overlap
+// (the same test as the oracle's binning).  Tile l of super-tile s owns
+// tile_keys[L * start_s + l * n_s ...] (never longer than the segment).  With
+// one tile per super-tile the sorted segment is the tile list: no rectangles.
+template <int T, bool SORT, int TW, int TH>
+__global__ void __launch_bounds__(T) sort_split_kernel(const __grid_constant__ ViewBatch vb) {
   constexpr int C = T * kPerThread;
+  constexpr int NWT = T / 32;
   __shared__ unsigned long long buf[2 * spad_size(C)];
+  __shared__ uint32_t s_cnt[4][NWT];
   const int slot = batch_slot(vb.sup_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
   unsigned long long* __restrict__ sup_keys = v.sup_keys;
-  unsigned long long* __restrict__ sup_rect = v.sup_rect;
-  const float4* __restrict__ rec = v.rec;
-  const int W = v.cam.W, H = v.cam.H;
-  const uint2 r = v.sup_ranges[blockIdx.x - vb.sup_start[slot]];
+  const int sh = v.sup_shift, sp = 1 << sh;
+  const int LX = sp / TW, LY = sp / TH, L = LX * LY;  // L <= 4
+  const int s = blockIdx.x - vb.sup_start[slot];
+  const int sx = s % v.sup_x, sy = s / v.sup_x;
+  const uint2 r = v.sup_ranges[s];
   const int n = (int)(r.y - r.x);
-  if (n <= 0) return;
+  // tile l of this super-tile: its index (or -1 past the image) and pixel box
+  auto tile_of = [&](int l, int& t, int& x0, int& y0) {
+    const int tx = sx * LX + l % LX, ty = sy * LY + l / LX;
+    t = tx < v.tiles_x && ty < v.tiles_y ? ty * v.tiles_x + tx : -1;
+    x0 = tx * TW;
+    y0 = ty * TH;
+  };
+  if (n <= 0) {
+    if (L > 1 && (int)threadIdx.x < L) {
+      int t, x0, y0;
+      tile_of(threadIdx.x, t, x0, y0);
+      if (t >= 0) v.tile_ranges[t] = make_uint2((uint32_t)L * r.x, (uint32_t)L * r.x);
+    }
+    return;
+  }
   const unsigned long long* sorted = sup_keys + r.x;
   bool padded = false;
   if (!SORT) {
-    // emission order kept: rectangles only
+    // emission order kept
   } else if (n <= C) {
     padded = true;
     sorted = block_merge_sort<T>(sup_keys + r.x, n, buf, buf + spad_size(C));
@@ -288,63 +302,54 @@ __global__ void __launch_bounds__(T) sort_super_kernel(const __grid_constant__ V
     sorted = large_sort<T>(sup_keys + r.x, v.sup_tmp + r.x, n, buf, buf + spad_size(C));
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < n; k += T) {
-    const unsigned long long key = padded ? sorted[spad(k)] : sorted[k];
-    const uint32_t gi = (uint32_t)key;
-    const float4 a = rec[4 * (size_t)gi], c = rec[4 * (size_t)gi + 2], e = rec[4 * (size_t)gi + 3];
-    int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
-    record_rect(a.x, a.y, c.w, e.x, W, H, x0, x1, y0, y1);
-    sup_rect[r.x + k] = pack_rect(x0, x1, y0, y1);
-    if (padded || sorted != sup_keys + r.x) sup_keys[r.x + k] = key;
+  if (L == 1) {
+    if (padded || sorted != sup_keys + r.x)
+      for (int k = threadIdx.x; k < n; k += T) sup_keys[r.x + k] = padded ? sorted[spad(k)] : sorted[k];
+    return;
   }
-}
-
-// One CTA per (view, tile): the tile's list is its super-tile's sorted segment
-// filtered, in order, by rectangle overlap.  Tile l of super-tile s owns
-// tile_keys[L * start_s + l * n_s ...] (never longer than the segment).
-template <int TW, int TH>
-__global__ void __launch_bounds__(128) split_tiles_kernel(const __grid_constant__ ViewBatch vb) {
-  const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
-  const ViewDev& v = vb.v[vb.order[slot]];
-  const uint2* __restrict__ sup_ranges = v.sup_ranges;
-  const unsigned long long* __restrict__ sup_keys = v.sup_keys;
-  const unsigned long long* __restrict__ sup_rect = v.sup_rect;
-  unsigned long long* __restrict__ tile_keys = v.keys;
-  uint2* __restrict__ tile_ranges = v.tile_ranges;
-  const int sh = v.sup_shift, sup_x = v.sup_x, tiles_x = v.tiles_x;
-  const int sp = 1 << sh, LX = sp / TW, LY = sp / TH, L = LX * LY;
-  __shared__ uint32_t s_cnt[4];
-  const int t = blockIdx.x - vb.tile_start[slot];
-  const int tx = t % tiles_x, ty = t / tiles_x;
-  const int x0 = tx * TW, x1 = x0 + TW - 1, y0 = ty * TH, y1 = y0 + TH - 1;
-  const int s = (y0 >> sh) * sup_x + (x0 >> sh);
-  const int l = ((y0 & (sp - 1)) / TH) * LX + (x0 & (sp - 1)) / TW;
-  const uint2 r = sup_ranges[s];
-  const int n = (int)(r.y - r.x);
-  const size_t base = (size_t)L * r.x + (size_t)l * n;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint32_t run = 0;
-  for (int c0 = 0; c0 < n; c0 += 128) {
-    const int k = c0 + tid;
-    bool mem = false;
+  const float4* __restrict__ rec = v.rec;
+  const int W = v.cam.W, H = v.cam.H;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t run[4] = {0u, 0u, 0u, 0u};
+  for (int c0 = 0; c0 < n; c0 += T) {
+    const int k = c0 + threadIdx.x;
     unsigned long long key = 0;
+    int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
     if (k < n) {
-      const unsigned long long pr = sup_rect[r.x + k];
-      const int rx0 = (int)(pr & 0xFFFF), rx1 = (int)((pr >> 16) & 0xFFFF);
-      const int ry0 = (int)((pr >> 32) & 0xFFFF), ry1 = (int)(pr >> 48);
-      mem = rx0 <= x1 && rx1 >= x0 && ry0 <= y1 && ry1 >= y0;
-      if (mem) key = sup_keys[r.x + k];
+      key = padded ? sorted[spad(k)] : sorted[k];
+      const uint32_t gi = (uint32_t)key;
+      const float4 a = rec[4 * (size_t)gi], c = rec[4 * (size_t)gi + 2], e = rec[4 * (size_t)gi + 3];
+      record_rect(a.x, a.y, c.w, e.x, W, H, x0, x1, y0, y1);
     }
-    const unsigned b = __ballot_sync(0xffffffffu, mem);
-    if (lane == 0) s_cnt[warp] = __popc(b);
+    unsigned bal[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      if (l >= L) break;
+      int t, tx0, ty0;
+      tile_of(l, t, tx0, ty0);
+      const bool mem = k < n && x0 <= tx0 + TW - 1 && x1 >= tx0 && y0 <= ty0 + TH - 1 && y1 >= ty0;
+      bal[l] = __ballot_sync(0xffffffffu, mem);
+      if (lane == 0) s_cnt[l][warp] = __popc(bal[l]);
+    }
     __syncthreads();
-    uint32_t off = run;
-    for (int w2 = 0; w2 < warp; ++w2) off += s_cnt[w2];
-    if (mem) tile_keys[base + off + __popc(b & ((1u << lane) - 1u))] = key;
-    run += s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      if (l >= L) break;
+      uint32_t off = run[l];
+      for (int w2 = 0; w2 < warp; ++w2) off += s_cnt[l][w2];
+      if ((bal[l] >> lane) & 1u)
+        v.keys[(size_t)L * r.x + (size_t)l * n + off + __popc(bal[l] & ((1u << lane) - 1u))] = key;
+      for (int w2 = 0; w2 < NWT; ++w2) run[l] += s_cnt[l][w2];
+    }
     __syncthreads();
   }
-  if (tid == 0) tile_ranges[t] = make_uint2((uint32_t)base, (uint32_t)(base + run));
+  if ((int)threadIdx.x < L) {
+    const int l = threadIdx.x;
+    int t, x0, y0;
+    tile_of(l, t, x0, y0);
+    const size_t base = (size_t)L * r.x + (size_t)l * n;
+    if (t >= 0) v.tile_ranges[t] = make_uint2((uint32_t)base, (uint32_t)(base + run[l]));
+  }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -373,28 +378,20 @@ cudaError_t launch_emit_super(int M, const ViewBatch& vb, int max_nsup, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_super(const ViewBatch& vb, int sort, cudaStream_t st) {
+cudaError_t launch_sort_split(const ViewBatch& vb, int tw, int th, int sort, cudaStream_t st) {
   const int items = vb.sup_start[vb.n];
   if (items <= 0) return cudaSuccess;
-  if (!sort) sort_super_kernel<128, false><<<items, 128, 0, st>>>(vb);
-  else if (vb.v[0].sup_shift > 4) sort_super_kernel<256, true><<<items, 256, 0, st>>>(vb);
-  else sort_super_kernel<128, true><<<items, 128, 0, st>>>(vb);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_split_tiles(int tw, int th, const ViewBatch& vb, cudaStream_t st) {
-  const int items = vb.tile_start[vb.n];
-  if (items <= 0) return cudaSuccess;
-#define GPS_SPLIT(a, b)                                   \
-  if (tw == a && th == b) {                               \
-    split_tiles_kernel<a, b><<<items, 128, 0, st>>>(vb);  \
-    return cudaGetLastError();                            \
+#define GPS_SORT_SPLIT(T, A, B)                                                  \
+  if (tw == A && th == B) {                                                      \
+    if (sort) sort_split_kernel<T, true, A, B><<<items, T, 0, st>>>(vb);         \
+    else sort_split_kernel<T, false, A, B><<<items, T, 0, st>>>(vb);             \
+    return cudaGetLastError();                                                   \
   }
-  GPS_SPLIT(16, 16)
-  GPS_SPLIT(16, 8)
-  GPS_SPLIT(8, 8)
-  GPS_SPLIT(32, 8)
-#undef GPS_SPLIT
+  GPS_SORT_SPLIT(128, 16, 16)
+  GPS_SORT_SPLIT(128, 16, 8)
+  GPS_SORT_SPLIT(128, 8, 8)
+  GPS_SORT_SPLIT(256, 32, 8)
+#undef GPS_SORT_SPLIT
   return cudaErrorInvalidValue;
 }
 

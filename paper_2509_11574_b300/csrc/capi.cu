@@ -22,8 +22,7 @@ cudaError_t launch_project_backward(const GpsGaussians&, float, const ViewBatch&
 cudaError_t launch_bin_histogram(int, const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_scan_super(const ViewBatch&, int*, cudaStream_t);
 cudaError_t launch_emit_super(int, const ViewBatch&, int, cudaStream_t);
-cudaError_t launch_sort_super(const ViewBatch&, int, cudaStream_t);
-cudaError_t launch_split_tiles(int, int, const ViewBatch&, cudaStream_t);
+cudaError_t launch_sort_split(const ViewBatch&, int, int, int, cudaStream_t);
 cudaError_t launch_composite_fwd(const ViewBatch&, int, int, float, int, int, int, int, cudaStream_t);
 cudaError_t launch_composite_bwd_per_gaussian(const ViewBatch&, int, float, float, const float*,
                                               int, cudaStream_t);
@@ -109,7 +108,6 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     L.super_ranges = off; off = align256(off + nsup * 8);
     L.super_keys = off; off = align256(off + (size_t)cap * 8);
     L.super_scratch = off; off = align256(off + (size_t)cap * 8);
-    L.super_rects = off; off = align256(off + (size_t)cap * 8);
     // with one tile per super-tile the tile lists are the sorted segments
     // themselves: tile ranges and pair keys alias the super-tile regions
     if (per_super == 1) {
@@ -191,7 +189,6 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int 
   v.sup_ranges = reinterpret_cast<uint2*>(ws + L.super_ranges);
   v.sup_keys = reinterpret_cast<unsigned long long*>(ws + L.super_keys);
   v.sup_tmp = reinterpret_cast<unsigned long long*>(ws + L.super_scratch);
-  v.sup_rect = reinterpret_cast<unsigned long long*>(ws + L.super_rects);
   v.tile_ranges = reinterpret_cast<uint2*>(ws + L.tile_ranges);
   v.keys = reinterpret_cast<unsigned long long*>(ws + L.pair_keys);
   const size_t npx = (size_t)vw.K.width * vw.K.height;
@@ -361,11 +358,10 @@ int32_t render_forward(const GpsGaussians* g, const GpsView* views, int32_t n_vi
     if (e == cudaSuccess && (stages & GPS_STAGE_BIN)) {
       e = launch_scan_super(vb, status, st);
       if (e == cudaSuccess && g->M > 0) e = launch_emit_super(g->M, vb, max_nsup, st);
-      // the per-Gaussian schedule keeps the lists in emission order (rectangles only)
-      if (e == cudaSuccess) e = launch_sort_super(vb, s->schedule == GPS_SCHEDULE_TILES, st);
-      // tiles that are whole super-tiles read the sorted segments directly
-      if (e == cudaSuccess && v0.tile_ranges != v0.sup_ranges)
-        e = launch_split_tiles(v0.tw, v0.th, vb, st);
+      // sort each super-tile's segment and split it into its tiles' lists (the
+      // per-Gaussian schedule keeps emission order)
+      if (e == cudaSuccess)
+        e = launch_sort_split(vb, v0.tw, v0.th, s->schedule == GPS_SCHEDULE_TILES, st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_COMPOSITE)) {
       for (int j = 0; j < vb.n && e == cudaSuccess && s->instrument; ++j)

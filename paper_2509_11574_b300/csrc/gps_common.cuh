@@ -49,7 +49,6 @@ struct ViewDev {
   uint2* sup_ranges;     // [nsup]
   unsigned long long* sup_keys;
   unsigned long long* sup_tmp;
-  unsigned long long* sup_rect;  // pixel rectangle of each sorted entry (4 x u16)
   uint2* tile_ranges;    // [tiles]
   unsigned long long* keys;  // tile lists
   float4* pix_a;  // [npx] (C*.rgb, D*)
