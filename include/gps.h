@@ -104,7 +104,13 @@ typedef struct GpsPose {
  *     sdf    float [n]    truncated signed distance / trunc, in [-1, 1]
  *     weight float [n]    fusion weight (0 = never observed)
  *     rgbw   float [n][4] colour (r, g, b) and its own weight.
- * A fresh volume is sdf = 1, weight = 0, rgbw = 0 (caller-initialised). */
+ * A fresh volume is sdf = 1, weight = 0, rgbw = 0 (caller-initialised).
+ * brick_flags (nullable) holds one byte per brick, in brick order: nonzero
+ * where some voxel of the brick may hold sdf != 1.  fuse_frame sets them;
+ * raycast_sdf then skips the voxel loads of every trilinear sample whose
+ * bricks are all clear (the sample is 1 there; the march is unchanged).  A
+ * fresh volume has all flags clear; a caller that writes sdf itself calls
+ * tsdf_mark_bricks afterwards, or passes NULL. */
 typedef struct GpsTsdf {
   int32_t nx, ny, nz;
   float voxel;      /* edge length in metres           */
@@ -114,6 +120,7 @@ typedef struct GpsTsdf {
   float* sdf;
   float* weight;
   float* rgbw;
+  uint8_t* brick_flags;
 } GpsTsdf;
 
 /* A Gaussian set, or a gradient / moment buffer of the same shape. */
@@ -245,6 +252,9 @@ GPS_API int32_t gps_query_status(const void* ws, size_t ws_bytes, int32_t* statu
  * device images of size K.  In-place on vol. */
 GPS_API int32_t fuse_frame(GpsTsdf* vol, const float* depth, const float* rgb, const GpsIntrinsics* K,
                    const GpsPose* T_wc, void* stream);
+
+/* Recompute vol->brick_flags from vol->sdf (flag = some voxel != 1). */
+GPS_API int32_t tsdf_mark_bricks(GpsTsdf* vol, void* stream);
 
 /* Ray-cast the TSDF (Sec. 3.1 first pass).  Per pixel, march the ray from
  * max(near, entry into the voxel-centre box) to min(far, exit) (far <= 0: exit)

@@ -57,7 +57,8 @@ class GpsPose(ctypes.Structure):
 class GpsTsdf(ctypes.Structure):
     _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("voxel", c_float),
                 ("origin", c_float * 3), ("trunc", c_float), ("max_weight", c_float),
-                ("sdf", c_void_p), ("weight", c_void_p), ("rgbw", c_void_p)]
+                ("sdf", c_void_p), ("weight", c_void_p), ("rgbw", c_void_p),
+                ("brick_flags", c_void_p)]
 
 
 class GpsGaussians(ctypes.Structure):
@@ -113,7 +114,8 @@ class GpsWorkspaceLayout(ctypes.Structure):
 EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspace_layout",
             "gps_query_status", "fuse_frame", "raycast_sdf", "render_forward", "render_backward",
             "adam_step", "render_forward_noalloc", "gps_autotune_tiles",
-            "gps_edit_scratch_size", "insert_gaussians", "remove_gaussians")
+            "gps_edit_scratch_size", "insert_gaussians", "remove_gaussians",
+            "tsdf_mark_bricks")
 AUTOTUNE_SHAPES = ((16, 16), (16, 8), (8, 8), (32, 8))  # the order of GPS_AUTOTUNE_SHAPES
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -161,6 +163,7 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
                                          ctypes.POINTER(c_float), c_void_p]
         P_G = ctypes.POINTER(GpsGaussians)
+        L.tsdf_mark_bricks.argtypes = [ctypes.POINTER(GpsTsdf), c_void_p]
         L.gps_edit_scratch_size.argtypes = [c_int32, c_int32, c_int32, ctypes.POINTER(c_size_t)]
         L.insert_gaussians.argtypes = [P_G, c_int32, P_G, P_G, P_G, ctypes.POINTER(GpsIntrinsics),
                                        ctypes.POINTER(GpsPose), c_void_p, c_void_p, c_void_p,
@@ -268,17 +271,24 @@ class Tsdf:
         self.sdf = torch.ones(n, dtype=torch.float32, device=device)
         self.weight = torch.zeros(n, dtype=torch.float32, device=device)
         self.rgbw = torch.zeros(n, 4, dtype=torch.float32, device=device)
+        self.brick_flags = torch.zeros(n // 512, dtype=torch.uint8, device=device)
 
     def reset(self):
         self.sdf.fill_(1.0)
         self.weight.zero_()
         self.rgbw.zero_()
+        self.brick_flags.zero_()
+
+    def mark_bricks(self, stream=None):
+        """Recompute the brick flags after writing sdf directly."""
+        t = self.c()
+        _check(lib().tsdf_mark_bricks(ctypes.byref(t), _stream(stream)))
 
     def c(self) -> GpsTsdf:
         s = self.spec
         return GpsTsdf(s.nx, s.ny, s.nz, float(s.voxel), (c_float * 3)(*map(float, s.origin)),
                        float(s.trunc), float(s.max_weight), _ptr(self.sdf), _ptr(self.weight),
-                       _ptr(self.rgbw))
+                       _ptr(self.rgbw), _ptr(self.brick_flags))
 
     def linear(self):
         s = self.spec

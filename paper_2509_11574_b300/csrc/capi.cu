@@ -14,6 +14,7 @@
 
 namespace gps {
 cudaError_t launch_fuse(const GpsTsdf&, const float*, const float*, const Cam&, cudaStream_t);
+cudaError_t launch_mark_bricks(const GpsTsdf&, cudaStream_t);
 cudaError_t launch_raycast(const GpsTsdf&, const Cam&, float, float, void*, int, float*, float*,
                            cudaStream_t);
 cudaError_t launch_project(const GpsGaussians&, float, const ViewBatch&, int, cudaStream_t);
@@ -309,6 +310,14 @@ int32_t fuse_frame(GpsTsdf* vol, const float* depth, const float* rgb, const Gps
   if (!finite_cam(*K, *T_wc)) return fail(GPS_ERR_INVALID_ARG, "bad intrinsics or pose");
   cudaError_t e = launch_fuse(*vol, depth, rgb, make_cam(*K, *T_wc), static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GPS_OK : cuda_fail(e, "fuse_frame");
+}
+
+int32_t tsdf_mark_bricks(GpsTsdf* vol, void* stream) {
+  if (!vol || !vol->sdf || !vol->brick_flags) return fail(GPS_ERR_INVALID_ARG, "NULL volume or flags");
+  if (vol->nx < 8 || vol->ny < 8 || vol->nz < 8 || vol->nx % 8 || vol->ny % 8 || vol->nz % 8)
+    return fail(GPS_ERR_INVALID_ARG, "volume dims must be positive multiples of 8");
+  const cudaError_t e = launch_mark_bricks(*vol, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GPS_OK : cuda_fail(e, "tsdf_mark_bricks");
 }
 
 int32_t raycast_sdf(const GpsTsdf* vol, const GpsIntrinsics* K, const GpsPose* T_wc,

@@ -17,7 +17,12 @@ struct VolDev {
   float* sdf;
   float* weight;
   float4* rgbw;
+  uint8_t* flags;  // nullable: per brick, nonzero if some voxel may be != 1
 };
+
+__device__ __forceinline__ long long brick_of(const VolDev& v, int x, int y, int z) {
+  return ((long long)(z >> 3) * (v.ny >> 3) + (y >> 3)) * (v.nx >> 3) + (x >> 3);
+}
 
 __device__ __forceinline__ long long vox_index(const VolDev& v, int x, int y, int z) {
   const int nbx = v.nx >> 3, nby = v.ny >> 3;
@@ -61,7 +66,9 @@ __global__ void __launch_bounds__(256) fuse_kernel(VolDev v, const float* __rest
   if (eta < -v.trunc) return;
   const float f = fminf(1.0f, eta / v.trunc);
   const float w0 = v.weight[id], s0 = v.sdf[id];
-  v.sdf[id] = (w0 * s0 + f) / (w0 + 1.0f);
+  const float s1 = (w0 * s0 + f) / (w0 + 1.0f);
+  v.sdf[id] = s1;
+  if (v.flags && s1 != 1.0f) v.flags[brick] = 1;
   v.weight[id] = fminf(w0 + 1.0f, v.wmax);
   if (fabsf(eta) < v.trunc) {
     float4 c = v.rgbw[id];
@@ -82,11 +89,27 @@ __device__ __forceinline__ float sample_sdf(const VolDev& v, float gx, float gy,
   iy = min(max(iy, 0), v.ny - 2);
   iz = min(max(iz, 0), v.nz - 2);
   const float fx = gx - ix, fy = gy - iy, fz = gz - iz;
-  const float* s = v.sdf;
-  const float c000 = __ldg(s + vox_index(v, ix, iy, iz)), c100 = __ldg(s + vox_index(v, ix + 1, iy, iz));
-  const float c010 = __ldg(s + vox_index(v, ix, iy + 1, iz)), c110 = __ldg(s + vox_index(v, ix + 1, iy + 1, iz));
-  const float c001 = __ldg(s + vox_index(v, ix, iy, iz + 1)), c101 = __ldg(s + vox_index(v, ix + 1, iy, iz + 1));
-  const float c011 = __ldg(s + vox_index(v, ix, iy + 1, iz + 1)), c111 = __ldg(s + vox_index(v, ix + 1, iy + 1, iz + 1));
+  // all eight voxels in clear bricks: they hold 1, no loads (the arithmetic
+  // below is the same, so is the sample)
+  bool clear = v.flags != nullptr;
+  if (clear) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      clear = clear && !v.flags[brick_of(v, ix + (k & 1), iy + ((k >> 1) & 1), iz + (k >> 2))];
+  }
+  float c000 = 1.0f, c100 = 1.0f, c010 = 1.0f, c110 = 1.0f, c001 = 1.0f, c101 = 1.0f,
+        c011 = 1.0f, c111 = 1.0f;
+  if (!clear) {
+    const float* s = v.sdf;
+    c000 = __ldg(s + vox_index(v, ix, iy, iz));
+    c100 = __ldg(s + vox_index(v, ix + 1, iy, iz));
+    c010 = __ldg(s + vox_index(v, ix, iy + 1, iz));
+    c110 = __ldg(s + vox_index(v, ix + 1, iy + 1, iz));
+    c001 = __ldg(s + vox_index(v, ix, iy, iz + 1));
+    c101 = __ldg(s + vox_index(v, ix + 1, iy, iz + 1));
+    c011 = __ldg(s + vox_index(v, ix, iy + 1, iz + 1));
+    c111 = __ldg(s + vox_index(v, ix + 1, iy + 1, iz + 1));
+  }
   const float c00 = c000 * (1.0f - fx) + c100 * fx, c10 = c010 * (1.0f - fx) + c110 * fx;
   const float c01 = c001 * (1.0f - fx) + c101 * fx, c11 = c011 * (1.0f - fx) + c111 * fx;
   const float c0 = c00 * (1.0f - fy) + c10 * fy, c1 = c01 * (1.0f - fy) + c11 * fy;
@@ -192,10 +215,25 @@ __global__ void __launch_bounds__(256) raycast_kernel(VolDev v, Cam cam, float n
   }
 }
 
+// One block per brick: flag = some voxel's sdf differs from 1.
+__global__ void __launch_bounds__(256) mark_bricks_kernel(const float* __restrict__ sdf,
+                                                          uint8_t* __restrict__ flags) {
+  const float* b = sdf + (size_t)blockIdx.x * 512;
+  const bool any = b[threadIdx.x] != 1.0f || b[threadIdx.x + 256] != 1.0f;
+  const int n = __syncthreads_or(any);
+  if (threadIdx.x == 0) flags[blockIdx.x] = n ? 1 : 0;
+}
+
+cudaError_t launch_mark_bricks(const GpsTsdf& t, cudaStream_t st) {
+  const long long nb = ((long long)t.nx * t.ny * t.nz) >> 9;
+  if (nb > 0) mark_bricks_kernel<<<(unsigned)nb, 256, 0, st>>>(t.sdf, t.brick_flags);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fuse(const GpsTsdf& t, const float* depth, const float* rgb, const Cam& cam,
                         cudaStream_t st) {
   VolDev v{t.nx, t.ny, t.nz, t.voxel, t.origin[0], t.origin[1], t.origin[2], t.trunc,
-           t.max_weight, t.sdf, t.weight, reinterpret_cast<float4*>(t.rgbw)};
+           t.max_weight, t.sdf, t.weight, reinterpret_cast<float4*>(t.rgbw), t.brick_flags};
   const long long n = (long long)t.nx * t.ny * t.nz;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   fuse_kernel<<<blocks, 256, 0, st>>>(v, depth, rgb, cam);
@@ -205,7 +243,7 @@ cudaError_t launch_fuse(const GpsTsdf& t, const float* depth, const float* rgb, 
 cudaError_t launch_raycast(const GpsTsdf& t, const Cam& cam, float near_, float far_, void* rgb,
                            int rgb_prec, float* depth, float* vertex, cudaStream_t st) {
   VolDev v{t.nx, t.ny, t.nz, t.voxel, t.origin[0], t.origin[1], t.origin[2], t.trunc,
-           t.max_weight, t.sdf, t.weight, reinterpret_cast<float4*>(t.rgbw)};
+           t.max_weight, t.sdf, t.weight, reinterpret_cast<float4*>(t.rgbw), t.brick_flags};
   dim3 grid((cam.W + 15) / 16, (cam.H + 15) / 16);
   raycast_kernel<<<grid, 256, 0, st>>>(v, cam, near_, far_, rgb, rgb_prec, depth, vertex);
   return cudaGetLastError();

@@ -72,6 +72,7 @@ def _raycast_vs_oracle(name, prec):
     Ct, Dt, V, amb = oracle.raycast(w.tsdf, sdf32, rgb32, f.cam)
     vg = gps.Tsdf(w.tsdf)
     vg.sdf.copy_(gps.linear_to_brick(torch.from_numpy(sdf32)).cuda())
+    vg.mark_bricks()  # sdf written directly: refresh the empty-space flags
     rgbw = np.concatenate([rgb32, np.ones(rgb32.shape[:3] + (1,), np.float32)], -1)
     vg.rgbw.copy_(gps.linear_to_brick(torch.from_numpy(rgbw)).cuda())
     c, d = gps.raycast_sdf(vg, f.cam, precision=prec)
