@@ -76,47 +76,69 @@ def dist_env():
 
 
 # ---------------------------------------------------------------- clocks
+class _NvmlC:
+    """The few read-only NVML queries the sampler needs, through the driver's
+    libnvidia-ml with ctypes (the Python bindings are not always installed)."""
+    CLOCK_SM = 1
+    # clock-event reason bits of the public NVML API
+    BITS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+            "sw_power_cap": 0x4, "hw_power_brake_slowdown": 0x80}
+
+    def __init__(self, index: int):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        n = ctypes.c_uint(0)
+        self.lib.nvmlDeviceGetCount_v2(ctypes.byref(n))
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(0 if n.value == 1 else index, ctypes.byref(self.h)):
+            raise RuntimeError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        ct = self.ct
+        sm, mx, r = ct.c_uint(0), ct.c_uint(0), ct.c_ulonglong(0)
+        self.lib.nvmlDeviceGetClockInfo(self.h, self.CLOCK_SM, ct.byref(sm))
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.CLOCK_SM, ct.byref(mx))
+        self.reasons_fn(self.h, ct.byref(r))
+        return float(sm.value), float(mx.value), {k for k, b in self.BITS.items() if r.value & b}
+
+
 class ClockSampler:
     """SM clock and clock-event (throttle) reasons sampled during the timed
-    region: NVML read-only queries polled every 5 ms from a thread (the
-    region lasts a fraction of a second, too short for nvidia-smi's loop),
-    nvidia-smi as the fallback when NVML cannot be opened."""
-    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap",
-             "hw_power_brake_slowdown")
+    region: NVML read-only queries polled every 5 ms from a thread (the region
+    lasts a fraction of a second, too short for nvidia-smi's loop), through
+    the driver's library; nvidia-smi as the fallback."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, smi_index: str, uuid: str | None):
-        self.smi_index, self.uuid = smi_index, uuid
-        self.rows, self.proc, self.thread, self.nv, self.h = [], None, None, None, None
+    def __init__(self, smi_index: str, uuid=None):
+        self.smi_index = smi_index
+        self.rows, self.proc, self.thread, self.nvml = [], None, None, None
+        self.why = None
         self.stop_flag = threading.Event()
         try:
-            import pynvml as nv
-            nv.nvmlInit()
-            self.nv = nv
-            self.h = (nv.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode()) if uuid
-                      else nv.nvmlDeviceGetHandleByIndex(int(smi_index)))
-            self.bits = (nv.nvmlClocksEventReasonHwSlowdown, nv.nvmlClocksEventReasonHwThermalSlowdown,
-                         nv.nvmlClocksEventReasonSwThermalSlowdown, nv.nvmlClocksEventReasonSwPowerCap,
-                         nv.nvmlClocksEventReasonHwPowerBrakeSlowdown)
-        except Exception:
-            self.nv = None
+            self.nvml = _NvmlC(int(smi_index) if str(smi_index).isdigit() else 0)
+            self.nvml.sample()
+        except Exception as e:  # no driver library or no permission: nvidia-smi below
+            self.why = f"NVML unavailable ({type(e).__name__})"
+            self.nvml = None
 
     def _poll(self):
-        nv, h = self.nv, self.h
         while not self.stop_flag.is_set():
             try:
-                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-                mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
-                r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-                self.rows.append((float(sm), float(mx), {n for n, b in zip(self.NAMES, self.bits) if r & b}))
+                self.rows.append(self.nvml.sample())
             except Exception:
                 pass
             self.stop_flag.wait(0.005)
 
     def start(self):
-        if self.nv is not None:
+        if self.nvml is not None:
             self.thread = threading.Thread(target=self._poll, daemon=True)
             self.thread.start()
             return
@@ -125,7 +147,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.smi_index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -144,11 +166,11 @@ class ClockSampler:
                     self.rows.append((float(parts[1]), float(parts[2]),
                                       {n for n, v in zip(self.NAMES, parts[5:9]) if v.lower() == "active"}))
             os.unlink(self.path)
-            src = "nvidia-smi"
+            src = "nvidia-smi" + (f"; {self.why}" if self.why else "")
         else:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"]}
         if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "source": src}
         return {"sm_mhz": statistics.median(r[0] for r in self.rows),
                 "sm_max_mhz": max(r[1] for r in self.rows),
                 "reasons": sorted(set().union(*(r[2] for r in self.rows))),
@@ -393,8 +415,7 @@ def run_ours(args, rank, world, local):
     # ---- headline: graph replay
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     smi_id = vis.split(",")[local].strip() if vis else str(local)
-    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
-    clocks = ClockSampler(smi_id, str(uuid) if uuid is not None else None)
+    clocks = ClockSampler(smi_id)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -733,7 +754,7 @@ def run_multiview(args, rank, world, local):
 
     res = {"batched_plain_ms": timed(batched), "sequential_plain_ms": timed(sequential)}
     gb, gs = graphed(batched), graphed(sequential)
-    clocks = ClockSampler(str(local), str(getattr(torch.cuda.get_device_properties(dev), "uuid", "")) or None)
+    clocks = ClockSampler(str(local))
     clocks.start()
     res["batched_graph_ms"] = timed(gb)
     clk = clocks.stop()
