@@ -30,6 +30,13 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
     mask, removal   - threshold cases by hand
     insert          - planes: means, colours, opacity, disc radius from pixel
                       spacing, short axis on the analytic normal (scipy Rotation)
+  schedule.py (keyframes and optimisation views, Sec. 3.2, Fig. 5, App. C):
+    is_keyframe     - rotations (scipy) and translations just under / over the
+                      thresholds, relative to a rotated last keyframe
+    local frames    - spacing by hand
+    global draw     - a hand value from SplitMix64's published first output;
+                      history bounds, no repeats; marginal, first-draw and pair
+                      frequencies of a uniform draw without replacement
 """
 from __future__ import annotations
 
