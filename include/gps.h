@@ -379,6 +379,50 @@ GPS_API int32_t remove_gaussians(GpsGaussians* gaussians, GpsGaussians* m, GpsGa
                                  GpsGaussians* grads, const GpsEditSettings* s, void* scratch,
                                  size_t scratch_bytes, int32_t* count, void* stream);
 
+/* ------------------------------------------- keyframes and optimisation views
+ * Host-only bookkeeping of the online loop (Sec. 3.2 "Gaussian optimization",
+ * Fig. 5, App. C): which frames become keyframes, and which frames one
+ * Gaussian optimisation renders.  These calls touch no device memory and
+ * launch nothing; they are deterministic functions of their arguments. */
+typedef struct GpsViewSchedule {
+  float delta_angle_deg; /* keyframe when the rotation from the last keyframe
+                            exceeds this many degrees [30] (App. C)          */
+  float delta_move;      /* ... or the camera centre moved more than this,
+                            metres [0.3] (App. C)                            */
+  int32_t interval;      /* delta_k: frames between optimisations [10]       */
+  int32_t n_global;      /* keyframes drawn from the history [4], <= 1024    */
+  int32_t n_local;       /* frames spread over the last interval [4]         */
+  int32_t reserved;      /* 0                                                */
+  uint64_t seed;         /* SplitMix64 seed of the keyframe draw             */
+} GpsViewSchedule;
+
+/* *is_keyframe = 1 when last_keyframe is NULL (the first frame), or when the
+ * relative pose last_keyframe^-1 * T_wc rotates by more than delta_angle_deg
+ * (angle of R_last^T R from its trace) or moves the camera centre by more
+ * than delta_move (both strict), else 0.  Evaluated in double precision.
+ * Errors: GPS_ERR_INVALID_ARG for NULL T_wc / s / is_keyframe or a
+ * non-finite threshold. */
+GPS_API int32_t gps_is_keyframe(const GpsPose* last_keyframe, const GpsPose* T_wc,
+                                const GpsViewSchedule* s, int32_t* is_keyframe);
+
+/* Views of the optimisation number `event` (0, 1, ...) taken at frame
+ * `frame` (Fig. 5).  Writes to views[0 .. *n_views):
+ *   1. n = min(n_local, L) local frames, L = min(interval, frame + 1):
+ *      frame - floor(j L / n) for j = 0 .. n - 1 (newest first);
+ *   2. min(n_global, H) keyframes drawn uniformly without replacement from
+ *      the H entries of `keyframes` (ascending frame ids, n_keyframes of them)
+ *      that are <= frame - interval: a partial Fisher-Yates shuffle whose
+ *      step i swaps position i with i + floor(hi32(r) (H - i) / 2^32), r the
+ *      (1024 event + i + 1)-th output of SplitMix64 seeded with s->seed;
+ *      written in draw order.
+ * Errors: GPS_ERR_INVALID_ARG for NULL pointers (keyframes may be NULL when
+ * n_keyframes is 0), frame < 0, event < 0, interval < 1, n_local < 0,
+ * n_global outside [0, 1024], keyframe ids not strictly ascending or
+ * negative, or capacity below the number of views. */
+GPS_API int32_t gps_select_views(const int32_t* keyframes, int32_t n_keyframes, int32_t frame,
+                                 int32_t event, const GpsViewSchedule* s, int32_t* views,
+                                 int32_t capacity, int32_t* n_views);
+
 /* Size of the static device array behind render_forward_noalloc: 64 MiB,
  * held by every GPU that loads this library until the process exits. */
 #define GPS_NOALLOC_SCRATCH_BYTES (64u << 20)

@@ -24,8 +24,12 @@ delta_smax or below delta_smin, are deleted; the rest keep their order.
 
 Readings of points the paper leaves open (listed with the other readings):
 - App. A writes the radius as the square root of the mean of the (unsquared)
-  distances; with centimetre spacings that saturates the 0.1 m cap for every
-  Gaussian, so the distances are read as squared, as in RTG-SLAM and 3DGS.
+  distances, which is not a length; the distances are read as squared, the
+  initialisation of RTG-SLAM and 3DGS (root mean squared distance to the
+  three nearest points).  Taken literally, neighbours one pixel apart at
+  1.5 m (2.7 mm at fx = 560) would give 5 cm discs, about twenty pixel
+  footprints; read as squared, the 0.1 m cap still bites where the window's
+  nearest mask pixels lie across a depth discontinuity.
 - Neighbours are searched among mask pixels in a (2R+1)^2 image window
   (R = 3), not among all mask pixels of the frame; fewer than three found:
   the mean over those found; none: s1 = D_t(u) / f_x (one pixel's footprint).

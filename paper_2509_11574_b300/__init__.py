@@ -94,6 +94,19 @@ def edit_settings(delta_c=0.05, delta_w=4.0, sample_fraction=0.25, radius=3, see
                            delta_smin, precision)
 
 
+class GpsViewSchedule(ctypes.Structure):
+    _fields_ = [("delta_angle_deg", c_float), ("delta_move", c_float), ("interval", c_int32),
+                ("n_global", c_int32), ("n_local", c_int32), ("reserved", c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+def view_schedule(delta_angle_deg=30.0, delta_move=0.3, interval=10, n_global=4, n_local=4,
+                  seed=0) -> "GpsViewSchedule":
+    """Keyframe thresholds of App. C (30 degrees, 0.3 m) and the optimisation
+    interval of Sec. 4.1 (every 10 frames); four global and four local views."""
+    return GpsViewSchedule(delta_angle_deg, delta_move, interval, n_global, n_local, 0, seed)
+
+
 class GpsAdamHyper(ctypes.Structure):
     _fields_ = [("lr", c_float * 5), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
 
@@ -115,7 +128,7 @@ EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspac
             "gps_query_status", "fuse_frame", "raycast_sdf", "render_forward", "render_backward",
             "adam_step", "render_forward_noalloc", "gps_autotune_tiles",
             "gps_edit_scratch_size", "insert_gaussians", "remove_gaussians",
-            "tsdf_mark_bricks")
+            "tsdf_mark_bricks", "gps_is_keyframe", "gps_select_views")
 AUTOTUNE_SHAPES = ((16, 16), (16, 8), (8, 8), (32, 8))  # the order of GPS_AUTOTUNE_SHAPES
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -178,6 +191,11 @@ def lib() -> ctypes.CDLL:
                                              ctypes.POINTER(GpsView), c_int32,
                                              ctypes.POINTER(GpsRenderSettings), c_void_p,
                                              c_void_p]
+        L.gps_is_keyframe.argtypes = [ctypes.POINTER(GpsPose), ctypes.POINTER(GpsPose),
+                                      ctypes.POINTER(GpsViewSchedule), ctypes.POINTER(c_int32)]
+        L.gps_select_views.argtypes = [ctypes.POINTER(c_int32), c_int32, c_int32, c_int32,
+                                       ctypes.POINTER(GpsViewSchedule), ctypes.POINTER(c_int32),
+                                       c_int32, ctypes.POINTER(c_int32)]
         _lib = L
     return _lib
 
@@ -481,6 +499,31 @@ def remove_gaussians(g: "Gaussians", M: int, m: Optional["Gaussians"], v: Option
     _check(lib().remove_gaussians(ctypes.byref(gc), _gs(m, M), _gs(v, M), _gs(grads, M),
                                   ctypes.byref(s), _ptr(scratch), scratch.numel(), _ptr(count),
                                   _stream(stream)))
+
+
+def gps_is_keyframe(last_cam, cam, sched: Optional[GpsViewSchedule] = None) -> bool:
+    """Host-only: does `cam`'s pose start a new keyframe after `last_cam`'s
+    (None: the first frame)?"""
+    sched = sched if sched is not None else view_schedule()
+    out = c_int32(0)
+    last = ctypes.byref(pose(last_cam)) if last_cam is not None else None
+    _check(lib().gps_is_keyframe(last, ctypes.byref(pose(cam)), ctypes.byref(sched),
+                                 ctypes.byref(out)))
+    return bool(out.value)
+
+
+def gps_select_views(keyframes: Sequence[int], frame: int, event: int,
+                     sched: Optional[GpsViewSchedule] = None) -> List[int]:
+    """Host-only: frame ids of the optimisation `event` taken at `frame`
+    (local frames newest first, then the keyframes drawn)."""
+    sched = sched if sched is not None else view_schedule()
+    kf = (c_int32 * max(1, len(keyframes)))(*[int(k) for k in keyframes])
+    cap = max(0, sched.n_local) + max(0, sched.n_global)
+    out = (c_int32 * max(1, cap))()
+    n = c_int32(0)
+    _check(lib().gps_select_views(kf, len(keyframes), frame, event, ctypes.byref(sched), out, cap,
+                                  ctypes.byref(n)))
+    return [int(out[i]) for i in range(n.value)]
 
 
 def adam_step(params: Gaussians, grads: Gaussians, m: Gaussians, v: Gaussians, lr=LR_APP_C,

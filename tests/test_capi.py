@@ -43,7 +43,8 @@ def test_library_exports_every_declared_symbol(L):
 
 def test_struct_layouts_match_header(tmp_path):
     structs = ["GpsIntrinsics", "GpsPose", "GpsTsdf", "GpsGaussians", "GpsView",
-               "GpsRenderSettings", "GpsAdamHyper", "GpsWorkspaceLayout", "GpsEditSettings"]
+               "GpsRenderSettings", "GpsAdamHyper", "GpsWorkspaceLayout", "GpsEditSettings",
+               "GpsViewSchedule"]
     prog = tmp_path / "sz.c"
     body = "".join(f'  printf("{s} %zu\\n", sizeof({s}));\n' for s in structs)
     body += '  printf("off_pair_capacity %zu\\n", offsetof(GpsRenderSettings, pair_capacity));\n'

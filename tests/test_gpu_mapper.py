@@ -1,0 +1,86 @@
+"""The online loop (Sec. 3.2, Fig. 2, Fig. 5) through `Mapper` on the GPU:
+its keyframes and optimisation views equal the oracle's decisions on the same
+poses, the Gaussian count follows insertion and removal, each optimisation
+lowers its loss, frames nobody can select are released, and a second run
+from scratch gives the same Gaussians bit for bit (deterministic reductions).
+Every numeric stage inside is covered against the oracle by the parity tests
+of its own call."""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2509_11574_b300 as gps
+from paper_2509_11574_b300.mapper import Mapper
+from datagen import workloads
+from oracle import schedule as osched
+
+pytestmark = pytest.mark.gpu
+
+INTERVAL, N_GLOBAL, N_LOCAL = 4, 2, 2
+
+
+@functools.lru_cache(maxsize=1)
+def _sequence():
+    return workloads.room(n_frames=13, M=16, width=160, height=120, n_vox=128)
+
+
+def _run(seq, iterations=5):
+    vol = gps.Tsdf(seq.tsdf)
+    sched = gps.view_schedule(delta_angle_deg=3.0, delta_move=0.05, interval=INTERVAL,
+                              n_global=N_GLOBAL, n_local=N_LOCAL, seed=11)
+    s = gps.settings(tile=(16, 8), deterministic=True)
+    mp = Mapper(vol, seq.frames[0].cam, capacity=60000, s=s, sched=sched, iterations=iterations)
+    out = []
+    for k, f in enumerate(seq.frames):
+        r = mp.process(k, f.cam, torch.as_tensor(f.rgb).cuda(), torch.as_tensor(f.depth).cuda())
+        out.append(r)
+    torch.cuda.synchronize()
+    return mp, out
+
+
+def _f32_pose(cam):
+    return (np.asarray(cam.R, np.float32).astype(np.float64).reshape(3, 3),
+            np.asarray(cam.t, np.float32).astype(np.float64))
+
+
+def test_mapper_schedule_counts_and_loss():
+    seq = _sequence()
+    mp, out = _run(seq)
+    # keyframes: the oracle's rule on the same float32 poses
+    kf, last = [], None
+    for k, f in enumerate(seq.frames):
+        p = _f32_pose(f.cam)
+        if osched.is_keyframe(last, p, 3.0, 0.05):
+            kf.append(k)
+            last = p
+    assert mp.keyframes == kf and len(kf) >= 2
+    recs = [r for r in out if r is not None]
+    assert [r.frame for r in recs] == [3, 7, 11]
+    count = 0
+    for e, r in enumerate(recs):
+        have = [k for k in kf if k <= r.frame]
+        assert r.views == osched.select_views(have, r.frame, e, INTERVAL, N_GLOBAL, N_LOCAL, 11)
+        assert r.inserted > 0 if e == 0 else r.inserted >= 0
+        assert r.count == count + r.inserted - r.removed
+        count = r.count
+        assert r.loss_last < r.loss_first, r
+    assert any(len(r.views) > N_LOCAL for r in recs)      # history keyframes were drawn
+    assert mp.M == count and 0 < count <= mp.capacity
+    # kept frames: the last interval and the keyframes
+    last = len(seq.frames) - 1
+    assert set(mp.frames) == set(range(last - INTERVAL + 1, last + 1)) | set(kf)
+    # the live Gaussians are finite and their Adam state is in use
+    g = mp.gaussians()
+    assert all(torch.isfinite(t).all() for t in g.tensors())
+    assert float(mp.v.means[:count].abs().sum()) > 0
+
+
+def test_mapper_is_reproducible():
+    seq = _sequence()
+    a, _ = _run(seq, iterations=3)
+    b, _ = _run(seq, iterations=3)
+    assert a.M == b.M
+    for x, y in zip(a.gaussians().tensors(), b.gaussians().tensors()):
+        assert torch.equal(x, y)
