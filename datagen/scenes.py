@@ -22,7 +22,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Callable, List, Sequence, Tuple
+from typing import Callable, List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -263,13 +263,21 @@ class GaussianSet:
     quats: np.ndarray        # (M, 4) w, x, y, z (not necessarily unit)
     opacity_logits: np.ndarray  # (M,)
     rgb: np.ndarray          # (M, 3)
+    sh_rest: Optional[np.ndarray] = None  # (M, (D+1)^2 - 1, 3) SH coefficients of degree 1..D
 
     @property
     def M(self) -> int:
         return int(self.means.shape[0])
 
+    @property
+    def sh_degree(self) -> int:
+        if self.sh_rest is None:
+            return 0
+        return {3: 1, 8: 2, 15: 3}[self.sh_rest.shape[1]]
+
     def astype(self, dt) -> "GaussianSet":
-        return GaussianSet(*(np.ascontiguousarray(getattr(self, f.name), dtype=dt)
+        return GaussianSet(*(None if getattr(self, f.name) is None else
+                             np.ascontiguousarray(getattr(self, f.name), dtype=dt)
                              for f in dataclasses.fields(self)))
 
     def arrays(self):
@@ -299,6 +307,16 @@ def init_gaussians(vertex_maps: Sequence[np.ndarray], M: int, seed: int) -> Gaus
     logits = rng.normal(0.0, 1.0, size=M)
     rgb = rng.uniform(0.0, 1.0, size=(M, 3))
     return GaussianSet(means, log_scales, q, logits, rgb).astype(np.float32)
+
+
+def with_sh(g: GaussianSet, degree: int, seed: int, scale: float = 0.1) -> GaussianSet:
+    """A copy of g with SH coefficients of degree 1..`degree` drawn from
+    N(0, scale^2) (float32)."""
+    rng = np.random.default_rng(seed)
+    K = (degree + 1) ** 2 - 1
+    out = GaussianSet(*(np.array(a) for a in g.arrays()))
+    out.sh_rest = rng.normal(0.0, scale, size=(g.M, K, 3)).astype(np.float32) if K else None
+    return out
 
 
 # ----------------------------------------------------------------------------

@@ -4,9 +4,10 @@ Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of `bench.py`
 may import this package.  It shares no code with the CUDA path
 (`paper_2509_11574_b300`), which never imports it.
 
-The arithmetic lives in `tsdf.cpp` (fusion, ray-cast) and `splat.cpp`
+The arithmetic lives in `tsdf.cpp` (fusion, ray-cast), `splat.cpp`
 (projection, compositing Eq. 1-4 and the Table 7 "with sort" variant, L1 loss
-Eq. 6, adjoints, tile binning, Adam).  This module builds `liboracle.so` with
+Eq. 6, adjoints, tile binning, Adam) and `sh.cpp` (view-dependent colour from
+spherical harmonics of degree 1-3 and its adjoint).  This module builds `liboracle.so` with
 g++ (FP64, `-ffp-contract=off`, OpenMP over independent pixels / voxels) and
 wraps it with ctypes on float64 numpy arrays.
 
@@ -24,6 +25,11 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   bin               - brute-force enumeration of tiles + Python sorted()
   adam              - torch.optim.Adam (FP64)
   quantise          - torch's float16 / bfloat16 casts, tie-to-even hand values
+  sh (sh.cpp)       - basis = sqrt2 Re / Im of scipy's complex harmonics (Condon-
+                      Shortley phase), orthonormal under exact quadrature; closed-
+                      form colours and parity under d -> -d; colour and whole-loss
+                      gradients (SH coefficients, means via the view direction)
+                      against central differences
   edit.py (insertion / removal, Sec. 3.2 and App. A, plain numpy):
     splitmix64      - the generator's published outputs from seed 0
     sampling        - fraction and uniformity over 10^6 pixels, seed independence
@@ -49,7 +55,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
-_SRCS = [os.path.join(_HERE, f) for f in ("tsdf.cpp", "splat.cpp")]
+_SRCS = [os.path.join(_HERE, f) for f in ("tsdf.cpp", "splat.cpp", "sh.cpp")]
 
 # projected record layout (FP64), mirrors the enum in splat.cpp
 R_MX, R_MY, R_D, R_SIG, R_CA, R_CB, R_CC, R_QMAX, R_R, R_G, R_B, R_EX, R_EY, R_VIS, \
@@ -150,10 +156,38 @@ def raycast(spec, sdf, rgb, cam, near=0.2, far=0.0):
     return out_rgb, out_d, out_v, amb
 
 
+def _sh_degree(g) -> int:
+    return int(getattr(g, "sh_degree", 0) or 0)
+
+
+def sh_basis(dirs, degree: int) -> np.ndarray:
+    """Real orthonormal SH Y_lm (l = 1..degree, m = -l..l) at unit directions
+    dirs [n][3] -> [n][(degree + 1)^2 - 1]."""
+    d = _f64(dirs).reshape(-1, 3)
+    K = (degree + 1) ** 2 - 1
+    Y = np.zeros((d.shape[0], K))
+    lib().orc_sh_basis(ctypes.c_int(d.shape[0]), ctypes.c_int(degree), _p(d), _p(Y))
+    return Y
+
+
+def sh_colour(g, cam) -> np.ndarray:
+    """View-dependent colour [M][3] of a GaussianSet seen from cam's centre
+    (rgb itself when the set has no SH coefficients)."""
+    rgb = _f64(g.rgb)
+    D = _sh_degree(g)
+    if D == 0:
+        return rgb
+    out = np.zeros_like(rgb)
+    lib().orc_sh_colour(ctypes.c_int(g.M), ctypes.c_int(D), _p(_f64(g.means)), _p(rgb),
+                        _p(_f64(g.sh_rest)), _p(_f64(cam.t).reshape(3)), _p(out))
+    return out
+
+
 def project(g, cam, near=0.2):
     """Projection of a GaussianSet into one view -> (rec [M][16] f64, amb [M])."""
     M = g.M
     arrs = [_f64(a) for a in g.arrays()]
+    arrs[4] = sh_colour(g, cam)
     K, R, t = _cam(cam)
     rec = np.zeros((M, R_N))
     amb = np.zeros(M, dtype=np.int32)
@@ -226,7 +260,8 @@ def composite_backward(rec, Ct, Dt, eps, dC, dD, mode=OIT, f32=False, flip=None)
 
 def project_backward(g, cam, g2, near=0.2):
     """Adjoint of `project` -> dict of gradients (means, log_scales, quats,
-    opacity_logits, rgb), float64."""
+    opacity_logits, rgb, and sh_rest when the set has SH coefficients),
+    float64."""
     M = g.M
     arrs = [_f64(a) for a in g.arrays()]
     K, R, t = _cam(cam)
@@ -237,6 +272,14 @@ def project_backward(g, cam, g2, near=0.2):
                                _p(t), ctypes.c_double(near), _p(_f64(g2)), _p(out["means"]),
                                _p(out["log_scales"]), _p(out["quats"]),
                                _p(out["opacity_logits"]), _p(out["rgb"]))
+    D = _sh_degree(g)
+    if D > 0:
+        # the colour gradient reaches rgb unchanged, the SH coefficients through
+        # Y_lm(d) and the mean through the viewing direction d
+        out["sh_rest"] = np.zeros(g.sh_rest.shape)
+        lib().orc_sh_backward(ctypes.c_int(M), ctypes.c_int(D), _p(arrs[0]),
+                              _p(_f64(g.sh_rest)), _p(t), _p(np.ascontiguousarray(out["rgb"])),
+                              _p(out["means"]), _p(out["sh_rest"]))
     return out
 
 
