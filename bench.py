@@ -57,6 +57,9 @@ def parse():
                     help=f"frames of the sequence (room: {N_FRAMES}, large: {N_FRAMES_LARGE})")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="storage type of the colour images C_t, C_k, C*")
+    ap.add_argument("--sh-degree", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="view-dependent colour: SH coefficients of degree 1..D per Gaussian "
+                         "(drawn from N(0, 0.05^2)); 0 = the colour is rgb")
     ap.add_argument("--schedule", default="tiles", choices=["tiles", "per-gaussian"],
                     help="per-gaussian: the paper's sort-free form (unsorted tile lists, "
                          "one warp per Gaussian in the backward; OIT only)")
@@ -185,12 +188,17 @@ class ClockSampler:
 # ---------------------------------------------------------------- workload
 def make_workload(rank: int, args):
     from datagen import workloads
+    from datagen.scenes import with_sh
     if args.workload == "large":
-        return workloads.room(n_frames=args.frames or N_FRAMES_LARGE, M=M_GAUSS_LARGE, width=1280,
-                              height=720, size=5.12, n_vox=512, seed_scene=2 + 1000 * rank,
-                              seed_path=3 + 1000 * rank)
-    return workloads.room(n_frames=args.frames or N_FRAMES, M=M_GAUSS, seed_scene=2 + 1000 * rank,
-                          seed_path=3 + 1000 * rank)
+        w = workloads.room(n_frames=args.frames or N_FRAMES_LARGE, M=M_GAUSS_LARGE, width=1280,
+                           height=720, size=5.12, n_vox=512, seed_scene=2 + 1000 * rank,
+                           seed_path=3 + 1000 * rank)
+    else:
+        w = workloads.room(n_frames=args.frames or N_FRAMES, M=M_GAUSS, seed_scene=2 + 1000 * rank,
+                           seed_path=3 + 1000 * rank)
+    if args.sh_degree:
+        w.gaussians = with_sh(w.gaussians, args.sh_degree, seed=6 + rank, scale=0.05)
+    return w
 
 
 def workload_config(args, w):
@@ -201,7 +209,7 @@ def workload_config(args, w):
                         f"{s.nx}^3 TSDF at {100 * s.voxel:.0f} cm, {w.gaussians.M} Gaussians, "
                         f"{ITERS_PER_FRAME} iterations/frame",
             "blend": args.mode, "tile": args.tile, "colour_storage": args.precision,
-            "schedule": args.schedule,
+            "schedule": args.schedule, "sh_degree": args.sh_degree,
             "form": "CUDA graph per frame", "l2": "256 MB buffer written between steps (untimed)"}
 
 
@@ -599,8 +607,10 @@ def _oracle_iteration(w, frame, band, lam):
     L, dC, dD, nv, _ = oracle.loss(out["C"], out["D"], Ctgt, Dtgt, Dt, lam)
     g2 = oracle.composite_backward(rec, Ct, Dt, w.eps_depth, dC, dD)
     gr = oracle.project_backward(g, f.cam, g2, w.near)
-    p = np.concatenate([a.reshape(-1) for a in g.arrays()])
-    gg = np.concatenate([gr[k].reshape(-1) for k in ("means", "log_scales", "quats", "opacity_logits", "rgb")])
+    extra = [g.sh_rest] if g.sh_rest is not None else []
+    p = np.concatenate([a.reshape(-1) for a in g.arrays() + extra])
+    gg = np.concatenate([gr[k].reshape(-1) for k in ("means", "log_scales", "quats", "opacity_logits",
+                                                     "rgb", "sh_rest") if k in gr])
     m = np.zeros_like(p)
     v = np.zeros_like(p)
     oracle.adam(p, gg, m, v, 1e-3)
@@ -864,7 +874,7 @@ def run_sequence(args, rank, world, local):
                      precision=prec)
     vol = gps.Tsdf(w.tsdf, dev)
     mp = Mapper(vol, w.frames[0].cam, SEQ_CAPACITY, s, iterations=SEQ_ITERS, near=w.near,
-                device=dev)
+                sh_degree=args.sh_degree, device=dev)
     dev_frames = [(torch.from_numpy(f.rgb).to(dev), torch.from_numpy(f.depth).to(dev))
                   for f in w.frames]
     host_frames = [(torch.from_numpy(f.rgb).pin_memory(), torch.from_numpy(f.depth).pin_memory())
@@ -925,6 +935,7 @@ def run_sequence(args, rank, world, local):
                                f"{mp.sched.interval} frames with {SEQ_ITERS} iterations over "
                                f"{mp.sched.n_local} local + up to {mp.sched.n_global} keyframe views",
                    "tile": f"{tile[0]}x{tile[1]}", "colour_storage": args.precision,
+                   "sh_degree": args.sh_degree,
                    "form": "plain launches; the whole sequence is one timed region, "
                            "run once untimed before",
                    "l2": "256 MB buffer written before the timed region; the 336 MB TSDF "

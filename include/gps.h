@@ -27,7 +27,12 @@
  *     z in metres, 0 = invalid / no surface.
  *   - Gaussian parameters are float32 arrays: means [M][3], log_scales [M][3],
  *     quats [M][4] (w, x, y, z; normalised inside), opacity_logits [M]
- *     (sigma = sigmoid(logit)), rgb [M][3] (colour c_i used directly).
+ *     (sigma = sigmoid(logit)), rgb [M][3], and optionally spherical-harmonic
+ *     coefficients sh_rest [M][K][3] of degree 1..D (K = (D+1)^2 - 1, D <= 3).
+ *     The colour seen from a camera centre o is
+ *       c_i = rgb_i + sum_{l=1..D} sum_{m=-l..l} Y_lm(d) f_lm,  d = (p_i - o)/|p_i - o|,
+ *     Y_lm the real orthonormal harmonics (Condon-Shortley phase; per l the
+ *     coefficients are stored for m = -l..l), so with D = 0 the colour is rgb.
  */
 #ifndef GPS_H_
 #define GPS_H_
@@ -123,7 +128,8 @@ typedef struct GpsTsdf {
   uint8_t* brick_flags;
 } GpsTsdf;
 
-/* A Gaussian set, or a gradient / moment buffer of the same shape. */
+/* A Gaussian set, or a gradient / moment buffer of the same shape (a
+ * buffer's sh_degree must equal the set's). */
 typedef struct GpsGaussians {
   float* means;          /* [M][3] */
   float* log_scales;     /* [M][3] */
@@ -131,6 +137,8 @@ typedef struct GpsGaussians {
   float* opacity_logits; /* [M]    */
   float* rgb;            /* [M][3] */
   int32_t M;
+  int32_t sh_degree;     /* 0..3: degree of the view-dependent colour terms     */
+  float* sh_rest;        /* [M][(sh_degree+1)^2 - 1][3]; NULL when sh_degree = 0 */
 } GpsGaussians;
 
 /* One view of the second rendering pass.  Inputs are device images of this
@@ -170,10 +178,12 @@ typedef struct GpsRenderSettings {
 } GpsRenderSettings;
 
 /* Adam hyper-parameters; lr per group in the order means, log_scales, quats,
- * opacity_logits, rgb (App. C: 1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3 * 0.28209479). */
+ * opacity_logits, rgb (App. C: 1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3 * 0.28209479),
+ * and lr_sh_rest for the SH coefficients of degree >= 1 (App. C: 5e-4). */
 typedef struct GpsAdamHyper {
   float lr[5];
   float beta1, beta2, eps;
+  float lr_sh_rest;
 } GpsAdamHyper;
 
 /* Byte offsets (from the workspace base) of the regions of view `v`.  The

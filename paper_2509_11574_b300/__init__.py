@@ -39,6 +39,8 @@ STAGE_PROJECT, STAGE_BIN, STAGE_COMPOSITE, STAGE_COMPOSITE_BWD, STAGE_PROJECT_BW
 # learning rates of App. C; the RGB colour plays the role of the degree-0 SH
 # coefficient, whose value is scaled by the SH basis constant 0.28209479
 LR_APP_C = (1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3 * 0.28209479177387814)
+LR_SH_REST = 5e-4  # App. C: SH coefficients of degree >= 1
+SH_DEGREE_OF = {3: 1, 8: 2, 15: 3}  # coefficients per colour channel -> degree
 
 c_float, c_int32, c_int64, c_size_t, c_void_p = (ctypes.c_float, ctypes.c_int32, ctypes.c_int64,
                                                  ctypes.c_size_t, ctypes.c_void_p)
@@ -63,7 +65,8 @@ class GpsTsdf(ctypes.Structure):
 
 class GpsGaussians(ctypes.Structure):
     _fields_ = [("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p),
-                ("opacity_logits", c_void_p), ("rgb", c_void_p), ("M", c_int32)]
+                ("opacity_logits", c_void_p), ("rgb", c_void_p), ("M", c_int32),
+                ("sh_degree", c_int32), ("sh_rest", c_void_p)]
 
 
 class GpsView(ctypes.Structure):
@@ -108,7 +111,8 @@ def view_schedule(delta_angle_deg=30.0, delta_move=0.3, interval=10, n_global=4,
 
 
 class GpsAdamHyper(ctypes.Structure):
-    _fields_ = [("lr", c_float * 5), ("beta1", c_float), ("beta2", c_float), ("eps", c_float)]
+    _fields_ = [("lr", c_float * 5), ("beta1", c_float), ("beta2", c_float), ("eps", c_float),
+                ("lr_sh_rest", c_float)]
 
 
 class GpsWorkspaceLayout(ctypes.Structure):
@@ -234,27 +238,39 @@ def pose(cam) -> GpsPose:
 
 @dataclasses.dataclass
 class Gaussians:
-    """Gaussian parameters (or same-shaped gradients / moments) on the device."""
+    """Gaussian parameters (or same-shaped gradients / moments) on the device;
+    sh_rest [M][K][3] (K = 3, 8 or 15) adds view-dependent colour of degree
+    1, 2 or 3."""
     means: torch.Tensor
     log_scales: torch.Tensor
     quats: torch.Tensor
     opacity_logits: torch.Tensor
     rgb: torch.Tensor
+    sh_rest: Optional[torch.Tensor] = None
 
     @property
     def M(self) -> int:
         return int(self.means.shape[0])
 
+    @property
+    def sh_degree(self) -> int:
+        return 0 if self.sh_rest is None else SH_DEGREE_OF[int(self.sh_rest.shape[1])]
+
     def tensors(self) -> List[torch.Tensor]:
-        return [self.means, self.log_scales, self.quats, self.opacity_logits, self.rgb]
+        t = [self.means, self.log_scales, self.quats, self.opacity_logits, self.rgb]
+        return t + ([self.sh_rest] if self.sh_rest is not None else [])
 
     def c(self) -> GpsGaussians:
-        return GpsGaussians(*[_ptr(t) for t in self.tensors()], self.M)
+        return GpsGaussians(*[_ptr(t) for t in self.tensors()[:5]], self.M, self.sh_degree,
+                            _ptr(self.sh_rest))
 
     @staticmethod
     def from_numpy(gs, device="cuda") -> "Gaussians":
+        arrs = list(gs.arrays())
+        if getattr(gs, "sh_rest", None) is not None:
+            arrs.append(gs.sh_rest)
         return Gaussians(*[torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
-                           for a in gs.arrays()])
+                           for a in arrs])
 
     def zeros_like(self) -> "Gaussians":
         return Gaussians(*[torch.zeros_like(t) for t in self.tensors()])
@@ -528,8 +544,9 @@ def gps_select_views(keyframes: Sequence[int], frame: int, event: int,
 
 def adam_step(params: Gaussians, grads: Gaussians, m: Gaussians, v: Gaussians, lr=LR_APP_C,
               beta1=0.9, beta2=0.999, eps=1e-15, step: int = 1,
-              device_step: Optional[torch.Tensor] = None, stream=None) -> None:
-    h = GpsAdamHyper((c_float * 5)(*lr), beta1, beta2, eps)
+              device_step: Optional[torch.Tensor] = None, stream=None,
+              lr_sh_rest: float = LR_SH_REST) -> None:
+    h = GpsAdamHyper((c_float * 5)(*lr), beta1, beta2, eps, lr_sh_rest)
     pc, gc, mc, vc = params.c(), grads.c(), m.c(), v.c()
     _check(lib().adam_step(ctypes.byref(pc), ctypes.byref(gc), ctypes.byref(mc), ctypes.byref(vc),
                            ctypes.byref(h), step, _ptr(device_step), _stream(stream)))
@@ -587,11 +604,11 @@ class Adam:
     """Adam state (FP32 moments) for a Gaussian set; step() calls adam_step."""
 
     def __init__(self, params: Gaussians, lr=LR_APP_C, betas=(0.9, 0.999), eps=1e-15,
-                 device_step: bool = False):
+                 device_step: bool = False, lr_sh_rest: float = LR_SH_REST):
         self.params = params
         self.m = params.zeros_like()
         self.v = params.zeros_like()
-        self.lr, self.betas, self.eps = lr, betas, eps
+        self.lr, self.betas, self.eps, self.lr_sh_rest = lr, betas, eps, lr_sh_rest
         self.t = 0
         self.device_step = (torch.zeros(1, dtype=torch.int32, device=params.means.device)
                             if device_step else None)
@@ -599,23 +616,24 @@ class Adam:
     def step(self, grads: Gaussians, stream=None):
         if self.device_step is not None:
             adam_step(self.params, grads, self.m, self.v, self.lr, *self.betas, self.eps, 0,
-                      self.device_step, stream)
+                      self.device_step, stream, self.lr_sh_rest)
         else:
             self.t += 1
             adam_step(self.params, grads, self.m, self.v, self.lr, *self.betas, self.eps, self.t,
-                      None, stream)
+                      None, stream, self.lr_sh_rest)
 
 
 class RenderImages(torch.autograd.Function):
-    """C*, D*, W_G of one view as differentiable outputs of the five parameter
-    tensors; the backward calls render_backward with dL/dC*, dL/dD*.  The
-    renderer's workspace holds this forward's state until the backward: one
-    forward in flight per renderer."""
+    """C*, D*, W_G of one view as differentiable outputs of the parameter
+    tensors (means, log_scales, quats, logits, rgb[, sh_rest]); the backward
+    calls render_backward with dL/dC*, dL/dD*.  The renderer's workspace holds
+    this forward's state until the backward: one forward in flight per
+    renderer."""
 
     @staticmethod
-    def forward(ctx, renderer: Renderer, view: View, means, log_scales, quats, logits, rgb):
-        g = Gaussians(means.detach(), log_scales.detach(), quats.detach(), logits.detach(),
-                      rgb.detach())
+    def forward(ctx, renderer: Renderer, view: View, *params):
+        g = Gaussians(*[t.detach() for t in params])
+        means = params[0]
         H, W = view.cam.height, view.cam.width
         dev = means.device
         cdt = PREC_DTYPE[renderer.s.precision]
@@ -643,14 +661,14 @@ class RenderImages(torch.autograd.Function):
 
 
 class RenderLoss(torch.autograd.Function):
-    """Fused colour (+ depth) L1 loss of Eq. 6 over views with targets."""
+    """Fused colour (+ depth) L1 loss of Eq. 6 over views with targets, as a
+    function of the parameter tensors (means, log_scales, quats, logits,
+    rgb[, sh_rest])."""
 
     @staticmethod
-    def forward(ctx, renderer: Renderer, views: Sequence[View], means, log_scales, quats, logits,
-                rgb):
-        g = Gaussians(means.detach(), log_scales.detach(), quats.detach(), logits.detach(),
-                      rgb.detach())
-        loss = torch.zeros(1, device=means.device)
+    def forward(ctx, renderer: Renderer, views: Sequence[View], *params):
+        g = Gaussians(*[t.detach() for t in params])
+        loss = torch.zeros(1, device=params[0].device)
         renderer.forward(g, views, loss)
         ctx.renderer, ctx.views, ctx.g = renderer, views, g
         return loss[0]

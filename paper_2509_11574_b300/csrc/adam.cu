@@ -1,4 +1,5 @@
-// Adam over the five parameter groups (App. C learning rates), torch.optim.Adam
+// Adam over the parameter groups (App. C learning rates: the five of every set,
+// plus the SH coefficients of degree >= 1 when present), torch.optim.Adam
 // semantics, FP32 moments.  One launch covers all groups; each thread updates
 // four consecutive floats with 16-byte loads where the group allows it.  The
 // gradient is zeroed in the same pass (its write replaces the zero_grad pass).
@@ -9,6 +10,7 @@
 #include <cmath>
 
 #include "gps_common.cuh"
+#include "sh.cuh"
 
 namespace gps {
 
@@ -22,9 +24,11 @@ struct AdamGroup {
   int vec4;  // all four pointers 16-byte aligned
 };
 
+constexpr int kAdamGroups = 6;
+
 struct AdamArgs {
-  AdamGroup grp[5];
-  long long first_block[6];  // block offsets per group
+  AdamGroup grp[kAdamGroups];
+  long long first_block[kAdamGroups + 1];  // block offsets per group (empty groups: n = 0)
   float b1, b2, eps;
   float bc1, sbc2;  // 1 - b1^t and sqrt(1 - b2^t) when the step is known on the host
   int* device_step; // else: step t = *device_step + 1
@@ -41,7 +45,7 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   const long long blk = blockIdx.x;
   int gidx = 0;
 #pragma unroll
-  for (int k = 1; k < 5; ++k)
+  for (int k = 1; k < kAdamGroups; ++k)
     if (blk >= a.first_block[k]) gidx = k;
   const AdamGroup& G = a.grp[gidx];
   const long long base = ((blk - a.first_block[gidx]) * 256 + threadIdx.x) * 4;
@@ -84,25 +88,29 @@ cudaError_t launch_adam(const GpsGaussians& P, const GpsGaussians& Gr, const Gps
                         const GpsGaussians& Vo, const GpsAdamHyper& h, int step, int* device_step,
                         cudaStream_t st) {
   AdamArgs a{};
-  float* const pp[5] = {P.means, P.log_scales, P.quats, P.opacity_logits, P.rgb};
-  float* const gg[5] = {Gr.means, Gr.log_scales, Gr.quats, Gr.opacity_logits, Gr.rgb};
-  float* const mm[5] = {Mo.means, Mo.log_scales, Mo.quats, Mo.opacity_logits, Mo.rgb};
-  float* const vv[5] = {Vo.means, Vo.log_scales, Vo.quats, Vo.opacity_logits, Vo.rgb};
-  const int width[5] = {3, 3, 4, 1, 3};
+  float* const pp[kAdamGroups] = {P.means, P.log_scales, P.quats, P.opacity_logits, P.rgb,
+                                  P.sh_rest};
+  float* const gg[kAdamGroups] = {Gr.means, Gr.log_scales, Gr.quats, Gr.opacity_logits, Gr.rgb,
+                                  Gr.sh_rest};
+  float* const mm[kAdamGroups] = {Mo.means, Mo.log_scales, Mo.quats, Mo.opacity_logits, Mo.rgb,
+                                  Mo.sh_rest};
+  float* const vv[kAdamGroups] = {Vo.means, Vo.log_scales, Vo.quats, Vo.opacity_logits, Vo.rgb,
+                                  Vo.sh_rest};
+  const int width[kAdamGroups] = {3, 3, 4, 1, 3, P.sh_degree > 0 ? 3 * sh_coeffs(P.sh_degree) : 0};
   long long blocks = 0;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < kAdamGroups; ++k) {
     AdamGroup& G = a.grp[k];
     G.p = pp[k];
     G.g = gg[k];
     G.m = mm[k];
     G.v = vv[k];
     G.n = (long long)P.M * width[k];
-    G.lr = h.lr[k];
+    G.lr = k < 5 ? h.lr[k] : h.lr_sh_rest;
     G.vec4 = aligned16(G.p) && aligned16(G.g) && aligned16(G.m) && aligned16(G.v);
     a.first_block[k] = blocks;
     blocks += (G.n + 1023) / 1024;
   }
-  a.first_block[5] = blocks;
+  a.first_block[kAdamGroups] = blocks;
   a.b1 = h.beta1;
   a.b2 = h.beta2;
   a.eps = h.eps;

@@ -161,7 +161,11 @@ bool finite_cam(const GpsIntrinsics& K, const GpsPose& P) {
 int32_t check_gaussians(const GpsGaussians* g, const char* what) {
   if (!g) return fail(GPS_ERR_INVALID_ARG, "%s is NULL", what);
   if (g->M < 0) return fail(GPS_ERR_INVALID_ARG, "%s.M < 0", what);
+  if (g->sh_degree < 0 || g->sh_degree > 3)
+    return fail(GPS_ERR_INVALID_ARG, "%s.sh_degree must be 0..3", what);
   if (g->M == 0) return GPS_OK;
+  if (g->sh_degree > 0 && (!g->sh_rest || !aligned(g->sh_rest, 4)))
+    return fail(GPS_ERR_INVALID_ARG, "%s.sh_rest must be a 4-byte aligned array", what);
   if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->rgb)
     return fail(GPS_ERR_INVALID_ARG, "%s has a NULL array", what);
   if (!aligned(g->means, 4) || !aligned(g->log_scales, 4) || !aligned(g->quats, 16) ||
@@ -392,6 +396,8 @@ int32_t render_backward(const GpsGaussians* g, const GpsView* views, int32_t n_v
   if (int32_t e = check_render_args(g, views, n_views, s, ws, ws_bytes)) return e;
   if (int32_t e = check_gaussians(grads, "grads")) return e;
   if (grads->M != g->M) return fail(GPS_ERR_INVALID_ARG, "grads.M != gaussians.M");
+  if (grads->sh_degree != g->sh_degree)
+    return fail(GPS_ERR_INVALID_ARG, "grads.sh_degree != gaussians.sh_degree");
   for (int vi = 0; vi < n_views; ++vi) {
     const GpsView& vw = views[vi];
     if (!vw.grad_rgb && !vw.grad_depth && (!vw.target_rgb || !vw.target_depth))
@@ -430,6 +436,9 @@ int32_t adam_step(GpsGaussians* params, GpsGaussians* grads, GpsGaussians* m, Gp
   if (int32_t e = check_gaussians(v, "v")) return e;
   if (grads->M != params->M || m->M != params->M || v->M != params->M)
     return fail(GPS_ERR_INVALID_ARG, "group sizes differ");
+  if (grads->sh_degree != params->sh_degree || m->sh_degree != params->sh_degree ||
+      v->sh_degree != params->sh_degree)
+    return fail(GPS_ERR_INVALID_ARG, "SH degrees differ");
   if (!hyper) return fail(GPS_ERR_INVALID_ARG, "hyper is NULL");
   if (step <= 0 && !device_step) return fail(GPS_ERR_INVALID_ARG, "step <= 0 needs device_step");
   if (!(hyper->beta1 >= 0 && hyper->beta1 < 1 && hyper->beta2 >= 0 && hyper->beta2 < 1 && hyper->eps >= 0))

@@ -14,6 +14,7 @@
 #include <cstdint>
 
 #include "gps_common.cuh"
+#include "sh.cuh"
 
 namespace gps {
 
@@ -216,6 +217,9 @@ __global__ void __launch_bounds__(kEditThreads) insert_emit_kernel(InsertArgs a)
   col[0] = ld_col(a.target, p, a.prec);
   col[1] = ld_col(a.target, npx + p, a.prec);
   col[2] = ld_col(a.target, 2 * npx + p, a.prec);
+  // no view dependence yet: SH coefficients of degree >= 1 start at zero
+  const int nsh = a.g.sh_degree > 0 ? 3 * sh_coeffs(a.g.sh_degree) : 0;
+  for (int c = 0; c < nsh; ++c) a.g.sh_rest[nsh * slot + c] = 0.f;
   const GpsGaussians* zs[3] = {&a.m, &a.v, &a.gr};
   for (int k = 0; k < 3; ++k) {
     const GpsGaussians& z = *zs[k];
@@ -227,6 +231,7 @@ __global__ void __launch_bounds__(kEditThreads) insert_emit_kernel(InsertArgs a)
     }
     reinterpret_cast<float4*>(z.quats)[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
     z.opacity_logits[slot] = 0.f;
+    for (int c = 0; c < nsh; ++c) z.sh_rest[nsh * slot + c] = 0.f;
   }
 }
 
@@ -312,16 +317,53 @@ __global__ void __launch_bounds__(kEditThreads) remove_scatter_kernel(RemoveArgs
   store_row(z, (size_t)i, r);
 }
 
+// The SH coefficient rows (3K floats) move through the same [M][14] scratch,
+// 14 columns [c0, c0 + w) at a time.
+__global__ void __launch_bounds__(kEditThreads) remove_gather_cols_kernel(RemoveArgs a,
+                                                                         const float* src,
+                                                                         int stride, int c0,
+                                                                         int w) {
+  __shared__ uint32_t s_warp[kEditThreads / 32];
+  const int i = blockIdx.x * kEditThreads + threadIdx.x;
+  const bool k = i < a.M && a.keep[i];
+  const uint32_t rank = block_rank(k, s_warp);
+  if (!k) return;
+  float* d = a.scratch + 14 * (size_t)(a.block_offsets[blockIdx.x] + rank);
+  for (int c = 0; c < w; ++c) d[c] = src[(size_t)i * stride + c0 + c];
+}
+
+__global__ void __launch_bounds__(kEditThreads) remove_scatter_cols_kernel(RemoveArgs a,
+                                                                          float* dst, int stride,
+                                                                          int c0, int w,
+                                                                          int clear) {
+  const int i = blockIdx.x * kEditThreads + threadIdx.x;
+  if (i >= a.M) return;
+  const int kept = *a.count;
+  if (i < kept) {
+    const float* s = a.scratch + 14 * (size_t)i;
+    for (int c = 0; c < w; ++c) dst[(size_t)i * stride + c0 + c] = s[c];
+  } else if (clear) {
+    for (int c = 0; c < w; ++c) dst[(size_t)i * stride + c0 + c] = 0.f;
+  }
+}
+
 cudaError_t launch_remove(const RemoveArgs& a, cudaStream_t st) {
   if (a.M <= 0) return cudaMemsetAsync(a.count, 0, sizeof(int32_t), st);
   const int nblk = (a.M + kEditThreads - 1) / kEditThreads;
   remove_flag_kernel<<<nblk, kEditThreads, 0, st>>>(a);
   edit_scan_kernel<<<1, 1024, 0, st>>>(a.block_counts, a.block_offsets, nblk, 0, a.M, a.count);
   const GpsGaussians* groups[4] = {&a.g, &a.m, &a.v, &a.gr};
+  const int nsh = a.g.sh_degree > 0 ? 3 * sh_coeffs(a.g.sh_degree) : 0;
   for (int k = 0; k < 4; ++k) {
     if (!groups[k]->means) continue;
     remove_gather_kernel<<<nblk, kEditThreads, 0, st>>>(a, *groups[k]);
     remove_scatter_kernel<<<nblk, kEditThreads, 0, st>>>(a, *groups[k], k > 0 ? 1 : 0);
+    for (int c0 = 0; c0 < nsh; c0 += 14) {
+      const int w = nsh - c0 < 14 ? nsh - c0 : 14;
+      remove_gather_cols_kernel<<<nblk, kEditThreads, 0, st>>>(a, groups[k]->sh_rest, nsh, c0, w);
+      remove_scatter_cols_kernel<<<nblk, kEditThreads, 0, st>>>(a, groups[k]->sh_rest, nsh, c0,
+                                                                w, k > 0 ? 1 : 0);
+    }
   }
   return cudaGetLastError();
 }
@@ -362,7 +404,8 @@ int32_t edit_fail(int32_t code, const char* msg) {
 
 bool complete(const GpsGaussians* z) {
   return z && z->means && z->log_scales && z->quats && z->opacity_logits && z->rgb &&
-         (reinterpret_cast<uintptr_t>(z->quats) & 15) == 0;
+         (reinterpret_cast<uintptr_t>(z->quats) & 15) == 0 && z->sh_degree >= 0 &&
+         z->sh_degree <= 3 && (z->sh_degree == 0 || z->sh_rest);
 }
 
 GpsGaussians or_null(const GpsGaussians* z) {
@@ -391,8 +434,9 @@ int32_t insert_gaussians(GpsGaussians* gaussians, int32_t capacity, GpsGaussians
       !target_rgb || !s || !scratch || !count)
     return edit_fail(GPS_ERR_INVALID_ARG, "insert_gaussians: NULL argument or Gaussian array");
   for (const GpsGaussians* z : {m, v, grads})
-    if (z && !complete(z))
-      return edit_fail(GPS_ERR_INVALID_ARG, "insert_gaussians: incomplete moment / gradient set");
+    if (z && (!complete(z) || z->sh_degree != gaussians->sh_degree))
+      return edit_fail(GPS_ERR_INVALID_ARG,
+                       "insert_gaussians: incomplete moment / gradient set or another SH degree");
   if (gaussians->M < 0 || capacity < gaussians->M || K->width <= 0 || K->height <= 0 ||
       !(K->fx > 0) || s->radius < 0 || s->radius > 16 || !(s->sample_fraction >= 0) ||
       !(s->sample_fraction <= 1) || !(s->delta_c >= 0) || !(s->delta_w > 0) ||
@@ -443,7 +487,7 @@ int32_t remove_gaussians(GpsGaussians* gaussians, GpsGaussians* m, GpsGaussians*
   if (!complete(gaussians) || !s || !scratch || !count || gaussians->M < 0)
     return edit_fail(GPS_ERR_INVALID_ARG, "remove_gaussians: NULL argument or Gaussian array");
   for (const GpsGaussians* z : {m, v, grads})
-    if (z && (!complete(z) || z->M != gaussians->M))
+    if (z && (!complete(z) || z->M != gaussians->M || z->sh_degree != gaussians->sh_degree))
       return edit_fail(GPS_ERR_INVALID_ARG, "remove_gaussians: moment / gradient set mismatch");
   if (!(s->delta_sigma > 0 && s->delta_sigma < 1) || !(s->delta_smax > 0) || !(s->delta_smin > 0))
     return edit_fail(GPS_ERR_INVALID_ARG, "remove_gaussians: bad thresholds");

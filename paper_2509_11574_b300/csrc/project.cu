@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "gps_common.cuh"
+#include "sh.cuh"
 
 namespace gps {
 
@@ -14,7 +15,116 @@ struct Params {
   const float* quats;
   const float* logits;
   const float* rgb;
+  const float* sh;  // [M][K][3], K = sh_coeffs(sh_degree); null when sh_degree = 0
+  int sh_degree;
 };
+
+// SH rows of a block's Gaussians are staged in shared memory: the global
+// rows (3K floats, 12 K bytes) are read and written with consecutive threads
+// on consecutive floats, and each thread then works on its own row at an odd
+// word stride, which keeps the per-thread accesses free of bank conflicts.
+template <int DEG>
+struct ShRows {
+  static constexpr int K = sh_coeffs(DEG);
+  static constexpr int K3 = 3 * K;
+  static constexpr int STRIDE = K3 | 1;
+};
+
+constexpr int kProjThreads = 256;  // block size of both projection kernels
+
+// rows [base, base + n) of a [M][K3] array -> s[r * STRIDE + c].  Each thread
+// issues its K3 loads before the first store, so they are in flight together.
+template <int DEG>
+__device__ __forceinline__ void stage_rows(const float* __restrict__ g, long long base, int n,
+                                           float* s) {
+  using R = ShRows<DEG>;
+  const float* src = g + base * R::K3;
+  const int total = n * R::K3;
+  float v[R::K3];
+#pragma unroll
+  for (int j = 0; j < R::K3; ++j) {
+    const int e = j * kProjThreads + threadIdx.x;
+    v[j] = e < total ? __ldg(src + e) : 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < R::K3; ++j) {
+    const int e = j * kProjThreads + threadIdx.x;
+    const int r = e / R::K3;
+    if (e < total) s[r * R::STRIDE + (e - r * R::K3)] = v[j];
+  }
+}
+
+// dst rows [base, base + n) += s rows, loads batched as in stage_rows.
+template <int DEG>
+__device__ __forceinline__ void add_rows(float* __restrict__ g, long long base, int n,
+                                         const float* s) {
+  using R = ShRows<DEG>;
+  float* dst = g + base * R::K3;
+  const int total = n * R::K3;
+  float v[R::K3];
+#pragma unroll
+  for (int j = 0; j < R::K3; ++j) {
+    const int e = j * kProjThreads + threadIdx.x;
+    v[j] = e < total ? dst[e] : 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < R::K3; ++j) {
+    const int e = j * kProjThreads + threadIdx.x;
+    const int r = e / R::K3;
+    if (e < total) dst[e] = v[j] + s[r * R::STRIDE + (e - r * R::K3)];
+  }
+}
+
+// Colour of Gaussian i seen from the camera centre (Sec. 3.1, SH of degree
+// DEG over rgb); f: its coefficient row (K3 floats).
+template <int DEG>
+__device__ __forceinline__ float3 view_colour(const Params& P, int i, const Cam& c,
+                                              const float* f) {
+  const float* col = P.rgb + 3 * (size_t)i;
+  float3 out = make_float3(col[0], col[1], col[2]);
+  if constexpr (DEG > 0) {
+    const float* p = P.means + 3 * (size_t)i;
+    const float vx = p[0] - c.t[0], vy = p[1] - c.t[1], vz = p[2] - c.t[2];
+    const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+    float Y[kShMaxCoeffs];
+    sh_eval(DEG, vx * inv, vy * inv, vz * inv, Y);
+#pragma unroll
+    for (int k = 0; k < ShRows<DEG>::K; ++k) {
+      out.x += Y[k] * f[3 * k];
+      out.y += Y[k] * f[3 * k + 1];
+      out.z += Y[k] * f[3 * k + 2];
+    }
+  }
+  return out;
+}
+
+// Adjoint of view_colour given dL/dc = g: adds Y_k(d) g to the coefficient
+// gradient row dsh and returns the mean's gradient through the direction,
+// (I - d d^T) / |v| sum_k grad Y_k (f_k . g).
+template <int DEG>
+__device__ __forceinline__ float3 view_colour_adjoint(const Params& P, int i, const Cam& c,
+                                                      float3 g, const float* f, float* dsh) {
+  const float* p = P.means + 3 * (size_t)i;
+  const float vx = p[0] - c.t[0], vy = p[1] - c.t[1], vz = p[2] - c.t[2];
+  const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+  const float dx = vx * inv, dy = vy * inv, dz = vz * inv;
+  float Y[kShMaxCoeffs], w[kShMaxCoeffs];
+  sh_eval(DEG, dx, dy, dz, Y);
+#pragma unroll
+  for (int k = 0; k < kShMaxCoeffs; ++k) {
+    if (k < ShRows<DEG>::K) {
+      dsh[3 * k] += Y[k] * g.x;
+      dsh[3 * k + 1] += Y[k] * g.y;
+      dsh[3 * k + 2] += Y[k] * g.z;
+      w[k] = f[3 * k] * g.x + f[3 * k + 1] * g.y + f[3 * k + 2] * g.z;
+    } else {
+      w[k] = 0.0f;
+    }
+  }
+  const float3 gd = sh_grad_dot(DEG, dx, dy, dz, w);
+  const float dot = gd.x * dx + gd.y * dy + gd.z * dz;
+  return make_float3((gd.x - dx * dot) * inv, (gd.y - dy * dot) * inv, (gd.z - dz * dot) * inv);
+}
 
 struct ProjState {
   bool vis;
@@ -102,12 +212,20 @@ __device__ __forceinline__ void project_gaussian(const Params& P, int i, const C
 // K3: records, plus the block's super-tile histogram and range reservation
 // (first half of the binning).  Block row blockIdx.y projects for view
 // blockIdx.y of the batch.  sup_count must be zero on entry.
-__global__ void __launch_bounds__(256) project_kernel(Params P, int M, float near_,
+// Shared memory: the super-tile histogram (max_nsup words, rounded up to an
+// even count) and, with DEG > 0, the block's SH rows.
+template <int DEG>
+__global__ void __launch_bounds__(256) project_kernel(Params P, int M, float near_, int hist_words,
                                                       const __grid_constant__ ViewBatch vb) {
   extern __shared__ uint32_t s_hist[];
+  float* s_f = reinterpret_cast<float*>(s_hist + hist_words);
   const ViewDev& v = vb.v[blockIdx.y];
   const int sh = v.sup_shift, sup_x = v.sup_x, nsup = v.sup_x * v.sup_y;
   for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_hist[s] = 0;
+  if constexpr (DEG > 0) {
+    const long long base = (long long)blockIdx.x * blockDim.x;
+    stage_rows<DEG>(P.sh, base, (int)min((long long)blockDim.x, M - base), s_f);
+  }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < M) {
@@ -121,10 +239,10 @@ __global__ void __launch_bounds__(256) project_kernel(Params P, int M, float nea
       r[2] = make_float4(0.f, 0.f, 0.f, -1.0f);
       r[3] = make_float4(-1.0f, 0.f, 0.f, 0.f);
     } else {
-      const float* col = P.rgb + 3 * (size_t)i;
+      const float3 col = view_colour<DEG>(P, i, cam, s_f + threadIdx.x * ShRows<DEG>::STRIDE);
       r[0] = make_float4(o.mx, o.my, o.tc[2], o.sig);
       r[1] = make_float4(o.ca, o.cb, o.cc, o.qmax);
-      r[2] = make_float4(col[0], col[1], col[2], o.ex);
+      r[2] = make_float4(col.x, col.y, col.z, o.ex);
       r[3] = make_float4(o.ey, 0.f, 0.f, 0.f);
       int x0, x1, y0, y1;
       record_rect(o.mx, o.my, o.ex, o.ey, cam.W, cam.H, x0, x1, y0, y1);
@@ -240,58 +358,118 @@ __device__ __forceinline__ void project_adjoint(const ProjState& o, const Cam& c
 }
 
 // K8: adjoint of the projection, summed over the batch's views in view order
-// and accumulated (+=) into the parameter gradients once per Gaussian.
+// and accumulated (+=) into the parameter gradients once per Gaussian.  With
+// DEG > 0 the block stages its Gaussians' SH rows and their gradient rows in
+// shared memory (2 x 256 x STRIDE floats).
+template <int DEG>
 __global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, float near_,
                                                                const __grid_constant__ ViewBatch vb,
                                                                GpsGaussians grads) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
+  extern __shared__ float s_sh[];
+  using R = ShRows<DEG>;
+  const long long base = (long long)blockIdx.x * blockDim.x;
+  const int n_blk = (int)min((long long)blockDim.x, M - base);
+  float* s_f = s_sh;
+  float* s_g = s_sh + blockDim.x * R::STRIDE;
+  if constexpr (DEG > 0) {
+    stage_rows<DEG>(P.sh, base, n_blk, s_f);
+#pragma unroll
+    for (int j = 0; j < R::STRIDE; ++j) s_g[j * kProjThreads + threadIdx.x] = 0.0f;
+    __syncthreads();
+  }
+  const int i = (int)base + threadIdx.x;
   ParamGrad a{};
   bool any = false;
-  for (int k = 0; k < vb.n; ++k) {
+  for (int k = 0; k < vb.n && i < M; ++k) {
     const Cam cam = vb.v[k].cam;
     ProjState o;
     project_gaussian(P, i, cam, near_, o);
     if (!o.vis) continue;
     const float4* g2 = vb.v[k].grad2d + 3 * (size_t)i;
-    project_adjoint(o, cam, g2[0], g2[1], g2[2], a);
+    const float4 ga = g2[0], gb = g2[1], gc = g2[2];
+    project_adjoint(o, cam, ga, gb, gc, a);
+    if constexpr (DEG > 0) {
+      const float3 gm = view_colour_adjoint<DEG>(P, i, cam, make_float3(gb.z, gb.w, gc.x),
+                                                 s_f + threadIdx.x * R::STRIDE,
+                                                 s_g + threadIdx.x * R::STRIDE);
+      a.mean[0] += gm.x;
+      a.mean[1] += gm.y;
+      a.mean[2] += gm.z;
+    }
     any = true;
   }
-  if (!any) return;
+  if (any) {
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    grads.means[3 * (size_t)i + r] += a.mean[r];
-    grads.log_scales[3 * (size_t)i + r] += a.ls[r];
-    grads.rgb[3 * (size_t)i + r] += a.rgb[r];
+    for (int r = 0; r < 3; ++r) {
+      grads.means[3 * (size_t)i + r] += a.mean[r];
+      grads.log_scales[3 * (size_t)i + r] += a.ls[r];
+      grads.rgb[3 * (size_t)i + r] += a.rgb[r];
+    }
+    float4* dq = reinterpret_cast<float4*>(grads.quats) + i;
+    float4 q = *dq;
+    q.x += a.q[0];
+    q.y += a.q[1];
+    q.z += a.q[2];
+    q.w += a.q[3];
+    *dq = q;
+    grads.opacity_logits[i] += a.logit;
   }
-  float4* dq = reinterpret_cast<float4*>(grads.quats) + i;
-  float4 q = *dq;
-  q.x += a.q[0];
-  q.y += a.q[1];
-  q.z += a.q[2];
-  q.w += a.q[3];
-  *dq = q;
-  grads.opacity_logits[i] += a.logit;
+  if constexpr (DEG > 0) {
+    __syncthreads();
+    add_rows<DEG>(grads.sh_rest, base, n_blk, s_g);
+  }
+}
+
+template <int DEG>
+cudaError_t launch_project_t(const Params& P, int M, float near_, const ViewBatch& vb,
+                             int max_nsup, cudaStream_t st) {
+  const int hist_words = (max_nsup + 1) & ~1;
+  const size_t smem =
+      (size_t)hist_words * 4 + (DEG > 0 ? kProjThreads * ShRows<DEG>::STRIDE * 4 : 0);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        project_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  project_kernel<DEG><<<dim3((M + kProjThreads - 1) / kProjThreads, vb.n), kProjThreads, smem,
+                       st>>>(P, M, near_, hist_words, vb);
+  return cudaGetLastError();
+}
+
+template <int DEG>
+cudaError_t launch_project_backward_t(const Params& P, int M, float near_, const ViewBatch& vb,
+                                      const GpsGaussians& grads, cudaStream_t st) {
+  const size_t smem = DEG > 0 ? 2 * kProjThreads * ShRows<DEG>::STRIDE * 4 : 0;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        project_backward_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  project_backward_kernel<DEG><<<(M + kProjThreads - 1) / kProjThreads, kProjThreads, smem, st>>>(
+      P, M, near_, vb, grads);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_project(const GpsGaussians& g, float near_, const ViewBatch& vb, int max_nsup,
                            cudaStream_t st) {
-  Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb};
-  const size_t smem = (size_t)max_nsup * sizeof(uint32_t);
-  if (smem > 48 * 1024) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  const Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb, g.sh_rest, g.sh_degree};
+  switch (g.sh_degree) {
+    case 1: return launch_project_t<1>(P, g.M, near_, vb, max_nsup, st);
+    case 2: return launch_project_t<2>(P, g.M, near_, vb, max_nsup, st);
+    case 3: return launch_project_t<3>(P, g.M, near_, vb, max_nsup, st);
+    default: return launch_project_t<0>(P, g.M, near_, vb, max_nsup, st);
   }
-  project_kernel<<<dim3((g.M + 255) / 256, vb.n), 256, smem, st>>>(P, g.M, near_, vb);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_project_backward(const GpsGaussians& g, float near_, const ViewBatch& vb,
                                     const GpsGaussians& grads, cudaStream_t st) {
-  Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb};
-  project_backward_kernel<<<(g.M + 255) / 256, 256, 0, st>>>(P, g.M, near_, vb, grads);
-  return cudaGetLastError();
+  const Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb, g.sh_rest, g.sh_degree};
+  switch (g.sh_degree) {
+    case 1: return launch_project_backward_t<1>(P, g.M, near_, vb, grads, st);
+    case 2: return launch_project_backward_t<2>(P, g.M, near_, vb, grads, st);
+    case 3: return launch_project_backward_t<3>(P, g.M, near_, vb, grads, st);
+    default: return launch_project_backward_t<0>(P, g.M, near_, vb, grads, st);
+  }
 }
 
 }  // namespace gps

@@ -43,7 +43,7 @@ class Reconstruction:
 
 
 def _rows(g: Gaussians, n: int) -> Gaussians:
-    return Gaussians(*[t[:n] for t in g.tensors()])
+    return Gaussians(*[t[:n] for t in g.tensors()])  # sh_rest too, when present
 
 
 class Mapper:
@@ -52,7 +52,7 @@ class Mapper:
                  edit: Optional[GpsEditSettings] = None,
                  sched: Optional[GpsViewSchedule] = None,
                  iterations: int = 20, lr=LR_APP_C, near: float = 0.2,
-                 max_views: Optional[int] = None, device="cuda"):
+                 max_views: Optional[int] = None, sh_degree: int = 0, device="cuda"):
         self.vol, self.cam, self.capacity = vol, cam, capacity
         self.s = GpsRenderSettings.from_buffer_copy(s if s is not None else
                                                     render_settings(tile=(16, 8)))
@@ -68,12 +68,15 @@ class Mapper:
         dev = torch.device(device)
         H, W = cam.height, cam.width
 
+        K = (sh_degree + 1) ** 2 - 1
+
         def zeros():
             return Gaussians(torch.zeros(capacity, 3, device=dev),
                              torch.zeros(capacity, 3, device=dev),
                              torch.zeros(capacity, 4, device=dev),
                              torch.zeros(capacity, device=dev),
-                             torch.zeros(capacity, 3, device=dev))
+                             torch.zeros(capacity, 3, device=dev),
+                             torch.zeros(capacity, K, 3, device=dev) if K else None)
         self.g, self.grads, self.m, self.v = zeros(), zeros(), zeros(), zeros()
         self.M = 0
         self.t = 0          # Adam step counter shared by all reconstructions

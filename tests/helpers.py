@@ -108,5 +108,8 @@ def sign_flip_allowance(g64, cam, rec, Ct, Dt, eps, mode, ambC, ambD, nv, lam):
         part = {k: 2.0 * np.abs(v) for k, v in gr.items()}
         total = part if total is None else {k: total[k] + part[k] for k in total}
     if total is None:
-        total = {k: 0.0 for k in ("means", "log_scales", "quats", "opacity_logits", "rgb")}
+        keys = ["means", "log_scales", "quats", "opacity_logits", "rgb"]
+        if getattr(g64, "sh_rest", None) is not None:
+            keys.append("sh_rest")
+        total = {k: 0.0 for k in keys}
     return total

@@ -301,19 +301,21 @@ def test_end_to_end_reduced_precision_colour(mode, prec):
     _end_to_end(w, mode, lam=1.0, prec=prec)
 
 
-def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False, prec=gps.PREC_FP32):
+def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False, prec=gps.PREC_FP32, gs=None):
+    """gs: the Gaussian set to render (default: the workload's)."""
     f = w.frames[0]
     H, W = f.cam.height, f.cam.width
+    gs = gs if gs is not None else w.gaussians
     Ct, Dt, _, _ = oracle_sdf_images(w)
     # colour images as stored (oracle.quantise: float32 for PREC_FP32)
     Ct = oracle.quantise(Ct, prec).astype(np.float32)
     Ctgt = oracle.quantise(f.rgb, prec).astype(np.float32)
-    ref = oracle.render_loss_grads(w.gaussians.astype(np.float64), f.cam, Ct, Dt, Ctgt, f.depth,
+    ref = oracle.render_loss_grads(gs.astype(np.float64), f.cam, Ct, Dt, Ctgt, f.depth,
                                    eps=w.eps_depth, lambda_depth=lam, mode=mode)
     s = gps.settings(eps_depth=w.eps_depth, lambda_depth=lam, blend_mode=mode, tile=tile,
                      deterministic=deterministic, precision=prec)
-    r = gps.Renderer(w.gaussians.M, [f.cam], s)
-    g = gps.Gaussians.from_numpy(w.gaussians)
+    r = gps.Renderer(gs.M, [f.cam], s)
+    g = gps.Gaussians.from_numpy(gs)
     cdt = gps.PREC_DTYPE[prec]
     v = gps.View(f.cam, cuda(Ct).to(cdt), cuda(Dt), cuda(Ctgt).to(cdt), cuda(f.depth),
                  out_rgb=torch.empty(3, H, W, device="cuda", dtype=cdt),
@@ -348,7 +350,7 @@ def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False, prec=gps.PREC_
     # A counting decision within the FP32 error band of its threshold may go
     # either way: the oracle evaluated with every such decision inverted
     # bounds how far the gradients can move (single flips per pixel).
-    alt = oracle.render_loss_grads(w.gaussians.astype(np.float64), f.cam, Ct, Dt, Ctgt, f.depth,
+    alt = oracle.render_loss_grads(gs.astype(np.float64), f.cam, Ct, Dt, Ctgt, f.depth,
                                    eps=w.eps_depth, lambda_depth=lam, mode=mode,
                                    flip=(4e-6, 2e-6))
     # Gaussians whose own near-threshold alpha is more than 1e-4 of their
@@ -360,7 +362,7 @@ def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False, prec=gps.PREC_
     valid = (f.depth > 0) & (Dt > 0)
     ambC = (np.abs(out["C"] - Ctgt) < 2e-5) & valid[None]
     ambD = (np.abs(out["D"] - f.depth) < 2e-5 * np.abs(f.depth)) & valid
-    ga = sign_flip_allowance(w.gaussians.astype(np.float64), f.cam, rec, Ct, Dt, w.eps_depth, mode,
+    ga = sign_flip_allowance(gs.astype(np.float64), f.cam, rec, Ct, Dt, w.eps_depth, mode,
                              ambC, ambD if lam else np.zeros_like(ambD), ref["n_valid"], lam)
     allow = {k: ga[k] + np.abs(alt["grads"][k] - ref["grads"][k]) for k in ga}
     # 1e-3 here (1e-4 in the staged tests, where decisions are identical):
