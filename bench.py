@@ -944,7 +944,9 @@ def run_sequence(args, rank, world, local):
         "reconstructions": hist,
         "keyframes": list(mp.keyframes),
         "e2e": {"value": n / ms_e2e * 1e3 * world, "unit": "frames/s",
-                "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": 8 * len(hist) // n},
+                "h2d_bytes_per_step": bytes_in,
+                # per reconstruction: two int32 counts, two float losses, one status word
+                "d2h_bytes_per_step": 20 * len(hist) / n},
         "status": st, "clocks": clk, "gpu": torch.cuda.get_device_name(dev),
     }
     print(json.dumps(line), flush=True)
