@@ -36,6 +36,14 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
     mask, removal   - threshold cases by hand
     insert          - planes: means, colours, opacity, disc radius from pixel
                       spacing, short axis on the analytic normal (scipy Rotation)
+  icp.py (camera tracking, Sec. 3.2, Eq. 5, point-to-plane ICP, plain numpy):
+    se3_exp         - scipy.linalg.expm of the twist matrix
+    residual / J    - central differences of the residual under exp(xi) T
+    pyramid, normals- 2x2 means and coarse intrinsics by hand; a tilted plane's
+                      analytic normal
+    track           - a rendered frame's known pose recovered from a 2 cm /
+                      1.5 degree start (3 seeds); a single plane leaves the
+                      pose unchanged (singular system)
   schedule.py (keyframes and optimisation views, Sec. 3.2, Fig. 5, App. C):
     is_keyframe     - rotations (scipy) and translations just under / over the
                       thresholds, relative to a rotated last keyframe
