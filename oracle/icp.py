@@ -27,8 +27,9 @@ Readings of points the paper leaves open (listed with the other readings):
 - Normals (current levels and reference): cross product of the central
   differences (V(x+1) - V(x-1)) x (V(y+1) - V(y-1)), turned towards the
   camera; a pixel lacking any of its four neighbours has no normal.
-- An iteration whose A is not positive definite (fewer than six independent
-  constraints) leaves T unchanged.
+- An iteration with fewer than six inliers, or whose A is not positive
+  definite with every Cholesky pivot above 1e-6 of A's largest diagonal entry
+  (fewer than six well-determined directions), leaves T unchanged.
 """
 from __future__ import annotations
 
@@ -150,10 +151,13 @@ def normal_equations(P, q, n):
 
 
 def gauss_newton_step(A, b):
-    """xi = -A^-1 b, or None when A is not positive definite."""
+    """xi = -A^-1 b, or None when A is not positive definite or a Cholesky
+    pivot L_jj^2 is at most 1e-6 of A's largest diagonal entry."""
     try:
         L = np.linalg.cholesky(A)
     except np.linalg.LinAlgError:
+        return None
+    if np.min(np.diag(L)) ** 2 <= 1e-6 * np.max(np.diag(A)):
         return None
     y = np.linalg.solve(L, -b)
     return np.linalg.solve(L.T, y)
