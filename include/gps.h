@@ -389,6 +389,52 @@ GPS_API int32_t remove_gaussians(GpsGaussians* gaussians, GpsGaussians* m, GpsGa
                                  GpsGaussians* grads, const GpsEditSettings* s, void* scratch,
                                  size_t scratch_bytes, int32_t* count, void* stream);
 
+/* ------------------------------------------------------------ camera tracking
+ * Point-to-plane ICP (Sec. 3.2 "Camera tracking", Eq. 5, after KinectFusion
+ * and InfiniTAM).  Gauss-Newton over a depth pyramid, coarsest level first;
+ * one iteration at one level:
+ *   1. p = T V_k(u) for every pixel u of the level with a depth and a normal
+ *      (V_k: the level's camera-frame vertex map, T the current estimate);
+ *   2. u^ = the nearest pixel, floor(x + 0.5), of p projected into the
+ *      reference view (intrinsics K, pose T_ref, full resolution);
+ *   3. u counts when u^ is inside, the reference has a hit and a normal
+ *      there, |p - V*(u^)| < eps_d and the angle between R N_k(u) and
+ *      N*(u^) is below eps_theta;
+ *   4. r = (p - V*(u^)) . N*(u^), J = [N*^T, (p x N*)^T];
+ *   5. xi = -(sum J^T J)^-1 sum J^T r (Cholesky, double precision), and
+ *      T <- exp(xi^) T with xi = (translation, rotation); a system that is
+ *      not positive definite leaves T unchanged.
+ * Level l + 1 holds the mean of the valid depths of each 2x2 block of level
+ * l, with intrinsics f / 2, c / 2 (coarse pixel i on fine pixel 2i).  Normals (current levels and
+ * reference) are the cross product of central differences, (V(x+1) - V(x-1))
+ * x (V(y+1) - V(y-1)), turned towards the camera; a pixel lacking one of its
+ * four neighbours has none. */
+typedef struct GpsIcpSettings {
+  int32_t levels;       /* pyramid levels [3], 1..4                             */
+  int32_t iters[4];     /* iterations per level, finest first [10, 5, 4, 0]     */
+  float eps_d;          /* association distance, metres [0.1]                   */
+  float eps_theta_deg;  /* association normal angle, degrees [20]              */
+} GpsIcpSettings;
+
+/* Workspace bytes icp_track needs for width x height frames. */
+GPS_API int32_t gps_icp_workspace_size(int32_t width, int32_t height, const GpsIcpSettings* s,
+                                       size_t* bytes);
+
+/* Tracks one frame.  depth [H][W] (metres, 0 = none): the current frame;
+ * ref_vertex [H][W][3] (world) and ref_depth [H][W] (> 0 where the ray hit):
+ * raycast_sdf's vertex and depth outputs at pose T_ref; pose (device float
+ * [12], R row-major then t, camera->world): the initial estimate on entry,
+ * the result on exit; stats (device float [sum of iters][2], nullable): per
+ * iteration the inlier count and sum r^2 before its update.  Everything runs
+ * on `stream` with no host synchronisation (graph capturable).  Errors:
+ * GPS_ERR_INVALID_ARG for NULL pointers, bad sizes or settings (levels
+ * outside 1..4, a level smaller than 3 x 3, negative iterations, non-positive
+ * thresholds), GPS_ERR_WORKSPACE_TOO_SMALL. */
+GPS_API int32_t icp_track(const GpsIntrinsics* K, const float* depth, const float* ref_vertex,
+                          const float* ref_depth, const GpsPose* T_ref,
+                          const GpsIcpSettings* s, float* pose, void* ws, size_t ws_bytes,
+                          float* stats, void* stream);
+
 /* ------------------------------------------- keyframes and optimisation views
  * Host-only bookkeeping of the online loop (Sec. 3.2 "Gaussian optimization",
  * Fig. 5, App. C): which frames become keyframes, and which frames one

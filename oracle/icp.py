@@ -20,8 +20,11 @@ over a depth pyramid, coarsest level first.  One iteration at one level:
 
 Readings of points the paper leaves open (listed with the other readings):
 - 3 levels; level l + 1 holds the mean of the valid depths of each 2x2 block
-  of level l (0 when none is valid), with f / 2 and (c - 0.5) / 2 (pixel
-  centres at integer coordinates).
+  of level l (0 when none is valid), with intrinsics f / 2 and c / 2, as
+  InfiniTAM halves them: coarse pixel i then sits on fine pixel 2i, so a
+  coarse point at the reference pose projects onto a reference pixel centre.
+  (With c' = (c - 0.5) / 2, the block's own centre, it would land on a pixel
+  corner, where the nearest-pixel association is a four-way tie.)
 - Iterations per level, finest first, 10, 5, 4 and the rejection thresholds
   eps_d = 0.1 m, eps_theta = 20 degrees (KinectFusion's values).
 - Normals (current levels and reference): cross product of the central
@@ -82,7 +85,7 @@ def pyramid(depth, K, levels=LEVELS):
         n = (b > 0).sum(axis=(1, 3))
         s = np.where(b > 0, b, 0.0).sum(axis=(1, 3))
         out.append((np.where(n > 0, s / np.maximum(n, 1), 0.0),
-                    (fx / 2, fy / 2, (cx - 0.5) / 2, (cy - 0.5) / 2)))
+                    (fx / 2, fy / 2, cx / 2, cy / 2)))
     return out
 
 

@@ -110,6 +110,18 @@ def view_schedule(delta_angle_deg=30.0, delta_move=0.3, interval=10, n_global=4,
     return GpsViewSchedule(delta_angle_deg, delta_move, interval, n_global, n_local, 0, seed)
 
 
+class GpsIcpSettings(ctypes.Structure):
+    _fields_ = [("levels", c_int32), ("iters", c_int32 * 4), ("eps_d", c_float),
+                ("eps_theta_deg", c_float)]
+
+
+def icp_settings(levels=3, iters=(10, 5, 4), eps_d=0.1, eps_theta_deg=20.0) -> GpsIcpSettings:
+    """Point-to-plane ICP over a `levels`-level pyramid; iters finest first
+    (KinectFusion's 10, 5, 4 and its 0.1 m / 20 degree rejection)."""
+    it = list(iters) + [0] * (4 - len(iters))
+    return GpsIcpSettings(levels, (c_int32 * 4)(*it), eps_d, eps_theta_deg)
+
+
 class GpsAdamHyper(ctypes.Structure):
     _fields_ = [("lr", c_float * 5), ("beta1", c_float), ("beta2", c_float), ("eps", c_float),
                 ("lr_sh_rest", c_float)]
@@ -132,7 +144,8 @@ EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspac
             "gps_query_status", "fuse_frame", "raycast_sdf", "render_forward", "render_backward",
             "adam_step", "render_forward_noalloc", "gps_autotune_tiles",
             "gps_edit_scratch_size", "insert_gaussians", "remove_gaussians",
-            "tsdf_mark_bricks", "gps_is_keyframe", "gps_select_views")
+            "tsdf_mark_bricks", "gps_is_keyframe", "gps_select_views",
+            "gps_icp_workspace_size", "icp_track")
 AUTOTUNE_SHAPES = ((16, 16), (16, 8), (8, 8), (32, 8))  # the order of GPS_AUTOTUNE_SHAPES
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -200,6 +213,11 @@ def lib() -> ctypes.CDLL:
         L.gps_select_views.argtypes = [ctypes.POINTER(c_int32), c_int32, c_int32, c_int32,
                                        ctypes.POINTER(GpsViewSchedule), ctypes.POINTER(c_int32),
                                        c_int32, ctypes.POINTER(c_int32)]
+        L.gps_icp_workspace_size.argtypes = [c_int32, c_int32, ctypes.POINTER(GpsIcpSettings),
+                                             ctypes.POINTER(c_size_t)]
+        L.icp_track.argtypes = [ctypes.POINTER(GpsIntrinsics), c_void_p, c_void_p, c_void_p,
+                                ctypes.POINTER(GpsPose), ctypes.POINTER(GpsIcpSettings), c_void_p,
+                                c_void_p, c_size_t, c_void_p, c_void_p]
         _lib = L
     return _lib
 
@@ -540,6 +558,63 @@ def gps_select_views(keyframes: Sequence[int], frame: int, event: int,
     _check(lib().gps_select_views(kf, len(keyframes), frame, event, ctypes.byref(sched), out, cap,
                                   ctypes.byref(n)))
     return [int(out[i]) for i in range(n.value)]
+
+
+def gps_icp_workspace_size(width: int, height: int, s: GpsIcpSettings) -> int:
+    n = c_size_t(0)
+    _check(lib().gps_icp_workspace_size(width, height, ctypes.byref(s), ctypes.byref(n)))
+    return int(n.value)
+
+
+def icp_track(cam, depth: torch.Tensor, ref_vertex: torch.Tensor, ref_depth: torch.Tensor,
+              ref_cam, pose_dev: torch.Tensor, s: GpsIcpSettings, ws: torch.Tensor,
+              stats: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Refines pose_dev (device float [12]: R row-major, t; camera->world) in
+    place against the reference ray-cast at ref_cam's pose; cam gives the
+    intrinsics of both."""
+    K, Pr = intrinsics(cam), pose(ref_cam)
+    _check(lib().icp_track(ctypes.byref(K), _ptr(depth), _ptr(ref_vertex), _ptr(ref_depth),
+                           ctypes.byref(Pr), ctypes.byref(s), _ptr(pose_dev), _ptr(ws),
+                           ws.numel(), _ptr(stats), _stream(stream)))
+
+
+class PoseCam:
+    """Intrinsics of `cam` with another camera->world pose (R [3][3], t [3])."""
+
+    def __init__(self, cam, R, t):
+        self.fx, self.fy, self.cx, self.cy = cam.fx, cam.fy, cam.cx, cam.cy
+        self.width, self.height = cam.width, cam.height
+        self.R = torch.as_tensor(R, dtype=torch.float64).reshape(3, 3).cpu()
+        self.t = torch.as_tensor(t, dtype=torch.float64).reshape(3).cpu()
+
+
+class Tracker:
+    """Workspace and device pose of icp_track for frames of `cam`'s size."""
+
+    def __init__(self, cam, s: Optional[GpsIcpSettings] = None, device="cuda"):
+        self.cam = cam
+        self.s = s if s is not None else icp_settings()
+        self.ws = torch.zeros(gps_icp_workspace_size(cam.width, cam.height, self.s),
+                              dtype=torch.uint8, device=device)
+        self.pose = torch.zeros(12, device=device)
+        n_it = sum(self.s.iters[l] for l in range(self.s.levels))
+        self.stats = torch.zeros(max(1, n_it), 2, device=device)
+
+    def track(self, depth: torch.Tensor, ref_vertex: torch.Tensor, ref_depth: torch.Tensor,
+              ref_cam, init_cam=None, stream=None) -> None:
+        """Pose of the frame `depth` against the reference ray-cast at
+        ref_cam; starts from init_cam's pose (default: ref_cam's).  The
+        result stays in self.pose (device); read it with `result()`."""
+        c = init_cam if init_cam is not None else ref_cam
+        R = torch.as_tensor(c.R, dtype=torch.float32).reshape(9)
+        t = torch.as_tensor(c.t, dtype=torch.float32).reshape(3)
+        self.pose.copy_(torch.cat([R, t]).to(self.pose.device), non_blocking=True)
+        icp_track(self.cam, depth, ref_vertex, ref_depth, ref_cam, self.pose, self.s, self.ws,
+                  self.stats, stream)
+
+    def result(self) -> PoseCam:
+        p = self.pose.double().cpu()
+        return PoseCam(self.cam, p[:9].reshape(3, 3), p[9:])
 
 
 def adam_step(params: Gaussians, grads: Gaussians, m: Gaussians, v: Gaussians, lr=LR_APP_C,

@@ -44,7 +44,7 @@ def test_library_exports_every_declared_symbol(L):
 def test_struct_layouts_match_header(tmp_path):
     structs = ["GpsIntrinsics", "GpsPose", "GpsTsdf", "GpsGaussians", "GpsView",
                "GpsRenderSettings", "GpsAdamHyper", "GpsWorkspaceLayout", "GpsEditSettings",
-               "GpsViewSchedule"]
+               "GpsViewSchedule", "GpsIcpSettings"]
     prog = tmp_path / "sz.c"
     body = "".join(f'  printf("{s} %zu\\n", sizeof({s}));\n' for s in structs)
     body += '  printf("off_pair_capacity %zu\\n", offsetof(GpsRenderSettings, pair_capacity));\n'
@@ -167,3 +167,18 @@ def test_layout_helpers_roundtrip():
     idx = ((1 * nby + 0) * nbx + 1) * 512 + 2 * 64 + 3 * 8 + 1
     assert torch.equal(b[idx], a[10, 3, 9])
     assert torch.equal(gps.brick_to_linear(b, 24, 8, 16), a)
+
+
+def test_icp_arguments_are_checked_on_the_host(L):
+    # sizes and settings are validated before anything touches the device
+    with pytest.raises(gps.GpsError):
+        gps.gps_icp_workspace_size(8, 8, gps.icp_settings(levels=3))     # level 2 is 2 x 2
+    with pytest.raises(gps.GpsError):
+        gps.gps_icp_workspace_size(64, 48, gps.icp_settings(levels=5))
+    with pytest.raises(gps.GpsError):
+        gps.gps_icp_workspace_size(64, 48, gps.icp_settings(eps_d=0.0))
+    with pytest.raises(gps.GpsError):
+        gps.gps_icp_workspace_size(64, 48, gps.icp_settings(iters=(3, -1, 2)))
+    n1 = gps.gps_icp_workspace_size(64, 48, gps.icp_settings(levels=1))
+    n3 = gps.gps_icp_workspace_size(64, 48, gps.icp_settings())
+    assert 0 < n1 < n3 and n3 % 256 == 0

@@ -53,12 +53,13 @@ def test_pyramid_by_hand():
                   [5.0, 0.0, 0.0, 2.0]])
     (d0, K0), (d1, K1) = icp.pyramid(d, (100.0, 80.0, 2.0, 1.0), levels=2)
     np.testing.assert_array_equal(d1, [[3.0, 2.0]])
-    assert K1 == (50.0, 40.0, 0.75, 0.25)
-    # a point seen at fine coordinate u sits at (u - 0.5) / 2 one level up
+    assert K1 == (50.0, 40.0, 1.0, 0.5)
+    # a point seen at fine coordinate u sits at u / 2 one level up, so coarse
+    # pixel centres back-project through fine pixel centres
     X = np.array([0.3, -0.2, 2.0])
     u0 = K0[0] * X[0] / X[2] + K0[2]
     u1 = K1[0] * X[0] / X[2] + K1[2]
-    assert abs(u1 - (u0 - 0.5) / 2) < 1e-12
+    assert abs(u1 - u0 / 2) < 1e-12
 
 
 def test_normals_of_a_tilted_plane():
