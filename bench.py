@@ -57,6 +57,9 @@ def parse():
                     help=f"frames of the sequence (room: {N_FRAMES}, large: {N_FRAMES_LARGE})")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="storage type of the colour images C_t, C_k, C*")
+    ap.add_argument("--track", action="store_true",
+                    help="sequence workload: track frames 1.. by ICP (Sec. 3.2) instead of "
+                         "using the given poses")
     ap.add_argument("--sh-degree", type=int, default=0, choices=[0, 1, 2, 3],
                     help="view-dependent colour: SH coefficients of degree 1..D per Gaussian "
                          "(drawn from N(0, 0.05^2)); 0 = the colour is rgb")
@@ -874,7 +877,7 @@ def run_sequence(args, rank, world, local):
                      precision=prec)
     vol = gps.Tsdf(w.tsdf, dev)
     mp = Mapper(vol, w.frames[0].cam, SEQ_CAPACITY, s, iterations=SEQ_ITERS, near=w.near,
-                sh_degree=args.sh_degree, device=dev)
+                sh_degree=args.sh_degree, track=args.track, device=dev)
     dev_frames = [(torch.from_numpy(f.rgb).to(dev), torch.from_numpy(f.depth).to(dev))
                   for f in w.frames]
     host_frames = [(torch.from_numpy(f.rgb).pin_memory(), torch.from_numpy(f.depth).pin_memory())
@@ -913,6 +916,30 @@ def run_sequence(args, rank, world, local):
     ms, wall_ms, clk = one_pass(clocks=ClockSampler(str(local)))
     hist = [dataclasses.asdict(r) for r in mp.history]
     st = gps.gps_query_status(mp.ws)
+    tracking = None
+    if args.track:
+        import numpy as np
+        est = np.array([np.asarray(c.t, np.float64) for c in mp.poses])
+        true = np.array([np.asarray(f.cam.t, np.float64) for f in w.frames])
+        err = np.linalg.norm(est - true, axis=1)
+        # icp_track alone: frame 1 against the ray-cast at frame 0's pose (final TSDF)
+        tr = mp.tracker
+        gps.raycast_sdf(vol, w.frames[0].cam, w.near, 0.0, mp.ref_rgb, mp.ref_depth,
+                        mp.ref_vertex)
+        d1 = dev_frames[1][1]
+        evs = []
+        for i in range(13):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tr.track(d1, mp.ref_vertex, mp.ref_depth, w.frames[0].cam)
+            e1.record()
+            if i >= 3:
+                evs.append((e0, e1))
+        torch.cuda.synchronize()
+        tracking = {"ate_rmse_m": float(np.sqrt((err ** 2).mean())), "max_err_m": float(err.max()),
+                    "icp_ms": sum(a.elapsed_time(b) for a, b in evs) / len(evs),
+                    "icp_iterations": [int(tr.s.iters[l]) for l in range(tr.s.levels)],
+                    "icp_launches": 2 * tr.s.levels + 2 + 1 + sum(tr.s.iters[l] for l in range(tr.s.levels))}
     ms_e2e, _, _ = one_pass(e2e=True)
     if world > 1:
         t = torch.tensor([ms, ms_e2e], device=dev)
@@ -936,11 +963,13 @@ def run_sequence(args, rank, world, local):
                                f"{mp.sched.n_local} local + up to {mp.sched.n_global} keyframe views",
                    "tile": f"{tile[0]}x{tile[1]}", "colour_storage": args.precision,
                    "sh_degree": args.sh_degree,
+                   "poses": "tracked by ICP from frame 1 on" if args.track else "given",
                    "form": "plain launches; the whole sequence is one timed region, "
                            "run once untimed before",
                    "l2": "256 MB buffer written before the timed region; the 336 MB TSDF "
                          "exceeds L2"},
         "wall_ms_per_step": wall_ms / n,
+        "tracking": tracking,
         "reconstructions": hist,
         "keyframes": list(mp.keyframes),
         "e2e": {"value": n / ms_e2e * 1e3 * world, "unit": "frames/s",

@@ -401,7 +401,7 @@ GPS_API int32_t remove_gaussians(GpsGaussians* gaussians, GpsGaussians* m, GpsGa
  *      there, |p - V*(u^)| < eps_d and the angle between R N_k(u) and
  *      N*(u^) is below eps_theta;
  *   4. r = (p - V*(u^)) . N*(u^), J = [N*^T, (p x N*)^T];
- *   5. xi = -(sum J^T J)^-1 sum J^T r (Cholesky, double precision), and
+ *   5. xi = -(sum J^T J)^-1 sum J^T r (Cholesky, single precision), and
  *      T <- exp(xi^) T with xi = (translation, rotation); a system that is
  *      not positive definite leaves T unchanged.
  * Level l + 1 holds the mean of the valid depths of each 2x2 block of level

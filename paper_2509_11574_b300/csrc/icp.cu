@@ -6,13 +6,14 @@
 // the level with the reference view, accumulates the 21 + 6 + 2 sums of the
 // normal equations per thread, reduces them per block in a fixed order, and
 // its last block (an atomic ticket; nothing waits) adds the block partials in
-// double precision, solves the 6x6 system by Cholesky and updates the pose in
-// device memory.  No host synchronisation: the whole track is one stream of
+// a fixed order, solves the 6x6 system by Cholesky and updates the pose in
+// device memory, all in single precision.  No host synchronisation: the whole track is one stream of
 // launches.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
+#include <algorithm>
 #include <cstdio>
 
 #include "gps_common.cuh"
@@ -113,88 +114,112 @@ struct IcpIter {
   float* stats;           // nullable: [2] for this iteration
 };
 
-// Cholesky of the 6x6 normal equations and the SE(3) exponential, double
-// precision, one thread.  Leaves the pose unchanged when the system has
-// fewer than six inliers or a pivot at most 1e-6 of the largest diagonal.
-__device__ void icp_solve_and_update(const double* S, float* pose, float* stats) {
-  double A[6][6], b[6];
+// Cholesky of the 6x6 normal equations and the SE(3) exponential in single
+// precision, one thread (B300's FP64 rate is a small fraction of its FP32
+// rate, and Gauss-Newton corrects the rounding of one step in the next).
+// Leaves the pose unchanged when the system has fewer than six inliers or a
+// pivot at most 1e-6 of the largest diagonal.
+__device__ void icp_solve_and_update(const float* S, float* pose, float* stats) {
+  float A[6][6], b[6];
   int k = 0;
+#pragma unroll
   for (int a = 0; a < 6; ++a)
+#pragma unroll
     for (int c = a; c < 6; ++c) {
       A[a][c] = S[k];
       A[c][a] = S[k];
       ++k;
     }
+#pragma unroll
   for (int a = 0; a < 6; ++a) b[a] = S[21 + a];
   if (stats) {
-    stats[0] = (float)S[28];
-    stats[1] = (float)S[27];
+    stats[0] = S[28];
+    stats[1] = S[27];
   }
-  if (!(S[28] >= 6.0)) return;
-  double dmax = 0.0;
-  for (int a = 0; a < 6; ++a) dmax = fmax(dmax, A[a][a]);
-  double L[6][6] = {};
+  if (!(S[28] >= 6.0f)) return;
+  float dmax = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) dmax = fmaxf(dmax, A[a][a]);
+  float L[6][6] = {};
+#pragma unroll
   for (int j = 0; j < 6; ++j) {
-    double s = A[j][j];
-    for (int m = 0; m < j; ++m) s -= L[j][m] * L[j][m];
-    if (!(s > 1e-6 * dmax)) return;
-    L[j][j] = sqrt(s);
+    float sj = A[j][j];
+#pragma unroll
+    for (int m = 0; m < j; ++m) sj -= L[j][m] * L[j][m];
+    if (!(sj > 1e-6f * dmax)) return;
+    L[j][j] = sqrtf(sj);
+#pragma unroll
     for (int i = j + 1; i < 6; ++i) {
-      double t = A[i][j];
+      float t = A[i][j];
+#pragma unroll
       for (int m = 0; m < j; ++m) t -= L[i][m] * L[j][m];
       L[i][j] = t / L[j][j];
     }
   }
-  double y[6], xi[6];
+  float y[6], xi[6];
+#pragma unroll
   for (int i = 0; i < 6; ++i) {
-    double t = -b[i];
+    float t = -b[i];
+#pragma unroll
     for (int m = 0; m < i; ++m) t -= L[i][m] * y[m];
     y[i] = t / L[i][i];
   }
+#pragma unroll
   for (int i = 5; i >= 0; --i) {
-    double t = y[i];
+    float t = y[i];
+#pragma unroll
     for (int m = i + 1; m < 6; ++m) t -= L[m][i] * xi[m];
     xi[i] = t / L[i][i];
   }
-  // exp of the twist (v, w): Rodrigues for R, V = I + B [w] + C [w]^2 for t
-  const double wx = xi[3], wy = xi[4], wz = xi[5];
-  const double th = sqrt(wx * wx + wy * wy + wz * wz);
-  const double W[9] = {0, -wz, wy, wz, 0, -wx, -wy, wx, 0};
-  double W2[9];
+  // exp of the twist (v, w): R = I + a [w] + b [w]^2, V = I + b [w] + c [w]^2
+  // with a = sin t / t, b = (1 - cos t) / t^2 = 2 sin^2(t/2) / t^2 and
+  // c = (t - sin t) / t^3, the last by its Taylor series below t = 0.1
+  // (truncation below 1e-12; the closed form cancels in single precision)
+  const float wx = xi[3], wy = xi[4], wz = xi[5];
+  const float th2 = wx * wx + wy * wy + wz * wz, th = sqrtf(th2);
+  float ca, cb, cc;
+  if (th < 0.1f) {
+    ca = 1.0f - th2 * (1.0f / 6.0f) * (1.0f - th2 * (1.0f / 20.0f));
+    cb = 0.5f - th2 * (1.0f / 24.0f) * (1.0f - th2 * (1.0f / 30.0f));
+    cc = (1.0f / 6.0f) - th2 * (1.0f / 120.0f) * (1.0f - th2 * (1.0f / 42.0f));
+  } else {
+    const float sh = sinf(0.5f * th);
+    ca = sinf(th) / th;
+    cb = 2.0f * sh * sh / th2;
+    cc = (th - sinf(th)) / (th2 * th);
+  }
+  const float W[9] = {0.f, -wz, wy, wz, 0.f, -wx, -wy, wx, 0.f};
+  float W2[9];
+#pragma unroll
   for (int r = 0; r < 3; ++r)
+#pragma unroll
     for (int c = 0; c < 3; ++c)
       W2[r * 3 + c] = W[r * 3] * W[c] + W[r * 3 + 1] * W[3 + c] + W[r * 3 + 2] * W[6 + c];
-  double ca, cb, cc;
-  if (th < 1e-12) {
-    ca = 1.0;
-    cb = 0.5;
-    cc = 0.0;
-  } else {
-    ca = sin(th) / th;
-    cb = (1.0 - cos(th)) / (th * th);
-    cc = (th - sin(th)) / (th * th * th);
-  }
-  double Re[9], Ve[9];
+  float Re[9], Ve[9];
+#pragma unroll
   for (int e = 0; e < 9; ++e) {
-    const double I = (e % 4 == 0) ? 1.0 : 0.0;
-    Re[e] = I + ca * W[e] + (th < 1e-12 ? 0.0 : cb) * W2[e];
+    const float I = (e % 4 == 0) ? 1.0f : 0.0f;
+    Re[e] = I + ca * W[e] + cb * W2[e];
     Ve[e] = I + cb * W[e] + cc * W2[e];
   }
-  double te[3];
-  for (int r = 0; r < 3; ++r) te[r] = Ve[r * 3] * xi[0] + Ve[r * 3 + 1] * xi[1] + Ve[r * 3 + 2] * xi[2];
-  double R[9], t[3];
+  float R[9], t[3];
+#pragma unroll
   for (int e = 0; e < 9; ++e) R[e] = pose[e];
+#pragma unroll
   for (int e = 0; e < 3; ++e) t[e] = pose[9 + e];
+#pragma unroll
   for (int r = 0; r < 3; ++r) {
+#pragma unroll
     for (int c = 0; c < 3; ++c)
-      pose[r * 3 + c] = (float)(Re[r * 3] * R[c] + Re[r * 3 + 1] * R[3 + c] + Re[r * 3 + 2] * R[6 + c]);
-    pose[9 + r] = (float)(Re[r * 3] * t[0] + Re[r * 3 + 1] * t[1] + Re[r * 3 + 2] * t[2] + te[r]);
+      pose[r * 3 + c] = Re[r * 3] * R[c] + Re[r * 3 + 1] * R[3 + c] + Re[r * 3 + 2] * R[6 + c];
+    pose[9 + r] = Re[r * 3] * t[0] + Re[r * 3 + 1] * t[1] + Re[r * 3 + 2] * t[2] +
+                  Ve[r * 3] * xi[0] + Ve[r * 3 + 1] * xi[1] + Ve[r * 3 + 2] * xi[2];
   }
 }
 
 __global__ void __launch_bounds__(kIcpThreads) icp_iteration_kernel(const __grid_constant__ IcpIter a) {
   __shared__ float s_part[kIcpThreads / 32][kIcpSums];
-  __shared__ double s_sum[kIcpSums];
+  __shared__ float s_sum[kIcpSums];
   __shared__ bool s_last;
   float R[9], t[3];
 #pragma unroll
@@ -261,11 +286,26 @@ __global__ void __launch_bounds__(kIcpThreads) icp_iteration_kernel(const __grid
   if (threadIdx.x == 0) s_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!s_last) return;
-  // last block: every partial is visible (fence before each ticket)
+  // last block: every partial is visible (fence before each ticket); the
+  // block's threads add them in the same fixed order as above
+#pragma unroll
+  for (int k = 0; k < kIcpSums; ++k) acc[k] = 0.f;
+  for (int bk = threadIdx.x; bk < (int)gridDim.x; bk += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < kIcpSums; ++k) acc[k] += __ldcg(a.partials + (size_t)bk * 32 + k);
+  }
+#pragma unroll
+  for (int k = 0; k < kIcpSums; ++k) {
+    float x = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_part[warp][k] = x;
+  }
+  __syncthreads();
   if (threadIdx.x < kIcpSums) {
-    double x = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b)
-      x += (double)__ldcg(a.partials + (size_t)b * 32 + threadIdx.x);
+    float x = 0.f;
+#pragma unroll
+    for (int w2 = 0; w2 < kIcpThreads / 32; ++w2) x += s_part[w2][threadIdx.x];
     s_sum[threadIdx.x] = x;
   }
   __syncthreads();
@@ -421,9 +461,11 @@ int32_t icp_track(const GpsIntrinsics* K, const float* depth, const float* ref_v
     a.vert = reinterpret_cast<const float4*>(b + L.vert[l]);
     a.norm = reinterpret_cast<const float4*>(b + L.norm[l]);
     a.n = L.W[l] * L.H[l];
+    // about two pixels per thread, at most L.grid blocks
+    const unsigned grid = (unsigned)std::min<size_t>(L.grid, (a.n + 2 * T - 1) / (2 * T));
     for (int it = 0; it < s->iters[l]; ++it, ++it_index) {
       a.stats = stats ? stats + 2 * it_index : nullptr;
-      gps::icp_iteration_kernel<<<L.grid, T, 0, st>>>(a);
+      gps::icp_iteration_kernel<<<grid, T, 0, st>>>(a);
     }
   }
   if (e == cudaSuccess) e = cudaGetLastError();

@@ -1,9 +1,14 @@
 """The online reconstruction loop (Sec. 3.2, Fig. 2) on one device, built on
-the C-ABI calls: every frame is fused into the TSDF and tested as a keyframe;
-every `interval` frames a Gaussian reconstruction runs - insertion on that
-frame, selection of the optimisation views (Fig. 5), one ray-cast per view,
-`iterations` batched forward + backward + Adam steps over those views, and
-removal.  Poses are given (tracking is not part of this loop).
+the C-ABI calls: every frame is tracked (optional), fused into the TSDF and
+tested as a keyframe; every `interval` frames a Gaussian reconstruction runs -
+insertion on that frame, selection of the optimisation views (Fig. 5), one
+ray-cast per view, `iterations` batched forward + backward + Adam steps over
+those views, and removal.
+
+With track=True, frame k > 0 is tracked by point-to-plane ICP against the
+ray-cast of the TSDF at frame k-1's estimated pose, starting from that pose,
+and is fused and later rendered at its estimate; frame 0 keeps the pose it
+is given (it anchors the map).  Without tracking the given poses are used.
 
 Device memory is fixed at construction: the Gaussians, their gradients and
 Adam moments have `capacity` rows, the render workspace is sized for
@@ -20,8 +25,9 @@ from typing import Dict, List, Optional
 
 import torch
 
-from . import (LR_APP_C, PREC_DTYPE, GpsEditSettings, GpsRenderSettings, GpsViewSchedule,
-               Gaussians, Tsdf, View, adam_step, edit_settings, fuse_frame, gps_edit_scratch_size,
+from . import (LR_APP_C, PREC_DTYPE, GpsEditSettings, GpsIcpSettings, GpsRenderSettings,
+               GpsViewSchedule, Gaussians, PoseCam, Tracker, Tsdf, View, adam_step,
+               edit_settings, fuse_frame, gps_edit_scratch_size,
                gps_is_keyframe, gps_query_status, gps_select_views, gps_workspace_size,
                insert_gaussians, raycast_sdf, remove_gaussians, render_backward, render_forward,
                settings as render_settings, view_schedule)
@@ -52,7 +58,8 @@ class Mapper:
                  edit: Optional[GpsEditSettings] = None,
                  sched: Optional[GpsViewSchedule] = None,
                  iterations: int = 20, lr=LR_APP_C, near: float = 0.2,
-                 max_views: Optional[int] = None, sh_degree: int = 0, device="cuda"):
+                 max_views: Optional[int] = None, sh_degree: int = 0, track: bool = False,
+                 icp: Optional[GpsIcpSettings] = None, device="cuda"):
         self.vol, self.cam, self.capacity = vol, cam, capacity
         self.s = GpsRenderSettings.from_buffer_copy(s if s is not None else
                                                     render_settings(tile=(16, 8)))
@@ -105,6 +112,13 @@ class Mapper:
         self.last_keyframe_cam = None
         self.event = 0
         self.history: List[Reconstruction] = []
+        # tracking: the reference ray-cast at the previous estimate
+        self.tracker = Tracker(cam, icp, device=dev) if track else None
+        if track:
+            self.ref_rgb = torch.zeros(3, H, W, device=dev)
+            self.ref_depth = torch.zeros(H, W, device=dev)
+            self.ref_vertex = torch.zeros(H, W, 3, device=dev)
+        self.poses: List = []     # estimated (or given) camera of every frame
 
     def reset(self) -> None:
         """Forget every frame, keyframe and Gaussian (the TSDF is the
@@ -115,6 +129,7 @@ class Mapper:
         self.M = self.t = self.event = 0
         self.frames.clear()
         self.keyframes.clear()
+        self.poses.clear()
         self.last_keyframe_cam = None
         self.history.clear()
 
@@ -125,6 +140,13 @@ class Mapper:
         at `cam`'s pose, then run a reconstruction if `frame` closes an
         interval.  Frames must arrive in order, numbered from 0.  Everything
         is enqueued on torch's current stream."""
+        if self.tracker is not None and self.poses:
+            prev = self.poses[-1]
+            raycast_sdf(self.vol, prev, self.near, 0.0, self.ref_rgb, self.ref_depth,
+                        self.ref_vertex)
+            self.tracker.track(depth, self.ref_vertex, self.ref_depth, prev)
+            cam = self.tracker.result()          # reads the pose back (synchronises)
+        self.poses.append(cam)
         fuse_frame(self.vol, depth, rgb, cam)
         if gps_is_keyframe(self.last_keyframe_cam, cam, self.sched):
             self.keyframes.append(frame)
