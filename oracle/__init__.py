@@ -13,6 +13,9 @@ wraps it with ctypes on float64 numpy arrays.
 
 Parity status per function (what pins it, see tests/test_oracle_*.py):
   fuse              - fronto-parallel plane closed form, weight / re-fusion invariants
+  fuse (hashed)     - the bricks a plane allocates, by hand; dense arithmetic
+                      inside allocated bricks; closed-form values of a brick
+                      allocated in a later frame (tests/test_oracle_hash.py)
   raycast           - analytic plane / box (exact) and sphere (0.1 voxel) hits
   project           - on-axis isotropic closed form, off-axis hand value, invariances
   composite (OIT)   - 1- and 2-Gaussian hand blends, M = 0, eps limits, brute force,
@@ -126,9 +129,11 @@ def _vol(spec):
 
 class Volume:
     """FP64 TSDF in linear storage (x fastest): sdf, w, cw [nz][ny][nx], rgb [...][3].
-    Unobserved voxels: sdf = 1, w = 0, rgb = 0, cw = 0."""
+    Unobserved voxels: sdf = 1, w = 0, rgb = 0, cw = 0.  hashed=True gives the
+    voxel-hashing semantics: `alloc` [nz/8][ny/8][nx/8] marks the allocated
+    bricks, and only their voxels are ever updated (see orc_fuse)."""
 
-    def __init__(self, spec):
+    def __init__(self, spec, hashed: bool = False):
         self.spec = spec
         shape = (spec.nz, spec.ny, spec.nx)
         self.sdf = np.ones(shape)
@@ -136,6 +141,8 @@ class Volume:
         self.rgb = np.zeros(shape + (3,))
         self.cw = np.zeros(shape)
         self.amb = np.zeros(shape, dtype=np.int32)
+        self.alloc = (np.zeros((spec.nz // 8, spec.ny // 8, spec.nx // 8), np.uint8)
+                      if hashed else None)
 
 
 def fuse(vol: Volume, depth, rgb, cam) -> None:
@@ -146,7 +153,7 @@ def fuse(vol: Volume, depth, rgb, cam) -> None:
     c = _f64(rgb)
     lib().orc_fuse(_p(dims), _p(geo), _p(vol.sdf), _p(vol.w), _p(vol.rgb), _p(vol.cw),
                    _p(vol.amb), _p(d), _p(c), ctypes.c_int(cam.width), ctypes.c_int(cam.height),
-                   _p(K), _p(R), _p(t))
+                   _p(K), _p(R), _p(t), _p(vol.alloc))
 
 
 def raycast(spec, sdf, rgb, cam, near=0.2, far=0.0):

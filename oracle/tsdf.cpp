@@ -80,14 +80,55 @@ extern "C" {
 // amb[v] |= 1 when a discrete decision of this update sits within a relative
 // 1e-6 of its threshold (pixel rounding, truncation tests), so a
 // single-precision implementation may legitimately take the other branch.
+//
+// Voxel hashing (Sec. 3.2.1: the SDF lives in a hash table of voxel blocks,
+// as in InfiniTAM), when `alloc` (one byte per 8^3 brick, brick index
+// bx + nbx (by + nby bz)) is given: before the update, every brick holding a
+// voxel with |eta| < trunc for this frame (the same projection and pixel as
+// above) is allocated (alloc = 1, for good); then only voxels of allocated
+// bricks are updated.  Unallocated bricks keep sdf 1, weight 0, colour 0.
+// amb[v] |= 2 marks a voxel whose band decision sits within a relative 1e-6
+// of trunc, or whose pixel rounding is that close.
 void orc_fuse(const int* dims, const double* geo, double* sdf, double* w, double* rgb,
               double* cw, int* amb, const double* depth, const double* img, int W, int H,
-              const double* K, const double* R, const double* t) {
+              const double* K, const double* R, const double* t, unsigned char* alloc) {
   const Vol v = make_vol(dims, geo);
   const double fx = K[0], fy = K[1], cx = K[2], cy = K[3];
   const long n = (long)v.nx * v.ny * v.nz;
+  const int nbx = v.nx / 8, nby = v.ny / 8;
+  auto brick = [&](long id) {
+    int x = (int)(id % v.nx), y = (int)((id / v.nx) % v.ny), z = (int)(id / ((long)v.nx * v.ny));
+    return (long)(x / 8) + nbx * ((long)(y / 8) + (long)nby * (z / 8));
+  };
+  if (alloc) {
+#pragma omp parallel for schedule(static)
+    for (long id = 0; id < n; ++id) {
+      int x = (int)(id % v.nx), y = (int)((id / v.nx) % v.ny), z = (int)(id / ((long)v.nx * v.ny));
+      double xw[3] = {v.ox + (x + 0.5) * v.voxel, v.oy + (y + 0.5) * v.voxel,
+                      v.oz + (z + 0.5) * v.voxel};
+      double xc[3];
+      world_to_cam(R, t, xw, xc);
+      if (!(xc[2] > 0.0)) continue;
+      double u = fx * xc[0] / xc[2] + cx, vv = fy * xc[1] / xc[2] + cy;
+      double fu = u + 0.5 - std::floor(u + 0.5), fv = vv + 0.5 - std::floor(vv + 0.5);
+      bool near_round = std::min(fu, 1.0 - fu) < 1e-6 * std::max(1.0, std::fabs(u)) ||
+                        std::min(fv, 1.0 - fv) < 1e-6 * std::max(1.0, std::fabs(vv));
+      double pu = std::floor(u + 0.5), pv = std::floor(vv + 0.5);
+      if (pu < 0 || pv < 0 || pu > W - 1 || pv > H - 1) continue;
+      double D = depth[(long)pv * W + (long)pu];
+      if (!(D > 0.0)) continue;
+      double eta = D - xc[2];
+      if (amb && (near_round || std::fabs(std::fabs(eta) - v.trunc) < 1e-6 * v.trunc))
+        amb[id] |= 2;
+      if (std::fabs(eta) < v.trunc) {
+#pragma omp atomic write
+        alloc[brick(id)] = 1;
+      }
+    }
+  }
 #pragma omp parallel for schedule(static)
   for (long id = 0; id < n; ++id) {
+    if (alloc && !alloc[brick(id)]) continue;
     int x = (int)(id % v.nx), y = (int)((id / v.nx) % v.ny), z = (int)(id / ((long)v.nx * v.ny));
     double xw[3] = {v.ox + (x + 0.5) * v.voxel, v.oy + (y + 0.5) * v.voxel,
                     v.oz + (z + 0.5) * v.voxel};
