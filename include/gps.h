@@ -389,6 +389,66 @@ GPS_API int32_t remove_gaussians(GpsGaussians* gaussians, GpsGaussians* m, GpsGa
                                  GpsGaussians* grads, const GpsEditSettings* s, void* scratch,
                                  size_t scratch_bytes, int32_t* count, void* stream);
 
+/* ------------------------------------------------------------ voxel hashing
+ * The TSDF of Sec. 3.2.1 kept in a hash table of voxel blocks, as InfiniTAM
+ * keeps it: 8^3-voxel bricks (x fastest inside, as in GpsTsdf) live in a pool
+ * of `capacity` bricks and are found through an open-addressing table keyed
+ * by the brick's linear index bx + nbx (by + nby bz) in an nx x ny x nz grid,
+ * which may be far larger than the pool.  A brick is allocated at the start
+ * of the frame in which one of its voxels first lies within the truncation
+ * band (|eta| < trunc, with fuse_frame's projection, pixel and arithmetic);
+ * from then on every fused frame updates its voxels by fuse_frame's rule.
+ * Bricks never allocated read as sdf 1, colour 0.  No brick is freed.
+ * The caller allocates every array and zeroes `keys` and `state` for a fresh
+ * volume; allocation initialises a brick's voxels (sdf 1, weights 0, colour 0).
+ * Device-side failures (pool full, candidate set full, a table probe over 64
+ * buckets) set state[1] to GPS_ERR_CAPACITY; the brick is then not stored. */
+typedef struct GpsHashTsdf {
+  int32_t nx, ny, nz;       /* index space, voxels; multiples of 8, each < 2^21  */
+  float voxel;              /* edge length, metres                               */
+  float origin[3];          /* world position of the grid corner                 */
+  float trunc;              /* truncation distance mu, metres                    */
+  float max_weight;         /* weight cap                                        */
+  int32_t n_buckets;        /* hash table size, a power of two >= 2 * capacity   */
+  int32_t capacity;         /* bricks in the pool                                */
+  uint64_t* keys;           /* [n_buckets]: 0 = empty, else brick index + 1      */
+  int32_t* slots;           /* [n_buckets]: pool slot of the bucket's brick      */
+  int64_t* brick_of_slot;   /* [capacity]: brick index held by each pool slot    */
+  int32_t* state;           /* [4] device: bricks in use, error code, -, -       */
+  float* sdf;               /* [capacity][512]                                   */
+  float* weight;            /* [capacity][512]                                   */
+  float* rgbw;              /* [capacity][512][4]: colour and its weight         */
+} GpsHashTsdf;
+
+/* Scratch bytes of fuse_frame_hashed for up to max_candidates candidate
+ * bricks per frame (bricks within the truncation band's reach of some pixel;
+ * a 640 x 480 frame of a room touches a few thousand). */
+GPS_API int32_t gps_hash_scratch_size(int32_t max_candidates, size_t* bytes);
+
+/* Fusion of one frame into the hashed volume: candidate bricks from every
+ * pixel's band segment (a conservative superset), the exact band test on
+ * each candidate's voxels, allocation of the bricks that pass, then
+ * fuse_frame's update on every allocated brick in view.  Errors:
+ * GPS_ERR_INVALID_ARG for NULL pointers or bad sizes,
+ * GPS_ERR_WORKSPACE_TOO_SMALL for scratch below gps_hash_scratch_size;
+ * capacity overflows are reported in state[1] (see above). */
+GPS_API int32_t fuse_frame_hashed(GpsHashTsdf* vol, const float* depth, const float* rgb,
+                                  const GpsIntrinsics* K, const GpsPose* T_wc, void* scratch,
+                                  size_t scratch_bytes, int32_t max_candidates, void* stream);
+
+/* raycast_sdf on the hashed volume (same march, same outputs; bricks not
+ * allocated are empty space). */
+GPS_API int32_t raycast_sdf_hashed(const GpsHashTsdf* vol, const GpsIntrinsics* K,
+                                   const GpsPose* T_wc, float near_plane, float far_plane,
+                                   void* out_rgb, int32_t rgb_precision, float* out_depth,
+                                   float* out_vertex, void* stream);
+
+/* Copies every allocated brick into the dense volume `dense` (same nx, ny,
+ * nz, brick-major layout) and sets its brick flag when a voxel's sdf differs
+ * from 1; the rest of `dense` is left as it is (initialise it as a fresh
+ * volume first).  For inspection and tests. */
+GPS_API int32_t tsdf_hash_to_dense(const GpsHashTsdf* vol, GpsTsdf* dense, void* stream);
+
 /* ------------------------------------------------------------ camera tracking
  * Point-to-plane ICP (Sec. 3.2 "Camera tracking", Eq. 5, after KinectFusion
  * and InfiniTAM).  Gauss-Newton over a depth pyramid, coarsest level first;

@@ -64,6 +64,12 @@ double trilinear(const Vol& v, const double* f, int stride, int comp, const doub
   return acc;
 }
 
+// Width of the band around a truncation threshold inside which a
+// single-precision evaluation of eta = D - z_c may fall on the other side:
+// z_c comes from a float transform of metre-scale coordinates (rounding about
+// 1e-7 m), so the band is 1e-6 of the magnitudes involved, in metres.
+inline double eta_band(double D, double zc) { return 1e-6 * (1.0 + std::fabs(D) + std::fabs(zc)); }
+
 }  // namespace
 
 extern "C" {
@@ -77,9 +83,10 @@ extern "C" {
 //   f = min(1, eta / trunc); sdf <- (w sdf + f) / (w + 1); w <- min(w + 1, wmax);
 //   if |eta| < trunc: rgb <- (cw rgb + C) / (cw + 1); cw <- min(cw + 1, wmax)
 // (the colour keeps its own weight cw, as InfiniTAM's coloured voxels do).
-// amb[v] |= 1 when a discrete decision of this update sits within a relative
-// 1e-6 of its threshold (pixel rounding, truncation tests), so a
-// single-precision implementation may legitimately take the other branch.
+// amb[v] |= 1 when a discrete decision of this update sits within rounding
+// reach of its threshold (pixel rounding within a relative 1e-6; truncation
+// tests within eta_band), so a single-precision implementation may
+// legitimately take the other branch.
 //
 // Voxel hashing (Sec. 3.2.1: the SDF lives in a hash table of voxel blocks,
 // as in InfiniTAM), when `alloc` (one byte per 8^3 brick, brick index
@@ -87,8 +94,8 @@ extern "C" {
 // voxel with |eta| < trunc for this frame (the same projection and pixel as
 // above) is allocated (alloc = 1, for good); then only voxels of allocated
 // bricks are updated.  Unallocated bricks keep sdf 1, weight 0, colour 0.
-// amb[v] |= 2 marks a voxel whose band decision sits within a relative 1e-6
-// of trunc, or whose pixel rounding is that close.
+// amb[v] |= 2 marks a voxel whose band decision sits within eta_band of
+// trunc, or whose pixel rounding is within a relative 1e-6.
 void orc_fuse(const int* dims, const double* geo, double* sdf, double* w, double* rgb,
               double* cw, int* amb, const double* depth, const double* img, int W, int H,
               const double* K, const double* R, const double* t, unsigned char* alloc) {
@@ -118,7 +125,7 @@ void orc_fuse(const int* dims, const double* geo, double* sdf, double* w, double
       double D = depth[(long)pv * W + (long)pu];
       if (!(D > 0.0)) continue;
       double eta = D - xc[2];
-      if (amb && (near_round || std::fabs(std::fabs(eta) - v.trunc) < 1e-6 * v.trunc))
+      if (amb && (near_round || std::fabs(std::fabs(eta) - v.trunc) < eta_band(D, xc[2])))
         amb[id] |= 2;
       if (std::fabs(eta) < v.trunc) {
 #pragma omp atomic write
@@ -151,8 +158,8 @@ void orc_fuse(const int* dims, const double* geo, double* sdf, double* w, double
       continue;
     }
     double eta = D - xc[2];
-    if (amb && (near_round || std::fabs(eta + v.trunc) < 1e-6 * v.trunc ||
-                std::fabs(std::fabs(eta) - v.trunc) < 1e-6 * v.trunc))
+    if (amb && (near_round || std::fabs(eta + v.trunc) < eta_band(D, xc[2]) ||
+                std::fabs(std::fabs(eta) - v.trunc) < eta_band(D, xc[2])))
       amb[id] |= 1;
     if (eta < -v.trunc) continue;
     double f = std::min(1.0, eta / v.trunc);

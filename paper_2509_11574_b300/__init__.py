@@ -63,6 +63,14 @@ class GpsTsdf(ctypes.Structure):
                 ("brick_flags", c_void_p)]
 
 
+class GpsHashTsdf(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("voxel", c_float),
+                ("origin", c_float * 3), ("trunc", c_float), ("max_weight", c_float),
+                ("n_buckets", c_int32), ("capacity", c_int32), ("keys", c_void_p),
+                ("slots", c_void_p), ("brick_of_slot", c_void_p), ("state", c_void_p),
+                ("sdf", c_void_p), ("weight", c_void_p), ("rgbw", c_void_p)]
+
+
 class GpsGaussians(ctypes.Structure):
     _fields_ = [("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p),
                 ("opacity_logits", c_void_p), ("rgb", c_void_p), ("M", c_int32),
@@ -145,7 +153,8 @@ EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspac
             "adam_step", "render_forward_noalloc", "gps_autotune_tiles",
             "gps_edit_scratch_size", "insert_gaussians", "remove_gaussians",
             "tsdf_mark_bricks", "gps_is_keyframe", "gps_select_views",
-            "gps_icp_workspace_size", "icp_track")
+            "gps_icp_workspace_size", "icp_track", "gps_hash_scratch_size", "fuse_frame_hashed",
+            "raycast_sdf_hashed", "tsdf_hash_to_dense")
 AUTOTUNE_SHAPES = ((16, 16), (16, 8), (8, 8), (32, 8))  # the order of GPS_AUTOTUNE_SHAPES
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -218,6 +227,15 @@ def lib() -> ctypes.CDLL:
         L.icp_track.argtypes = [ctypes.POINTER(GpsIntrinsics), c_void_p, c_void_p, c_void_p,
                                 ctypes.POINTER(GpsPose), ctypes.POINTER(GpsIcpSettings), c_void_p,
                                 c_void_p, c_size_t, c_void_p, c_void_p]
+        P_H = ctypes.POINTER(GpsHashTsdf)
+        L.gps_hash_scratch_size.argtypes = [c_int32, ctypes.POINTER(c_size_t)]
+        L.fuse_frame_hashed.argtypes = [P_H, c_void_p, c_void_p, ctypes.POINTER(GpsIntrinsics),
+                                        ctypes.POINTER(GpsPose), c_void_p, c_size_t, c_int32,
+                                        c_void_p]
+        L.raycast_sdf_hashed.argtypes = [P_H, ctypes.POINTER(GpsIntrinsics),
+                                         ctypes.POINTER(GpsPose), c_float, c_float, c_void_p,
+                                         c_int32, c_void_p, c_void_p, c_void_p]
+        L.tsdf_hash_to_dense.argtypes = [P_H, ctypes.POINTER(GpsTsdf), c_void_p]
         _lib = L
     return _lib
 
@@ -347,6 +365,91 @@ class Tsdf:
         return (brick_to_linear(self.sdf, s.nx, s.ny, s.nz),
                 brick_to_linear(self.weight, s.nx, s.ny, s.nz),
                 brick_to_linear(self.rgbw, s.nx, s.ny, s.nz))
+
+
+class HashTsdf:
+    """Voxel-hashed TSDF on the device (see GpsHashTsdf): a pool of `capacity`
+    8^3 bricks, a table of n_buckets buckets (default: the power of two at
+    least 4 x capacity), the same index space and fusion parameters as the
+    dense `spec`, and the per-frame candidate scratch."""
+
+    def __init__(self, spec, capacity: int, n_buckets: Optional[int] = None,
+                 max_candidates: int = 1 << 17, device="cuda"):
+        self.spec = spec
+        self.capacity = capacity
+        nb = 2
+        while nb < (n_buckets or 4 * capacity):
+            nb <<= 1
+        self.n_buckets = nb
+        self.max_candidates = max_candidates
+        dev = torch.device(device)
+        self.keys = torch.zeros(nb, dtype=torch.int64, device=dev)
+        self.slots = torch.zeros(nb, dtype=torch.int32, device=dev)
+        self.brick_of_slot = torch.zeros(capacity, dtype=torch.int64, device=dev)
+        self.state = torch.zeros(4, dtype=torch.int32, device=dev)
+        self.sdf = torch.ones(capacity * 512, device=dev)
+        self.weight = torch.zeros(capacity * 512, device=dev)
+        self.rgbw = torch.zeros(capacity * 512, 4, device=dev)
+        self.scratch = torch.zeros(gps_hash_scratch_size(max_candidates), dtype=torch.uint8,
+                                   device=dev)
+
+    def reset(self):
+        self.keys.zero_()
+        self.state.zero_()
+
+    def c(self) -> GpsHashTsdf:
+        s = self.spec
+        return GpsHashTsdf(s.nx, s.ny, s.nz, float(s.voxel), (c_float * 3)(*map(float, s.origin)),
+                           float(s.trunc), float(s.max_weight), self.n_buckets, self.capacity,
+                           _ptr(self.keys), _ptr(self.slots), _ptr(self.brick_of_slot),
+                           _ptr(self.state), _ptr(self.sdf), _ptr(self.weight), _ptr(self.rgbw))
+
+    def allocated(self) -> int:
+        """Bricks in use (reads the device counter: synchronises)."""
+        return min(int(self.state[0].item()), self.capacity)
+
+    def error(self) -> int:
+        return int(self.state[1].item())
+
+    def bricks(self) -> torch.Tensor:
+        """Brick indices of the allocated bricks, in pool order."""
+        return self.brick_of_slot[:self.allocated()]
+
+    def to_dense(self, dense: "Tsdf", stream=None) -> None:
+        h, d = self.c(), dense.c()
+        _check(lib().tsdf_hash_to_dense(ctypes.byref(h), ctypes.byref(d), _stream(stream)))
+
+
+def gps_hash_scratch_size(max_candidates: int) -> int:
+    n = c_size_t(0)
+    _check(lib().gps_hash_scratch_size(max_candidates, ctypes.byref(n)))
+    return int(n.value)
+
+
+def fuse_frame_hashed(vol: HashTsdf, depth: torch.Tensor, rgb: torch.Tensor, cam,
+                      stream=None) -> None:
+    K, P = intrinsics(cam), pose(cam)
+    h = vol.c()
+    _check(lib().fuse_frame_hashed(ctypes.byref(h), _ptr(depth), _ptr(rgb), ctypes.byref(K),
+                                   ctypes.byref(P), _ptr(vol.scratch), vol.scratch.numel(),
+                                   vol.max_candidates, _stream(stream)))
+
+
+def raycast_sdf_hashed(vol: HashTsdf, cam, near=0.2, far=0.0, out_rgb=None, out_depth=None,
+                       out_vertex=None, stream=None, precision=PREC_FP32):
+    """raycast_sdf on a hashed volume."""
+    H, W = cam.height, cam.width
+    dev = vol.sdf.device
+    if out_rgb is None:
+        out_rgb = torch.empty(3, H, W, device=dev, dtype=PREC_DTYPE[precision])
+    prec = _precision_of(out_rgb)
+    out_depth = out_depth if out_depth is not None else torch.empty(H, W, device=dev)
+    K, P = intrinsics(cam), pose(cam)
+    h = vol.c()
+    _check(lib().raycast_sdf_hashed(ctypes.byref(h), ctypes.byref(K), ctypes.byref(P), near, far,
+                                    _ptr(out_rgb), prec, _ptr(out_depth), _ptr(out_vertex),
+                                    _stream(stream)))
+    return out_rgb, out_depth
 
 
 def settings(eps_depth=0.01, lambda_depth=0.0, near=0.2, blend_mode=BLEND_OIT,

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgps.so")
 SOURCES = ["tsdf.cu", "project.cu", "binning.cu", "composite.cu", "adam.cu", "capi.cu",
-           "noalloc.cu", "autotune.cu", "edit.cu", "schedule.cu", "icp.cu"]
+           "noalloc.cu", "autotune.cu", "edit.cu", "schedule.cu", "icp.cu", "hash.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -141,15 +141,6 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
   return GPS_OK;
 }
 
-Cam make_cam(const GpsIntrinsics& K, const GpsPose& P) {
-  Cam c;
-  c.fx = K.fx; c.fy = K.fy; c.cx = K.cx; c.cy = K.cy;
-  c.W = K.width; c.H = K.height;
-  for (int k = 0; k < 9; ++k) c.R[k] = P.R[k];
-  for (int k = 0; k < 3; ++k) c.t[k] = P.t[k];
-  return c;
-}
-
 bool finite_cam(const GpsIntrinsics& K, const GpsPose& P) {
   bool ok = std::isfinite(K.fx) && std::isfinite(K.fy) && std::isfinite(K.cx) &&
             std::isfinite(K.cy) && K.fx > 0 && K.fy > 0 && K.width > 0 && K.height > 0;

@@ -30,6 +30,16 @@ struct Cam {
   float t[3];
 };
 
+// Device camera from the ABI's intrinsics and pose.
+inline Cam make_cam(const GpsIntrinsics& K, const GpsPose& P) {
+  Cam c;
+  c.fx = K.fx; c.fy = K.fy; c.cx = K.cx; c.cy = K.cy;
+  c.W = K.width; c.H = K.height;
+  for (int k = 0; k < 9; ++k) c.R[k] = P.R[k];
+  for (int k = 0; k < 3; ++k) c.t[k] = P.t[k];
+  return c;
+}
+
 // Per-view device-side description (passed by value to kernels).
 struct ViewDev {
   Cam cam;

@@ -44,7 +44,7 @@ def test_library_exports_every_declared_symbol(L):
 def test_struct_layouts_match_header(tmp_path):
     structs = ["GpsIntrinsics", "GpsPose", "GpsTsdf", "GpsGaussians", "GpsView",
                "GpsRenderSettings", "GpsAdamHyper", "GpsWorkspaceLayout", "GpsEditSettings",
-               "GpsViewSchedule", "GpsIcpSettings"]
+               "GpsViewSchedule", "GpsIcpSettings", "GpsHashTsdf"]
     prog = tmp_path / "sz.c"
     body = "".join(f'  printf("{s} %zu\\n", sizeof({s}));\n' for s in structs)
     body += '  printf("off_pair_capacity %zu\\n", offsetof(GpsRenderSettings, pair_capacity));\n'
@@ -182,3 +182,22 @@ def test_icp_arguments_are_checked_on_the_host(L):
     n1 = gps.gps_icp_workspace_size(64, 48, gps.icp_settings(levels=1))
     n3 = gps.gps_icp_workspace_size(64, 48, gps.icp_settings())
     assert 0 < n1 < n3 and n3 % 256 == 0
+
+
+def test_hashed_volume_arguments_are_checked_on_the_host(L):
+    import ctypes as C
+    fake = C.c_void_p(256)     # never dereferenced: validation fails before any launch
+    h = gps.GpsHashTsdf(64, 64, 64, 0.02, (C.c_float * 3)(0, 0, 0), 0.06, 100.0, 1024, 256,
+                        fake, fake, fake, fake, fake, fake, fake)
+    K = gps.GpsIntrinsics(100.0, 100.0, 50.0, 40.0, 100, 80)
+    P = gps.GpsPose((C.c_float * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1), (C.c_float * 3)(0, 0, 0))
+    n = gps.gps_hash_scratch_size(1000)
+    for field, bad in (("nx", 60), ("n_buckets", 1000), ("capacity", 0), ("voxel", 0.0)):
+        hb = gps.GpsHashTsdf.from_buffer_copy(h)
+        setattr(hb, field, bad)
+        assert L.fuse_frame_hashed(C.byref(hb), fake, fake, C.byref(K), C.byref(P), fake, n,
+                                   1000, None) == gps.GPS_ERR_INVALID_ARG, field
+    assert L.fuse_frame_hashed(C.byref(h), fake, fake, C.byref(K), C.byref(P), fake, n - 1,
+                               1000, None) == gps.GPS_ERR_WORKSPACE_TOO_SMALL
+    with pytest.raises(gps.GpsError):
+        gps.gps_hash_scratch_size(0)
