@@ -66,14 +66,18 @@ def parse():
     ap.add_argument("--schedule", default="tiles", choices=["tiles", "per-gaussian"],
                     help="per-gaussian: the paper's sort-free form (unsorted tile lists, "
                          "one warp per Gaussian in the backward; OIT only)")
+    ap.add_argument("--hash", action="store_true",
+                    help="sequence workload: keep the TSDF in the voxel-hash volume")
     ap.add_argument("--workload", default="room",
-                    choices=["room", "large", "multiview", "sequence"],
+                    choices=["room", "large", "multiview", "sequence", "fusion"],
                     help="room: 640x480, 100k Gaussians (the headline); large: 1280x720, "
                          "5.12 m room, 512^3 TSDF, 1M Gaussians; multiview: 8 mixed-resolution "
                          "views of one scene, 300k Gaussians, one call for all views vs one per "
                          "view; sequence: the online loop of Sec. 3.2 over the room's frames "
                          "(fusion every frame; every 10 frames insertion, keyframe + local view "
-                         "selection, 20 iterations over the views, removal), from no Gaussians")
+                         "selection, 20 iterations over the views, removal), from no Gaussians; "
+                         "fusion: TSDF fusion + ray-cast per frame, dense grid vs voxel hashing, "
+                         "at 1 cm and 0.5 cm")
     ap.add_argument("--profile", action="store_true",
                     help="short plain run (3 frames) for ncu captures; prints no JSON line")
     return ap.parse_args()
@@ -857,7 +861,7 @@ def run_sequence(args, rank, world, local):
     import torch
     import paper_2509_11574_b300 as gps
     from paper_2509_11574_b300 import build
-    from paper_2509_11574_b300.mapper import Mapper
+    from paper_2509_11574_b300.mapper import Mapper, raycast_volume
     from datagen import workloads
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -875,7 +879,7 @@ def run_sequence(args, rank, world, local):
     prec = PRECISIONS[args.precision]
     s = gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, near=w.near, tile=tile,
                      precision=prec)
-    vol = gps.Tsdf(w.tsdf, dev)
+    vol = gps.HashTsdf(w.tsdf, HASH_BRICKS_1CM, device=dev) if args.hash else gps.Tsdf(w.tsdf, dev)
     mp = Mapper(vol, w.frames[0].cam, SEQ_CAPACITY, s, iterations=SEQ_ITERS, near=w.near,
                 sh_degree=args.sh_degree, track=args.track, device=dev)
     dev_frames = [(torch.from_numpy(f.rgb).to(dev), torch.from_numpy(f.depth).to(dev))
@@ -924,8 +928,7 @@ def run_sequence(args, rank, world, local):
         err = np.linalg.norm(est - true, axis=1)
         # icp_track alone: frame 1 against the ray-cast at frame 0's pose (final TSDF)
         tr = mp.tracker
-        gps.raycast_sdf(vol, w.frames[0].cam, w.near, 0.0, mp.ref_rgb, mp.ref_depth,
-                        mp.ref_vertex)
+        raycast_volume(vol, w.frames[0].cam, w.near, mp.ref_rgb, mp.ref_depth, mp.ref_vertex)
         d1 = dev_frames[1][1]
         evs = []
         for i in range(13):
@@ -964,6 +967,7 @@ def run_sequence(args, rank, world, local):
                    "tile": f"{tile[0]}x{tile[1]}", "colour_storage": args.precision,
                    "sh_degree": args.sh_degree,
                    "poses": "tracked by ICP from frame 1 on" if args.track else "given",
+                   "tsdf": "voxel hashing" if args.hash else "dense grid",
                    "form": "plain launches; the whole sequence is one timed region, "
                            "run once untimed before",
                    "l2": "256 MB buffer written before the timed region; the 336 MB TSDF "
@@ -981,6 +985,102 @@ def run_sequence(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ fusion
+HASH_BRICKS_1CM = 60_000     # pool bricks (12 KB each) for the 2.56 m room at 1 cm
+HASH_BRICKS_05CM = 240_000   # and at 0.5 cm
+
+
+def run_fusion(args, rank, world, local):
+    """TSDF fusion and ray-cast of the room's 640x480 frames into a dense grid
+    and into the voxel-hash volume, at 1 cm (256^3) and at the paper's 0.5 cm
+    (512^3 index space).  One step = one frame: fuse + ray-cast; the timed
+    region is all frames (CUDA events per stage), run once untimed before.
+    value = frames/s of the hashed volume at 0.5 cm."""
+    import torch
+    import paper_2509_11574_b300 as gps
+    from paper_2509_11574_b300 import build
+    from datagen import workloads
+    from datagen.scenes import TsdfSpec
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    gps.lib()
+    w = workloads.room(n_frames=args.frames or N_FRAMES, M=16, seed_scene=2 + 1000 * rank,
+                       seed_path=3 + 1000 * rank)
+    frames = [(torch.from_numpy(f.depth).to(dev), torch.from_numpy(f.rgb).to(dev), f.cam)
+              for f in w.frames]
+    H, W = w.frames[0].cam.height, w.frames[0].cam.width
+    out_rgb = torch.empty(3, H, W, device=dev)
+    out_d = torch.empty(H, W, device=dev)
+    s1 = w.tsdf
+    s05 = TsdfSpec(2 * s1.nx, 2 * s1.ny, 2 * s1.nz, s1.voxel / 2, s1.origin, s1.trunc / 2)
+    res = {}
+    for name, spec, hashed, cap in (("dense_1cm", s1, False, 0), ("hash_1cm", s1, True, HASH_BRICKS_1CM),
+                                    ("dense_0.5cm", s05, False, 0),
+                                    ("hash_0.5cm", s05, True, HASH_BRICKS_05CM)):
+        vol = gps.HashTsdf(spec, cap, device=dev) if hashed else gps.Tsdf(spec, dev)
+        fuse = (lambda d, c, cam: gps.fuse_frame_hashed(vol, d, c, cam)) if hashed else \
+            (lambda d, c, cam: gps.fuse_frame(vol, d, c, cam))
+        cast = (lambda cam: gps.raycast_sdf_hashed(vol, cam, w.near, 0.0, out_rgb, out_d)) if hashed \
+            else (lambda cam: gps.raycast_sdf(vol, cam, w.near, 0.0, out_rgb, out_d))
+        ev = []
+        for rep in range(2):              # untimed pass, then the timed one
+            vol.reset()
+            torch.cuda.synchronize()
+            ev = []
+            for d, c, cam in frames:
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record()
+                fuse(d, c, cam)
+                e[1].record()
+                cast(cam)
+                e[2].record()
+                ev.append(e)
+            torch.cuda.synchronize()
+        fuse_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / len(ev)
+        cast_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / len(ev)
+        entry = {"fuse_ms": fuse_ms, "raycast_ms": cast_ms, "frame_ms": fuse_ms + cast_ms,
+                 "hit_fraction": float((out_d > 0).float().mean())}
+        if hashed:
+            n = vol.allocated()
+            entry.update(bricks=n, error=vol.error(),
+                         bytes=int(n * 512 * 24 + vol.n_buckets * 12 + cap * 8))
+        else:
+            entry["bytes"] = int(spec.nx * spec.ny * spec.nz * 24)
+        res[name] = entry
+        del vol
+        torch.cuda.empty_cache()
+    ms = res["hash_0.5cm"]["frame_ms"]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        return
+    n = len(frames)
+    line = {
+        "metric": f"TSDF fusion + ray-cast frames/sec ({W}x{H} room, voxel hashing at 0.5 cm)",
+        "value": 1e3 / ms * world, "unit": "frames/s", "n_gpus": world, "steps": n, "warmup": n,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"room {s1.nx * s1.voxel:.2f} m, {n} frames {W}x{H}; "
+                               "dense 256^3 / 512^3 grids vs voxel hashing at 1 cm / 0.5 cm "
+                               "(trunc 3 / 1.5 cm)",
+                   "form": "plain launches, CUDA events per stage, all frames timed after one "
+                           "untimed pass",
+                   "l2": "the volumes (0.4-3.2 GB dense) exceed L2"},
+        "volumes": res,
+        "gpu": torch.cuda.get_device_name(dev),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -990,6 +1090,8 @@ def main():
         run_multiview(args, rank, world, local)
     elif args.workload == "sequence":
         run_sequence(args, rank, world, local)
+    elif args.workload == "fusion":
+        run_fusion(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

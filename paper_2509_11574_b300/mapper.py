@@ -5,7 +5,8 @@ insertion on that frame, selection of the optimisation views (Fig. 5), one
 ray-cast per view, `iterations` batched forward + backward + Adam steps over
 those views, and removal.
 
-With track=True, frame k > 0 is tracked by point-to-plane ICP against the
+The volume is a dense `Tsdf` or a voxel-hashed `HashTsdf`.  With
+track=True, frame k > 0 is tracked by point-to-plane ICP against the
 ray-cast of the TSDF at frame k-1's estimated pose, starting from that pose,
 and is fused and later rendered at its estimate; frame 0 keeps the pose it
 is given (it anchors the map).  Without tracking the given poses are used.
@@ -26,14 +27,29 @@ from typing import Dict, List, Optional
 import torch
 
 from . import (LR_APP_C, PREC_DTYPE, GpsEditSettings, GpsIcpSettings, GpsRenderSettings,
-               GpsViewSchedule, Gaussians, PoseCam, Tracker, Tsdf, View, adam_step,
-               edit_settings, fuse_frame, gps_edit_scratch_size,
+               GpsViewSchedule, Gaussians, HashTsdf, PoseCam, Tracker, Tsdf, View, adam_step,
+               edit_settings, fuse_frame, fuse_frame_hashed, gps_edit_scratch_size,
                gps_is_keyframe, gps_query_status, gps_select_views, gps_workspace_size,
-               insert_gaussians, raycast_sdf, remove_gaussians, render_backward, render_forward,
-               settings as render_settings, view_schedule)
+               insert_gaussians, raycast_sdf, raycast_sdf_hashed, remove_gaussians,
+               render_backward, render_forward, settings as render_settings, view_schedule)
 from . import GPS_OK, GpsError
 
 MAX_VIEWS_PER_CALL = 8  # views one render_forward / render_backward call takes
+
+
+def fuse_volume(vol, depth, rgb, cam):
+    """fuse_frame or fuse_frame_hashed, by the volume's type."""
+    if isinstance(vol, HashTsdf):
+        fuse_frame_hashed(vol, depth, rgb, cam)
+    else:
+        fuse_frame(vol, depth, rgb, cam)
+
+
+def raycast_volume(vol, cam, near, out_rgb, out_depth, out_vertex=None):
+    """raycast_sdf or raycast_sdf_hashed, by the volume's type."""
+    if isinstance(vol, HashTsdf):
+        return raycast_sdf_hashed(vol, cam, near, 0.0, out_rgb, out_depth, out_vertex)
+    return raycast_sdf(vol, cam, near, 0.0, out_rgb, out_depth, out_vertex)
 
 
 @dataclasses.dataclass
@@ -53,7 +69,7 @@ def _rows(g: Gaussians, n: int) -> Gaussians:
 
 
 class Mapper:
-    def __init__(self, vol: Tsdf, cam, capacity: int,
+    def __init__(self, vol, cam, capacity: int,
                  s: Optional[GpsRenderSettings] = None,
                  edit: Optional[GpsEditSettings] = None,
                  sched: Optional[GpsViewSchedule] = None,
@@ -142,12 +158,11 @@ class Mapper:
         is enqueued on torch's current stream."""
         if self.tracker is not None and self.poses:
             prev = self.poses[-1]
-            raycast_sdf(self.vol, prev, self.near, 0.0, self.ref_rgb, self.ref_depth,
-                        self.ref_vertex)
+            raycast_volume(self.vol, prev, self.near, self.ref_rgb, self.ref_depth, self.ref_vertex)
             self.tracker.track(depth, self.ref_vertex, self.ref_depth, prev)
             cam = self.tracker.result()          # reads the pose back (synchronises)
         self.poses.append(cam)
-        fuse_frame(self.vol, depth, rgb, cam)
+        fuse_volume(self.vol, depth, rgb, cam)
         if gps_is_keyframe(self.last_keyframe_cam, cam, self.sched):
             self.keyframes.append(frame)
             self.last_keyframe_cam = cam
@@ -169,7 +184,7 @@ class Mapper:
         cam, rgb, depth = self.frames[frame]
         # insertion (Sec. 3.2): second-pass render of this frame with the
         # current Gaussians gives C* and W_G
-        ct, dt = raycast_sdf(self.vol, cam, self.near, 0.0, self.ct[0], self.dt[0], self.vertex)
+        ct, dt = raycast_volume(self.vol, cam, self.near, self.ct[0], self.dt[0], self.vertex)
         if self.M > 0:
             v = View(cam, ct, dt, out_rgb=self.c_star, out_depth=self.d_star, out_weight=self.w_g)
             render_forward(_rows(self.g, self.M), [v], self.s, self.ws, None)
@@ -187,7 +202,7 @@ class Mapper:
         for k, f in enumerate(ids):
             c, col, dep = self.frames[f]
             if not (k == 0 and f == frame):    # view 0 is usually this frame: ray-cast above
-                raycast_sdf(self.vol, c, self.near, 0.0, self.ct[k], self.dt[k], None)
+                raycast_volume(self.vol, c, self.near, self.ct[k], self.dt[k], None)
             views.append(View(c, self.ct[k], self.dt[k], col, dep))
         g, gr = _rows(self.g, self.M), _rows(self.grads, self.M)
         m, v = _rows(self.m, self.M), _rows(self.v, self.M)
