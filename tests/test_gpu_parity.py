@@ -541,8 +541,27 @@ def test_per_gaussian_schedule_matches_tile_schedule(name):
     (c0, l0, g0), (c1, l1, g1) = res
     np.testing.assert_allclose(c1, c0, atol=2e-6)
     np.testing.assert_allclose(l1, l0, rtol=1e-5)
-    # a residual within FP32 rounding of zero can flip its L1 sign between the
-    # two summation orders; everything else agrees to accumulation rounding
+    # A residual within FP32 rounding of zero can flip its L1 sign between the
+    # two summation orders (the unsorted forward's order also varies run to
+    # run), moving the gradients of every Gaussian over that pixel; the flips
+    # touch well under 1% of the elements
     scale = np.abs(g0).max()
     close = np.abs(g1 - g0) <= 1e-4 * scale + 1e-4 * np.abs(g0)
-    assert close.mean() > 0.999, close.mean()
+    assert close.mean() > 0.99, close.mean()
+    # with the same upstream gradients on both sides every element agrees to
+    # accumulation rounding
+    up = np.sign(c0 - f.rgb) * ((f.depth > 0) & (Dt > 0))[None] / 3.0
+    outs = []
+    for sched in (gps.SCHEDULE_TILES, gps.SCHEDULE_PER_GAUSSIAN):
+        s = gps.settings(eps_depth=w.eps_depth, tile=(16, 8), schedule=sched)
+        r = gps.Renderer(w.gaussians.M, [f.cam], s)
+        g = gps.Gaussians.from_numpy(w.gaussians)
+        v = gps.View(f.cam, cuda(Ct), cuda(Dt), grad_rgb=cuda(up),
+                     grad_depth=torch.zeros(H, W, device="cuda"))
+        r.forward(g, [v])
+        grads = g.zeros_like()
+        r.backward(g, [v], grads)
+        assert r.status() == gps.GPS_OK
+        outs.append(grads.flat().cpu().numpy())
+    scale = np.abs(outs[0]).max()
+    assert np.all(np.abs(outs[1] - outs[0]) <= 1e-4 * scale + 1e-4 * np.abs(outs[0]))
