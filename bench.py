@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--hash", action="store_true",
                     help="sequence workload: keep the TSDF in the voxel-hash volume")
     ap.add_argument("--workload", default="room",
-                    choices=["room", "large", "multiview", "sequence", "fusion"],
+                    choices=["room", "large", "multiview", "sequence", "fusion", "track"],
                     help="room: 640x480, 100k Gaussians (the headline); large: 1280x720, "
                          "5.12 m room, 512^3 TSDF, 1M Gaussians; multiview: 8 mixed-resolution "
                          "views of one scene, 300k Gaussians, one call for all views vs one per "
@@ -77,7 +77,8 @@ def parse():
                          "(fusion every frame; every 10 frames insertion, keyframe + local view "
                          "selection, 20 iterations over the views, removal), from no Gaussians; "
                          "fusion: TSDF fusion + ray-cast per frame, dense grid vs voxel hashing, "
-                         "at 1 cm and 0.5 cm")
+                         "at 1 cm and 0.5 cm; track: ICP alone, each frame against the ray-cast "
+                         "at the previous frame's pose")
     ap.add_argument("--profile", action="store_true",
                     help="short plain run (3 frames) for ncu captures; prints no JSON line")
     return ap.parse_args()
@@ -1081,6 +1082,80 @@ def run_fusion(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ tracking
+def run_track(args, rank, world, local):
+    """Camera tracking alone (Sec. 3.2, Eq. 5): the room's frames are fused
+    with their given poses, then every frame k >= 1 is tracked by icp_track
+    against the ray-cast at frame k - 1's pose, starting from that pose.  One
+    step = one icp_track call (CUDA events around it); W warm-up calls on
+    frame 1 first.  value = tracked frames/s; the JSON line also reports the
+    error of the tracked camera centres."""
+    import numpy as np
+    import torch
+    import paper_2509_11574_b300 as gps
+    from paper_2509_11574_b300 import build
+    from datagen import workloads
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    gps.lib()
+    w = workloads.room(n_frames=args.frames or N_FRAMES, M=16, seed_scene=2 + 1000 * rank,
+                       seed_path=3 + 1000 * rank)
+    vol = gps.Tsdf(w.tsdf, dev)
+    depths = [torch.from_numpy(f.depth).to(dev) for f in w.frames]
+    for f, d in zip(w.frames, depths):
+        gps.fuse_frame(vol, d, torch.from_numpy(f.rgb).to(dev), f.cam)
+    H, W = w.frames[0].cam.height, w.frames[0].cam.width
+    refs = []
+    for f in w.frames[:-1]:
+        v = torch.empty(H, W, 3, device=dev)
+        c, d = gps.raycast_sdf(vol, f.cam, w.near, 0.0, None, None, v)
+        refs.append((v, d))
+    tr = gps.Tracker(w.frames[0].cam, device=dev)
+    for _ in range(args.warmup):
+        tr.track(depths[1], refs[0][0], refs[0][1], w.frames[0].cam)
+    torch.cuda.synchronize()
+    ev, err = [], []
+    for k in range(1, len(w.frames)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tr.track(depths[k], refs[k - 1][0], refs[k - 1][1], w.frames[k - 1].cam)
+        e1.record()
+        ev.append((e0, e1))
+        est = tr.result()                 # synchronises
+        err.append(float(np.linalg.norm(est.t.numpy() - np.asarray(w.frames[k].cam.t))))
+    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        return
+    n_it = sum(tr.s.iters[l] for l in range(tr.s.levels))
+    line = {
+        "metric": f"ICP tracked frames/sec ({W}x{H} room, 3-level point-to-plane)",
+        "value": 1e3 / ms * world, "unit": "frames/s", "n_gpus": world, "steps": len(ev),
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"room, {len(w.frames)} frames {W}x{H}, each tracked against "
+                               "the ray-cast at the previous frame's pose",
+                   "icp": {"levels": tr.s.levels, "iterations": [int(tr.s.iters[l]) for l in
+                                                                 range(tr.s.levels)],
+                           "eps_d": tr.s.eps_d, "eps_theta_deg": tr.s.eps_theta_deg},
+                   "form": "plain launches, CUDA events around each icp_track"},
+        "gpu_launches_per_step": (tr.s.levels - 1) + 2 * tr.s.levels + 2 + n_it,
+        "centre_error_m": {"rmse": float(np.sqrt(np.mean(np.square(err)))), "max": max(err)},
+        "gpu": torch.cuda.get_device_name(dev),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -1092,6 +1167,8 @@ def main():
         run_sequence(args, rank, world, local)
     elif args.workload == "fusion":
         run_fusion(args, rank, world, local)
+    elif args.workload == "track":
+        run_track(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 
