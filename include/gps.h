@@ -169,7 +169,10 @@ typedef struct GpsRenderSettings {
   int32_t precision;     /* GPS_PREC_*: element type of the colour images      */
   int32_t tile_w, tile_h;/* pixels per tile; 0, 0 = 16 x 8; supported: 16x16,
                             16x8, 8x8, 32x8 (gps_autotune_tiles picks one)   */
-  int32_t deterministic; /* 1: fixed-order gradient reduction, no float atomics */
+  int32_t deterministic; /* 1: bitwise reproducible: tile lists sorted by
+                            (depth, index), fixed-order gradient reduction, no
+                            float atomics.  0 (OIT): lists in emission order,
+                            which may change the last bits of C* run to run  */
   int32_t stages;        /* GPS_STAGE_* mask, 0 = all                          */
   int32_t instrument;    /* 1: count Gaussian-pixel evaluations (slower; for
                             measurement runs) into the view scalars           */
@@ -283,7 +286,11 @@ GPS_API int32_t raycast_sdf(const GpsTsdf* vol, const GpsIntrinsics* K, const Gp
  * fused L1 loss (Eq. 6) written to *loss (device float, nullable):
  *   L = sum_v [ sum |C* - C_k| / (3 N_v) + lambda_depth sum |D* - D_k| / N_v ]
  * over pixels with D_k > 0 and D_t > 0 (N_v of them).  Writes the views'
- * non-null outputs and the state render_backward needs into the workspace. */
+ * non-null outputs and the state render_backward needs into the workspace.
+ * The OIT blend is order-independent, so unless settings.deterministic asks
+ * for a fixed order it runs sort-free: each tile's list keeps the order of
+ * the binning's emission and every warp skips the Gaussians behind all of its
+ * pixels.  The "with sort" blend always sorts by (depth, index). */
 GPS_API int32_t render_forward(const GpsGaussians* gaussians, const GpsView* views, int32_t n_views,
                        const GpsRenderSettings* settings, void* ws, size_t ws_bytes,
                        float* loss, void* stream);

@@ -28,7 +28,7 @@ cudaError_t launch_composite_fwd(const ViewBatch&, int, int, float, int, int, in
 cudaError_t launch_composite_bwd_per_gaussian(const ViewBatch&, int, float, float, const float*,
                                               int, cudaStream_t);
 cudaError_t launch_composite_bwd(const ViewBatch&, int, int, float, float, const float*, int, int,
-                                 int, cudaStream_t);
+                                 int, int, cudaStream_t);
 cudaError_t launch_finalize_loss(const ViewBatch&, float, float*, int, cudaStream_t);
 cudaError_t launch_gather_pair_grads(const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_adam(const GpsGaussians&, const GpsGaussians&, const GpsGaussians&,
@@ -139,6 +139,17 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
   if (out) out->total_bytes = off;
   if (total) *total = off;
   return GPS_OK;
+}
+
+// Are the tile lists sorted by (depth, index)?  The "with sort" blend needs
+// front-to-back order, and deterministic mode needs one fixed order for the
+// forward's sums and the pair-slot gather.  The OIT blend of Eq. 1-4 is
+// order-independent, so by default it skips the sort (the paper's sort-free
+// pass): its lists keep emission order, which varies with the order in which
+// the binning's atomics ran, so its FP32 sums may differ run to run in the
+// last bits.  The per-Gaussian schedule never sorts.
+int depth_sorted(const GpsRenderSettings& s) {
+  return s.schedule == GPS_SCHEDULE_TILES && (s.blend_mode == GPS_BLEND_ALPHA || s.deterministic);
 }
 
 bool finite_cam(const GpsIntrinsics& K, const GpsPose& P) {
@@ -362,17 +373,16 @@ int32_t render_forward(const GpsGaussians* g, const GpsView* views, int32_t n_vi
     if (e == cudaSuccess && (stages & GPS_STAGE_BIN)) {
       e = launch_scan_super(vb, status, st);
       if (e == cudaSuccess && g->M > 0) e = launch_emit_super(g->M, vb, max_nsup, st);
-      // sort each super-tile's segment and split it into its tiles' lists (the
-      // per-Gaussian schedule keeps emission order)
-      if (e == cudaSuccess)
-        e = launch_sort_split(vb, v0.tw, v0.th, s->schedule == GPS_SCHEDULE_TILES, st);
+      // split each super-tile's segment into its tiles' lists, sorted by depth
+      // where the settings ask for an order (see depth_sorted)
+      if (e == cudaSuccess) e = launch_sort_split(vb, v0.tw, v0.th, depth_sorted(*s), st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_COMPOSITE)) {
       for (int j = 0; j < vb.n && e == cudaSuccess && s->instrument; ++j)
         e = cudaMemsetAsync(vb.v[j].scalars + 8, 0, 32, st);
       if (e == cudaSuccess)
         e = launch_composite_fwd(vb, v0.tw, v0.th, s->eps_depth, s->blend_mode, has_tgt ? 1 : 0,
-                                 s->instrument ? 1 : 0, s->schedule == GPS_SCHEDULE_TILES, st);
+                                 s->instrument ? 1 : 0, depth_sorted(*s), st);
       if (e == cudaSuccess && has_tgt)
         e = launch_finalize_loss(vb, s->lambda_depth, loss, b0 == 0 ? 1 : 0, st);
     }
@@ -410,7 +420,8 @@ int32_t render_backward(const GpsGaussians* g, const GpsView* views, int32_t n_v
         e = cudaMemsetAsync(vb.v[j].grad2d, 0, (size_t)g->M * 48, st);
       if (e == cudaSuccess)
         e = launch_composite_bwd(vb, vb.v[0].tw, vb.v[0].th, s->eps_depth, s->lambda_depth, dloss,
-                                 s->blend_mode, s->deterministic ? 1 : 0, s->instrument ? 1 : 0, st);
+                                 s->blend_mode, s->deterministic ? 1 : 0, s->instrument ? 1 : 0,
+                                 depth_sorted(*s), st);
       if (e == cudaSuccess && s->deterministic && g->M > 0) e = launch_gather_pair_grads(vb, g->M, st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_PROJECT_BWD) && g->M > 0)

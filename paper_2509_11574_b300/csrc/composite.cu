@@ -439,7 +439,8 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
           const float4 A = s_a[j];
           const float2 E = s_e[j];
           stop = sorted && A.z >= wthr;
-          ok = A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 && A.y - E.y <= by1;
+          ok = A.z < wthr && A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 &&
+               A.y - E.y <= by1;
           if (ok) {
             const float4 B = s_b[j];
             ok = ellipse_meets_rect(A.x, A.y, B.x, 0.5f * B.y, B.z, B.w, bx0, bx1, by0, by1);
@@ -658,7 +659,7 @@ template <int TW, int TH, bool INSTR>
 __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_constant__ ViewBatch vb,
                                                                    float eps, float lambda,
                                                                    const float* dloss,
-                                                                   int deterministic) {
+                                                                   int deterministic, int sorted) {
   constexpr int NT = TW * TH;
   constexpr int NW = NT / 32;
   constexpr int NB = BwdBatch<NT>::value;
@@ -702,7 +703,10 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
   uint32_t gi_next = tid < NB && r.x + tid < r.y ? (uint32_t)v.keys[r.x + tid] : 0u;
   const float wthr = warp_max(thr);
   const float bthr = block_max<NT>(thr, s_tmp);
-  const uint32_t end = depth_cut_block<NT>(v.keys, r.x, r.y, bthr);
+  // a depth-sorted list ends at the first Gaussian behind every pixel of the
+  // tile; an unsorted one is walked to its end, each warp skipping the
+  // Gaussians behind all of its pixels
+  const uint32_t end = sorted ? depth_cut_block<NT>(v.keys, r.x, r.y, bthr) : r.y;
   const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
   const float by0 = (float)(ty * TH + oy), by1 = by0 + 3.0f;
   const int blk = warp * 32;  // this warp's pixels in s_h / s_s
@@ -735,8 +739,9 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
         if (j < nb) {
           const float4 A = s_a[j];
           const float2 E = s_e[j];
-          stop = A.z >= wthr;
-          ok = A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 && A.y - E.y <= by1;
+          stop = sorted && A.z >= wthr;
+          ok = A.z < wthr && A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 &&
+               A.y - E.y <= by1;
           if (ok) {
             const float4 B = s_b[j];
             ok = ellipse_meets_rect(A.x, A.y, B.x, 0.5f * B.y, B.z, B.w, bx0, bx1, by0, by1);
@@ -1165,14 +1170,16 @@ static cudaError_t fwd_tw(const ViewBatch& vb, float eps, int mode, int has_tgt,
 
 template <int TW, int TH>
 static cudaError_t bwd_tw(const ViewBatch& vb, float eps, float lambda, const float* dloss, int mode,
-                          int det, int instr, cudaStream_t st) {
+                          int det, int instr, int sorted, cudaStream_t st) {
   const int items = vb.tile_start[vb.n];
   if (items <= 0) return cudaSuccess;
   if (mode == GPS_BLEND_OIT) {
     if (instr)
-      composite_bwd_oit_kernel<TW, TH, true><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss, det);
+      composite_bwd_oit_kernel<TW, TH, true><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss, det,
+                                                                        sorted);
     else
-      composite_bwd_oit_kernel<TW, TH, false><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss, det);
+      composite_bwd_oit_kernel<TW, TH, false><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss,
+                                                                         det, sorted);
   } else
     composite_bwd_alpha_kernel<TW, TH><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss, det);
   return cudaGetLastError();
@@ -1188,11 +1195,12 @@ cudaError_t launch_composite_fwd(const ViewBatch& vb, int tw, int th, float eps,
 }
 
 cudaError_t launch_composite_bwd(const ViewBatch& vb, int tw, int th, float eps, float lambda,
-                                 const float* dloss, int mode, int det, int instr, cudaStream_t st) {
-  if (tw == 16 && th == 16) return bwd_tw<16, 16>(vb, eps, lambda, dloss, mode, det, instr, st);
-  if (tw == 16 && th == 8) return bwd_tw<16, 8>(vb, eps, lambda, dloss, mode, det, instr, st);
-  if (tw == 8 && th == 8) return bwd_tw<8, 8>(vb, eps, lambda, dloss, mode, det, instr, st);
-  if (tw == 32 && th == 8) return bwd_tw<32, 8>(vb, eps, lambda, dloss, mode, det, instr, st);
+                                 const float* dloss, int mode, int det, int instr, int sorted,
+                                 cudaStream_t st) {
+  if (tw == 16 && th == 16) return bwd_tw<16, 16>(vb, eps, lambda, dloss, mode, det, instr, sorted, st);
+  if (tw == 16 && th == 8) return bwd_tw<16, 8>(vb, eps, lambda, dloss, mode, det, instr, sorted, st);
+  if (tw == 8 && th == 8) return bwd_tw<8, 8>(vb, eps, lambda, dloss, mode, det, instr, sorted, st);
+  if (tw == 32 && th == 8) return bwd_tw<32, 8>(vb, eps, lambda, dloss, mode, det, instr, sorted, st);
   return cudaErrorInvalidValue;
 }
 

@@ -147,15 +147,18 @@ def test_projection_matches_oracle():
 
 
 # --------------------------------------------------------------- binning
+@pytest.mark.parametrize("det", [True, False])
 @pytest.mark.parametrize("tile", [(16, 16), (16, 8), (8, 8), (32, 8)])
-def test_binning_bit_exact(tile):
-    """Identical FP32 records in, identical sorted (tile, depth, index) lists out."""
+def test_binning_bit_exact(tile, det):
+    """Identical FP32 records in, identical sorted (tile, depth, index) lists out
+    (deterministic mode); the sort-free default gives every tile the same
+    entries in emission order."""
     w = workload("small", M=3000, width=150, height=100)  # ragged tiles
     f = w.frames[0]
     rec_o, _ = oracle.project(w.gaussians.astype(np.float64), f.cam)
     r32 = oracle.records_f32(rec_o)
     keys_o, vals_o, ranges_o = oracle.bin_records(r32, f.cam.width, f.cam.height, *tile)
-    r = _renderer(w, [f.cam], stages=gps.STAGE_BIN, tile=tile)
+    r = _renderer(w, [f.cam], stages=gps.STAGE_BIN, tile=tile, deterministic=det)
     r.region(0, "records", torch.float32, r.M * 16).copy_(torch.from_numpy(r32.reshape(-1)).cuda())
     g = gps.Gaussians.from_numpy(w.gaussians)
     Ct, Dt = np.zeros((3, f.cam.height, f.cam.width), np.float32), np.zeros((f.cam.height, f.cam.width), np.float32)
@@ -167,6 +170,8 @@ def test_binning_bit_exact(tile):
     total = 0
     for t in range(nt):
         seg = allkeys[ranges[t, 0]:ranges[t, 1]]
+        if not det:
+            seg = np.sort(seg)  # (depth bits, index) order, as the oracle's values
         lo, hi = int(ranges_o[t, 0]), int(ranges_o[t, 1])
         total += len(seg)
         # device key = bits(d) << 32 | index; oracle key = tile << 32 | bits(d), value = index
@@ -436,10 +441,11 @@ def test_adam_device_step_counter_matches_host_steps():
 
 # ------------------------------------------------------------- autotuner
 def test_autotuner_picks_a_shape_that_renders_identically():
-    """gps_autotune_tiles times every tile shape on the caller's data; the
-    forward images do not depend on the tile shape (each pixel counts the same
-    Gaussians in the same depth order), and the gradients only through the
-    order of the per-tile partial sums."""
+    """gps_autotune_tiles times every tile shape on the caller's data; in
+    deterministic mode (depth-sorted lists) the forward images do not depend
+    on the tile shape (each pixel counts the same Gaussians in the same depth
+    order), and the gradients only through the order of the per-tile partial
+    sums."""
     w = workload("small")
     f = w.frames[0]
     H, W = f.cam.height, f.cam.width
@@ -447,7 +453,7 @@ def test_autotuner_picks_a_shape_that_renders_identically():
     g = gps.Gaussians.from_numpy(w.gaussians)
     res = {}
     for tune in (False, True):
-        s = gps.settings(eps_depth=w.eps_depth, tile=(16, 16))
+        s = gps.settings(eps_depth=w.eps_depth, tile=(16, 16), deterministic=True)
         r = gps.Renderer(g.M, [f.cam], s)
         v = gps.View(f.cam, cuda(Ct), cuda(Dt), cuda(f.rgb), cuda(f.depth),
                      out_rgb=torch.empty(3, H, W, device="cuda"))
