@@ -57,6 +57,9 @@ def parse():
                     help=f"frames of the sequence (room: {N_FRAMES}, large: {N_FRAMES_LARGE})")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="storage type of the colour images C_t, C_k, C*")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="bitwise reproducible rendering: depth-sorted tile lists and the "
+                         "fixed-order gradient reduction (the OIT default is sort-free)")
     ap.add_argument("--track", action="store_true",
                     help="sequence workload: track frames 1.. by ICP (Sec. 3.2) instead of "
                          "using the given poses")
@@ -218,6 +221,7 @@ def workload_config(args, w):
                         f"{ITERS_PER_FRAME} iterations/frame",
             "blend": args.mode, "tile": args.tile, "colour_storage": args.precision,
             "schedule": args.schedule, "sh_degree": args.sh_degree,
+            "deterministic": bool(getattr(args, "deterministic", False)),
             "form": "CUDA graph per frame", "l2": "256 MB buffer written between steps (untimed)"}
 
 
@@ -227,7 +231,8 @@ PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 class GpuPipeline:
     """Device-resident state of one replica and the per-frame step."""
 
-    def __init__(self, w, tile, mode, device, precision="fp32", schedule="tiles"):
+    def __init__(self, w, tile, mode, device, precision="fp32", schedule="tiles",
+                 deterministic=False):
         import torch
         import paper_2509_11574_b300 as gps
         self.gps, self.torch = gps, torch
@@ -251,7 +256,8 @@ class GpuPipeline:
         self.s = gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, near=w.near,
                               blend_mode=gps.BLEND_ALPHA if mode == "alpha" else gps.BLEND_OIT,
                               tile=tile, pair_capacity=64 * w.gaussians.M, precision=prec,
-                              schedule=1 if schedule == "per-gaussian" else 0)
+                              schedule=1 if schedule == "per-gaussian" else 0,
+                              deterministic=deterministic)
         self.r = gps.Renderer(w.gaussians.M, self.cams[:1], self.s, device)
         self.Ct = torch.zeros(3, H, W, device=device, dtype=self.cdt)
         self.Dt = torch.zeros(H, W, device=device)
@@ -393,7 +399,7 @@ def run_ours(args, rank, world, local):
     t0 = time.time()
     w = make_workload(rank, args)
     gen_s = time.time() - t0
-    pipe = GpuPipeline(w, tile, args.mode, dev, args.precision, args.schedule)
+    pipe = GpuPipeline(w, tile, args.mode, dev, args.precision, args.schedule, args.deterministic)
     tuned = None
     if args.tile == "auto":
         tuned = pipe.autotune()
