@@ -94,6 +94,28 @@ def dist_env():
     return rank, world, local
 
 
+def replica_seeds(rank):
+    """Scene and camera-path seeds of rank `rank`'s independent replica."""
+    return 2 + 1000 * rank, 3 + 1000 * rank
+
+
+def max_over_ranks(values, world, device):
+    """Element-wise maximum of per-rank values (step times) over all ranks of
+    the default process group; the values themselves for one rank."""
+    if world <= 1:
+        return [float(x) for x in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x) for x in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(units_per_rank, max_seconds, world):
+    """Units all ranks processed per second of the slowest rank's time."""
+    return units_per_rank * world / max_seconds
+
+
 # ---------------------------------------------------------------- clocks
 class _NvmlC:
     """The few read-only NVML queries the sampler needs, through the driver's
@@ -202,11 +224,11 @@ def make_workload(rank: int, args):
     from datagen.scenes import with_sh
     if args.workload == "large":
         w = workloads.room(n_frames=args.frames or N_FRAMES_LARGE, M=M_GAUSS_LARGE, width=1280,
-                           height=720, size=5.12, n_vox=512, seed_scene=2 + 1000 * rank,
-                           seed_path=3 + 1000 * rank)
+                           height=720, size=5.12, n_vox=512, seed_scene=replica_seeds(rank)[0],
+                           seed_path=replica_seeds(rank)[1])
     else:
-        w = workloads.room(n_frames=args.frames or N_FRAMES, M=M_GAUSS, seed_scene=2 + 1000 * rank,
-                           seed_path=3 + 1000 * rank)
+        w = workloads.room(n_frames=args.frames or N_FRAMES, M=M_GAUSS,
+                           seed_scene=replica_seeds(rank)[0], seed_path=replica_seeds(rank)[1])
     if args.sh_degree:
         w.gaussians = with_sh(w.gaussians, args.sh_degree, seed=6 + rank, scale=0.05)
     return w
@@ -452,11 +474,7 @@ def run_ours(args, rank, world, local):
     wall = time.time() - wall0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks([sum(step_ms) / 1e3], world, dev)[0]
     status = pipe.r.status()
     losses = pipe.loss.cpu().numpy().tolist()
 
@@ -509,7 +527,8 @@ def run_ours(args, rank, world, local):
             if i >= Wu:
                 e2e_ms.append(e0.elapsed_time(e1))
         h2d = sum(t.numel() * t.element_size() for t in host[0])
-        e2e = {"value": ITERS_PER_FRAME * K / (sum(e2e_ms) / 1e3) * world, "unit": "iterations/s",
+        e2e_s = max_over_ranks([sum(e2e_ms) / 1e3], world, dev)[0]
+        e2e = {"value": whole_job_rate(ITERS_PER_FRAME * K, e2e_s, world), "unit": "iterations/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": ITERS_PER_FRAME * 4}
 
     if rank != 0:
@@ -523,7 +542,7 @@ def run_ours(args, rank, world, local):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    value = ITERS_PER_FRAME * K / total_s * world
+    value = whole_job_rate(ITERS_PER_FRAME * K, total_s, world)
     # ---- roofline of the dominant kernel
     dom = max(stage_ms, key=stage_ms.get)
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
@@ -788,10 +807,7 @@ def run_multiview(args, rank, world, local):
     clk = clocks.stop()
     res["sequential_graph_ms"] = timed(gs)
     st_b, st_s = rb.status(), max((r.status() for r in rs), key=abs)
-    if world > 1:
-        t = torch.tensor([res["batched_graph_ms"]], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        res["batched_graph_ms"] = float(t.item())
+    res["batched_graph_ms"] = max_over_ranks([res["batched_graph_ms"]], world, dev)[0]
     if rank != 0:
         return
     ms = res["batched_graph_ms"]
@@ -881,8 +897,8 @@ def run_sequence(args, rank, world, local):
         dist.barrier()
     gps.lib()
     tile = (16, 8) if args.tile == "auto" else tuple(int(x) for x in args.tile.split("x"))
-    w = workloads.room(n_frames=args.frames or N_FRAMES, M=16, seed_scene=2 + 1000 * rank,
-                       seed_path=3 + 1000 * rank)
+    w = workloads.room(n_frames=args.frames or N_FRAMES, M=16, seed_scene=replica_seeds(rank)[0],
+                       seed_path=replica_seeds(rank)[1])
     prec = PRECISIONS[args.precision]
     s = gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, near=w.near, tile=tile,
                      precision=prec)
@@ -951,10 +967,7 @@ def run_sequence(args, rank, world, local):
                     "icp_iterations": [int(tr.s.iters[l]) for l in range(tr.s.levels)],
                     "icp_launches": 2 * tr.s.levels + 2 + 1 + sum(tr.s.iters[l] for l in range(tr.s.levels))}
     ms_e2e, _, _ = one_pass(e2e=True)
-    if world > 1:
-        t = torch.tensor([ms, ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = (float(x) for x in t.tolist())
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], world, dev)
     if rank != 0:
         return
     n = len(w.frames)
@@ -1018,8 +1031,8 @@ def run_fusion(args, rank, world, local):
     if world > 1:
         dist.barrier()
     gps.lib()
-    w = workloads.room(n_frames=args.frames or N_FRAMES, M=16, seed_scene=2 + 1000 * rank,
-                       seed_path=3 + 1000 * rank)
+    w = workloads.room(n_frames=args.frames or N_FRAMES, M=16, seed_scene=replica_seeds(rank)[0],
+                       seed_path=replica_seeds(rank)[1])
     frames = [(torch.from_numpy(f.depth).to(dev), torch.from_numpy(f.rgb).to(dev), f.cam)
               for f in w.frames]
     H, W = w.frames[0].cam.height, w.frames[0].cam.width
@@ -1063,11 +1076,7 @@ def run_fusion(args, rank, world, local):
         res[name] = entry
         del vol
         torch.cuda.empty_cache()
-    ms = res["hash_0.5cm"]["frame_ms"]
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks([res["hash_0.5cm"]["frame_ms"]], world, dev)[0]
     if rank != 0:
         return
     n = len(frames)
@@ -1111,8 +1120,8 @@ def run_track(args, rank, world, local):
     if world > 1:
         dist.barrier()
     gps.lib()
-    w = workloads.room(n_frames=args.frames or N_FRAMES, M=16, seed_scene=2 + 1000 * rank,
-                       seed_path=3 + 1000 * rank)
+    w = workloads.room(n_frames=args.frames or N_FRAMES, M=16, seed_scene=replica_seeds(rank)[0],
+                       seed_path=replica_seeds(rank)[1])
     vol = gps.Tsdf(w.tsdf, dev)
     depths = [torch.from_numpy(f.depth).to(dev) for f in w.frames]
     for f, d in zip(w.frames, depths):
@@ -1136,11 +1145,7 @@ def run_track(args, rank, world, local):
         ev.append((e0, e1))
         est = tr.result()                 # synchronises
         err.append(float(np.linalg.norm(est.t.numpy() - np.asarray(w.frames[k].cam.t))))
-    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks([sum(a.elapsed_time(b) for a, b in ev) / len(ev)], world, dev)[0]
     if rank != 0:
         return
     n_it = sum(tr.s.iters[l] for l in range(tr.s.levels))
