@@ -55,7 +55,10 @@ extern "C" {
 #define GPS_ERR_INVALID_ARG (-1)         /* bad pointer, size or setting       */
 #define GPS_ERR_WORKSPACE_TOO_SMALL (-2) /* ws_bytes < gps_workspace_size()     */
 #define GPS_ERR_CAPACITY (-3)            /* more (super-tile, Gaussian) entries
-                                            than pair_capacity; found on the
+                                            than pair_capacity (with tile bins:
+                                            (tile, Gaussian) entries than
+                                            tiles per super-tile times
+                                            pair_capacity); found on the
                                             device */
 #define GPS_ERR_CUDA (-4)                /* a CUDA launch / copy failed         */
 #define GPS_ERR_TIMEOUT (-5)             /* a bounded device wait gave up       */
@@ -177,7 +180,9 @@ typedef struct GpsRenderSettings {
   int32_t instrument;    /* 1: count Gaussian-pixel evaluations (slower; for
                             measurement runs) into the view scalars           */
   int32_t schedule;      /* GPS_SCHEDULE_*                                     */
-  int64_t pair_capacity; /* (super-tile, Gaussian) entries per view; 0 = 16 * M */
+  int64_t pair_capacity; /* (super-tile, Gaussian) entries per view; 0 = 16 * M;
+                            tile bins hold tiles per super-tile times as many
+                            (tile, Gaussian) entries                          */
 } GpsRenderSettings;
 
 /* Adam hyper-parameters; lr per group in the order means, log_scales, quats,
@@ -194,29 +199,37 @@ typedef struct GpsAdamHyper {
  *   mx, my, d, sigma, conic_a, conic_b, conic_c, qmax, r, g, b, ext_x, ext_y, 0, 0, 0
  * with q = a dx^2 + 2 b dx dy + c dy^2, support {q <= qmax}, qmax =
  * 2 ln(255 sigma), and a conservative half-extent ext (ext_x < 0: culled).
- * Binning first buckets Gaussians into super-tiles of super_px x super_px
- * pixels, sorts each segment, then splits it into its tiles (when a tile is a
- * whole super-tile its list is the segment itself: tile_ranges ==
- * super_ranges and pair_keys == super_keys).  Tile lists: keys u64 =
- * bits(d) << 32 | index, sorted ascending; tile t's list is pair_keys[
- * tile_ranges[t][0] .. tile_ranges[t][1]) (lists are not contiguous).
+ * Binning buckets Gaussians into bins with a per-bin histogram, a scan and an
+ * emission.  Where the lists are depth-sorted (blend ALPHA or deterministic)
+ * the bins are super-tiles of super_px x super_px pixels: each segment is
+ * sorted, then split into its tiles (when a tile is a whole super-tile its
+ * list is the segment itself: tile_ranges == super_ranges and pair_keys ==
+ * super_keys).  Otherwise (tile_bins = 1, super_px = 0) the bins are the tiles
+ * themselves (super_x = tiles_x, super_y = tiles_y) and the emission writes
+ * the tile lists directly: tile_ranges == super_ranges, pair_keys ==
+ * super_keys == super_scratch; this needs tiles_x * tiles_y <= 16384 in every
+ * view, else the super-tile path is taken.  Tile lists: keys u64 =
+ * bits(d) << 32 | index, sorted ascending where depth-sorted, else in
+ * emission order; tile t's list is pair_keys[tile_ranges[t][0] ..
+ * tile_ranges[t][1]) (lists are not contiguous).
  * grad2d holds 12 floats per Gaussian: d/d(mx, my, conic_a, conic_b, conic_c,
  * sigma, r, g, b, d), 0, 0. */
 typedef struct GpsWorkspaceLayout {
   size_t total_bytes;
   size_t status;        /* int32 status word (shared by all views)            */
   size_t records;       /* float [M][16]                                      */
-  size_t super_counts;  /* uint32 [super_tiles]                               */
-  size_t block_base;    /* uint32 [ceil(M/256)][super_tiles]                  */
-  size_t super_ranges;  /* uint32 [super_tiles][2]                            */
-  size_t super_keys;    /* uint64 [pair_capacity] super-tile segments         */
+  size_t super_counts;  /* uint32 [bins]                                      */
+  size_t block_base;    /* uint32 [ceil(M/256)][bins]                         */
+  size_t super_ranges;  /* uint32 [bins][2]                                   */
+  size_t super_keys;    /* uint64 [pair_capacity] super-tile segments (tile
+                           bins: the tile lists)                              */
   size_t super_scratch; /* uint64 [pair_capacity] (sort scratch)              */
   size_t tile_ranges;   /* uint32 [tiles][2]                                  */
   size_t pair_keys;     /* uint64 [tiles per super-tile * pair_capacity]      */
   size_t pix_state;     /* float [H*W][8] saved per-pixel forward state       */
   size_t tile_partials; /* float [tiles][4] loss partial sums                 */
   size_t view_scalars;  /* float [8]: loss, colour sum, depth sum, N_valid,
-                           super-tile entries; then uint64 [4] evaluation
+                           (bin, Gaussian) entries; then uint64 [4] evaluation
                            counters: forward tested, forward counted, backward
                            tested, backward counted (instrument = 1)          */
   size_t grad2d;        /* float [M][12]                                      */
@@ -227,8 +240,9 @@ typedef struct GpsWorkspaceLayout {
                            dL/dC* / N, dL/dD* / N, sum dL/d(C*, D*) (C*, D*) / N,
                            D_t + eps (or -inf if the pixel has no gradient)   */
   int32_t tiles_x, tiles_y, tile_w, tile_h, super_x, super_y;
-  int32_t super_px;     /* super-tile edge in pixels (16, or 32 for 32-px-wide tiles) */
-  int32_t reserved;
+  int32_t super_px;     /* super-tile edge in pixels (16, or 32 for 32-px-wide
+                           tiles); 0 with tile bins                           */
+  int32_t tile_bins;    /* 1: the bins are the tiles (unsorted lists)         */
   int64_t pair_capacity;
 } GpsWorkspaceLayout;
 

@@ -1,7 +1,8 @@
-// Tile binning: per-tile Gaussian lists sorted by (depth, index).
+// Tile binning: per-tile Gaussian lists, sorted by (depth, index) where an
+// order is wanted, in emission order otherwise.
 //
-// The sort key is (tile, bits(depth), index).  Its most significant part is
-// placed in two levels:
+// Depth-sorted lists: the sort key is (tile, bits(depth), index).  Its most
+// significant part is placed in two levels:
 //   1. super-tiles (16 x 16 px, or 32 x 32 px for 32-px-wide tiles): every
 //      block of the projection histograms its
 //      Gaussians' super-tile rectangles in shared memory and reserves one range
@@ -16,6 +17,10 @@
 //      is a whole super-tile reads the sorted segment itself.
 // The result equals a stable sort of (tile << 32 | bits(d)) keys with ties in
 // index order, independent of the order the atomics ran in.
+//
+// Unsorted lists: the same histogram / scan / emission with the tiles as the
+// bins writes each tile's list directly (same entries as the split would
+// give, in the order the atomics ran); no second pass.
 #include <cuda_runtime.h>
 
 #include "gps_common.cuh"
@@ -24,15 +29,16 @@ namespace gps {
 
 constexpr int kScanThreads = 1024;
 
-// -------------------------------------------------- super-tile histograms
-__device__ __forceinline__ bool super_rect(float mx, float my, float ex, float ey, int W, int H,
-                                           int sh, int& sx0, int& sx1, int& sy0, int& sy1) {
+// -------------------------------------------------------- bin histograms
+// The bins a record's pixel rectangle meets: [sx0, sx1] x [sy0, sy1].
+__device__ __forceinline__ bool bin_rect(float mx, float my, float ex, float ey, const ViewDev& v,
+                                         int& sx0, int& sx1, int& sy0, int& sy1) {
   int x0, x1, y0, y1;
-  if (!record_rect(mx, my, ex, ey, W, H, x0, x1, y0, y1)) return false;
-  sx0 = x0 >> sh;
-  sx1 = x1 >> sh;
-  sy0 = y0 >> sh;
-  sy1 = y1 >> sh;
+  if (!record_rect(mx, my, ex, ey, v.cam.W, v.cam.H, x0, x1, y0, y1)) return false;
+  sx0 = x0 >> v.bin_sx;
+  sx1 = x1 >> v.bin_sx;
+  sy0 = y0 >> v.bin_sy;
+  sy1 = y1 >> v.bin_sy;
   return true;
 }
 
@@ -50,16 +56,16 @@ __global__ void __launch_bounds__(256) bin_histogram_kernel(int M,
     const float4* rec = v.rec;
     const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
     int sx0, sx1, sy0, sy1;
-    if (super_rect(a.x, a.y, c.w, e.x, v.cam.W, v.cam.H, v.sup_shift, sx0, sx1, sy0, sy1))
+    if (bin_rect(a.x, a.y, c.w, e.x, v, sx0, sx1, sy0, sy1))
       for (int sy = sy0; sy <= sy1; ++sy)
         for (int sx = sx0; sx <= sx1; ++sx) atomicAdd(s_hist + sy * v.sup_x + sx, 1u);
   }
   reserve_block_ranges(s_hist, nsup, v.sup_count, v.block_base);
 }
 
-// Exclusive scan of the super-tile counts -> [start, end) (clipped to the
-// capacity; overflow raises GPS_ERR_CAPACITY).  Resets the counts for the next
-// call.  scalars[4] = number of (super-tile, Gaussian) entries.  One block
+// Exclusive scan of the bin counts -> [start, end) (clipped to the capacity;
+// overflow raises GPS_ERR_CAPACITY).  Resets the counts for the next call.
+// scalars[4] = number of (bin, Gaussian) entries.  One block
 // per view of the batch.
 __global__ void __launch_bounds__(kScanThreads) scan_super_kernel(const __grid_constant__ ViewBatch vb,
                                                                   int* status) {
@@ -109,31 +115,79 @@ __global__ void __launch_bounds__(kScanThreads) scan_super_kernel(const __grid_c
 }
 
 // Emission into the reserved ranges; same block partition as the histogram.
+// The block's next write position in every bin (range start + the block's
+// base) is staged in shared memory first, so an entry costs one shared atomic
+// and one store.  A warp's entries are dealt to its lanes round-robin (an
+// entry finds its Gaussian by a binary search over the warp's prefix sums of
+// entry counts), so a Gaussian with many bins does not hold up its warp.
+// Position pos of a bin is stored when pos < cap: the same test as against
+// the bin's clipped range [min(start, cap), min(end, cap)).
 __global__ void __launch_bounds__(256) emit_super_kernel(int M, const __grid_constant__ ViewBatch vb) {
-  extern __shared__ uint32_t s_rank[];
+  extern __shared__ uint32_t s_pos[];
   const ViewDev& v = vb.v[blockIdx.y];
   const float4* __restrict__ rec = v.rec;
-  const int W = v.cam.W, H = v.cam.H, sh = v.sup_shift, sup_x = v.sup_x;
+  const int sup_x = v.sup_x;
   const int nsup = v.sup_x * v.sup_y;
   const uint2* __restrict__ sup_ranges = v.sup_ranges;
-  const uint32_t* __restrict__ block_base = v.block_base;
+  const uint32_t* __restrict__ bb = v.block_base + (size_t)blockIdx.x * nsup;
   unsigned long long* __restrict__ keys = v.sup_keys;
-  for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_rank[s] = 0;
-  __syncthreads();
+  const uint32_t cap = (uint32_t)min(v.cap, 0xFFFFFFFFLL);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
-  int sx0, sx1, sy0, sy1;
-  if (!super_rect(a.x, a.y, c.w, e.x, W, H, sh, sx0, sx1, sy0, sy1)) return;
-  const unsigned long long key = key_of(a.z, (uint32_t)i);
-  const uint32_t* bb = block_base + (size_t)blockIdx.x * nsup;
-  for (int sy = sy0; sy <= sy1; ++sy)
-    for (int sx = sx0; sx <= sx1; ++sx) {
-      const int s = sy * sup_x + sx;
-      const uint2 r = sup_ranges[s];
-      const uint32_t pos = r.x + bb[s] + atomicAdd(s_rank + s, 1u);
-      if (pos < r.y) keys[pos] = key;
+  int sx0 = 0, sx1 = -1, sy0 = 0, sy1 = -1;
+  unsigned long long key = 0;
+  if (i < M) {
+    const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
+    if (bin_rect(a.x, a.y, c.w, e.x, v, sx0, sx1, sy0, sy1)) key = key_of(a.z, (uint32_t)i);
+    else sx1 = -1;
+  }
+  constexpr int U = 8;  // loads in flight per thread
+  for (int s0 = threadIdx.x; s0 < nsup; s0 += U * blockDim.x) {
+    uint32_t p[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u * blockDim.x;
+      p[u] = s < nsup ? sup_ranges[s].x + bb[s] : 0u;
     }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (s0 + u * (int)blockDim.x < nsup) s_pos[s0 + u * blockDim.x] = p[u];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nx = sx1 - sx0 + 1;
+  const int cnt = nx > 0 ? nx * (sy1 - sy0 + 1) : 0;
+  // row of entry e of the rectangle: floor((e + 1/2) / nx) in float is exact,
+  // as (e + 1/2) / nx lies at least 1/(2 nx) from an integer while the two
+  // roundings move it by under (e / nx + 1) 2^-23 (e, nx <= 16384)
+  const float inv_nx = nx > 0 ? 1.0f / (float)nx : 0.f;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  for (int k0 = 0; k0 < total; k0 += 32) {
+    const int k = k0 + lane;
+    int j = 0;  // first lane whose inclusive count exceeds k
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int c = __shfl_sync(0xffffffffu, incl, j + step - 1);
+      if (c <= k) j += step;
+    }
+    const int jc = __shfl_sync(0xffffffffu, cnt, j), ji = __shfl_sync(0xffffffffu, incl, j);
+    const int jnx = __shfl_sync(0xffffffffu, nx, j);
+    const float jinv = __shfl_sync(0xffffffffu, inv_nx, j);
+    const int jx0 = __shfl_sync(0xffffffffu, sx0, j), jy0 = __shfl_sync(0xffffffffu, sy0, j);
+    const unsigned long long jkey = __shfl_sync(0xffffffffu, key, j);
+    if (k < total) {
+      const int e = k - (ji - jc);
+      const int row = (int)(((float)e + 0.5f) * jinv);
+      const int s = (jy0 + row) * sup_x + jx0 + (e - row * jnx);
+      const uint32_t pos = atomicAdd(s_pos + s, 1u);
+      if (pos < cap) keys[pos] = jkey;
+    }
+  }
 }
 
 // ------------------------------------------------------ per-super-tile sort
@@ -270,7 +324,7 @@ __global__ void __launch_bounds__(T) sort_split_kernel(const __grid_constant__ V
   const int slot = batch_slot(vb.sup_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
   unsigned long long* __restrict__ sup_keys = v.sup_keys;
-  const int sh = v.sup_shift, sp = 1 << sh;
+  const int sp = 1 << v.bin_sx;  // square super-tiles
   const int LX = sp / TW, LY = sp / TH, L = LX * LY;  // L <= 4
   const int s = blockIdx.x - vb.sup_start[slot];
   const int sx = s % v.sup_x, sy = s / v.sup_x;

@@ -78,7 +78,24 @@ long long pair_cap(const GpsRenderSettings* s, int M) {
   return s->pair_capacity > 0 ? s->pair_capacity : 16LL * (M > 0 ? M : 1);
 }
 
-constexpr int kSuperMax = 16384;  // super-tile histogram lives in shared memory
+constexpr int kSuperMax = 16384;  // the bin histogram lives in shared memory
+
+int depth_sorted(const GpsRenderSettings& s);
+
+// Bins of the binning pass.  Lists that stay unsorted are binned straight
+// into tiles (one pass: histogram, scan, emission) when every view's tile grid
+// fits the shared-memory histogram; otherwise Gaussians go into square
+// super-tiles, whose segments are sorted (where an order is wanted) and split
+// into their tiles.
+bool tile_bins(const GpsView* views, int32_t n_views, const GpsRenderSettings* s, const TileCfg& tc) {
+  if (depth_sorted(*s)) return false;
+  for (int v = 0; v < n_views; ++v) {
+    const long long tx = (views[v].K.width + tc.tw - 1) / tc.tw;
+    const long long ty = (views[v].K.height + tc.th - 1) / tc.th;
+    if (tx * ty > kSuperMax) return false;
+  }
+  return true;
+}
 
 // Workspace: [status 256 B] then per view, in order, its regions.
 int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRenderSettings* s,
@@ -92,29 +109,42 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
   if (cap <= 0 || cap * per_super > 0xFFFFFFF0LL)
     return fail(GPS_ERR_INVALID_ARG, "pair_capacity out of range");
   const size_t nblocks = ((size_t)M + 255) / 256;
+  for (int v = 0; v < n_views; ++v)
+    if (views[v].K.width <= 0 || views[v].K.height <= 0)
+      return fail(GPS_ERR_INVALID_ARG, "view %d has size %dx%d", v, views[v].K.width,
+                  views[v].K.height);
+  const bool by_tile = tile_bins(views, n_views, s, tc);
   size_t off = 256;
   for (int v = 0; v < n_views; ++v) {
     const int W = views[v].K.width, H = views[v].K.height;
-    if (W <= 0 || H <= 0) return fail(GPS_ERR_INVALID_ARG, "view %d has size %dx%d", v, W, H);
     const int tx = (W + tc.tw - 1) / tc.tw, ty = (H + tc.th - 1) / tc.th;
-    const int sx = (W + sp - 1) / sp, sy = (H + sp - 1) / sp;
+    const int sx = by_tile ? tx : (W + sp - 1) / sp, sy = by_tile ? ty : (H + sp - 1) / sp;
     if ((long long)sx * sy > kSuperMax)
       return fail(GPS_ERR_INVALID_ARG, "view %d: image too large (%d super-tiles)", v, sx * sy);
-    const size_t ntiles = (size_t)tx * ty, npx = (size_t)W * H, nsup = (size_t)sx * sy;
+    const size_t ntiles = (size_t)tx * ty, npx = (size_t)W * H, nbins = (size_t)sx * sy;
     GpsWorkspaceLayout L{};
     L.status = 0;
     L.records = off; off = align256(off + (size_t)M * 64);
-    L.super_counts = off; off = align256(off + nsup * 4);
-    L.block_base = off; off = align256(off + nblocks * nsup * 4);
-    L.super_ranges = off; off = align256(off + nsup * 8);
-    L.super_keys = off; off = align256(off + (size_t)cap * 8);
-    L.super_scratch = off; off = align256(off + (size_t)cap * 8);
-    // with one tile per super-tile the tile lists are the sorted segments
-    // themselves: tile ranges and pair keys alias the super-tile regions
-    if (per_super == 1) {
+    L.super_counts = off; off = align256(off + nbins * 4);
+    L.block_base = off; off = align256(off + nblocks * nbins * 4);
+    L.super_ranges = off; off = align256(off + nbins * 8);
+    if (by_tile) {
+      // the emission writes the tile lists themselves (room for per_super *
+      // cap entries, as the split's output); no segments, no sort scratch
+      L.super_keys = off; off = align256(off + (size_t)cap * per_super * 8);
+      L.super_scratch = L.super_keys;
       L.tile_ranges = L.super_ranges;
       L.pair_keys = L.super_keys;
     } else {
+      L.super_keys = off; off = align256(off + (size_t)cap * 8);
+      L.super_scratch = off; off = align256(off + (size_t)cap * 8);
+    }
+    // with one tile per super-tile the tile lists are the sorted segments
+    // themselves: tile ranges and pair keys alias the super-tile regions
+    if (!by_tile && per_super == 1) {
+      L.tile_ranges = L.super_ranges;
+      L.pair_keys = L.super_keys;
+    } else if (!by_tile) {
       L.tile_ranges = off; off = align256(off + ntiles * 8);
       L.pair_keys = off; off = align256(off + (size_t)cap * per_super * 8);
     }
@@ -132,7 +162,8 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     L.tile_h = tc.th;
     L.super_x = sx;
     L.super_y = sy;
-    L.super_px = sp;
+    L.super_px = by_tile ? 0 : sp;
+    L.tile_bins = by_tile ? 1 : 0;
     L.pair_capacity = cap;
     if (v == want && out) *out = L;
   }
@@ -212,8 +243,15 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int 
   v.th = L.tile_h;
   v.sup_x = L.super_x;
   v.sup_y = L.super_y;
-  v.sup_shift = L.super_px == 32 ? 5 : 4;
-  v.cap = L.pair_capacity;
+  if (L.tile_bins) {
+    v.bin_sx = L.tile_w == 32 ? 5 : L.tile_w == 16 ? 4 : 3;
+    v.bin_sy = L.tile_h == 16 ? 4 : 3;
+    v.cap = L.pair_capacity * (((1 << super_shift_for(L.tile_w)) / L.tile_w) *
+                               ((1 << super_shift_for(L.tile_w)) / L.tile_h));
+  } else {
+    v.bin_sx = v.bin_sy = L.super_px == 32 ? 5 : 4;
+    v.cap = L.pair_capacity;
+  }
   return v;
 }
 
@@ -373,9 +411,12 @@ int32_t render_forward(const GpsGaussians* g, const GpsView* views, int32_t n_vi
     if (e == cudaSuccess && (stages & GPS_STAGE_BIN)) {
       e = launch_scan_super(vb, status, st);
       if (e == cudaSuccess && g->M > 0) e = launch_emit_super(g->M, vb, max_nsup, st);
-      // split each super-tile's segment into its tiles' lists, sorted by depth
-      // where the settings ask for an order (see depth_sorted)
-      if (e == cudaSuccess) e = launch_sort_split(vb, v0.tw, v0.th, depth_sorted(*s), st);
+      // super-tile bins: split each segment into its tiles' lists, sorted by
+      // depth where the settings ask for an order (see depth_sorted)
+      TileCfg tc;
+      tile_cfg(s, tc);
+      if (e == cudaSuccess && !tile_bins(views, n_views, s, tc))
+        e = launch_sort_split(vb, v0.tw, v0.th, depth_sorted(*s), st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_COMPOSITE)) {
       for (int j = 0; j < vb.n && e == cudaSuccess && s->instrument; ++j)

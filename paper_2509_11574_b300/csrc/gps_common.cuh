@@ -69,7 +69,9 @@ struct ViewDev {
   float4* pair_grads;     // [cap][3] float4
   float4* pix_g;          // [npx][2] per-Gaussian backward: (h), (sv, thr, -, -)
   int tiles_x, tiles_y, tw, th;
-  int sup_x, sup_y, sup_shift;
+  // bins of the binning pass (sup_x * sup_y of them, 2^bin_sx x 2^bin_sy
+  // pixels each): square super-tiles, or the tiles themselves
+  int sup_x, sup_y, bin_sx, bin_sy;
   int fused;  // backward: upstream gradients from the fused L1 loss (1) or g_rgb/g_depth (0)
   int prec;   // GPS_PREC_* storage type of the colour images Ct, Ctgt, out_rgb
   long long cap;
@@ -151,11 +153,21 @@ __device__ __forceinline__ void reserve_block_ranges(uint32_t* s_hist, int nsup,
                                                      uint32_t* __restrict__ sup_count,
                                                      uint32_t* __restrict__ block_base) {
   __syncthreads();
-  for (int s = threadIdx.x; s < nsup; s += blockDim.x) {
-    const uint32_t h = s_hist[s];
-    uint32_t base = 0;
-    if (h) base = atomicAdd(sup_count + s, h);
-    block_base[(size_t)blockIdx.x * nsup + s] = base;
+  // eight bins per thread in flight: the atomics' round trips overlap
+  constexpr int U = 8;
+  for (int s0 = threadIdx.x; s0 < nsup; s0 += U * blockDim.x) {
+    uint32_t base[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u * blockDim.x;
+      const uint32_t h = s < nsup ? s_hist[s] : 0u;
+      base[u] = h ? atomicAdd(sup_count + s, h) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u * blockDim.x;
+      if (s < nsup) block_base[(size_t)blockIdx.x * nsup + s] = base[u];
+    }
   }
 }
 

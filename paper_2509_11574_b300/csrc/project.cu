@@ -209,18 +209,18 @@ __device__ __forceinline__ void project_gaussian(const Params& P, int i, const C
   o.vis = isfinite(o.mx) && isfinite(o.my) && isfinite(o.ca) && isfinite(o.cb) && isfinite(o.cc);
 }
 
-// K3: records, plus the block's super-tile histogram and range reservation
-// (first half of the binning).  Block row blockIdx.y projects for view
-// blockIdx.y of the batch.  sup_count must be zero on entry.
-// Shared memory: the super-tile histogram (max_nsup words, rounded up to an
-// even count) and, with DEG > 0, the block's SH rows.
+// K3: records, plus the block's bin histogram and range reservation (first
+// half of the binning; bins are super-tiles or tiles).  Block row blockIdx.y
+// projects for view blockIdx.y of the batch.  sup_count must be zero on entry.
+// Shared memory: the bin histogram (max_nsup words, rounded up to an even
+// count) and, with DEG > 0, the block's SH rows.
 template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(Params P, int M, float near_, int hist_words,
                                                       const __grid_constant__ ViewBatch vb) {
   extern __shared__ uint32_t s_hist[];
   float* s_f = reinterpret_cast<float*>(s_hist + hist_words);
   const ViewDev& v = vb.v[blockIdx.y];
-  const int sh = v.sup_shift, sup_x = v.sup_x, nsup = v.sup_x * v.sup_y;
+  const int bsx = v.bin_sx, bsy = v.bin_sy, sup_x = v.sup_x, nsup = v.sup_x * v.sup_y;
   for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_hist[s] = 0;
   if constexpr (DEG > 0) {
     const long long base = (long long)blockIdx.x * blockDim.x;
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(256) project_kernel(Params P, int M, float nea
       r[3] = make_float4(o.ey, 0.f, 0.f, 0.f);
       int x0, x1, y0, y1;
       record_rect(o.mx, o.my, o.ex, o.ey, cam.W, cam.H, x0, x1, y0, y1);
-      for (int sy = y0 >> sh; sy <= (y1 >> sh); ++sy)
-        for (int sx = x0 >> sh; sx <= (x1 >> sh); ++sx)
+      for (int sy = y0 >> bsy; sy <= (y1 >> bsy); ++sy)
+        for (int sx = x0 >> bsx; sx <= (x1 >> bsx); ++sx)
           atomicAdd(s_hist + sy * sup_x + sx, 1u);
     }
   }

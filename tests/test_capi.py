@@ -72,7 +72,8 @@ class _Cam:
 
 
 def test_workspace_size_and_layout_host_only(L):
-    s = gps.settings()
+    # depth-sorted lists (deterministic): super-tile bins
+    s = gps.settings(deterministic=True)
     cams = [_Cam(160, 120), _Cam(77, 33)]
     n = gps.gps_workspace_size(2000, cams, s)
     assert n > 0 and n % 256 == 0
@@ -86,13 +87,26 @@ def test_workspace_size_and_layout_host_only(L):
         assert off % 256 == 0
     assert L0.pair_capacity == 16 * 2000
     assert (L0.super_px, L0.super_x, L0.super_y, L1.super_x, L1.super_y) == (16, 10, 8, 5, 3)
-    L8 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(16, 8)), 0)
+    assert L0.tile_bins == 0
+    L8 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(16, 8), deterministic=True), 0)
     assert L8.super_keys < L8.pair_keys and L8.super_ranges < L8.tile_ranges
     assert L8.tiles_y == 15
-    L32 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(32, 8)), 0)
+    L32 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(32, 8), blend_mode=gps.BLEND_ALPHA), 0)
     assert L32.super_px == 32 and (L32.super_x, L32.super_y) == (5, 4)
-    s2 = gps.settings(deterministic=True)
-    assert gps.gps_workspace_size(2000, cams, s2) > n
+    # unsorted lists (the default): the bins are the tiles, the emission writes
+    # the lists (room for tiles per super-tile x pair_capacity entries)
+    T8 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(16, 8)), 0)
+    assert T8.tile_bins == 1 and T8.super_px == 0
+    assert (T8.super_x, T8.super_y) == (T8.tiles_x, T8.tiles_y) == (10, 15)
+    assert T8.pair_keys == T8.super_keys == T8.super_scratch and T8.tile_ranges == T8.super_ranges
+    assert T8.pix_state - T8.pair_keys >= 2 * 16 * 2000 * 8
+    T32 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(32, 8)), 1)
+    assert T32.tile_bins == 1 and (T32.super_x, T32.super_y) == (3, 5)
+    # a tile grid too large for the shared-memory histogram: super-tile bins
+    big = gps.gps_workspace_layout(10, [_Cam(2048, 1040)], gps.settings(tile=(8, 8)), 0)
+    assert big.tile_bins == 0 and big.super_px == 16
+    n = gps.gps_workspace_size(2000, cams, gps.settings())
+    assert gps.gps_workspace_size(2000, cams, s) > n
     with pytest.raises(gps.GpsError) as e:
         gps.gps_workspace_size(2000, cams, gps.settings(tile=(12, 12)))
     assert e.value.code == gps.GPS_ERR_INVALID_ARG

@@ -84,7 +84,10 @@ def test_finite_differences_of_the_gpu_forward():
     """Central differences of L = <w_c, C*> + <w_d, D*> (images read back and
     summed in FP64) against RenderImages' gradient: every rgb entry of a few
     Gaussians (L is linear in rgb) and the opacity logits of Gaussians whose
-    +-h perturbation leaves the oracle's per-pixel counts unchanged."""
+    +-h perturbation leaves the oracle's per-pixel counts unchanged.  The
+    differenced forwards run with depth-sorted lists (deterministic mode), so
+    that both see one summation order and the difference holds no rounding
+    noise from the sort-free lists' varying order."""
     w = workload("small")
     f = w.frames[0]
     H, W = f.cam.height, f.cam.width
@@ -98,6 +101,7 @@ def test_finite_differences_of_the_gpu_forward():
     ((C * cuda(wc)).sum() + (D * cuda(wd)).sum()).backward()
     grad = {n: p.grad.cpu().numpy().astype(np.float64) for n, p in zip(NAMES, ps)}
 
+    r = gps.Renderer(w.gaussians.M, [f.cam], gps.settings(eps_depth=w.eps_depth, deterministic=True))
     base = gps.Gaussians.from_numpy(w.gaussians)
     view = gps.View(f.cam, cuda(Ct), cuda(Dt), out_rgb=torch.empty(3, H, W, device="cuda"),
                     out_depth=torch.empty(H, W, device="cuda"))
