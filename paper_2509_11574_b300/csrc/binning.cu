@@ -51,10 +51,12 @@ __global__ void __launch_bounds__(256) bin_histogram_kernel(int M,
   const int nsup = v.sup_x * v.sup_y;
   for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_hist[s] = 0;
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < M) {
+  const int chunks = bin_chunks(M);
+  for (int ch = 0; ch < chunks; ++ch) {
+    const long long i = ((long long)blockIdx.x * chunks + ch) * blockDim.x + threadIdx.x;
+    if (i >= M) break;
     const float4* rec = v.rec;
-    const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
+    const float4 a = rec[4 * i], c = rec[4 * i + 2], e = rec[4 * i + 3];
     int sx0, sx1, sy0, sy1;
     if (bin_rect(a.x, a.y, c.w, e.x, v, sx0, sx1, sy0, sy1))
       for (int sy = sy0; sy <= sy1; ++sy)
@@ -114,46 +116,23 @@ __global__ void __launch_bounds__(kScanThreads) scan_super_kernel(const __grid_c
   }
 }
 
-// Emission into the reserved ranges; same block partition as the histogram.
-// The block's next write position in every bin (range start + the block's
-// base) is staged in shared memory first, so an entry costs one shared atomic
-// and one store.  A warp's entries are dealt to its lanes round-robin (an
-// entry finds its Gaussian by a binary search over the warp's prefix sums of
-// entry counts), so a Gaussian with many bins does not hold up its warp.
-// Position pos of a bin is stored when pos < cap: the same test as against
-// the bin's clipped range [min(start, cap), min(end, cap)).
-__global__ void __launch_bounds__(256) emit_super_kernel(int M, const __grid_constant__ ViewBatch vb) {
-  extern __shared__ uint32_t s_pos[];
-  const ViewDev& v = vb.v[blockIdx.y];
+// Emission of Gaussian i (i < M) of a warp's 32: its entries go to the
+// positions staged in s_pos.  The warp's entries are dealt to its lanes
+// round-robin (an entry finds its Gaussian by a binary search over the warp's
+// prefix sums of entry counts), so a Gaussian with many bins does not hold up
+// its warp.  Position pos of a bin is stored when pos < cap: the same test as
+// against the bin's clipped range [min(start, cap), min(end, cap)).
+__device__ __forceinline__ void emit_warp(long long i, int M, const ViewDev& v, uint32_t* s_pos,
+                                          uint32_t cap) {
   const float4* __restrict__ rec = v.rec;
-  const int sup_x = v.sup_x;
-  const int nsup = v.sup_x * v.sup_y;
-  const uint2* __restrict__ sup_ranges = v.sup_ranges;
-  const uint32_t* __restrict__ bb = v.block_base + (size_t)blockIdx.x * nsup;
-  unsigned long long* __restrict__ keys = v.sup_keys;
-  const uint32_t cap = (uint32_t)min(v.cap, 0xFFFFFFFFLL);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   int sx0 = 0, sx1 = -1, sy0 = 0, sy1 = -1;
   unsigned long long key = 0;
   if (i < M) {
-    const float4 a = rec[4 * (size_t)i], c = rec[4 * (size_t)i + 2], e = rec[4 * (size_t)i + 3];
+    const float4 a = rec[4 * i], c = rec[4 * i + 2], e = rec[4 * i + 3];
     if (bin_rect(a.x, a.y, c.w, e.x, v, sx0, sx1, sy0, sy1)) key = key_of(a.z, (uint32_t)i);
     else sx1 = -1;
   }
-  constexpr int U = 8;  // loads in flight per thread
-  for (int s0 = threadIdx.x; s0 < nsup; s0 += U * blockDim.x) {
-    uint32_t p[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int s = s0 + u * blockDim.x;
-      p[u] = s < nsup ? sup_ranges[s].x + bb[s] : 0u;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (s0 + u * (int)blockDim.x < nsup) s_pos[s0 + u * blockDim.x] = p[u];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
   const int nx = sx1 - sx0 + 1;
   const int cnt = nx > 0 ? nx * (sy1 - sy0 + 1) : 0;
   // row of entry e of the rectangle: floor((e + 1/2) / nx) in float is exact,
@@ -183,11 +162,40 @@ __global__ void __launch_bounds__(256) emit_super_kernel(int M, const __grid_con
     if (k < total) {
       const int e = k - (ji - jc);
       const int row = (int)(((float)e + 0.5f) * jinv);
-      const int s = (jy0 + row) * sup_x + jx0 + (e - row * jnx);
+      const int s = (jy0 + row) * v.sup_x + jx0 + (e - row * jnx);
       const uint32_t pos = atomicAdd(s_pos + s, 1u);
-      if (pos < cap) keys[pos] = jkey;
+      if (pos < cap) v.sup_keys[pos] = jkey;
     }
   }
+}
+
+// Emission into the reserved ranges; same block partition (bin_chunks(M)
+// chunks of 256 Gaussians per block) as the histogram.  The block's next
+// write position in every bin (range start + the block's base) is staged in
+// shared memory first, so an entry costs one shared atomic and one store.
+__global__ void __launch_bounds__(256) emit_super_kernel(int M, const __grid_constant__ ViewBatch vb) {
+  extern __shared__ uint32_t s_pos[];
+  const ViewDev& v = vb.v[blockIdx.y];
+  const int nsup = v.sup_x * v.sup_y;
+  const uint2* __restrict__ sup_ranges = v.sup_ranges;
+  const uint32_t* __restrict__ bb = v.block_base + (size_t)blockIdx.x * nsup;
+  constexpr int U = 8;  // loads in flight per thread
+  for (int s0 = threadIdx.x; s0 < nsup; s0 += U * blockDim.x) {
+    uint32_t p[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u * blockDim.x;
+      p[u] = s < nsup ? sup_ranges[s].x + bb[s] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (s0 + u * (int)blockDim.x < nsup) s_pos[s0 + u * blockDim.x] = p[u];
+  }
+  __syncthreads();
+  const uint32_t cap = (uint32_t)min(v.cap, 0xFFFFFFFFLL);
+  const int chunks = bin_chunks(M);
+  for (int ch = 0; ch < chunks; ++ch)
+    emit_warp(((long long)blockIdx.x * chunks + ch) * blockDim.x + threadIdx.x, M, v, s_pos, cap);
 }
 
 // ------------------------------------------------------ per-super-tile sort
@@ -416,7 +424,7 @@ static cudaError_t allow_smem(K kernel, size_t smem) {
 cudaError_t launch_bin_histogram(int M, const ViewBatch& vb, int max_nsup, cudaStream_t st) {
   const size_t smem = (size_t)max_nsup * sizeof(uint32_t);
   if (cudaError_t e = allow_smem(bin_histogram_kernel, smem)) return e;
-  bin_histogram_kernel<<<dim3((M + 255) / 256, vb.n), 256, smem, st>>>(M, vb);
+  bin_histogram_kernel<<<dim3(bin_blocks(M), vb.n), 256, smem, st>>>(M, vb);
   return cudaGetLastError();
 }
 
@@ -428,7 +436,7 @@ cudaError_t launch_scan_super(const ViewBatch& vb, int* status, cudaStream_t st)
 cudaError_t launch_emit_super(int M, const ViewBatch& vb, int max_nsup, cudaStream_t st) {
   const size_t smem = (size_t)max_nsup * sizeof(uint32_t);
   if (cudaError_t e = allow_smem(emit_super_kernel, smem)) return e;
-  emit_super_kernel<<<dim3((M + 255) / 256, vb.n), 256, smem, st>>>(M, vb);
+  emit_super_kernel<<<dim3(bin_blocks(M), vb.n), 256, smem, st>>>(M, vb);
   return cudaGetLastError();
 }
 

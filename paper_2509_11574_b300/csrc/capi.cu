@@ -108,7 +108,7 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
   const int per_super = (sp / tc.tw) * (sp / tc.th);
   if (cap <= 0 || cap * per_super > 0xFFFFFFF0LL)
     return fail(GPS_ERR_INVALID_ARG, "pair_capacity out of range");
-  const size_t nblocks = ((size_t)M + 255) / 256;
+  const size_t nblocks = (size_t)bin_blocks(M);
   for (int v = 0; v < n_views; ++v)
     if (views[v].K.width <= 0 || views[v].K.height <= 0)
       return fail(GPS_ERR_INVALID_ARG, "view %d has size %dx%d", v, views[v].K.width,

@@ -55,7 +55,7 @@ struct ViewDev {
   // workspace regions
   float4* rec;           // [M][4] float4
   uint32_t* sup_count;   // [nsup]
-  uint32_t* block_base;  // [ceil(M/256)][nsup]
+  uint32_t* block_base;  // [bin_blocks(M)][nsup]
   uint2* sup_ranges;     // [nsup]
   unsigned long long* sup_keys;
   unsigned long long* sup_tmp;
@@ -143,6 +143,17 @@ __device__ __forceinline__ float depth_threshold(float Dt, float eps) {
 
 __device__ __forceinline__ unsigned long long key_of(float d, uint32_t idx) {
   return ((unsigned long long)__float_as_uint(d) << 32) | idx;
+}
+
+// Binning CTAs take bin_chunks(M) consecutive chunks of 256 Gaussians each,
+// and one range per (CTA, bin) is reserved.  Every CTA stages a word per bin,
+// so CTAs should be few, but enough to fill the 148 SMs: about 600 (four per
+// SM) once M passes 600 * 256, at most 8 chunks per CTA.
+__host__ __device__ constexpr int bin_chunks(int M) {
+  return M / (256 * 600) < 1 ? 1 : (M / (256 * 600) > 8 ? 8 : M / (256 * 600));
+}
+__host__ __device__ constexpr int bin_blocks(int M) {
+  return (M + 256 * bin_chunks(M) - 1) / (256 * bin_chunks(M));
 }
 
 // Binning: after every thread of the block has added its Gaussians' super-tiles

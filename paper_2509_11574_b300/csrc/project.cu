@@ -209,47 +209,58 @@ __device__ __forceinline__ void project_gaussian(const Params& P, int i, const C
   o.vis = isfinite(o.mx) && isfinite(o.my) && isfinite(o.ca) && isfinite(o.cb) && isfinite(o.cc);
 }
 
+// K3 for Gaussian i: its record, and its bins added to the block histogram.
+template <int DEG>
+__device__ __forceinline__ void project_one(const Params& P, int i, float near_, const ViewDev& v,
+                                            const float* s_row, uint32_t* s_hist) {
+  const Cam cam = v.cam;
+  ProjState o;
+  project_gaussian(P, i, cam, near_, o);
+  float4* r = v.rec + 4 * (size_t)i;
+  if (!o.vis) {
+    r[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    r[2] = make_float4(0.f, 0.f, 0.f, -1.0f);
+    r[3] = make_float4(-1.0f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const float3 col = view_colour<DEG>(P, i, cam, s_row);
+  r[0] = make_float4(o.mx, o.my, o.tc[2], o.sig);
+  r[1] = make_float4(o.ca, o.cb, o.cc, o.qmax);
+  r[2] = make_float4(col.x, col.y, col.z, o.ex);
+  r[3] = make_float4(o.ey, 0.f, 0.f, 0.f);
+  int x0, x1, y0, y1;
+  record_rect(o.mx, o.my, o.ex, o.ey, cam.W, cam.H, x0, x1, y0, y1);
+  for (int sy = y0 >> v.bin_sy; sy <= (y1 >> v.bin_sy); ++sy)
+    for (int sx = x0 >> v.bin_sx; sx <= (x1 >> v.bin_sx); ++sx)
+      atomicAdd(s_hist + sy * v.sup_x + sx, 1u);
+}
+
 // K3: records, plus the block's bin histogram and range reservation (first
 // half of the binning; bins are super-tiles or tiles).  Block row blockIdx.y
-// projects for view blockIdx.y of the batch.  sup_count must be zero on entry.
+// projects for view blockIdx.y of the batch; a block takes bin_chunks(M)
+// chunks of 256 Gaussians.  sup_count must be zero on entry.
 // Shared memory: the bin histogram (max_nsup words, rounded up to an even
-// count) and, with DEG > 0, the block's SH rows.
+// count) and, with DEG > 0, the chunk's SH rows.
 template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(Params P, int M, float near_, int hist_words,
                                                       const __grid_constant__ ViewBatch vb) {
   extern __shared__ uint32_t s_hist[];
   float* s_f = reinterpret_cast<float*>(s_hist + hist_words);
   const ViewDev& v = vb.v[blockIdx.y];
-  const int bsx = v.bin_sx, bsy = v.bin_sy, sup_x = v.sup_x, nsup = v.sup_x * v.sup_y;
+  const int nsup = v.sup_x * v.sup_y;
   for (int s = threadIdx.x; s < nsup; s += blockDim.x) s_hist[s] = 0;
-  if constexpr (DEG > 0) {
-    const long long base = (long long)blockIdx.x * blockDim.x;
-    stage_rows<DEG>(P.sh, base, (int)min((long long)blockDim.x, M - base), s_f);
-  }
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < M) {
-    const Cam cam = v.cam;
-    ProjState o;
-    project_gaussian(P, i, cam, near_, o);
-    float4* r = v.rec + 4 * (size_t)i;
-    if (!o.vis) {
-      r[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-      r[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-      r[2] = make_float4(0.f, 0.f, 0.f, -1.0f);
-      r[3] = make_float4(-1.0f, 0.f, 0.f, 0.f);
-    } else {
-      const float3 col = view_colour<DEG>(P, i, cam, s_f + threadIdx.x * ShRows<DEG>::STRIDE);
-      r[0] = make_float4(o.mx, o.my, o.tc[2], o.sig);
-      r[1] = make_float4(o.ca, o.cb, o.cc, o.qmax);
-      r[2] = make_float4(col.x, col.y, col.z, o.ex);
-      r[3] = make_float4(o.ey, 0.f, 0.f, 0.f);
-      int x0, x1, y0, y1;
-      record_rect(o.mx, o.my, o.ex, o.ey, cam.W, cam.H, x0, x1, y0, y1);
-      for (int sy = y0 >> bsy; sy <= (y1 >> bsy); ++sy)
-        for (int sx = x0 >> bsx; sx <= (x1 >> bsx); ++sx)
-          atomicAdd(s_hist + sy * sup_x + sx, 1u);
+  const int chunks = bin_chunks(M);
+  for (int ch = 0; ch < chunks; ++ch) {
+    const long long base = ((long long)blockIdx.x * chunks + ch) * blockDim.x;
+    if constexpr (DEG > 0) {
+      if (ch > 0) __syncthreads();  // the previous chunk's rows are read
+      if (base < M) stage_rows<DEG>(P.sh, base, (int)min((long long)blockDim.x, M - base), s_f);
     }
+    if (DEG > 0 || ch == 0) __syncthreads();
+    if (base + threadIdx.x < M)
+      project_one<DEG>(P, (int)(base + threadIdx.x), near_, v,
+                       s_f + threadIdx.x * ShRows<DEG>::STRIDE, s_hist);
   }
   reserve_block_ranges(s_hist, nsup, v.sup_count, v.block_base);
 }
@@ -431,8 +442,9 @@ cudaError_t launch_project_t(const Params& P, int M, float near_, const ViewBatc
         project_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  project_kernel<DEG><<<dim3((M + kProjThreads - 1) / kProjThreads, vb.n), kProjThreads, smem,
-                       st>>>(P, M, near_, hist_words, vb);
+  static_assert(kProjThreads == 256, "binning chunks hold 256 Gaussians");
+  project_kernel<DEG><<<dim3(bin_blocks(M), vb.n), kProjThreads, smem, st>>>(P, M, near_,
+                                                                           hist_words, vb);
   return cudaGetLastError();
 }
 

@@ -105,6 +105,12 @@ def test_workspace_size_and_layout_host_only(L):
     # a tile grid too large for the shared-memory histogram: super-tile bins
     big = gps.gps_workspace_layout(10, [_Cam(2048, 1040)], gps.settings(tile=(8, 8)), 0)
     assert big.tile_bins == 0 and big.super_px == 16
+    # binning blocks take 256 Gaussians, or up to 8 chunks of 256 so that
+    # about 600 blocks remain: one block-base row per block
+    Lm = gps.gps_workspace_layout(1_000_000, cams[:1], gps.settings(tile=(16, 8)), 0)
+    assert Lm.super_ranges - Lm.block_base == -(-652 * 150 * 4 // 256) * 256  # 6 chunks
+    Ls = gps.gps_workspace_layout(100_000, cams[:1], gps.settings(tile=(16, 8)), 0)
+    assert Ls.super_ranges - Ls.block_base == -(-391 * 150 * 4 // 256) * 256  # 1 chunk
     n = gps.gps_workspace_size(2000, cams, gps.settings())
     assert gps.gps_workspace_size(2000, cams, s) > n
     with pytest.raises(gps.GpsError) as e:

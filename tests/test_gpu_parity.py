@@ -147,13 +147,18 @@ def test_projection_matches_oracle():
 
 
 # --------------------------------------------------------------- binning
-@pytest.mark.parametrize("det", [True, False])
-@pytest.mark.parametrize("tile", [(16, 16), (16, 8), (8, 8), (32, 8)])
-def test_binning_bit_exact(tile, det):
+_BIN_CASES = [(tile, det, 3000) for det in (True, False)
+              for tile in ((16, 16), (16, 8), (8, 8), (32, 8))]
+# 320k and 1.3M Gaussians: 2 and 8 chunks of 256 Gaussians per binning block
+_BIN_CASES += [((16, 8), True, 320000), ((16, 8), False, 320000), ((16, 8), False, 1300000)]
+
+
+@pytest.mark.parametrize("tile,det,M", _BIN_CASES)
+def test_binning_bit_exact(tile, det, M):
     """Identical FP32 records in, identical sorted (tile, depth, index) lists out
     (deterministic mode); the sort-free default gives every tile the same
     entries in emission order."""
-    w = workload("small", M=3000, width=150, height=100)  # ragged tiles
+    w = workload("small", M=M, width=150, height=100)  # ragged tiles
     f = w.frames[0]
     rec_o, _ = oracle.project(w.gaussians.astype(np.float64), f.cam)
     r32 = oracle.records_f32(rec_o)
@@ -178,7 +183,7 @@ def test_binning_bit_exact(tile, det):
         assert len(seg) == hi - lo, (t, len(seg), hi - lo)
         np.testing.assert_array_equal(seg >> np.uint64(32), keys_o[lo:hi] & np.uint64(0xffffffff))
         np.testing.assert_array_equal((seg & np.uint64(0xffffffff)).astype(np.uint32), vals_o[lo:hi])
-    assert total == len(keys_o) > 1000
+    assert total == len(keys_o) > M // 3
     assert r.status() == gps.GPS_OK
 
 
