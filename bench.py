@@ -300,7 +300,7 @@ class GpuPipeline:
         d, c, _ = self.frames[0]
         self.gps.fuse_frame(self.vol, d, c, self.cams[0])
         self.gps.raycast_sdf(self.vol, self.cams[0], self.w.near, 0.0, self.Ct, self.Dt, None)
-        best, times = self.r.autotune(self.g, [self.view(0)], repeats=3)
+        best, times = self.r.autotune(self.g, [self.view(0)], repeats=15)
         self.s = self.r.s
         self.reset()
         return {"chosen": f"{best[0]}x{best[1]}",
@@ -745,7 +745,7 @@ def run_multiview(args, rank, world, local):
     rb = gps.Renderer(MV_GAUSS, cams, s, dev)
     tuned = None
     if args.tile == "auto":
-        best, times = rb.autotune(g, views, repeats=2)
+        best, times = rb.autotune(g, views, repeats=5)
         s = rb.s
         tuned = {"chosen": f"{best[0]}x{best[1]}",
                  "ms_fwd_bwd": {f"{a}x{b}": t for (a, b), t in times.items()}}

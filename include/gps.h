@@ -333,14 +333,15 @@ GPS_API int32_t adam_step(GpsGaussians* params, GpsGaussians* grads, GpsGaussian
 /* Tile-shape autotuner (the paper has no counterpart).  For every shape above
  * whose workspace (gps_workspace_size) fits in ws_bytes, runs render_forward +
  * render_backward on the caller's own Gaussians and views once untimed, then
- * `repeats` times timed with CUDA events on `stream`, and returns the fastest
- * in *best_tile_w, *best_tile_h; times_ms[GPS_AUTOTUNE_SHAPES] (nullable)
- * receives each shape's mean milliseconds per forward + backward, -1 for a
+ * times every shape once per round for `repeats` rounds (at most 64) with
+ * CUDA events on `stream`, and returns the shape of the lowest median in
+ * *best_tile_w, *best_tile_h; times_ms[GPS_AUTOTUNE_SHAPES] (nullable)
+ * receives each shape's median milliseconds per forward + backward, -1 for a
  * shape that was skipped (workspace too small, or the pair capacity
  * overflowed).  settings supplies everything but the tile (stages and
  * instrument are ignored).  The backward accumulates into scratch_grads (same
  * shape as the Gaussians), which the caller discards; the views' outputs
- * are overwritten.  Synchronises `stream` after every shape: call it before
+ * are overwritten.  Synchronises `stream` after every timed pass: call it before
  * capturing graphs, then pass the chosen shape in GpsRenderSettings (and size
  * the workspace for it).  Errors: GPS_ERR_INVALID_ARG for NULL arguments,
  * render_forward's and render_backward's own errors, GPS_ERR_WORKSPACE_TOO_SMALL

@@ -3,6 +3,7 @@
 // timing render_forward + render_backward on the caller's own data.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -18,6 +19,7 @@ struct Shape {
   int tw, th;
 };
 constexpr Shape kShapes[GPS_AUTOTUNE_SHAPES] = {{16, 16}, {16, 8}, {8, 8}, {32, 8}};
+constexpr int kMaxRepeats = 64;  // timed rounds kept per shape
 
 int32_t cuda_error(cudaError_t e, const char* where) {
   char buf[200];
@@ -47,42 +49,57 @@ extern "C" int32_t gps_autotune_tiles(const GpsGaussians* g, const GpsView* view
     return cuda_error(ce, "cudaEventCreate");
   }
   int32_t rc = GPS_OK;
+  // every candidate runs once untimed (and must leave status GPS_OK); then
+  // the shapes are timed in interleaved rounds, so that drifting clocks or a
+  // neighbour's load hit all of them alike, and each keeps its median
+  const int reps = repeats < kMaxRepeats ? repeats : kMaxRepeats;
+  bool cand[GPS_AUTOTUNE_SHAPES];
+  float samples[GPS_AUTOTUNE_SHAPES][kMaxRepeats];
+  GpsRenderSettings sk[GPS_AUTOTUNE_SHAPES];
+  for (int k = 0; k < GPS_AUTOTUNE_SHAPES && rc == GPS_OK; ++k) {
+    cand[k] = false;
+    if (times_ms) times_ms[k] = -1.0f;
+    sk[k] = *settings;
+    sk[k].tile_w = kShapes[k].tw;
+    sk[k].tile_h = kShapes[k].th;
+    sk[k].stages = 0;
+    sk[k].instrument = 0;
+    size_t need = 0;
+    if ((rc = gps_workspace_size(g->M, views, n_views, &sk[k], &need)) != GPS_OK) break;
+    if (need > ws_bytes) continue;  // this shape's workspace does not fit: not a candidate
+    rc = render_forward(g, views, n_views, &sk[k], ws, ws_bytes, nullptr, stream);
+    if (rc == GPS_OK)
+      rc = render_backward(g, views, n_views, &sk[k], ws, ws_bytes, nullptr, scratch_grads, stream);
+    int32_t status = GPS_OK;
+    if (rc == GPS_OK) rc = gps_query_status(ws, ws_bytes, &status, stream);
+    cand[k] = rc == GPS_OK && status == GPS_OK;  // e.g. pair capacity exceeded with this shape
+  }
+  for (int r = 0; r < reps && rc == GPS_OK; ++r) {
+    for (int k = 0; k < GPS_AUTOTUNE_SHAPES && rc == GPS_OK; ++k) {
+      if (!cand[k]) continue;
+      if ((ce = cudaEventRecord(e0, st)) != cudaSuccess) rc = cuda_error(ce, "record");
+      if (rc == GPS_OK) rc = render_forward(g, views, n_views, &sk[k], ws, ws_bytes, nullptr, stream);
+      if (rc == GPS_OK)
+        rc = render_backward(g, views, n_views, &sk[k], ws, ws_bytes, nullptr, scratch_grads, stream);
+      if (rc != GPS_OK) break;
+      if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) rc = cuda_error(ce, "record");
+      else if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_error(ce, "synchronize");
+      float ms = 0.0f;
+      if (rc == GPS_OK && (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+        rc = cuda_error(ce, "elapsed time");
+      samples[k][r] = ms;
+    }
+  }
   float best = INFINITY;
   int best_k = -1;
   for (int k = 0; k < GPS_AUTOTUNE_SHAPES && rc == GPS_OK; ++k) {
-    GpsRenderSettings s = *settings;
-    s.tile_w = kShapes[k].tw;
-    s.tile_h = kShapes[k].th;
-    s.stages = 0;
-    s.instrument = 0;
-    if (times_ms) times_ms[k] = -1.0f;
-    size_t need = 0;
-    if ((rc = gps_workspace_size(g->M, views, n_views, &s, &need)) != GPS_OK) break;
-    if (need > ws_bytes) continue;  // this shape's workspace does not fit: not a candidate
-    float total = 0.0f;
-    // one untimed pass, then `repeats` timed forward + backward passes
-    for (int r = 0; r <= repeats && rc == GPS_OK; ++r) {
-      if (r > 0 && (ce = cudaEventRecord(e0, st)) != cudaSuccess) rc = cuda_error(ce, "record");
-      if (rc == GPS_OK) rc = render_forward(g, views, n_views, &s, ws, ws_bytes, nullptr, stream);
-      if (rc == GPS_OK)
-        rc = render_backward(g, views, n_views, &s, ws, ws_bytes, nullptr, scratch_grads, stream);
-      if (rc == GPS_OK && r > 0) {
-        if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) rc = cuda_error(ce, "record");
-        else if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_error(ce, "synchronize");
-        float ms = 0.0f;
-        if (rc == GPS_OK && (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
-          rc = cuda_error(ce, "elapsed time");
-        total += ms;
-      }
-    }
-    if (rc != GPS_OK) break;
-    int32_t status = GPS_OK;
-    if ((rc = gps_query_status(ws, ws_bytes, &status, stream)) != GPS_OK) break;
-    if (status != GPS_OK) continue;  // e.g. pair capacity exceeded with this shape
-    const float per = total / (float)repeats;
-    if (times_ms) times_ms[k] = per;
-    if (per < best) {
-      best = per;
+    if (!cand[k]) continue;
+    std::sort(samples[k], samples[k] + reps);
+    const float med = reps % 2 ? samples[k][reps / 2]
+                               : 0.5f * (samples[k][reps / 2 - 1] + samples[k][reps / 2]);
+    if (times_ms) times_ms[k] = med;
+    if (med < best) {
+      best = med;
       best_k = k;
     }
   }

@@ -642,6 +642,114 @@ __device__ __forceinline__ void store_grad2d(const ViewDev& v, int deterministic
 }
 
 // ------------------------------------------------------- backward, OIT mode
+// A lane's Gaussian in the OIT backward's pixel walk.
+struct BwdGauss {
+  float mx, my, d, lns, sig, ca, b2, cc, qmax, cr, cg, cb;
+  uint32_t gi;
+  int kx0, kx1, ky0, ky1;  // its rectangle inside the block (instrumented runs)
+};
+
+// Staged record (A, B with B.y = 2 b, C, E = extents) -> lane registers.
+template <bool INSTR>
+__device__ __forceinline__ BwdGauss bwd_gauss(const float4& A, const float4& B, const float4& C,
+                                              const float2& E, uint32_t gi, float bx0, float by0) {
+  BwdGauss G;
+  G.mx = A.x; G.my = A.y; G.d = A.z; G.sig = A.w; G.lns = __log2f(A.w);
+  G.ca = B.x; G.b2 = B.y; G.cc = B.z; G.qmax = B.w;
+  G.cr = C.x; G.cg = C.y; G.cb = C.z;
+  G.gi = gi;
+  G.kx0 = 8; G.kx1 = -1; G.ky0 = 4; G.ky1 = -1;
+  if (INSTR) {
+    G.kx0 = max(0, (int)ceilf(G.mx - E.x - bx0));
+    G.kx1 = min(7, (int)floorf(G.mx + E.x - bx0));
+    G.ky0 = max(0, (int)ceilf(G.my - E.y - by0));
+    G.ky1 = min(3, (int)floorf(G.my + E.y - by0));
+  }
+  return G;
+}
+
+// An idle lane: q >= 0 > qmax, so it adds alpha = 0 everywhere.
+__device__ __forceinline__ BwdGauss bwd_idle() {
+  BwdGauss G;
+  G.mx = G.my = G.d = G.lns = 0.f;
+  G.sig = 1.f;
+  G.ca = G.b2 = G.cc = 0.f;
+  G.qmax = -1.f;
+  G.cr = G.cg = G.cb = 0.f;
+  G.gi = 0u;
+  G.kx0 = 8; G.kx1 = -1; G.ky0 = 4; G.ky1 = -1;
+  return G;
+}
+
+// The lane's Gaussian over the warp's 8 x 4 pixel block (pixels blk ..
+// blk + 31 of s_h / s_s, row-major), unrolled and branch-free: a pixel
+// outside the support fails q <= qmax and adds alpha = 0 (cheaper than
+// bounding each lane's loop by its rectangle).  m = (sum alpha h (4),
+// sum v, sum v dx, sum v dy, sum v dx^2, sum v dx dy, sum v dy^2) with
+// v = dL/dalpha * alpha.
+template <bool INSTR>
+__device__ __forceinline__ void bwd_walk(const BwdGauss& G, bool has, int blk, float bx0, float by0,
+                                         const float4* s_h, const float2* s_s, float (&m)[10],
+                                         unsigned& n_tested, unsigned& n_counted) {
+  float dcr = 0.f, dcg = 0.f, dcb = 0.f, dd = 0.f, sa = 0.f;
+  float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+#pragma unroll 2
+  for (int ky = 0; ky < 4; ++ky) {
+    const float dy = __fsub_rn(by0 + (float)ky, G.my);
+    // the dy terms of quad_form, hoisted out of the row (same roundings)
+    const float t1 = __fmul_rn(G.b2, dy);
+    const float s3 = __fmul_rn(__fmul_rn(G.cc, dy), dy);
+    // row sums of v, v dx, v dx^2; the dy moments follow per row
+    float ra = 0.f, rx = 0.f, rxx = 0.f;
+#pragma unroll
+    for (int kx = 0; kx < 8; ++kx) {
+      const int p = blk + ky * 8 + kx;
+      const float2 ss = s_s[p];
+      const float dx = __fsub_rn(bx0 + (float)kx, G.mx);
+      const float q = __fmaf_rn(dx, __fmaf_rn(G.ca, dx, t1), s3);
+      const bool counted = q <= G.qmax && G.d < ss.y;
+      if (INSTR) {
+        n_tested += has && kx >= G.kx0 && kx <= G.kx1 && ky >= G.ky0 && ky <= G.ky1;
+        n_counted += counted;
+      }
+      const float4 hh = s_h[p];
+      const float al = counted ? alpha_of(q, G.lns) : 0.0f;
+      dcr = fmaf(al, hh.x, dcr);
+      dcg = fmaf(al, hh.y, dcg);
+      dcb = fmaf(al, hh.z, dcb);
+      dd = fmaf(al, hh.w, dd);
+      const float dLda = fmaf(hh.x, G.cr, fmaf(hh.y, G.cg, fmaf(hh.z, G.cb, fmaf(hh.w, G.d, -ss.x))));
+      const float vv = dLda * al;
+      ra += vv;
+      const float tx_ = vv * dx;
+      rx += tx_;
+      rxx = fmaf(tx_, dx, rxx);
+    }
+    sa += ra;
+    sx += rx;
+    sxx += rxx;
+    sy = fmaf(ra, dy, sy);
+    sxy = fmaf(rx, dy, sxy);
+    syy = fmaf(ra * dy, dy, syy);
+  }
+  m[0] = dcr; m[1] = dcg; m[2] = dcb; m[3] = dd; m[4] = sa;
+  m[5] = sx; m[6] = sy; m[7] = sxx; m[8] = sxy; m[9] = syy;
+}
+
+// 2D gradient of a Gaussian from its summed moments m (see bwd_walk):
+// d/d(mx, my, conic a, b, c, sigma, r, g, b, d); dL/dsigma = sum dL/dalpha G
+// = (sum dL/dalpha alpha) / sigma.
+__device__ __forceinline__ void grad2d_of(const float (&m)[10], float ca, float cb, float cc,
+                                          float sig, float (&g)[10]) {
+  g[0] = ca * m[5] + cb * m[6];
+  g[1] = cb * m[5] + cc * m[6];
+  g[2] = -0.5f * m[7];
+  g[3] = -m[8];
+  g[4] = -0.5f * m[9];
+  g[5] = m[4] / sig;
+  g[6] = m[0]; g[7] = m[1]; g[8] = m[2]; g[9] = m[3];
+}
+
 // list entries staged per round of the OIT backward (per-warp partials of
 // NW x NB x 10 floats stay within 20 KB of shared memory)
 template <int NT>
@@ -764,72 +872,14 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
       const int t = c0 + lane;
       const bool has = t < cnt;
       const int j = has ? s_list[warp][t] : 0;
-      float mx = 0.f, my = 0.f, d = 0.f, lns = 0.f, ca = 0.f, b2 = 0.f, cc = 0.f, qmax = -1.f;
-      float cr = 0.f, cg = 0.f, cbl = 0.f;
-      int kx0 = 8, kx1 = -1, ky0 = 4, ky1 = -1;  // own rectangle (instrumented runs)
-      if (has) {
-        const float4 A = s_a[j], B = s_b[j], C = s_c[j];
-        mx = A.x; my = A.y; d = A.z; lns = __log2f(A.w);
-        ca = B.x; b2 = B.y; cc = B.z; qmax = B.w;
-        cr = C.x; cg = C.y; cbl = C.z;
-        if (INSTR) {
-          const float2 E = s_e[j];
-          kx0 = max(0, (int)ceilf(mx - E.x - bx0));
-          kx1 = min(7, (int)floorf(mx + E.x - bx0));
-          ky0 = max(0, (int)ceilf(my - E.y - by0));
-          ky1 = min(3, (int)floorf(my + E.y - by0));
-        }
-      }
-      // every lane walks all 32 pixels of the block, unrolled and branch-free:
-      // a pixel outside a Gaussian's support fails q <= qmax and adds alpha = 0
-      // (cheaper than bounding each group's loop by the union of its
-      // Gaussians' rectangles)
-      float dcr = 0.f, dcg = 0.f, dcb = 0.f, dd = 0.f, sa = 0.f;
-      float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
-#pragma unroll 2
-      for (int ky = 0; ky < 4; ++ky) {
-        const float dy = __fsub_rn(by0 + (float)ky, my);
-        // the dy terms of quad_form, hoisted out of the row (same roundings)
-        const float t1 = __fmul_rn(b2, dy);
-        const float s3 = __fmul_rn(__fmul_rn(cc, dy), dy);
-        // row sums of v, v dx, v dx^2; the dy moments follow per row
-        float ra = 0.f, rx = 0.f, rxx = 0.f;
-#pragma unroll
-        for (int kx = 0; kx < 8; ++kx) {
-          const int p = blk + ky * 8 + kx;
-          const float2 ss = s_s[p];
-          const float dx = __fsub_rn(bx0 + (float)kx, mx);
-          const float q = __fmaf_rn(dx, __fmaf_rn(ca, dx, t1), s3);
-          const bool counted = q <= qmax && d < ss.y;
-          if (INSTR) {
-            n_tested += has && kx >= kx0 && kx <= kx1 && ky >= ky0 && ky <= ky1;
-            n_counted += counted;
-          }
-          const float4 hh = s_h[p];
-          const float al = counted ? alpha_of(q, lns) : 0.0f;
-          dcr = fmaf(al, hh.x, dcr);
-          dcg = fmaf(al, hh.y, dcg);
-          dcb = fmaf(al, hh.z, dcb);
-          dd = fmaf(al, hh.w, dd);
-          const float dLda =
-              fmaf(hh.x, cr, fmaf(hh.y, cg, fmaf(hh.z, cbl, fmaf(hh.w, d, -ss.x))));
-          const float vv = dLda * al;
-          ra += vv;
-          const float tx_ = vv * dx;
-          rx += tx_;
-          rxx = fmaf(tx_, dx, rxx);
-        }
-        sa += ra;
-        sx += rx;
-        sxx += rxx;
-        sy = fmaf(ra, dy, sy);
-        sxy = fmaf(rx, dy, sxy);
-        syy = fmaf(ra * dy, dy, syy);
-      }
+      const BwdGauss G = has ? bwd_gauss<INSTR>(s_a[j], s_b[j], s_c[j], s_e[j], 0u, bx0, by0)
+                             : bwd_idle();
+      float m[10];
+      bwd_walk<INSTR>(G, has, blk, bx0, by0, s_h, s_s, m, n_tested, n_counted);
       if (has) {
         float* o = s_part[warp][j];
-        o[0] = dcr; o[1] = dcg; o[2] = dcb; o[3] = dd; o[4] = sa;
-        o[5] = sx; o[6] = sy; o[7] = sxx; o[8] = sxy; o[9] = syy;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) o[c] = m[c];
       }
     }
     __syncthreads();
@@ -848,10 +898,8 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
       }
       if (any || deterministic) {
         const float4 A = s_a[t], B = s_b[t];
-        const float ca = B.x, cb = 0.5f * B.y, cc = B.z;
-        // dL/dsigma = sum dL/dalpha * G = (sum dL/dalpha * alpha) / sigma
-        const float g[10] = {ca * m[5] + cb * m[6], cb * m[5] + cc * m[6], -0.5f * m[7], -m[8],
-                             -0.5f * m[9], m[4] / A.w, m[0], m[1], m[2], m[3]};
+        float g[10];
+        grad2d_of(m, B.x, 0.5f * B.y, B.z, A.w, g);
         store_grad2d(v, deterministic, b + t, (uint32_t)v.keys[b + t], g);
       }
     }
@@ -864,6 +912,153 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
       o[0] = o[1] = o[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
+}
+
+// Sort-free OIT backward, not deterministic.  As composite_bwd_oit_kernel,
+// but a warp walks only full groups of 32 Gaussians: the culled Gaussians
+// that do not fill a group wait in their lanes' registers for the next
+// staged batch (one partial group per warp and tile, at its end), and each
+// lane adds its Gaussian's block gradient to grad2d with vector atomics, so
+// no per-warp partials are combined in shared memory.
+template <int NT>
+struct BwdCarryBatch {
+  static constexpr int value = NT >= 128 ? 256 : 128;
+};
+
+template <bool INSTR>
+__device__ __forceinline__ void bwd_flush(const ViewDev& v, const BwdGauss& G, bool has, int blk,
+                                          float bx0, float by0, const float4* s_h,
+                                          const float2* s_s, unsigned& n_tested,
+                                          unsigned& n_counted) {
+  float m[10], g[10];
+  bwd_walk<INSTR>(G, has, blk, bx0, by0, s_h, s_s, m, n_tested, n_counted);
+  if (has) {
+    grad2d_of(m, G.ca, 0.5f * G.b2, G.cc, G.sig, g);
+    store_grad2d(v, 0, 0u, G.gi, g);
+  }
+}
+
+template <int TW, int TH, bool INSTR>
+__global__ void __launch_bounds__(TW* TH)
+    composite_bwd_oit_carry_kernel(const __grid_constant__ ViewBatch vb, float eps, float lambda,
+                                   const float* dloss) {
+  constexpr int NT = TW * TH;
+  constexpr int NB = BwdCarryBatch<NT>::value;
+  constexpr int NW = NT / 32;
+  constexpr int KPT = NB / NT;  // entries staged per thread
+  static_assert(KPT >= 1 && KPT * NT == NB, "a batch is a whole number of entries per thread");
+  __shared__ float4 s_h[NT];
+  __shared__ float2 s_s[NT];
+  __shared__ float4 s_a[NB], s_b[NB], s_c[NB];
+  __shared__ float2 s_e[NB];
+  __shared__ uint32_t s_gi[NB];
+  __shared__ uint8_t s_list[NW][NB];
+  const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
+  const ViewDev& v = vb.v[vb.order[slot]];
+  const int tile = blockIdx.x - vb.tile_start[slot];
+  const int fused = v.fused;
+  const int W = v.cam.W, H = v.cam.H;
+  const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int ox, oy, lx, ly;
+  warp_block<TW>(warp, lane, ox, oy, lx, ly);
+  const int px = tx * TW + lx, py = ty * TH + ly;
+  const bool inside = px < W && py < H;
+  const long long npx = (long long)W * H, pix = (long long)py * W + px;
+  const float scale = loss_scale(v, fused, dloss);
+  float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+  float sv = 0.f, thr = -INFINITY;
+  if (inside) {
+    const float4 st = v.pix_a[pix];
+    const float iN = 1.0f / (1.0f + v.pix_b[pix].x);
+    const float dt = __ldg(v.Dt + pix);
+    float g0, g1, g2, gD;
+    upstream(v, pix, npx, st, dt, fused, lambda, scale, g0, g1, g2, gD);
+    h = make_float4(g0 * iN, g1 * iN, g2 * iN, gD * iN);
+    sv = (g0 * st.x + g1 * st.y + g2 * st.z + gD * st.w) * iN;
+    if (g0 != 0.f || g1 != 0.f || g2 != 0.f || gD != 0.f) thr = depth_threshold(dt, eps);
+  }
+  s_h[tid] = h;
+  s_s[tid] = make_float2(sv, thr);
+  const uint2 r = v.tile_ranges[tile];
+  uint32_t gi_next[KPT];
+#pragma unroll
+  for (int u = 0; u < KPT; ++u)
+    gi_next[u] = r.x + u * NT + tid < r.y ? (uint32_t)v.keys[r.x + u * NT + tid] : 0u;
+  const float wthr = warp_max(thr);
+  const bool wdone = wthr == -INFINITY;  // no pixel of the warp has a gradient
+  if (__syncthreads_and(wdone)) return;
+  const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
+  const float by0 = (float)(ty * TH + oy), by1 = by0 + 3.0f;
+  const int blk = warp * 32;
+  unsigned n_tested = 0, n_counted = 0;
+  int pend = 0;  // lanes [0, pend) hold culled Gaussians waiting for a full group
+  BwdGauss G = bwd_idle();
+  for (uint32_t b = r.x; b < r.y; b += NB) {
+    __syncthreads();  // the previous batch's records are no longer read
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+      const int k = u * NT + tid;
+      const uint32_t gi = gi_next[u];
+      gi_next[u] = b + NB + k < r.y ? (uint32_t)v.keys[b + NB + k] : 0u;
+      if (b + k < r.y) {
+        const float4* rr = v.rec + 4 * (size_t)gi;
+        float4 B = rr[1];
+        const float4 C = rr[2];
+        B.y = 2.0f * B.y;
+        s_a[k] = rr[0];
+        s_b[k] = B;
+        s_c[k] = C;
+        s_e[k] = make_float2(C.w, rr[3].x);
+        s_gi[k] = gi;
+      }
+    }
+    __syncthreads();
+    if (wdone) continue;
+    const int nb = (int)min((uint32_t)NB, r.y - b);
+    int cnt = 0;
+    for (int j0 = 0; j0 < nb; j0 += 32) {
+      const int j = j0 + lane;
+      bool ok = false;
+      if (j < nb) {
+        const float4 A = s_a[j];
+        const float2 E = s_e[j];
+        ok = A.z < wthr && A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 &&
+             A.y - E.y <= by1;
+        if (ok) {
+          const float4 B = s_b[j];
+          ok = ellipse_meets_rect(A.x, A.y, B.x, 0.5f * B.y, B.z, B.w, bx0, bx1, by0, by1);
+        }
+      }
+      const unsigned ob = __ballot_sync(0xffffffffu, ok);
+      if (ok) s_list[warp][cnt + __popc(ob & ((1u << lane) - 1u))] = (uint8_t)j;
+      cnt += __popc(ob);
+    }
+    __syncwarp();
+    // full groups: the waiting lanes keep their Gaussians, the others load
+    int t0 = 0;
+    while (pend + cnt - t0 >= 32) {
+      if (lane >= pend) {
+        const int j = s_list[warp][t0 + lane - pend];
+        G = bwd_gauss<INSTR>(s_a[j], s_b[j], s_c[j], s_e[j], s_gi[j], bx0, by0);
+      }
+      bwd_flush<INSTR>(v, G, true, blk, bx0, by0, s_h, s_s, n_tested, n_counted);
+      t0 += 32 - pend;
+      pend = 0;
+    }
+    // the rest waits
+    if (lane >= pend && lane < pend + cnt - t0) {
+      const int j = s_list[warp][t0 + lane - pend];
+      G = bwd_gauss<INSTR>(s_a[j], s_b[j], s_c[j], s_e[j], s_gi[j], bx0, by0);
+    }
+    pend += cnt - t0;
+  }
+  if (pend > 0) {
+    const bool has = lane < pend;
+    if (!has) G = bwd_idle();
+    bwd_flush<INSTR>(v, G, has, blk, bx0, by0, s_h, s_s, n_tested, n_counted);
+  }
+  if (INSTR) add_counters(v, 2, n_tested, n_counted);
 }
 
 // ----------------------------------------------------- backward, alpha mode
@@ -1173,7 +1368,13 @@ static cudaError_t bwd_tw(const ViewBatch& vb, float eps, float lambda, const fl
                           int det, int instr, int sorted, cudaStream_t st) {
   const int items = vb.tile_start[vb.n];
   if (items <= 0) return cudaSuccess;
-  if (mode == GPS_BLEND_OIT) {
+  if (mode == GPS_BLEND_OIT && !det && !sorted) {
+    if (instr)
+      composite_bwd_oit_carry_kernel<TW, TH, true><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss);
+    else
+      composite_bwd_oit_carry_kernel<TW, TH, false><<<items, TW * TH, 0, st>>>(vb, eps, lambda,
+                                                                                dloss);
+  } else if (mode == GPS_BLEND_OIT) {
     if (instr)
       composite_bwd_oit_kernel<TW, TH, true><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss, det,
                                                                         sorted);
