@@ -35,6 +35,7 @@ struct AdamArgs {
 };
 
 __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
+  chain_wait();
   float bc1 = a.bc1, sbc2 = a.sbc2;
   if (a.device_step) {
     // 1 - b^t = -expm1(t ln b), with ln b = log1p(b - 1): accurate for b near 1
@@ -80,7 +81,10 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   }
 }
 
-__global__ void adam_step_advance_kernel(int* device_step) { *device_step += 1; }
+__global__ void adam_step_advance_kernel(int* device_step) {
+  chain_wait();
+  *device_step += 1;
+}
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -122,10 +126,10 @@ cudaError_t launch_adam(const GpsGaussians& P, const GpsGaussians& Gr, const Gps
     a.device_step = device_step;
   }
   if (blocks == 0) return cudaSuccess;
-  adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
+  launch_chained(adam_kernel, dim3((unsigned)blocks), dim3(256), 0, st, a);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && step <= 0) {
-    adam_step_advance_kernel<<<1, 1, 0, st>>>(device_step);
+    launch_chained(adam_step_advance_kernel, dim3(1), dim3(1), 0, st, device_step);
     e = cudaGetLastError();
   }
   return e;

@@ -46,6 +46,7 @@ __device__ __forceinline__ bool bin_rect(float mx, float my, float ex, float ey,
 // projection kernel fuses the same histogram).  Block row blockIdx.y: view.
 __global__ void __launch_bounds__(256) bin_histogram_kernel(int M,
                                                             const __grid_constant__ ViewBatch vb) {
+  chain_wait();
   extern __shared__ uint32_t s_hist[];
   const ViewDev& v = vb.v[blockIdx.y];
   const int nsup = v.sup_x * v.sup_y;
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(256) bin_histogram_kernel(int M,
 // per view of the batch.
 __global__ void __launch_bounds__(kScanThreads) scan_super_kernel(const __grid_constant__ ViewBatch vb,
                                                                   int* status) {
+  chain_wait();
   __shared__ unsigned long long warp_sums[kScanThreads / 32];
   const ViewDev& v = vb.v[blockIdx.x];
   uint32_t* __restrict__ counts = v.sup_count;
@@ -174,6 +176,7 @@ __device__ __forceinline__ void emit_warp(long long i, int M, const ViewDev& v, 
 // write position in every bin (range start + the block's base) is staged in
 // shared memory first, so an entry costs one shared atomic and one store.
 __global__ void __launch_bounds__(256) emit_super_kernel(int M, const __grid_constant__ ViewBatch vb) {
+  chain_wait();
   extern __shared__ uint32_t s_pos[];
   const ViewDev& v = vb.v[blockIdx.y];
   const int nsup = v.sup_x * v.sup_y;
@@ -325,6 +328,7 @@ __device__ unsigned long long* large_sort(unsigned long long* seg, unsigned long
 // one tile per super-tile the sorted segment is the tile list: no rectangles.
 template <int T, bool SORT, int TW, int TH>
 __global__ void __launch_bounds__(T) sort_split_kernel(const __grid_constant__ ViewBatch vb) {
+  chain_wait();
   constexpr int C = T * kPerThread;
   constexpr int NWT = T / 32;
   __shared__ unsigned long long buf[2 * spad_size(C)];
@@ -424,30 +428,30 @@ static cudaError_t allow_smem(K kernel, size_t smem) {
 cudaError_t launch_bin_histogram(int M, const ViewBatch& vb, int max_nsup, cudaStream_t st) {
   const size_t smem = (size_t)max_nsup * sizeof(uint32_t);
   if (cudaError_t e = allow_smem(bin_histogram_kernel, smem)) return e;
-  bin_histogram_kernel<<<dim3(bin_blocks(M), vb.n), 256, smem, st>>>(M, vb);
+  launch_chained(bin_histogram_kernel, dim3(bin_blocks(M), vb.n), dim3(256), smem, st, M, vb);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scan_super(const ViewBatch& vb, int* status, cudaStream_t st) {
-  scan_super_kernel<<<vb.n, kScanThreads, 0, st>>>(vb, status);
+  launch_chained(scan_super_kernel, dim3(vb.n), dim3(kScanThreads), 0, st, vb, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_emit_super(int M, const ViewBatch& vb, int max_nsup, cudaStream_t st) {
   const size_t smem = (size_t)max_nsup * sizeof(uint32_t);
   if (cudaError_t e = allow_smem(emit_super_kernel, smem)) return e;
-  emit_super_kernel<<<dim3(bin_blocks(M), vb.n), 256, smem, st>>>(M, vb);
+  launch_chained(emit_super_kernel, dim3(bin_blocks(M), vb.n), dim3(256), smem, st, M, vb);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sort_split(const ViewBatch& vb, int tw, int th, int sort, cudaStream_t st) {
   const int items = vb.sup_start[vb.n];
   if (items <= 0) return cudaSuccess;
-#define GPS_SORT_SPLIT(T, A, B)                                                  \
-  if (tw == A && th == B) {                                                      \
-    if (sort) sort_split_kernel<T, true, A, B><<<items, T, 0, st>>>(vb);         \
-    else sort_split_kernel<T, false, A, B><<<items, T, 0, st>>>(vb);             \
-    return cudaGetLastError();                                                   \
+#define GPS_SORT_SPLIT(T, A, B)                                                       \
+  if (tw == A && th == B) {                                                           \
+    if (sort) launch_chained(sort_split_kernel<T, true, A, B>, dim3(items), dim3(T), 0, st, vb); \
+    else launch_chained(sort_split_kernel<T, false, A, B>, dim3(items), dim3(T), 0, st, vb);     \
+    return cudaGetLastError();                                                        \
   }
   GPS_SORT_SPLIT(128, 16, 16)
   GPS_SORT_SPLIT(128, 16, 8)

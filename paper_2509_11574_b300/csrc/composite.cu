@@ -164,6 +164,7 @@ __device__ __forceinline__ void warp_block(int warp, int lane, int& ox, int& oy,
 template <int TW, int TH, int MODE, bool INSTR>
 __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_constant__ ViewBatch vb,
                                                               float eps, int has_tgt) {
+  chain_wait();
   constexpr int NT = TW * TH;
   constexpr int NW = NT / 32;
   __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
@@ -360,6 +361,7 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
 template <int TW, int TH, bool INSTR>
 __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
     const __grid_constant__ ViewBatch vb, float eps, int has_tgt, int sorted) {
+  chain_wait();
   constexpr int NTT = TW * TH / 2;  // threads
   constexpr int NW = NTT / 32;
   constexpr int NB = 2 * NTT;       // staged entries per batch
@@ -548,6 +550,7 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
 __global__ void __launch_bounds__(256) finalize_loss_kernel(const __grid_constant__ ViewBatch vb,
                                                             float lambda_depth, float* loss,
                                                             int first) {
+  chain_wait();
   __shared__ float s[3][8];
   float total = 0.f;
   for (int k = 0; k < vb.n; ++k) {
@@ -768,6 +771,7 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
                                                                    float eps, float lambda,
                                                                    const float* dloss,
                                                                    int deterministic, int sorted) {
+  chain_wait();
   constexpr int NT = TW * TH;
   constexpr int NW = NT / 32;
   constexpr int NB = BwdBatch<NT>::value;
@@ -942,6 +946,7 @@ template <int TW, int TH, bool INSTR>
 __global__ void __launch_bounds__(TW* TH)
     composite_bwd_oit_carry_kernel(const __grid_constant__ ViewBatch vb, float eps, float lambda,
                                    const float* dloss) {
+  chain_wait();
   constexpr int NT = TW * TH;
   constexpr int NB = BwdCarryBatch<NT>::value;
   constexpr int NW = NT / 32;
@@ -1069,6 +1074,7 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
                                                                      float eps, float lambda,
                                                                      const float* dloss,
                                                                      int deterministic) {
+  chain_wait();
   constexpr int NT = TW * TH;
   constexpr int NW = NT / 32;
   __shared__ float4 s_a[kAlphaBatch], s_b[kAlphaBatch], s_c[kAlphaBatch];
@@ -1202,6 +1208,7 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
 // Block row blockIdx.y: view.
 __global__ void __launch_bounds__(256) gather_pair_grads_kernel(const __grid_constant__ ViewBatch vb,
                                                                 int M) {
+  chain_wait();
   const ViewDev& v = vb.v[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
@@ -1248,6 +1255,7 @@ __global__ void __launch_bounds__(256) gather_pair_grads_kernel(const __grid_con
 __global__ void __launch_bounds__(256) bwd_pixel_terms_kernel(const __grid_constant__ ViewBatch vb,
                                                               float eps, float lambda,
                                                               const float* dloss) {
+  chain_wait();
   const ViewDev& v = vb.v[blockIdx.y];
   const int W = v.cam.W, H = v.cam.H;
   const long long npx = (long long)W * H;
@@ -1268,6 +1276,7 @@ __global__ void __launch_bounds__(256) bwd_pixel_terms_kernel(const __grid_const
 template <bool INSTR>
 __global__ void __launch_bounds__(256) composite_bwd_per_gaussian_kernel(
     const __grid_constant__ ViewBatch vb, int M) {
+  chain_wait();
   const ViewDev& v = vb.v[blockIdx.y];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gi = blockIdx.x * 8 + warp;
@@ -1333,13 +1342,16 @@ cudaError_t launch_composite_bwd_per_gaussian(const ViewBatch& vb, int M, float 
                                               const float* dloss, int instr, cudaStream_t st) {
   int max_px = 0;
   for (int k = 0; k < vb.n; ++k) max_px = max(max_px, vb.v[k].cam.W * vb.v[k].cam.H);
-  bwd_pixel_terms_kernel<<<dim3((max_px + 255) / 256, vb.n), 256, 0, st>>>(vb, eps, lambda, dloss);
+  launch_chained(bwd_pixel_terms_kernel, dim3((max_px + 255) / 256, vb.n), dim3(256), 0, st,
+      vb, eps, lambda, dloss);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || M <= 0) return e;
   if (instr)
-    composite_bwd_per_gaussian_kernel<true><<<dim3((M + 7) / 8, vb.n), 256, 0, st>>>(vb, M);
+    launch_chained(composite_bwd_per_gaussian_kernel<true>, dim3((M + 7) / 8, vb.n), dim3(256), 0, st,
+        vb, M);
   else
-    composite_bwd_per_gaussian_kernel<false><<<dim3((M + 7) / 8, vb.n), 256, 0, st>>>(vb, M);
+    launch_chained(composite_bwd_per_gaussian_kernel<false>, dim3((M + 7) / 8, vb.n), dim3(256), 0, st,
+        vb, M);
   return cudaGetLastError();
 }
 
@@ -1351,14 +1363,18 @@ static cudaError_t fwd_tw(const ViewBatch& vb, float eps, int mode, int has_tgt,
   if (items <= 0) return cudaSuccess;
   if (mode == GPS_BLEND_OIT) {
     if (instr)
-      composite_fwd_oit2_kernel<TW, TH, true><<<items, TW * TH / 2, 0, st>>>(vb, eps, has_tgt, sorted);
+      launch_chained(composite_fwd_oit2_kernel<TW, TH, true>, dim3(items), dim3(TW * TH / 2), 0, st,
+          vb, eps, has_tgt, sorted);
     else
-      composite_fwd_oit2_kernel<TW, TH, false><<<items, TW * TH / 2, 0, st>>>(vb, eps, has_tgt, sorted);
+      launch_chained(composite_fwd_oit2_kernel<TW, TH, false>, dim3(items), dim3(TW * TH / 2), 0, st,
+          vb, eps, has_tgt, sorted);
   } else {
     if (instr)
-      composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, true><<<items, TW * TH, 0, st>>>(vb, eps, has_tgt);
+      launch_chained(composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, true>, dim3(items), dim3(TW * TH), 0, st,
+          vb, eps, has_tgt);
     else
-      composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, false><<<items, TW * TH, 0, st>>>(vb, eps, has_tgt);
+      launch_chained(composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, false>, dim3(items), dim3(TW * TH), 0, st,
+          vb, eps, has_tgt);
   }
   return cudaGetLastError();
 }
@@ -1370,19 +1386,21 @@ static cudaError_t bwd_tw(const ViewBatch& vb, float eps, float lambda, const fl
   if (items <= 0) return cudaSuccess;
   if (mode == GPS_BLEND_OIT && !det && !sorted) {
     if (instr)
-      composite_bwd_oit_carry_kernel<TW, TH, true><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss);
+      launch_chained(composite_bwd_oit_carry_kernel<TW, TH, true>, dim3(items), dim3(TW * TH), 0, st,
+          vb, eps, lambda, dloss);
     else
-      composite_bwd_oit_carry_kernel<TW, TH, false><<<items, TW * TH, 0, st>>>(vb, eps, lambda,
-                                                                                dloss);
+      launch_chained(composite_bwd_oit_carry_kernel<TW, TH, false>, dim3(items), dim3(TW * TH), 0, st,
+          vb, eps, lambda, dloss);
   } else if (mode == GPS_BLEND_OIT) {
     if (instr)
-      composite_bwd_oit_kernel<TW, TH, true><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss, det,
-                                                                        sorted);
+      launch_chained(composite_bwd_oit_kernel<TW, TH, true>, dim3(items), dim3(TW * TH), 0, st,
+          vb, eps, lambda, dloss, det, sorted);
     else
-      composite_bwd_oit_kernel<TW, TH, false><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss,
-                                                                         det, sorted);
+      launch_chained(composite_bwd_oit_kernel<TW, TH, false>, dim3(items), dim3(TW * TH), 0, st,
+          vb, eps, lambda, dloss, det, sorted);
   } else
-    composite_bwd_alpha_kernel<TW, TH><<<items, TW * TH, 0, st>>>(vb, eps, lambda, dloss, det);
+    launch_chained(composite_bwd_alpha_kernel<TW, TH>, dim3(items), dim3(TW * TH), 0, st,
+        vb, eps, lambda, dloss, det);
   return cudaGetLastError();
 }
 
@@ -1407,12 +1425,12 @@ cudaError_t launch_composite_bwd(const ViewBatch& vb, int tw, int th, float eps,
 
 cudaError_t launch_finalize_loss(const ViewBatch& vb, float lambda, float* loss, int first,
                                  cudaStream_t st) {
-  finalize_loss_kernel<<<1, 256, 0, st>>>(vb, lambda, loss, first);
+  launch_chained(finalize_loss_kernel, dim3(1), dim3(256), 0, st, vb, lambda, loss, first);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_pair_grads(const ViewBatch& vb, int M, cudaStream_t st) {
-  gather_pair_grads_kernel<<<dim3((M + 255) / 256, vb.n), 256, 0, st>>>(vb, M);
+  launch_chained(gather_pair_grads_kernel, dim3((M + 255) / 256, vb.n), dim3(256), 0, st, vb, M);
   return cudaGetLastError();
 }
 

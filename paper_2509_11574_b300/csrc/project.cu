@@ -245,6 +245,7 @@ __device__ __forceinline__ void project_one(const Params& P, int i, float near_,
 template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(Params P, int M, float near_, int hist_words,
                                                       const __grid_constant__ ViewBatch vb) {
+  chain_wait();
   extern __shared__ uint32_t s_hist[];
   float* s_f = reinterpret_cast<float*>(s_hist + hist_words);
   const ViewDev& v = vb.v[blockIdx.y];
@@ -376,6 +377,7 @@ template <int DEG>
 __global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, float near_,
                                                                const __grid_constant__ ViewBatch vb,
                                                                GpsGaussians grads) {
+  chain_wait();
   extern __shared__ float s_sh[];
   using R = ShRows<DEG>;
   const long long base = (long long)blockIdx.x * blockDim.x;
@@ -443,8 +445,8 @@ cudaError_t launch_project_t(const Params& P, int M, float near_, const ViewBatc
     if (e != cudaSuccess) return e;
   }
   static_assert(kProjThreads == 256, "binning chunks hold 256 Gaussians");
-  project_kernel<DEG><<<dim3(bin_blocks(M), vb.n), kProjThreads, smem, st>>>(P, M, near_,
-                                                                           hist_words, vb);
+  launch_chained(project_kernel<DEG>, dim3(bin_blocks(M), vb.n), dim3(kProjThreads), smem, st,
+      P, M, near_, hist_words, vb);
   return cudaGetLastError();
 }
 
@@ -457,7 +459,7 @@ cudaError_t launch_project_backward_t(const Params& P, int M, float near_, const
         project_backward_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  project_backward_kernel<DEG><<<(M + kProjThreads - 1) / kProjThreads, kProjThreads, smem, st>>>(
+  launch_chained(project_backward_kernel<DEG>, dim3((M + kProjThreads - 1) / kProjThreads), dim3(kProjThreads), smem, st,
       P, M, near_, vb, grads);
   return cudaGetLastError();
 }
