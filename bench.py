@@ -7,7 +7,8 @@ Workload (synthetic stand-in for the paper's Kinect-class sequences): a
 1 cm, 100,000 Gaussians, 10 fwd+bwd+Adam iterations per frame.
 
 One step = one frame: fuse_frame + raycast_sdf + 10 x (render_forward with
-the fused L1 loss, render_backward, adam_step), all through the C ABI.  The
+the fused L1 loss, render_backward_adam: the backward and the Adam step in
+one call), all through the C ABI.  The
 timed form replays one CUDA graph per frame; the plain (uncaptured) form is
 timed beside it.  value = iterations / s over whole steps (fusion and ray-cast
 included); ms_per_step = ms per frame.
@@ -275,6 +276,10 @@ class GpuPipeline:
         self.g = gps.Gaussians(*[t.clone() for t in self.g0.tensors()])
         self.grads = self.g.zeros_like()
         self.opt = gps.Adam(self.g, device_step=True)
+        # the backward feeds Adam directly (render_backward_adam) without SH
+        # colour; with SH rows the separate render_backward + adam_step
+        # measured faster (the fused kernel updates the rows at 2 CTAs / SM)
+        self.fused = w.gaussians.sh_degree == 0
         self.s = gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, near=w.near,
                               blend_mode=gps.BLEND_ALPHA if mode == "alpha" else gps.BLEND_OIT,
                               tile=tile, pair_capacity=64 * w.gaussians.M, precision=prec,
@@ -319,23 +324,23 @@ class GpuPipeline:
         for it in range(ITERS_PER_FRAME):
             if stage_events is None:
                 gps.render_forward(self.g, v, self.s, self.r.ws, self.loss[it:it + 1], stream)
-                gps.render_backward(self.g, v, self.s, self.r.ws, self.grads, None, stream)
-                self.opt.step(self.grads, stream)
+                if self.fused:
+                    self.opt.backward_step(v, self.s, self.r.ws, None, stream)
+                else:
+                    gps.render_backward(self.g, v, self.s, self.r.ws, self.grads, None, stream)
+                    self.opt.step(self.grads, stream)
             else:
                 self._staged_iteration(v, it, stage_events, stream)
-                e0 = self.torch.cuda.Event(enable_timing=True)
-                e1 = self.torch.cuda.Event(enable_timing=True)
-                e0.record()
-                self.opt.step(self.grads, stream)
-                e1.record()
-                stage_events.setdefault("adam", []).append((e0, e1))
 
     def _staged_iteration(self, v, it, ev, stream):
         gps = self.gps
         parts = [("project+bin", gps.STAGE_PROJECT | gps.STAGE_BIN, "f"),
                  ("composite_fwd", gps.STAGE_COMPOSITE, "f"),
-                 ("composite_bwd", gps.STAGE_COMPOSITE_BWD, "b"),
-                 ("project_bwd", gps.STAGE_PROJECT_BWD, "b")]
+                 ("composite_bwd", gps.STAGE_COMPOSITE_BWD, "b")]
+        if self.fused:
+            parts.append(("project_bwd+adam", gps.STAGE_PROJECT_BWD, "a"))
+        else:
+            parts += [("project_bwd", gps.STAGE_PROJECT_BWD, "b"), ("adam", 0, "o")]
         for name, stg, kind in parts:
             s = gps.GpsRenderSettings.from_buffer_copy(self.s)
             s.stages = stg
@@ -344,8 +349,12 @@ class GpuPipeline:
             e0.record()
             if kind == "f":
                 gps.render_forward(self.g, v, s, self.r.ws, self.loss[it:it + 1], stream)
-            else:
+            elif kind == "b":
                 gps.render_backward(self.g, v, s, self.r.ws, self.grads, None, stream)
+            elif kind == "a":
+                self.opt.backward_step(v, s, self.r.ws, None, stream)
+            else:
+                self.opt.step(self.grads, stream)
             e1.record()
             ev.setdefault(name, []).append((e0, e1))
 
@@ -363,12 +372,15 @@ class GpuPipeline:
         return g
 
 
-def kernels_per_step(mode, tile, schedule="tiles"):
-    # fuse, raycast + per iteration: project, scan, emit, sort + split, composite,
-    # finalize, composite_bwd [per-Gaussian schedule: pixel terms + per-Gaussian],
-    # project_bwd, adam, step counter
-    pg = 1 if schedule == "per-gaussian" else 0
-    return 2 + ITERS_PER_FRAME * (10 + pg)
+def kernels_per_step(mode, tile, schedule="tiles", deterministic=False, fused=True):
+    # fuse, raycast + per iteration: project, scan, emit, [sort + split where the
+    # lists are depth-sorted], composite, finalize, composite_bwd [deterministic:
+    # + pair gather; per-Gaussian schedule: pixel terms + per-Gaussian],
+    # projection adjoint + Adam (fused: one kernel, else two), step counter
+    tiles = schedule != "per-gaussian"
+    split = 1 if tiles and (mode == "alpha" or deterministic) else 0
+    extra = 1 if (tiles and deterministic) or not tiles else 0
+    return 2 + ITERS_PER_FRAME * (8 + split + extra + (0 if fused else 1))
 
 
 def count_evaluations(pipe, k):
@@ -590,7 +602,9 @@ def run_ours(args, rank, world, local):
         "hbm_model": {"bytes_per_iteration": it_bytes, "peak_gbs": hbm,
                       "frac_at_iteration_time": it_bytes / (it_ms * 1e-3) / 1e9 / hbm if it_ms else None},
         "roofline": roofline,
-        "clocks": clk, "gpu_launches": kernels_per_step(args.mode, tile, args.schedule) * K,
+        "clocks": clk, "gpu_launches": kernels_per_step(args.mode, tile, args.schedule,
+                                                        bool(getattr(args, "deterministic", False)),
+                                                        pipe.fused) * K,
         "status": status, "last_frame_losses": losses[-3:], "wall_s": wall,
         "gen_s": gen_s, "gpu": props.name,
     }

@@ -325,6 +325,23 @@ GPS_API int32_t render_backward(const GpsGaussians* gaussians, const GpsView* vi
 GPS_API int32_t adam_step(GpsGaussians* params, GpsGaussians* grads, GpsGaussians* m, GpsGaussians* v,
                   const GpsAdamHyper* hyper, int32_t step, int32_t* device_step, void* stream);
 
+/* render_backward followed by adam_step in one call, for up to 8 views: the
+ * composite adjoint runs as in render_backward, then one kernel takes each
+ * Gaussian's projection adjoint (summed over the views) straight into its
+ * Adam update, so no parameter-gradient array is written or read.  The result
+ * equals render_backward into zeroed grads followed by adam_step with the
+ * same hyper-parameters and step (the same FP32 operations); `gaussians` is
+ * updated in place, m and v as in adam_step.  settings.stages: 0 (all), or
+ * a set holding GPS_STAGE_PROJECT_BWD (GPS_STAGE_COMPOSITE_BWD optional).
+ * Errors: GPS_ERR_INVALID_ARG for more than 8 views, stages without
+ * GPS_STAGE_PROJECT_BWD, and the argument errors of render_backward and
+ * adam_step. */
+GPS_API int32_t render_backward_adam(GpsGaussians* gaussians, const GpsView* views, int32_t n_views,
+                             const GpsRenderSettings* settings, void* ws, size_t ws_bytes,
+                             const float* dloss, GpsGaussians* m, GpsGaussians* v,
+                             const GpsAdamHyper* hyper, int32_t step, int32_t* device_step,
+                             void* stream);
+
 /* Number of tile shapes gps_autotune_tiles tries, in this order:
  * 16x16, 16x8, 8x8, 32x8 (pixels; the binning split and both composite kernels
  * run one thread per tile pixel, so this also picks their CTA shape). */

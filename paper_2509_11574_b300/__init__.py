@@ -154,7 +154,7 @@ EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspac
             "gps_edit_scratch_size", "insert_gaussians", "remove_gaussians",
             "tsdf_mark_bricks", "gps_is_keyframe", "gps_select_views",
             "gps_icp_workspace_size", "icp_track", "gps_hash_scratch_size", "fuse_frame_hashed",
-            "raycast_sdf_hashed", "tsdf_hash_to_dense")
+            "raycast_sdf_hashed", "tsdf_hash_to_dense", "render_backward_adam")
 AUTOTUNE_SHAPES = ((16, 16), (16, 8), (8, 8), (32, 8))  # the order of GPS_AUTOTUNE_SHAPES
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -196,6 +196,11 @@ def lib() -> ctypes.CDLL:
         L.render_backward.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsView),
                                       c_int32, ctypes.POINTER(GpsRenderSettings), c_void_p,
                                       c_size_t, c_void_p, ctypes.POINTER(GpsGaussians), c_void_p]
+        L.render_backward_adam.argtypes = [
+            ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsView), c_int32,
+            ctypes.POINTER(GpsRenderSettings), c_void_p, c_size_t, c_void_p,
+            ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsGaussians),
+            ctypes.POINTER(GpsAdamHyper), c_int32, c_void_p, c_void_p]
         L.gps_autotune_tiles.argtypes = [ctypes.POINTER(GpsGaussians), ctypes.POINTER(GpsView),
                                          c_int32, ctypes.POINTER(GpsRenderSettings), c_void_p,
                                          c_size_t, ctypes.POINTER(GpsGaussians), c_int32,
@@ -579,6 +584,24 @@ def render_backward(g: Gaussians, views: Sequence[View], s: GpsRenderSettings, w
                                  ws.numel(), _ptr(dloss), ctypes.byref(gr), _stream(stream)))
 
 
+def render_backward_adam(g: Gaussians, views: Sequence[View], s: GpsRenderSettings,
+                         ws: torch.Tensor, m: Gaussians, v: Gaussians, lr=None, beta1=0.9,
+                         beta2=0.999, eps=1e-15, step: int = 1,
+                         device_step: Optional[torch.Tensor] = None,
+                         dloss: Optional[torch.Tensor] = None, stream=None,
+                         lr_sh_rest: float = None) -> None:
+    """render_backward + adam_step in one call (at most 8 views); g is updated
+    in place."""
+    lr = LR_APP_C if lr is None else lr
+    h = GpsAdamHyper((c_float * 5)(*lr), beta1, beta2, eps,
+                     LR_SH_REST if lr_sh_rest is None else lr_sh_rest)
+    gc, mc, vc = g.c(), m.c(), v.c()
+    va = _views(views, s)
+    _check(lib().render_backward_adam(ctypes.byref(gc), va, len(views), ctypes.byref(s), _ptr(ws),
+                                      ws.numel(), _ptr(dloss), ctypes.byref(mc), ctypes.byref(vc),
+                                      ctypes.byref(h), step, _ptr(device_step), _stream(stream)))
+
+
 def gps_autotune_tiles(g: Gaussians, views: Sequence[View], s: GpsRenderSettings,
                        ws: torch.Tensor, scratch_grads: Gaussians, repeats: int = 3,
                        stream=None):
@@ -799,6 +822,18 @@ class Adam:
             self.t += 1
             adam_step(self.params, grads, self.m, self.v, self.lr, *self.betas, self.eps, self.t,
                       None, stream, self.lr_sh_rest)
+
+    def backward_step(self, views: Sequence[View], s: GpsRenderSettings, ws: torch.Tensor,
+                      dloss: Optional[torch.Tensor] = None, stream=None):
+        """render_backward of the last forward and this optimiser's step in one
+        call (render_backward_adam: no gradient array)."""
+        if self.device_step is not None:
+            step = 0
+        else:
+            self.t += 1
+            step = self.t
+        render_backward_adam(self.params, views, s, ws, self.m, self.v, self.lr, *self.betas,
+                             self.eps, step, self.device_step, dloss, stream, self.lr_sh_rest)
 
 
 class RenderImages(torch.autograd.Function):

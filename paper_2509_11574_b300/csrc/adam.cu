@@ -3,12 +3,12 @@
 // semantics, FP32 moments.  One launch covers all groups; each thread updates
 // four consecutive floats with 16-byte loads where the group allows it.  The
 // gradient is zeroed in the same pass (its write replaces the zero_grad pass).
-//   m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2
-//   p <- p - (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+// The update itself is adam_update (adam.cuh).
 #include <cuda_runtime.h>
 
 #include <cmath>
 
+#include "adam.cuh"
 #include "gps_common.cuh"
 #include "sh.cuh"
 
@@ -37,12 +37,7 @@ struct AdamArgs {
 __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   chain_wait();
   float bc1 = a.bc1, sbc2 = a.sbc2;
-  if (a.device_step) {
-    // 1 - b^t = -expm1(t ln b), with ln b = log1p(b - 1): accurate for b near 1
-    const float t = (float)(*a.device_step + 1);
-    bc1 = -expm1f(t * log1pf(a.b1 - 1.0f));
-    sbc2 = sqrtf(-expm1f(t * log1pf(a.b2 - 1.0f)));
-  }
+  if (a.device_step) adam_bias(*a.device_step + 1, a.b1, a.b2, bc1, sbc2);
   const long long blk = blockIdx.x;
   int gidx = 0;
 #pragma unroll
@@ -58,24 +53,21 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
     const float4 g = *reinterpret_cast<float4*>(G.g + base);
     float4 m = *reinterpret_cast<float4*>(G.m + base);
     float4 v = *reinterpret_cast<float4*>(G.v + base);
-#define GPS_ADAM1(c)                                           \
-  m.c = b1 * m.c + (1.0f - b1) * g.c;                          \
-  v.c = b2 * v.c + (1.0f - b2) * g.c * g.c;                    \
-  p.c = p.c - step_size * m.c / (sqrtf(v.c) / sbc2 + eps);
-    GPS_ADAM1(x) GPS_ADAM1(y) GPS_ADAM1(z) GPS_ADAM1(w)
-#undef GPS_ADAM1
+    adam_update(p.x, g.x, m.x, v.x, b1, b2, eps, step_size, sbc2);
+    adam_update(p.y, g.y, m.y, v.y, b1, b2, eps, step_size, sbc2);
+    adam_update(p.z, g.z, m.z, v.z, b1, b2, eps, step_size, sbc2);
+    adam_update(p.w, g.w, m.w, v.w, b1, b2, eps, step_size, sbc2);
     *reinterpret_cast<float4*>(G.p + base) = p;
     *reinterpret_cast<float4*>(G.m + base) = m;
     *reinterpret_cast<float4*>(G.v + base) = v;
     *reinterpret_cast<float4*>(G.g + base) = make_float4(0.f, 0.f, 0.f, 0.f);
   } else {
     for (long long k = base; k < min(base + 4, G.n); ++k) {
-      const float g = G.g[k];
-      const float m = b1 * G.m[k] + (1.0f - b1) * g;
-      const float v = b2 * G.v[k] + (1.0f - b2) * g * g;
+      float p = G.p[k], m = G.m[k], v = G.v[k];
+      adam_update(p, G.g[k], m, v, b1, b2, eps, step_size, sbc2);
       G.m[k] = m;
       G.v[k] = v;
-      G.p[k] = G.p[k] - step_size * m / (sqrtf(v) / sbc2 + eps);
+      G.p[k] = p;
       G.g[k] = 0.0f;
     }
   }
@@ -84,6 +76,11 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
 __global__ void adam_step_advance_kernel(int* device_step) {
   chain_wait();
   *device_step += 1;
+}
+
+cudaError_t launch_adam_step_advance(int* device_step, cudaStream_t st) {
+  launch_chained(adam_step_advance_kernel, dim3(1), dim3(1), 0, st, device_step);
+  return cudaGetLastError();
 }
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -128,10 +125,7 @@ cudaError_t launch_adam(const GpsGaussians& P, const GpsGaussians& Gr, const Gps
   if (blocks == 0) return cudaSuccess;
   launch_chained(adam_kernel, dim3((unsigned)blocks), dim3(256), 0, st, a);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && step <= 0) {
-    launch_chained(adam_step_advance_kernel, dim3(1), dim3(1), 0, st, device_step);
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess && step <= 0) e = launch_adam_step_advance(device_step, st);
   return e;
 }
 

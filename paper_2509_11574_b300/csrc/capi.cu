@@ -33,6 +33,9 @@ cudaError_t launch_finalize_loss(const ViewBatch&, float, float*, int, cudaStrea
 cudaError_t launch_gather_pair_grads(const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_adam(const GpsGaussians&, const GpsGaussians&, const GpsGaussians&,
                         const GpsGaussians&, const GpsAdamHyper&, int, int*, cudaStream_t);
+cudaError_t launch_project_backward_adam(const GpsGaussians&, float, const ViewBatch&,
+                                         const GpsGaussians&, const GpsGaussians&,
+                                         const GpsAdamHyper&, int, int*, cudaStream_t);
 }  // namespace gps
 
 using namespace gps;
@@ -308,6 +311,49 @@ int32_t check_render_args(const GpsGaussians* g, const GpsView* views, int32_t n
   return GPS_OK;
 }
 
+// The composite adjoint of one batch of views, into the views' grad2d.
+cudaError_t composite_backward(const ViewBatch& vb, int M, const GpsRenderSettings* s, int stages,
+                               const float* dloss, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if ((stages & GPS_STAGE_COMPOSITE_BWD) && s->schedule == GPS_SCHEDULE_PER_GAUSSIAN) {
+    e = launch_composite_bwd_per_gaussian(vb, M, s->eps_depth, s->lambda_depth, dloss,
+                                          s->instrument ? 1 : 0, st);
+  } else if (stages & GPS_STAGE_COMPOSITE_BWD) {
+    for (int j = 0; j < vb.n && e == cudaSuccess && !s->deterministic; ++j)
+      e = cudaMemsetAsync(vb.v[j].grad2d, 0, (size_t)M * 48, st);
+    if (e == cudaSuccess)
+      e = launch_composite_bwd(vb, vb.v[0].tw, vb.v[0].th, s->eps_depth, s->lambda_depth, dloss,
+                               s->blend_mode, s->deterministic ? 1 : 0, s->instrument ? 1 : 0,
+                               depth_sorted(*s), st);
+    if (e == cudaSuccess && s->deterministic && M > 0) e = launch_gather_pair_grads(vb, M, st);
+  }
+  return e;
+}
+
+int32_t check_backward_views(const GpsView* views, int32_t n_views) {
+  for (int vi = 0; vi < n_views; ++vi) {
+    const GpsView& vw = views[vi];
+    if (!vw.grad_rgb && !vw.grad_depth && (!vw.target_rgb || !vw.target_depth))
+      return fail(GPS_ERR_INVALID_ARG, "view %d: no upstream gradients and no targets", vi);
+  }
+  return GPS_OK;
+}
+
+int32_t check_adam(const GpsGaussians* params, const GpsGaussians* m, const GpsGaussians* v,
+                   const GpsAdamHyper* hyper, int32_t step, const int32_t* device_step) {
+  if (int32_t e = check_gaussians(m, "m")) return e;
+  if (int32_t e = check_gaussians(v, "v")) return e;
+  if (m->M != params->M || v->M != params->M) return fail(GPS_ERR_INVALID_ARG, "group sizes differ");
+  if (m->sh_degree != params->sh_degree || v->sh_degree != params->sh_degree)
+    return fail(GPS_ERR_INVALID_ARG, "SH degrees differ");
+  if (!hyper) return fail(GPS_ERR_INVALID_ARG, "hyper is NULL");
+  if (step <= 0 && !device_step) return fail(GPS_ERR_INVALID_ARG, "step <= 0 needs device_step");
+  if (!(hyper->beta1 >= 0 && hyper->beta1 < 1 && hyper->beta2 >= 0 && hyper->beta2 < 1 &&
+        hyper->eps >= 0))
+    return fail(GPS_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+  return GPS_OK;
+}
+
 }  // namespace
 
 namespace gps {
@@ -440,11 +486,7 @@ int32_t render_backward(const GpsGaussians* g, const GpsView* views, int32_t n_v
   if (grads->M != g->M) return fail(GPS_ERR_INVALID_ARG, "grads.M != gaussians.M");
   if (grads->sh_degree != g->sh_degree)
     return fail(GPS_ERR_INVALID_ARG, "grads.sh_degree != gaussians.sh_degree");
-  for (int vi = 0; vi < n_views; ++vi) {
-    const GpsView& vw = views[vi];
-    if (!vw.grad_rgb && !vw.grad_depth && (!vw.target_rgb || !vw.target_depth))
-      return fail(GPS_ERR_INVALID_ARG, "view %d: no upstream gradients and no targets", vi);
-  }
+  if (int32_t e = check_backward_views(views, n_views)) return e;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int stages = s->stages ? s->stages : 0x1f;
   char* base = static_cast<char*>(ws);
@@ -453,39 +495,43 @@ int32_t render_backward(const GpsGaussians* g, const GpsView* views, int32_t n_v
     ViewBatch vb;
     int max_nsup = 0;
     make_batch(g->M, views, n_views, s, base, b0, vb, max_nsup);
-    if ((stages & GPS_STAGE_COMPOSITE_BWD) && s->schedule == GPS_SCHEDULE_PER_GAUSSIAN) {
-      e = launch_composite_bwd_per_gaussian(vb, g->M, s->eps_depth, s->lambda_depth, dloss,
-                                            s->instrument ? 1 : 0, st);
-    } else if (stages & GPS_STAGE_COMPOSITE_BWD) {
-      for (int j = 0; j < vb.n && e == cudaSuccess && !s->deterministic; ++j)
-        e = cudaMemsetAsync(vb.v[j].grad2d, 0, (size_t)g->M * 48, st);
-      if (e == cudaSuccess)
-        e = launch_composite_bwd(vb, vb.v[0].tw, vb.v[0].th, s->eps_depth, s->lambda_depth, dloss,
-                                 s->blend_mode, s->deterministic ? 1 : 0, s->instrument ? 1 : 0,
-                                 depth_sorted(*s), st);
-      if (e == cudaSuccess && s->deterministic && g->M > 0) e = launch_gather_pair_grads(vb, g->M, st);
-    }
+    e = composite_backward(vb, g->M, s, stages, dloss, st);
     if (e == cudaSuccess && (stages & GPS_STAGE_PROJECT_BWD) && g->M > 0)
       e = launch_project_backward(*g, s->near_plane, vb, *grads, st);
   }
   return e == cudaSuccess ? GPS_OK : cuda_fail(e, "render_backward");
 }
 
+int32_t render_backward_adam(GpsGaussians* g, const GpsView* views, int32_t n_views,
+                             const GpsRenderSettings* s, void* ws, size_t ws_bytes,
+                             const float* dloss, GpsGaussians* m, GpsGaussians* v,
+                             const GpsAdamHyper* hyper, int32_t step, int32_t* device_step,
+                             void* stream) {
+  if (int32_t e = check_render_args(g, views, n_views, s, ws, ws_bytes)) return e;
+  if (n_views > kMaxBatch)
+    return fail(GPS_ERR_INVALID_ARG, "render_backward_adam takes at most %d views", kMaxBatch);
+  const int stages = s->stages ? s->stages : 0x1f;
+  if (!(stages & GPS_STAGE_PROJECT_BWD))
+    return fail(GPS_ERR_INVALID_ARG, "render_backward_adam needs the GPS_STAGE_PROJECT_BWD stage");
+  if (int32_t e = check_backward_views(views, n_views)) return e;
+  if (int32_t e = check_adam(g, m, v, hyper, step, device_step)) return e;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ViewBatch vb;
+  int max_nsup = 0;
+  make_batch(g->M, views, n_views, s, static_cast<char*>(ws), 0, vb, max_nsup);
+  cudaError_t e = composite_backward(vb, g->M, s, stages, dloss, st);
+  if (e == cudaSuccess && g->M > 0)
+    e = launch_project_backward_adam(*g, s->near_plane, vb, *m, *v, *hyper, step, device_step, st);
+  return e == cudaSuccess ? GPS_OK : cuda_fail(e, "render_backward_adam");
+}
+
 int32_t adam_step(GpsGaussians* params, GpsGaussians* grads, GpsGaussians* m, GpsGaussians* v,
                   const GpsAdamHyper* hyper, int32_t step, int32_t* device_step, void* stream) {
   if (int32_t e = check_gaussians(params, "params")) return e;
   if (int32_t e = check_gaussians(grads, "grads")) return e;
-  if (int32_t e = check_gaussians(m, "m")) return e;
-  if (int32_t e = check_gaussians(v, "v")) return e;
-  if (grads->M != params->M || m->M != params->M || v->M != params->M)
-    return fail(GPS_ERR_INVALID_ARG, "group sizes differ");
-  if (grads->sh_degree != params->sh_degree || m->sh_degree != params->sh_degree ||
-      v->sh_degree != params->sh_degree)
-    return fail(GPS_ERR_INVALID_ARG, "SH degrees differ");
-  if (!hyper) return fail(GPS_ERR_INVALID_ARG, "hyper is NULL");
-  if (step <= 0 && !device_step) return fail(GPS_ERR_INVALID_ARG, "step <= 0 needs device_step");
-  if (!(hyper->beta1 >= 0 && hyper->beta1 < 1 && hyper->beta2 >= 0 && hyper->beta2 < 1 && hyper->eps >= 0))
-    return fail(GPS_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+  if (grads->M != params->M) return fail(GPS_ERR_INVALID_ARG, "group sizes differ");
+  if (grads->sh_degree != params->sh_degree) return fail(GPS_ERR_INVALID_ARG, "SH degrees differ");
+  if (int32_t e = check_adam(params, m, v, hyper, step, device_step)) return e;
   cudaError_t e = launch_adam(*params, *grads, *m, *v, *hyper, step, device_step,
                               static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? GPS_OK : cuda_fail(e, "adam_step");

@@ -4,10 +4,15 @@
 // super-tiles touched and reserves the block's ranges (first half of the binning).
 #include <cuda_runtime.h>
 
+#include <cmath>
+
+#include "adam.cuh"
 #include "gps_common.cuh"
 #include "sh.cuh"
 
 namespace gps {
+
+cudaError_t launch_adam_step_advance(int* device_step, cudaStream_t st);  // adam.cu
 
 struct Params {
   const float* means;
@@ -374,7 +379,7 @@ __device__ __forceinline__ void project_adjoint(const ProjState& o, const Cam& c
 // DEG > 0 the block stages its Gaussians' SH rows and their gradient rows in
 // shared memory (2 x 256 x STRIDE floats).
 template <int DEG>
-__global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, float near_,
+__global__ void __launch_bounds__(256, DEG == 0 ? 3 : 2) project_backward_kernel(Params P, int M, float near_,
                                                                const __grid_constant__ ViewBatch vb,
                                                                GpsGaussians grads) {
   chain_wait();
@@ -392,7 +397,6 @@ __global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, 
   }
   const int i = (int)base + threadIdx.x;
   ParamGrad a{};
-  bool any = false;
   for (int k = 0; k < vb.n && i < M; ++k) {
     const Cam cam = vb.v[k].cam;
     ProjState o;
@@ -409,27 +413,191 @@ __global__ void __launch_bounds__(256) project_backward_kernel(Params P, int M, 
       a.mean[1] += gm.y;
       a.mean[2] += gm.z;
     }
-    any = true;
   }
-  if (any) {
+  // grads += a, through shared memory and coalesced over each group's
+  // contiguous [256 x width] slice, all loads before the first store
+  constexpr int kRow = kProjThreads + 1;
+  __shared__ float s_grad[14 * kRow];
+  {
+    const float comp[14] = {a.mean[0], a.mean[1], a.mean[2], a.ls[0], a.ls[1], a.ls[2],
+                            a.q[0],    a.q[1],    a.q[2],    a.q[3],  a.logit, a.rgb[0],
+                            a.rgb[1],  a.rgb[2]};
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      grads.means[3 * (size_t)i + r] += a.mean[r];
-      grads.log_scales[3 * (size_t)i + r] += a.ls[r];
-      grads.rgb[3 * (size_t)i + r] += a.rgb[r];
+    for (int q = 0; q < 14; ++q) s_grad[q * kRow + threadIdx.x] = comp[q];
+  }
+  __syncthreads();
+  {
+    float* const dst[5] = {grads.means, grads.log_scales, grads.quats, grads.opacity_logits,
+                           grads.rgb};
+    constexpr int width[5] = {3, 3, 4, 1, 3};
+    constexpr int first[5] = {0, 3, 6, 10, 11};
+    float gv[14];
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int j = 0; j < width[k]; ++j, ++q) {
+        const int e = j * kProjThreads + threadIdx.x;
+        if (e < n_blk * width[k]) gv[q] = dst[k][(size_t)base * width[k] + e];
+      }
+    q = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int j = 0; j < width[k]; ++j, ++q) {
+        const int e = j * kProjThreads + threadIdx.x;
+        if (e < n_blk * width[k]) {
+          const int r = e / width[k], c = e - r * width[k];
+          dst[k][(size_t)base * width[k] + e] = gv[q] + s_grad[(first[k] + c) * kRow + r];
+        }
+      }
+  }
+  if constexpr (DEG > 0) add_rows<DEG>(grads.sh_rest, base, n_blk, s_g);
+}
+
+// Adam state of the fused projection adjoint + Adam step: per group (means,
+// log_scales, quats, opacity_logits, rgb, sh_rest) parameters (updated in
+// place), moments and learning rate.
+struct AdamFused {
+  float* p[6];
+  float* m[6];
+  float* v[6];
+  float lr[6];
+  float b1, b2, eps;
+  float bc1, sbc2;        // 1 - b1^t and sqrt(1 - b2^t) when the step is known on the host
+  const int* device_step; // else: step t = *device_step + 1
+};
+
+// K8 and Adam in one pass: as project_backward_kernel, but each Gaussian's
+// parameter gradient (summed over the batch's views, zero if no view sees
+// it) feeds adam_update directly instead of being added to a gradient array.
+// With the gradient array zeroed before render_backward, the same FP32
+// operations as render_backward followed by adam_step.
+template <int DEG>
+__global__ void __launch_bounds__(256, DEG == 0 ? 3 : 2) project_backward_adam_kernel(
+    Params P, int M, float near_, const __grid_constant__ ViewBatch vb, AdamFused A) {
+  chain_wait();
+  extern __shared__ float s_sh[];
+  using R = ShRows<DEG>;
+  const long long base = (long long)blockIdx.x * blockDim.x;
+  const int n_blk = (int)min((long long)blockDim.x, M - base);
+  float* s_f = s_sh;
+  float* s_g = s_sh + blockDim.x * R::STRIDE;
+  if constexpr (DEG > 0) {
+    stage_rows<DEG>(P.sh, base, n_blk, s_f);
+#pragma unroll
+    for (int j = 0; j < R::STRIDE; ++j) s_g[j * kProjThreads + threadIdx.x] = 0.0f;
+    __syncthreads();
+  }
+  const int i = (int)base + threadIdx.x;
+  ParamGrad a{};
+  for (int k = 0; k < vb.n && i < M; ++k) {
+    const Cam cam = vb.v[k].cam;
+    ProjState o;
+    project_gaussian(P, i, cam, near_, o);
+    if (!o.vis) continue;
+    const float4* g2 = vb.v[k].grad2d + 3 * (size_t)i;
+    const float4 ga = g2[0], gb = g2[1], gc = g2[2];
+    project_adjoint(o, cam, ga, gb, gc, a);
+    if constexpr (DEG > 0) {
+      const float3 gm = view_colour_adjoint<DEG>(P, i, cam, make_float3(gb.z, gb.w, gc.x),
+                                                 s_f + threadIdx.x * R::STRIDE,
+                                                 s_g + threadIdx.x * R::STRIDE);
+      a.mean[0] += gm.x;
+      a.mean[1] += gm.y;
+      a.mean[2] += gm.z;
     }
-    float4* dq = reinterpret_cast<float4*>(grads.quats) + i;
-    float4 q = *dq;
-    q.x += a.q[0];
-    q.y += a.q[1];
-    q.z += a.q[2];
-    q.w += a.q[3];
-    *dq = q;
-    grads.opacity_logits[i] += a.logit;
+  }
+  float bc1 = A.bc1, sbc2 = A.sbc2;
+  if (A.device_step) adam_bias(*A.device_step + 1, A.b1, A.b2, bc1, sbc2);
+  // The block's 14 gradient components go through shared memory
+  // (component-major, 257-float rows against bank conflicts), and the Adam
+  // update then walks each group's contiguous [256 x width] slice with
+  // consecutive threads on consecutive floats: coalesced, and the adjoint's
+  // registers are free again.  The gradient is taken as render_backward
+  // leaves it in a zeroed array: 0 + a.
+  constexpr int kRow = kProjThreads + 1;
+  __shared__ float s_grad[14 * kRow];
+  {
+    const float comp[14] = {a.mean[0], a.mean[1], a.mean[2], a.ls[0], a.ls[1], a.ls[2],
+                            a.q[0],    a.q[1],    a.q[2],    a.q[3],  a.logit, a.rgb[0],
+                            a.rgb[1],  a.rgb[2]};
+#pragma unroll
+    for (int q = 0; q < 14; ++q) s_grad[q * kRow + threadIdx.x] = 0.0f + comp[q];
+  }
+  __syncthreads();
+  {
+    constexpr int width[5] = {3, 3, 4, 1, 3};
+    constexpr int first[5] = {0, 3, 6, 10, 11};  // first component of each group
+    constexpr int NP = 14;
+    float pr[NP], mr[NP], vr[NP];
+    // all loads first (in flight together), then the updates and stores
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int j = 0; j < width[k]; ++j, ++q) {
+        const int e = j * kProjThreads + threadIdx.x;
+        if (e < n_blk * width[k]) {
+          const size_t x = (size_t)base * width[k] + e;
+          pr[q] = A.p[k][x];
+          mr[q] = A.m[k][x];
+          vr[q] = A.v[k][x];
+        }
+      }
+    q = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float step_size = A.lr[k] / bc1;
+#pragma unroll
+      for (int j = 0; j < width[k]; ++j, ++q) {
+        const int e = j * kProjThreads + threadIdx.x;
+        if (e < n_blk * width[k]) {
+          const int r = e / width[k], c = e - r * width[k];
+          adam_update(pr[q], s_grad[(first[k] + c) * kRow + r], mr[q], vr[q], A.b1, A.b2, A.eps,
+                      step_size, sbc2);
+          const size_t x = (size_t)base * width[k] + e;
+          A.p[k][x] = pr[q];
+          A.m[k][x] = mr[q];
+          A.v[k][x] = vr[q];
+        }
+      }
+    }
   }
   if constexpr (DEG > 0) {
+    // the block's SH rows, coalesced as in add_rows, in chunks of CH floats
+    // per thread whose loads are in flight together
     __syncthreads();
-    add_rows<DEG>(grads.sh_rest, base, n_blk, s_g);
+    const float step_size = A.lr[5] / bc1;
+    const int total = n_blk * R::K3;
+    constexpr int CH = 16;
+#pragma unroll
+    for (int j0 = 0; j0 < R::K3; j0 += CH) {
+      float pr[CH], mr[CH], vr[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int e = (j0 + u) * kProjThreads + threadIdx.x;
+        if (j0 + u < R::K3 && e < total) {
+          const size_t x = (size_t)base * R::K3 + e;
+          pr[u] = A.p[5][x];
+          mr[u] = A.m[5][x];
+          vr[u] = A.v[5][x];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int e = (j0 + u) * kProjThreads + threadIdx.x;
+        if (j0 + u < R::K3 && e < total) {
+          const int r = e / R::K3;
+          const size_t x = (size_t)base * R::K3 + e;
+          adam_update(pr[u], 0.0f + s_g[r * R::STRIDE + (e - r * R::K3)], mr[u], vr[u], A.b1,
+                      A.b2, A.eps, step_size, sbc2);
+          A.p[5][x] = pr[u];
+          A.m[5][x] = mr[u];
+          A.v[5][x] = vr[u];
+        }
+      }
+    }
   }
 }
 
@@ -462,6 +630,60 @@ cudaError_t launch_project_backward_t(const Params& P, int M, float near_, const
   launch_chained(project_backward_kernel<DEG>, dim3((M + kProjThreads - 1) / kProjThreads), dim3(kProjThreads), smem, st,
       P, M, near_, vb, grads);
   return cudaGetLastError();
+}
+
+template <int DEG>
+cudaError_t launch_project_backward_adam_t(const Params& P, int M, float near_,
+                                           const ViewBatch& vb, const AdamFused& A,
+                                           cudaStream_t st) {
+  const size_t smem = DEG > 0 ? 2 * kProjThreads * ShRows<DEG>::STRIDE * 4 : 0;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(project_backward_adam_kernel<DEG>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  launch_chained(project_backward_adam_kernel<DEG>, dim3((M + kProjThreads - 1) / kProjThreads),
+                 dim3(kProjThreads), smem, st, P, M, near_, vb, A);
+  return cudaGetLastError();
+}
+
+// Fused projection adjoint + Adam (one batch of views); afterwards the device
+// step counter advances when the step is read on the device.
+cudaError_t launch_project_backward_adam(const GpsGaussians& g, float near_, const ViewBatch& vb,
+                                         const GpsGaussians& Mo, const GpsGaussians& Vo,
+                                         const GpsAdamHyper& h, int step, int* device_step,
+                                         cudaStream_t st) {
+  const Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb, g.sh_rest, g.sh_degree};
+  AdamFused A{};
+  float* const pp[6] = {g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb, g.sh_rest};
+  float* const mm[6] = {Mo.means, Mo.log_scales, Mo.quats, Mo.opacity_logits, Mo.rgb, Mo.sh_rest};
+  float* const vv[6] = {Vo.means, Vo.log_scales, Vo.quats, Vo.opacity_logits, Vo.rgb, Vo.sh_rest};
+  for (int k = 0; k < 6; ++k) {
+    A.p[k] = pp[k];
+    A.m[k] = mm[k];
+    A.v[k] = vv[k];
+    A.lr[k] = k < 5 ? h.lr[k] : h.lr_sh_rest;
+  }
+  A.b1 = h.beta1;
+  A.b2 = h.beta2;
+  A.eps = h.eps;
+  if (step > 0) {
+    A.bc1 = (float)(1.0 - std::pow((double)h.beta1, (double)step));
+    A.sbc2 = (float)std::sqrt(1.0 - std::pow((double)h.beta2, (double)step));
+    A.device_step = nullptr;
+  } else {
+    A.device_step = device_step;
+  }
+  cudaError_t e = cudaSuccess;
+  switch (g.sh_degree) {
+    case 1: e = launch_project_backward_adam_t<1>(P, g.M, near_, vb, A, st); break;
+    case 2: e = launch_project_backward_adam_t<2>(P, g.M, near_, vb, A, st); break;
+    case 3: e = launch_project_backward_adam_t<3>(P, g.M, near_, vb, A, st); break;
+    default: e = launch_project_backward_adam_t<0>(P, g.M, near_, vb, A, st); break;
+  }
+  if (e == cudaSuccess && step <= 0) e = launch_adam_step_advance(device_step, st);
+  return e;
 }
 
 cudaError_t launch_project(const GpsGaussians& g, float near_, const ViewBatch& vb, int max_nsup,

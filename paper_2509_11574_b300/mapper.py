@@ -31,7 +31,8 @@ from . import (LR_APP_C, PREC_DTYPE, GpsEditSettings, GpsIcpSettings, GpsRenderS
                edit_settings, fuse_frame, fuse_frame_hashed, gps_edit_scratch_size,
                gps_is_keyframe, gps_query_status, gps_select_views, gps_workspace_size,
                insert_gaussians, raycast_sdf, raycast_sdf_hashed, remove_gaussians,
-               render_backward, render_forward, settings as render_settings, view_schedule)
+               render_backward, render_backward_adam, render_forward,
+               settings as render_settings, view_schedule)
 from . import GPS_OK, GpsError
 
 MAX_VIEWS_PER_CALL = 8  # views one render_forward / render_backward call takes
@@ -209,15 +210,23 @@ class Mapper:
         self.loss.zero_()
         if self.M > 0:
             for it in range(self.iterations):
-                for b in range(0, len(views), MAX_VIEWS_PER_CALL):
-                    k = b // MAX_VIEWS_PER_CALL
-                    part = views[b:b + MAX_VIEWS_PER_CALL]
-                    render_forward(g, part, self.s, self.ws, self.loss_parts[k:k + 1])
-                    render_backward(g, part, self.s, self.ws, gr, None)
+                if len(views) <= MAX_VIEWS_PER_CALL:
+                    # one call per stage for all views; the backward feeds Adam
+                    # directly (render_backward_adam)
+                    render_forward(g, views, self.s, self.ws, self.loss_parts[:1])
+                    self.t += 1
+                    render_backward_adam(g, views, self.s, self.ws, m, v, self.lr, 0.9, 0.999,
+                                         1e-15, self.t)
+                else:
+                    for b in range(0, len(views), MAX_VIEWS_PER_CALL):
+                        k = b // MAX_VIEWS_PER_CALL
+                        part = views[b:b + MAX_VIEWS_PER_CALL]
+                        render_forward(g, part, self.s, self.ws, self.loss_parts[k:k + 1])
+                        render_backward(g, part, self.s, self.ws, gr, None)
+                    self.t += 1
+                    adam_step(g, gr, m, v, self.lr, 0.9, 0.999, 1e-15, self.t, None)
                 if it == 0 or it == self.iterations - 1:
                     self.loss[min(it, 1)] = self.loss_parts.sum()
-                self.t += 1
-                adam_step(g, gr, m, v, self.lr, 0.9, 0.999, 1e-15, self.t, None)
         st = gps_query_status(self.ws)
         if st != GPS_OK:
             raise GpsError(st, "device status after the optimisation")

@@ -175,6 +175,25 @@ def test_invalid_arguments_fail_before_launch(L):
     h = gps.GpsAdamHyper((ctypes.c_float * 5)(*gps.LR_APP_C), 0.9, 0.999, 1e-15)
     assert L.adam_step(ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(gz),
                        ctypes.byref(h), 0, None, None) == gps.GPS_ERR_INVALID_ARG
+    # the fused backward + Adam: one batch of at most 8 views, every stage,
+    # targets or upstream gradients, and adam_step's own checks
+    v9 = (gps.GpsView * 9)(*[gps.GpsView(K, P, fake, fake, fake, fake) for _ in range(9)])
+    assert L.render_backward_adam(ctypes.byref(gz), v9, 9, ctypes.byref(s), fake, 1 << 30, None,
+                                  ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(h), 1, None,
+                                  None) == gps.GPS_ERR_INVALID_ARG
+    assert b"at most 8 views" in L.gps_last_error()
+    staged = gps.settings()
+    staged.stages = gps.STAGE_COMPOSITE_BWD   # the Adam step needs the projection adjoint
+    assert L.render_backward_adam(ctypes.byref(gz), v9, 1, ctypes.byref(staged), fake, 1 << 30,
+                                  None, ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(h), 1,
+                                  None, None) == gps.GPS_ERR_INVALID_ARG
+    assert L.render_backward_adam(ctypes.byref(gz), v, 1, ctypes.byref(s), fake, 1 << 30, None,
+                                  ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(h), 1, None,
+                                  None) == gps.GPS_ERR_INVALID_ARG  # no targets, no gradients
+    assert L.render_backward_adam(ctypes.byref(gz), v9, 1, ctypes.byref(s), fake, 1 << 30, None,
+                                  ctypes.byref(gz), ctypes.byref(gz), ctypes.byref(h), 0, None,
+                                  None) == gps.GPS_ERR_INVALID_ARG  # step 0 without device_step
+    assert b"device_step" in L.gps_last_error()
 
 
 def test_layout_helpers_roundtrip():
