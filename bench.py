@@ -375,11 +375,12 @@ class GpuPipeline:
 def kernels_per_step(mode, tile, schedule="tiles", deterministic=False, fused=True):
     # fuse, raycast + per iteration: project, scan, emit, [sort + split where the
     # lists are depth-sorted], composite, finalize, composite_bwd [deterministic:
-    # + pair gather; per-Gaussian schedule: pixel terms + per-Gaussian],
+    # + slot placement and pair gather; per-Gaussian schedule: pixel terms +
+    # per-Gaussian],
     # projection adjoint + Adam (fused: one kernel, else two), step counter
     tiles = schedule != "per-gaussian"
     split = 1 if tiles and (mode == "alpha" or deterministic) else 0
-    extra = 1 if (tiles and deterministic) or not tiles else 0
+    extra = 2 if tiles and deterministic else (0 if tiles else 1)
     return 2 + ITERS_PER_FRAME * (8 + split + extra + (0 if fused else 1))
 
 

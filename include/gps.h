@@ -234,7 +234,8 @@ typedef struct GpsWorkspaceLayout {
                            tested, backward counted (instrument = 1)          */
   size_t grad2d;        /* float [M][12]                                      */
   size_t pair_grads;    /* float [tiles per super-tile * pair_capacity][12]
-                           (deterministic mode)                               */
+                           (deterministic mode): one slot per (tile,
+                           Gaussian) pair, Gaussian-major (see pair_base)     */
   size_t pix_grad;      /* float [H*W][8] per-pixel upstream terms of the
                            per-Gaussian backward (GPS_SCHEDULE_PER_GAUSSIAN):
                            dL/dC* / N, dL/dD* / N, sum dL/d(C*, D*) (C*, D*) / N,
@@ -244,6 +245,9 @@ typedef struct GpsWorkspaceLayout {
                            tiles); 0 with tile bins                           */
   int32_t tile_bins;    /* 1: the bins are the tiles (unsorted lists)         */
   int64_t pair_capacity;
+  size_t pair_base;     /* uint32 [M] (deterministic mode): Gaussian i's first
+                           pair_grads slot; its slots follow in row-major
+                           order of the tiles of its rectangle                */
 } GpsWorkspaceLayout;
 
 /* ---------------------------------------------------------------- calls */

@@ -31,6 +31,7 @@ cudaError_t launch_composite_bwd(const ViewBatch&, int, int, float, float, const
                                  int, int, cudaStream_t);
 cudaError_t launch_finalize_loss(const ViewBatch&, float, float*, int, cudaStream_t);
 cudaError_t launch_gather_pair_grads(const ViewBatch&, int, cudaStream_t);
+cudaError_t launch_pair_base(const ViewBatch&, int, const int*, cudaStream_t);
 cudaError_t launch_adam(const GpsGaussians&, const GpsGaussians&, const GpsGaussians&,
                         const GpsGaussians&, const GpsAdamHyper&, int, int*, cudaStream_t);
 cudaError_t launch_project_backward_adam(const GpsGaussians&, float, const ViewBatch&,
@@ -159,6 +160,8 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     off = align256(off + (s->deterministic ? (size_t)cap * per_super * 48 : 0));
     L.pix_grad = off;
     off = align256(off + (s->schedule == GPS_SCHEDULE_PER_GAUSSIAN ? npx * 32 : 0));
+    L.pair_base = off;
+    off = align256(off + (s->deterministic ? (size_t)M * 4 : 0));
     L.tiles_x = tx;
     L.tiles_y = ty;
     L.tile_w = tc.tw;
@@ -240,6 +243,11 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int 
   v.grad2d = reinterpret_cast<float4*>(ws + L.grad2d);
   v.pair_grads = reinterpret_cast<float4*>(ws + L.pair_grads);
   v.pix_g = reinterpret_cast<float4*>(ws + L.pix_grad);
+  v.pair_base = reinterpret_cast<uint32_t*>(ws + L.pair_base);
+  {
+    const int sp = 1 << super_shift_for(L.tile_w);
+    v.pair_slots = L.pair_capacity * ((sp / L.tile_w) * (sp / L.tile_h));
+  }
   v.tiles_x = L.tiles_x;
   v.tiles_y = L.tiles_y;
   v.tw = L.tile_w;
@@ -312,15 +320,20 @@ int32_t check_render_args(const GpsGaussians* g, const GpsView* views, int32_t n
 }
 
 // The composite adjoint of one batch of views, into the views' grad2d.
+// Deterministic mode first places each Gaussian's pair slots (pair_base),
+// writes every pair's gradient into its slot and sums each Gaussian's slots
+// in order.
 cudaError_t composite_backward(const ViewBatch& vb, int M, const GpsRenderSettings* s, int stages,
-                               const float* dloss, cudaStream_t st) {
+                               const float* dloss, const int* status, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if ((stages & GPS_STAGE_COMPOSITE_BWD) && s->schedule == GPS_SCHEDULE_PER_GAUSSIAN) {
     e = launch_composite_bwd_per_gaussian(vb, M, s->eps_depth, s->lambda_depth, dloss,
                                           s->instrument ? 1 : 0, st);
   } else if (stages & GPS_STAGE_COMPOSITE_BWD) {
-    for (int j = 0; j < vb.n && e == cudaSuccess && !s->deterministic; ++j)
-      e = cudaMemsetAsync(vb.v[j].grad2d, 0, (size_t)M * 48, st);
+    for (int j = 0; j < vb.n && e == cudaSuccess; ++j)
+      e = s->deterministic ? cudaMemsetAsync(vb.v[j].scalars + 5, 0, sizeof(float), st)
+                           : cudaMemsetAsync(vb.v[j].grad2d, 0, (size_t)M * 48, st);
+    if (e == cudaSuccess && s->deterministic && M > 0) e = launch_pair_base(vb, M, status, st);
     if (e == cudaSuccess)
       e = launch_composite_bwd(vb, vb.v[0].tw, vb.v[0].th, s->eps_depth, s->lambda_depth, dloss,
                                s->blend_mode, s->deterministic ? 1 : 0, s->instrument ? 1 : 0,
@@ -495,7 +508,7 @@ int32_t render_backward(const GpsGaussians* g, const GpsView* views, int32_t n_v
     ViewBatch vb;
     int max_nsup = 0;
     make_batch(g->M, views, n_views, s, base, b0, vb, max_nsup);
-    e = composite_backward(vb, g->M, s, stages, dloss, st);
+    e = composite_backward(vb, g->M, s, stages, dloss, reinterpret_cast<const int*>(base), st);
     if (e == cudaSuccess && (stages & GPS_STAGE_PROJECT_BWD) && g->M > 0)
       e = launch_project_backward(*g, s->near_plane, vb, *grads, st);
   }
@@ -519,7 +532,7 @@ int32_t render_backward_adam(GpsGaussians* g, const GpsView* views, int32_t n_vi
   ViewBatch vb;
   int max_nsup = 0;
   make_batch(g->M, views, n_views, s, static_cast<char*>(ws), 0, vb, max_nsup);
-  cudaError_t e = composite_backward(vb, g->M, s, stages, dloss, st);
+  cudaError_t e = composite_backward(vb, g->M, s, stages, dloss, static_cast<const int*>(ws), st);
   if (e == cudaSuccess && g->M > 0)
     e = launch_project_backward_adam(*g, s->near_plane, vb, *m, *v, *hyper, step, device_step, st);
   return e == cudaSuccess ? GPS_OK : cuda_fail(e, "render_backward_adam");

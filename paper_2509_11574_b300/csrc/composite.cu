@@ -626,13 +626,36 @@ __device__ __forceinline__ float loss_scale(const ViewDev& v, int fused, const f
   return (nv > 0.f ? 1.0f / nv : 0.f) * (dloss ? *dloss : 1.0f);
 }
 
-__device__ __forceinline__ void store_grad2d(const ViewDev& v, int deterministic, uint32_t k,
+// Deterministic mode: the pair_grads slot of the pair (tile (tx, ty),
+// Gaussian gi): the Gaussian's first slot (pair_base) + the tile's row-major
+// index inside the Gaussian's tile rectangle (from its record: centre mx, my,
+// extents ex, ey).
+__device__ __forceinline__ long long pair_slot(const ViewDev& v, uint32_t gi, int tx, int ty,
+                                               float mx, float my, float ex, float ey) {
+  int x0, x1, y0, y1;
+  record_rect(mx, my, ex, ey, v.cam.W, v.cam.H, x0, x1, y0, y1);
+  const int tx0 = x0 / v.tw, tx1 = x1 / v.tw, ty0 = y0 / v.th;
+  return (long long)v.pair_base[gi] + (long long)(ty - ty0) * (tx1 - tx0 + 1) + (tx - tx0);
+}
+
+__device__ __forceinline__ void zero_slot(const ViewDev& v, long long slot) {
+  if (slot < v.pair_slots) {
+    float4* o = v.pair_grads + 3 * slot;
+    o[0] = o[1] = o[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// 2D gradient g of a (tile, Gaussian gi) pair: deterministic mode writes it
+// into the pair's slot (skipped beyond the slot capacity), else adds it to
+// grad2d with vector atomics.
+__device__ __forceinline__ void store_grad2d(const ViewDev& v, int deterministic, long long slot,
                                              uint32_t gi, const float (&g)[10]) {
   const float4 a = make_float4(g[0], g[1], g[2], g[3]);
   const float4 b = make_float4(g[4], g[5], g[6], g[7]);
   const float4 c = make_float4(g[8], g[9], 0.f, 0.f);
   if (deterministic) {
-    float4* o = v.pair_grads + 3 * (size_t)k;
+    if (slot >= v.pair_slots) return;
+    float4* o = v.pair_grads + 3 * slot;
     o[0] = a;
     o[1] = b;
     o[2] = c;
@@ -902,9 +925,12 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
       }
       if (any || deterministic) {
         const float4 A = s_a[t], B = s_b[t];
+        const float2 E = s_e[t];
+        const uint32_t gi = (uint32_t)v.keys[b + t];
         float g[10];
         grad2d_of(m, B.x, 0.5f * B.y, B.z, A.w, g);
-        store_grad2d(v, deterministic, b + t, (uint32_t)v.keys[b + t], g);
+        store_grad2d(v, deterministic,
+                     deterministic ? pair_slot(v, gi, tx, ty, A.x, A.y, E.x, E.y) : 0, gi, g);
       }
     }
   }
@@ -912,8 +938,9 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
   if (deterministic) {
     // pairs behind the depth cut contribute nothing; give their slots zeros
     for (uint32_t k = end + tid; k < r.y; k += NT) {
-      float4* o = v.pair_grads + 3 * (size_t)k;
-      o[0] = o[1] = o[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const uint32_t gi = (uint32_t)v.keys[k];
+      const float4 A = v.rec[4 * (size_t)gi], C = v.rec[4 * (size_t)gi + 2];
+      zero_slot(v, pair_slot(v, gi, tx, ty, A.x, A.y, C.w, v.rec[4 * (size_t)gi + 3].x));
     }
   }
 }
@@ -1193,19 +1220,61 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
         for (int w = 0; w < NW; ++w) acc += s_part[w][tid][c];
         g[c] = acc;
       }
-      store_grad2d(v, deterministic, lo + tid, s_gi[tid], g);
+      long long ps = 0;
+      if (deterministic) {
+        const uint32_t gi = s_gi[tid];
+        ps = pair_slot(v, gi, tx, ty, s_a[tid].x, s_a[tid].y, s_c[tid].w,
+                       v.rec[4 * (size_t)gi + 3].x);
+      }
+      store_grad2d(v, deterministic, ps, s_gi[tid], g);
     }
   }
   if (deterministic) {
     for (uint32_t k = top + tid; k < r.y; k += NT) {
-      float4* o = v.pair_grads + 3 * (size_t)k;
-      o[0] = o[1] = o[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const uint32_t gi = (uint32_t)v.keys[k];
+      const float4 A = v.rec[4 * (size_t)gi], C = v.rec[4 * (size_t)gi + 2];
+      zero_slot(v, pair_slot(v, gi, tx, ty, A.x, A.y, C.w, v.rec[4 * (size_t)gi + 3].x));
     }
   }
 }
 
-// Deterministic mode: per Gaussian, sum its pair slots in row-major tile order.
-// Block row blockIdx.y: view.
+// Deterministic mode, before the backward: the first pair_grads slot of each
+// Gaussian, its rectangle's tile count after those of the Gaussians placed
+// before it (warp prefix sums, one atomic per warp on the view's counter,
+// scalars[5], zero on entry).  The placement varies with the atomics' order;
+// the sums do not, as each Gaussian's slots are summed in its own tile order.
+// If the forward overflowed the pair capacity, some lists lost pairs whose
+// slots nothing writes: then the Gaussian's slots are zeroed here first.
+__global__ void __launch_bounds__(256) pair_base_kernel(const __grid_constant__ ViewBatch vb,
+                                                        int M, const int* status) {
+  chain_wait();
+  const ViewDev& v = vb.v[blockIdx.y];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+  int cnt = 0;
+  if (i < M) {
+    const float4 A = v.rec[4 * (size_t)i], C = v.rec[4 * (size_t)i + 2];
+    int x0, x1, y0, y1;
+    if (record_rect(A.x, A.y, C.w, v.rec[4 * (size_t)i + 3].x, v.cam.W, v.cam.H, x0, x1, y0, y1))
+      cnt = (x1 / v.tw - x0 / v.tw + 1) * (y1 / v.th - y0 / v.th + 1);
+  }
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  uint32_t base = 0;
+  if (lane == 31) base = atomicAdd(reinterpret_cast<uint32_t*>(v.scalars + 5), (uint32_t)incl);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  if (i >= M) return;
+  const uint32_t first = base + (uint32_t)(incl - cnt);
+  v.pair_base[i] = first;
+  if (*status == GPS_ERR_CAPACITY)
+    for (int k = 0; k < cnt; ++k) zero_slot(v, (long long)first + k);
+}
+
+// Deterministic mode: per Gaussian, sum its pair slots in row-major tile
+// order (contiguous from pair_base).  Block row blockIdx.y: view.
 __global__ void __launch_bounds__(256) gather_pair_grads_kernel(const __grid_constant__ ViewBatch vb,
                                                                 int M) {
   chain_wait();
@@ -1216,24 +1285,15 @@ __global__ void __launch_bounds__(256) gather_pair_grads_kernel(const __grid_con
   float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
   int x0, x1, y0, y1;
   if (record_rect(A.x, A.y, C.w, E.x, v.cam.W, v.cam.H, x0, x1, y0, y1)) {
-    const unsigned long long key = key_of(A.z, (uint32_t)i);
-    for (int ty = y0 / v.th; ty <= y1 / v.th; ++ty)
-      for (int tx = x0 / v.tw; tx <= x1 / v.tw; ++tx) {
-        const uint2 r = v.tile_ranges[ty * v.tiles_x + tx];
-        uint32_t lo = r.x, hi = r.y;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (v.keys[mid] < key) lo = mid + 1;
-          else hi = mid;
-        }
-        if (lo < r.y && v.keys[lo] == key) {
-          const float4* p = v.pair_grads + 3 * (size_t)lo;
-          const float4 a = p[0], b = p[1], c = p[2];
-          s0.x += a.x; s0.y += a.y; s0.z += a.z; s0.w += a.w;
-          s1.x += b.x; s1.y += b.y; s1.z += b.z; s1.w += b.w;
-          s2.x += c.x; s2.y += c.y;
-        }
-      }
+    const int cnt = (x1 / v.tw - x0 / v.tw + 1) * (y1 / v.th - y0 / v.th + 1);
+    const long long first = v.pair_base[i];
+    for (int k = 0; k < cnt && first + k < v.pair_slots; ++k) {
+      const float4* p = v.pair_grads + 3 * (first + k);
+      const float4 a = p[0], b = p[1], c = p[2];
+      s0.x += a.x; s0.y += a.y; s0.z += a.z; s0.w += a.w;
+      s1.x += b.x; s1.y += b.y; s1.z += b.z; s1.w += b.w;
+      s2.x += c.x; s2.y += c.y;
+    }
   }
   float4* o = v.grad2d + 3 * (size_t)i;
   o[0] = s0;
@@ -1426,6 +1486,11 @@ cudaError_t launch_composite_bwd(const ViewBatch& vb, int tw, int th, float eps,
 cudaError_t launch_finalize_loss(const ViewBatch& vb, float lambda, float* loss, int first,
                                  cudaStream_t st) {
   launch_chained(finalize_loss_kernel, dim3(1), dim3(256), 0, st, vb, lambda, loss, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_base(const ViewBatch& vb, int M, const int* status, cudaStream_t st) {
+  launch_chained(pair_base_kernel, dim3((M + 255) / 256, vb.n), dim3(256), 0, st, vb, M, status);
   return cudaGetLastError();
 }
 

@@ -67,7 +67,9 @@ struct ViewDev {
   float4* tile_partials;  // [tiles] (sum|dC|, sum|dD|, n_valid, -)
   float* scalars;         // [8]
   float4* grad2d;         // [M][3] float4
-  float4* pair_grads;     // [cap][3] float4
+  float4* pair_grads;     // [pair_slots][3] float4, Gaussian-major (deterministic mode)
+  uint32_t* pair_base;    // [M] first slot of each Gaussian (deterministic mode)
+  long long pair_slots;
   float4* pix_g;          // [npx][2] per-Gaussian backward: (h), (sv, thr, -, -)
   int tiles_x, tiles_y, tw, th;
   // bins of the binning pass (sup_x * sup_y of them, 2^bin_sx x 2^bin_sy
