@@ -30,14 +30,14 @@ struct AdamArgs {
   AdamGroup grp[kAdamGroups];
   long long first_block[kAdamGroups + 1];  // block offsets per group (empty groups: n = 0)
   float b1, b2, eps;
-  float bc1, sbc2;  // 1 - b1^t and sqrt(1 - b2^t) when the step is known on the host
+  float bc1, inv_sbc2;  // 1 - b1^t and 1 / sqrt(1 - b2^t) when the step is known on the host
   int* device_step; // else: step t = *device_step + 1
 };
 
 __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   chain_wait();
-  float bc1 = a.bc1, sbc2 = a.sbc2;
-  if (a.device_step) adam_bias(*a.device_step + 1, a.b1, a.b2, bc1, sbc2);
+  float bc1 = a.bc1, inv_sbc2 = a.inv_sbc2;
+  if (a.device_step) adam_bias(*a.device_step + 1, a.b1, a.b2, bc1, inv_sbc2);
   const long long blk = blockIdx.x;
   int gidx = 0;
 #pragma unroll
@@ -53,10 +53,10 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
     const float4 g = *reinterpret_cast<float4*>(G.g + base);
     float4 m = *reinterpret_cast<float4*>(G.m + base);
     float4 v = *reinterpret_cast<float4*>(G.v + base);
-    adam_update(p.x, g.x, m.x, v.x, b1, b2, eps, step_size, sbc2);
-    adam_update(p.y, g.y, m.y, v.y, b1, b2, eps, step_size, sbc2);
-    adam_update(p.z, g.z, m.z, v.z, b1, b2, eps, step_size, sbc2);
-    adam_update(p.w, g.w, m.w, v.w, b1, b2, eps, step_size, sbc2);
+    adam_update(p.x, g.x, m.x, v.x, b1, b2, eps, step_size, inv_sbc2);
+    adam_update(p.y, g.y, m.y, v.y, b1, b2, eps, step_size, inv_sbc2);
+    adam_update(p.z, g.z, m.z, v.z, b1, b2, eps, step_size, inv_sbc2);
+    adam_update(p.w, g.w, m.w, v.w, b1, b2, eps, step_size, inv_sbc2);
     *reinterpret_cast<float4*>(G.p + base) = p;
     *reinterpret_cast<float4*>(G.m + base) = m;
     *reinterpret_cast<float4*>(G.v + base) = v;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
   } else {
     for (long long k = base; k < min(base + 4, G.n); ++k) {
       float p = G.p[k], m = G.m[k], v = G.v[k];
-      adam_update(p, G.g[k], m, v, b1, b2, eps, step_size, sbc2);
+      adam_update(p, G.g[k], m, v, b1, b2, eps, step_size, inv_sbc2);
       G.m[k] = m;
       G.v[k] = v;
       G.p[k] = p;
@@ -117,7 +117,7 @@ cudaError_t launch_adam(const GpsGaussians& P, const GpsGaussians& Gr, const Gps
   a.eps = h.eps;
   if (step > 0) {
     a.bc1 = (float)(1.0 - std::pow((double)h.beta1, (double)step));
-    a.sbc2 = (float)std::sqrt(1.0 - std::pow((double)h.beta2, (double)step));
+    a.inv_sbc2 = (float)(1.0 / std::sqrt(1.0 - std::pow((double)h.beta2, (double)step)));
     a.device_step = nullptr;
   } else {
     a.device_step = device_step;

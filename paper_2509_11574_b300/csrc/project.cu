@@ -464,7 +464,7 @@ struct AdamFused {
   float* v[6];
   float lr[6];
   float b1, b2, eps;
-  float bc1, sbc2;        // 1 - b1^t and sqrt(1 - b2^t) when the step is known on the host
+  float bc1, inv_sbc2;    // 1 - b1^t and 1 / sqrt(1 - b2^t) when the step is known on the host
   const int* device_step; // else: step t = *device_step + 1
 };
 
@@ -508,8 +508,8 @@ __global__ void __launch_bounds__(256, DEG == 0 ? 3 : 2) project_backward_adam_k
       a.mean[2] += gm.z;
     }
   }
-  float bc1 = A.bc1, sbc2 = A.sbc2;
-  if (A.device_step) adam_bias(*A.device_step + 1, A.b1, A.b2, bc1, sbc2);
+  float bc1 = A.bc1, inv_sbc2 = A.inv_sbc2;
+  if (A.device_step) adam_bias(*A.device_step + 1, A.b1, A.b2, bc1, inv_sbc2);
   // The block's 14 gradient components go through shared memory
   // (component-major, 257-float rows against bank conflicts), and the Adam
   // update then walks each group's contiguous [256 x width] slice with
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(256, DEG == 0 ? 3 : 2) project_backward_adam_k
         if (e < n_blk * width[k]) {
           const int r = e / width[k], c = e - r * width[k];
           adam_update(pr[q], s_grad[(first[k] + c) * kRow + r], mr[q], vr[q], A.b1, A.b2, A.eps,
-                      step_size, sbc2);
+                      step_size, inv_sbc2);
           const size_t x = (size_t)base * width[k] + e;
           A.p[k][x] = pr[q];
           A.m[k][x] = mr[q];
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(256, DEG == 0 ? 3 : 2) project_backward_adam_k
           const int r = e / R::K3;
           const size_t x = (size_t)base * R::K3 + e;
           adam_update(pr[u], 0.0f + s_g[r * R::STRIDE + (e - r * R::K3)], mr[u], vr[u], A.b1,
-                      A.b2, A.eps, step_size, sbc2);
+                      A.b2, A.eps, step_size, inv_sbc2);
           A.p[5][x] = pr[u];
           A.m[5][x] = mr[u];
           A.v[5][x] = vr[u];
@@ -670,7 +670,7 @@ cudaError_t launch_project_backward_adam(const GpsGaussians& g, float near_, con
   A.eps = h.eps;
   if (step > 0) {
     A.bc1 = (float)(1.0 - std::pow((double)h.beta1, (double)step));
-    A.sbc2 = (float)std::sqrt(1.0 - std::pow((double)h.beta2, (double)step));
+    A.inv_sbc2 = (float)(1.0 / std::sqrt(1.0 - std::pow((double)h.beta2, (double)step)));
     A.device_step = nullptr;
   } else {
     A.device_step = device_step;
