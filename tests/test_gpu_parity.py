@@ -387,6 +387,16 @@ def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False, prec=gps.PREC_
           "worst (norm, elem)", worst)
 
 
+def test_end_to_end_room_bench_configuration():
+    """The bench's workload at full size (room, 640x480, 100k Gaussians, the
+    256^3 TSDF's ray-cast) in the bench's launch configuration (16x8 tiles,
+    sort-free OIT lists, the carry-over backward): every pixel, the loss and
+    every Gaussian's gradient against the FP64 oracle, with the end-to-end
+    envelopes above."""
+    w = workloads.room(n_frames=1, M=100_000)
+    _end_to_end(w, oracle.OIT, w.lambda_depth, tile=(16, 8))
+
+
 def test_deterministic_mode_is_bitwise_reproducible_and_matches():
     w = workload("small")
     f = w.frames[0]
