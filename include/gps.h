@@ -104,7 +104,8 @@ typedef struct GpsPose {
 } GpsPose;
 
 /* Dense colourised TSDF (Sec. 3.1: every voxel stores d(p) and c(p)).
- * nx, ny, nz must be positive multiples of 8.  Voxel (x, y, z) has its centre
+ * nx, ny, nz must be positive multiples of 8 (fuse_frame: ny, nz at most
+ * 8 * 65535).  Voxel (x, y, z) has its centre
  * at origin + (x + 0.5, y + 0.5, z + 0.5) * voxel and is stored at the
  * brick-major index
  *     ((bz * (ny/8) + by) * (nx/8) + bx) * 512 + (z%8) * 64 + (y%8) * 8 + (x%8),

@@ -406,6 +406,8 @@ int32_t fuse_frame(GpsTsdf* vol, const float* depth, const float* rgb, const Gps
   if (!vol || !depth || !rgb || !K || !T_wc) return fail(GPS_ERR_INVALID_ARG, "NULL argument");
   if (vol->nx <= 0 || vol->ny <= 0 || vol->nz <= 0 || vol->nx % 8 || vol->ny % 8 || vol->nz % 8)
     return fail(GPS_ERR_INVALID_ARG, "volume dims must be positive multiples of 8");
+  if ((vol->ny >> 3) > 65535 || (vol->nz >> 3) > 65535)
+    return fail(GPS_ERR_INVALID_ARG, "ny and nz must be at most 8 * 65535");
   if (!vol->sdf || !vol->weight || !vol->rgbw || !aligned(vol->rgbw, 16))
     return fail(GPS_ERR_INVALID_ARG, "volume arrays missing or rgbw not 16-byte aligned");
   if (!(vol->voxel > 0) || !(vol->trunc > 0) || !(vol->max_weight > 0))

@@ -34,12 +34,20 @@ __device__ __forceinline__ long long vox_index(const VolDev& v, int x, int y, in
 // Dense accessor of the shared sampling and ray-cast code.
 struct DenseVol : VolDev {
   __device__ __forceinline__ bool load8(int ix, int iy, int iz, float* c) const {
-    // all eight voxels in clear bricks: they hold 1, no loads
+    // all eight voxels in clear bricks: they hold 1, no loads.  The stencil
+    // spans one or two bricks per axis; each distinct brick's flag is read
+    // once (one flag for the 2 x 2 x 2 stencils inside one brick).
     if (flags) {
-      bool clear = true;
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        clear = clear && !flags[brick_of(*this, ix + (k & 1), iy + ((k >> 1) & 1), iz + (k >> 2))];
+      const int nbx = nx >> 3, nby = ny >> 3;
+      const bool dx = ((ix + 1) >> 3) != (ix >> 3), dy = ((iy + 1) >> 3) != (iy >> 3),
+                 dz = ((iz + 1) >> 3) != (iz >> 3);
+      const long long b0 = brick_of(*this, ix, iy, iz), sy = nbx, sz = (long long)nbx * nby;
+      bool clear = !flags[b0] && !(dx && flags[b0 + 1]);
+      if (dy) clear = clear && !flags[b0 + sy] && !(dx && flags[b0 + sy + 1]);
+      if (dz) {
+        clear = clear && !flags[b0 + sz] && !(dx && flags[b0 + sz + 1]);
+        if (dy) clear = clear && !flags[b0 + sz + sy] && !(dx && flags[b0 + sz + sy + 1]);
+      }
       if (clear) return false;
     }
 #pragma unroll
@@ -52,16 +60,15 @@ struct DenseVol : VolDev {
   }
 };
 
-__global__ void __launch_bounds__(256) fuse_kernel(VolDev v, const float* __restrict__ depth,
+// One CTA of 512 threads per 8^3 brick, the grid laid out as the bricks
+// (gridDim = bricks per axis), so a voxel's coordinates come from its block
+// and thread indices without integer division.
+__global__ void __launch_bounds__(512) fuse_kernel(VolDev v, const float* __restrict__ depth,
                                                    const float* __restrict__ rgb, Cam cam) {
-  const long long n = (long long)v.nx * v.ny * v.nz;
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= n) return;
-  const int local = (int)(id & 511);
-  const long long brick = id >> 9;
-  const int nbx = v.nx >> 3, nby = v.ny >> 3;
-  const int bx = (int)(brick % nbx), by = (int)((brick / nbx) % nby),
-            bz = (int)(brick / ((long long)nbx * nby));
+  const int local = threadIdx.x;
+  const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+  const long long brick = ((long long)bz * gridDim.y + by) * gridDim.x + bx;
+  const long long id = brick * 512 + local;
   const int x = (bx << 3) + (local & 7), y = (by << 3) + ((local >> 3) & 7),
             z = (bz << 3) + (local >> 6);
   float eta;
@@ -90,9 +97,8 @@ cudaError_t launch_fuse(const GpsTsdf& t, const float* depth, const float* rgb, 
                         cudaStream_t st) {
   VolDev v{t.nx, t.ny, t.nz, t.voxel, t.origin[0], t.origin[1], t.origin[2], t.trunc,
            t.max_weight, t.sdf, t.weight, reinterpret_cast<float4*>(t.rgbw), t.brick_flags};
-  const long long n = (long long)t.nx * t.ny * t.nz;
-  const unsigned blocks = (unsigned)((n + 255) / 256);
-  fuse_kernel<<<blocks, 256, 0, st>>>(v, depth, rgb, cam);
+  const dim3 grid((unsigned)(t.nx >> 3), (unsigned)(t.ny >> 3), (unsigned)(t.nz >> 3));
+  fuse_kernel<<<grid, 512, 0, st>>>(v, depth, rgb, cam);
   return cudaGetLastError();
 }
 
