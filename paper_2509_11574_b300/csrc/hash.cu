@@ -172,19 +172,30 @@ __global__ void __launch_bounds__(256) hash_candidates_kernel(HashDev h, Cam cam
   }
 }
 
+// Coordinates (in bricks) of linear brick index b (x fastest).
+__device__ __forceinline__ void brick_xyz(long long b, int nbx, int nby, int* out) {
+  const long long q = b / nbx, r = q / nby;
+  out[0] = (int)(b - q * nbx);
+  out[1] = (int)(q - r * nby);
+  out[2] = (int)r;
+}
+
 // 2. allocation: the exact band test on each candidate's voxels, then the
 // table insert and the initialisation of new bricks.  One 512-thread CTA per
 // candidate (grid-stride over the candidates).
 __global__ void __launch_bounds__(512) hash_alloc_kernel(HashDev h, Cam cam,
                                                          const float* __restrict__ depth,
                                                          CandDev c) {
-  __shared__ int s_slot, s_new;
+  __shared__ int s_slot, s_new, s_b[3];
   const int n = min(*c.count, c.max);
   const int local = threadIdx.x;
   for (int ci = blockIdx.x; ci < n; ci += gridDim.x) {
     const long long b = (long long)c.list[ci];
-    const int nbx = h.nx >> 3, nby = h.ny >> 3;
-    const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
+    // the brick's coordinates: 64-bit divisions, once per CTA
+    __syncthreads();
+    if (local == 0) brick_xyz(b, h.nx >> 3, h.ny >> 3, s_b);
+    __syncthreads();
+    const int bx = s_b[0], by = s_b[1], bz = s_b[2];
     const int x = (bx << 3) + (local & 7), y = (by << 3) + ((local >> 3) & 7),
               z = (bz << 3) + (local >> 6);
     float eta = 0.0f;
@@ -238,11 +249,15 @@ __global__ void __launch_bounds__(512) hash_alloc_kernel(HashDev h, Cam cam,
 // more than a pixel; the per-voxel test then decides exactly as fuse_frame.
 __global__ void __launch_bounds__(256) hash_fuse_kernel(HashDev h, const float* __restrict__ depth,
                                                         const float* __restrict__ rgb, Cam cam) {
+  __shared__ int s_b[3];
   const int n = min(*h.state, h.capacity);
-  const int nbx = h.nx >> 3, nby = h.ny >> 3;
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
     const long long b = h.brick_of_slot[s];
-    const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
+    // the brick's coordinates: 64-bit divisions, once per CTA
+    __syncthreads();
+    if (threadIdx.x == 0) brick_xyz(b, h.nx >> 3, h.ny >> 3, s_b);
+    __syncthreads();
+    const int bx = s_b[0], by = s_b[1], bz = s_b[2];
     int behind = 0, front = 0;
     float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
 #pragma unroll
