@@ -220,7 +220,8 @@ typedef struct GpsWorkspaceLayout {
   size_t status;        /* int32 status word (shared by all views)            */
   size_t records;       /* float [M][16]                                      */
   size_t super_counts;  /* uint32 [bins]                                      */
-  size_t block_base;    /* uint32 [ceil(M/256)][bins]                         */
+  size_t block_base;    /* uint32 [binning CTAs][bins] (a CTA takes up to 8
+                           chunks of 256 Gaussians)                           */
   size_t super_ranges;  /* uint32 [bins][2]                                   */
   size_t super_keys;    /* uint64 [pair_capacity] super-tile segments (tile
                            bins: the tile lists)                              */
