@@ -27,6 +27,7 @@ constexpr int kIcpMaxLevels = 4;
 // level l + 1 = mean of the valid depths of each 2x2 block of level l
 __global__ void icp_downsample_kernel(const float* __restrict__ src, int Ws, float* dst, int Wd,
                                       int Hd) {
+  chain_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Wd * Hd) return;
   const int x = i % Wd, y = i / Wd;
@@ -48,6 +49,7 @@ __global__ void icp_downsample_kernel(const float* __restrict__ src, int Ws, flo
 // camera-frame vertex map (x, y, z, valid)
 __global__ void icp_vertex_kernel(const float* __restrict__ depth, int W, int H, float fx,
                                   float fy, float cx, float cy, float4* __restrict__ vert) {
+  chain_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= W * H) return;
   const float z = depth[i];
@@ -60,6 +62,7 @@ __global__ void icp_vertex_kernel(const float* __restrict__ depth, int W, int H,
 __global__ void icp_pack_reference_kernel(const float* __restrict__ v3,
                                           const float* __restrict__ depth, int n,
                                           float4* __restrict__ vert) {
+  chain_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   vert[i] = depth[i] > 0.f ? make_float4(v3[3 * (size_t)i], v3[3 * (size_t)i + 1],
@@ -71,6 +74,7 @@ __global__ void icp_pack_reference_kernel(const float* __restrict__ v3,
 // valid, turned to face `centre`
 __global__ void icp_normal_kernel(const float4* __restrict__ vert, int W, int H, float ox,
                                   float oy, float oz, float4* __restrict__ norm) {
+  chain_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= W * H) return;
   const int x = i % W, y = i / W;
@@ -218,6 +222,7 @@ __device__ void icp_solve_and_update(const float* S, float* pose, float* stats) 
 }
 
 __global__ void __launch_bounds__(kIcpThreads) icp_iteration_kernel(const __grid_constant__ IcpIter a) {
+  chain_wait();
   __shared__ float s_part[kIcpThreads / 32][kIcpSums];
   __shared__ float s_sum[kIcpSums];
   __shared__ bool s_last;
@@ -416,8 +421,8 @@ int32_t icp_track(const GpsIntrinsics* K, const float* depth, const float* ref_v
   for (int l = 0; l < s->levels; ++l) {
     if (l) {
       float* d = reinterpret_cast<float*>(b + L.depth[l]);
-      gps::icp_downsample_kernel<<<blocks((size_t)L.W[l] * L.H[l]), T, 0, st>>>(
-          dl[l - 1], L.W[l - 1], d, L.W[l], L.H[l]);
+      gps::launch_chained(gps::icp_downsample_kernel, dim3(blocks((size_t)L.W[l] * L.H[l])),
+                          dim3(T), 0, st, dl[l - 1], L.W[l - 1], d, L.W[l], L.H[l]);
       dl[l] = d;
       fx *= 0.5f;
       fy *= 0.5f;
@@ -428,16 +433,18 @@ int32_t icp_track(const GpsIntrinsics* K, const float* depth, const float* ref_v
     }
     float4* v = reinterpret_cast<float4*>(b + L.vert[l]);
     const size_t n = (size_t)L.W[l] * L.H[l];
-    gps::icp_vertex_kernel<<<blocks(n), T, 0, st>>>(dl[l], L.W[l], L.H[l], fx, fy, cx, cy, v);
-    gps::icp_normal_kernel<<<blocks(n), T, 0, st>>>(v, L.W[l], L.H[l], 0.f, 0.f, 0.f,
-                                                    reinterpret_cast<float4*>(b + L.norm[l]));
+    gps::launch_chained(gps::icp_vertex_kernel, dim3(blocks(n)), dim3(T), 0, st, dl[l], L.W[l],
+                        L.H[l], fx, fy, cx, cy, v);
+    gps::launch_chained(gps::icp_normal_kernel, dim3(blocks(n)), dim3(T), 0, st, v, L.W[l], L.H[l],
+                        0.f, 0.f, 0.f, reinterpret_cast<float4*>(b + L.norm[l]));
   }
   const size_t n0 = (size_t)K->width * K->height;
   float4* rv = reinterpret_cast<float4*>(b + L.rvert);
   float4* rn = reinterpret_cast<float4*>(b + L.rnorm);
-  gps::icp_pack_reference_kernel<<<blocks(n0), T, 0, st>>>(ref_vertex, ref_depth, (int)n0, rv);
-  gps::icp_normal_kernel<<<blocks(n0), T, 0, st>>>(rv, K->width, K->height, T_ref->t[0],
-                                                   T_ref->t[1], T_ref->t[2], rn);
+  gps::launch_chained(gps::icp_pack_reference_kernel, dim3(blocks(n0)), dim3(T), 0, st,
+                      ref_vertex, ref_depth, (int)n0, rv);
+  gps::launch_chained(gps::icp_normal_kernel, dim3(blocks(n0)), dim3(T), 0, st, rv, K->width,
+                      K->height, T_ref->t[0], T_ref->t[1], T_ref->t[2], rn);
   unsigned int* ticket = reinterpret_cast<unsigned int*>(b + L.ticket);
   cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st);
   gps::IcpIter a{};
@@ -465,7 +472,7 @@ int32_t icp_track(const GpsIntrinsics* K, const float* depth, const float* ref_v
     const unsigned grid = (unsigned)std::min<size_t>(L.grid, (a.n + 2 * T - 1) / (2 * T));
     for (int it = 0; it < s->iters[l]; ++it, ++it_index) {
       a.stats = stats ? stats + 2 * it_index : nullptr;
-      gps::icp_iteration_kernel<<<grid, T, 0, st>>>(a);
+      gps::launch_chained(gps::icp_iteration_kernel, dim3(grid), dim3(T), 0, st, a);
     }
   }
   if (e == cudaSuccess) e = cudaGetLastError();
