@@ -136,6 +136,7 @@ __device__ __forceinline__ void candidate_insert(const CandDev& c, unsigned long
 __global__ void __launch_bounds__(256) hash_candidates_kernel(HashDev h, Cam cam,
                                                               const float* __restrict__ depth,
                                                               CandDev c) {
+  chain_wait();
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= cam.W * cam.H) return;
   const float D = __ldg(depth + pix);
@@ -186,6 +187,7 @@ __device__ __forceinline__ void brick_xyz(long long b, int nbx, int nby, int* ou
 __global__ void __launch_bounds__(512) hash_alloc_kernel(HashDev h, Cam cam,
                                                          const float* __restrict__ depth,
                                                          CandDev c) {
+  chain_wait();
   __shared__ int s_slot, s_new, s_b[3];
   const int n = min(*c.count, c.max);
   const int local = threadIdx.x;
@@ -249,6 +251,7 @@ __global__ void __launch_bounds__(512) hash_alloc_kernel(HashDev h, Cam cam,
 // more than a pixel; the per-voxel test then decides exactly as fuse_frame.
 __global__ void __launch_bounds__(256) hash_fuse_kernel(HashDev h, const float* __restrict__ depth,
                                                         const float* __restrict__ rgb, Cam cam) {
+  chain_wait();
   __shared__ int s_b[3];
   const int n = min(*h.state, h.capacity);
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
@@ -298,6 +301,7 @@ __global__ void __launch_bounds__(256) hash_to_dense_kernel(HashDev h, float* __
                                                             float* __restrict__ weight,
                                                             float4* __restrict__ rgbw,
                                                             uint8_t* __restrict__ flags) {
+  chain_wait();
   const int n = min(*h.state, h.capacity);
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
     const long long b = h.brick_of_slot[s];
@@ -447,9 +451,12 @@ int32_t fuse_frame_hashed(GpsHashTsdf* vol, const float* depth, const float* rgb
   const gps::Cam cam = gps::make_cam(*K, *T_wc);
   const long long npx = (long long)K->width * K->height;
   if (e == cudaSuccess) {
-    gps::hash_candidates_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(h, cam, depth, c);
-    gps::hash_alloc_kernel<<<4 * sm_count(), 512, 0, st>>>(h, cam, depth, c);
-    gps::hash_fuse_kernel<<<8 * sm_count(), 256, 0, st>>>(h, depth, rgb, cam);
+    gps::launch_chained(gps::hash_candidates_kernel, dim3((unsigned)((npx + 255) / 256)),
+                        dim3(256), 0, st, h, cam, depth, c);
+    gps::launch_chained(gps::hash_alloc_kernel, dim3(4 * sm_count()), dim3(512), 0, st, h, cam,
+                        depth, c);
+    gps::launch_chained(gps::hash_fuse_kernel, dim3(8 * sm_count()), dim3(256), 0, st, h, depth,
+                        rgb, cam);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return hash_fail(GPS_ERR_CUDA, cudaGetErrorString(e));
@@ -466,8 +473,9 @@ int32_t raycast_sdf_hashed(const GpsHashTsdf* vol, const GpsIntrinsics* K, const
   const gps::HashDev h = hash_dev(*vol);
   const gps::Cam cam = gps::make_cam(*K, *T_wc);
   dim3 grid((K->width + 15) / 16, (K->height + 15) / 16);
-  gps::raycast_kernel<gps::HashDev><<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      h, cam, near_plane, far_plane, out_rgb, rgb_precision, out_depth, out_vertex);
+  gps::launch_chained(gps::raycast_kernel<gps::HashDev>, grid, dim3(256), 0,
+                      static_cast<cudaStream_t>(stream), h, cam, near_plane, far_plane, out_rgb,
+                      rgb_precision, out_depth, out_vertex);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hash_fail(GPS_ERR_CUDA, cudaGetErrorString(e));
   return GPS_OK;
@@ -478,8 +486,9 @@ int32_t tsdf_hash_to_dense(const GpsHashTsdf* vol, GpsTsdf* dense, void* stream)
       dense->nx != vol->nx || dense->ny != vol->ny || dense->nz != vol->nz)
     return hash_fail(GPS_ERR_INVALID_ARG, "tsdf_hash_to_dense: bad volumes or sizes differ");
   const gps::HashDev h = hash_dev(*vol);
-  gps::hash_to_dense_kernel<<<8 * sm_count(), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      h, dense->sdf, dense->weight, reinterpret_cast<float4*>(dense->rgbw), dense->brick_flags);
+  gps::launch_chained(gps::hash_to_dense_kernel, dim3(8 * sm_count()), dim3(256), 0,
+                      static_cast<cudaStream_t>(stream), h, dense->sdf, dense->weight,
+                      reinterpret_cast<float4*>(dense->rgbw), dense->brick_flags);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hash_fail(GPS_ERR_CUDA, cudaGetErrorString(e));
   return GPS_OK;

@@ -65,6 +65,7 @@ struct DenseVol : VolDev {
 // and thread indices without integer division.
 __global__ void __launch_bounds__(512) fuse_kernel(VolDev v, const float* __restrict__ depth,
                                                    const float* __restrict__ rgb, Cam cam) {
+  chain_wait();
   const int local = threadIdx.x;
   const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
   const long long brick = ((long long)bz * gridDim.y + by) * gridDim.x + bx;
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(512) fuse_kernel(VolDev v, const float* __rest
 // One block per brick: flag = some voxel's sdf differs from 1.
 __global__ void __launch_bounds__(256) mark_bricks_kernel(const float* __restrict__ sdf,
                                                           uint8_t* __restrict__ flags) {
+  chain_wait();
   const float* b = sdf + (size_t)blockIdx.x * 512;
   const bool any = b[threadIdx.x] != 1.0f || b[threadIdx.x + 256] != 1.0f;
   const int n = __syncthreads_or(any);
@@ -89,7 +91,8 @@ __global__ void __launch_bounds__(256) mark_bricks_kernel(const float* __restric
 
 cudaError_t launch_mark_bricks(const GpsTsdf& t, cudaStream_t st) {
   const long long nb = ((long long)t.nx * t.ny * t.nz) >> 9;
-  if (nb > 0) mark_bricks_kernel<<<(unsigned)nb, 256, 0, st>>>(t.sdf, t.brick_flags);
+  if (nb > 0) launch_chained(mark_bricks_kernel, dim3((unsigned)nb), dim3(256), 0, st, t.sdf,
+                             t.brick_flags);
   return cudaGetLastError();
 }
 
@@ -98,7 +101,7 @@ cudaError_t launch_fuse(const GpsTsdf& t, const float* depth, const float* rgb, 
   VolDev v{t.nx, t.ny, t.nz, t.voxel, t.origin[0], t.origin[1], t.origin[2], t.trunc,
            t.max_weight, t.sdf, t.weight, reinterpret_cast<float4*>(t.rgbw), t.brick_flags};
   const dim3 grid((unsigned)(t.nx >> 3), (unsigned)(t.ny >> 3), (unsigned)(t.nz >> 3));
-  fuse_kernel<<<grid, 512, 0, st>>>(v, depth, rgb, cam);
+  launch_chained(fuse_kernel, grid, dim3(512), 0, st, v, depth, rgb, cam);
   return cudaGetLastError();
 }
 
@@ -109,7 +112,8 @@ cudaError_t launch_raycast(const GpsTsdf& t, const Cam& cam, float near_, float 
                                    t.origin[2], t.trunc, t.max_weight, t.sdf, t.weight,
                                    reinterpret_cast<float4*>(t.rgbw), t.brick_flags};
   dim3 grid((cam.W + 15) / 16, (cam.H + 15) / 16);
-  raycast_kernel<DenseVol><<<grid, 256, 0, st>>>(v, cam, near_, far_, rgb, rgb_prec, depth, vertex);
+  launch_chained(raycast_kernel<DenseVol>, grid, dim3(256), 0, st, v, cam, near_, far_, rgb,
+                 rgb_prec, depth, vertex);
   return cudaGetLastError();
 }
 

@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(256) raycast_kernel(const __grid_constant__ Vo
                                                       void* __restrict__ out_rgb, int rgb_prec,
                                                       float* __restrict__ out_depth,
                                                       float* __restrict__ out_vertex) {
+  chain_wait();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
   const int py = blockIdx.y * 16 + (warp >> 1) * 4 + (lane >> 3);

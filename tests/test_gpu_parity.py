@@ -254,9 +254,16 @@ def test_composite_forward_and_backward_staged(mode, tile):
     # exponent argument and ex2), which 1 / (1 - alpha) <= 100 amplifies for
     # every near-opaque Gaussian the reverse walk passes: 2e-4.
     tol = 1e-4 if mode == gps.BLEND_OIT else 2e-4
+    # OIT (sort-free default): each (warp block, Gaussian) partial is added
+    # to grad2d by an atomic in no fixed order, so an element's FP32 sum is
+    # off by up to about n u sum|t| (n ~ 32 pixels + the atomics, u = 2^-24):
+    # relative to |sum t| that exceeds 1e-4 only where the terms cancel more
+    # than ~30-fold.  Elementwise, 99.9% must meet 1e-4 and all 1e-3; the
+    # norm criterion stays 1e-4.
+    quant = (0.999, 1e-3) if mode == gps.BLEND_OIT else None
     assert_grads_close({n: g2[:, k] for k, n in enumerate(names)},
                        {n: g2_o[:, k] for k, n in enumerate(names)}, exclude=excl,
-                       norm_tol=tol, elem_tol=tol, label=f"grad2d mode={mode}")
+                       norm_tol=tol, elem_tol=tol, label=f"grad2d mode={mode}", quantile=quant)
 
 
 def test_projection_backward_staged():
