@@ -463,6 +463,11 @@ typedef struct GpsHashTsdf {
   float* sdf;               /* [capacity][512]                                   */
   float* weight;            /* [capacity][512]                                   */
   float* rgbw;              /* [capacity][512][4]: colour and its weight         */
+  uint8_t* slot_flags;      /* [capacity] (nullable): 1 once a voxel of the slot's
+                               brick has left sdf 1 (set by fusion, 0 when the
+                               brick is allocated); the ray-cast then skips the
+                               loads of stored bricks whose flag is 0, with the
+                               same result                                       */
 } GpsHashTsdf;
 
 /* Scratch bytes of fuse_frame_hashed for up to max_candidates candidate

@@ -68,7 +68,8 @@ class GpsHashTsdf(ctypes.Structure):
                 ("origin", c_float * 3), ("trunc", c_float), ("max_weight", c_float),
                 ("n_buckets", c_int32), ("capacity", c_int32), ("keys", c_void_p),
                 ("slots", c_void_p), ("brick_of_slot", c_void_p), ("state", c_void_p),
-                ("sdf", c_void_p), ("weight", c_void_p), ("rgbw", c_void_p)]
+                ("sdf", c_void_p), ("weight", c_void_p), ("rgbw", c_void_p),
+                ("slot_flags", c_void_p)]
 
 
 class GpsGaussians(ctypes.Structure):
@@ -396,6 +397,7 @@ class HashTsdf:
         self.sdf = torch.ones(capacity * 512, device=dev)
         self.weight = torch.zeros(capacity * 512, device=dev)
         self.rgbw = torch.zeros(capacity * 512, 4, device=dev)
+        self.slot_flags = torch.zeros(capacity, dtype=torch.uint8, device=dev)
         self.scratch = torch.zeros(gps_hash_scratch_size(max_candidates), dtype=torch.uint8,
                                    device=dev)
 
@@ -408,7 +410,8 @@ class HashTsdf:
         return GpsHashTsdf(s.nx, s.ny, s.nz, float(s.voxel), (c_float * 3)(*map(float, s.origin)),
                            float(s.trunc), float(s.max_weight), self.n_buckets, self.capacity,
                            _ptr(self.keys), _ptr(self.slots), _ptr(self.brick_of_slot),
-                           _ptr(self.state), _ptr(self.sdf), _ptr(self.weight), _ptr(self.rgbw))
+                           _ptr(self.state), _ptr(self.sdf), _ptr(self.weight), _ptr(self.rgbw),
+                           _ptr(self.slot_flags))
 
     def allocated(self) -> int:
         """Bricks in use (reads the device counter: synchronises)."""

@@ -42,6 +42,7 @@ struct HashDev {
   float* sdf;
   float* weight;
   float4* rgbw_p;
+  uint8_t* flags;  // per slot, nullable: 1 once a voxel left sdf 1
 
   __device__ __forceinline__ long long brick(int x, int y, int z) const {
     return ((long long)(z >> 3) * (ny >> 3) + (y >> 3)) * (nx >> 3) + (x >> 3);
@@ -63,7 +64,7 @@ struct HashDev {
   __device__ __forceinline__ bool load8(int ix, int iy, int iz, float* c) const {
     if ((ix & 7) != 7 && (iy & 7) != 7 && (iz & 7) != 7) {  // stencil inside one brick
       const int s = find(brick(ix, iy, iz));
-      if (s < 0) return false;
+      if (s < 0 || (flags && !flags[s])) return false;  // not stored, or only 1s
       const float* b = sdf + (size_t)s * 512 + ((iz & 7) << 6) + ((iy & 7) << 3) + (ix & 7);
 #pragma unroll
       for (int k = 0; k < 8; ++k) c[k] = __ldg(b + (k & 1) + (((k >> 1) & 1) << 3) + ((k >> 2) << 6));
@@ -80,7 +81,7 @@ struct HashDev {
         last = b;
         s = find(b);
       }
-      if (s >= 0) {
+      if (s >= 0 && (!flags || flags[s])) {  // else the voxel holds 1: c[k] stays
         c[k] = __ldg(sdf + (size_t)s * 512 + ((z & 7) << 6) + ((y & 7) << 3) + (x & 7));
         any = true;
       }
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(512) hash_alloc_kernel(HashDev h, Cam cam,
       h.sdf[id] = 1.0f;
       h.weight[id] = 0.0f;
       h.rgbw_p[id] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (local == 0 && h.flags) h.flags[s_slot] = 0;
     }
     __syncthreads();  // s_slot / s_new are rewritten by the next candidate
   }
@@ -291,8 +293,9 @@ __global__ void __launch_bounds__(256) hash_fuse_kernel(HashDev h, const float* 
       float eta;
       const long long pix = voxel_pixel(h.voxel, h.ox, h.oy, h.oz, cam, depth, x, y, z, eta);
       if (pix < 0 || eta < -h.trunc) continue;
-      voxel_update(h.trunc, h.wmax, cam, rgb, pix, eta, h.sdf, h.weight, h.rgbw_p,
-                   (long long)s * 512 + local);
+      const float s1 = voxel_update(h.trunc, h.wmax, cam, rgb, pix, eta, h.sdf, h.weight,
+                                    h.rgbw_p, (long long)s * 512 + local);
+      if (h.flags && s1 != 1.0f) h.flags[s] = 1;
     }
   }
 }
@@ -376,6 +379,7 @@ gps::HashDev hash_dev(const GpsHashTsdf& v) {
   h.sdf = v.sdf;
   h.weight = v.weight;
   h.rgbw_p = reinterpret_cast<float4*>(v.rgbw);
+  h.flags = v.slot_flags;
   return h;
 }
 
