@@ -67,6 +67,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRCS = [os.path.join(_HERE, f) for f in ("tsdf.cpp", "splat.cpp", "sh.cpp")]
+_HDRS = [os.path.join(_HERE, "mag.h")]
 
 # projected record layout (FP64), mirrors the enum in splat.cpp
 R_MX, R_MY, R_D, R_SIG, R_CA, R_CB, R_CC, R_QMAX, R_R, R_G, R_B, R_EX, R_EY, R_VIS, \
@@ -83,7 +84,7 @@ FP32, FP16, BF16 = 0, 1, 2
 
 def build(force: bool = False) -> str:
     """Compile liboracle.so next to the sources (g++, FP64, OpenMP)."""
-    newest = max(os.path.getmtime(s) for s in _SRCS)
+    newest = max(os.path.getmtime(s) for s in _SRCS + _HDRS)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
                "-o", _SO] + _SRCS
@@ -212,17 +213,12 @@ def project(g, cam, near=0.2):
     return rec, amb
 
 
-def composite(rec, Ct, Dt, eps, mode=OIT, f32=False, brute=False, window=None,
-              band=(4e-6, 2e-6), flip=None):
+def composite(rec, Ct, Dt, eps, mode=OIT, f32=False, brute=False, window=None, flip=None):
     """Eq. 1-4 (mode OIT) or the Table 7 variant (mode ALPHA) for one view.
-    Returns dict C [3][H][W], D, W (= W_G), T (T_end), n (counted), amb, and the
-    flip allowance: allow_C, allow_D [H][W] bound how far C*, D* can move if
-    the counting decisions within `band` of their thresholds went the other
-    way (band[0]: relative error of the conic, scaled by the magnitude of the
-    quadratic form's terms; band[1]: relative error of d vs D_t + eps);
-    g_amb [M] sums the alpha
-    of a Gaussian's such decisions, g_mass [M] its total counted alpha.
-    flip (diagnostic): take every decision within that band the other way."""
+    Returns dict C [3][H][W], D, W (= W_G), T (T_end), n (counted) and amb
+    (ALPHA clamp / termination decisions near their thresholds).
+    flip (diagnostic, see `flip_spec`): the decisions inside the error bands
+    taken the other way, or by a seeded coin."""
     Ct = _f64(Ct)
     Dt = _f64(Dt)
     H, W = Dt.shape
@@ -231,19 +227,22 @@ def composite(rec, Ct, Dt, eps, mode=OIT, f32=False, brute=False, window=None,
     M = rec.shape[0]
     out = dict(C=np.zeros((3, H, W)), D=np.zeros((H, W)), W=np.zeros((H, W)),
                T=np.zeros((H, W)), n=np.zeros((H, W), np.int32), amb=np.zeros((H, W), np.int32))
-    allow = np.zeros((2, H, W))
-    g_amb, g_mass = np.zeros(M), np.zeros(M)
-    b = _f64(band)
     lib().orc_composite(ctypes.c_int(M), _p(rec), ctypes.c_int(W), ctypes.c_int(H),
                         _p(Ct), _p(Dt), ctypes.c_double(eps), ctypes.c_int(mode),
                         ctypes.c_int(int(f32)), ctypes.c_int(int(brute)), ctypes.c_int(x0),
                         ctypes.c_int(x1), ctypes.c_int(y0), ctypes.c_int(y1), _p(out["C"]),
                         _p(out["D"]), _p(out["W"]), _p(out["T"]), _p(out["n"]), _p(out["amb"]),
-                        _p(b), _p(allow), _p(g_amb), _p(g_mass),
                         _p(_f64(flip)) if flip is not None else None)
-    out["allow_C"], out["allow_D"] = allow[0], allow[1]
-    out["g_amb"], out["g_mass"] = g_amb, g_mass
     return out
+
+
+def flip_spec(bands: dict, seed=0) -> np.ndarray:
+    """The `flip` argument of composite / composite_backward / render_loss_grads:
+    the decisions `envelope` calls ambiguous under `bands` (see `bands_for`)
+    are inverted (seed 0) or decided by a coin drawn from the seed
+    (diagnostic only)."""
+    b = bands
+    return _f64([b["conic"], b["mean"], b["qmax"], b["depth"], 0.0, 0.0, float(seed)])
 
 
 def loss(C, D, Ctgt, Dtgt, Dt, lambda_depth=0.0):
@@ -296,6 +295,131 @@ def project_backward(g, cam, g2, near=0.2):
                               _p(_f64(g.sh_rest)), _p(t), _p(np.ascontiguousarray(out["rgb"])),
                               _p(out["means"]), _p(out["sh_rest"]))
     return out
+
+
+PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "rgb", "sh_rest")
+
+
+def project_backward_magnitude(g, cam, g2, near=0.2):
+    """Magnitudes of `project_backward`'s results: the same adjoint evaluated
+    in magnitude arithmetic (mag.h: |operands|, subtractions as additions)
+    from |g2|.  An FP32 adjoint's rounding error is a small multiple of u
+    times these, per element (running error analysis)."""
+    M = g.M
+    arrs = [_f64(a) for a in g.arrays()]
+    K, R, t = _cam(cam)
+    out = dict(means=np.zeros((M, 3)), log_scales=np.zeros((M, 3)), quats=np.zeros((M, 4)),
+               opacity_logits=np.zeros(M), rgb=np.zeros((M, 3)))
+    lib().orc_project_backward_mag(ctypes.c_int(M), *[_p(a) for a in arrs[:4]],
+                                   ctypes.c_int(cam.width), ctypes.c_int(cam.height), _p(K),
+                                   _p(R), _p(t), ctypes.c_double(near), _p(_f64(g2)),
+                                   _p(out["means"]), _p(out["log_scales"]), _p(out["quats"]),
+                                   _p(out["opacity_logits"]), _p(out["rgb"]))
+    D = _sh_degree(g)
+    if D > 0:
+        out["sh_rest"] = np.zeros(g.sh_rest.shape)
+        lib().orc_sh_backward_mag(ctypes.c_int(M), ctypes.c_int(D), _p(arrs[0]),
+                                  _p(_f64(g.sh_rest)), _p(t), _p(np.ascontiguousarray(out["rgb"])),
+                                  _p(out["means"]), _p(out["sh_rest"]))
+    return out
+
+
+def projection_adjoint_matrix(g, cam, near=0.2) -> np.ndarray:
+    """J^T of every Gaussian's projection, [M][P][G_N]: the parameter gradient
+    of a per-Gaussian 2D gradient g2 [M][G_N] is JT[i] @ g2[i], parameters in
+    PARAM_KEYS order flattened (P = 14, plus 3 K SH coefficients).  Built
+    column by column from `project_backward` (linear in g2)."""
+    M = g.M
+    cols = []
+    for c in range(G_N):
+        e = np.zeros((M, G_N))
+        e[:, c] = 1.0
+        gr = project_backward(g, cam, e, near)
+        cols.append(np.concatenate([gr[k].reshape(M, -1) for k in PARAM_KEYS if k in gr], axis=1))
+    return np.ascontiguousarray(np.stack(cols, axis=2))
+
+
+def split_params(v: np.ndarray, like: dict) -> dict:
+    """[M][P] per-parameter array -> dict shaped like a project_backward result."""
+    out, o = {}, 0
+    for k in PARAM_KEYS:
+        if k not in like:
+            continue
+        n = int(np.prod(like[k].shape[1:])) if like[k].ndim > 1 else 1
+        out[k] = v[:, o:o + n].reshape(like[k].shape)
+        o += n
+    return out
+
+
+U32 = 2.0 ** -24  # unit roundoff of binary32
+
+
+def bands_for(W: int, H: int, **over) -> dict:
+    """Error bands of a single-precision (FP32) evaluation of a W x H view, the
+    `bands` of `envelope` and `flip_spec`:
+      conic 2.5e-6: the conic entries within 2e-6 of cn = |a| + 2|b| + |c|,
+        plus the rounding of q's own products (8 u cn r^2);
+      mean 4 u (W + H) px: m = f t_x / t_z + c carries a few roundings of
+        numbers below W + H;
+      qmax 2e-7 and depth 3.5e-7 (relative): a few roundings each, the depth
+        threshold D_t + eps rounded once more (2 u);
+      res_colour 1e-4 and res_depth 1e-4 (relative): the image tolerance.
+    The record bounds these assume are asserted on the kernels' records by the
+    end-to-end tests."""
+    b = dict(conic=2.5e-6, mean=4.0 * U32 * (W + H), qmax=2e-7, depth=3.5e-7,
+             res_colour=1e-4, res_depth=1e-4)
+    b.update(over)
+    return b
+
+
+def envelope(rec, Ct, Dt, eps, mode, Ctgt, Dtgt, lambda_depth, n_valid, JT=None, bands=None,
+             kmax=12, f32=False, dC=None, dD=None):
+    """Decision envelope of one view (orc_envelope in splat.cpp): how far a
+    single-precision evaluation that takes every decision outside the error
+    bands as the FP64 definition does can be from it, per pixel, for the loss
+    and per parameter.  Bands (dict, default `bands_for(W, H)`): the counting decision
+    q <= qmax is ambiguous where |qmax - q| < conic cn r^2 + 2 mean cn r +
+    qmax |qmax| (cn = |a| + 2|b| + |c|, r the pixel's distance from the mean:
+    a conic known within `conic` of cn, a mean within `mean` px, qmax within
+    `qmax` of itself), the depth test where |d - (D_t + eps)| < depth
+    (D_t + eps); residual signs where |C* - C| < res_colour or
+    |D* - D| < res_depth D.  JT = None: the image and loss envelope only.
+    f32=True: FP32 decisions on records holding FP32 values (as `composite`
+    with f32), nothing ambiguous - for the reference terms' sums s2, s2q.
+    dC, dD: explicit upstream gradients in place of the L1 loss's.
+    Returns allow_C, allow_D, allow_W [H][W] (C*, D*, W_G; inf where
+    unbounded), allow_L, n_amb,
+    unbounded [H][W], allow3 [M][P] (per parameter, PARAM_KEYS order), g2ref
+    [M][G_N] (the FP64 2D gradient), s2, s2q [M][G_N] (sums over pixels of
+    |term| and |term| qband / 2)."""
+    rec = _f64(rec)
+    Ct, Dt, Ctgt, Dtgt = (_f64(a) for a in (Ct, Dt, Ctgt, Dtgt))
+    H, W = Dt.shape
+    b = bands if bands is not None else bands_for(W, H)
+    M = rec.shape[0]
+    if JT is None:
+        JT = np.zeros((M, 0, G_N))
+    JT = np.ascontiguousarray(JT, dtype=np.float64)
+    P = JT.shape[1]
+    assert JT.shape == (M, P, G_N)
+    band = _f64([b["conic"], b["mean"], b["qmax"], b["depth"], b["res_colour"], b["res_depth"]])
+    allow_img = np.zeros((3, H, W))
+    allow_L = ctypes.c_double(0.0)
+    n_amb = np.zeros((H, W), np.int32)
+    unb = np.zeros((H, W), np.int32)
+    allow3 = np.zeros((M, max(P, 1)))
+    g2ref, s2, s2q = np.zeros((M, G_N)), np.zeros((M, G_N)), np.zeros((M, G_N))
+    lib().orc_envelope(ctypes.c_int(M), _p(rec), ctypes.c_int(W), ctypes.c_int(H), _p(Ct),
+                       _p(Dt), ctypes.c_double(eps), ctypes.c_int(mode), _p(Ctgt), _p(Dtgt),
+                       ctypes.c_double(lambda_depth), ctypes.c_long(n_valid), _p(band),
+                       ctypes.c_int(P), _p(JT), ctypes.c_int(kmax), ctypes.c_int(int(f32)),
+                       _p(_f64(dC)) if dC is not None else None,
+                       _p(_f64(dD)) if dD is not None else None, _p(allow_img),
+                       ctypes.byref(allow_L), _p(n_amb), _p(unb), _p(allow3), _p(g2ref), _p(s2),
+                       _p(s2q))
+    return dict(allow_C=allow_img[0], allow_D=allow_img[1], allow_W=allow_img[2],
+                allow_L=allow_L.value, n_amb=n_amb,
+                unbounded=unb, allow3=allow3, g2ref=g2ref, s2=s2, s2q=s2q)
 
 
 def bin_records(rec32: np.ndarray, W: int, H: int, TW: int, TH: int, cap: int = 1 << 26):

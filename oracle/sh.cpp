@@ -16,6 +16,9 @@
 // normalisation: dL/dp = (I - d d^T) / |p - o| * sum_lm (dY_lm/dd) (f_lm . dL/dc).
 #include <cmath>
 #include <cstddef>
+#include <vector>
+
+#include "mag.h"
 
 namespace {
 
@@ -67,6 +70,43 @@ void basis(int degree, double x, double y, double z, double* Y, double* dY) {
   }
 }
 
+
+inline bool is_zero(double v) { return v == 0.0; }
+inline bool is_zero(Mag m) { return m.v == 0.0; }
+
+// Body of orc_sh_backward; T = double is the adjoint, T = Mag its magnitudes.
+template <class T>
+void sh_backward_t(int M, int degree, const double* means, const double* sh,
+                   const double* centre, const T* dc, T* d_means, T* d_sh) {
+  const int K = sh_count(degree);
+  double Y[15], dY[45];
+  for (int i = 0; i < M; ++i) {
+    const T* g = dc + 3 * i;
+    if (is_zero(g[0]) && is_zero(g[1]) && is_zero(g[2])) continue;
+    double v[3], n2 = 0;
+    for (int a = 0; a < 3; ++a) {
+      v[a] = means[3 * i + a] - centre[a];
+      n2 += v[a] * v[a];
+    }
+    const double n = std::sqrt(n2);
+    const double d[3] = {v[0] / n, v[1] / n, v[2] / n};
+    basis(degree, d[0], d[1], d[2], Y, dY);
+    T gd[3] = {0.0, 0.0, 0.0};  // dL/dd (ambient)
+    for (int k = 0; k < K; ++k) {
+      const double* f = sh + ((size_t)i * K + k) * 3;
+      T* df = d_sh + ((size_t)i * K + k) * 3;
+      T w = 0.0;
+      for (int ch = 0; ch < 3; ++ch) {
+        df[ch] += Y[k] * g[ch];
+        w += f[ch] * g[ch];
+      }
+      for (int a = 0; a < 3; ++a) gd[a] += dY[3 * k + a] * w;
+    }
+    const T dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+    for (int a = 0; a < 3; ++a) d_means[3 * i + a] += (gd[a] - d[a] * dot) / n;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -103,33 +143,19 @@ void orc_sh_colour(int M, int degree, const double* means, const double* rgb, co
 // d_sh [M][K][3] (dL/drgb = dL/dc, left to the caller).
 void orc_sh_backward(int M, int degree, const double* means, const double* sh,
                      const double* centre, const double* dc, double* d_means, double* d_sh) {
+  sh_backward_t<double>(M, degree, means, sh, centre, dc, d_means, d_sh);
+}
+
+// The same adjoint in magnitude arithmetic (mag.h) from |dL/dc|: adds the
+// magnitudes of its terms to d_means and d_sh.
+void orc_sh_backward_mag(int M, int degree, const double* means, const double* sh,
+                         const double* centre, const double* dc, double* d_means, double* d_sh) {
   const int K = sh_count(degree);
-  double Y[15], dY[45];
-  for (int i = 0; i < M; ++i) {
-    const double* g = dc + 3 * i;
-    if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
-    double v[3], n2 = 0;
-    for (int a = 0; a < 3; ++a) {
-      v[a] = means[3 * i + a] - centre[a];
-      n2 += v[a] * v[a];
-    }
-    const double n = std::sqrt(n2);
-    const double d[3] = {v[0] / n, v[1] / n, v[2] / n};
-    basis(degree, d[0], d[1], d[2], Y, dY);
-    double gd[3] = {0, 0, 0};  // dL/dd (ambient)
-    for (int k = 0; k < K; ++k) {
-      const double* f = sh + ((size_t)i * K + k) * 3;
-      double* df = d_sh + ((size_t)i * K + k) * 3;
-      double w = 0;
-      for (int ch = 0; ch < 3; ++ch) {
-        df[ch] += Y[k] * g[ch];
-        w += f[ch] * g[ch];
-      }
-      for (int a = 0; a < 3; ++a) gd[a] += dY[3 * k + a] * w;
-    }
-    const double dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
-    for (int a = 0; a < 3; ++a) d_means[3 * i + a] += (gd[a] - d[a] * dot) / n;
-  }
+  std::vector<Mag> gm(3 * (size_t)M), dm(3 * (size_t)M), ds((size_t)M * K * 3);
+  for (size_t k = 0; k < gm.size(); ++k) gm[k] = Mag(dc[k]);
+  sh_backward_t<Mag>(M, degree, means, sh, centre, gm.data(), dm.data(), ds.data());
+  for (size_t k = 0; k < dm.size(); ++k) d_means[k] += dm[k].v;
+  for (size_t k = 0; k < ds.size(); ++k) d_sh[k] += ds[k].v;
 }
 
 }  // extern "C"

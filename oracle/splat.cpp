@@ -28,6 +28,8 @@
 #include <cstring>
 #include <vector>
 
+#include "mag.h"
+
 namespace {
 
 // projected record, FP64 (index names shared with the Python wrapper)
@@ -146,6 +148,21 @@ struct Item {
   double alpha, G, dx, dy;
 };
 
+// Front-to-back order: by depth (compared in float when the decisions are
+// taken in FP32), ties by ascending index.
+void sort_front_to_back(std::vector<Item>& its, const double* rec, int f32) {
+  std::stable_sort(its.begin(), its.end(), [&](const Item& a, const Item& b) {
+    double da = rec[(size_t)a.id * R_N + R_D], db = rec[(size_t)b.id * R_N + R_D];
+    if (f32) {
+      float fa = (float)da, fb = (float)db;
+      if (fa != fb) return fa < fb;
+    } else if (da != db) {
+      return da < db;
+    }
+    return a.id < b.id;
+  });
+}
+
 // Candidates of one pixel: every visible Gaussian whose bounding box (extent +
 // 1 px) contains it, in index order.  `brute` = every visible Gaussian.
 struct Lists {
@@ -176,55 +193,511 @@ Lists build_lists(int M, const double* rec, int W, int H, int brute, int x0, int
   return L;
 }
 
+// One (pixel, Gaussian) counting decision (Eq. 1-3: alpha >= 1/255 and
+// d < thr, thr = D_t + eps or +inf where the ray-cast missed) in FP64, and
+// whether it lies within the error band of a single-precision evaluation
+// (band: conic, mean, qmax, depth; see orc_envelope; null: never ambiguous):
+// support ambiguous where |qmax - q| < qband = band[0] cn r^2 + 2 band[1] cn r
+// + band[2] |qmax| (cn = |a| + 2|b| + |c|, r = |(dx, dy)|), depth where
+// |d - thr| < band[3] thr; the pair is ambiguous where either test is near
+// and the other passes or is near.
+struct Decision {
+  double q, G, alpha, dx, dy, qband;
+  bool ref_in, ambiguous;
+};
+
+Decision classify(const double* r, int x, int y, double Dt, double eps, const double* band,
+                  int f32 = 0) {
+  const double thr = Dt > 0.0 ? Dt + eps : INFINITY;
+  Decision d;
+  d.dx = x - r[R_MX];
+  d.dy = y - r[R_MY];
+  d.q = r[R_CA] * d.dx * d.dx + 2.0 * r[R_CB] * d.dx * d.dy + r[R_CC] * d.dy * d.dy;
+  d.G = std::exp(-0.5 * d.q);
+  d.alpha = r[R_SIG] * d.G;
+  if (f32) {
+    const float tf = Dt > 0.0 ? (float)Dt + (float)eps : INFINITY;
+    d.ref_in = support_f32((float)r[R_MX], (float)r[R_MY], (float)r[R_CA], (float)r[R_CB],
+                           (float)r[R_CC], (float)r[R_QMAX], x, y) &&
+               (float)r[R_D] < tf;
+  } else {
+    d.ref_in = d.alpha >= 1.0 / 255.0 && r[R_D] < thr;
+  }
+  d.qband = 0.0;
+  d.ambiguous = false;
+  if (band) {
+    const double cn = std::fabs(r[R_CA]) + 2.0 * std::fabs(r[R_CB]) + std::fabs(r[R_CC]);
+    const double r2 = d.dx * d.dx + d.dy * d.dy;
+    d.qband = band[0] * cn * r2 + 2.0 * band[1] * cn * std::sqrt(r2) +
+              band[2] * std::fabs(r[R_QMAX]);
+    const bool in_s = d.q <= r[R_QMAX], near_s = std::fabs(r[R_QMAX] - d.q) < d.qband;
+    const bool in_d = r[R_D] < thr,
+               near_d = std::isfinite(thr) && std::fabs(r[R_D] - thr) < band[3] * thr;
+    d.ambiguous = (near_s || near_d) && (in_s || near_s) && (in_d || near_d);
+  }
+  return d;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): the diagnostic's coin per decision.
+inline uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 // The Gaussians counted at pixel (x, y), sorted front to back by (d, index).
 // f32 != 0: decisions in FP32 from the record's float values (see support_f32);
 // otherwise alpha >= 1/255 and d < D_t + eps in FP64.
-// flip (diagnostic only, nullable): decisions lying within the error band of
-// their threshold (flip[0]: conic, flip[1]: depth; see the allowance in
-// orc_composite) are taken the other way, giving the result a single-precision
-// evaluation reaches when it decides each of them differently.
+// flip (diagnostic only, nullable; 7 values: the 4 bands of `classify`, two
+// unused, a seed): the decisions `classify` calls ambiguous are taken the
+// other way (seed 0) or by a coin drawn from the seed, pixel and Gaussian -
+// results a single-precision evaluation may reach.
 std::vector<Item> counted(const std::vector<int>& cand, const double* rec, int x, int y,
                           double Dt, double eps, int f32, const double* flip = nullptr) {
   std::vector<Item> out;
   for (int i : cand) {
     const double* r = rec + (size_t)i * R_N;
-    double dx = x - r[R_MX], dy = y - r[R_MY];
-    double q = r[R_CA] * dx * dx + 2.0 * r[R_CB] * dx * dy + r[R_CC] * dy * dy;
-    double G = std::exp(-0.5 * q);
-    double alpha = r[R_SIG] * G;
     bool keep;
+    const Decision d = classify(r, x, y, Dt, eps, flip);
     if (flip) {
-      const double thr = Dt > 0.0 ? Dt + eps : INFINITY;
-      const double cn = std::fabs(r[R_CA]) + 2.0 * std::fabs(r[R_CB]) + std::fabs(r[R_CC]);
-      const double qband = flip[0] * (std::fabs(q) + cn * (dx * dx + dy * dy));
-      const bool in_s = q <= r[R_QMAX], near_s = std::fabs(r[R_QMAX] - q) < qband;
-      const bool in_d = r[R_D] < thr, near_d = std::isfinite(thr) && std::fabs(r[R_D] - thr) < flip[1] * thr;
-      keep = (in_s != near_s) && (in_d != near_d);
-      if (keep) out.push_back({i, alpha, G, dx, dy});
-      continue;
-    }
-    if (f32) {
+      keep = d.ref_in;
+      if (d.ambiguous) {
+        const uint64_t seed = (uint64_t)flip[6];
+        keep = seed == 0 ? !d.ref_in
+                         : (mix64(seed ^ mix64(((uint64_t)y << 40) ^ ((uint64_t)x << 20) ^
+                                               (uint64_t)i)) & 1) != 0;
+      }
+    } else if (f32) {
       float thr = Dt > 0.0 ? (float)Dt + (float)eps : INFINITY;
       keep = support_f32((float)r[R_MX], (float)r[R_MY], (float)r[R_CA], (float)r[R_CB],
                          (float)r[R_CC], (float)r[R_QMAX], x, y) &&
              (float)r[R_D] < thr;
     } else {
-      double thr = Dt > 0.0 ? Dt + eps : INFINITY;
-      keep = alpha >= 1.0 / 255.0 && r[R_D] < thr;
+      keep = d.ref_in;
     }
-    if (keep) out.push_back({i, alpha, G, dx, dy});
+    if (keep) out.push_back({i, d.alpha, d.G, d.dx, d.dy});
   }
-  std::stable_sort(out.begin(), out.end(), [&](const Item& a, const Item& b) {
-    double da = rec[(size_t)a.id * R_N + R_D], db = rec[(size_t)b.id * R_N + R_D];
-    if (f32) {
-      float fa = (float)da, fb = (float)db;
-      if (fa != fb) return fa < fb;
-    } else if (da != db) {
-      return da < db;
-    }
-    return a.id < b.id;
-  });
+  sort_front_to_back(out, rec, f32);
   return out;
+}
+
+// Per-pixel adjoint of the blend.  `its`: the Gaussians counted at the pixel,
+// front to back; Ctp, Dtp: C_t, D_t there; g, gD: dL/dC* (3) and dL/dD*.
+// out[k] (G_N entries, overwritten) receives item k's contribution to its
+// Gaussian's 2D gradient.  Returns the number of items the blend uses (all in
+// mode 0; mode 1 stops before the first that would take T below 1e-4).
+//   mode 0 (Eq. 4), N = 1 + W_G:  dC*/dc_i = a_i / N,  dC*/da_i = (c_i - C*) / N;
+//   mode 1: dC*/dc_i = a_i T_i,
+//           dC*/da_i = c_i T_i - (sum_{j>i} c_j a_j T_j + T_end C_t) / (1 - a_i);
+// likewise for depth (d_i in place of c_i).  Then through alpha = sigma G,
+// G = exp(-q/2): dL/dsigma = dL/da G, dL/dq = -dL/da alpha / 2, dq/dconic and
+// dq/dmean from q = a dx^2 + 2 b dx dy + c dy^2, dx = x - m_x.  An alpha
+// clamped at 0.99 has zero derivative.
+size_t pixel_adjoint(const std::vector<Item>& its, const double* rec, const double* Ctp, double Dtp,
+                     const double* g, double gD, int mode,
+                     std::vector<std::array<double, G_N>>& out) {
+  const size_t n = its.size();
+  out.assign(n, std::array<double, G_N>{});
+  if (n == 0) return 0;
+  std::vector<double> a(n), T(n), dLda(n), dLdd(n);
+  std::vector<bool> clamped(n, false);
+  std::vector<std::array<double, 3>> dLdc(n);
+  size_t used = n;
+  if (mode == 0) {
+    double Cg[3] = {0, 0, 0}, Wg = 0, Z = 0;
+    for (size_t k = 0; k < n; ++k) {
+      const double* r = rec + (size_t)its[k].id * R_N;
+      a[k] = its[k].alpha;
+      for (int ch = 0; ch < 3; ++ch) Cg[ch] += r[R_R + ch] * a[k];
+      Wg += a[k];
+      Z += r[R_D] * a[k];
+    }
+    double N = 1.0 + Wg, Cs[3], Ds = (Dtp + Z) / N;
+    for (int ch = 0; ch < 3; ++ch) Cs[ch] = (Ctp[ch] + Cg[ch]) / N;
+    for (size_t k = 0; k < n; ++k) {
+      const double* r = rec + (size_t)its[k].id * R_N;
+      double v = 0;
+      for (int ch = 0; ch < 3; ++ch) {
+        dLdc[k][ch] = g[ch] * a[k] / N;
+        v += g[ch] * (r[R_R + ch] - Cs[ch]) / N;
+      }
+      v += gD * (r[R_D] - Ds) / N;
+      dLda[k] = v;
+      dLdd[k] = gD * a[k] / N;
+    }
+  } else {
+    double Tc = 1.0;
+    used = 0;
+    for (size_t k = 0; k < n; ++k) {
+      double al = its[k].alpha;
+      clamped[k] = al > 0.99;
+      al = std::min(al, 0.99);
+      if (Tc * (1.0 - al) < 1e-4) break;
+      a[k] = al;
+      T[k] = Tc;
+      Tc *= (1.0 - al);
+      ++used;
+    }
+    const double Tend = Tc;
+    double S[3] = {Tend * Ctp[0], Tend * Ctp[1], Tend * Ctp[2]}, SD = Tend * Dtp;
+    for (size_t kk = used; kk-- > 0;) {
+      const double* r = rec + (size_t)its[kk].id * R_N;
+      double v = 0;
+      for (int ch = 0; ch < 3; ++ch) {
+        dLdc[kk][ch] = g[ch] * a[kk] * T[kk];
+        v += g[ch] * (r[R_R + ch] * T[kk] - S[ch] / (1.0 - a[kk]));
+      }
+      v += gD * (r[R_D] * T[kk] - SD / (1.0 - a[kk]));
+      dLda[kk] = v;
+      dLdd[kk] = gD * a[kk] * T[kk];
+      for (int ch = 0; ch < 3; ++ch) S[ch] += r[R_R + ch] * a[kk] * T[kk];
+      SD += r[R_D] * a[kk] * T[kk];
+    }
+  }
+  for (size_t k = 0; k < used; ++k) {
+    const double* r = rec + (size_t)its[k].id * R_N;
+    std::array<double, G_N>& o = out[k];
+    for (int ch = 0; ch < 3; ++ch) o[G_R + ch] = dLdc[k][ch];
+    o[G_D] = dLdd[k];
+    if (clamped[k]) continue;
+    const double G = its[k].G, al = its[k].alpha, dx = its[k].dx, dy = its[k].dy;
+    o[G_SIG] = dLda[k] * G;
+    double dq = dLda[k] * (-0.5 * al);
+    o[G_CA] = dq * dx * dx;
+    o[G_CB] = dq * 2.0 * dx * dy;
+    o[G_CC] = dq * dy * dy;
+    // dq/dmean = -2 (conic . delta)
+    o[G_MX] = dq * -2.0 * (r[R_CA] * dx + r[R_CB] * dy);
+    o[G_MY] = dq * -2.0 * (r[R_CB] * dx + r[R_CC] * dy);
+  }
+  return used;
+}
+
+// Adjoint of one Gaussian's projection: its 2D gradient g (G_N entries) ->
+// dm (mean, 3), dl (log-scales, 3), dq (quaternion, 4, through the
+// normalisation), *dlogit and drgb (3).  P must be visible.  The Jacobian
+// clamp is differentiated exactly (a clamped t_x' = +-lim t_z).  T = double
+// is the adjoint; T = Mag evaluates its magnitudes (mag.h).
+template <class T>
+void proj_adjoint_t(const Cam& c, const Proj& P, const T* g, T* dm, T* dl, T* dq, T* dlogit,
+                    T* drgb) {
+  const double* R = c.R;
+  for (int k = 0; k < 3; ++k) drgb[k] = g[G_R + k];
+  *dlogit = g[G_SIG] * P.sig * (1.0 - P.sig);
+  // conic = inverse(Sigma_2D): dL/dSigma_2D = -C Gs C with Gs the symmetric
+  // gradient of the conic matrix (off-diagonals carry half of dL/db).
+  const double Cm[4] = {P.conic[0], P.conic[1], P.conic[1], P.conic[2]};
+  const T Gs[4] = {g[G_CA], 0.5 * g[G_CB], 0.5 * g[G_CB], g[G_CC]};
+  T tmp[4], dS2[4];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      tmp[a * 2 + b] = 0.0;
+      for (int k = 0; k < 2; ++k) tmp[a * 2 + b] += Cm[a * 2 + k] * Gs[k * 2 + b];
+    }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      dS2[a * 2 + b] = 0.0;
+      for (int k = 0; k < 2; ++k) dS2[a * 2 + b] -= tmp[a * 2 + k] * Cm[k * 2 + b];
+    }
+  // Sigma_2D = T Sigma T^T (+0.3 I): dT = 2 dS2 T Sigma, dSigma = T^T dS2 T
+  T dT[6], dSig[9];
+  for (int a = 0; a < 2; ++a)
+    for (int j = 0; j < 3; ++j) {
+      T s = 0.0;
+      for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 3; ++k) s += dS2[a * 2 + b] * P.T[b * 3 + k] * P.Sig[k * 3 + j];
+      dT[a * 3 + j] = 2.0 * s;
+    }
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      T s = 0.0;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) s += P.T[a * 3 + k] * dS2[a * 2 + b] * P.T[b * 3 + l];
+      dSig[k * 3 + l] = s;
+    }
+  // T = J W with W[k][j] = R[j][k]  =>  dJ[a][k] = sum_j dT[a][j] R[j][k]
+  T dJ[6];
+  for (int a = 0; a < 2; ++a)
+    for (int k = 0; k < 3; ++k) {
+      T s = 0.0;
+      for (int j = 0; j < 3; ++j) s += dT[a * 3 + j] * R[j * 3 + k];
+      dJ[a * 3 + k] = s;
+    }
+  const double tz = P.tc[2], tz2 = tz * tz, tz3 = tz2 * tz;
+  T dtc[3] = {0.0, 0.0, 0.0};
+  dtc[2] += dJ[0] * (-c.fx / tz2) + dJ[4] * (-c.fy / tz2) + dJ[2] * (2.0 * c.fx * P.txp / tz3) +
+            dJ[5] * (2.0 * c.fy * P.typ / tz3);
+  const T dtxp = dJ[2] * (-c.fx / tz2), dtyp = dJ[5] * (-c.fy / tz2);
+  if (P.clx)
+    dtc[2] += dtxp * (P.txp / tz);  // t_x' = +-lim t_z
+  else
+    dtc[0] += dtxp;
+  if (P.cly)
+    dtc[2] += dtyp * (P.typ / tz);
+  else
+    dtc[1] += dtyp;
+  // mean2D = (fx tx / tz + cx, fy ty / tz + cy); depth = tz
+  dtc[0] += g[G_MX] * c.fx / tz;
+  dtc[1] += g[G_MY] * c.fy / tz;
+  dtc[2] += -g[G_MX] * c.fx * P.tc[0] / tz2 - g[G_MY] * c.fy * P.tc[1] / tz2 + g[G_D];
+  // tc = R^T (p - c)  =>  dp = R dtc
+  for (int r = 0; r < 3; ++r) dm[r] = R[r * 3 + 0] * dtc[0] + R[r * 3 + 1] * dtc[1] + R[r * 3 + 2] * dtc[2];
+  // Sigma = Mg Mg^T, Mg = Rg diag(s): dMg = 2 dSigma Mg
+  double Mg[9];
+  T dMg[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Mg[a * 3 + b] = P.Rg[a * 3 + b] * P.s[b];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      T s = 0.0;
+      for (int k = 0; k < 3; ++k) s += dSig[a * 3 + k] * Mg[k * 3 + b];
+      dMg[a * 3 + b] = 2.0 * s;
+    }
+  T dRg[9];
+  for (int b = 0; b < 3; ++b) {
+    T ds = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      dRg[a * 3 + b] = dMg[a * 3 + b] * P.s[b];
+      ds += dMg[a * 3 + b] * P.Rg[a * 3 + b];
+    }
+    dl[b] = ds * P.s[b];
+  }
+  // rotation matrix entries as polynomials of the unit quaternion (w, x, y, z)
+  const double w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
+  T dqn[4];
+  dqn[0] = dRg[1] * (-2 * z) + dRg[2] * (2 * y) + dRg[3] * (2 * z) + dRg[5] * (-2 * x) +
+           dRg[6] * (-2 * y) + dRg[7] * (2 * x);
+  dqn[1] = dRg[1] * (2 * y) + dRg[2] * (2 * z) + dRg[3] * (2 * y) + dRg[4] * (-4 * x) +
+           dRg[5] * (-2 * w) + dRg[6] * (2 * z) + dRg[7] * (2 * w) + dRg[8] * (-4 * x);
+  dqn[2] = dRg[0] * (-4 * y) + dRg[1] * (2 * x) + dRg[2] * (2 * w) + dRg[3] * (2 * x) +
+           dRg[5] * (2 * z) + dRg[6] * (-2 * w) + dRg[7] * (2 * z) + dRg[8] * (-4 * y);
+  dqn[3] = dRg[0] * (-4 * z) + dRg[1] * (-2 * w) + dRg[2] * (2 * x) + dRg[3] * (2 * w) +
+           dRg[4] * (-4 * z) + dRg[5] * (2 * y) + dRg[6] * (2 * x) + dRg[7] * (2 * y);
+  // qn = q / |q|: dq = (dqn - qn (qn . dqn)) / |q|
+  T dot = w * dqn[0] + x * dqn[1] + y * dqn[2] + z * dqn[3];
+  for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - P.qn[k] * dot) / P.qnorm;
+}
+
+void proj_adjoint(const Cam& c, const Proj& P, const double* g, double* dm, double* dl,
+                  double* dq, double* dlogit, double* drgb) {
+  proj_adjoint_t<double>(c, P, g, dm, dl, dq, dlogit, drgb);
+}
+
+struct EnvView {
+  int M, W, H, mode, P, kmax, f32;
+  const double *rec, *Ct, *Dt, *Ctgt, *Dtgt, *band, *JT;
+  double eps, sc, sd, lambda;
+  long n_valid;
+  const double *dC, *dD;
+};
+
+struct EnvPixel {  // per-pixel results
+  int n_amb = 0, unbounded = 0;
+  double aC = 0, aD = 0, aW = 0, aL = 0;
+};
+
+// One pixel of orc_envelope.  With P > 0, the reference terms are added to
+// g2ref / s2 / s2q and the parameter ranges to allow3 (callers run pixels of
+// one view in sequence then); with P == 0 only the image and loss envelope.
+EnvPixel envelope_pixel(const EnvView& v, const Lists& L, long pix, double* allow3,
+                        double* g2ref, double* s2, double* s2q) {
+  EnvPixel res;
+  const long npx = (long)v.W * v.H;
+  const int x = (int)(pix % v.W), y = (int)(pix / v.W);
+  const double* rec = v.rec;
+  const double Ctp[3] = {v.Ct[pix], v.Ct[npx + pix], v.Ct[2 * npx + pix]};
+  const bool valid = v.Dtgt[pix] > 0.0 && v.Dt[pix] > 0.0 && v.n_valid > 0;
+  auto sgn = [](double s) { return s > 0 ? 1.0 : (s < 0 ? -1.0 : 0.0); };
+  // classify the candidates: fixed (decided as here whatever the rounding)
+  // or ambiguous (within a band of a threshold)
+  std::vector<Item> fixed, amb;
+  std::vector<double> qb_fixed, qb_amb;
+  std::vector<int> amb_ref;  // the FP64 decision of each ambiguous pair
+  for (int i : L.cand[pix]) {
+    const Decision d = classify(rec + (size_t)i * R_N, x, y, v.Dt[pix], v.eps, v.band, v.f32);
+    if (d.ambiguous) {
+      amb_ref.push_back(d.ref_in ? 1 : 0);
+      amb.push_back({i, d.alpha, d.G, d.dx, d.dy});
+      qb_amb.push_back(d.qband);
+    } else if (d.ref_in) {
+      fixed.push_back({i, d.alpha, d.G, d.dx, d.dy});
+      qb_fixed.push_back(d.qband);
+    }
+  }
+  const int k = (int)amb.size();
+  res.n_amb = k;
+  const bool too_many = k > v.kmax;
+  if (too_many) res.unbounded = 1;
+  int ref_mask = 0;
+  if (!too_many)
+    for (int j = 0; j < k; ++j) ref_mask |= amb_ref[j] << j;
+  const size_t nf = fixed.size(), nu = nf + (size_t)k;  // the touched Gaussians
+  const int P = v.P;
+  std::vector<double> vmax(nu * P, -INFINITY), vmin(nu * P, INFINITY);
+  std::vector<double> Cm, Dm, Wm, Lm;  // per combination
+  std::vector<std::array<double, G_N>> terms, tch;
+  bool any_free = false;
+  // with too many ambiguous decisions only the FP64 combination is evaluated
+  const int nmask = too_many ? 1 : (1 << k);
+  for (int mask = 0; mask < nmask; ++mask) {
+    const int m = too_many ? ref_mask : mask;
+    const bool is_ref = m == ref_mask;
+    auto chosen = [&](int j) { return too_many ? amb_ref[j] != 0 : ((m >> j) & 1) != 0; };
+    // the counted items, each with its slot in the union and its band
+    std::vector<Item> its = fixed;
+    std::vector<size_t> slot(nf);
+    std::vector<double> qbs = qb_fixed;
+    for (size_t t = 0; t < nf; ++t) slot[t] = t;
+    for (int j = 0; j < k; ++j)
+      if (chosen(j)) {
+        its.push_back(amb[j]);
+        slot.push_back(nf + (size_t)j);
+        qbs.push_back(qb_amb[j]);
+      }
+    std::vector<size_t> ord(its.size());
+    for (size_t t = 0; t < ord.size(); ++t) ord[t] = t;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+      double da = rec[(size_t)its[a].id * R_N + R_D], db = rec[(size_t)its[b].id * R_N + R_D];
+      if (v.f32) {
+        const float fa = (float)da, fb = (float)db;
+        if (fa != fb) return fa < fb;
+      } else if (da != db) {
+        return da < db;
+      }
+      return its[a].id < its[b].id;
+    });
+    std::vector<Item> it2(its.size());
+    std::vector<size_t> sl2(its.size());
+    std::vector<double> qb2(its.size());
+    for (size_t t = 0; t < ord.size(); ++t) {
+      it2[t] = its[ord[t]];
+      sl2[t] = slot[ord[t]];
+      qb2[t] = qbs[ord[t]];
+    }
+    // C*, D* (Eq. 4, or the front-to-back variant)
+    double Cs[3], Ds, Ws;
+    if (v.mode == 0) {
+      double Cg[3] = {0, 0, 0}, Wg = 0, Z = 0;
+      for (const Item& it : it2) {
+        const double* r = rec + (size_t)it.id * R_N;
+        for (int ch = 0; ch < 3; ++ch) Cg[ch] += r[R_R + ch] * it.alpha;
+        Wg += it.alpha;
+        Z += r[R_D] * it.alpha;
+      }
+      for (int ch = 0; ch < 3; ++ch) Cs[ch] = (Ctp[ch] + Cg[ch]) / (1.0 + Wg);
+      Ds = (v.Dt[pix] + Z) / (1.0 + Wg);
+      Ws = Wg;
+    } else {
+      double Cg[3] = {0, 0, 0}, Z = 0, T = 1.0;
+      for (const Item& it : it2) {
+        const double* r = rec + (size_t)it.id * R_N;
+        if (std::fabs(it.alpha - 0.99) < 1e-5) res.unbounded = 1;
+        const double al = std::min(it.alpha, 0.99);
+        const double test = T * (1.0 - al);
+        if (std::fabs(test - 1e-4) < 1e-9) res.unbounded = 1;
+        if (test < 1e-4) break;
+        for (int ch = 0; ch < 3; ++ch) Cg[ch] += r[R_R + ch] * al * T;
+        Z += r[R_D] * al * T;
+        T = test;
+      }
+      for (int ch = 0; ch < 3; ++ch) Cs[ch] = Cg[ch] + T * Ctp[ch];
+      Ds = Z + T * v.Dt[pix];
+      Ws = 1.0 - T;
+    }
+    // upstream gradient: the L1 signs, and the channels whose sign is free
+    double g[4] = {0, 0, 0, 0};
+    bool freec[4] = {false, false, false, false};
+    double Lx = 0.0;
+    if (v.dC) {
+      for (int ch = 0; ch < 3; ++ch) g[ch] = v.dC[ch * npx + pix];
+      g[3] = v.dD[pix];
+    } else if (valid) {
+      for (int ch = 0; ch < 3; ++ch) {
+        const double rr = Cs[ch] - v.Ctgt[ch * npx + pix];
+        Lx += std::fabs(rr) * v.sc;
+        g[ch] = sgn(rr) * v.sc;
+        freec[ch] = std::fabs(rr) < v.band[4];
+      }
+      if (v.lambda != 0.0) {
+        const double rd = Ds - v.Dtgt[pix];
+        Lx += std::fabs(rd) * v.sd;
+        g[3] = sgn(rd) * v.sd;
+        freec[3] = std::fabs(rd) < v.band[5] * v.Dtgt[pix];
+      }
+    }
+    Cm.insert(Cm.end(), Cs, Cs + 3);
+    Dm.push_back(Ds);
+    Wm.push_back(Ws);
+    Lm.push_back(Lx);
+    for (int ch = 0; ch < 4; ++ch) any_free = any_free || freec[ch];
+    if (P == 0) continue;
+    if (is_ref) {
+      // the FP64 decisions: reference gradient and the rounding sums
+      const size_t used = pixel_adjoint(it2, rec, Ctp, v.Dt[pix], g, g[3], v.mode, terms);
+      for (size_t t = 0; t < used; ++t) {
+        const size_t id = (size_t)it2[t].id;
+        for (int c = 0; c < G_N; ++c) {
+          g2ref[id * G_N + c] += terms[t][c];
+          s2[id * G_N + c] += std::fabs(terms[t][c]);
+          s2q[id * G_N + c] += std::fabs(terms[t][c]) * 0.5 * qb2[t];
+        }
+      }
+    }
+    if (res.unbounded || (k == 0 && !any_free)) continue;
+    // each touched Gaussian's term over this combination: base (free channels
+    // at 0) +- the sum over free channels of |J^T t_ch|
+    double gb[4];
+    for (int ch = 0; ch < 4; ++ch) gb[ch] = freec[ch] ? 0.0 : g[ch];
+    const size_t used = pixel_adjoint(it2, rec, Ctp, v.Dt[pix], gb, gb[3], v.mode, terms);
+    std::vector<double> vb(nu * P, 0.0), vf(nu * P, 0.0);
+    std::vector<char> present(nu, 0);
+    auto project_term = [&](size_t t, const std::array<double, G_N>& tt, bool absval,
+                            std::vector<double>& dst) {
+      const size_t id = (size_t)it2[t].id, uu = sl2[t];
+      present[uu] = 1;
+      const double* J = v.JT + id * (size_t)P * G_N;
+      for (int p = 0; p < P; ++p) {
+        double a = 0.0;
+        for (int c = 0; c < G_N; ++c) a += J[p * G_N + c] * tt[c];
+        dst[uu * P + p] += absval ? std::fabs(a) : a;
+      }
+    };
+    for (size_t t = 0; t < used; ++t) project_term(t, terms[t], false, vb);
+    for (int ch = 0; ch < 4; ++ch) {
+      if (!freec[ch]) continue;
+      double gu[4] = {0, 0, 0, 0};
+      gu[ch] = ch < 3 ? v.sc : v.sd;
+      const size_t used2 = pixel_adjoint(it2, rec, Ctp, v.Dt[pix], gu, gu[3], v.mode, tch);
+      for (size_t t = 0; t < used2; ++t) project_term(t, tch[t], true, vf);
+    }
+    for (size_t uu = 0; uu < nu; ++uu)
+      for (int p = 0; p < P; ++p) {
+        const double hi = present[uu] ? vb[uu * P + p] + vf[uu * P + p] : 0.0;
+        const double lo = present[uu] ? vb[uu * P + p] - vf[uu * P + p] : 0.0;
+        vmax[uu * P + p] = std::max(vmax[uu * P + p], hi);
+        vmin[uu * P + p] = std::min(vmin[uu * P + p], lo);
+      }
+  }
+  if (res.unbounded) {
+    res.aC = res.aD = res.aW = INFINITY;
+    return res;
+  }
+  if (k == 0 && !any_free) return res;  // one combination, fixed signs: no range
+  const size_t r0 = (size_t)ref_mask;
+  for (size_t mm = 0; mm < Dm.size(); ++mm) {
+    for (int ch = 0; ch < 3; ++ch)
+      res.aC = std::max(res.aC, std::fabs(Cm[3 * mm + ch] - Cm[3 * r0 + ch]));
+    res.aD = std::max(res.aD, std::fabs(Dm[mm] - Dm[r0]));
+    res.aW = std::max(res.aW, std::fabs(Wm[mm] - Wm[r0]));
+    res.aL = std::max(res.aL, std::fabs(Lm[mm] - Lm[r0]));
+  }
+  if (P > 0)
+    for (size_t uu = 0; uu < nu; ++uu) {
+      const size_t id = (size_t)(uu < nf ? fixed[uu].id : amb[uu - nf].id);
+      for (int p = 0; p < P; ++p) allow3[id * P + p] += vmax[uu * P + p] - vmin[uu * P + p];
+    }
+  return res;
 }
 
 }  // namespace
@@ -232,8 +705,11 @@ std::vector<Item> counted(const std::vector<int>& cand, const double* rec, int x
 extern "C" {
 
 // Projection of M Gaussians into one view.  rec: M x R_N doubles (layout in the
-// enum above).  amb[i] = 1 when a visibility or clamp decision sits within a
-// relative 1e-6 of its threshold.  Returns the number of visible Gaussians.
+// enum above).  amb[i] != 0 when a decision of the projection sits within a
+// relative 1e-6 of its threshold: bit 0 the visibility (near plane, sigma >=
+// 1/255), bit 1 the Jacobian clamp (continuous in the forward; only its
+// derivative jumps), bit 2 the extent's test against the image border (within
+// 1e-3 px).  Returns the number of visible Gaussians.
 int orc_project(int M, const double* means, const double* log_scales, const double* quats,
                 const double* logits, const double* rgb, int W, int H, const double* K,
                 const double* R, const double* t, double near_, double* rec, int* amb) {
@@ -252,17 +728,18 @@ int orc_project(int M, const double* means, const double* log_scales, const doub
     if (amb) {
       const double limx = 1.3 * (W / (2.0 * K[0])), limy = 1.3 * (H / (2.0 * K[1]));
       double tz = P.tc[2];
-      bool a = std::fabs(tz - near_) < 1e-6 * near_ ||
-               std::fabs(P.sig - 1.0 / 255.0) < 1e-6 / 255.0;
+      int a = (std::fabs(tz - near_) < 1e-6 * near_ ||
+               std::fabs(P.sig - 1.0 / 255.0) < 1e-6 / 255.0) ? 1 : 0;
       if (tz > near_) {
-        a = a || std::fabs(std::fabs(P.tc[0] / tz) - limx) < 1e-6 * limx ||
-            std::fabs(std::fabs(P.tc[1] / tz) - limy) < 1e-6 * limy;
-        if (P.det > 0 && P.sig >= 1.0 / 255.0) {
-          a = a || std::fabs(P.mx + P.ex) < 1e-3 || std::fabs(P.mx - P.ex - (W - 1)) < 1e-3 ||
-              std::fabs(P.my + P.ey) < 1e-3 || std::fabs(P.my - P.ey - (H - 1)) < 1e-3;
-        }
+        if (std::fabs(std::fabs(P.tc[0] / tz) - limx) < 1e-6 * limx ||
+            std::fabs(std::fabs(P.tc[1] / tz) - limy) < 1e-6 * limy)
+          a |= 2;
+        if (P.det > 0 && P.sig >= 1.0 / 255.0 &&
+            (std::fabs(P.mx + P.ex) < 1e-3 || std::fabs(P.mx - P.ex - (W - 1)) < 1e-3 ||
+             std::fabs(P.my + P.ey) < 1e-3 || std::fabs(P.my - P.ey - (H - 1)) < 1e-3))
+          a |= 4;
       }
-      amb[i] = a ? 1 : 0;
+      amb[i] = a;
     }
   }
   return nvis;
@@ -279,11 +756,11 @@ int orc_project(int M, const double* means, const double* log_scales, const doub
 // Outputs: C* [3][H][W], D*, W_G, T_end, n_counted (all [H][W]); amb[pix] = 1 when
 // a FP32 implementation could take a different clamp / termination decision.
 // Window [x0, x1] x [y0, y1] restricts the work (pixels outside are left 0).
+// flip: the diagnostic decisions of `counted`.
 void orc_composite(int M, const double* rec, int W, int H, const double* Ct, const double* Dt,
                    double eps, int mode, int f32, int brute, int x0, int x1, int y0, int y1,
                    double* out_C, double* out_D, double* out_W, double* out_T, int* out_n,
-                   int* amb, const double* band, double* allow, double* g_amb, double* g_mass,
-                   const double* flip) {
+                   int* amb, const double* flip) {
   Lists L = build_lists(M, rec, W, H, brute, x0, x1, y0, y1);
   const long npx = (long)W * H;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -329,51 +806,6 @@ void orc_composite(int M, const double* rec, int W, int H, const double* Ct, con
     }
     out_n[pix] = n;
     if (amb) amb[pix] = a ? 1 : 0;
-    if (allow) {
-      // Bound on how much C* (allow[0]) and D* (allow[1]) can move
-      // if every counting decision lying within the error band of its
-      // threshold were taken the other way, as a single-precision evaluation
-      // may.  Support: |qmax - q| < band[0] (|q| + (|a| + 2|b| + |c|)(dx^2 + dy^2)),
-      // the rounding error of q from a conic known to a relative band[0];
-      // depth: |d - (D_t + eps)| < band[1] (D_t + eps).  g_amb / g_mass collect,
-      // per Gaussian, the alpha of such decisions and its total counted alpha.
-      const double thr = Dt[pix] > 0.0 ? Dt[pix] + eps : INFINITY;
-      const double N = 1.0 + Wg;
-      const double Cs[3] = {out_C[pix], out_C[npx + pix], out_C[2 * npx + pix]};
-      double aC = 0.0, aD = 0.0;
-      for (int i : L.cand[pix]) {
-        const double* r = rec + (size_t)i * R_N;
-        double dx = x - r[R_MX], dy = y - r[R_MY];
-        double q = r[R_CA] * dx * dx + 2.0 * r[R_CB] * dx * dy + r[R_CC] * dy * dy;
-        double al = r[R_SIG] * std::exp(-0.5 * q);
-        const double cn = std::fabs(r[R_CA]) + 2.0 * std::fabs(r[R_CB]) + std::fabs(r[R_CC]);
-        const double qband = band[0] * (std::fabs(q) + cn * (dx * dx + dy * dy));
-        bool near_s = std::fabs(r[R_QMAX] - q) < qband;
-        bool near_d = std::isfinite(thr) && std::fabs(r[R_D] - thr) < band[1] * thr;
-        bool in_s = q <= r[R_QMAX] + qband;
-        bool cnt = al >= 1.0 / 255.0 && r[R_D] < thr;
-        if (cnt) {
-#pragma omp atomic
-          g_mass[i] += al;
-        }
-        if (!(near_s || (near_d && in_s))) continue;
-        double dc = 0.0;
-        for (int ch = 0; ch < 3; ++ch) dc = std::max(dc, std::fabs(r[R_R + ch] - Cs[ch]));
-        if (mode == 0) {
-          // exact change of (C_t + C_G) / N when alpha leaves (N - alpha) or joins (N + alpha)
-          const double Nm = std::max(N - al, 1.0);
-          aC += al * dc / Nm;
-          aD += al * std::fabs(r[R_D] - out_D[pix]) / Nm;
-        } else {
-          aC += al * (1.0 + 1.0 / (1.0 - std::min(al, 0.99)));
-          aD += al * (r[R_D] + out_D[pix] / (1.0 - std::min(al, 0.99)));
-        }
-#pragma omp atomic
-        g_amb[i] += al;
-      }
-      allow[pix] = a ? INFINITY : aC;
-      allow[npx + pix] = a ? INFINITY : aD;
-    }
   }
 }
 
@@ -420,16 +852,15 @@ double orc_loss(int W, int H, const double* C, const double* D, const double* Ct
 // Adjoint of orc_composite with respect to the per-Gaussian 2D quantities,
 // accumulated into g2 (M x G_N, zeroed here): d/d mean(2), d/d conic (a, b, c
 // with q = a dx^2 + 2 b dx dy + c dy^2), d/d sigma, d/d rgb(3), d/d depth.
-// The counting decisions are constants; alpha clamped at 0.99 has zero
-// derivative.  Mode 0 (Eq. 4): with N = 1 + W_G,
-//   dC*/dc_i = a_i / N,  dC*/da_i = (c_i - C*) / N,  and likewise for depth.
-// Mode 1: dC*/dc_i = a_i T_i,  dC*/da_i = c_i T_i - (sum_{j>i} c_j a_j T_j + T_end C_t) / (1 - a_i).
+// The counting decisions are constants; the per-pixel terms are those of
+// pixel_adjoint, summed over the pixels in row-major order.
 void orc_composite_backward(int M, const double* rec, int W, int H, const double* Ct,
                             const double* Dt, double eps, int mode, int f32, const double* dC,
                             const double* dD, double* g2, const double* flip) {
   Lists L = build_lists(M, rec, W, H, 0, 0, W - 1, 0, H - 1);
   std::memset(g2, 0, sizeof(double) * (size_t)M * G_N);
   const long npx = (long)W * H;
+  std::vector<std::array<double, G_N>> terms;
   for (long pix = 0; pix < npx; ++pix) {
     int x = (int)(pix % W), y = (int)(pix / W);
     const double g[3] = {dC[pix], dC[npx + pix], dC[2 * npx + pix]};
@@ -438,86 +869,18 @@ void orc_composite_backward(int M, const double* rec, int W, int H, const double
     std::vector<Item> its = counted(L.cand[pix], rec, x, y, Dt[pix], eps, f32, flip);
     if (its.empty()) continue;
     const double Ctp[3] = {Ct[pix], Ct[npx + pix], Ct[2 * npx + pix]};
-    const size_t n = its.size();
-    std::vector<double> a(n), T(n), dLda(n), dLdd(n);
-    std::vector<bool> clamped(n, false);
-    std::vector<std::array<double, 3>> dLdc(n);
-    size_t used = n;
-    if (mode == 0) {
-      double Cg[3] = {0, 0, 0}, Wg = 0, Z = 0;
-      for (size_t k = 0; k < n; ++k) {
-        const double* r = rec + (size_t)its[k].id * R_N;
-        a[k] = its[k].alpha;
-        for (int ch = 0; ch < 3; ++ch) Cg[ch] += r[R_R + ch] * a[k];
-        Wg += a[k];
-        Z += r[R_D] * a[k];
-      }
-      double N = 1.0 + Wg, Cs[3], Ds = (Dt[pix] + Z) / N;
-      for (int ch = 0; ch < 3; ++ch) Cs[ch] = (Ctp[ch] + Cg[ch]) / N;
-      for (size_t k = 0; k < n; ++k) {
-        const double* r = rec + (size_t)its[k].id * R_N;
-        double v = 0;
-        for (int ch = 0; ch < 3; ++ch) {
-          dLdc[k][ch] = g[ch] * a[k] / N;
-          v += g[ch] * (r[R_R + ch] - Cs[ch]) / N;
-        }
-        v += gD * (r[R_D] - Ds) / N;
-        dLda[k] = v;
-        dLdd[k] = gD * a[k] / N;
-      }
-    } else {
-      double Tc = 1.0;
-      used = 0;
-      for (size_t k = 0; k < n; ++k) {
-        double al = its[k].alpha;
-        clamped[k] = al > 0.99;
-        al = std::min(al, 0.99);
-        if (Tc * (1.0 - al) < 1e-4) break;
-        a[k] = al;
-        T[k] = Tc;
-        Tc *= (1.0 - al);
-        ++used;
-      }
-      const double Tend = Tc;
-      double S[3] = {Tend * Ctp[0], Tend * Ctp[1], Tend * Ctp[2]}, SD = Tend * Dt[pix];
-      for (size_t kk = used; kk-- > 0;) {
-        const double* r = rec + (size_t)its[kk].id * R_N;
-        double v = 0;
-        for (int ch = 0; ch < 3; ++ch) {
-          dLdc[kk][ch] = g[ch] * a[kk] * T[kk];
-          v += g[ch] * (r[R_R + ch] * T[kk] - S[ch] / (1.0 - a[kk]));
-        }
-        v += gD * (r[R_D] * T[kk] - SD / (1.0 - a[kk]));
-        dLda[kk] = v;
-        dLdd[kk] = gD * a[kk] * T[kk];
-        for (int ch = 0; ch < 3; ++ch) S[ch] += r[R_R + ch] * a[kk] * T[kk];
-        SD += r[R_D] * a[kk] * T[kk];
-      }
-    }
+    const size_t used = pixel_adjoint(its, rec, Ctp, Dt[pix], g, gD, mode, terms);
     for (size_t k = 0; k < used; ++k) {
-      const double* r = rec + (size_t)its[k].id * R_N;
       double* o = g2 + (size_t)its[k].id * G_N;
-      for (int ch = 0; ch < 3; ++ch) o[G_R + ch] += dLdc[k][ch];
-      o[G_D] += dLdd[k];
-      if (clamped[k]) continue;
-      // alpha = sigma G, G = exp(-q/2)
-      const double G = its[k].G, al = its[k].alpha, dx = its[k].dx, dy = its[k].dy;
-      o[G_SIG] += dLda[k] * G;
-      double dq = dLda[k] * (-0.5 * al);
-      o[G_CA] += dq * dx * dx;
-      o[G_CB] += dq * 2.0 * dx * dy;
-      o[G_CC] += dq * dy * dy;
-      // dq/dmean = -2 (conic . delta)
-      o[G_MX] += dq * -2.0 * (r[R_CA] * dx + r[R_CB] * dy);
-      o[G_MY] += dq * -2.0 * (r[R_CB] * dx + r[R_CC] * dy);
+      for (int c = 0; c < G_N; ++c) o[c] += terms[k][c];
     }
   }
 }
 
 // Adjoint of orc_project: per-Gaussian 2D gradients (M x G_N) -> gradients of
 // means, log-scales, quaternions (through the normalisation), opacity logits
-// and rgb.  Outputs are overwritten.  Invisible Gaussians get zeros.  The
-// Jacobian clamp is differentiated exactly (a clamped t_x' = +-lim t_z).
+// and rgb (proj_adjoint per Gaussian).  Outputs are overwritten.  Invisible
+// Gaussians get zeros.
 void orc_project_backward(int M, const double* means, const double* log_scales,
                           const double* quats, const double* logits, int W, int H,
                           const double* K, const double* R, const double* t, double near_,
@@ -526,7 +889,6 @@ void orc_project_backward(int M, const double* means, const double* log_scales,
   Cam c{K[0], K[1], K[2], K[3], W, H, R, t};
   for (int i = 0; i < M; ++i) {
     Proj P = project_one(c, means + 3 * i, log_scales + 3 * i, quats + 4 * i, logits[i], near_);
-    const double* g = g2 + (size_t)i * G_N;
     double* dm = d_means + 3 * i;
     double* dl = d_ls + 3 * i;
     double* dq = d_quats + 4 * i;
@@ -534,99 +896,117 @@ void orc_project_backward(int M, const double* means, const double* log_scales,
     for (int k = 0; k < 4; ++k) dq[k] = 0;
     d_logits[i] = 0;
     if (!P.vis) continue;
-    for (int k = 0; k < 3; ++k) d_rgb[3 * i + k] = g[G_R + k];
-    d_logits[i] = g[G_SIG] * P.sig * (1.0 - P.sig);
-    // conic = inverse(Sigma_2D): dL/dSigma_2D = -C Gs C with Gs the symmetric
-    // gradient of the conic matrix (off-diagonals carry half of dL/db).
-    const double Cm[4] = {P.conic[0], P.conic[1], P.conic[1], P.conic[2]};
-    const double Gs[4] = {g[G_CA], 0.5 * g[G_CB], 0.5 * g[G_CB], g[G_CC]};
-    double tmp[4], dS2[4];
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b) {
-        tmp[a * 2 + b] = 0;
-        for (int k = 0; k < 2; ++k) tmp[a * 2 + b] += Cm[a * 2 + k] * Gs[k * 2 + b];
-      }
-    for (int a = 0; a < 2; ++a)
-      for (int b = 0; b < 2; ++b) {
-        dS2[a * 2 + b] = 0;
-        for (int k = 0; k < 2; ++k) dS2[a * 2 + b] -= tmp[a * 2 + k] * Cm[k * 2 + b];
-      }
-    // Sigma_2D = T Sigma T^T (+0.3 I): dT = 2 dS2 T Sigma, dSigma = T^T dS2 T
-    double dT[6], dSig[9];
-    for (int a = 0; a < 2; ++a)
-      for (int j = 0; j < 3; ++j) {
-        double s = 0;
-        for (int b = 0; b < 2; ++b)
-          for (int k = 0; k < 3; ++k) s += dS2[a * 2 + b] * P.T[b * 3 + k] * P.Sig[k * 3 + j];
-        dT[a * 3 + j] = 2.0 * s;
-      }
-    for (int k = 0; k < 3; ++k)
-      for (int l = 0; l < 3; ++l) {
-        double s = 0;
-        for (int a = 0; a < 2; ++a)
-          for (int b = 0; b < 2; ++b) s += P.T[a * 3 + k] * dS2[a * 2 + b] * P.T[b * 3 + l];
-        dSig[k * 3 + l] = s;
-      }
-    // T = J W with W[k][j] = R[j][k]  =>  dJ[a][k] = sum_j dT[a][j] R[j][k]
-    double dJ[6];
-    for (int a = 0; a < 2; ++a)
-      for (int k = 0; k < 3; ++k) {
-        double s = 0;
-        for (int j = 0; j < 3; ++j) s += dT[a * 3 + j] * R[j * 3 + k];
-        dJ[a * 3 + k] = s;
-      }
-    const double tz = P.tc[2], tz2 = tz * tz, tz3 = tz2 * tz;
-    double dtc[3] = {0, 0, 0};
-    dtc[2] += dJ[0] * (-c.fx / tz2) + dJ[4] * (-c.fy / tz2) + dJ[2] * (2.0 * c.fx * P.txp / tz3) +
-              dJ[5] * (2.0 * c.fy * P.typ / tz3);
-    const double dtxp = dJ[2] * (-c.fx / tz2), dtyp = dJ[5] * (-c.fy / tz2);
-    if (P.clx)
-      dtc[2] += dtxp * (P.txp / tz);  // t_x' = +-lim t_z
-    else
-      dtc[0] += dtxp;
-    if (P.cly)
-      dtc[2] += dtyp * (P.typ / tz);
-    else
-      dtc[1] += dtyp;
-    // mean2D = (fx tx / tz + cx, fy ty / tz + cy); depth = tz
-    dtc[0] += g[G_MX] * c.fx / tz;
-    dtc[1] += g[G_MY] * c.fy / tz;
-    dtc[2] += -g[G_MX] * c.fx * P.tc[0] / tz2 - g[G_MY] * c.fy * P.tc[1] / tz2 + g[G_D];
-    // tc = R^T (p - c)  =>  dp = R dtc
-    for (int r = 0; r < 3; ++r) dm[r] = R[r * 3 + 0] * dtc[0] + R[r * 3 + 1] * dtc[1] + R[r * 3 + 2] * dtc[2];
-    // Sigma = Mg Mg^T, Mg = Rg diag(s): dMg = 2 dSigma Mg
-    double Mg[9], dMg[9];
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) Mg[a * 3 + b] = P.Rg[a * 3 + b] * P.s[b];
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        double s = 0;
-        for (int k = 0; k < 3; ++k) s += dSig[a * 3 + k] * Mg[k * 3 + b];
-        dMg[a * 3 + b] = 2.0 * s;
-      }
-    double dRg[9];
-    for (int b = 0; b < 3; ++b) {
-      double ds = 0;
-      for (int a = 0; a < 3; ++a) {
-        dRg[a * 3 + b] = dMg[a * 3 + b] * P.s[b];
-        ds += dMg[a * 3 + b] * P.Rg[a * 3 + b];
-      }
-      dl[b] = ds * P.s[b];
+    proj_adjoint(c, P, g2 + (size_t)i * G_N, dm, dl, dq, d_logits + i, d_rgb + 3 * i);
+  }
+}
+
+// Decision envelope of one view (test infrastructure for comparing a
+// single-precision evaluation with this FP64 one).
+//
+// Gradient and image are sums over pixels of per-pixel terms (Eq. 4 and the
+// Eq. 6 loss are per pixel; N_v does not depend on the Gaussians), and each
+// pixel's terms depend only on that pixel's discrete decisions: which
+// Gaussians count (alpha >= 1/255 and d < D_t + eps, Eq. 1-3) and the sign
+// of each L1 residual.  A decision whose quantity lies within the error band
+// of its threshold may be taken either way by an FP32 evaluation:
+//   support:  |qmax - q| < qband = band[0] cn r^2 + 2 band[1] cn r + band[2] qmax,
+//             cn = |a| + 2|b| + |c|, r = |(dx, dy)|: the change of q when the
+//             conic moves by band[0] cn, the mean by band[1] px and qmax by
+//             band[2] of itself (the FP32 rounding of q's own products is
+//             below u cn r^2 and taken into band[0]);
+//   depth:    |d - (D_t + eps)| < band[3] (D_t + eps);
+//   colour residual |C* - C| < band[4], depth residual |D* - D| < band[5] D.
+// Every other decision is taken as here.  Per pixel the envelope enumerates
+// every combination of its k ambiguous counting decisions (k <= kmax, else
+// the pixel is flagged in `unbounded`) and, per combination, lets each
+// ambiguous residual sign range over +-1 (the terms are linear in the
+// upstream gradient, so the extremes lie at the signs).  For every
+// Gaussian touched and every parameter p it takes the range (max - min over
+// the combinations, a Gaussian absent from a combination contributing 0) of
+// the pixel's term J^T t, J^T = JT[i] (P x G_N, the projection adjoint of
+// Gaussian i), and adds it to allow3[i][p].  So a single-precision gradient
+// that decides everything outside the bands as here lies within allow3 of
+// the FP64 gradient, up to its own rounding.  Likewise allow_img[0][pix]
+// (max over channels), allow_img[1][pix] and allow_img[2][pix] bound
+// |C* - C*_ref|, |D* - D*_ref| and |W_G - W_G,ref|, and *allow_loss the loss.
+// Also returned: n_amb[pix] (ambiguous counting decisions), g2ref (the 2D
+// gradient of the FP64 decisions, the sum of pixel_adjoint terms in row-major
+// pixel order, as orc_composite_backward), s2[i][c] = sum over pixels of
+// |term| and s2q[i][c] = sum over pixels of |term| * qband / 2 (alpha's
+// relative error bound from q's band), both per 2D component.
+// In mode 1 a pixel whose clamp or termination decision lies within 1e-5
+// (1e-9 on T) of its threshold is flagged in `unbounded` too.
+// f32 != 0: the counting decisions in FP32 as `counted` takes them (records
+// holding FP32 values), nothing ambiguous: only g2ref, s2 and s2q are of use.
+// dC, dD (nullable): explicit upstream gradients dL/dC*, dL/dD* in place of
+// the L1 loss's (then no sign is free and the loss envelope is 0).
+// Returns the number of unbounded pixels.
+int orc_envelope(int M, const double* rec, int W, int H, const double* Ct, const double* Dt,
+                 double eps, int mode, const double* Ctgt, const double* Dtgt, double lambda,
+                 long n_valid, const double* band, int P, const double* JT, int kmax, int f32,
+                 const double* dC, const double* dD, double* allow_img, double* allow_loss, int* n_amb, int* unbounded,
+                 double* allow3, double* g2ref, double* s2, double* s2q) {
+  Lists L = build_lists(M, rec, W, H, 0, 0, W - 1, 0, H - 1);
+  const long npx = (long)W * H;
+  const double no_band[6] = {0, 0, 0, 0, 0, 0};
+  if (f32) band = no_band;
+  EnvView v{M, W, H, mode, P, kmax, f32, rec, Ct, Dt, Ctgt, Dtgt, band, JT, eps,
+            n_valid > 0 ? 1.0 / (3.0 * (double)n_valid) : 0.0,
+            n_valid > 0 ? lambda / (double)n_valid : 0.0, lambda, n_valid, dC, dD};
+  if (P > 0) {
+    std::memset(allow3, 0, sizeof(double) * (size_t)M * P);
+    std::memset(g2ref, 0, sizeof(double) * (size_t)M * G_N);
+    std::memset(s2, 0, sizeof(double) * (size_t)M * G_N);
+    std::memset(s2q, 0, sizeof(double) * (size_t)M * G_N);
+  }
+  std::vector<EnvPixel> res((size_t)npx);
+  if (P > 0) {
+    // per-Gaussian sums in row-major pixel order (g2ref equals
+    // orc_composite_backward's sum bit for bit)
+    for (long pix = 0; pix < npx; ++pix)
+      res[pix] = envelope_pixel(v, L, pix, allow3, g2ref, s2, s2q);
+  } else {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long pix = 0; pix < npx; ++pix)
+      res[pix] = envelope_pixel(v, L, pix, nullptr, nullptr, nullptr, nullptr);
+  }
+  int n_unb = 0;
+  double aL = 0.0;
+  for (long pix = 0; pix < npx; ++pix) {
+    n_amb[pix] = res[pix].n_amb;
+    unbounded[pix] = res[pix].unbounded;
+    allow_img[pix] = res[pix].aC;
+    allow_img[npx + pix] = res[pix].aD;
+    allow_img[2 * npx + pix] = res[pix].aW;
+    aL += res[pix].aL;
+    n_unb += res[pix].unbounded;
+  }
+  *allow_loss = aL;
+  return n_unb;
+}
+
+// Magnitudes of orc_project_backward's results (same arguments; outputs
+// overwritten): the adjoint evaluated in magnitude arithmetic (mag.h) from
+// |g2|, so that a single-precision adjoint's rounding error is bounded by a
+// small multiple of u times these, per element.
+void orc_project_backward_mag(int M, const double* means, const double* log_scales,
+                              const double* quats, const double* logits, int W, int H,
+                              const double* K, const double* R, const double* t, double near_,
+                              const double* g2, double* d_means, double* d_ls, double* d_quats,
+                              double* d_logits, double* d_rgb) {
+  Cam c{K[0], K[1], K[2], K[3], W, H, R, t};
+  for (int i = 0; i < M; ++i) {
+    Proj P = project_one(c, means + 3 * i, log_scales + 3 * i, quats + 4 * i, logits[i], near_);
+    Mag g[G_N], dm[3], dl[3], dq[4], dlg, drgb[3];
+    for (int k = 0; k < G_N; ++k) g[k] = Mag(g2[(size_t)i * G_N + k]);
+    if (P.vis) proj_adjoint_t<Mag>(c, P, g, dm, dl, dq, &dlg, drgb);
+    for (int k = 0; k < 3; ++k) {
+      d_means[3 * i + k] = dm[k].v;
+      d_ls[3 * i + k] = dl[k].v;
+      d_rgb[3 * i + k] = drgb[k].v;
     }
-    // rotation matrix entries as polynomials of the unit quaternion (w, x, y, z)
-    const double w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
-    double dqn[4];
-    dqn[0] = dRg[1] * (-2 * z) + dRg[2] * (2 * y) + dRg[3] * (2 * z) + dRg[5] * (-2 * x) +
-             dRg[6] * (-2 * y) + dRg[7] * (2 * x);
-    dqn[1] = dRg[1] * (2 * y) + dRg[2] * (2 * z) + dRg[3] * (2 * y) + dRg[4] * (-4 * x) +
-             dRg[5] * (-2 * w) + dRg[6] * (2 * z) + dRg[7] * (2 * w) + dRg[8] * (-4 * x);
-    dqn[2] = dRg[0] * (-4 * y) + dRg[1] * (2 * x) + dRg[2] * (2 * w) + dRg[3] * (2 * x) +
-             dRg[5] * (2 * z) + dRg[6] * (-2 * w) + dRg[7] * (2 * z) + dRg[8] * (-4 * y);
-    dqn[3] = dRg[0] * (-4 * z) + dRg[1] * (-2 * w) + dRg[2] * (2 * x) + dRg[3] * (2 * w) +
-             dRg[4] * (-4 * z) + dRg[5] * (2 * y) + dRg[6] * (2 * x) + dRg[7] * (2 * y);
-    // qn = q / |q|: dq = (dqn - qn (qn . dqn)) / |q|
-    double dot = w * dqn[0] + x * dqn[1] + y * dqn[2] + z * dqn[3];
-    for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - P.qn[k] * dot) / P.qnorm;
+    for (int k = 0; k < 4; ++k) d_quats[4 * i + k] = dq[k].v;
+    d_logits[i] = dlg.v;
   }
 }
 

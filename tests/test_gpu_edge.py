@@ -103,9 +103,12 @@ def test_image_smaller_than_a_tile_matches_oracle(tile):
     rec, _ = oracle.project(gs.astype(np.float64), cam)
     out = oracle.composite(rec, Ct, Dt, 0.01, oracle.OIT, brute=True)
     assert out["W"].max() > 0.1
-    ok = np.isfinite(out["allow_C"])
-    np.testing.assert_allclose(c[:, ok], out["C"][:, ok], atol=1e-4 + out["allow_C"][ok].max())
-    np.testing.assert_allclose(wg[ok], out["W"][ok], atol=1e-4 + out["allow_C"][ok].max())
+    # per pixel: 1e-4 plus the oracle's envelope of decisions within the FP32 bands
+    env = oracle.envelope(rec, Ct, Dt, 0.01, oracle.OIT, tgt, Dt, 0.0, 1)
+    ok = env["unbounded"] == 0
+    assert ok.all()
+    assert np.all(np.abs(c - out["C"]).max(0) <= 1e-4 + env["allow_C"])
+    assert np.all(np.abs(wg - out["W"]) <= 1e-4 + env["allow_W"])
 
 
 def test_one_gaussian_covering_the_whole_image():

@@ -2,13 +2,20 @@
 
 Stage by stage (each stage fed identical inputs, written into the workspace
 where needed, so both sides take identical counting decisions) and end to
-end.  Tolerances, derived from the FP32 arithmetic of each step: staged
-images 1e-5, staged 2D gradients per tensor ||g - o||_inf <= 1e-4 ||o||_inf
-and 1e-4 relative elementwise where |o| > 1e-3 ||o||_inf (the sort-free
-backward's atomics in no fixed order: 99.9% of those within 1e-4, all within
-1e-3); end to end: images 1e-4 plus the flip allowance, gradients after the
-flip / sign envelopes 1e-3 norm-wise, 99.5% of elements within 1e-3 and all
-within 5e-2; binning and sort order bit-exact."""
+end.  Tolerances, derived from the FP32 arithmetic of each step:
+  * staged images 1e-5; staged 2D gradients per element 1e-4 |o| (ALPHA
+    2e-4) plus the FP32 sum bound KAPPA_SUM u sum|t| from the oracle's own
+    terms, and 1e-4 ||o||_inf plus that bound for every element;
+  * staged projection adjoint: 1e-4 |o| plus (8 cond(Sigma_2D) + 64) u
+    |J^T| |g2| per element;
+  * end to end (kernel FP32 projection vs oracle FP64): the kernel's records
+    first held to the bounds the oracle's error bands assume; images 1e-4
+    plus the exact decision envelope; gradients 1e-4 |o| plus the envelope
+    and the rounding terms of assert_grads_in_envelope, per element, with no
+    fraction of elements exempt;
+  * binning and sort order bit-exact."""
+import json
+
 import numpy as np
 import pytest
 import torch
@@ -17,7 +24,9 @@ import oracle
 import paper_2509_11574_b300 as gps
 from datagen import GaussianSet, workloads
 
-from helpers import assert_grads_close, cuda, oracle_sdf_images, sign_flip_allowance, workload
+from helpers import (KAPPA_SUM, U32, assert_grads_close, assert_grads_in_envelope,
+                     assert_projection_adjoint, assert_record_bounds, cuda, gaussians_over,
+                     oracle_sdf_images, projection_skip, workload)
 
 pytestmark = pytest.mark.gpu
 
@@ -250,21 +259,29 @@ def test_composite_forward_and_backward_staged(mode, tile):
                 ex, ey = rr[i, oracle.R_EX] + 1, rr[i, oracle.R_EY] + 1
                 excl[i] = np.any((np.abs(xs - rr[i, oracle.R_MX]) <= ex) & (np.abs(ys - rr[i, oracle.R_MY]) <= ey))
     names = ["mx", "my", "ca", "cb", "cc", "sig", "r", "g", "b", "d"]
-    # OIT: 1e-4.  ALPHA: the backward recomputes T_i = T_{i+1} / (1 - alpha_i)
-    # from T_end; the kernel's alpha carries ~5e-7 relative rounding (FP32
-    # exponent argument and ex2), which 1 / (1 - alpha) <= 100 amplifies for
-    # every near-opaque Gaussian the reverse walk passes: 2e-4.
-    tol = 1e-4 if mode == gps.BLEND_OIT else 2e-4
-    # OIT (sort-free default): each (warp block, Gaussian) partial is added
-    # to grad2d by an atomic in no fixed order, so an element's FP32 sum is
-    # off by up to about n u sum|t| (n ~ 32 pixels + the atomics, u = 2^-24):
-    # relative to |sum t| that exceeds 1e-4 only where the terms cancel more
-    # than ~30-fold.  Elementwise, 99.9% must meet 1e-4 and all 1e-3; the
-    # norm criterion stays 1e-4.
-    quant = (0.999, 1e-3) if mode == gps.BLEND_OIT else None
-    assert_grads_close({n: g2[:, k] for k, n in enumerate(names)},
-                       {n: g2_o[:, k] for k, n in enumerate(names)}, exclude=excl,
-                       norm_tol=tol, elem_tol=tol, label=f"grad2d mode={mode}", quantile=quant)
+    # Per element: rel |o| + KAPPA_SUM u s2, s2 the sum over pixels of the
+    # oracle's |terms| of that element (same FP32 records and decisions on both
+    # sides, so only the kernel's FP32 sums and terms differ; the sort-free
+    # backward's atomics add in no fixed order, which the bound covers).
+    # rel = 1e-4 (OIT); ALPHA 2e-4: its backward recomputes T_i =
+    # T_{i+1} / (1 - alpha_i) from T_end, and the kernel's alpha carries
+    # ~5e-7 relative rounding (FP32 exponent argument and ex2), which
+    # 1 / (1 - alpha) <= 100 amplifies at every near-opaque Gaussian passed.
+    rel = 1e-4 if mode == gps.BLEND_OIT else 2e-4
+    env = oracle.envelope(rr, Ct, Dt, w.eps_depth, mode, f.rgb, f.depth, 0.0, 1,
+                          JT=np.tile(np.eye(oracle.G_N)[None], (r.M, 1, 1)), f32=True, dC=dC, dD=dD)
+    np.testing.assert_array_equal(env["g2ref"], g2_o)
+    slack = KAPPA_SUM * U32 * env["s2"]
+    keep = np.ones(r.M, bool) if excl is None else ~excl
+    for k, n in enumerate(names):
+        o, gg, sl = g2_o[keep, k], g2[keep, k].astype(np.float64), slack[keep, k]
+        scale = np.abs(o).max()
+        err = np.abs(gg - o)
+        big = np.abs(o) > 1e-3 * scale
+        assert np.all(err <= rel * scale + sl), (n, ((err - sl) / scale).max())
+        assert np.all(err[big] <= rel * np.abs(o[big]) + sl[big]), \
+            (n, ((err - sl)[big] / np.abs(o[big])).max())
+        print(f"grad2d mode={mode} {n}: within {rel} |o| raw {np.mean(err[big] <= rel * np.abs(o[big])):.5f}")
 
 
 def test_projection_backward_staged():
@@ -290,8 +307,10 @@ def test_projection_backward_staged():
     for k in ref:
         ref[k] = np.where(vis.reshape((-1,) + (1,) * (ref[k].ndim - 1)), ref[k], 0)
         got[k] = np.where(vis.reshape((-1,) + (1,) * (got[k].ndim - 1)), got[k], 0)
-    # the adjoint of a projection with cond(Sigma_2D) up to ~1e4 in FP32
-    assert_grads_close(got, ref, norm_tol=1e-4, elem_tol=1e-3, label="project_backward")
+    # per element 1e-4 |o| plus the FP32 bound of the adjoint's chain
+    # (see projection_rounding)
+    worst = assert_projection_adjoint(got, ref, g64, f.cam, g2, rec_o, vis, label="project_backward")
+    print("project_backward: worst error / bound", worst)
 
 
 # ---------------------------------------------------------- end to end
@@ -319,19 +338,25 @@ def test_end_to_end_reduced_precision_colour(mode, prec):
     _end_to_end(w, mode, lam=1.0, prec=prec)
 
 
-def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False, prec=gps.PREC_FP32, gs=None):
-    """gs: the Gaussian set to render (default: the workload's)."""
+def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False, prec=gps.PREC_FP32, gs=None,
+                schedule=gps.SCHEDULE_TILES):
+    """gs: the Gaussian set to render (default: the workload's).  Images,
+    loss and every parameter gradient against the FP64 oracle under its
+    decision envelope (see assert_grads_in_envelope); the kernel's own
+    records are first held to the error bounds the envelope's bands assume.
+    Returns what the checks saw."""
     f = w.frames[0]
     H, W = f.cam.height, f.cam.width
     gs = gs if gs is not None else w.gaussians
+    g64 = gs.astype(np.float64)
     Ct, Dt, _, _ = oracle_sdf_images(w)
     # colour images as stored (oracle.quantise: float32 for PREC_FP32)
     Ct = oracle.quantise(Ct, prec).astype(np.float32)
     Ctgt = oracle.quantise(f.rgb, prec).astype(np.float32)
-    ref = oracle.render_loss_grads(gs.astype(np.float64), f.cam, Ct, Dt, Ctgt, f.depth,
-                                   eps=w.eps_depth, lambda_depth=lam, mode=mode)
+    ref = oracle.render_loss_grads(g64, f.cam, Ct, Dt, Ctgt, f.depth, eps=w.eps_depth,
+                                   lambda_depth=lam, mode=mode)
     s = gps.settings(eps_depth=w.eps_depth, lambda_depth=lam, blend_mode=mode, tile=tile,
-                     deterministic=deterministic, precision=prec)
+                     deterministic=deterministic, precision=prec, schedule=schedule)
     r = gps.Renderer(gs.M, [f.cam], s)
     g = gps.Gaussians.from_numpy(gs)
     cdt = gps.PREC_DTYPE[prec]
@@ -343,56 +368,33 @@ def _end_to_end(w, mode, lam, tile=(16, 16), deterministic=False, prec=gps.PREC_
     grads = g.zeros_like()
     r.backward(g, [v], grads)
     assert r.status() == gps.GPS_OK
-    out = ref["out"]
-    # pixels under a Gaussian whose visibility / clamp decision is itself
-    # ambiguous are left out; everywhere else every pixel must be within
-    # 1e-4 plus the flip allowance of its near-threshold decisions
-    rec = ref["rec"]
-    skip = np.zeros((H, W), bool)
-    for i in np.nonzero(ref["proj_amb"])[0]:
-        x0, x1 = int(max(0, rec[i, oracle.R_MX] - rec[i, oracle.R_EX] - 2)), int(min(W - 1, rec[i, oracle.R_MX] + rec[i, oracle.R_EX] + 2))
-        y0, y1 = int(max(0, rec[i, oracle.R_MY] - rec[i, oracle.R_EY] - 2)), int(min(H - 1, rec[i, oracle.R_MY] + rec[i, oracle.R_EY] + 2))
-        skip[y0:y1 + 1, x0:x1 + 1] = True
-    assert skip.mean() < 0.01
-    ok = ~skip & np.isfinite(out["allow_C"])
+    out, rec, pamb = ref["out"], ref["rec"], ref["proj_amb"]
+    # the kernel's records hold the error bounds the oracle's bands assume
+    vis = (rec[:, oracle.R_VIS] > 0) & (pamb == 0)
+    rec_errs = assert_record_bounds(_records(r), rec, vis, W, H, label="e2e records")
+    # projection decisions near their thresholds leave pixels and Gaussians out
+    skip, excl = projection_skip(rec, pamb, H, W)
+    JT = oracle.projection_adjoint_matrix(g64, f.cam)
+    env = oracle.envelope(rec, Ct, Dt, w.eps_depth, mode, Ctgt, f.depth, lam, ref["n_valid"], JT)
+    unb = env["unbounded"] != 0
+    excl |= gaussians_over(unb, rec)
+    ok = ~skip & ~unb
     assert ok.mean() > 0.99, ok.mean()
-    # stored C*: FP32 error and flip allowance, plus half an ulp of the storage type
-    tolC = 1e-4 + out["allow_C"]
+    # images: FP32 error 1e-4, the decision envelope, half an ulp of the storage type
+    tolC = 1e-4 + env["allow_C"]
     tolC = tolC + _HALF_ULP[prec] * (np.abs(out["C"]).max(0) + tolC)
     dC = np.abs(v.out_rgb.float().cpu().numpy() - out["C"]).max(0)
     dD = np.abs(v.out_depth.cpu().numpy() - out["D"])
     assert np.all(dC[ok] <= tolC[ok]), (dC[ok] - tolC[ok]).max()
-    assert np.all(dD[ok] <= 1e-4 * np.abs(out["D"][ok]) + out["allow_D"][ok])
-    np.testing.assert_allclose(loss.item(), ref["L"], rtol=1e-4)
+    assert np.all(dD[ok] <= 1e-4 * np.abs(out["D"][ok]) + env["allow_D"][ok])
+    assert abs(loss.item() - ref["L"]) <= 1e-4 * abs(ref["L"]) + env["allow_L"]
     got = {k: t.cpu().numpy() for k, t in zip(ref["grads"].keys(), grads.tensors())}
-    # A counting decision within the FP32 error band of its threshold may go
-    # either way: the oracle evaluated with every such decision inverted
-    # bounds how far the gradients can move (single flips per pixel).
-    alt = oracle.render_loss_grads(gs.astype(np.float64), f.cam, Ct, Dt, Ctgt, f.depth,
-                                   eps=w.eps_depth, lambda_depth=lam, mode=mode,
-                                   flip=(4e-6, 2e-6))
-    # Gaussians whose own near-threshold alpha is more than 1e-4 of their
-    # counted alpha take part of their decisions either way: left out
-    excl = (ref["proj_amb"] != 0) | (out["g_amb"] > 1e-4 * out["g_mass"])
-    # L1 residuals within 2e-5 of zero may take the other sign in FP32; the
-    # gradient then moves by at most twice those pixels' absolute
-    # contributions, which the oracle's own adjoint gives exactly
-    valid = (f.depth > 0) & (Dt > 0)
-    ambC = (np.abs(out["C"] - Ctgt) < 2e-5) & valid[None]
-    ambD = (np.abs(out["D"] - f.depth) < 2e-5 * np.abs(f.depth)) & valid
-    ga = sign_flip_allowance(gs.astype(np.float64), f.cam, rec, Ct, Dt, w.eps_depth, mode,
-                             ambC, ambD if lam else np.zeros_like(ambD), ref["n_valid"], lam)
-    allow = {k: ga[k] + np.abs(alt["grads"][k] - ref["grads"][k]) for k in ga}
-    # 1e-3 here (1e-4 in the staged tests, where decisions are identical):
-    # the flip envelope covers inverting all near-threshold decisions at once,
-    # not every combination of them (a Gaussian whose decisions split across
-    # its pixels moves its neighbours' gradients by up to a few percent), so
-    # 99.5% of the elements must be within 1e-3 and all within 5e-2
-    worst = assert_grads_close(got, ref["grads"], exclude=excl, norm_tol=1e-3, elem_tol=1e-3,
-                               label="e2e", allow=allow, quantile=(0.995, 5e-2))
-    print("e2e: allowance>0 px", (out["allow_C"] > 0).mean(), "excluded Gaussians", excl.mean(),
-          "Gaussians with flip allowance", (np.abs(alt["grads"]["means"] - ref["grads"]["means"]).max(1) > 0).mean(),
-          "worst (norm, elem)", worst)
+    stats = assert_grads_in_envelope(got, ref["grads"], env, JT, rec, excl, g64, f.cam, label="e2e")
+    stats.update(pixels_with_ambiguous_decision=float((env["n_amb"] > 0).mean()),
+                 pixels_left_out=float(1 - ok.mean()), max_ambiguous_per_pixel=int(env["n_amb"].max()),
+                 record_errors=rec_errs)
+    print("e2e", json.dumps(stats))
+    return stats
 
 
 def test_end_to_end_room_bench_configuration():
@@ -540,6 +542,14 @@ def test_per_gaussian_schedule_staged_vs_oracle():
 
 
 @pytest.mark.parametrize("name", ["small", "grad"])
+def test_end_to_end_per_gaussian_schedule(name):
+    """The paper's sort-free schedule with the fused loss against the FP64
+    oracle under the same envelope as the tile schedule."""
+    w = workload(name)
+    _end_to_end(w, gps.BLEND_OIT, w.lambda_depth, tile=(16, 8), schedule=gps.SCHEDULE_PER_GAUSSIAN)
+
+
+@pytest.mark.parametrize("name", ["small", "grad"])
 def test_per_gaussian_schedule_matches_tile_schedule(name):
     """End to end with the fused loss: both schedules give the same images (up to
     FP32 rounding of the summation order), loss and gradients; the per-Gaussian
@@ -570,13 +580,13 @@ def test_per_gaussian_schedule_matches_tile_schedule(name):
     (c0, l0, g0), (c1, l1, g1) = res
     np.testing.assert_allclose(c1, c0, atol=2e-6)
     np.testing.assert_allclose(l1, l0, rtol=1e-5)
-    # A residual within FP32 rounding of zero can flip its L1 sign between the
-    # two summation orders (the unsorted forward's order also varies run to
-    # run), moving the gradients of every Gaussian over that pixel; the flips
-    # touch well under 1% of the elements
-    scale = np.abs(g0).max()
-    close = np.abs(g1 - g0) <= 1e-4 * scale + 1e-4 * np.abs(g0)
-    assert close.mean() > 0.99, close.mean()
+    # A residual within FP32 rounding of zero can take either L1 sign in either
+    # schedule (the unsorted forward's summation order varies run to run), so
+    # the gradients of the fused loss are compared with the oracle's, under
+    # its envelope, for each schedule (test_end_to_end_per_gaussian_schedule
+    # and the end-to-end tests above); here they meet with the same upstream
+    # gradients on both sides, where every element agrees to accumulation
+    # rounding
     # with the same upstream gradients on both sides every element agrees to
     # accumulation rounding
     up = np.sign(c0 - f.rgb) * ((f.depth > 0) & (Dt > 0))[None] / 3.0

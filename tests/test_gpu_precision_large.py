@@ -19,7 +19,7 @@ import torch
 
 import oracle
 import paper_2509_11574_b300 as gps
-from helpers import cuda, workload
+from helpers import cuda, projection_skip, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -42,14 +42,11 @@ def test_large_config_colour_precision_errors_vs_fp64(capsys):
         ref = oracle.render_loss_grads(g64, f.cam, f.rgb, f.depth, f.rgb, f.depth,
                                        eps=w.eps_depth, lambda_depth=0.0, mode=oracle.OIT)
         out, rec, pamb = ref["out"], ref["rec"], ref["proj_amb"]
-        skip = np.zeros((H, W), bool)
-        for i in np.nonzero(pamb)[0]:
-            x0 = int(max(0, rec[i, oracle.R_MX] - rec[i, oracle.R_EX] - 2))
-            x1 = int(min(W - 1, rec[i, oracle.R_MX] + rec[i, oracle.R_EX] + 2))
-            y0 = int(max(0, rec[i, oracle.R_MY] - rec[i, oracle.R_EY] - 2))
-            y1 = int(min(H - 1, rec[i, oracle.R_MY] + rec[i, oracle.R_EY] + 2))
-            skip[y0:y1 + 1, x0:x1 + 1] = True
-        ok = ~skip & np.isfinite(out["allow_C"])
+        skip, _ = projection_skip(rec, pamb, H, W)
+        # the oracle's envelope of decisions within the FP32 bands (images only)
+        env = oracle.envelope(rec, f.rgb, f.depth, w.eps_depth, oracle.OIT, f.rgb, f.depth, 0.0,
+                              ref["n_valid"])
+        ok = ~skip & (env["unbounded"] == 0)
         assert ok.mean() > 0.99
         for prec in (gps.PREC_FP32, gps.PREC_FP16, gps.PREC_BF16):
             cdt = gps.PREC_DTYPE[prec]
@@ -67,7 +64,7 @@ def test_large_config_colour_precision_errors_vs_fp64(capsys):
             err = np.abs(v.out_rgb.float().cpu().numpy() - out["C"])
             u = _U[prec]
             Ct_part = np.abs(f.rgb) / (1.0 + out["W"])[None]
-            tol = 1e-4 + out["allow_C"][None] + u * (Ct_part + np.abs(out["C"]) + 1e-4)
+            tol = 1e-4 + env["allow_C"][None] + u * (Ct_part + np.abs(out["C"]) + 1e-4)
             assert np.all(err[:, ok] <= tol[:, ok]), (prec, (err - tol)[:, ok].max())
             got = {n: t.cpu().numpy().astype(np.float64)
                    for n, t in zip(ref["grads"].keys(), grads.tensors())}
