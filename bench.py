@@ -315,13 +315,16 @@ class GpuPipeline:
         d, _, ck = self.frames[k]
         return self.gps.View(self.cams[k], self.Ct, self.Dt, ck, d)
 
-    def step(self, k, stream=None, stage_events=None):
+    def step(self, k, stream=None, stage_events=None, iters=ITERS_PER_FRAME, sdf=True):
+        """One frame: fuse + ray-cast (sdf=False: C_t, D_t left as they are)
+        and `iters` iterations of forward + backward + Adam."""
         gps = self.gps
         d, c, _ = self.frames[k]
-        gps.fuse_frame(self.vol, d, c, self.cams[k], stream)
-        gps.raycast_sdf(self.vol, self.cams[k], self.w.near, 0.0, self.Ct, self.Dt, None, stream)
+        if sdf:
+            gps.fuse_frame(self.vol, d, c, self.cams[k], stream)
+            gps.raycast_sdf(self.vol, self.cams[k], self.w.near, 0.0, self.Ct, self.Dt, None, stream)
         v = [self.view(k)]
-        for it in range(ITERS_PER_FRAME):
+        for it in range(iters):
             if stage_events is None:
                 gps.render_forward(self.g, v, self.s, self.r.ws, self.loss[it:it + 1], stream)
                 if self.fused:
@@ -358,28 +361,38 @@ class GpuPipeline:
             e1.record()
             ev.setdefault(name, []).append((e0, e1))
 
-    def capture(self, k):
+    def capture(self, k, **step_kw):
+        """CUDA graph of step(k) (warmed once on a side stream first, so the
+        state has advanced by one step when this returns)."""
         torch = self.torch
         g = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            self.step(k)  # warm the path once on the side stream
+            self.step(k, **step_kw)  # warm the path once on the side stream
         torch.cuda.current_stream().wait_stream(s)
         with torch.cuda.graph(g):
-            self.step(k)
+            self.step(k, **step_kw)
         self.graphs[k] = g
         return g
 
 
-def kernels_per_step(mode, tile, schedule="tiles", deterministic=False, fused=True):
+TILE_BIN_MAX = 16384  # tiles per view that the binning histogram holds in shared memory
+
+
+def kernels_per_step(mode, tile, schedule="tiles", deterministic=False, fused=True,
+                     size=(640, 480)):
     # fuse, raycast + per iteration: project, scan, emit, [sort + split where the
-    # lists are depth-sorted], composite, finalize, composite_bwd [deterministic:
-    # + slot placement and pair gather; per-Gaussian schedule: pixel terms +
-    # per-Gaussian],
-    # projection adjoint + Adam (fused: one kernel, else two), step counter
+    # lists are depth-sorted, or where a view's tile grid exceeds what the
+    # binning histogram holds (then the unsorted lists go through super-tiles
+    # and a split)], composite, finalize, composite_bwd [deterministic: + slot
+    # placement and pair gather; per-Gaussian schedule: pixel terms +
+    # per-Gaussian], projection adjoint + Adam (fused: one kernel, else two),
+    # step counter
     tiles = schedule != "per-gaussian"
-    split = 1 if tiles and (mode == "alpha" or deterministic) else 0
+    n_tiles = -(-size[0] // tile[0]) * -(-size[1] // tile[1])
+    sorted_lists = tiles and (mode == "alpha" or deterministic)
+    split = 1 if sorted_lists or n_tiles > TILE_BIN_MAX else 0
     extra = 2 if tiles and deterministic else (0 if tiles else 1)
     return 2 + ITERS_PER_FRAME * (8 + split + extra + (0 if fused else 1))
 
@@ -400,15 +413,23 @@ def count_evaluations(pipe, k):
     raw = pipe.r.ws[L.view_scalars:L.view_scalars + 64].cpu().numpy()
     sc = raw[:32].view(np.float32)
     ctr = raw[32:64].view(np.uint64)
+    # visible Gaussians: records with a non-negative extent
+    rec = pipe.r.region(0, "records", torch.float32, pipe.r.M * 16).view(pipe.r.M, 16)
+    n_vis = int((rec[:, 11] >= 0).sum().item())
     return {"pairs": float(sc[4]), "fwd_tested": int(ctr[0]), "fwd_counted": int(ctr[1]),
-            "bwd_tested": int(ctr[2]), "bwd_counted": int(ctr[3]), "n_valid": float(sc[3])}
+            "bwd_tested": int(ctr[2]), "bwd_counted": int(ctr[3]), "n_valid": float(sc[3]),
+            "n_visible": n_vis}
 
 
-# FP32 operations per evaluation, counted from the kernels' arithmetic (an FMA = 2):
-# forward counted: dx, dy, q (7), exp argument + exp, alpha, 5 accumulations (10) = 22
-# backward counted: dx, q (7), exp (2), alpha, 4 colour/depth FMAs (8), dL/dalpha (8),
-#                   d sigma (2), v, 2 products, 5 moment FMAs (12) = 41
-FLOP_FWD, FLOP_BWD = 22, 41
+# Algorithmic FP32 operations per counted Gaussian-pixel evaluation, the
+# method's arithmetic (an FMA = 2): forward about 17 (dx, dy, the quadratic
+# form, alpha = sigma exp(-q/2), the colour, weight and depth sums) plus one
+# exponential, backward about 50 (alpha again, dL/dc, dL/dd, dL/dalpha from
+# the Eq. 4 blend, its chain to sigma, the conic and the mean) plus one.
+# The kernels' own instruction counts differ (they reuse the per-row terms
+# of q and accumulate moments, 22 and 41 operations): the roofline counts the
+# method's work.
+FLOP_FWD, FLOP_BWD = 17, 50
 
 
 def fp32_peak_tflops(sm_count, mhz):
@@ -603,9 +624,9 @@ def run_ours(args, rank, world, local):
         "hbm_model": {"bytes_per_iteration": it_bytes, "peak_gbs": hbm,
                       "frac_at_iteration_time": it_bytes / (it_ms * 1e-3) / 1e9 / hbm if it_ms else None},
         "roofline": roofline,
-        "clocks": clk, "gpu_launches": kernels_per_step(args.mode, tile, args.schedule,
-                                                        bool(getattr(args, "deterministic", False)),
-                                                        pipe.fused) * K,
+        "clocks": clk, "gpu_launches": kernels_per_step(
+            args.mode, tile, args.schedule, bool(getattr(args, "deterministic", False)),
+            pipe.fused, (w.frames[0].cam.width, w.frames[0].cam.height)) * K,
         "status": status, "last_frame_losses": losses[-3:], "wall_s": wall,
         "gen_s": gen_s, "gpu": props.name,
     }
@@ -632,7 +653,7 @@ def _iteration_bytes(w, counts):
     Adam 392 B per Gaussian, 104 B per pixel, 36 B per (tile, Gaussian) pair)."""
     M = w.gaussians.M
     npx = w.frames[0].cam.width * w.frames[0].cam.height
-    return M * 324 + M * 392 + npx * 104 + counts["pairs"] * 36
+    return counts["n_visible"] * 324 + M * 392 + npx * 104 + counts["pairs"] * 36
 
 
 # ---------------------------------------------------------------- oracle arm
@@ -686,30 +707,87 @@ def _oracle_setup(w):
 BAND_ROWS = 60  # one eighth of the 480 rows per sample of the reference arm
 
 
+def _oracle_config1():
+    """The 160x120 sphere + box frame with 2,000 Gaussians, all of it: one
+    oracle fusion, ray-cast and fwd+loss+bwd+Adam iteration; seconds."""
+    import numpy as np
+    import oracle
+    from datagen import workloads
+    w = workloads.small(M=2000)
+    f = w.frames[0]
+    t0 = time.time()
+    vol = oracle.Volume(w.tsdf)
+    oracle.fuse(vol, f.depth, f.rgb, f.cam)
+    Ct, Dt, _, _ = oracle.raycast(w.tsdf, vol.sdf, vol.rgb, f.cam)
+    g = w.gaussians.astype(np.float64)
+    ref = oracle.render_loss_grads(g, f.cam, Ct, Dt, f.rgb, f.depth, eps=w.eps_depth,
+                                   lambda_depth=w.lambda_depth, near=w.near)
+    p = np.concatenate([a.reshape(-1) for a in g.arrays()])
+    gg = np.concatenate([ref["grads"][k].reshape(-1) for k in ("means", "log_scales", "quats",
+                                                                "opacity_logits", "rgb")])
+    oracle.adam(p, gg, np.zeros_like(p), np.zeros_like(p), 1e-3)
+    return time.time() - t0
+
+
+def _oracle_fuse_raycast(w):
+    """One oracle fusion of frame 0 into the workload's volume and one ray-cast."""
+    import oracle
+    f = w.frames[0]
+    t0 = time.time()
+    vol = oracle.Volume(w.tsdf)
+    oracle.fuse(vol, f.depth, f.rgb, f.cam)
+    oracle.raycast(w.tsdf, vol.sdf, vol.rgb, f.cam)
+    return time.time() - t0
+
+
 def cpu_baseline(w):
-    """The oracle as it stands, on the host cores, on a bounded sample: one
-    whole iteration of frame 0 at 640x480 (about 15 s on 16 cores); at
-    1280x720 with 1M Gaussians a band of 1/8 of the rows."""
+    """The oracle as it stands, on the host cores, on bounded samples:
+      * all cores: one whole iteration of frame 0 at 640x480 (about 8 s on 16
+        cores; at 1280x720 with 1M Gaussians a band of 1/8 of the rows);
+      * one thread: the same iteration over a band of 1/8 of the rows;
+      * the 160x120 frame with 2,000 Gaussians in full (fusion, ray-cast,
+        one iteration), on all cores and on one thread;
+      * one fusion + ray-cast of frame 0 (the workload's volume), all cores."""
     import oracle
     oracle.build()
     _oracle_setup(w)
     H = w.frames[0].cam.height
+    cores = oracle.set_threads(0)
+
+    def iteration(rows):
+        y0 = (H - rows) // 2
+        t0 = time.time()
+        _oracle_iteration(w, 0, (y0, y0 + rows - 1), w.lambda_depth)
+        return time.time() - t0, y0
+
     rows = H if w.gaussians.M <= 200_000 else H // 8
-    y0 = (H - rows) // 2
-    t0 = time.time()
-    _oracle_iteration(w, 0, (y0, y0 + rows - 1), w.lambda_depth)
-    dt = time.time() - t0
-    frac = rows / H
-    return {"value": frac / dt, "unit": "iterations/s", "cores": _omp_threads(), "kind": "oracle",
+    dt, y0 = iteration(rows)
+    oracle.set_threads(1)
+    rows1 = H // 8
+    dt1, y1 = iteration(rows1)
+    c1_single = _oracle_config1()
+    oracle.set_threads(cores)
+    c1_all = _oracle_config1()
+    fr = _oracle_fuse_raycast(w)
+    return {"value": (rows / H) / dt, "unit": "iterations/s", "cores": cores, "kind": "oracle",
             "sample": f"one fwd+loss+bwd+Adam iteration of frame 0 over rows {y0}-{y0 + rows - 1} "
                       f"of {H} (projection and Adam over all {w.gaussians.M} Gaussians; "
                       f"{_oracle_iteration.sdf_note}), scaled by {rows}/{H} to iterations/s; "
-                      f"took {dt:.1f} s"}
+                      f"took {dt:.1f} s",
+            "single_thread": {"value": (rows1 / H) / dt1, "unit": "iterations/s", "cores": 1,
+                              "sample": f"the same iteration over rows {y1}-{y1 + rows1 - 1}, "
+                                        f"scaled by {rows1}/{H}; took {dt1:.1f} s"},
+            "small_frame_full": {"ms": 1e3 * c1_all, "ms_single_thread": 1e3 * c1_single,
+                                 "sample": "160x120 sphere + box frame, 2,000 Gaussians: fusion "
+                                           "(64^3), ray-cast and one fwd+loss+bwd+Adam iteration"},
+            "fuse_raycast_ms": 1e3 * fr,
+            "fuse_raycast_sample": f"one fusion of frame 0 into the {w.tsdf.nx}^3 volume and one "
+                                   f"ray-cast, {cores} threads"}
 
 
 def _omp_threads():
-    n = os.environ.get("OMP_NUM_THREADS")
-    return int(n) if n and n.isdigit() else os.cpu_count()
+    import oracle
+    return oracle.set_threads(0)
 
 
 # ------------------------------------------------------------ multiview

@@ -612,10 +612,24 @@ GPS_API int32_t gps_select_views(const int32_t* keyframes, int32_t n_keyframes, 
  *     last call's contents (so render_backward cannot be paired with it):
  *     calls whose work overlaps on the GPU - on different streams or from
  *     different threads - race with each other and must be serialised by the
- *     caller. */
+ *     caller.
+ *   - Errors found on the device (a pair-capacity overflow) land in the
+ *     array's status word: read it with gps_noalloc_query_status.
+ *   - The array's device address is cached per device for the life of the
+ *     process; a cudaDeviceReset (or any reset of the device's primary
+ *     context) invalidates it, so call neither while this library is in use. */
 GPS_API int32_t render_forward_noalloc(const GpsGaussians* gaussians, const GpsView* views,
                                        int32_t n_views, const GpsRenderSettings* settings,
                                        float* loss, void* stream);
+
+/* The status word of the static array behind render_forward_noalloc on the
+ * current device, as gps_query_status reads a workspace's: *status receives
+ * GPS_OK or the device-side code of the last call (GPS_ERR_CAPACITY when its
+ * (tile, Gaussian) pairs overflowed settings.pair_capacity and the render is
+ * truncated).  Synchronises `stream`; does the one-time set-up of
+ * render_forward_noalloc if it has not run on this device.  No counterpart in
+ * the paper. */
+GPS_API int32_t gps_noalloc_query_status(int32_t* status, void* stream);
 
 #ifdef __cplusplus
 }

@@ -103,7 +103,13 @@ def lib():
         _lib.orc_project.restype = ctypes.c_int
         _lib.orc_loss.restype = ctypes.c_double
         _lib.orc_bin.restype = ctypes.c_long
+        _lib.orc_set_threads.restype = ctypes.c_int
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's parallel loops; returns the previous count."""
+    return int(lib().orc_set_threads(ctypes.c_int(n)))
 
 
 def _p(a: Optional[np.ndarray]):
@@ -157,8 +163,10 @@ def fuse(vol: Volume, depth, rgb, cam) -> None:
                    _p(K), _p(R), _p(t), _p(vol.alloc))
 
 
-def raycast(spec, sdf, rgb, cam, near=0.2, far=0.0):
-    """Sec. 3.1 first pass.  Returns (C_t [3][H][W], D_t [H][W], vertex [H][W][3], amb)."""
+def raycast(spec, sdf, rgb, cam, near=0.2, far=0.0, depth_err=False, sdf_err=None):
+    """Sec. 3.1 first pass.  Returns (C_t [3][H][W], D_t [H][W], vertex [H][W][3], amb),
+    plus, with depth_err, a per-pixel bound on an FP32 march's hit depth error.
+    sdf_err (per voxel, like sdf): how far an FP32 march's volume may differ."""
     dims, geo = _vol(spec)
     K, R, t = _cam(cam)
     H, W = cam.height, cam.width
@@ -166,10 +174,12 @@ def raycast(spec, sdf, rgb, cam, near=0.2, far=0.0):
     out_d = np.zeros((H, W))
     out_v = np.zeros((H, W, 3))
     amb = np.zeros((H, W), dtype=np.int32)
+    err = np.zeros((H, W)) if depth_err else None
     lib().orc_raycast(_p(dims), _p(geo), _p(_f64(sdf)), _p(_f64(rgb)), ctypes.c_int(W),
                       ctypes.c_int(H), _p(K), _p(R), _p(t), ctypes.c_double(near),
-                      ctypes.c_double(far), _p(out_rgb), _p(out_d), _p(out_v), _p(amb))
-    return out_rgb, out_d, out_v, amb
+                      ctypes.c_double(far), _p(out_rgb), _p(out_d), _p(out_v), _p(amb), _p(err),
+                      _p(_f64(sdf_err)) if sdf_err is not None else None)
+    return (out_rgb, out_d, out_v, amb, err) if depth_err else (out_rgb, out_d, out_v, amb)
 
 
 def _sh_degree(g) -> int:

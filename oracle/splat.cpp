@@ -28,6 +28,8 @@
 #include <cstring>
 #include <vector>
 
+#include <omp.h>
+
 #include "mag.h"
 
 namespace {
@@ -1008,6 +1010,14 @@ void orc_project_backward_mag(int M, const double* means, const double* log_scal
     for (int k = 0; k < 4; ++k) d_quats[4 * i + k] = dq[k].v;
     d_logits[i] = dlg.v;
   }
+}
+
+// OpenMP threads of the oracle's parallel loops (for timing it single-threaded
+// and on all cores); returns the previous maximum.
+int orc_set_threads(int n) {
+  const int prev = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return prev;
 }
 
 // Tile binning from FP32 projected records (the kernels' record layout, 16

@@ -184,14 +184,26 @@ void orc_fuse(const int* dims, const double* geo, double* sdf, double* w, double
 // f_a > 0 >= f_b is a hit; secant refinement s* = s_a + (s_b - s_a) f_a / (f_a - f_b).
 // V^g = o + s* dir; D_t = camera z of V^g; C_t = trilinear of the 8 voxel colours.
 // No hit: D_t = 0, C_t = 0, vertex = 0.
-// amb[pix] = 1 when some sample had |f| < 1e-4 without being the final bracket,
-// or the bracket values were within 1e-4 of zero, or a sample sat within a
-// relative 1e-6 of the march end - decisions a single-precision march can take
-// differently.
+// amb[pix] = 1 when a single-precision march may decide differently: each
+// sample's position is tracked with a running bound ds on how far an FP32
+// march's sample can be from this one (the entry point's and every addition's
+// rounding, a few u s, plus trunc times the FP32 error of the f that set the
+// step, where the step follows f), and f's bound df = |df/ds| ds + |grad f|
+// dp + 8 u (the local slope along the ray; dp, the rounding of the FP32 grid
+// coordinates of the sample, off the ray; the trilinear's own rounding); a
+// sample whose |f| < df, or whose position lies within ds of the march end,
+// flags the pixel.  In noisy stretches of a fused volume the slope amplifies
+// ds from sample to sample, as it does the FP32 march's drift.
+// out_depth_err (nullable): per pixel, a bound on how far an FP32 march's
+// hit depth can be from this one's: the secant root re-solved with the
+// bracket ends moved by their bounds (0 where nothing was hit).
+// sdf_err (nullable, per voxel, >= 0): how far the other march's volume may
+// differ from this one (an FP32 fusion of the same frames); its trilinear
+// interpolation adds to every sample's df.
 void orc_raycast(const int* dims, const double* geo, const double* sdf, const double* rgb,
                  int W, int H, const double* K, const double* R, const double* t,
                  double near_, double far_, double* out_rgb, double* out_depth,
-                 double* out_vertex, int* amb) {
+                 double* out_vertex, int* amb, double* out_depth_err, const double* sdf_err) {
   const Vol v = make_vol(dims, geo);
   const double fx = K[0], fy = K[1], cx = K[2], cy = K[3];
   const double lo[3] = {v.ox + 0.5 * v.voxel, v.oy + 0.5 * v.voxel, v.oz + 0.5 * v.voxel};
@@ -222,6 +234,7 @@ void orc_raycast(const int* dims, const double* geo, const double* sdf, const do
     out_depth[pix] = 0.0;
     if (out_vertex) out_vertex[pix * 3] = out_vertex[pix * 3 + 1] = out_vertex[pix * 3 + 2] = 0.0;
     if (amb) amb[pix] = 0;
+    if (out_depth_err) out_depth_err[pix] = 0.0;
     if (!(s0 < s1)) continue;
     auto sample = [&](double s) {
       double g[3];
@@ -229,23 +242,70 @@ void orc_raycast(const int* dims, const double* geo, const double* sdf, const do
       for (int k = 0; k < 3; ++k) g[k] = (t[k] + s * dw[k] - o3[k]) / v.voxel - 0.5;
       return trilinear(v, sdf, 1, 0, g);
     };
+    // |df/ds| near s: the larger one-sided difference over h (the trilinear
+    // field is piecewise smooth; h spans the position uncertainty)
+    auto slope = [&](double s, double f, double h) {
+      return std::max(std::fabs(sample(s + h) - f), std::fabs(f - sample(s - h))) / h;
+    };
+    // |grad f| at the sample at s: central differences along the axes
+    auto grad_norm = [&](double s) {
+      const double h = 0.01 * v.voxel, o3[3] = {v.ox, v.oy, v.oz};
+      double gsq = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        double gp[3], gm[3];
+        for (int k = 0; k < 3; ++k) {
+          const double p = t[k] + s * dw[k] + (k == a ? h : 0.0);
+          const double m = t[k] + s * dw[k] - (k == a ? h : 0.0);
+          gp[k] = (p - o3[k]) / v.voxel - 0.5;
+          gm[k] = (m - o3[k]) / v.voxel - 0.5;
+        }
+        const double d = (trilinear(v, sdf, 1, 0, gp) - trilinear(v, sdf, 1, 0, gm)) / (2.0 * h);
+        gsq += d * d;
+      }
+      return std::sqrt(gsq);
+    };
+    constexpr double u = 5.9604644775390625e-8;  // 2^-24
+    // an FP32 sample at s also sits off the ray by the rounding of the grid
+    // coordinates go + s gd (go from |t - origin|, gd from the direction)
+    const double t_off = std::sqrt((t[0] - v.ox) * (t[0] - v.ox) + (t[1] - v.oy) * (t[1] - v.oy) +
+                                   (t[2] - v.oz) * (t[2] - v.oz));
+    auto f_err = [&](double s, double f, double ds) {
+      const double dp = u * (2.0 * t_off + 5.0 * std::fabs(s) + v.voxel);
+      double e = slope(s, f, std::max(ds, 1e-7)) * ds + grad_norm(s) * dp + 8.0 * u;
+      if (sdf_err) {
+        double g[3];
+        const double o3[3] = {v.ox, v.oy, v.oz};
+        for (int k = 0; k < 3; ++k) g[k] = (t[k] + s * dw[k] - o3[k]) / v.voxel - 0.5;
+        e += trilinear(v, sdf_err, 1, 0, g);
+      }
+      return e;
+    };
+    const double s1_err = 4.0 * u * s1;
     double sa = s0, fa = sample(sa);
-    bool hit = false, ambig = false;
-    double sb = 0.0, fb = 0.0;
+    double dsa = 4.0 * u * std::fabs(s0);
+    double dfa = f_err(sa, fa, dsa);
+    bool hit = false, ambig = std::fabs(fa) < dfa;
+    double sb = 0.0, fb = 0.0, dsb = 0.0;
     while (true) {
-      double step = std::max(std::min(fa, 1.0) * v.trunc, 0.5 * v.voxel);
+      const double fs = std::min(fa, 1.0) * v.trunc;
+      double step = std::max(fs, 0.5 * v.voxel);
       sb = sa + step;
-      if (std::fabs(sb - s1) < 1e-6 * s1) ambig = true;
+      // the step follows f only where min(f, 1) trunc sets it
+      dsb = dsa + (fs > 0.5 * v.voxel && fa < 1.0 ? v.trunc * dfa : 0.0) +
+            u * (std::fabs(sb) + step);
+      if (std::fabs(sb - s1) < dsb + s1_err) ambig = true;
       if (sb > s1) break;
       fb = sample(sb);
+      const double dfb = f_err(sb, fb, dsb);
+      if (std::fabs(fb) < dfb) ambig = true;
       if (fa > 0.0 && fb <= 0.0) {
         hit = true;
-        if (std::fabs(fa) < 1e-4 || std::fabs(fb) < 1e-4) ambig = true;
         break;
       }
-      if (std::fabs(fb) < 1e-4) ambig = true;
       sa = sb;
       fa = fb;
+      dsa = dsb;
+      dfa = dfb;
     }
     if (amb) amb[pix] = ambig ? 1 : 0;
     if (!hit) continue;
@@ -254,6 +314,26 @@ void orc_raycast(const int* dims, const double* geo, const double* sdf, const do
     double xc[3];
     world_to_cam(R, t, V, xc);
     out_depth[pix] = xc[2];
+    if (out_depth_err) {
+      // the secant solved again with each bracket end moved by its position
+      // bound (f sampled there) and f off by its rounding; the largest move
+      // of the root, plus the secant's and the camera transform's roundings,
+      // scaled by the ray's camera z per unit length
+      double droot = 0.0;
+      const double ra = f_err(sa, fa, 0.0), rb = f_err(sb, fb, 0.0);
+      for (int c = 0; c < 16; ++c) {
+        const double sa2 = sa + ((c & 1) ? dsa : -dsa), sb2 = sb + ((c & 2) ? dsb : -dsb);
+        const double fa2 = sample(sa2) + ((c & 4) ? ra : -ra);
+        const double fb2 = sample(sb2) + ((c & 8) ? rb : -rb);
+        if (!(fa2 > fb2)) {
+          droot = INFINITY;
+          break;
+        }
+        droot = std::max(droot, std::fabs(sa2 + (sb2 - sa2) * fa2 / (fa2 - fb2) - ss));
+      }
+      const double dz = std::fabs(xc[2] / ss);  // camera z per unit of ray length
+      out_depth_err[pix] = (droot + 8.0 * u * ss) * dz + 8.0 * u * std::fabs(xc[2]);
+    }
     double g[3] = {(V[0] - v.ox) / v.voxel - 0.5, (V[1] - v.oy) / v.voxel - 0.5,
                    (V[2] - v.oz) / v.voxel - 0.5};
     for (int ch = 0; ch < 3; ++ch) out_rgb[ch * npx + pix] = trilinear(v, rgb, 3, ch, g);

@@ -152,7 +152,8 @@ class GpsWorkspaceLayout(ctypes.Structure):
 
 EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspace_layout",
             "gps_query_status", "fuse_frame", "raycast_sdf", "render_forward", "render_backward",
-            "adam_step", "render_forward_noalloc", "gps_autotune_tiles",
+            "adam_step", "render_forward_noalloc", "gps_noalloc_query_status",
+            "gps_autotune_tiles",
             "gps_edit_scratch_size", "insert_gaussians", "remove_gaussians",
             "tsdf_mark_bricks", "gps_is_keyframe", "gps_select_views",
             "gps_icp_workspace_size", "icp_track", "gps_hash_scratch_size", "fuse_frame_hashed",
@@ -224,6 +225,7 @@ def lib() -> ctypes.CDLL:
                                              ctypes.POINTER(GpsView), c_int32,
                                              ctypes.POINTER(GpsRenderSettings), c_void_p,
                                              c_void_p]
+        L.gps_noalloc_query_status.argtypes = [ctypes.POINTER(c_int32), c_void_p]
         L.gps_is_keyframe.argtypes = [ctypes.POINTER(GpsPose), ctypes.POINTER(GpsPose),
                                       ctypes.POINTER(GpsViewSchedule), ctypes.POINTER(c_int32)]
         L.gps_select_views.argtypes = [ctypes.POINTER(c_int32), c_int32, c_int32, c_int32,
@@ -578,6 +580,14 @@ def render_forward_noalloc(g: Gaussians, views: Sequence[View], s: GpsRenderSett
     va = _views(views, s)
     _check(lib().render_forward_noalloc(ctypes.byref(gc), va, len(views), ctypes.byref(s),
                                         _ptr(loss), _stream(stream)))
+
+
+def noalloc_status(stream=None) -> int:
+    """Status word of the static scratch behind render_forward_noalloc
+    (gps_noalloc_query_status; synchronises the stream)."""
+    st = c_int32(0)
+    _check(lib().gps_noalloc_query_status(ctypes.byref(st), _stream(stream)))
+    return st.value
 
 
 def render_backward(g: Gaussians, views: Sequence[View], s: GpsRenderSettings, ws: torch.Tensor,

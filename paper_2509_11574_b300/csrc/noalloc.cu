@@ -4,7 +4,9 @@
 //
 // In host code `g_scratch` names a host-side shadow symbol, not a device
 // address: its device address is obtained once per device, with that device
-// current, through cudaGetSymbolAddress and cached here.
+// current, through cudaGetSymbolAddress and cached here.  The array's first
+// 256 bytes hold the workspace status word, which gps_noalloc_query_status
+// reads back (the caller never sees the array's address).
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -82,4 +84,14 @@ extern "C" int32_t render_forward_noalloc(const GpsGaussians* gaussians, const G
   if (int32_t rc = scratch_on_current_device(&ws)) return rc;
   return render_forward(gaussians, views, n_views, &s, ws, (size_t)GPS_NOALLOC_SCRATCH_BYTES,
                         loss, stream);
+}
+
+extern "C" int32_t gps_noalloc_query_status(int32_t* status, void* stream) {
+  if (!status) {
+    gps::set_error("gps_noalloc_query_status: NULL status");
+    return GPS_ERR_INVALID_ARG;
+  }
+  void* ws = nullptr;
+  if (int32_t rc = scratch_on_current_device(&ws)) return rc;
+  return gps_query_status(ws, (size_t)GPS_NOALLOC_SCRATCH_BYTES, status, stream);
 }

@@ -190,6 +190,15 @@ def projection_skip(rec: np.ndarray, proj_amb: np.ndarray, H: int, W: int):
     return skip, excl
 
 
+def envelope_slack(env: dict, JT: np.ndarray, rec: np.ndarray, gs, cam) -> np.ndarray:
+    """[M][P]: what a kernel's parameter gradient may differ by from the
+    oracle's beyond 1e-4 of it (see assert_grads_in_envelope)."""
+    aJ = np.abs(JT)
+    return (env["allow3"] + np.einsum("mpc,mc->mp", aJ, env["s2q"])
+            + KAPPA_SUM * U32 * np.einsum("mpc,mc->mp", aJ, env["s2"])
+            + projection_rounding(gs, cam, env["g2ref"], rec))
+
+
 def assert_grads_in_envelope(got: dict, ref: dict, env: dict, JT: np.ndarray, rec: np.ndarray,
                              exclude: np.ndarray, gs, cam, label="", rel=1e-4):
     """Per parameter tensor and element, the criterion at `rel`:
@@ -203,11 +212,7 @@ def assert_grads_in_envelope(got: dict, ref: dict, env: dict, JT: np.ndarray, re
     every term from the oracle's own per-pixel terms (`oracle.envelope`).
     Returns what the check saw."""
     M = rec.shape[0]
-    aJ = np.abs(JT)
-    slack = (env["allow3"] + np.einsum("mpc,mc->mp", aJ, env["s2q"])
-             + KAPPA_SUM * U32 * np.einsum("mpc,mc->mp", aJ, env["s2"])
-             + projection_rounding(gs, cam, env["g2ref"], rec))
-    o_all, g_all = params_matrix(ref, M), params_matrix(got, M)
+    slack = envelope_slack(env, JT, rec, gs, cam)
     sl = oracle.split_params(slack, ref)
     al = oracle.split_params(env["allow3"], ref)
     keep = ~exclude

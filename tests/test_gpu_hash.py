@@ -90,12 +90,16 @@ def test_hashed_raycast_equals_dense_raycast_of_the_same_values():
 
 def test_hashed_raycast_matches_oracle():
     """Fusion and ray-cast end to end against the oracle (FP64 hashed volume):
-    hit pattern, depth to 1e-4 and colour as in the dense ray-cast test, away
-    from pixels whose march the oracle flags as near a decision."""
+    hit pattern, depth to 1e-4 plus the oracle's bound on an FP32 march's hit,
+    and colour as in the dense ray-cast test, away from pixels whose march
+    the oracle flags as near a decision.  The two volumes differ by their
+    fusions' rounding and by the bricks whose allocation lies within rounding
+    of its threshold (allocated on one side only), which the oracle's march
+    bound does not model: a few pixels may then hit on one side only."""
     w = _room()
     vol_o, vol_h = _fuse_both(w, 3)
     f = w.frames[2]
-    Ct, Dt, _, amb = oracle.raycast(w.tsdf, vol_o.sdf, vol_o.rgb, f.cam)
+    Ct, Dt, _, amb, derr = oracle.raycast(w.tsdf, vol_o.sdf, vol_o.rgb, f.cam, depth_err=True)
     c, d = gps.raycast_sdf_hashed(vol_h, f.cam)
     c, d = c.cpu().numpy(), d.cpu().numpy()
     ok = amb == 0
@@ -103,7 +107,7 @@ def test_hashed_raycast_matches_oracle():
     agree = (d > 0) == (Dt > 0)
     assert agree[ok].mean() > 0.999
     hit = ok & agree & (Dt > 0)
-    np.testing.assert_allclose(d[hit], Dt[hit], rtol=1e-4)
+    assert np.all(np.abs(d[hit] - Dt[hit]) <= 1e-4 * Dt[hit] + derr[hit])
     assert np.abs(c[:, hit] - Ct[:, hit]).max() < 2e-3
 
 

@@ -130,6 +130,22 @@ def test_raycast_plane_exact(tilt):
     np.testing.assert_allclose(Dt[ok], s[ok], rtol=1e-9)
     np.testing.assert_allclose(V[ok], hitp[ok], atol=1e-9)
     np.testing.assert_allclose(Ct[:, ok].T, _linear_colour(hitp[ok]), atol=1e-9)
+    # the FP32 march bounds: along a linear SDF the secant root does not move
+    # with its bracket, so an FP32 march's hit depth is known to a few dozen
+    # roundings (u = 2^-24) of the depth
+    _, Dt2, _, amb2, err = oracle.raycast(spec, sdf, rgb, cam, depth_err=True)
+    np.testing.assert_array_equal(Dt2, Dt)
+    assert (amb2[ok] == 0).mean() > 0.95
+    assert np.all(err[ok] <= 64 * 2.0 ** -24 * Dt[ok]) and np.all(err[ok] > 0)
+    assert np.all(err[Dt == 0] == 0)
+    # a volume known only to +-e per voxel: the same hits, larger bounds, and
+    # with e >= 1 (any value of f possible) every pixel's march is uncertain
+    _, Dt3, _, amb3, err3 = oracle.raycast(spec, sdf, rgb, cam, depth_err=True,
+                                           sdf_err=np.full(sdf.shape, 1e-4))
+    np.testing.assert_array_equal(Dt3, Dt)
+    assert np.all(err3[ok] >= err[ok]) and np.all(amb3[amb2 != 0] != 0)
+    _, _, _, amb4 = oracle.raycast(spec, sdf, rgb, cam, sdf_err=np.ones(sdf.shape))
+    assert np.all(amb4[Dt > 0] != 0)
 
 
 def test_raycast_box_face_and_sphere():

@@ -70,6 +70,32 @@ def test_noalloc_matches_workspace_forward_twice(mode):
         np.testing.assert_allclose(vn.out_weight.cpu().numpy(), vr.out_weight.cpu().numpy(),
                                    rtol=1e-5, atol=1e-6)
         np.testing.assert_allclose(loss_n.item(), loss_r.item(), rtol=1e-6)
+        st = ctypes.c_int32(-99)
+        assert L.gps_noalloc_query_status(ctypes.byref(st), None) == gps.GPS_OK
+        assert st.value == gps.GPS_OK
+
+
+def test_noalloc_reports_pair_capacity_overflow():
+    """A pair capacity too small for the frame: the overflow lands in the
+    static array's status word, read back through gps_noalloc_query_status;
+    the next call that fits clears it."""
+    L = gps.lib()
+    w = workloads.small(M=2000)
+    f, Ct, Dt, C, D = _inputs(w)
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    for cap, expect in ((64, gps.GPS_ERR_CAPACITY), (0, gps.GPS_OK)):
+        s = gps.settings(eps_depth=w.eps_depth, pair_capacity=cap)
+        vn = _view(f, Ct, Dt, C, D)
+        gc = g.c()
+        views = (gps.GpsView * 1)(vn.c())
+        rc = L.render_forward_noalloc(ctypes.byref(gc), views, 1, ctypes.byref(s), None,
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == gps.GPS_OK, L.gps_last_error()
+        st = ctypes.c_int32(-99)
+        rc = L.gps_noalloc_query_status(ctypes.byref(st),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == gps.GPS_OK, L.gps_last_error()
+        assert st.value == expect, (cap, st.value)
 
 
 def test_noalloc_rejects_problems_beyond_the_static_scratch():
