@@ -250,6 +250,10 @@ typedef struct GpsWorkspaceLayout {
   size_t pair_base;     /* uint32 [M] (deterministic mode): Gaussian i's first
                            pair_grads slot; its slots follow in row-major
                            order of the tiles of its rectangle                */
+  size_t tile_order;    /* int32 [tiles] (tile bins): the tiles in order of
+                           decreasing list length, in buckets of half an
+                           octave; the composites take their tiles in this
+                           order, longest lists first                         */
 } GpsWorkspaceLayout;
 
 /* ---------------------------------------------------------------- calls */

@@ -116,6 +116,31 @@ __global__ void __launch_bounds__(kScanThreads) scan_super_kernel(const __grid_c
     scalars[4] = (float)run;
     if (run > (unsigned long long)cap) set_status(status, GPS_ERR_CAPACITY);
   }
+  if (v.tile_order) {
+    // tiles as bins: order them by decreasing list length (a counting sort
+    // on half-octave buckets of the length; order inside a bucket arbitrary)
+    __shared__ uint32_t s_bucket[64];
+    auto bucket = [&](int k) {
+      const uint32_t c = ranges[k].y - ranges[k].x;
+      if (c == 0) return 0;
+      const int l = 31 - __clz(c);  // floor(log2 c)
+      return min(63, 1 + 2 * l + (2 * c >= 3u << l ? 1 : 0));
+    };
+    if (tid < 64) s_bucket[tid] = 0u;
+    __syncthreads();
+    for (int k = b; k < e; ++k) atomicAdd(s_bucket + bucket(k), 1u);
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t base = 0;
+      for (int q = 63; q >= 0; --q) {
+        const uint32_t t = s_bucket[q];
+        s_bucket[q] = base;
+        base += t;
+      }
+    }
+    __syncthreads();
+    for (int k = b; k < e; ++k) v.tile_order[atomicAdd(s_bucket + bucket(k), 1u)] = k;
+  }
 }
 
 // Emission of Gaussian i (i < M) of a warp's 32: its entries go to the

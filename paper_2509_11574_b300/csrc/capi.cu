@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -162,6 +163,8 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     off = align256(off + (s->schedule == GPS_SCHEDULE_PER_GAUSSIAN ? npx * 32 : 0));
     L.pair_base = off;
     off = align256(off + (s->deterministic ? (size_t)M * 4 : 0));
+    L.tile_order = off;
+    off = align256(off + (by_tile ? ntiles * 4 : 0));
     L.tiles_x = tx;
     L.tiles_y = ty;
     L.tile_w = tc.tw;
@@ -244,6 +247,7 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int 
   v.pair_grads = reinterpret_cast<float4*>(ws + L.pair_grads);
   v.pix_g = reinterpret_cast<float4*>(ws + L.pix_grad);
   v.pair_base = reinterpret_cast<uint32_t*>(ws + L.pair_base);
+  v.tile_order = L.tile_bins ? reinterpret_cast<int*>(ws + L.tile_order) : nullptr;
   {
     const int sp = 1 << super_shift_for(L.tile_w);
     v.pair_slots = L.pair_capacity * ((sp / L.tile_w) * (sp / L.tile_h));

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
   __shared__ float s_tmp[NW * 3];
   const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
-  const int tile = blockIdx.x - vb.tile_start[slot];
+  const int tile = tile_of(v, blockIdx.x - vb.tile_start[slot]);
   const int W = v.cam.W, H = v.cam.H;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
   __shared__ float s_tmp[NW * 3];
   const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
-  const int tile = blockIdx.x - vb.tile_start[slot];
+  const int tile = tile_of(v, blockIdx.x - vb.tile_start[slot]);
   const int W = v.cam.W, H = v.cam.H;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_oit_kernel(const __grid_
   __shared__ float s_tmp[NW];
   const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
-  const int tile = blockIdx.x - vb.tile_start[slot];
+  const int tile = tile_of(v, blockIdx.x - vb.tile_start[slot]);
   const int fused = v.fused;
   const int W = v.cam.W, H = v.cam.H;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
@@ -987,7 +987,7 @@ __global__ void __launch_bounds__(TW* TH)
   __shared__ uint8_t s_list[NW][NB];
   const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
-  const int tile = blockIdx.x - vb.tile_start[slot];
+  const int tile = tile_of(v, blockIdx.x - vb.tile_start[slot]);
   const int fused = v.fused;
   const int W = v.cam.W, H = v.cam.H;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
@@ -1111,7 +1111,7 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
   __shared__ float s_l2[kAlphaBatch];  // log2 sigma, as staged by the forward
   const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
-  const int tile = blockIdx.x - vb.tile_start[slot];
+  const int tile = tile_of(v, blockIdx.x - vb.tile_start[slot]);
   const int fused = v.fused;
   const int W = v.cam.W, H = v.cam.H;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;

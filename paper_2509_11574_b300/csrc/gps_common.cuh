@@ -71,6 +71,7 @@ struct ViewDev {
   uint32_t* pair_base;    // [M] first slot of each Gaussian (deterministic mode)
   long long pair_slots;
   float4* pix_g;          // [npx][2] per-Gaussian backward: (h), (sv, thr, -, -)
+  int* tile_order;        // [tiles] longest lists first (tile bins), else null
   int tiles_x, tiles_y, tw, th;
   // bins of the binning pass (sup_x * sup_y of them, 2^bin_sx x 2^bin_sy
   // pixels each): square super-tiles, or the tiles themselves
@@ -100,6 +101,13 @@ __device__ __forceinline__ int batch_slot(const int* start, int n, int item) {
 #pragma unroll 1
   while (k + 1 < n && item >= start[k + 1]) ++k;
   return k;
+}
+
+// The tile of a view's per-tile work item: its tiles are taken in order of
+// decreasing list length where the binning has ordered them, so that the
+// longest lists start first and the grid's tail holds short ones.
+__device__ __forceinline__ int tile_of(const ViewDev& v, int item) {
+  return v.tile_order ? __ldg(v.tile_order + item) : item;
 }
 
 // Colour images are stored as float, IEEE binary16 or bfloat16 (GPS_PREC_*);
