@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--mode", default="oit", choices=["oit", "alpha"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-speedup", action="store_true",
+                    help="skip the batched / graph / reduced-precision against plain comparison")
     ap.add_argument("--frames", type=int, default=None,
                     help=f"frames of the sequence (room: {N_FRAMES}, large: {N_FRAMES_LARGE})")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
@@ -380,20 +382,181 @@ class GpuPipeline:
 TILE_BIN_MAX = 16384  # tiles per view that the binning histogram holds in shared memory
 
 
+def batched_speedup(pipe, w, dev, K, Wu, n_views=8, precision="bf16"):
+    """The benchmark spec's comparison, per rendered pixel-iteration: the batched,
+    graph-captured form with reduced-precision colour storage (n_views room
+    frames per iteration, one render_forward and one render_backward_adam call
+    for all of them, one CUDA graph) against the plain single-frame FP32 form
+    (one view per iteration, eager C-ABI calls), on the same device and the
+    same Gaussians.  Both forms run n_views fwd+bwd+Adam view-renders per
+    step; the batched one takes one Adam step per step, the plain one
+    n_views.  C_t, D_t of each view come from the room's fusion of the first
+    n_views frames (set-up, untimed)."""
+    import torch
+    gps = pipe.gps
+    frames = w.frames[:n_views]
+    cams = [f.cam for f in frames]
+    vol = gps.Tsdf(w.tsdf, dev)
+    imgs = [(torch.from_numpy(f.depth).to(dev), torch.from_numpy(f.rgb).to(dev)) for f in frames]
+    for f, (d, c) in zip(frames, imgs):
+        gps.fuse_frame(vol, d, c, f.cam)
+
+    def views_for(prec):
+        dt = gps.PREC_DTYPE[prec]
+        vs = []
+        for f, (d, c) in zip(frames, imgs):
+            H, W = f.cam.height, f.cam.width
+            Ct, Dt = torch.empty(3, H, W, device=dev, dtype=dt), torch.empty(H, W, device=dev)
+            gps.raycast_sdf(vol, f.cam, w.near, 0.0, Ct, Dt, None)  # C_t in Ct's type
+            vs.append(gps.View(f.cam, Ct, Dt, c.to(dt), d))
+        return vs
+
+    def settings(prec):
+        return gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, near=w.near,
+                            tile=(pipe.s.tile_w, pipe.s.tile_h),
+                            pair_capacity=64 * w.gaussians.M, precision=prec)
+
+    g = gps.Gaussians(*[t.clone() for t in pipe.g0.tensors()])
+    opt = gps.Adam(g, device_step=True)
+    loss = torch.zeros(n_views, device=dev)
+
+    def reset():
+        for a, b in zip(g.tensors(), pipe.g0.tensors()):
+            a.copy_(b)
+        for t in opt.m.tensors() + opt.v.tensors():
+            t.zero_()
+        opt.device_step.zero_()
+
+    def plain_form():
+        s = settings(0)
+        r = gps.Renderer(w.gaussians.M, cams[:1], s, dev)
+        vs = views_for(0)
+
+        def step():
+            for k, v in enumerate(vs):
+                gps.render_forward(g, [v], s, r.ws, loss[k:k + 1])
+                opt.backward_step([v], s, r.ws)
+        return step, r
+
+    def batched_form(prec):
+        s = settings(prec)
+        r = gps.Renderer(w.gaussians.M, cams, s, dev)
+        vs = views_for(prec)
+
+        def step():
+            gps.render_forward(g, vs, s, r.ws, loss[:1])
+            opt.backward_step(vs, s, r.ws)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            step()
+        torch.cuda.current_stream().wait_stream(side)
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            step()
+        return gr.replay, r
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        reset()
+        ev = []
+        for i in range(Wu + K):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            if i >= Wu:
+                ev.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / K
+
+    px = sum(c.width * c.height for c in cams)
+    prec = PRECISIONS[precision]
+    forms = {}
+    for name, make in (("plain_fp32_single_frame_eager", plain_form),
+                       ("batched_fp32_graph", lambda: batched_form(0)),
+                       (f"batched_{precision}_graph", lambda: batched_form(prec))):
+        fn, r = make()
+        ms = timed(fn)
+        forms[name] = {"ms_per_step": ms, "pixel_iterations_per_s": px / (ms * 1e-3),
+                       "status": r.status()}
+        del r
+    plain = forms["plain_fp32_single_frame_eager"]["ms_per_step"]
+    return {"metric": "rendered pixel-iterations/s (fwd+bwd+Adam)",
+            "views": f"{n_views} room frames {cams[0].width}x{cams[0].height}",
+            "forms": forms,
+            "speedup": plain / forms[f"batched_{precision}_graph"]["ms_per_step"],
+            "speedup_fp32_batched_graph": plain / forms["batched_fp32_graph"]["ms_per_step"]}
+
+
+def precision_errors(pipe, w, dev):
+    """Max and mean error of the GPU's images, loss and gradients against the
+    FP64 oracle, for each colour storage type, on frame 0 with the oracle's
+    fusion + ray-cast images (the oracle run of cpu_baseline): the kernel takes
+    C_t and the colour target rounded to the storage type, the oracle the
+    float values."""
+    import numpy as np
+    import torch
+    gps = pipe.gps
+    ref = getattr(_oracle_iteration, "last", None)
+    if ref is None:
+        return None
+    f = w.frames[0]
+    H, W = f.cam.height, f.cam.width
+    Ct, Dt = _oracle_iteration.sdf
+    out = {}
+    for name, prec in PRECISIONS.items():
+        dt = gps.PREC_DTYPE[prec]
+        s = gps.settings(eps_depth=w.eps_depth, lambda_depth=w.lambda_depth, near=w.near,
+                         tile=(pipe.s.tile_w, pipe.s.tile_h), precision=prec)
+        r = gps.Renderer(w.gaussians.M, [f.cam], s, dev)
+        g = gps.Gaussians.from_numpy(w.gaussians, dev)
+        cu = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+        v = gps.View(f.cam, cu(Ct).to(dt), cu(Dt), cu(f.rgb).to(dt), cu(f.depth),
+                     out_rgb=torch.empty(3, H, W, device=dev, dtype=dt))
+        loss = torch.zeros(1, device=dev)
+        gps.render_forward(g, [v], s, r.ws, loss)
+        grads = g.zeros_like()
+        gps.render_backward(g, [v], s, r.ws, grads)
+        torch.cuda.synchronize()
+        img = np.abs(v.out_rgb.float().cpu().numpy() - ref["C"])
+        ent = {"image_max_abs": float(img.max()), "image_mean_abs": float(img.mean()),
+               "loss_rel": abs(loss.item() - ref["L"]) / abs(ref["L"]), "grads": {}}
+        for k, t in zip(("means", "log_scales", "quats", "opacity_logits", "rgb"), grads.tensors()):
+            o = ref["grads"][k]
+            d = np.abs(t.cpu().numpy().reshape(o.shape) - o)
+            ent["grads"][k] = {"max_rel": float(d.max() / np.abs(o).max()),
+                               "mean_rel": float(d.mean() / np.abs(o).mean())}
+        out[name] = ent
+    return {"workload": f"frame 0, {W}x{H}, {w.gaussians.M} Gaussians, fused colour L1 + depth",
+            "note": "max errors include counting decisions within FP32 rounding of their "
+                    "thresholds (bounded per pixel and per parameter by the parity tests); "
+                    "the means show the storage rounding",
+            "by_storage": out}
+
+
 def kernels_per_step(mode, tile, schedule="tiles", deterministic=False, fused=True,
                      size=(640, 480)):
     # fuse, raycast + per iteration: project, scan, emit, [sort + split where the
     # lists are depth-sorted, or where a view's tile grid exceeds what the
     # binning histogram holds (then the unsorted lists go through super-tiles
-    # and a split)], composite, finalize, composite_bwd [deterministic: + slot
-    # placement and pair gather; per-Gaussian schedule: pixel terms +
+    # and a split)], composite, finalize, composite_bwd [deterministic: + the
+    # upstream maxima, the fixed-point exponents and the conversion (OIT), or
+    # the pair-slot placement and gather (alpha); per-Gaussian schedule: pixel terms +
     # per-Gaussian], projection adjoint + Adam (fused: one kernel, else two),
     # step counter
     tiles = schedule != "per-gaussian"
     n_tiles = -(-size[0] // tile[0]) * -(-size[1] // tile[1])
     sorted_lists = tiles and (mode == "alpha" or deterministic)
     split = 1 if sorted_lists or n_tiles > TILE_BIN_MAX else 0
-    extra = 2 if tiles and deterministic else (0 if tiles else 1)
+    if not tiles:
+        extra = 1
+    elif deterministic:
+        extra = 3 if mode == "oit" else 2
+    else:
+        extra = 0
     return 2 + ITERS_PER_FRAME * (8 + split + extra + (0 if fused else 1))
 
 
@@ -632,8 +795,12 @@ def run_ours(args, rank, world, local):
     }
     if e2e:
         line["e2e"] = e2e
+    if args.workload == "room" and not args.no_speedup:
+        line["batched_speedup"] = batched_speedup(pipe, w, dev, K, Wu)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
+        if args.workload == "room":
+            line["precision_errors_vs_fp64"] = precision_errors(pipe, w, dev)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -676,6 +843,8 @@ def _oracle_iteration(w, frame, band, lam):
     L, dC, dD, nv, _ = oracle.loss(out["C"], out["D"], Ctgt, Dtgt, Dt, lam)
     g2 = oracle.composite_backward(rec, Ct, Dt, w.eps_depth, dC, dD)
     gr = oracle.project_backward(g, f.cam, g2, w.near)
+    if y0 == 0 and y1 == H - 1:  # a whole frame: kept for precision_errors
+        _oracle_iteration.last = {"C": out["C"], "L": L, "grads": gr}
     extra = [g.sh_rest] if g.sh_rest is not None else []
     p = np.concatenate([a.reshape(-1) for a in g.arrays() + extra])
     gg = np.concatenate([gr[k].reshape(-1) for k in ("means", "log_scales", "quats", "opacity_logits",

@@ -174,9 +174,10 @@ typedef struct GpsRenderSettings {
   int32_t tile_w, tile_h;/* pixels per tile; 0, 0 = 16 x 8; supported: 16x16,
                             16x8, 8x8, 32x8 (gps_autotune_tiles picks one)   */
   int32_t deterministic; /* 1: bitwise reproducible: tile lists sorted by
-                            (depth, index), fixed-order gradient reduction, no
-                            float atomics.  0 (OIT): lists in emission order,
-                            which may change the last bits of C* run to run  */
+                            (depth, index); gradient sums in 64-bit fixed
+                            point (OIT) or in fixed order (alpha), no float
+                            atomics.  0 (OIT): lists in emission order, which
+                            may change the last bits of C* run to run         */
   int32_t stages;        /* GPS_STAGE_* mask, 0 = all                          */
   int32_t instrument;    /* 1: count Gaussian-pixel evaluations (slower; for
                             measurement runs) into the view scalars           */
@@ -231,7 +232,9 @@ typedef struct GpsWorkspaceLayout {
   size_t pix_state;     /* float [H*W][8] saved per-pixel forward state       */
   size_t tile_partials; /* float [tiles][4] loss partial sums                 */
   size_t view_scalars;  /* float [8]: loss, colour sum, depth sum, N_valid,
-                           (bin, Gaussian) entries; then uint64 [4] evaluation
+                           (bin, Gaussian) entries, the deterministic pair
+                           counter, then the upstream maxima max|h|, max|sv|
+                           of the fixed-point backward; then uint64 [4] evaluation
                            counters: forward tested, forward counted, backward
                            tested, backward counted (instrument = 1)          */
   size_t grad2d;        /* float [M][12]                                      */
@@ -250,10 +253,19 @@ typedef struct GpsWorkspaceLayout {
   size_t pair_base;     /* uint32 [M] (deterministic mode): Gaussian i's first
                            pair_grads slot; its slots follow in row-major
                            order of the tiles of its rectangle                */
-  size_t tile_order;    /* int32 [tiles] (tile bins): the tiles in order of
-                           decreasing list length, in buckets of half an
-                           octave; the composites take their tiles in this
-                           order, longest lists first                         */
+  size_t tile_order;    /* int32 [tiles]: the tiles in order of decreasing
+                           entry count of their bin (the tile itself, or its
+                           super-tile), in buckets of half an octave; the
+                           composites take their tiles in this order, longest
+                           lists first                                        */
+  size_t grad_fixed;    /* int64 [M][10], then uint8 [M][16] (deterministic
+                           mode, OIT blend, tile schedule): each Gaussian's 2D
+                           gradient summed as integers in units of a
+                           power-of-two quantum from a bound on every addend
+                           (see composite.cu), so the sum is the same in any
+                           order; then each component's quantum exponent
+                           (+128); pair_grads and pair_base are empty in that
+                           mode                                              */
 } GpsWorkspaceLayout;
 
 /* ---------------------------------------------------------------- calls */

@@ -147,7 +147,7 @@ class GpsWorkspaceLayout(ctypes.Structure):
                 ("tiles_x", c_int32), ("tiles_y", c_int32), ("tile_w", c_int32),
                 ("tile_h", c_int32), ("super_x", c_int32), ("super_y", c_int32),
                 ("super_px", c_int32), ("tile_bins", c_int32), ("pair_capacity", c_int64),
-                ("pair_base", c_size_t), ("tile_order", c_size_t)]
+                ("pair_base", c_size_t), ("tile_order", c_size_t), ("grad_fixed", c_size_t)]
 
 
 EXPORTED = ("gps_last_error", "gps_version", "gps_workspace_size", "gps_workspace_layout",

@@ -117,8 +117,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_super_kernel(const __grid_c
     if (run > (unsigned long long)cap) set_status(status, GPS_ERR_CAPACITY);
   }
   if (v.tile_order) {
-    // tiles as bins: order them by decreasing list length (a counting sort
-    // on half-octave buckets of the length; order inside a bucket arbitrary)
+    // the tiles in order of decreasing list length: a counting sort on
+    // half-octave buckets of their bin's entry count (a bin holds LX x LY
+    // tiles, each listing at most the bin's entries; tiles themselves as
+    // bins: LX = LY = 1), order inside a bucket arbitrary
+    const int LX = max(1, (1 << v.bin_sx) / v.tw), LY = max(1, (1 << v.bin_sy) / v.th);
     __shared__ uint32_t s_bucket[64];
     auto bucket = [&](int k) {
       const uint32_t c = ranges[k].y - ranges[k].x;
@@ -126,9 +129,20 @@ __global__ void __launch_bounds__(kScanThreads) scan_super_kernel(const __grid_c
       const int l = 31 - __clz(c);  // floor(log2 c)
       return min(63, 1 + 2 * l + (2 * c >= 3u << l ? 1 : 0));
     };
+    // tiles of bin k inside the tile grid: [tx0, tx0 + nx) x [ty0, ty0 + ny)
+    auto tiles_of = [&](int k, int& tx0, int& ty0, int& nx, int& ny) {
+      tx0 = (k % v.sup_x) * LX;
+      ty0 = (k / v.sup_x) * LY;
+      nx = max(0, min(LX, v.tiles_x - tx0));
+      ny = max(0, min(LY, v.tiles_y - ty0));
+    };
     if (tid < 64) s_bucket[tid] = 0u;
     __syncthreads();
-    for (int k = b; k < e; ++k) atomicAdd(s_bucket + bucket(k), 1u);
+    for (int k = b; k < e; ++k) {
+      int tx0, ty0, nx, ny;
+      tiles_of(k, tx0, ty0, nx, ny);
+      if (nx * ny) atomicAdd(s_bucket + bucket(k), (uint32_t)(nx * ny));
+    }
     __syncthreads();
     if (tid == 0) {
       uint32_t base = 0;
@@ -139,7 +153,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_super_kernel(const __grid_c
       }
     }
     __syncthreads();
-    for (int k = b; k < e; ++k) v.tile_order[atomicAdd(s_bucket + bucket(k), 1u)] = k;
+    for (int k = b; k < e; ++k) {
+      int tx0, ty0, nx, ny;
+      tiles_of(k, tx0, ty0, nx, ny);
+      for (int ly = 0; ly < ny; ++ly)
+        for (int lx = 0; lx < nx; ++lx)
+          v.tile_order[atomicAdd(s_bucket + bucket(k), 1u)] = (ty0 + ly) * v.tiles_x + tx0 + lx;
+    }
   }
 }
 

@@ -32,6 +32,9 @@ cudaError_t launch_composite_bwd(const ViewBatch&, int, int, float, float, const
                                  int, int, cudaStream_t);
 cudaError_t launch_finalize_loss(const ViewBatch&, float, float*, int, cudaStream_t);
 cudaError_t launch_gather_pair_grads(const ViewBatch&, int, cudaStream_t);
+cudaError_t launch_upstream_max(const ViewBatch&, float, float, const float*, cudaStream_t);
+cudaError_t launch_fixed_scale(const ViewBatch&, int, cudaStream_t);
+cudaError_t launch_fixed_to_grad2d(const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_pair_base(const ViewBatch&, int, const int*, cudaStream_t);
 cudaError_t launch_adam(const GpsGaussians&, const GpsGaussians&, const GpsGaussians&,
                         const GpsGaussians&, const GpsAdamHyper&, int, int*, cudaStream_t);
@@ -103,6 +106,12 @@ bool tile_bins(const GpsView* views, int32_t n_views, const GpsRenderSettings* s
 }
 
 // Workspace: [status 256 B] then per view, in order, its regions.
+// Deterministic mode sums the OIT blend's 2D gradients in fixed point (any
+// order of the carry-over backward's additions gives the same bits).
+bool fixed_point_grads(const GpsRenderSettings& s) {
+  return s.deterministic && s.blend_mode == GPS_BLEND_OIT && s.schedule == GPS_SCHEDULE_TILES;
+}
+
 int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRenderSettings* s,
                int32_t want, GpsWorkspaceLayout* out, size_t* total) {
   if (M < 0 || n_views <= 0 || !views || !s) return fail(GPS_ERR_INVALID_ARG, "bad layout arguments");
@@ -157,14 +166,19 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     L.tile_partials = off; off = align256(off + ntiles * 16);
     L.view_scalars = off; off = align256(off + 64);
     L.grad2d = off; off = align256(off + (size_t)M * 48);
+    // deterministic mode: fixed-point sums (OIT, tile schedule) or one slot
+    // per (tile, Gaussian) pair (the front-to-back variant)
+    const bool fixed = fixed_point_grads(*s);
     L.pair_grads = off;
-    off = align256(off + (s->deterministic ? (size_t)cap * per_super * 48 : 0));
+    off = align256(off + (s->deterministic && !fixed ? (size_t)cap * per_super * 48 : 0));
     L.pix_grad = off;
     off = align256(off + (s->schedule == GPS_SCHEDULE_PER_GAUSSIAN ? npx * 32 : 0));
     L.pair_base = off;
-    off = align256(off + (s->deterministic ? (size_t)M * 4 : 0));
+    off = align256(off + (s->deterministic && !fixed ? (size_t)M * 4 : 0));
     L.tile_order = off;
-    off = align256(off + (by_tile ? ntiles * 4 : 0));
+    off = align256(off + ntiles * 4);
+    L.grad_fixed = off;
+    off = align256(off + (fixed ? (size_t)M * 96 : 0));
     L.tiles_x = tx;
     L.tiles_y = ty;
     L.tile_w = tc.tw;
@@ -216,7 +230,8 @@ int32_t check_gaussians(const GpsGaussians* g, const char* what) {
   return GPS_OK;
 }
 
-ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int prec) {
+ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int prec, int M,
+                  bool fixed) {
   ViewDev v{};
   v.cam = make_cam(vw.K, vw.T_wc);
   v.Ct = vw.sdf_rgb;
@@ -247,7 +262,9 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int 
   v.pair_grads = reinterpret_cast<float4*>(ws + L.pair_grads);
   v.pix_g = reinterpret_cast<float4*>(ws + L.pix_grad);
   v.pair_base = reinterpret_cast<uint32_t*>(ws + L.pair_base);
-  v.tile_order = L.tile_bins ? reinterpret_cast<int*>(ws + L.tile_order) : nullptr;
+  v.tile_order = reinterpret_cast<int*>(ws + L.tile_order);
+  v.grad_fixed = fixed ? reinterpret_cast<long long*>(ws + L.grad_fixed) : nullptr;
+  v.fixed_exp = fixed ? reinterpret_cast<uint4*>(ws + L.grad_fixed + (size_t)M * 80) : nullptr;
   {
     const int sp = 1 << super_shift_for(L.tile_w);
     v.pair_slots = L.pair_capacity * ((sp / L.tile_w) * (sp / L.tile_h));
@@ -281,7 +298,7 @@ void make_batch(int M, const GpsView* views, int32_t n_views, const GpsRenderSet
   for (int j = 0; j < vb.n; ++j) {
     GpsWorkspaceLayout L;
     layout(M, views, n_views, s, b0 + j, &L, nullptr);
-    vb.v[j] = make_view(views[b0 + j], base, L, s->precision);
+    vb.v[j] = make_view(views[b0 + j], base, L, s->precision, M, fixed_point_grads(*s));
     max_nsup = std::max(max_nsup, vb.v[j].sup_x * vb.v[j].sup_y);
     tiles[j] = vb.v[j].tiles_x * vb.v[j].tiles_y;
     vb.order[j] = j;
@@ -333,6 +350,16 @@ cudaError_t composite_backward(const ViewBatch& vb, int M, const GpsRenderSettin
   if ((stages & GPS_STAGE_COMPOSITE_BWD) && s->schedule == GPS_SCHEDULE_PER_GAUSSIAN) {
     e = launch_composite_bwd_per_gaussian(vb, M, s->eps_depth, s->lambda_depth, dloss,
                                           s->instrument ? 1 : 0, st);
+  } else if ((stages & GPS_STAGE_COMPOSITE_BWD) && fixed_point_grads(*s)) {
+    // deterministic, OIT: the carry-over walk with fixed-point sums
+    for (int j = 0; j < vb.n && e == cudaSuccess; ++j)
+      e = cudaMemsetAsync(vb.v[j].scalars + 6, 0, 2 * sizeof(float), st);
+    if (e == cudaSuccess) e = launch_upstream_max(vb, s->eps_depth, s->lambda_depth, dloss, st);
+    if (e == cudaSuccess && M > 0) e = launch_fixed_scale(vb, M, st);
+    if (e == cudaSuccess)
+      e = launch_composite_bwd(vb, vb.v[0].tw, vb.v[0].th, s->eps_depth, s->lambda_depth, dloss,
+                               s->blend_mode, 1, s->instrument ? 1 : 0, depth_sorted(*s), st);
+    if (e == cudaSuccess && M > 0) e = launch_fixed_to_grad2d(vb, M, st);
   } else if (stages & GPS_STAGE_COMPOSITE_BWD) {
     for (int j = 0; j < vb.n && e == cudaSuccess; ++j)
       e = s->deterministic ? cudaMemsetAsync(vb.v[j].scalars + 5, 0, sizeof(float), st)

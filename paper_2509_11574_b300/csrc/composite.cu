@@ -645,6 +645,162 @@ __device__ __forceinline__ void zero_slot(const ViewDev& v, long long slot) {
   }
 }
 
+// ----------------------------------------- deterministic fixed-point sums
+// Deterministic mode (OIT blend, tile schedule) runs the carry-over backward,
+// whose (warp block, Gaussian) partials reach a Gaussian in an order that
+// varies from run to run.  Each partial is therefore added as a 64-bit
+// integer in units of 2^e[k] for component k: integer addition is
+// associative, so the sum is the same whatever the order, and converting
+// back to float is one rounding.  e[k] comes from a bound b_k on the
+// magnitude of any partial of that component of that Gaussian, computed once
+// per Gaussian (fixed_scale_kernel) from its record and the view's upstream
+// maxima (hmax >= |h| of every pixel's dL/dC* / N, dL/dD* / N; smax >= |sv|):
+//   a counted pixel has alpha <= sigma <= 1, |dx| <= ext_x, |dy| <= ext_y;
+//   with V = hmax (|r| + |g| + |b| + |d|) + smax >= |dL/dalpha|, over a warp
+//   block's 32 pixels |m_0..3| <= 32 hmax, |m4| <= 32 V sigma,
+//   |m5| <= 32 V ext_x, |m6| <= 32 V ext_y, |m7| <= 32 V ext_x^2,
+//   |m8| <= 32 V ext_x ext_y, |m9| <= 32 V ext_y^2, and grad2d_of's
+//   combinations follow; the bounds below carry a factor 2 for the FP32
+//   rounding of the partial and of the bound itself.
+// With at most n = (tiles of the Gaussian's rectangle) x (warps per tile)
+// partials, 2^e[k] >= b_k 2^-(62 - ceil(log2 n)) keeps every partial below
+// 2^(62 - ceil(log2 n)) quanta and every sum below 2^62: no overflow.  The
+// quantum is about 2^-56 of the bound at the room workload's sizes.  e is
+// clamped to [-120, 126] so that 2^-e and 2^e are normal floats (raising e
+// only coarsens the quantum; a bound above 2^(188 - ceil(log2 n)) is not met
+// by finite FP32 gradients).
+constexpr int kFixedEMin = -120, kFixedEMax = 126;
+
+__device__ __forceinline__ void fixed_exponents(float ca, float cb, float cc, float cr, float cg,
+                                                float cbl, float d, float ex, float ey, float hmax,
+                                                float smax, int n_part, int (&e)[10]) {
+  const float V = hmax * (fabsf(cr) + fabsf(cg) + fabsf(cbl) + fabsf(d)) + smax;
+  float b[10];
+  b[0] = 64.0f * V * (fabsf(ca) * ex + fabsf(cb) * ey);
+  b[1] = 64.0f * V * (fabsf(cb) * ex + fabsf(cc) * ey);
+  b[2] = 32.0f * V * ex * ex;
+  b[3] = 64.0f * V * ex * ey;
+  b[4] = 32.0f * V * ey * ey;
+  b[5] = 64.0f * V;
+  b[6] = b[7] = b[8] = b[9] = 64.0f * hmax;
+  const int ln = n_part > 1 ? 32 - __clz(n_part - 1) : 0;  // ceil(log2 n)
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    int x = 0;
+    frexpf(fminf(b[k], 3.0e38f), &x);  // b < 2^x (NaN -> 3e38)
+    e[k] = min(max(x - (62 - ln), kFixedEMin), kFixedEMax);
+  }
+}
+
+// Exponent k of a Gaussian's packed exponents (byte k, biased by 128).
+__device__ __forceinline__ int fixed_e(const uint4& p, int k) {
+  const uint32_t w = k < 4 ? p.x : (k < 8 ? p.y : p.z);
+  return (int)((w >> (8 * (k & 3))) & 0xffu) - 128;
+}
+
+// Add a (warp block, Gaussian gi) partial g to gi's fixed-point sums.  The
+// integer q = g 2^-e, rounded half away from zero, is formed from the
+// float's fields: g = +-m 2^(E - 150) with the 24-bit significand m, so
+// q = m 2^(E - 150 - e) (an exact left shift: the bound keeps it below
+// 2^62; or a right shift with rounding).  Subnormal g (below 2^-126, under
+// the smallest quantum 2^-120) adds nothing.
+__device__ __forceinline__ void fixed_add(const ViewDev& v, uint32_t gi, const float (&g)[10]) {
+  const uint4 p = __ldg(v.fixed_exp + gi);
+  unsigned long long* o = reinterpret_cast<unsigned long long*>(v.grad_fixed + 10 * (size_t)gi);
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    const int bits = __float_as_int(g[k]);
+    const int E = (bits >> 23) & 0xff;
+    const int sh = E - 150 - fixed_e(p, k);
+    const unsigned long long m = (unsigned long long)((bits & 0x7fffff) | 0x800000);
+    unsigned long long q =
+        sh >= 0 ? m << min(sh, 63) : (sh > -25 ? (m + (1ull << (-sh - 1))) >> (-sh) : 0ull);
+    if (E == 0) q = 0ull;
+    if (bits < 0) q = 0ull - q;
+    if (q != 0ull) atomicAdd(o + k, q);
+  }
+}
+
+// Per Gaussian, after the upstream maxima: its packed exponents, and zeroed
+// sums.  Block row blockIdx.y: view.
+__global__ void __launch_bounds__(256) fixed_scale_kernel(const __grid_constant__ ViewBatch vb,
+                                                          int M) {
+  chain_wait();
+  const ViewDev& v = vb.v[blockIdx.y];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const float4 A = v.rec[4 * (size_t)i], B = v.rec[4 * (size_t)i + 1], C = v.rec[4 * (size_t)i + 2];
+  const float ey = v.rec[4 * (size_t)i + 3].x;
+  int n_part = 1, x0, x1, y0, y1;
+  if (record_rect(A.x, A.y, C.w, ey, v.cam.W, v.cam.H, x0, x1, y0, y1))
+    n_part = (x1 / v.tw - x0 / v.tw + 1) * (y1 / v.th - y0 / v.th + 1) * (v.tw * v.th / 32);
+  int e[10];
+  fixed_exponents(B.x, B.y, B.z, C.x, C.y, C.z, A.z, C.w, ey, v.scalars[6], v.scalars[7], n_part,
+                  e);
+  uint32_t w[3] = {0u, 0u, 0u};
+#pragma unroll
+  for (int k = 0; k < 10; ++k) w[k >> 2] |= (uint32_t)(e[k] + 128) << (8 * (k & 3));
+  v.fixed_exp[i] = make_uint4(w[0], w[1], w[2], 0u);
+  longlong2* o = reinterpret_cast<longlong2*>(v.grad_fixed + 10 * (size_t)i);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) o[k] = make_longlong2(0, 0);
+}
+
+// The views' upstream maxima (scalars[6] = hmax, scalars[7] = smax, zero on
+// entry), from the same per-pixel terms the backward stages.  Block row
+// blockIdx.y: view.
+__global__ void __launch_bounds__(256) upstream_max_kernel(const __grid_constant__ ViewBatch vb,
+                                                           float eps, float lambda,
+                                                           const float* dloss) {
+  chain_wait();
+  const ViewDev& v = vb.v[blockIdx.y];
+  const long long npx = (long long)v.cam.W * v.cam.H;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float hm = 0.f, sm = 0.f;
+  if (pix < npx) {
+    const float scale = loss_scale(v, v.fused, dloss);
+    const float4 st = v.pix_a[pix];
+    const float iN = 1.0f / (1.0f + v.pix_b[pix].x);
+    const float dt = __ldg(v.Dt + pix);
+    float g0, g1, g2, gD;
+    upstream(v, pix, npx, st, dt, v.fused, lambda, scale, g0, g1, g2, gD);
+    hm = fmaxf(fmaxf(fabsf(g0 * iN), fabsf(g1 * iN)), fmaxf(fabsf(g2 * iN), fabsf(gD * iN)));
+    sm = fabsf((g0 * st.x + g1 * st.y + g2 * st.z + gD * st.w) * iN);
+  }
+  hm = warp_max(hm);
+  sm = warp_max(sm);
+  if ((threadIdx.x & 31) == 0) {
+    // non-negative floats order as their bit patterns
+    atomicMax(reinterpret_cast<unsigned*>(v.scalars + 6), __float_as_uint(hm));
+    atomicMax(reinterpret_cast<unsigned*>(v.scalars + 7), __float_as_uint(sm));
+  }
+}
+
+// Fixed-point sums -> grad2d (float): one rounding of the integer sum, then
+// the exact power-of-two scale 2^e.  Block row blockIdx.y: view.
+__global__ void __launch_bounds__(256) fixed_to_grad2d_kernel(const __grid_constant__ ViewBatch vb,
+                                                              int M) {
+  chain_wait();
+  const ViewDev& v = vb.v[blockIdx.y];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const uint4 p = v.fixed_exp[i];
+  const longlong2* s = reinterpret_cast<const longlong2*>(v.grad_fixed + 10 * (size_t)i);
+  float g[12];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const longlong2 t = s[k];
+    g[2 * k] = __fmul_rn(__ll2float_rn(t.x), __int_as_float((127 + fixed_e(p, 2 * k)) << 23));
+    g[2 * k + 1] =
+        __fmul_rn(__ll2float_rn(t.y), __int_as_float((127 + fixed_e(p, 2 * k + 1)) << 23));
+  }
+  g[10] = g[11] = 0.f;
+  float4* o = v.grad2d + 3 * (size_t)i;
+  o[0] = make_float4(g[0], g[1], g[2], g[3]);
+  o[1] = make_float4(g[4], g[5], g[6], g[7]);
+  o[2] = make_float4(g[8], g[9], g[10], g[11]);
+}
+
 // 2D gradient g of a (tile, Gaussian gi) pair: deterministic mode writes it
 // into the pair's slot (skipped beyond the slot capacity), else adds it to
 // grad2d with vector atomics.
@@ -965,7 +1121,10 @@ __device__ __forceinline__ void bwd_flush(const ViewDev& v, const BwdGauss& G, b
   bwd_walk<INSTR>(G, has, blk, bx0, by0, s_h, s_s, m, n_tested, n_counted);
   if (has) {
     grad2d_of(m, G.ca, 0.5f * G.b2, G.cc, G.sig, g);
-    store_grad2d(v, 0, 0u, G.gi, g);
+    if (v.grad_fixed)
+      fixed_add(v, G.gi, g);
+    else
+      store_grad2d(v, 0, 0u, G.gi, g);
   }
 }
 
@@ -1444,7 +1603,8 @@ static cudaError_t bwd_tw(const ViewBatch& vb, float eps, float lambda, const fl
                           int det, int instr, int sorted, cudaStream_t st) {
   const int items = vb.tile_start[vb.n];
   if (items <= 0) return cudaSuccess;
-  if (mode == GPS_BLEND_OIT && !det && !sorted) {
+  // the carry-over walk: sort-free lists, or deterministic mode's fixed-point sums
+  if (mode == GPS_BLEND_OIT && ((!det && !sorted) || vb.v[0].grad_fixed)) {
     if (instr)
       launch_chained(composite_bwd_oit_carry_kernel<TW, TH, true>, dim3(items), dim3(TW * TH), 0, st,
           vb, eps, lambda, dloss);
@@ -1491,6 +1651,25 @@ cudaError_t launch_finalize_loss(const ViewBatch& vb, float lambda, float* loss,
 
 cudaError_t launch_pair_base(const ViewBatch& vb, int M, const int* status, cudaStream_t st) {
   launch_chained(pair_base_kernel, dim3((M + 255) / 256, vb.n), dim3(256), 0, st, vb, M, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_upstream_max(const ViewBatch& vb, float eps, float lambda, const float* dloss,
+                                cudaStream_t st) {
+  int max_px = 0;
+  for (int k = 0; k < vb.n; ++k) max_px = max(max_px, vb.v[k].cam.W * vb.v[k].cam.H);
+  launch_chained(upstream_max_kernel, dim3((max_px + 255) / 256, vb.n), dim3(256), 0, st, vb, eps,
+      lambda, dloss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixed_scale(const ViewBatch& vb, int M, cudaStream_t st) {
+  launch_chained(fixed_scale_kernel, dim3((M + 255) / 256, vb.n), dim3(256), 0, st, vb, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixed_to_grad2d(const ViewBatch& vb, int M, cudaStream_t st) {
+  launch_chained(fixed_to_grad2d_kernel, dim3((M + 255) / 256, vb.n), dim3(256), 0, st, vb, M);
   return cudaGetLastError();
 }
 

@@ -71,7 +71,9 @@ struct ViewDev {
   uint32_t* pair_base;    // [M] first slot of each Gaussian (deterministic mode)
   long long pair_slots;
   float4* pix_g;          // [npx][2] per-Gaussian backward: (h), (sv, thr, -, -)
-  int* tile_order;        // [tiles] longest lists first (tile bins), else null
+  int* tile_order;        // [tiles] longest lists first (by their bin's entry count)
+  long long* grad_fixed;  // [M][10] fixed-point 2D gradient sums (deterministic OIT), else null
+  uint4* fixed_exp;       // [M] their quantum exponents, 10 bytes biased by 128 (same mode)
   int tiles_x, tiles_y, tw, th;
   // bins of the binning pass (sup_x * sup_y of them, 2^bin_sx x 2^bin_sy
   // pixels each): square super-tiles, or the tiles themselves
@@ -104,10 +106,14 @@ __device__ __forceinline__ int batch_slot(const int* start, int n, int item) {
 }
 
 // The tile of a view's per-tile work item: its tiles are taken in order of
-// decreasing list length where the binning has ordered them, so that the
-// longest lists start first and the grid's tail holds short ones.
+// decreasing list length (the binning's tile_order), so that the longest
+// lists start first and the grid's tail holds short ones.  An entry outside
+// the tile grid (a workspace that no binning pass has written) falls back to
+// the item's own tile.
 __device__ __forceinline__ int tile_of(const ViewDev& v, int item) {
-  return v.tile_order ? __ldg(v.tile_order + item) : item;
+  if (!v.tile_order) return item;
+  const int t = __ldg(v.tile_order + item);
+  return (unsigned)t < (unsigned)(v.tiles_x * v.tiles_y) ? t : item;
 }
 
 // Colour images are stored as float, IEEE binary16 or bfloat16 (GPS_PREC_*);

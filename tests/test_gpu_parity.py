@@ -336,10 +336,19 @@ def test_end_to_end_small(mode):
     _end_to_end(w, mode, lam=0.0)
 
 
-def test_end_to_end_grad_config():
-    """320x240 view, 20,000 Gaussians, colour + depth L1."""
+@pytest.mark.parametrize("det", [False, True])
+def test_end_to_end_grad_config(det):
+    """320x240 view, 20,000 Gaussians, colour + depth L1; deterministic mode
+    sums each Gaussian's gradient in 64-bit fixed point."""
     w = workload("grad")
-    _end_to_end(w, gps.BLEND_OIT, lam=1.0)
+    _end_to_end(w, gps.BLEND_OIT, lam=1.0, deterministic=det)
+
+
+@pytest.mark.parametrize("mode", [gps.BLEND_OIT, gps.BLEND_ALPHA])
+def test_end_to_end_small_deterministic(mode):
+    """Deterministic mode: fixed-point sums (OIT), ordered pair slots (alpha)."""
+    w = workload("small")
+    _end_to_end(w, mode, lam=1.0, deterministic=True)
 
 
 @pytest.mark.parametrize("prec", [gps.PREC_FP16, gps.PREC_BF16])
@@ -419,6 +428,13 @@ def test_end_to_end_room_bench_configuration():
     envelopes above."""
     w = workloads.room(n_frames=1, M=100_000)
     _end_to_end(w, oracle.OIT, w.lambda_depth, tile=(16, 8))
+
+
+def test_end_to_end_room_bench_configuration_deterministic():
+    """As above with deterministic mode: depth-sorted lists, the carry-over
+    backward adding every partial as a 64-bit integer."""
+    w = workloads.room(n_frames=1, M=100_000)
+    _end_to_end(w, oracle.OIT, w.lambda_depth, tile=(16, 8), deterministic=True)
 
 
 def test_deterministic_mode_is_bitwise_reproducible_and_matches():
