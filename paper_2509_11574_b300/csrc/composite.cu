@@ -1253,8 +1253,60 @@ __global__ void __launch_bounds__(TW* TH)
 }
 
 // ----------------------------------------------------- backward, alpha mode
-constexpr int kAlphaBatch = 32;
+// Transposing butterfly over a warp: the warp's sums of 10 per-lane values
+// in 12 shuffles (a separate reduction per value takes 50).  At each level a
+// lane keeps part of the values it carries, sends the rest to its partner
+// and adds what the partner sent for its own part: 10 -> 5 (xor 16), 5 -> 3
+// or 2 (xor 8), -> 2 or 1 (xor 4), -> 1 (xor 2), then the pair adds (xor 1).
+// Returns the lane's sum and sets comp to its component (-1: none); lanes 2m
+// and 2m + 1 hold the same one.  The order of the additions is fixed.
+__device__ __forceinline__ float warp_sum10(const float (&v)[10], int lane, int& comp) {
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+  float a[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float r = __shfl_xor_sync(0xffffffffu, h4 ? v[i] : v[5 + i], 16);
+    a[i] = (h4 ? v[5 + i] : v[i]) + r;
+  }
+  // h3 = 0 keeps a0..a2, h3 = 1 keeps a3, a4
+  float b[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float send = h3 ? a[i] : (i < 2 ? a[3 + i] : 0.f);
+    const float r = __shfl_xor_sync(0xffffffffu, send, 8);
+    b[i] = h3 ? (i < 2 ? a[3 + i] + r : 0.f) : a[i] + r;
+  }
+  // h2 = 0 keeps b0, b1, h2 = 1 keeps b2
+  float c[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = h2 ? b[i] : (i == 0 ? b[2] : 0.f);
+    const float r = __shfl_xor_sync(0xffffffffu, send, 4);
+    c[i] = h2 ? (i == 0 ? b[2] + r : 0.f) : b[i] + r;
+  }
+  float d = (h1 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h1 ? c[0] : c[1], 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  const int ai = h3 ? (h2 ? -1 : 3 + (h1 ? 1 : 0)) : (h2 ? (h1 ? -1 : 2) : (h1 ? 1 : 0));
+  comp = ai < 0 ? -1 : ai + (h4 ? 5 : 0);
+  return d;
+}
 
+// list entries staged per round of the alpha backward (per-warp partials of
+// NW x NB x 10 floats stay within 20 KB of shared memory)
+template <int NT>
+struct AlphaBatch {
+  static constexpr int value = NT >= 256 ? 64 : NT;
+};
+
+// The front-to-back (alpha) backward: each pixel walks its list from its
+// last contributing entry back to the first, undoing the forward's
+// transmittance, T_j = T_{j+1} / (1 - alpha_j), and carrying the colour and
+// depth composited behind j.  A warp owns an 8 x 4 pixel block and walks only
+// the entries of the batch that can reach it (conservative ellipse test, in
+// front of its depth threshold, before its last contributing entry): the
+// skipped ones leave every pixel of the block unchanged.  Per entry the
+// warp's 10 gradient sums come from warp_sum10, per (tile, Gaussian) pair
+// the warps' sums are added in warp order.
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __grid_constant__ ViewBatch vb,
                                                                      float eps, float lambda,
@@ -1263,11 +1315,16 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
   chain_wait();
   constexpr int NT = TW * TH;
   constexpr int NW = NT / 32;
-  __shared__ float4 s_a[kAlphaBatch], s_b[kAlphaBatch], s_c[kAlphaBatch];
-  __shared__ float s_part[NW][kAlphaBatch][10];
+  constexpr int NB = AlphaBatch<NT>::value;
+  constexpr int NM = NB / 32;
+  static_assert(NB <= NT && NM * 32 == NB, "one staged entry per thread at most");
+  __shared__ float4 s_a[NB], s_b[NB], s_c[NB];
+  __shared__ float2 s_e[NB];
+  __shared__ float s_l2[NB];  // log2 sigma, as staged by the forward
+  __shared__ uint32_t s_gi[NB];
+  __shared__ float s_part[NW][NB][10];
+  __shared__ uint32_t s_mask[NW][NM];
   __shared__ float s_tmp[NW];
-  __shared__ uint32_t s_gi[kAlphaBatch];
-  __shared__ float s_l2[kAlphaBatch];  // log2 sigma, as staged by the forward
   const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
   const int tile = tile_of(v, blockIdx.x - vb.tile_start[slot]);
@@ -1275,7 +1332,9 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
   const int W = v.cam.W, H = v.cam.H;
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
+  int ox, oy, lx, ly;
+  warp_block<TW>(warp, lane, ox, oy, lx, ly);
+  const int px = tx * TW + lx, py = ty * TH + ly;
   const bool inside = px < W && py < H;
   const long long npx = (long long)W * H, pix = (long long)py * W + px;
   const float scale = loss_scale(v, fused, dloss);
@@ -1300,8 +1359,13 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
   const float fpx = (float)px, fpy = (float)py;
   const float maxlast = block_max<NT>((float)(mylast - r.x), s_tmp);
   const uint32_t top = r.x + (uint32_t)maxlast;
-  for (uint32_t hi = top; hi > r.x; hi = hi > r.x + kAlphaBatch ? hi - kAlphaBatch : r.x) {
-    const uint32_t lo = hi > r.x + kAlphaBatch ? hi - kAlphaBatch : r.x;
+  // this warp's block, last entry and depth threshold
+  const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
+  const float by0 = (float)(ty * TH + oy), by1 = by0 + 3.0f;
+  const uint32_t wlast = __reduce_max_sync(0xffffffffu, mylast);
+  const float wthr = warp_max(thr);
+  for (uint32_t hi = top; hi > r.x; hi = hi > r.x + NB ? hi - NB : r.x) {
+    const uint32_t lo = hi > r.x + NB ? hi - NB : r.x;
     const int nb = (int)(hi - lo);
     __syncthreads();
     if (tid < nb) {
@@ -1309,83 +1373,114 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
       const float4* rr = v.rec + 4 * (size_t)gi;
       float4 B = rr[1];
       B.y = 2.0f * B.y;
-      const float4 A0 = rr[0];
+      const float4 A0 = rr[0], C = rr[2];
       s_a[tid] = A0;
       s_b[tid] = B;
-      s_c[tid] = rr[2];
+      s_c[tid] = C;
+      s_e[tid] = make_float2(C.w, rr[3].x);
       s_gi[tid] = gi;
       s_l2[tid] = __log2f(A0.w);
     }
     __syncthreads();
-    for (int j = nb - 1; j >= 0; --j) {
-      const uint32_t k = lo + j;
-      float gv[10];
+    // the batch's entries this warp walks
+    uint32_t msk[NM];
 #pragma unroll
-      for (int c = 0; c < 10; ++c) gv[c] = 0.f;
-      bool contrib = false;
-      if (k < mylast) {
-        const float4 A = s_a[j], B = s_b[j], C = s_c[j];
-        const float dx = __fsub_rn(fpx, A.x), dy = __fsub_rn(fpy, A.y);
-        const float q = quad_form(B.x, B.y, B.z, dx, dy);
-        if (q <= B.w && A.z < thr) {
-          // the forward's alpha, bit for bit, so that T_i = T_{i+1} / (1 - alpha_i)
-          // undoes exactly what the forward multiplied in
-          const float raw = alpha_of(q, s_l2[j]);
-          const bool clamped = raw > kAlphaMax;
-          const float a = fminf(raw, kAlphaMax);
-          const float ia = 1.0f / (1.0f - a);
-          const float Tj = T * ia;
-          const float aT = a * Tj;
-          gv[6] = g0 * aT;
-          gv[7] = g1 * aT;
-          gv[8] = g2 * aT;
-          gv[9] = gD * aT;
-          const float dLda = g0 * (C.x * Tj - S0 * ia) + g1 * (C.y * Tj - S1 * ia) +
-                             g2 * (C.z * Tj - S2 * ia) + gD * (A.z * Tj - SD * ia);
-          S0 += C.x * aT;
-          S1 += C.y * aT;
-          S2 += C.z * aT;
-          SD += A.z * aT;
-          T = Tj;
-          if (!clamped) {
-            const float vv = dLda * a;
-            const float cb = 0.5f * B.y;
-            gv[0] = vv * (B.x * dx + cb * dy);
-            gv[1] = vv * (cb * dx + B.z * dy);
-            gv[2] = -0.5f * vv * dx * dx;
-            gv[3] = -vv * dx * dy;
-            gv[4] = -0.5f * vv * dy * dy;
-            gv[5] = __fdividef(dLda * raw, A.w);  // dL/dsigma = dL/dalpha * G, G = alpha / sigma
-          }
-          contrib = true;
+    for (int m = 0; m < NM; ++m) {
+      const int j = m * 32 + lane;
+      bool ok = false;
+      if (j < nb && lo + j < wlast) {
+        const float4 A = s_a[j];
+        const float2 E = s_e[j];
+        ok = A.z < wthr && A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 &&
+             A.y - E.y <= by1;
+        if (ok) {
+          const float4 B = s_b[j];
+          ok = ellipse_meets_rect(A.x, A.y, B.x, 0.5f * B.y, B.z, B.w, bx0, bx1, by0, by1);
         }
       }
-      if (__any_sync(0xffffffffu, contrib)) {
+      msk[m] = __ballot_sync(0xffffffffu, ok);
+    }
 #pragma unroll
-        for (int c = 0; c < 10; ++c) gv[c] = warp_sum(gv[c]);
-      }
-      if (lane == 0) {
+    for (int m = NM - 1; m >= 0; --m) {
+      uint32_t mm = msk[m], keep = 0u;
+      while (mm) {
+        const int jj = 31 - __clz(mm);
+        mm &= ~(1u << jj);
+        const int j = m * 32 + jj;
+        float gv[10];
 #pragma unroll
-        for (int c = 0; c < 10; ++c) s_part[warp][j][c] = gv[c];
+        for (int c = 0; c < 10; ++c) gv[c] = 0.f;
+        bool contrib = false;
+        if (lo + j < mylast) {
+          const float4 A = s_a[j], B = s_b[j];
+          const float dx = __fsub_rn(fpx, A.x), dy = __fsub_rn(fpy, A.y);
+          const float q = quad_form(B.x, B.y, B.z, dx, dy);
+          if (q <= B.w && A.z < thr) {
+            const float4 C = s_c[j];
+            // the forward's alpha, bit for bit, so that T_j = T_{j+1} / (1 - alpha_j)
+            // undoes what the forward multiplied in
+            const float raw = alpha_of(q, s_l2[j]);
+            const bool clamped = raw > kAlphaMax;
+            const float a = fminf(raw, kAlphaMax);
+            const float ia = 1.0f / (1.0f - a);
+            const float Tj = T * ia;
+            const float aT = a * Tj;
+            gv[6] = g0 * aT;
+            gv[7] = g1 * aT;
+            gv[8] = g2 * aT;
+            gv[9] = gD * aT;
+            const float dLda = g0 * (C.x * Tj - S0 * ia) + g1 * (C.y * Tj - S1 * ia) +
+                               g2 * (C.z * Tj - S2 * ia) + gD * (A.z * Tj - SD * ia);
+            S0 += C.x * aT;
+            S1 += C.y * aT;
+            S2 += C.z * aT;
+            SD += A.z * aT;
+            T = Tj;
+            if (!clamped) {
+              const float vv = dLda * a;
+              const float cb = 0.5f * B.y;
+              gv[0] = vv * (B.x * dx + cb * dy);
+              gv[1] = vv * (cb * dx + B.z * dy);
+              gv[2] = -0.5f * vv * dx * dx;
+              gv[3] = -vv * dx * dy;
+              gv[4] = -0.5f * vv * dy * dy;
+              gv[5] = __fdividef(dLda * raw, A.w);  // dL/dsigma = dL/dalpha * G, G = alpha / sigma
+            }
+            contrib = true;
+          }
+        }
+        if (__any_sync(0xffffffffu, contrib)) {
+          int comp;
+          const float t = warp_sum10(gv, lane, comp);
+          if (comp >= 0 && !(lane & 1)) s_part[warp][j][comp] = t;
+          keep |= 1u << jj;
+        }
       }
+      if (lane == 0) s_mask[warp][m] = keep;
     }
     __syncthreads();
-    // fixed-order sum over warps, then one write per (tile, Gaussian) pair
+    // fixed-order sum over the warps that walked the entry, then one write
+    // per (tile, Gaussian) pair
     if (tid < nb) {
       float g[10];
 #pragma unroll
-      for (int c = 0; c < 10; ++c) {
-        float acc = 0.f;
-        for (int w = 0; w < NW; ++w) acc += s_part[w][tid][c];
-        g[c] = acc;
+      for (int c = 0; c < 10; ++c) g[c] = 0.f;
+      bool any = false;
+      for (int w = 0; w < NW; ++w) {
+        if ((s_mask[w][tid >> 5] >> (tid & 31)) & 1u) {
+          any = true;
+#pragma unroll
+          for (int c = 0; c < 10; ++c) g[c] += s_part[w][tid][c];
+        }
       }
-      long long ps = 0;
-      if (deterministic) {
-        const uint32_t gi = s_gi[tid];
-        ps = pair_slot(v, gi, tx, ty, s_a[tid].x, s_a[tid].y, s_c[tid].w,
-                       v.rec[4 * (size_t)gi + 3].x);
+      if (any || deterministic) {
+        long long ps = 0;
+        if (deterministic) {
+          const uint32_t gi = s_gi[tid];
+          ps = pair_slot(v, gi, tx, ty, s_a[tid].x, s_a[tid].y, s_e[tid].x, s_e[tid].y);
+        }
+        store_grad2d(v, deterministic, ps, s_gi[tid], g);
       }
-      store_grad2d(v, deterministic, ps, s_gi[tid], g);
     }
   }
   if (deterministic) {
@@ -1395,6 +1490,227 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
       zero_slot(v, pair_slot(v, gi, tx, ty, A.x, A.y, C.w, v.rec[4 * (size_t)gi + 3].x));
     }
   }
+}
+
+// The alpha backward, not deterministic: the walk of composite_bwd_alpha_kernel
+// with the per-entry warp reduction replaced by a transpose through shared
+// memory.  Each warp gathers the entries that can reach its 8 x 4 block, in
+// walk order, into groups of 16; for a group,
+//   1. pixel lanes walk its entries in order (the per-pixel transmittance
+//      and composited colour behind each entry are sequential) and leave,
+//      per (pixel, entry), w = (alpha T_j, dL/dalpha alpha) (zero where the
+//      entry does not count, and the second zero where alpha is clamped) in
+//      shared memory;
+//   2. two lanes per entry (rows 0-1 and 2-3 of the block) walk the pixels
+//      and sum, from w and each pixel's upstream gradient, the moments of
+//      grad2d_of (as the OIT backward does); the pair adds its halves and the
+//      entry's Gaussian's block gradient goes to grad2d with vector atomics.
+// w is stored at [pixel][entry ^ (pixel mod 16)], so both phases touch
+// distinct banks.
+constexpr int kAlphaGroup = 16;
+
+template <int NT>
+struct AlphaCarryBatch {
+  static constexpr int value = NT >= 256 ? 64 : NT;
+};
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW* TH)
+    composite_bwd_alpha_carry_kernel(const __grid_constant__ ViewBatch vb, float eps, float lambda,
+                                     const float* dloss) {
+  chain_wait();
+  constexpr int NT = TW * TH;
+  constexpr int NW = NT / 32;
+  constexpr int NB = AlphaCarryBatch<NT>::value;
+  constexpr int NM = NB / 32;
+  constexpr int G = kAlphaGroup;
+  static_assert(NB <= NT && NM * 32 == NB, "one staged entry per thread at most");
+  __shared__ float4 s_a[NB], s_b[NB], s_c[NB];
+  __shared__ float2 s_e[NB];
+  __shared__ uint32_t s_gi[NB];
+  __shared__ float4 s_pg[NT];  // each pixel's upstream gradient, by warp block
+  // groups: (mx, my, d, log2 sigma), (a, 2b, c, qmax), (r, g, b, sigma), (list index, gi)
+  __shared__ float4 s_ga[NW][G], s_gb[NW][G], s_gc[NW][G];
+  __shared__ uint2 s_gk[NW][G];
+  __shared__ float2 s_w[NW][32][G];
+  __shared__ float s_tmp[NW];
+  const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
+  const ViewDev& v = vb.v[vb.order[slot]];
+  const int tile = tile_of(v, blockIdx.x - vb.tile_start[slot]);
+  const int fused = v.fused;
+  const int W = v.cam.W, H = v.cam.H;
+  const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int ox, oy, lx, ly;
+  warp_block<TW>(warp, lane, ox, oy, lx, ly);
+  const int px = tx * TW + lx, py = ty * TH + ly;
+  const bool inside = px < W && py < H;
+  const long long npx = (long long)W * H, pix = (long long)py * W + px;
+  const float scale = loss_scale(v, fused, dloss);
+  const uint2 r = v.tile_ranges[tile];
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, T = 1.f, thr = -INFINITY;
+  float S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
+  uint32_t mylast = r.x;
+  if (inside) {
+    const float4 st = v.pix_a[pix];
+    const float4 sb = v.pix_b[pix];
+    const float dt = __ldg(v.Dt + pix);
+    upstream(v, pix, npx, st, dt, fused, lambda, scale, g0, g1, g2, gD);
+    T = sb.x;
+    mylast = min(max(__float_as_uint(sb.y), r.x), r.y);  // stays inside this tile's list
+    thr = depth_threshold(dt, eps);
+    S0 = T * ld_col(v.Ct, pix, v.prec);
+    S1 = T * ld_col(v.Ct, npx + pix, v.prec);
+    S2 = T * ld_col(v.Ct, 2 * npx + pix, v.prec);
+    SD = T * dt;
+    if (g0 == 0.f && g1 == 0.f && g2 == 0.f && gD == 0.f) mylast = r.x;
+  }
+  s_pg[tid] = make_float4(g0, g1, g2, gD);
+  const float maxlast = block_max<NT>((float)(mylast - r.x), s_tmp);
+  const uint32_t top = r.x + (uint32_t)maxlast;
+  const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
+  const float by0 = (float)(ty * TH + oy), by1 = by0 + 3.0f;
+  const uint32_t wlast = __reduce_max_sync(0xffffffffu, mylast);
+  const float wthr = warp_max(thr);
+  float4* __restrict__ ga = s_ga[warp];
+  float4* __restrict__ gb = s_gb[warp];
+  float4* __restrict__ gc = s_gc[warp];
+  uint2* __restrict__ gk = s_gk[warp];
+  float2(*__restrict__ w)[G] = s_w[warp];
+  const float4* __restrict__ pg = s_pg + warp * 32;
+  const int ge = lane & (G - 1), half = lane >> 4;  // phase 2: entry, rows 2 half .. 2 half + 1
+
+  // one group of n entries: phase 1 (pixel lanes), then phase 2 (entry lanes)
+  auto run_group = [&](int n) {
+    __syncwarp();
+    const float fpx = (float)px, fpy = (float)py;
+    const int sw = lane & (G - 1);
+    for (int e = 0; e < n; ++e) {
+      const float4 A = ga[e];
+      const uint2 K = gk[e];
+      float aT = 0.f, vv = 0.f;
+      if (K.x < mylast) {
+        const float4 B = gb[e];
+        const float dx = __fsub_rn(fpx, A.x), dy = __fsub_rn(fpy, A.y);
+        const float q = quad_form(B.x, B.y, B.z, dx, dy);
+        if (q <= B.w && A.z < thr) {
+          const float4 C = gc[e];
+          // the forward's alpha, bit for bit (see composite_bwd_alpha_kernel)
+          const float raw = alpha_of(q, A.w);
+          const float a = fminf(raw, kAlphaMax);
+          const float ia = 1.0f / (1.0f - a);
+          const float Tj = T * ia;
+          aT = a * Tj;
+          const float dLda = g0 * (C.x * Tj - S0 * ia) + g1 * (C.y * Tj - S1 * ia) +
+                             g2 * (C.z * Tj - S2 * ia) + gD * (A.z * Tj - SD * ia);
+          S0 += C.x * aT;
+          S1 += C.y * aT;
+          S2 += C.z * aT;
+          SD += A.z * aT;
+          T = Tj;
+          if (!(raw > kAlphaMax)) vv = dLda * a;
+        }
+      }
+      w[lane][e ^ sw] = make_float2(aT, vv);
+    }
+    __syncwarp();
+    const float4 A = ga[ge];
+    float dcr = 0.f, dcg = 0.f, dcb = 0.f, dd = 0.f, sa = 0.f;
+    float sx = 0.f, sy = 0.f, sxx = 0.f, sxy = 0.f, syy = 0.f;
+#pragma unroll
+    for (int k2 = 0; k2 < 2; ++k2) {
+      const int ky = 2 * half + k2;
+      const float dy = __fsub_rn(by0 + (float)ky, A.y);
+      float ra = 0.f, rx = 0.f, rxx = 0.f;
+#pragma unroll
+      for (int kx = 0; kx < 8; ++kx) {
+        const int p = ky * 8 + kx;
+        const float2 wv = w[p][ge ^ (p & (G - 1))];
+        const float4 hh = pg[p];
+        dcr = fmaf(wv.x, hh.x, dcr);
+        dcg = fmaf(wv.x, hh.y, dcg);
+        dcb = fmaf(wv.x, hh.z, dcb);
+        dd = fmaf(wv.x, hh.w, dd);
+        const float dx = __fsub_rn(bx0 + (float)kx, A.x);
+        ra += wv.y;
+        const float tx_ = wv.y * dx;
+        rx += tx_;
+        rxx = fmaf(tx_, dx, rxx);
+      }
+      sa += ra;
+      sx += rx;
+      sxx += rxx;
+      sy = fmaf(ra, dy, sy);
+      sxy = fmaf(rx, dy, sxy);
+      syy = fmaf(ra * dy, dy, syy);
+    }
+    float m[10] = {dcr, dcg, dcb, dd, sa, sx, sy, sxx, sxy, syy};
+#pragma unroll
+    for (int c = 0; c < 10; ++c) m[c] += __shfl_xor_sync(0xffffffffu, m[c], 16);
+    if (half == 0 && ge < n) {
+      const float4 B = gb[ge], C = gc[ge];
+      float g[10];
+      grad2d_of(m, B.x, 0.5f * B.y, B.z, C.w, g);
+      store_grad2d(v, 0, 0, gk[ge].y, g);
+    }
+    __syncwarp();
+  };
+
+  int cnt = 0;  // entries in this warp's open group
+  for (uint32_t hi = top; hi > r.x; hi = hi > r.x + NB ? hi - NB : r.x) {
+    const uint32_t lo = hi > r.x + NB ? hi - NB : r.x;
+    const int nb = (int)(hi - lo);
+    __syncthreads();
+    if (tid < nb) {
+      const uint32_t gi = (uint32_t)v.keys[lo + tid];
+      const float4* rr = v.rec + 4 * (size_t)gi;
+      float4 B = rr[1];
+      B.y = 2.0f * B.y;
+      const float4 C = rr[2];
+      s_a[tid] = rr[0];
+      s_b[tid] = B;
+      s_c[tid] = C;
+      s_e[tid] = make_float2(C.w, rr[3].x);
+      s_gi[tid] = gi;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = NM - 1; m >= 0; --m) {
+      const int j = m * 32 + lane;
+      bool ok = false;
+      if (j < nb && lo + j < wlast) {
+        const float4 A = s_a[j];
+        const float2 E = s_e[j];
+        ok = A.z < wthr && A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 &&
+             A.y - E.y <= by1;
+        if (ok) {
+          const float4 B = s_b[j];
+          ok = ellipse_meets_rect(A.x, A.y, B.x, 0.5f * B.y, B.z, B.w, bx0, bx1, by0, by1);
+        }
+      }
+      uint32_t mask = __ballot_sync(0xffffffffu, ok);
+      while (mask) {
+        // the highest (G - cnt) entries of the mask join the group, highest first
+        uint32_t take = mask;
+        for (int extra = __popc(mask) - (G - cnt); extra > 0; --extra) take &= take - 1u;
+        if ((take >> lane) & 1u) {
+          const int e = cnt + __popc(take >> lane) - 1;
+          const float4 A = s_a[j], B = s_b[j], C = s_c[j];
+          ga[e] = make_float4(A.x, A.y, A.z, __log2f(A.w));
+          gb[e] = B;
+          gc[e] = make_float4(C.x, C.y, C.z, A.w);
+          gk[e] = make_uint2(lo + j, s_gi[j]);
+        }
+        cnt += __popc(take);
+        mask &= ~take;
+        if (cnt == G) {
+          run_group(G);
+          cnt = 0;
+        }
+      }
+    }
+  }
+  if (cnt > 0) run_group(cnt);
 }
 
 // Deterministic mode, before the backward: the first pair_grads slot of each
@@ -1618,9 +1934,13 @@ static cudaError_t bwd_tw(const ViewBatch& vb, float eps, float lambda, const fl
     else
       launch_chained(composite_bwd_oit_kernel<TW, TH, false>, dim3(items), dim3(TW * TH), 0, st,
           vb, eps, lambda, dloss, det, sorted);
-  } else
+  } else if (det) {
     launch_chained(composite_bwd_alpha_kernel<TW, TH>, dim3(items), dim3(TW * TH), 0, st,
         vb, eps, lambda, dloss, det);
+  } else {
+    launch_chained(composite_bwd_alpha_carry_kernel<TW, TH>, dim3(items), dim3(TW * TH), 0, st,
+        vb, eps, lambda, dloss);
+  }
   return cudaGetLastError();
 }
 
