@@ -1585,32 +1585,29 @@ __global__ void __launch_bounds__(TW* TH)
     __syncwarp();
     const float fpx = (float)px, fpy = (float)py;
     const int sw = lane & (G - 1);
+    // branch-free: an entry that does not count takes alpha = 0, which
+    // leaves T (T / 1) and the sums behind it (+ 0) exactly as they are
+#pragma unroll 4
     for (int e = 0; e < n; ++e) {
-      const float4 A = ga[e];
+      const float4 A = ga[e], B = gb[e], C = gc[e];
       const uint2 K = gk[e];
-      float aT = 0.f, vv = 0.f;
-      if (K.x < mylast) {
-        const float4 B = gb[e];
-        const float dx = __fsub_rn(fpx, A.x), dy = __fsub_rn(fpy, A.y);
-        const float q = quad_form(B.x, B.y, B.z, dx, dy);
-        if (q <= B.w && A.z < thr) {
-          const float4 C = gc[e];
-          // the forward's alpha, bit for bit (see composite_bwd_alpha_kernel)
-          const float raw = alpha_of(q, A.w);
-          const float a = fminf(raw, kAlphaMax);
-          const float ia = 1.0f / (1.0f - a);
-          const float Tj = T * ia;
-          aT = a * Tj;
-          const float dLda = g0 * (C.x * Tj - S0 * ia) + g1 * (C.y * Tj - S1 * ia) +
-                             g2 * (C.z * Tj - S2 * ia) + gD * (A.z * Tj - SD * ia);
-          S0 += C.x * aT;
-          S1 += C.y * aT;
-          S2 += C.z * aT;
-          SD += A.z * aT;
-          T = Tj;
-          if (!(raw > kAlphaMax)) vv = dLda * a;
-        }
-      }
+      const float dx = __fsub_rn(fpx, A.x), dy = __fsub_rn(fpy, A.y);
+      const float q = quad_form(B.x, B.y, B.z, dx, dy);
+      const bool counted = K.x < mylast && q <= B.w && A.z < thr;
+      // the forward's alpha, bit for bit (see composite_bwd_alpha_kernel)
+      const float raw = alpha_of(q, A.w);
+      const float a = counted ? fminf(raw, kAlphaMax) : 0.0f;
+      const float ia = 1.0f / (1.0f - a);
+      const float Tj = T * ia;
+      const float aT = a * Tj;
+      const float dLda = g0 * (C.x * Tj - S0 * ia) + g1 * (C.y * Tj - S1 * ia) +
+                         g2 * (C.z * Tj - S2 * ia) + gD * (A.z * Tj - SD * ia);
+      S0 += C.x * aT;
+      S1 += C.y * aT;
+      S2 += C.z * aT;
+      SD += A.z * aT;
+      T = Tj;
+      const float vv = counted && !(raw > kAlphaMax) ? dLda * a : 0.0f;
       w[lane][e ^ sw] = make_float2(aT, vv);
     }
     __syncwarp();
@@ -1657,7 +1654,10 @@ __global__ void __launch_bounds__(TW* TH)
   };
 
   int cnt = 0;  // entries in this warp's open group
-  for (uint32_t hi = top; hi > r.x; hi = hi > r.x + NB ? hi - NB : r.x) {
+  // batches from the back of the list; a last round without entries runs
+  // the open group (one call site keeps the kernel's code small)
+  for (uint32_t hi = top;; hi = hi > r.x + NB ? hi - NB : r.x) {
+    const bool flush = hi <= r.x;
     const uint32_t lo = hi > r.x + NB ? hi - NB : r.x;
     const int nb = (int)(hi - lo);
     __syncthreads();
@@ -1674,8 +1674,8 @@ __global__ void __launch_bounds__(TW* TH)
       s_gi[tid] = gi;
     }
     __syncthreads();
-#pragma unroll
-    for (int m = NM - 1; m >= 0; --m) {
+#pragma unroll 1
+    for (int m = flush ? 0 : NM - 1; m >= 0; --m) {
       const int j = m * 32 + lane;
       bool ok = false;
       if (j < nb && lo + j < wlast) {
@@ -1689,7 +1689,7 @@ __global__ void __launch_bounds__(TW* TH)
         }
       }
       uint32_t mask = __ballot_sync(0xffffffffu, ok);
-      while (mask) {
+      while (mask || (flush && cnt > 0)) {
         // the highest (G - cnt) entries of the mask join the group, highest first
         uint32_t take = mask;
         for (int extra = __popc(mask) - (G - cnt); extra > 0; --extra) take &= take - 1u;
@@ -1703,14 +1703,14 @@ __global__ void __launch_bounds__(TW* TH)
         }
         cnt += __popc(take);
         mask &= ~take;
-        if (cnt == G) {
-          run_group(G);
+        if (cnt == G || flush) {
+          run_group(cnt);
           cnt = 0;
         }
       }
     }
+    if (flush) break;
   }
-  if (cnt > 0) run_group(cnt);
 }
 
 // Deterministic mode, before the backward: the first pair_grads slot of each
