@@ -1511,7 +1511,7 @@ constexpr int kAlphaGroup = 16;
 
 template <int NT>
 struct AlphaCarryBatch {
-  static constexpr int value = NT >= 256 ? 64 : NT;
+  static constexpr int value = NT >= 256 ? 64 : 2 * NT;
 };
 
 template <int TW, int TH>
@@ -1524,7 +1524,8 @@ __global__ void __launch_bounds__(TW* TH)
   constexpr int NB = AlphaCarryBatch<NT>::value;
   constexpr int NM = NB / 32;
   constexpr int G = kAlphaGroup;
-  static_assert(NB <= NT && NM * 32 == NB, "one staged entry per thread at most");
+  constexpr int KPT = (NB + NT - 1) / NT;  // entries staged per thread
+  static_assert(NM * 32 == NB && KPT * NT >= NB, "whole chunks of 32 entries");
   __shared__ float4 s_a[NB], s_b[NB], s_c[NB];
   __shared__ float2 s_e[NB];
   __shared__ uint32_t s_gi[NB];
@@ -1656,22 +1657,39 @@ __global__ void __launch_bounds__(TW* TH)
   int cnt = 0;  // entries in this warp's open group
   // batches from the back of the list; a last round without entries runs
   // the open group (one call site keeps the kernel's code small)
+  // the first batch's keys (the next batch's are fetched while this one is
+  // walked)
+  uint32_t gi_next[KPT];
+  {
+    const uint32_t lo0 = top > r.x + NB ? top - NB : r.x;
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+      const uint32_t k = lo0 + u * NT + tid;
+      gi_next[u] = u * NT + tid < NB && k < top ? (uint32_t)v.keys[k] : 0u;
+    }
+  }
   for (uint32_t hi = top;; hi = hi > r.x + NB ? hi - NB : r.x) {
     const bool flush = hi <= r.x;
     const uint32_t lo = hi > r.x + NB ? hi - NB : r.x;
     const int nb = (int)(hi - lo);
+    const uint32_t lo2 = lo > r.x + NB ? lo - NB : r.x;  // the next batch: [lo2, lo)
     __syncthreads();
-    if (tid < nb) {
-      const uint32_t gi = (uint32_t)v.keys[lo + tid];
-      const float4* rr = v.rec + 4 * (size_t)gi;
-      float4 B = rr[1];
-      B.y = 2.0f * B.y;
-      const float4 C = rr[2];
-      s_a[tid] = rr[0];
-      s_b[tid] = B;
-      s_c[tid] = C;
-      s_e[tid] = make_float2(C.w, rr[3].x);
-      s_gi[tid] = gi;
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+      const int t = u * NT + tid;
+      const uint32_t gi = gi_next[u];
+      gi_next[u] = t < NB && lo2 + t < lo ? (uint32_t)v.keys[lo2 + t] : 0u;
+      if (t < nb) {
+        const float4* rr = v.rec + 4 * (size_t)gi;
+        float4 B = rr[1];
+        B.y = 2.0f * B.y;
+        const float4 C = rr[2];
+        s_a[t] = rr[0];
+        s_b[t] = B;
+        s_c[t] = C;
+        s_e[t] = make_float2(C.w, rr[3].x);
+        s_gi[t] = gi;
+      }
     }
     __syncthreads();
 #pragma unroll 1
