@@ -123,6 +123,16 @@ __device__ __forceinline__ float alpha_of(float q, float log2_sigma) {
   return ex2_approx(fmaf(q, -kHalfLog2e, log2_sigma));
 }
 
+// 1 / x by the hardware reciprocal (rcp.approx, within 1 ulp over the whole
+// range): the alpha backward's 1 / (1 - alpha) with 1 - alpha in [0.01, 1].
+// The correctly rounded rcp.rn took about 15 instructions with two branches
+// against one here.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Does the support {q <= qmax} of a Gaussian centred at (mx, my) meet the
 // rectangle [x0, x1] x [y0, y1]?  The minimum of the convex quadratic q over
 // the rectangle is 0 if the centre lies inside, else it lies on an edge, at
@@ -354,10 +364,11 @@ __global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_cons
 }
 
 // OIT forward with two pixels per lane: warp w covers the 8 x 8 pixel block
-// (w % (TW/8), w / (TW/8)) of the tile, lane l the pixels (l % 8, l / 8) and
-// (l % 8, l / 8 + 4) of it.  Each staged record is read once for both pixels,
-// which share dx.  Otherwise as composite_fwd_kernel (same decisions, same
-// per-pixel summation order, so the same images bit for bit).
+// (w % (TW/8), w / (TW/8)) of the tile, lane l the pixels (2 (l % 4), l / 4)
+// and (2 (l % 4) + 1, l / 4) of it.  Each staged record is read once for both
+// pixels, which share the dy terms of q.  Otherwise as composite_fwd_kernel
+// (same decisions, same per-pixel summation order, so the same images bit
+// for bit).
 template <int TW, int TH, bool INSTR>
 __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
     const __grid_constant__ ViewBatch vb, float eps, int has_tgt, int sorted) {
@@ -377,20 +388,17 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
   const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ox = (warp % BX) * 8, oy = (warp / BX) * 8;
-  const int px = tx * TW + ox + (lane & 7);
-  const int py0 = ty * TH + oy + (lane >> 3), py1 = py0 + 4;
-  const bool in0 = px < W && py0 < H, in1 = px < W && py1 < H;
+  // lane (c, r) = (lane & 3, lane >> 2) owns pixels (2c, r) and (2c + 1, r)
+  // of the warp's 8 x 8 block: one row, so the dy terms of q are shared
+  const int px0 = tx * TW + ox + 2 * (lane & 3), px1 = px0 + 1;
+  const int py = ty * TH + oy + (lane >> 2);
+  const bool in0 = px0 < W && py < H, in1 = px1 < W && py < H;
   const long long npx = (long long)W * H;
-  const long long pix0 = (long long)py0 * W + px, pix1 = (long long)py1 * W + px;
-  float ct[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, dt[2] = {0.f, 0.f};
-  if (in0) {
-    for (int c = 0; c < 3; ++c) ct[0][c] = ld_col(v.Ct, c * npx + pix0, v.prec);
-    dt[0] = __ldg(v.Dt + pix0);
-  }
-  if (in1) {
-    for (int c = 0; c < 3; ++c) ct[1][c] = ld_col(v.Ct, c * npx + pix1, v.prec);
-    dt[1] = __ldg(v.Dt + pix1);
-  }
+  const long long pix0 = (long long)py * W + px0, pix1 = pix0 + 1;
+  // C_t is read only at the end (fewer live registers in the list walk)
+  float dt[2] = {0.f, 0.f};
+  if (in0) dt[0] = __ldg(v.Dt + pix0);
+  if (in1) dt[1] = __ldg(v.Dt + pix1);
   const float thr0 = in0 ? depth_threshold(dt[0], eps) : -INFINITY;
   const float thr1 = in1 ? depth_threshold(dt[1], eps) : -INFINITY;
   const uint2 r = v.tile_ranges[tile];
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
   const uint32_t end = sorted ? depth_cut_block<NTT>(v.keys, r.x, r.y, bthr) : r.y;
   const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
   const float by0 = (float)(ty * TH + oy), by1 = by0 + 7.0f;
-  const float fpx = (float)px, fpy0 = (float)py0, fpy1 = (float)py1;
+  const float fpx0 = (float)px0, fpx1 = (float)px1, fpy = (float)py;
   float acc[2][5] = {{0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f}};  // r, g, b, W_G, Z
   bool wdone = wthr == -INFINITY;
   unsigned n_tested = 0, n_counted = 0;
@@ -460,13 +468,18 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
       }
     }
     __syncwarp();
+#pragma unroll 4
     for (int t = 0; t < cnt; ++t) {
       const int j = s_list[warp][t];
       const float4 A = s_a[j], B = s_b[j];
       const float4 C = s_c[j];
-      const float dx = __fsub_rn(fpx, A.x);
-      const float q0 = quad_form(B.x, B.y, B.z, dx, __fsub_rn(fpy0, A.y));
-      const float q1 = quad_form(B.x, B.y, B.z, dx, __fsub_rn(fpy1, A.y));
+      // quad_form's roundings, its dy terms computed once for the row
+      const float dy = __fsub_rn(fpy, A.y);
+      const float t1 = __fmul_rn(B.y, dy);
+      const float s3 = __fmul_rn(__fmul_rn(B.z, dy), dy);
+      const float dx0 = __fsub_rn(fpx0, A.x), dx1 = __fsub_rn(fpx1, A.x);
+      const float q0 = __fmaf_rn(dx0, __fmaf_rn(B.x, dx0, t1), s3);
+      const float q1 = __fmaf_rn(dx1, __fmaf_rn(B.x, dx1, t1), s3);
       const bool c0 = q0 <= B.w && A.z < thr0, c1 = q1 <= B.w && A.z < thr1;
       if (INSTR) {
         n_tested += in0 + in1;
@@ -492,10 +505,13 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
   for (int h = 0; h < 2; ++h) {
     const bool in = h ? in1 : in0;
     const long long pix = h ? pix1 : pix0;
+    float ct[3] = {0.f, 0.f, 0.f};
+    if (in)
+      for (int c = 0; c < 3; ++c) ct[c] = ld_col(v.Ct, c * npx + pix, v.prec);
     const float iN = 1.0f / (1.0f + acc[h][3]);
-    const float o0 = (ct[h][0] + acc[h][0]) * iN;
-    const float o1 = (ct[h][1] + acc[h][1]) * iN;
-    const float o2 = (ct[h][2] + acc[h][2]) * iN;
+    const float o0 = (ct[0] + acc[h][0]) * iN;
+    const float o1 = (ct[1] + acc[h][1]) * iN;
+    const float o2 = (ct[2] + acc[h][2]) * iN;
     const float od = (dt[h] + acc[h][4]) * iN;
     if (in) {
       v.pix_a[pix] = make_float4(o0, o1, o2, od);
@@ -698,26 +714,19 @@ __device__ __forceinline__ int fixed_e(const uint4& p, int k) {
   return (int)((w >> (8 * (k & 3))) & 0xffu) - 128;
 }
 
-// Add a (warp block, Gaussian gi) partial g to gi's fixed-point sums.  The
-// integer q = g 2^-e, rounded half away from zero, is formed from the
-// float's fields: g = +-m 2^(E - 150) with the 24-bit significand m, so
-// q = m 2^(E - 150 - e) (an exact left shift: the bound keeps it below
-// 2^62; or a right shift with rounding).  Subnormal g (below 2^-126, under
-// the smallest quantum 2^-120) adds nothing.
+// Add a (warp block, Gaussian gi) partial g to gi's fixed-point sums: the
+// integer q = g 2^-e, rounded to nearest (ties to even).  The product with
+// the power of two 2^-e (a normal float: -e in [-126, 120]) is exact while it
+// stays normal, and below 2^-126 it rounds to 0 either way; the bound keeps
+// |q| below 2^62.
 __device__ __forceinline__ void fixed_add(const ViewDev& v, uint32_t gi, const float (&g)[10]) {
   const uint4 p = __ldg(v.fixed_exp + gi);
   unsigned long long* o = reinterpret_cast<unsigned long long*>(v.grad_fixed + 10 * (size_t)gi);
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
-    const int bits = __float_as_int(g[k]);
-    const int E = (bits >> 23) & 0xff;
-    const int sh = E - 150 - fixed_e(p, k);
-    const unsigned long long m = (unsigned long long)((bits & 0x7fffff) | 0x800000);
-    unsigned long long q =
-        sh >= 0 ? m << min(sh, 63) : (sh > -25 ? (m + (1ull << (-sh - 1))) >> (-sh) : 0ull);
-    if (E == 0) q = 0ull;
-    if (bits < 0) q = 0ull - q;
-    if (q != 0ull) atomicAdd(o + k, q);
+    const float x = __fmul_rn(g[k], __int_as_float((127 - fixed_e(p, k)) << 23));
+    const long long q = __float2ll_rn(x);
+    if (q != 0) atomicAdd(o + k, (unsigned long long)q);
   }
 }
 
@@ -748,28 +757,41 @@ __global__ void __launch_bounds__(256) fixed_scale_kernel(const __grid_constant_
 
 // The views' upstream maxima (scalars[6] = hmax, scalars[7] = smax, zero on
 // entry), from the same per-pixel terms the backward stages.  Block row
-// blockIdx.y: view.
+// blockIdx.y: view; the blocks stride over the pixels, reduce in shared
+// memory and add one atomic maximum per block (one atomic per warp, all on
+// the same two words, took 19 us at 640 x 480).
 __global__ void __launch_bounds__(256) upstream_max_kernel(const __grid_constant__ ViewBatch vb,
                                                            float eps, float lambda,
                                                            const float* dloss) {
   chain_wait();
+  __shared__ float s_m[2][8];
   const ViewDev& v = vb.v[blockIdx.y];
   const long long npx = (long long)v.cam.W * v.cam.H;
-  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const float scale = loss_scale(v, v.fused, dloss);
   float hm = 0.f, sm = 0.f;
-  if (pix < npx) {
-    const float scale = loss_scale(v, v.fused, dloss);
+  for (long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x; pix < npx;
+       pix += (long long)gridDim.x * blockDim.x) {
     const float4 st = v.pix_a[pix];
     const float iN = 1.0f / (1.0f + v.pix_b[pix].x);
     const float dt = __ldg(v.Dt + pix);
     float g0, g1, g2, gD;
     upstream(v, pix, npx, st, dt, v.fused, lambda, scale, g0, g1, g2, gD);
-    hm = fmaxf(fmaxf(fabsf(g0 * iN), fabsf(g1 * iN)), fmaxf(fabsf(g2 * iN), fabsf(gD * iN)));
-    sm = fabsf((g0 * st.x + g1 * st.y + g2 * st.z + gD * st.w) * iN);
+    hm = fmaxf(hm, fmaxf(fmaxf(fabsf(g0 * iN), fabsf(g1 * iN)), fmaxf(fabsf(g2 * iN), fabsf(gD * iN))));
+    sm = fmaxf(sm, fabsf((g0 * st.x + g1 * st.y + g2 * st.z + gD * st.w) * iN));
   }
   hm = warp_max(hm);
   sm = warp_max(sm);
+  const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
+    s_m[0][w] = hm;
+    s_m[1][w] = sm;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      hm = fmaxf(hm, s_m[0][k]);
+      sm = fmaxf(sm, s_m[1][k]);
+    }
     // non-negative floats order as their bit patterns
     atomicMax(reinterpret_cast<unsigned*>(v.scalars + 6), __float_as_uint(hm));
     atomicMax(reinterpret_cast<unsigned*>(v.scalars + 7), __float_as_uint(sm));
@@ -1339,8 +1361,11 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
   const long long npx = (long long)W * H, pix = (long long)py * W + px;
   const float scale = loss_scale(v, fused, dloss);
   const uint2 r = v.tile_ranges[tile];
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, T = 1.f, thr = -INFINITY;
-  float S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
+  // P: the upstream gradient dotted with the colour and depth composited
+  // behind the current entry (T_end (C_t, D_t) at the start), so that
+  // dL/dalpha_j = (g . c_j) T_j - P / (1 - alpha_j) and P grows by
+  // (g . c_j) alpha_j T_j as the walk passes j
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, T = 1.f, thr = -INFINITY, P = 0.f;
   uint32_t mylast = r.x;
   if (inside) {
     const float4 st = v.pix_a[pix];
@@ -1350,10 +1375,8 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
     T = sb.x;
     mylast = min(max(__float_as_uint(sb.y), r.x), r.y);  // stays inside this tile's list
     thr = depth_threshold(dt, eps);
-    S0 = T * ld_col(v.Ct, pix, v.prec);
-    S1 = T * ld_col(v.Ct, npx + pix, v.prec);
-    S2 = T * ld_col(v.Ct, 2 * npx + pix, v.prec);
-    SD = T * dt;
+    P = T * (g0 * ld_col(v.Ct, pix, v.prec) + g1 * ld_col(v.Ct, npx + pix, v.prec) +
+             g2 * ld_col(v.Ct, 2 * npx + pix, v.prec) + gD * dt);
     if (g0 == 0.f && g1 == 0.f && g2 == 0.f && gD == 0.f) mylast = r.x;
   }
   const float fpx = (float)px, fpy = (float)py;
@@ -1422,19 +1445,16 @@ __global__ void __launch_bounds__(TW* TH) composite_bwd_alpha_kernel(const __gri
             const float raw = alpha_of(q, s_l2[j]);
             const bool clamped = raw > kAlphaMax;
             const float a = fminf(raw, kAlphaMax);
-            const float ia = 1.0f / (1.0f - a);
+            const float ia = rcp_approx(1.0f - a);
             const float Tj = T * ia;
             const float aT = a * Tj;
             gv[6] = g0 * aT;
             gv[7] = g1 * aT;
             gv[8] = g2 * aT;
             gv[9] = gD * aT;
-            const float dLda = g0 * (C.x * Tj - S0 * ia) + g1 * (C.y * Tj - S1 * ia) +
-                               g2 * (C.z * Tj - S2 * ia) + gD * (A.z * Tj - SD * ia);
-            S0 += C.x * aT;
-            S1 += C.y * aT;
-            S2 += C.z * aT;
-            SD += A.z * aT;
+            const float gc = g0 * C.x + g1 * C.y + g2 * C.z + gD * A.z;
+            const float dLda = gc * Tj - P * ia;
+            P = fmaf(gc, aT, P);
             T = Tj;
             if (!clamped) {
               const float vv = dLda * a;
@@ -1549,8 +1569,11 @@ __global__ void __launch_bounds__(TW* TH)
   const long long npx = (long long)W * H, pix = (long long)py * W + px;
   const float scale = loss_scale(v, fused, dloss);
   const uint2 r = v.tile_ranges[tile];
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, T = 1.f, thr = -INFINITY;
-  float S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
+  // P: the upstream gradient dotted with the colour and depth composited
+  // behind the current entry (T_end (C_t, D_t) at the start), so that
+  // dL/dalpha_j = (g . c_j) T_j - P / (1 - alpha_j) and P grows by
+  // (g . c_j) alpha_j T_j as the walk passes j
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, T = 1.f, thr = -INFINITY, P = 0.f;
   uint32_t mylast = r.x;
   if (inside) {
     const float4 st = v.pix_a[pix];
@@ -1560,10 +1583,8 @@ __global__ void __launch_bounds__(TW* TH)
     T = sb.x;
     mylast = min(max(__float_as_uint(sb.y), r.x), r.y);  // stays inside this tile's list
     thr = depth_threshold(dt, eps);
-    S0 = T * ld_col(v.Ct, pix, v.prec);
-    S1 = T * ld_col(v.Ct, npx + pix, v.prec);
-    S2 = T * ld_col(v.Ct, 2 * npx + pix, v.prec);
-    SD = T * dt;
+    P = T * (g0 * ld_col(v.Ct, pix, v.prec) + g1 * ld_col(v.Ct, npx + pix, v.prec) +
+             g2 * ld_col(v.Ct, 2 * npx + pix, v.prec) + gD * dt);
     if (g0 == 0.f && g1 == 0.f && g2 == 0.f && gD == 0.f) mylast = r.x;
   }
   s_pg[tid] = make_float4(g0, g1, g2, gD);
@@ -1598,15 +1619,12 @@ __global__ void __launch_bounds__(TW* TH)
       // the forward's alpha, bit for bit (see composite_bwd_alpha_kernel)
       const float raw = alpha_of(q, A.w);
       const float a = counted ? fminf(raw, kAlphaMax) : 0.0f;
-      const float ia = 1.0f / (1.0f - a);
+      const float ia = rcp_approx(1.0f - a);
       const float Tj = T * ia;
       const float aT = a * Tj;
-      const float dLda = g0 * (C.x * Tj - S0 * ia) + g1 * (C.y * Tj - S1 * ia) +
-                         g2 * (C.z * Tj - S2 * ia) + gD * (A.z * Tj - SD * ia);
-      S0 += C.x * aT;
-      S1 += C.y * aT;
-      S2 += C.z * aT;
-      SD += A.z * aT;
+      const float gc = g0 * C.x + g1 * C.y + g2 * C.z + gD * A.z;
+      const float dLda = gc * Tj - P * ia;
+      P = fmaf(gc, aT, P);
       T = Tj;
       const float vv = counted && !(raw > kAlphaMax) ? dLda * a : 0.0f;
       w[lane][e ^ sw] = make_float2(aT, vv);
@@ -1996,8 +2014,9 @@ cudaError_t launch_upstream_max(const ViewBatch& vb, float eps, float lambda, co
                                 cudaStream_t st) {
   int max_px = 0;
   for (int k = 0; k < vb.n; ++k) max_px = max(max_px, vb.v[k].cam.W * vb.v[k].cam.H);
-  launch_chained(upstream_max_kernel, dim3((max_px + 255) / 256, vb.n), dim3(256), 0, st, vb, eps,
-      lambda, dloss);
+  // about two blocks per SM, each striding over its view's pixels
+  const int blocks = max(1, min((max_px + 255) / 256, 296));
+  launch_chained(upstream_max_kernel, dim3(blocks, vb.n), dim3(256), 0, st, vb, eps, lambda, dloss);
   return cudaGetLastError();
 }
 

@@ -171,23 +171,30 @@ def test_projection_matches_oracle():
 
 
 # --------------------------------------------------------------- binning
-_BIN_CASES = [(tile, det, 3000) for det in (True, False)
+_BIN_CASES = [(tile, det, 3000, (150, 100)) for det in (True, False)
               for tile in ((16, 16), (16, 8), (8, 8), (32, 8))]
 # 320k and 1.3M Gaussians: 2 and 8 chunks of 256 Gaussians per binning block
-_BIN_CASES += [((16, 8), True, 320000), ((16, 8), False, 320000), ((16, 8), False, 1300000)]
+# (tile lists beyond the sort's shared buffers merge through its scratch)
+_BIN_CASES += [((16, 8), True, 320000, (150, 100)), ((16, 8), False, 320000, (150, 100)),
+               ((16, 8), False, 1300000, (150, 100))]
+# tile grids beyond the shared-memory histogram (257 x 129 tiles of 8 x 8):
+# super-tile bins, sorted and split, or split in emission order
+_BIN_CASES += [((8, 8), True, 3000, (2050, 1030)), ((8, 8), False, 3000, (2050, 1030))]
 
 
-@pytest.mark.parametrize("tile,det,M", _BIN_CASES)
-def test_binning_bit_exact(tile, det, M):
+@pytest.mark.parametrize("tile,det,M,size", _BIN_CASES)
+def test_binning_bit_exact(tile, det, M, size):
     """Identical FP32 records in, identical sorted (tile, depth, index) lists out
     (deterministic mode); the sort-free default gives every tile the same
     entries in emission order."""
-    w = workload("small", M=M, width=150, height=100)  # ragged tiles
+    w = workload("small", M=M, width=size[0], height=size[1])  # ragged tiles
     f = w.frames[0]
     rec_o, _ = oracle.project(w.gaussians.astype(np.float64), f.cam)
     r32 = oracle.records_f32(rec_o)
     keys_o, vals_o, ranges_o = oracle.bin_records(r32, f.cam.width, f.cam.height, *tile)
-    r = _renderer(w, [f.cam], stages=gps.STAGE_BIN, tile=tile, deterministic=det)
+    # the large view's Gaussians span tens of bins each: room for all entries
+    r = _renderer(w, [f.cam], stages=gps.STAGE_BIN, tile=tile, deterministic=det,
+                  pair_capacity=64 * M if size[0] > 1000 else 0)
     r.region(0, "records", torch.float32, r.M * 16).copy_(torch.from_numpy(r32.reshape(-1)).cuda())
     g = gps.Gaussians.from_numpy(w.gaussians)
     Ct, Dt = np.zeros((3, f.cam.height, f.cam.width), np.float32), np.zeros((f.cam.height, f.cam.width), np.float32)
