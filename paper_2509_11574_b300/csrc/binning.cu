@@ -287,9 +287,22 @@ __device__ __forceinline__ void merge_slice(const unsigned long long* src, int a
     else hi = mid;
   }
   int i = lo, j = d0 - lo;
+  // the two runs' next keys stay in registers, so each output costs one
+  // load; past a run's end its key reads ~0, above every real key (d > 0
+  // keeps the top bit clear) and equal only to the pads, which all hold ~0
+  // (a pad taken from either run is the same value), ties going to the
+  // second run as in the split search above
+  unsigned long long ka = i < na ? at(a0 + i) : ~0ull, kb = j < nb ? at(b0 + j) : ~0ull;
   for (int d = 0; d < cnt; ++d) {
-    const bool takeA = j >= nb || (i < na && at(a0 + i) < at(b0 + j));
-    const unsigned long long k = takeA ? at(a0 + i++) : at(b0 + j++);
+    const bool takeA = ka < kb;
+    const unsigned long long k = takeA ? ka : kb;
+    if (takeA) {
+      ++i;
+      ka = i < na ? at(a0 + i) : ~0ull;
+    } else {
+      ++j;
+      kb = j < nb ? at(b0 + j) : ~0ull;
+    }
     if (P) dst[spad(o0 + d)] = k;
     else dst[o0 + d] = k;
   }
@@ -317,12 +330,15 @@ __device__ unsigned long long* block_merge_sort(const unsigned long long* __rest
   __syncthreads();
   unsigned long long* src = buf0;
   unsigned long long* dst = buf1;
+  // merge rounds: four outputs per thread, so that twice as many threads
+  // share each round's (latency-bound) work
+  constexpr int kOut = 4;
   for (int w = 8; w < n8; w <<= 1) {
-    for (int t = tid; t * kPerThread < n8; t += T) {
-      const int d = t * kPerThread;
+    for (int t = tid; t * kOut < n8; t += T) {
+      const int d = t * kOut;
       const int p = d / (2 * w), base = p * 2 * w;
       const int na = min(w, n8 - base), nb = max(0, min(w, n8 - base - w));
-      merge_slice<true>(src, base, na, base + na, nb, d - base, kPerThread, dst, d);
+      merge_slice<true>(src, base, na, base + na, nb, d - base, kOut, dst, d);
     }
     __syncthreads();
     unsigned long long* tmp = src;
