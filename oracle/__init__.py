@@ -373,11 +373,14 @@ def bands_for(W: int, H: int, **over) -> dict:
         numbers below W + H;
       qmax 2e-7 and depth 3.5e-7 (relative): a few roundings each, the depth
         threshold D_t + eps rounded once more (2 u);
-      res_colour 1e-4 and res_depth 1e-4 (relative): the image tolerance.
+      res_colour 1e-4 and res_depth 1e-4 (relative): the image tolerance;
+      order 2.3e-7 (relative): the front-to-back blend's order of two
+        Gaussians whose depths, each within 2.3e-7 of itself, lie within
+        order (|d_a| + |d_b|) of each other can go either way.
     The record bounds these assume are asserted on the kernels' records by the
     end-to-end tests."""
     b = dict(conic=2.5e-6, mean=4.0 * U32 * (W + H), qmax=2e-7, depth=3.5e-7,
-             res_colour=1e-4, res_depth=1e-4)
+             res_colour=1e-4, res_depth=1e-4, order=2.3e-7)
     b.update(over)
     return b
 
@@ -393,7 +396,9 @@ def envelope(rec, Ct, Dt, eps, mode, Ctgt, Dtgt, lambda_depth, n_valid, JT=None,
     a conic known within `conic` of cn, a mean within `mean` px, qmax within
     `qmax` of itself), the depth test where |d - (D_t + eps)| < depth
     (D_t + eps); residual signs where |C* - C| < res_colour or
-    |D* - D| < res_depth D.  JT = None: the image and loss envelope only.
+    |D* - D| < res_depth D; in the front-to-back (ALPHA) blend the order of
+    two touched Gaussians where |d_a - d_b| < order (|d_a| + |d_b|) (both
+    orders evaluated).  JT = None: the image and loss envelope only.
     f32=True: FP32 decisions on records holding FP32 values (as `composite`
     with f32), nothing ambiguous - for the reference terms' sums s2, s2q.
     dC, dD: explicit upstream gradients in place of the L1 loss's.
@@ -412,7 +417,8 @@ def envelope(rec, Ct, Dt, eps, mode, Ctgt, Dtgt, lambda_depth, n_valid, JT=None,
     JT = np.ascontiguousarray(JT, dtype=np.float64)
     P = JT.shape[1]
     assert JT.shape == (M, P, G_N)
-    band = _f64([b["conic"], b["mean"], b["qmax"], b["depth"], b["res_colour"], b["res_depth"]])
+    band = _f64([b["conic"], b["mean"], b["qmax"], b["depth"], b["res_colour"], b["res_depth"],
+                 b.get("order", 0.0)])
     allow_img = np.zeros((3, H, W))
     allow_L = ctypes.c_double(0.0)
     n_amb = np.zeros((H, W), np.int32)

@@ -528,10 +528,29 @@ EnvPixel envelope_pixel(const EnvView& v, const Lists& L, long pix, double* allo
     }
   }
   const int k = (int)amb.size();
-  res.n_amb = k;
-  const bool too_many = k > v.kmax;
+  // front-to-back blend: the order of two touched Gaussians whose depths lie
+  // within the order band of each other, |d_a - d_b| < band (|d_a| + |d_b|),
+  // is a decision of its own (either order follows from depths within their
+  // rounding), one more bit per such pair: set, the two trade places in the
+  // depth-sorted list
+  std::vector<std::pair<int, int>> swaps;
+  if (v.mode != 0 && v.band[6] > 0.0) {
+    std::vector<std::pair<double, int>> byd;
+    for (const Item& it : fixed) byd.push_back({rec[(size_t)it.id * R_N + R_D], it.id});
+    for (const Item& it : amb) byd.push_back({rec[(size_t)it.id * R_N + R_D], it.id});
+    std::sort(byd.begin(), byd.end());
+    for (size_t a = 0; a < byd.size(); ++a)
+      for (size_t b = a + 1; b < byd.size(); ++b) {
+        if (byd[b].first - byd[a].first >= v.band[6] * (std::fabs(byd[a].first) + std::fabs(byd[b].first)))
+          break;
+        swaps.push_back({byd[a].second, byd[b].second});
+      }
+  }
+  const int kd = k + (int)swaps.size();  // decision bits: k thresholds, then the pairs
+  res.n_amb = kd;
+  const bool too_many = kd > v.kmax;
   if (too_many) res.unbounded = 1;
-  int ref_mask = 0;
+  int ref_mask = 0;  // the pairs' reference bit is 0: the FP64 order
   if (!too_many)
     for (int j = 0; j < k; ++j) ref_mask |= amb_ref[j] << j;
   const size_t nf = fixed.size(), nu = nf + (size_t)k;  // the touched Gaussians
@@ -541,7 +560,7 @@ EnvPixel envelope_pixel(const EnvView& v, const Lists& L, long pix, double* allo
   std::vector<std::array<double, G_N>> terms, tch;
   bool any_free = false;
   // with too many ambiguous decisions only the FP64 combination is evaluated
-  const int nmask = too_many ? 1 : (1 << k);
+  const int nmask = too_many ? 1 : (1 << kd);
   for (int mask = 0; mask < nmask; ++mask) {
     const int m = too_many ? ref_mask : mask;
     const bool is_ref = m == ref_mask;
@@ -577,6 +596,20 @@ EnvPixel envelope_pixel(const EnvView& v, const Lists& L, long pix, double* allo
       sl2[t] = slot[ord[t]];
       qb2[t] = qbs[ord[t]];
     }
+    // the pair decisions of this combination: swapped pairs trade places
+    if (!too_many)
+      for (size_t j = 0; j < swaps.size(); ++j) {
+        if (!((m >> (k + (int)j)) & 1)) continue;
+        size_t pa = it2.size(), pb = it2.size();
+        for (size_t t = 0; t < it2.size(); ++t) {
+          if (it2[t].id == swaps[j].first) pa = t;
+          if (it2[t].id == swaps[j].second) pb = t;
+        }
+        if (pa == it2.size() || pb == it2.size()) continue;
+        std::swap(it2[pa], it2[pb]);
+        std::swap(sl2[pa], sl2[pb]);
+        std::swap(qb2[pa], qb2[pb]);
+      }
     // C*, D* (Eq. 4, or the front-to-back variant)
     double Cs[3], Ds, Ws;
     if (v.mode == 0) {
@@ -646,7 +679,7 @@ EnvPixel envelope_pixel(const EnvView& v, const Lists& L, long pix, double* allo
         }
       }
     }
-    if (res.unbounded || (k == 0 && !any_free)) continue;
+    if (res.unbounded || (kd == 0 && !any_free)) continue;
     // each touched Gaussian's term over this combination: base (free channels
     // at 0) +- the sum over free channels of |J^T t_ch|
     double gb[4];
@@ -685,7 +718,7 @@ EnvPixel envelope_pixel(const EnvView& v, const Lists& L, long pix, double* allo
     res.aC = res.aD = res.aW = INFINITY;
     return res;
   }
-  if (k == 0 && !any_free) return res;  // one combination, fixed signs: no range
+  if (kd == 0 && !any_free) return res;  // one combination, fixed signs: no range
   const size_t r0 = (size_t)ref_mask;
   for (size_t mm = 0; mm < Dm.size(); ++mm) {
     for (int ch = 0; ch < 3; ++ch)
@@ -917,7 +950,10 @@ void orc_project_backward(int M, const double* means, const double* log_scales,
 //             band[2] of itself (the FP32 rounding of q's own products is
 //             below u cn r^2 and taken into band[0]);
 //   depth:    |d - (D_t + eps)| < band[3] (D_t + eps);
-//   colour residual |C* - C| < band[4], depth residual |D* - D| < band[5] D.
+//   colour residual |C* - C| < band[4], depth residual |D* - D| < band[5] D;
+//   mode 1 (front to back) only, the order of two touched Gaussians:
+//             |d_a - d_b| < band[6] (|d_a| + |d_b|) (a pair bit; set, the two
+//             trade places in the sorted list; the FP64 order has it clear).
 // Every other decision is taken as here.  Per pixel the envelope enumerates
 // every combination of its k ambiguous counting decisions (k <= kmax, else
 // the pixel is flagged in `unbounded`) and, per combination, lets each
@@ -931,7 +967,7 @@ void orc_project_backward(int M, const double* means, const double* log_scales,
 // the FP64 gradient, up to its own rounding.  Likewise allow_img[0][pix]
 // (max over channels), allow_img[1][pix] and allow_img[2][pix] bound
 // |C* - C*_ref|, |D* - D*_ref| and |W_G - W_G,ref|, and *allow_loss the loss.
-// Also returned: n_amb[pix] (ambiguous counting decisions), g2ref (the 2D
+// Also returned: n_amb[pix] (ambiguous decisions, order pairs included), g2ref (the 2D
 // gradient of the FP64 decisions, the sum of pixel_adjoint terms in row-major
 // pixel order, as orc_composite_backward), s2[i][c] = sum over pixels of
 // |term| and s2q[i][c] = sum over pixels of |term| * qband / 2 (alpha's
@@ -950,7 +986,7 @@ int orc_envelope(int M, const double* rec, int W, int H, const double* Ct, const
                  double* allow3, double* g2ref, double* s2, double* s2q) {
   Lists L = build_lists(M, rec, W, H, 0, 0, W - 1, 0, H - 1);
   const long npx = (long)W * H;
-  const double no_band[6] = {0, 0, 0, 0, 0, 0};
+  const double no_band[7] = {0, 0, 0, 0, 0, 0, 0};
   if (f32) band = no_band;
   EnvView v{M, W, H, mode, P, kmax, f32, rec, Ct, Dt, Ctgt, Dtgt, band, JT, eps,
             n_valid > 0 ? 1.0 / (3.0 * (double)n_valid) : 0.0,

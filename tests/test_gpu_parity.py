@@ -444,6 +444,15 @@ def test_end_to_end_room_bench_configuration_deterministic():
     _end_to_end(w, oracle.OIT, w.lambda_depth, tile=(16, 8), deterministic=True)
 
 
+def test_end_to_end_room_bench_configuration_alpha():
+    """The bench's `--mode alpha` form at full size: depth-sorted lists, the
+    front-to-back blend over C_t and its reverse-walk backward (carry groups
+    of 16 entries), against the oracle's ALPHA reading with the same
+    envelopes."""
+    w = workloads.room(n_frames=1, M=100_000)
+    _end_to_end(w, oracle.ALPHA, w.lambda_depth, tile=(16, 8))
+
+
 def test_deterministic_mode_is_bitwise_reproducible_and_matches():
     w = workload("small")
     f = w.frames[0]

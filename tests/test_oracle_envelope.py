@@ -129,6 +129,45 @@ def test_free_residual_sign_at_one_pixel():
     assert np.all(env["allow_C"] == 0) and env["allow_L"] == 0.0
 
 
+@pytest.mark.parametrize("gap", [1e-7, 1e-5])
+def test_alpha_order_of_two_gaussians_at_equal_depth(gap):
+    """Two concentric Gaussians whose depths differ by `gap` of themselves: in
+    the front-to-back blend, within the order band (2.3e-7 of each depth) the
+    two orders are both FP32 outcomes, and at a pixel where both count they
+    differ by alpha_a alpha_b (c_a - c_b) in C* (a then b: c_a a_a + c_b a_b
+    (1 - a_a); b then a: c_b a_b + c_a a_a (1 - a_b); the rest, T_end C_t,
+    is the same).  Outside the band, and in the order-independent blend,
+    nothing is ambiguous."""
+    v, d = 1.5, 0.9
+    sa, sb = 0.5, 0.4
+    ca, cb = np.array([0.9, 0.1, 0.3]), np.array([0.2, 0.8, 0.35])
+    ra = record(4.0, 4.0, d, sa, 1 / v, 0.0, 1 / v, 2 * math.log(255 * sa), rgb=ca)
+    rb = record(4.0, 4.0, d * (1 + gap), sb, 1 / v, 0.0, 1 / v, 2 * math.log(255 * sb), rgb=cb)
+    rec = np.concatenate([ra, rb])
+    Ct, Dt, Ctg, Dtg = images(Dt=2.0)
+    ys, xs = np.mgrid[0:H9, 0:W9]
+    q = ((xs - 4.0) ** 2 + (ys - 4.0) ** 2) / v
+    both = q <= 2 * math.log(255 * sb)  # b's support lies inside a's
+    assert np.all(np.abs(q - 2 * math.log(255 * sb)) > 1e-3)
+    assert np.all(np.abs(q - 2 * math.log(255 * sa)) > 1e-3)
+    env = oracle.envelope(rec, Ct, Dt, 0.01, oracle.ALPHA, Ctg, Dtg, 0.0, NPX)
+    env_oit = oracle.envelope(rec, Ct, Dt, 0.01, oracle.OIT, Ctg, Dtg, 0.0, NPX)
+    assert env_oit["n_amb"].sum() == 0 and np.all(env_oit["allow_C"] == 0)
+    assert env["unbounded"].sum() == 0
+    if gap > 2 * 2.3e-7:
+        assert env["n_amb"].sum() == 0 and np.all(env["allow_C"] == 0)
+        return
+    np.testing.assert_array_equal(env["n_amb"] > 0, both)
+    aa, ab = sa * np.exp(-0.5 * q), sb * np.exp(-0.5 * q)
+    want = aa * ab * np.max(np.abs(ca - cb))
+    np.testing.assert_allclose(env["allow_C"][both], want[both], rtol=1e-12)
+    # D* moves by alpha_a alpha_b (d_b - d_a): a difference of two sums near
+    # 1, known to their rounding
+    np.testing.assert_allclose(env["allow_D"][both], (aa * ab * d * gap)[both], rtol=0, atol=1e-15)
+    assert np.all(env["allow_W"] <= 1e-15)  # 1 - T_end does not depend on the order
+    assert np.all(env["allow_C"][~both] == 0)
+
+
 def _scene(lam=1.0):
     w = workloads.small(M=600, width=64, height=48)
     f = w.frames[0]
@@ -177,7 +216,9 @@ def test_every_flipped_combination_lies_inside_the_envelope(mode):
     w, f, Ct, Dt, lam = _scene()
     g64 = w.gaussians.astype(np.float64)
     H, W = Dt.shape
-    bands = {k: v * (200.0 if k not in ("res_colour", "res_depth") else 1.0)
+    # the order band stays at its FP32 size: the seeded flips below invert
+    # counting decisions and residual signs only
+    bands = {k: v * (200.0 if k not in ("res_colour", "res_depth", "order") else 1.0)
              for k, v in oracle.bands_for(W, H).items()}
     ref = oracle.render_loss_grads(g64, f.cam, Ct, Dt, f.rgb, f.depth, eps=w.eps_depth,
                                    lambda_depth=lam, mode=mode)
