@@ -161,7 +161,8 @@ __device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float a, 
 }
 
 // ------------------------------------------------------------------ forward
-// Warp w covers the 8 x 4 pixel block (w % (TW/8), w / (TW/8)) of the tile.
+// (the backward kernels' layout) Warp w covers the 8 x 4 pixel block
+// (w % (TW/8), w / (TW/8)) of the tile, lane l its pixel (l % 8, l / 8).
 template <int TW>
 __device__ __forceinline__ void warp_block(int warp, int lane, int& ox, int& oy, int& lx, int& ly) {
   constexpr int BX = TW / 8;
@@ -171,204 +172,16 @@ __device__ __forceinline__ void warp_block(int warp, int lane, int& ox, int& oy,
   ly = oy + (lane >> 3);
 }
 
-template <int TW, int TH, int MODE, bool INSTR>
-__global__ void __launch_bounds__(TW* TH) composite_fwd_kernel(const __grid_constant__ ViewBatch vb,
-                                                              float eps, int has_tgt) {
-  chain_wait();
-  constexpr int NT = TW * TH;
-  constexpr int NW = NT / 32;
-  __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
-  __shared__ float2 s_e[NT];
-  __shared__ uint8_t s_list[NW][NT];
-  __shared__ float s_tmp[NW * 3];
-  const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
-  const ViewDev& v = vb.v[vb.order[slot]];
-  const int tile = tile_of(v, blockIdx.x - vb.tile_start[slot]);
-  const int W = v.cam.W, H = v.cam.H;
-  const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int ox, oy, lx, ly;
-  warp_block<TW>(warp, lane, ox, oy, lx, ly);
-  const int px = tx * TW + lx, py = ty * TH + ly;
-  const bool inside = px < W && py < H;
-  const long long npx = (long long)W * H, pix = (long long)py * W + px;
-  float ct0 = 0.f, ct1 = 0.f, ct2 = 0.f, dt = 0.f;
-  if (inside) {
-    ct0 = ld_col(v.Ct, pix, v.prec);
-    ct1 = ld_col(v.Ct, npx + pix, v.prec);
-    ct2 = ld_col(v.Ct, 2 * npx + pix, v.prec);
-    dt = __ldg(v.Dt + pix);
-  }
-  const float thr = inside ? depth_threshold(dt, eps) : -INFINITY;
-  const uint2 r = v.tile_ranges[tile];
-  // the first batch's key is fetched before the cut is known (it lies in the list)
-  uint32_t gi_next = r.x + tid < r.y ? (uint32_t)v.keys[r.x + tid] : 0u;
-  const float wthr = warp_max(thr);
-  const float bthr = block_max<NT>(thr, s_tmp);
-  const uint32_t end = depth_cut_block<NT>(v.keys, r.x, r.y, bthr);
-  // this warp's pixel block, in image coordinates
-  const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
-  const float by0 = (float)(ty * TH + oy), by1 = by0 + 3.0f;
-  const float fpx = (float)px, fpy = (float)py;
-  float cr = 0.f, cg = 0.f, cb = 0.f, wsum = 0.f, zsum = 0.f, T = 1.0f;
-  uint32_t last = r.x;
-  bool done = !inside;
-  bool wdone = wthr == -INFINITY;  // warp-uniform: nothing left for this warp
-  unsigned n_tested = 0, n_counted = 0;
-  for (uint32_t b = r.x; b < end; b += NT) {
-    __syncthreads();
-    if (__syncthreads_and(MODE == GPS_BLEND_ALPHA ? (done || wdone) : wdone)) break;
-    const uint32_t k = b + tid;
-    const uint32_t gi = gi_next;
-    // next batch's key, in flight while this batch is staged and evaluated
-    gi_next = k + NT < r.y ? (uint32_t)v.keys[k + NT] : 0u;
-    if (k < end) {
-      const float4* rr = v.rec + 4 * (size_t)gi;
-      float4 A = rr[0], B = rr[1];
-      const float4 C = rr[2];
-      A.w = __log2f(A.w);  // log2 sigma, see alpha_of
-      B.y = 2.0f * B.y;  // 2 b, exact
-      s_a[tid] = A;
-      s_b[tid] = B;
-      s_c[tid] = C;
-      s_e[tid] = make_float2(C.w, rr[3].x);
-    }
-    __syncthreads();
-    const int nb = (int)min((uint32_t)NT, end - b);
-    // warp-parallel culling of the batch against this warp's block, in depth
-    // order, stopping at the first Gaussian at or behind the warp's threshold
-    int cnt = 0;
-    if (!wdone) {
-      for (int j0 = 0; j0 < nb; j0 += 32) {
-        const int j = j0 + lane;
-        bool stop = false, ok = false;
-        if (j < nb) {
-          const float4 A = s_a[j];
-          const float2 E = s_e[j];
-          stop = A.z >= wthr;
-          ok = A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 && A.y - E.y <= by1;
-          if (ok) {
-            const float4 B = s_b[j];
-            ok = ellipse_meets_rect(A.x, A.y, B.x, 0.5f * B.y, B.z, B.w, bx0, bx1, by0, by1);
-          }
-        }
-        const unsigned sb = __ballot_sync(0xffffffffu, stop);
-        unsigned ob = __ballot_sync(0xffffffffu, ok);
-        if (sb) ob &= (sb & (0u - sb)) - 1u;  // keep the entries before the first stop
-        if ((ob >> lane) & 1u) s_list[warp][cnt + __popc(ob & ((1u << lane) - 1u))] = (uint8_t)j;
-        cnt += __popc(ob);
-        if (sb) {
-          wdone = true;
-          break;
-        }
-      }
-    }
-    __syncwarp();
-    for (int t = 0; t < cnt; ++t) {
-      const int j = s_list[warp][t];
-      const float4 A = s_a[j], B = s_b[j];
-      const float q = quad_form(B.x, B.y, B.z, __fsub_rn(fpx, A.x), __fsub_rn(fpy, A.y));
-      if (INSTR) n_tested += inside;
-      const bool counted = q <= B.w && A.z < thr;
-      if (MODE == GPS_BLEND_OIT) {
-        // branch-free: a pixel that does not count adds alpha = 0 (exactly
-        // the same sums), and the warp never splits on the decision
-        if (INSTR) n_counted += counted;
-        const float al = counted ? alpha_of(q, A.w) : 0.0f;
-        const float4 C = s_c[j];
-        cr = fmaf(al, C.x, cr);
-        cg = fmaf(al, C.y, cg);
-        cb = fmaf(al, C.z, cb);
-        wsum += al;
-        zsum = fmaf(al, A.z, zsum);
-      } else if (counted) {
-        if (INSTR) ++n_counted;
-        const float al = alpha_of(q, A.w);
-        const float4 C = s_c[j];
-        if (!done) {
-          const float a = fminf(al, kAlphaMax);
-          const float test = T * (1.0f - a);
-          if (test < kTMin) {
-            done = true;
-          } else {
-            const float aT = a * T;
-            cr += C.x * aT;
-            cg += C.y * aT;
-            cb += C.z * aT;
-            zsum += A.z * aT;
-            T = test;
-            last = b + j + 1;
-          }
-        }
-      }
-    }
-  }
-  if (INSTR) add_counters(v, 0, n_tested, n_counted);
-  float o0, o1, o2, od, ow;
-  if (MODE == GPS_BLEND_OIT) {
-    const float iN = 1.0f / (1.0f + wsum);
-    o0 = (ct0 + cr) * iN;
-    o1 = (ct1 + cg) * iN;
-    o2 = (ct2 + cb) * iN;
-    od = (dt + zsum) * iN;
-    ow = wsum;
-  } else {
-    o0 = cr + T * ct0;
-    o1 = cg + T * ct1;
-    o2 = cb + T * ct2;
-    od = zsum + T * dt;
-    ow = 1.0f - T;
-  }
-  if (inside) {
-    v.pix_a[pix] = make_float4(o0, o1, o2, od);
-    v.pix_b[pix] = make_float4(MODE == GPS_BLEND_OIT ? wsum : T, __uint_as_float(last), 0.f, 0.f);
-    if (v.out_rgb) {
-      st_col(v.out_rgb, pix, v.prec, o0);
-      st_col(v.out_rgb, npx + pix, v.prec, o1);
-      st_col(v.out_rgb, 2 * npx + pix, v.prec, o2);
-    }
-    if (v.out_depth) v.out_depth[pix] = od;
-    if (v.out_weight) v.out_weight[pix] = ow;
-  }
-  if (has_tgt) {
-    float lr = 0.f, ld = 0.f, nv = 0.f;
-    if (inside) {
-      const float dk = __ldg(v.Dtgt + pix);
-      if (dk > 0.0f && dt > 0.0f) {
-        lr = fabsf(o0 - ld_col(v.Ctgt, pix, v.prec)) + fabsf(o1 - ld_col(v.Ctgt, npx + pix, v.prec)) +
-             fabsf(o2 - ld_col(v.Ctgt, 2 * npx + pix, v.prec));
-        ld = fabsf(od - dk);
-        nv = 1.0f;
-      }
-    }
-    lr = warp_sum(lr);
-    ld = warp_sum(ld);
-    nv = warp_sum(nv);
-    __syncthreads();
-    if (lane == 0) {
-      s_tmp[warp * 3 + 0] = lr;
-      s_tmp[warp * 3 + 1] = ld;
-      s_tmp[warp * 3 + 2] = nv;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      float a = 0.f, bsum = 0.f, c = 0.f;
-      for (int k = 0; k < NW; ++k) {
-        a += s_tmp[k * 3];
-        bsum += s_tmp[k * 3 + 1];
-        c += s_tmp[k * 3 + 2];
-      }
-      v.tile_partials[tile] = make_float4(a, bsum, c, 0.f);
-    }
-  }
-}
-
-// OIT forward with two pixels per lane: warp w covers the 8 x 8 pixel block
-// (w % (TW/8), w / (TW/8)) of the tile, lane l the pixels (2 (l % 4), l / 4)
-// and (2 (l % 4) + 1, l / 4) of it.  Each staged record is read once for both
-// pixels, which share the dy terms of q.  Otherwise as composite_fwd_kernel
-// (same decisions, same per-pixel summation order, so the same images bit
-// for bit).
+// OIT forward (Eq. 1-4) with two pixels per lane.  One CTA per tile; warp w
+// covers the 8 x 8 pixel block (w % (TW/8), w / (TW/8)) of the tile, lane l
+// the pixels (2 (l % 4), l / 4) and (2 (l % 4) + 1, l / 4) of it.  Per batch
+// of staged records each warp compacts, 32 at a time with ballots, the
+// Gaussians whose conservative rectangle meets its block and that lie in
+// front of its largest depth threshold, then walks them with broadcast
+// reads.  Each staged record is read once for both pixels of a lane, which
+// share the dy terms of q.  Branch-free: a pixel where a Gaussian does not
+// count adds alpha = 0 (exactly the same sums), so the warp never splits on
+// the decision.
 template <int TW, int TH, bool INSTR>
 __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
     const __grid_constant__ ViewBatch vb, float eps, int has_tgt, int sorted) {
@@ -523,6 +336,205 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
       }
       if (v.out_depth) v.out_depth[pix] = od;
       if (v.out_weight) v.out_weight[pix] = acc[h][3];
+      if (has_tgt) {
+        const float dk = __ldg(v.Dtgt + pix);
+        if (dk > 0.0f && dt[h] > 0.0f) {
+          lr += fabsf(o0 - ld_col(v.Ctgt, pix, v.prec)) +
+                fabsf(o1 - ld_col(v.Ctgt, npx + pix, v.prec)) +
+                fabsf(o2 - ld_col(v.Ctgt, 2 * npx + pix, v.prec));
+          ld += fabsf(od - dk);
+          nv += 1.0f;
+        }
+      }
+    }
+  }
+  if (has_tgt) {
+    lr = warp_sum(lr);
+    ld = warp_sum(ld);
+    nv = warp_sum(nv);
+    __syncthreads();
+    if (lane == 0) {
+      s_tmp[warp * 3 + 0] = lr;
+      s_tmp[warp * 3 + 1] = ld;
+      s_tmp[warp * 3 + 2] = nv;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float a = 0.f, bsum = 0.f, c = 0.f;
+      for (int k = 0; k < NW; ++k) {
+        a += s_tmp[k * 3];
+        bsum += s_tmp[k * 3 + 1];
+        c += s_tmp[k * 3 + 2];
+      }
+      v.tile_partials[tile] = make_float4(a, bsum, c, 0.f);
+    }
+  }
+}
+
+// The "with sort" forward (Table 7 reading: front to back, alpha clamped
+// to 0.99, a pixel stops before T (1 - alpha) < 1e-4, C* = sum c alpha T +
+// T_end C_t) with two pixels per lane, laid out as in composite_fwd_oit2_kernel
+// (warp w the 8 x 8 block, lane (c, r) the pixels (2c, r), (2c + 1, r)).  The
+// blend is branch-free: an entry that does not count, or reaches a finished
+// pixel, or would end it, adds alpha T = 0 and leaves T as it is, so each
+// pixel takes exactly the steps of the sequential blend (its T_end and last
+// entry are what the backward's reverse walk starts from).
+template <int TW, int TH, bool INSTR>
+__global__ void __launch_bounds__(TW* TH / 2) composite_fwd_alpha2_kernel(
+    const __grid_constant__ ViewBatch vb, float eps, int has_tgt) {
+  chain_wait();
+  constexpr int NTT = TW * TH / 2;  // threads
+  constexpr int NW = NTT / 32;
+  constexpr int NB = 2 * NTT;       // staged entries per batch
+  constexpr int BX = TW / 8;
+  __shared__ float4 s_a[NB], s_b[NB], s_c[NB];
+  __shared__ float2 s_e[NB];
+  __shared__ uint8_t s_list[NW][NB];
+  __shared__ float s_tmp[NW * 3];
+  const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
+  const ViewDev& v = vb.v[vb.order[slot]];
+  const int tile = tile_of(v, blockIdx.x - vb.tile_start[slot]);
+  const int W = v.cam.W, H = v.cam.H;
+  const int tx = tile % v.tiles_x, ty = tile / v.tiles_x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ox = (warp % BX) * 8, oy = (warp / BX) * 8;
+  const int px0 = tx * TW + ox + 2 * (lane & 3), px1 = px0 + 1;
+  const int py = ty * TH + oy + (lane >> 2);
+  const bool in0 = px0 < W && py < H, in1 = px1 < W && py < H;
+  const long long npx = (long long)W * H;
+  const long long pix0 = (long long)py * W + px0, pix1 = pix0 + 1;
+  float dt[2] = {0.f, 0.f};
+  if (in0) dt[0] = __ldg(v.Dt + pix0);
+  if (in1) dt[1] = __ldg(v.Dt + pix1);
+  const float thr0 = in0 ? depth_threshold(dt[0], eps) : -INFINITY;
+  const float thr1 = in1 ? depth_threshold(dt[1], eps) : -INFINITY;
+  const uint2 r = v.tile_ranges[tile];
+  uint32_t gi_next0 = r.x + tid < r.y ? (uint32_t)v.keys[r.x + tid] : 0u;
+  uint32_t gi_next1 = r.x + NTT + tid < r.y ? (uint32_t)v.keys[r.x + NTT + tid] : 0u;
+  const float wthr = warp_max(fmaxf(thr0, thr1));
+  const float bthr = block_max<NTT>(fmaxf(thr0, thr1), s_tmp);
+  // the lists are depth-sorted: they end at the first Gaussian behind every
+  // pixel of the tile
+  const uint32_t end = depth_cut_block<NTT>(v.keys, r.x, r.y, bthr);
+  const float bx0 = (float)(tx * TW + ox), bx1 = bx0 + 7.0f;
+  const float by0 = (float)(ty * TH + oy), by1 = by0 + 7.0f;
+  const float fpx0 = (float)px0, fpx1 = (float)px1, fpy = (float)py;
+  float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};  // r, g, b, depth
+  float T[2] = {1.0f, 1.0f};
+  uint32_t last[2] = {r.x, r.x};
+  bool done0 = !in0, done1 = !in1;
+  bool wdone = wthr == -INFINITY;
+  unsigned n_tested = 0, n_counted = 0;
+  for (uint32_t b = r.x; b < end; b += NB) {
+    __syncthreads();
+    wdone = wdone || __all_sync(0xffffffffu, done0 && done1);
+    if (__syncthreads_and(wdone)) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t k = b + h * NTT + tid;
+      const uint32_t gi = h ? gi_next1 : gi_next0;
+      const uint32_t kn = k + NB;
+      const uint32_t nxt = kn < r.y ? (uint32_t)v.keys[kn] : 0u;
+      if (h) gi_next1 = nxt; else gi_next0 = nxt;
+      if (k < end) {
+        const float4* rr = v.rec + 4 * (size_t)gi;
+        float4 A = rr[0], B = rr[1];
+        const float4 C = rr[2];
+        A.w = __log2f(A.w);  // log2 sigma, see alpha_of
+        B.y = 2.0f * B.y;    // 2 b, exact
+        const int e = h * NTT + tid;
+        s_a[e] = A;
+        s_b[e] = B;
+        s_c[e] = C;
+        s_e[e] = make_float2(C.w, rr[3].x);
+      }
+    }
+    __syncthreads();
+    const int nb = (int)min((uint32_t)NB, end - b);
+    int cnt = 0;
+    if (!wdone) {
+      for (int j0 = 0; j0 < nb; j0 += 32) {
+        const int j = j0 + lane;
+        bool stop = false, ok = false;
+        if (j < nb) {
+          const float4 A = s_a[j];
+          const float2 E = s_e[j];
+          stop = A.z >= wthr;
+          ok = A.x + E.x >= bx0 && A.x - E.x <= bx1 && A.y + E.y >= by0 && A.y - E.y <= by1;
+          if (ok) {
+            const float4 B = s_b[j];
+            ok = ellipse_meets_rect(A.x, A.y, B.x, 0.5f * B.y, B.z, B.w, bx0, bx1, by0, by1);
+          }
+        }
+        const unsigned sb = __ballot_sync(0xffffffffu, stop);
+        unsigned ob = __ballot_sync(0xffffffffu, ok);
+        if (sb) ob &= (sb & (0u - sb)) - 1u;  // keep the entries before the first stop
+        if ((ob >> lane) & 1u) s_list[warp][cnt + __popc(ob & ((1u << lane) - 1u))] = (uint8_t)j;
+        cnt += __popc(ob);
+        if (sb) {
+          wdone = true;
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    for (int t = 0; t < cnt; ++t) {
+      const int j = s_list[warp][t];
+      const float4 A = s_a[j], B = s_b[j];
+      const float4 C = s_c[j];
+      const float dy = __fsub_rn(fpy, A.y);
+      const float t1 = __fmul_rn(B.y, dy);
+      const float s3 = __fmul_rn(__fmul_rn(B.z, dy), dy);
+      const float dx0 = __fsub_rn(fpx0, A.x), dx1 = __fsub_rn(fpx1, A.x);
+      const float q0 = __fmaf_rn(dx0, __fmaf_rn(B.x, dx0, t1), s3);
+      const float q1 = __fmaf_rn(dx1, __fmaf_rn(B.x, dx1, t1), s3);
+      const bool c0 = q0 <= B.w && A.z < thr0, c1 = q1 <= B.w && A.z < thr1;
+      if (INSTR) {
+        n_tested += in0 + in1;
+        n_counted += c0 + c1;
+      }
+      const uint32_t idx = b + (uint32_t)j + 1u;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool live = (h ? c1 : c0) && !(h ? done1 : done0);
+        const float a = live ? fminf(alpha_of(h ? q1 : q0, A.w), kAlphaMax) : 0.0f;
+        const float test = T[h] * (1.0f - a);
+        const bool stop = live && test < kTMin;
+        if (h) done1 = done1 || stop; else done0 = done0 || stop;
+        const float aT = stop ? 0.0f : a * T[h];
+        acc[h][0] = fmaf(C.x, aT, acc[h][0]);
+        acc[h][1] = fmaf(C.y, aT, acc[h][1]);
+        acc[h][2] = fmaf(C.z, aT, acc[h][2]);
+        acc[h][3] = fmaf(A.z, aT, acc[h][3]);
+        const bool step = live && !stop;
+        T[h] = step ? test : T[h];
+        last[h] = step ? idx : last[h];
+      }
+    }
+  }
+  if (INSTR) add_counters(v, 0, n_tested, n_counted);
+  float lr = 0.f, ld = 0.f, nv = 0.f;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const bool in = h ? in1 : in0;
+    const long long pix = h ? pix1 : pix0;
+    float ct[3] = {0.f, 0.f, 0.f};
+    if (in)
+      for (int c = 0; c < 3; ++c) ct[c] = ld_col(v.Ct, c * npx + pix, v.prec);
+    const float o0 = acc[h][0] + T[h] * ct[0];
+    const float o1 = acc[h][1] + T[h] * ct[1];
+    const float o2 = acc[h][2] + T[h] * ct[2];
+    const float od = acc[h][3] + T[h] * dt[h];
+    if (in) {
+      v.pix_a[pix] = make_float4(o0, o1, o2, od);
+      v.pix_b[pix] = make_float4(T[h], __uint_as_float(last[h]), 0.f, 0.f);
+      if (v.out_rgb) {
+        st_col(v.out_rgb, pix, v.prec, o0);
+        st_col(v.out_rgb, npx + pix, v.prec, o1);
+        st_col(v.out_rgb, 2 * npx + pix, v.prec, o2);
+      }
+      if (v.out_depth) v.out_depth[pix] = od;
+      if (v.out_weight) v.out_weight[pix] = 1.0f - T[h];
       if (has_tgt) {
         const float dk = __ldg(v.Dtgt + pix);
         if (dk > 0.0f && dt[h] > 0.0f) {
@@ -1941,10 +1953,10 @@ static cudaError_t fwd_tw(const ViewBatch& vb, float eps, int mode, int has_tgt,
           vb, eps, has_tgt, sorted);
   } else {
     if (instr)
-      launch_chained(composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, true>, dim3(items), dim3(TW * TH), 0, st,
+      launch_chained(composite_fwd_alpha2_kernel<TW, TH, true>, dim3(items), dim3(TW * TH / 2), 0, st,
           vb, eps, has_tgt);
     else
-      launch_chained(composite_fwd_kernel<TW, TH, GPS_BLEND_ALPHA, false>, dim3(items), dim3(TW * TH), 0, st,
+      launch_chained(composite_fwd_alpha2_kernel<TW, TH, false>, dim3(items), dim3(TW * TH / 2), 0, st,
           vb, eps, has_tgt);
   }
   return cudaGetLastError();
