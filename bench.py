@@ -711,24 +711,54 @@ def run_ours(args, rank, world, local):
             if pipe.frames[k][2] is not pipe.frames[k][1]:
                 hk.append(pipe.frames[k][2].cpu().pin_memory())
             host.append(hk)
-        loss_host = torch.zeros(ITERS_PER_FRAME, pin_memory=True)
+        loss_host = torch.zeros(Wu + K, ITERS_PER_FRAME, pin_memory=True)
         pipe.reset()
         torch.cuda.synchronize()
-        e2e_ms = []
+        # Pipelined as a streaming caller would run it: step i's timed region
+        # (e0 -> e1 on the compute stream) runs frame k's graph and, on a copy
+        # stream that starts after e0, the host -> device copy of the next
+        # frame's inputs; the step ends (e1) only once that copy and the
+        # device -> host read of its losses are done, so every copy lies
+        # inside a timed region.  Frame 0's inputs are copied before the first
+        # (warm-up) step.  A frame's buffers are overwritten only after every
+        # earlier step on the compute stream (the copy stream waits on e0).
+        cs = torch.cuda.Stream()
+        main = torch.cuda.current_stream()
+
+        def copy_in(k, after=None):
+            with torch.cuda.stream(cs):
+                if after is not None:
+                    cs.wait_event(after)
+                for dst, src in zip(pipe.frames[k], host[k]):
+                    dst.copy_(src, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(cs)
+            return ev
+
+        ready = copy_in(0)
+        e2e_ev = []
         for i in range(Wu + K):
-            k = i % nF
-            flush.zero_()
+            k, kn = i % nF, (i + 1) % nF
+            flush.zero_()  # untimed, between steps
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            for dst, src in zip(pipe.frames[k], host[k]):
-                dst.copy_(src, non_blocking=True)
+            main.wait_event(ready)
+            if kn != k:
+                ready_next = copy_in(kn, after=e0)
             pipe.graphs[k].replay()
-            loss_host.copy_(pipe.loss, non_blocking=True)
+            loss_host[i].copy_(pipe.loss, non_blocking=True)
+            if kn == k:  # one frame: its inputs are rewritten after its graph ran
+                done = torch.cuda.Event()
+                done.record(main)
+                ready_next = copy_in(kn, after=done)
+            main.wait_event(ready_next)
             e1.record()
-            e1.synchronize()
+            ready = ready_next
             if i >= Wu:
-                e2e_ms.append(e0.elapsed_time(e1))
+                e2e_ev.append((e0, e1))
+        torch.cuda.synchronize()
+        e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
         h2d = sum(t.numel() * t.element_size() for t in host[0])
         e2e_s = max_over_ranks([sum(e2e_ms) / 1e3], world, dev)[0]
         e2e = {"value": whole_job_rate(ITERS_PER_FRAME * K, e2e_s, world), "unit": "iterations/s",
