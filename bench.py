@@ -380,6 +380,7 @@ class GpuPipeline:
 
 
 TILE_BIN_MAX = 16384  # tiles per view that the binning histogram holds in shared memory
+FIXED_BINS_MAX = 6144  # tiles per view of the fixed-order (deterministic OIT) emission
 
 
 def batched_speedup(dev, K, Wu, tile, precision="bf16"):
@@ -549,21 +550,24 @@ def kernels_per_step(mode, tile, schedule="tiles", deterministic=False, fused=Tr
     # lists are depth-sorted, or where a view's tile grid exceeds what the
     # binning histogram holds (then the unsorted lists go through super-tiles
     # and a split)], composite, finalize, composite_bwd [deterministic: + the
-    # upstream maxima, the fixed-point exponents and the conversion (OIT), or
-    # the pair-slot placement and gather (alpha); per-Gaussian schedule: pixel terms +
-    # per-Gaussian], projection adjoint + Adam (fused: one kernel, else two),
-    # step counter
+    # upstream maxima, the fixed-point exponents and the conversion (OIT; its
+    # fixed-order lists add the block prefix where the tile grid allows, else
+    # they are depth-sorted), or the pair-slot placement and gather (alpha);
+    # per-Gaussian schedule: pixel terms + per-Gaussian], projection adjoint +
+    # Adam (fused: one kernel, else two), step counter
     tiles = schedule != "per-gaussian"
     n_tiles = -(-size[0] // tile[0]) * -(-size[1] // tile[1])
-    sorted_lists = tiles and (mode == "alpha" or deterministic)
+    fixed_order = tiles and deterministic and mode == "oit" and n_tiles <= FIXED_BINS_MAX
+    sorted_lists = tiles and (mode == "alpha" or (deterministic and not fixed_order))
     split = 1 if sorted_lists or n_tiles > TILE_BIN_MAX else 0
+    prefix = 1 if fixed_order else 0
     if not tiles:
         extra = 1
     elif deterministic:
         extra = 3 if mode == "oit" else 2
     else:
         extra = 0
-    return 2 + ITERS_PER_FRAME * (8 + split + extra + (0 if fused else 1))
+    return 2 + ITERS_PER_FRAME * (8 + split + prefix + extra + (0 if fused else 1))
 
 
 def count_evaluations(pipe, k):

@@ -77,7 +77,7 @@ extern "C" {
 #define GPS_PREC_BF16 2
 
 /* work schedule of the second pass (GpsRenderSettings.schedule) */
-#define GPS_SCHEDULE_TILES 0        /* depth-sorted tile lists; tile-parallel backward      */
+#define GPS_SCHEDULE_TILES 0        /* tile lists; tile-parallel backward                    */
 #define GPS_SCHEDULE_PER_GAUSSIAN 1 /* OIT only, the paper's sort-free form (Sec. 3.1,
                                        App. B): unsorted tile lists for the forward (no
                                        depth cut), and a backward with one warp per
@@ -173,9 +173,12 @@ typedef struct GpsRenderSettings {
   int32_t precision;     /* GPS_PREC_*: element type of the colour images      */
   int32_t tile_w, tile_h;/* pixels per tile; 0, 0 = 16 x 8; supported: 16x16,
                             16x8, 8x8, 32x8 (gps_autotune_tiles picks one)   */
-  int32_t deterministic; /* 1: bitwise reproducible: tile lists sorted by
-                            (depth, index); gradient sums in 64-bit fixed
-                            point (OIT) or in fixed order (alpha), no float
+  int32_t deterministic; /* 1: bitwise reproducible, also across batching of
+                            views: OIT tile lists in ascending Gaussian index
+                            (fixed-order emission, views of <= 6144 tiles)
+                            or sorted by (depth, index) (larger views, and the
+                            alpha blend); gradient sums in 64-bit fixed point
+                            (OIT) or in fixed order (alpha), no float
                             atomics.  0 (OIT): lists in emission order, which
                             may change the last bits of C* run to run         */
   int32_t stages;        /* GPS_STAGE_* mask, 0 = all                          */
@@ -202,18 +205,23 @@ typedef struct GpsAdamHyper {
  * with q = a dx^2 + 2 b dx dy + c dy^2, support {q <= qmax}, qmax =
  * 2 ln(255 sigma), and a conservative half-extent ext (ext_x < 0: culled).
  * Binning buckets Gaussians into bins with a per-bin histogram, a scan and an
- * emission.  Where the lists are depth-sorted (blend ALPHA or deterministic)
- * the bins are super-tiles of super_px x super_px pixels: each segment is
- * sorted, then split into its tiles (when a tile is a whole super-tile its
- * list is the segment itself: tile_ranges == super_ranges and pair_keys ==
- * super_keys).  Otherwise (tile_bins = 1, super_px = 0) the bins are the tiles
- * themselves (super_x = tiles_x, super_y = tiles_y) and the emission writes
- * the tile lists directly: tile_ranges == super_ranges, pair_keys ==
- * super_keys == super_scratch; this needs tiles_x * tiles_y <= 16384 in every
- * view, else the super-tile path is taken.  Tile lists: keys u64 =
- * bits(d) << 32 | index, sorted ascending where depth-sorted, else in
- * emission order; tile t's list is pair_keys[tile_ranges[t][0] ..
- * tile_ranges[t][1]) (lists are not contiguous).
+ * emission, decided per view.  Where a view's lists are depth-sorted (blend
+ * ALPHA; deterministic OIT views of more than 6144 tiles) the bins are
+ * super-tiles of super_px x super_px pixels: each segment is sorted, then
+ * split into its tiles (when a tile is a whole super-tile its list is the
+ * segment itself: tile_ranges == super_ranges and pair_keys == super_keys).
+ * Otherwise (tile_bins = 1, super_px = 0) the bins are the tiles themselves
+ * (super_x = tiles_x, super_y = tiles_y) and the emission writes the tile
+ * lists directly: tile_ranges == super_ranges, pair_keys == super_keys ==
+ * super_scratch; this needs tiles_x * tiles_y <= 16384, else the view takes
+ * the super-tile path.  Deterministic OIT views binned into tiles get their
+ * lists in ascending Gaussian index: the histogram's per-block counts in
+ * block_base become bases by a prefix over the blocks, and the emission
+ * places each block's entries warp by warp.  Tile lists: keys u64 =
+ * bits(d) << 32 | index, sorted ascending where depth-sorted, by index in
+ * deterministic mode's fixed order, else in emission order; tile t's list is
+ * pair_keys[tile_ranges[t][0] .. tile_ranges[t][1]) (lists are not
+ * contiguous).
  * grad2d holds 12 floats per Gaussian: d/d(mx, my, conic_a, conic_b, conic_c,
  * sigma, r, g, b, d), 0, 0. */
 typedef struct GpsWorkspaceLayout {
@@ -323,10 +331,11 @@ GPS_API int32_t raycast_sdf(const GpsTsdf* vol, const GpsIntrinsics* K, const Gp
  *   L = sum_v [ sum |C* - C_k| / (3 N_v) + lambda_depth sum |D* - D_k| / N_v ]
  * over pixels with D_k > 0 and D_t > 0 (N_v of them).  Writes the views'
  * non-null outputs and the state render_backward needs into the workspace.
- * The OIT blend is order-independent, so unless settings.deterministic asks
- * for a fixed order it runs sort-free: each tile's list keeps the order of
- * the binning's emission and every warp skips the Gaussians behind all of its
- * pixels.  The "with sort" blend always sorts by (depth, index). */
+ * The OIT blend is order-independent, so it runs sort-free: each tile's list
+ * keeps the order of the binning's emission (in deterministic mode a fixed
+ * order, ascending index; depth-sorted for views of more than 6144 tiles)
+ * and every warp skips the Gaussians behind all of its pixels.  The "with
+ * sort" blend always sorts by (depth, index). */
 GPS_API int32_t render_forward(const GpsGaussians* gaussians, const GpsView* views, int32_t n_views,
                        const GpsRenderSettings* settings, void* ws, size_t ws_bytes,
                        float* loss, void* stream);

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) bin_histogram_kernel(int M,
       for (int sy = sy0; sy <= sy1; ++sy)
         for (int sx = sx0; sx <= sx1; ++sx) atomicAdd(s_hist + sy * v.sup_x + sx, 1u);
   }
-  reserve_block_ranges(s_hist, nsup, v.sup_count, v.block_base);
+  reserve_block_ranges(s_hist, nsup, v.sup_count, v.block_base, v.fixed_order);
 }
 
 // Exclusive scan of the bin counts -> [start, end) (clipped to the capacity;
@@ -216,6 +216,43 @@ __device__ __forceinline__ void emit_warp(long long i, int M, const ViewDev& v, 
   }
 }
 
+// Fixed-order emission of a warp's 32 Gaussians (each lane's bins [sx0, sx1]
+// x [sy0, sy1], empty where sx1 < sx0, and key): every entry's place follows
+// from counts alone, so each bin's list holds its Gaussians in ascending
+// index.  wc: this warp's row of 16-bit per-bin offsets (two bins per word),
+// holding on entry the number of the chunk's entries of warps before this
+// one in each bin.  The warp takes its Gaussians one at a time, in lane
+// order, their entries dealt to the lanes: a Gaussian meets each bin once,
+// so an entry takes its bin's offset with one shared atomic (the neighbour
+// bin sharing the word belongs to another lane's entry of the same
+// Gaussian, its half of the word untouched), and the Gaussians before it in
+// the warp have all advanced their bins' offsets.
+__device__ __forceinline__ void emit_warp_fixed(int sx0, int sx1, int sy0, int sy1,
+                                                unsigned long long key, const ViewDev& v,
+                                                const uint32_t* s_pos, uint32_t* wc,
+                                                uint32_t cap) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < 32; ++j) {
+    const int jx0 = __shfl_sync(0xffffffffu, sx0, j), jx1 = __shfl_sync(0xffffffffu, sx1, j);
+    const int jy0 = __shfl_sync(0xffffffffu, sy0, j), jy1 = __shfl_sync(0xffffffffu, sy1, j);
+    const unsigned long long jkey = __shfl_sync(0xffffffffu, key, j);
+    const int jnx = jx1 - jx0 + 1;
+    if (jnx <= 0) continue;  // warp-uniform
+    const int jcnt = jnx * (jy1 - jy0 + 1);
+    // row of entry e: floor((e + 1/2) / nx) in float is exact (see emit_warp)
+    const float jinv = 1.0f / (float)jnx;
+    for (int e = lane; e < jcnt; e += 32) {
+      const int row = (int)(((float)e + 0.5f) * jinv);
+      const int b = (jy0 + row) * v.sup_x + jx0 + (e - row * jnx);
+      const int sh = 16 * (b & 1);
+      const uint32_t off = (atomicAdd(wc + (b >> 1), 1u << sh) >> sh) & 0xffffu;
+      const uint32_t pos = s_pos[b] + off;
+      if (pos < cap) v.sup_keys[pos] = jkey;
+    }
+    __syncwarp();
+  }
+}
+
 // Emission into the reserved ranges; same block partition (bin_chunks(M)
 // chunks of 256 Gaussians per block) as the histogram.  The block's next
 // write position in every bin (range start + the block's base) is staged in
@@ -242,8 +279,105 @@ __global__ void __launch_bounds__(256) emit_super_kernel(int M, const __grid_con
   __syncthreads();
   const uint32_t cap = (uint32_t)min(v.cap, 0xFFFFFFFFLL);
   const int chunks = bin_chunks(M);
-  for (int ch = 0; ch < chunks; ++ch)
-    emit_warp(((long long)blockIdx.x * chunks + ch) * blockDim.x + threadIdx.x, M, v, s_pos, cap);
+  if (!v.fixed_order) {
+    for (int ch = 0; ch < chunks; ++ch)
+      emit_warp(((long long)blockIdx.x * chunks + ch) * blockDim.x + threadIdx.x, M, v, s_pos, cap);
+    return;
+  }
+  // fixed order, chunk by chunk: each warp counts its Gaussians' bins, the
+  // counts become offsets in warp order, the warps emit, and the bins' bases
+  // move past the chunk (warp 7's offsets end at the chunk's totals)
+  constexpr int NWE = 8;  // warps of the 256-thread block
+  const int nwords = (nsup + 1) >> 1;
+  uint32_t* s_wc = s_pos + nsup;  // [NWE][nwords]
+  const int warp = threadIdx.x >> 5;
+  uint32_t* wc = s_wc + (size_t)warp * nwords;
+  for (int ch = 0; ch < chunks; ++ch) {
+    const long long i = ((long long)blockIdx.x * chunks + ch) * blockDim.x + threadIdx.x;
+    // this thread's Gaussian: its bins and key, kept for the emission below
+    int sx0 = 0, sx1 = -1, sy0 = 0, sy1 = -1;
+    unsigned long long key = 0;
+    if (i < M) {
+      const float4 a = v.rec[4 * i], c = v.rec[4 * i + 2], e = v.rec[4 * i + 3];
+      if (bin_rect(a.x, a.y, c.w, e.x, v, sx0, sx1, sy0, sy1)) key = key_of(a.z, (uint32_t)i);
+      else sx1 = -1;
+    }
+    for (int w = threadIdx.x; w < NWE * nwords; w += blockDim.x) s_wc[w] = 0u;
+    __syncthreads();
+    for (int sy = sy0; sy <= sy1 && sx0 <= sx1; ++sy)
+      for (int sx = sx0; sx <= sx1; ++sx) {
+        const int b = sy * v.sup_x + sx;
+        atomicAdd(wc + (b >> 1), 1u << (16 * (b & 1)));
+      }
+    __syncthreads();
+    // exclusive prefix over the warps, both halves of a word at once (no
+    // half exceeds 8 x 32 entries)
+    for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+      uint32_t run = 0u;
+#pragma unroll
+      for (int q = 0; q < NWE; ++q) {
+        const uint32_t c = s_wc[q * nwords + w];
+        s_wc[q * nwords + w] = run;
+        run += c;
+      }
+    }
+    __syncthreads();
+    emit_warp_fixed(sx0, sx1, sy0, sy1, key, v, s_pos, wc, cap);
+    __syncthreads();
+    if (warp == NWE - 1)
+      for (int w = threadIdx.x & 31; w < nwords; w += 32) {
+        const uint32_t t = wc[w];
+        s_pos[2 * w] += t & 0xffffu;
+        if (2 * w + 1 < nsup) s_pos[2 * w + 1] += t >> 16;
+      }
+    __syncthreads();
+  }
+}
+
+// Fixed-order bins: each bin's per-block counts (block_base[b][s], written
+// by the histogram) become the exclusive prefix over the blocks in block
+// order, and the bin's total goes to sup_count[s] for the scan.  A CTA takes
+// 32 bins (one per lane) and up to 32 groups of consecutive blocks (one per
+// warp, so that a warp reads 32 neighbouring bins of one block row): each
+// warp sums its group, warp 0 scans the group sums, and each warp rewrites
+// its rows as running prefixes.  Block row blockIdx.y: view.
+__global__ void __launch_bounds__(1024) block_prefix_kernel(int M, const __grid_constant__ ViewBatch vb) {
+  chain_wait();
+  __shared__ uint32_t s_sum[32][33];
+  const ViewDev& v = vb.v[blockIdx.y];
+  if (!v.fixed_order) return;
+  const int nsup = v.sup_x * v.sup_y;
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const int s = blockIdx.x * 32 + lane;
+  const int nb = bin_blocks(M);
+  const int R = (nb + 31) / 32;  // blocks per group
+  const int b0 = min(nb, q * R), b1 = min(nb, b0 + R);
+  uint32_t sum = 0u;
+  if (s < nsup) {
+#pragma unroll 4
+    for (int b = b0; b < b1; ++b) sum += v.block_base[(size_t)b * nsup + s];
+  }
+  s_sum[q][lane] = sum;
+  __syncthreads();
+  if (q == 0) {
+    uint32_t run = 0u;
+    for (int k = 0; k < 32; ++k) {
+      const uint32_t t = s_sum[k][lane];
+      s_sum[k][lane] = run;
+      run += t;
+    }
+    if (s < nsup) v.sup_count[s] = run;
+  }
+  __syncthreads();
+  if (s < nsup) {
+    uint32_t run = s_sum[q][lane];
+    for (int b = b0; b < b1; ++b) {
+      const size_t o = (size_t)b * nsup + s;
+      const uint32_t c = v.block_base[o];
+      v.block_base[o] = run;
+      run += c;
+    }
+  }
 }
 
 // ------------------------------------------------------ per-super-tile sort
@@ -396,6 +530,7 @@ __global__ void __launch_bounds__(T) sort_split_kernel(const __grid_constant__ V
   __shared__ uint32_t s_cnt[4][NWT];
   const int slot = batch_slot(vb.sup_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
+  if (v.tile_bin) return;  // its lists came straight from the emission
   unsigned long long* __restrict__ sup_keys = v.sup_keys;
   const int sp = 1 << v.bin_sx;  // square super-tiles
   const int LX = sp / TW, LY = sp / TH, L = LX * LY;  // L <= 4
@@ -498,8 +633,17 @@ cudaError_t launch_scan_super(const ViewBatch& vb, int* status, cudaStream_t st)
   return cudaGetLastError();
 }
 
+cudaError_t launch_block_prefix(int M, const ViewBatch& vb, int max_nsup, cudaStream_t st) {
+  launch_chained(block_prefix_kernel, dim3((max_nsup + 31) / 32, vb.n), dim3(1024), 0, st, M, vb);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_emit_super(int M, const ViewBatch& vb, int max_nsup, cudaStream_t st) {
-  const size_t smem = (size_t)max_nsup * sizeof(uint32_t);
+  // fixed order: the bins' offsets per warp (8 x 16 bits per bin) beside s_pos
+  bool fixed = false;
+  for (int j = 0; j < vb.n; ++j) fixed = fixed || vb.v[j].fixed_order;
+  const size_t smem = (size_t)max_nsup * sizeof(uint32_t) +
+                      (fixed ? (size_t)8 * ((max_nsup + 1) / 2) * sizeof(uint32_t) : 0);
   if (cudaError_t e = allow_smem(emit_super_kernel, smem)) return e;
   launch_chained(emit_super_kernel, dim3(bin_blocks(M), vb.n), dim3(256), smem, st, M, vb);
   return cudaGetLastError();

@@ -24,6 +24,7 @@ cudaError_t launch_project_backward(const GpsGaussians&, float, const ViewBatch&
 cudaError_t launch_bin_histogram(int, const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_scan_super(const ViewBatch&, int*, cudaStream_t);
 cudaError_t launch_emit_super(int, const ViewBatch&, int, cudaStream_t);
+cudaError_t launch_block_prefix(int, const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_sort_split(const ViewBatch&, int, int, int, cudaStream_t);
 cudaError_t launch_composite_fwd(const ViewBatch&, int, int, float, int, int, int, int, cudaStream_t);
 cudaError_t launch_composite_bwd_per_gaussian(const ViewBatch&, int, float, float, const float*,
@@ -87,22 +88,49 @@ long long pair_cap(const GpsRenderSettings* s, int M) {
 }
 
 constexpr int kSuperMax = 16384;  // the bin histogram lives in shared memory
+// fixed-order emission: 8 warps' 16-bit offsets per bin beside the bin bases
+// in shared memory (20 B per bin: 120 KB at this size)
+constexpr int kFixedBinsMax = 6144;
 
-int depth_sorted(const GpsRenderSettings& s);
+long long view_tiles(const GpsView& vw, const TileCfg& tc) {
+  return (long long)((vw.K.width + tc.tw - 1) / tc.tw) * ((vw.K.height + tc.th - 1) / tc.th);
+}
 
-// Bins of the binning pass.  Lists that stay unsorted are binned straight
-// into tiles (one pass: histogram, scan, emission) when every view's tile grid
-// fits the shared-memory histogram; otherwise Gaussians go into square
-// super-tiles, whose segments are sorted (where an order is wanted) and split
-// into their tiles.
-bool tile_bins(const GpsView* views, int32_t n_views, const GpsRenderSettings* s, const TileCfg& tc) {
-  if (depth_sorted(*s)) return false;
-  for (int v = 0; v < n_views; ++v) {
-    const long long tx = (views[v].K.width + tc.tw - 1) / tc.tw;
-    const long long ty = (views[v].K.height + tc.th - 1) / tc.th;
-    if (tx * ty > kSuperMax) return false;
-  }
-  return true;
+// The binning of each view is decided from the settings and that view's
+// own tile grid alone, so that a view renders bit for bit the same whether
+// it is batched with other views or not.
+//
+// Deterministic mode with the order-independent blend needs one fixed list
+// order, not a depth sort: a view's lists go straight into its tile bins in
+// ascending Gaussian index, their places computed from counts (block bases
+// by a prefix over the binning blocks, warp offsets inside a block), where
+// its tile grid fits the emission's shared memory.
+bool view_fixed_order(const GpsView& vw, const GpsRenderSettings& s, const TileCfg& tc) {
+  return s.deterministic && s.blend_mode == GPS_BLEND_OIT && s.schedule == GPS_SCHEDULE_TILES &&
+         view_tiles(vw, tc) <= kFixedBinsMax;
+}
+
+// Are a view's tile lists sorted by (depth, index)?  The "with sort" blend
+// needs front-to-back order, and deterministic mode needs one fixed order for
+// the forward's sums and the pair-slot gather: with the OIT blend that is the
+// fixed-order emission where the tile grid allows it (no sort), else the
+// depth sort.  The OIT blend of Eq. 1-4 is order-independent, so by default
+// it skips the sort (the paper's sort-free pass): its lists keep emission
+// order, which varies with the order in which the binning's atomics ran, so
+// its FP32 sums may differ run to run in the last bits.  The per-Gaussian
+// schedule never sorts.
+bool view_sorted(const GpsView& vw, const GpsRenderSettings& s, const TileCfg& tc) {
+  return s.schedule == GPS_SCHEDULE_TILES &&
+         (s.blend_mode == GPS_BLEND_ALPHA || (s.deterministic && !view_fixed_order(vw, s, tc)));
+}
+
+// Bins of a view's binning pass.  Lists that stay unsorted are binned
+// straight into tiles (one pass: histogram, scan, emission) when the view's
+// tile grid fits the shared-memory histogram; otherwise its Gaussians go into
+// square super-tiles, whose segments are sorted (where an order is wanted)
+// and split into their tiles.
+bool view_tile_bins(const GpsView& vw, const GpsRenderSettings& s, const TileCfg& tc) {
+  return !view_sorted(vw, s, tc) && view_tiles(vw, tc) <= kSuperMax;
 }
 
 // Workspace: [status 256 B] then per view, in order, its regions.
@@ -127,9 +155,9 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     if (views[v].K.width <= 0 || views[v].K.height <= 0)
       return fail(GPS_ERR_INVALID_ARG, "view %d has size %dx%d", v, views[v].K.width,
                   views[v].K.height);
-  const bool by_tile = tile_bins(views, n_views, s, tc);
   size_t off = 256;
   for (int v = 0; v < n_views; ++v) {
+    const bool by_tile = view_tile_bins(views[v], *s, tc);
     const int W = views[v].K.width, H = views[v].K.height;
     const int tx = (W + tc.tw - 1) / tc.tw, ty = (H + tc.th - 1) / tc.th;
     const int sx = by_tile ? tx : (W + sp - 1) / sp, sy = by_tile ? ty : (H + sp - 1) / sp;
@@ -195,15 +223,13 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
   return GPS_OK;
 }
 
-// Are the tile lists sorted by (depth, index)?  The "with sort" blend needs
-// front-to-back order, and deterministic mode needs one fixed order for the
-// forward's sums and the pair-slot gather.  The OIT blend of Eq. 1-4 is
-// order-independent, so by default it skips the sort (the paper's sort-free
-// pass): its lists keep emission order, which varies with the order in which
-// the binning's atomics ran, so its FP32 sums may differ run to run in the
-// last bits.  The per-Gaussian schedule never sorts.
-int depth_sorted(const GpsRenderSettings& s) {
-  return s.schedule == GPS_SCHEDULE_TILES && (s.blend_mode == GPS_BLEND_ALPHA || s.deterministic);
+// Does any view of the batch have depth-sorted lists?  (The super-tile views
+// of one call are all sorted or all unsorted: sorting follows the blend and
+// deterministic mode, and deterministic OIT views sort only as super-tiles.)
+int batch_sorted(const ViewBatch& vb) {
+  for (int j = 0; j < vb.n; ++j)
+    if (vb.v[j].sorted) return 1;
+  return 0;
 }
 
 bool finite_cam(const GpsIntrinsics& K, const GpsPose& P) {
@@ -231,7 +257,7 @@ int32_t check_gaussians(const GpsGaussians* g, const char* what) {
 }
 
 ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int prec, int M,
-                  bool fixed) {
+                  bool fixed, bool fixed_order, bool sorted) {
   ViewDev v{};
   v.cam = make_cam(vw.K, vw.T_wc);
   v.Ct = vw.sdf_rgb;
@@ -263,6 +289,9 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int 
   v.pix_g = reinterpret_cast<float4*>(ws + L.pix_grad);
   v.pair_base = reinterpret_cast<uint32_t*>(ws + L.pair_base);
   v.tile_order = reinterpret_cast<int*>(ws + L.tile_order);
+  v.fixed_order = fixed_order && L.tile_bins ? 1 : 0;
+  v.tile_bin = L.tile_bins;
+  v.sorted = sorted ? 1 : 0;
   v.grad_fixed = fixed ? reinterpret_cast<long long*>(ws + L.grad_fixed) : nullptr;
   v.fixed_exp = fixed ? reinterpret_cast<uint4*>(ws + L.grad_fixed + (size_t)M * 80) : nullptr;
   {
@@ -295,10 +324,14 @@ void make_batch(int M, const GpsView* views, int32_t n_views, const GpsRenderSet
   vb.n = std::min(kMaxBatch, n_views - b0);
   max_nsup = 0;
   int tiles[kMaxBatch];
+  TileCfg tc;
+  tile_cfg(s, tc);
   for (int j = 0; j < vb.n; ++j) {
     GpsWorkspaceLayout L;
     layout(M, views, n_views, s, b0 + j, &L, nullptr);
-    vb.v[j] = make_view(views[b0 + j], base, L, s->precision, M, fixed_point_grads(*s));
+    const GpsView& vw = views[b0 + j];
+    vb.v[j] = make_view(vw, base, L, s->precision, M, fixed_point_grads(*s),
+                        view_fixed_order(vw, *s, tc), view_sorted(vw, *s, tc));
     max_nsup = std::max(max_nsup, vb.v[j].sup_x * vb.v[j].sup_y);
     tiles[j] = vb.v[j].tiles_x * vb.v[j].tiles_y;
     vb.order[j] = j;
@@ -358,7 +391,7 @@ cudaError_t composite_backward(const ViewBatch& vb, int M, const GpsRenderSettin
     if (e == cudaSuccess && M > 0) e = launch_fixed_scale(vb, M, st);
     if (e == cudaSuccess)
       e = launch_composite_bwd(vb, vb.v[0].tw, vb.v[0].th, s->eps_depth, s->lambda_depth, dloss,
-                               s->blend_mode, 1, s->instrument ? 1 : 0, depth_sorted(*s), st);
+                               s->blend_mode, 1, s->instrument ? 1 : 0, batch_sorted(vb), st);
     if (e == cudaSuccess && M > 0) e = launch_fixed_to_grad2d(vb, M, st);
   } else if (stages & GPS_STAGE_COMPOSITE_BWD) {
     for (int j = 0; j < vb.n && e == cudaSuccess; ++j)
@@ -368,7 +401,7 @@ cudaError_t composite_backward(const ViewBatch& vb, int M, const GpsRenderSettin
     if (e == cudaSuccess)
       e = launch_composite_bwd(vb, vb.v[0].tw, vb.v[0].th, s->eps_depth, s->lambda_depth, dloss,
                                s->blend_mode, s->deterministic ? 1 : 0, s->instrument ? 1 : 0,
-                               depth_sorted(*s), st);
+                               batch_sorted(vb), st);
     if (e == cudaSuccess && s->deterministic && M > 0) e = launch_gather_pair_grads(vb, M, st);
   }
   return e;
@@ -501,21 +534,29 @@ int32_t render_forward(const GpsGaussians* g, const GpsView* views, int32_t n_vi
                                          : launch_bin_histogram(g->M, vb, max_nsup, st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_BIN)) {
-      e = launch_scan_super(vb, status, st);
+      // fixed order: the histogram wrote per-block counts; turn them into
+      // bases in block order and the bins' totals (the views with other
+      // bins return at once)
+      bool any_fixed = false, any_super = false;
+      for (int j = 0; j < vb.n; ++j) {
+        any_fixed = any_fixed || vb.v[j].fixed_order;
+        any_super = any_super || !vb.v[j].tile_bin;
+      }
+      if (any_fixed && g->M > 0) e = launch_block_prefix(g->M, vb, max_nsup, st);
+      if (e == cudaSuccess) e = launch_scan_super(vb, status, st);
       if (e == cudaSuccess && g->M > 0) e = launch_emit_super(g->M, vb, max_nsup, st);
       // super-tile bins: split each segment into its tiles' lists, sorted by
-      // depth where the settings ask for an order (see depth_sorted)
-      TileCfg tc;
-      tile_cfg(s, tc);
-      if (e == cudaSuccess && !tile_bins(views, n_views, s, tc))
-        e = launch_sort_split(vb, v0.tw, v0.th, depth_sorted(*s), st);
+      // depth where the settings ask for an order (see view_sorted); views
+      // binned straight into tiles return at once
+      if (e == cudaSuccess && any_super)
+        e = launch_sort_split(vb, v0.tw, v0.th, batch_sorted(vb), st);
     }
     if (e == cudaSuccess && (stages & GPS_STAGE_COMPOSITE)) {
       for (int j = 0; j < vb.n && e == cudaSuccess && s->instrument; ++j)
         e = cudaMemsetAsync(vb.v[j].scalars + 8, 0, 32, st);
       if (e == cudaSuccess)
         e = launch_composite_fwd(vb, v0.tw, v0.th, s->eps_depth, s->blend_mode, has_tgt ? 1 : 0,
-                                 s->instrument ? 1 : 0, depth_sorted(*s), st);
+                                 s->instrument ? 1 : 0, batch_sorted(vb), st);
       if (e == cudaSuccess && has_tgt)
         e = launch_finalize_loss(vb, s->lambda_depth, loss, b0 == 0 ? 1 : 0, st);
     }

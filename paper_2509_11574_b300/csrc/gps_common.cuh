@@ -78,6 +78,11 @@ struct ViewDev {
   // bins of the binning pass (sup_x * sup_y of them, 2^bin_sx x 2^bin_sy
   // pixels each): square super-tiles, or the tiles themselves
   int sup_x, sup_y, bin_sx, bin_sy;
+  // the bins' lists in ascending Gaussian index, placed without atomics
+  // (deterministic mode, OIT blend, tile bins; see emit_super_kernel)
+  int fixed_order;
+  int tile_bin;  // the bins are the tiles (else super-tiles, sorted and split)
+  int sorted;    // the tile lists are sorted by (depth, index)
   int fused;  // backward: upstream gradients from the fused L1 loss (1) or g_rgb/g_depth (0)
   int prec;   // GPS_PREC_* storage type of the colour images Ct, Ctgt, out_rgb
   long long cap;
@@ -176,11 +181,18 @@ __host__ __device__ constexpr int bin_blocks(int M) {
 // Binning: after every thread of the block has added its Gaussians' super-tiles
 // to the shared histogram s_hist, reserve one range per nonzero super-tile with
 // one global atomic; the block's base inside super-tile s goes to
-// block_base[block][s].
+// block_base[block][s].  With fixed_order the block writes its counts there
+// instead, and block_prefix_kernel turns them into bases in block order.
 __device__ __forceinline__ void reserve_block_ranges(uint32_t* s_hist, int nsup,
                                                      uint32_t* __restrict__ sup_count,
-                                                     uint32_t* __restrict__ block_base) {
+                                                     uint32_t* __restrict__ block_base,
+                                                     int fixed_order) {
   __syncthreads();
+  if (fixed_order) {
+    for (int s = threadIdx.x; s < nsup; s += blockDim.x)
+      block_base[(size_t)blockIdx.x * nsup + s] = s_hist[s];
+    return;
+  }
   // eight bins per thread in flight: the atomics' round trips overlap
   constexpr int U = 8;
   for (int s0 = threadIdx.x; s0 < nsup; s0 += U * blockDim.x) {

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) project_kernel(Params P, int M, float nea
       project_one<DEG>(P, (int)(base + threadIdx.x), near_, v,
                        s_f + threadIdx.x * ShRows<DEG>::STRIDE, s_hist);
   }
-  reserve_block_ranges(s_hist, nsup, v.sup_count, v.block_base);
+  reserve_block_ranges(s_hist, nsup, v.sup_count, v.block_base, v.fixed_order);
 }
 
 // Parameter gradients of one Gaussian, summed over the views of a batch.

@@ -14,9 +14,12 @@ def test_kernels_per_step_counts_each_form():
     assert bench.kernels_per_step("oit", (16, 8), fused=False) == per_frame + it * 9
     # depth-sorted lists add the sort + split; deterministic mode also takes
     # the upstream maxima, the fixed-point exponents and converts the sums
-    # (OIT), or places and gathers pair slots (alpha)
+    # (OIT, whose fixed-order lists need the block prefix and no sort up to
+    # 6144 tiles), or places and gathers pair slots (alpha)
     assert bench.kernels_per_step("alpha", (16, 8)) == per_frame + it * 9
     assert bench.kernels_per_step("oit", (16, 8), deterministic=True) == per_frame + it * 12
+    assert bench.kernels_per_step("oit", (8, 8), deterministic=True,
+                                  size=(1280, 720)) == per_frame + it * 12
     assert bench.kernels_per_step("alpha", (16, 8), deterministic=True) == per_frame + it * 11
     # the per-Gaussian schedule: pixel terms + per-Gaussian backward, no sort
     assert bench.kernels_per_step("oit", (16, 8), schedule="per-gaussian") == per_frame + it * 9

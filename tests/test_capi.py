@@ -72,8 +72,8 @@ class _Cam:
 
 
 def test_workspace_size_and_layout_host_only(L):
-    # depth-sorted lists (deterministic): super-tile bins
-    s = gps.settings(deterministic=True)
+    # depth-sorted lists (the "with sort" blend): super-tile bins
+    s = gps.settings(deterministic=True, blend_mode=gps.BLEND_ALPHA)
     cams = [_Cam(160, 120), _Cam(77, 33)]
     n = gps.gps_workspace_size(2000, cams, s)
     assert n > 0 and n % 256 == 0
@@ -88,9 +88,16 @@ def test_workspace_size_and_layout_host_only(L):
     assert L0.pair_capacity == 16 * 2000
     assert (L0.super_px, L0.super_x, L0.super_y, L1.super_x, L1.super_y) == (16, 10, 8, 5, 3)
     assert L0.tile_bins == 0
-    L8 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(16, 8), deterministic=True), 0)
+    L8 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(16, 8), blend_mode=gps.BLEND_ALPHA), 0)
     assert L8.super_keys < L8.pair_keys and L8.super_ranges < L8.tile_ranges
     assert L8.tiles_y == 15
+    # deterministic mode with the OIT blend: fixed-order lists straight into
+    # tile bins (no sort) up to 6144 tiles per view, else depth-sorted super-tiles
+    D8 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(16, 8), deterministic=True), 0)
+    assert D8.tile_bins == 1 and D8.super_px == 0 and D8.pair_keys == D8.super_keys
+    D_big = gps.gps_workspace_layout(10, [_Cam(1280, 720)], gps.settings(tile=(8, 8), deterministic=True), 0)
+    assert D_big.tiles_x * D_big.tiles_y == 14400 > 6144
+    assert D_big.tile_bins == 0 and D_big.super_px == 16
     L32 = gps.gps_workspace_layout(2000, cams, gps.settings(tile=(32, 8), blend_mode=gps.BLEND_ALPHA), 0)
     assert L32.super_px == 32 and (L32.super_x, L32.super_y) == (5, 4)
     # unsorted lists (the default): the bins are the tiles, the emission writes

@@ -88,9 +88,10 @@ def test_finite_differences_of_the_gpu_forward():
     summed in FP64) against RenderImages' gradient: every rgb entry of a few
     Gaussians (L is linear in rgb) and the opacity logits of Gaussians whose
     +-h perturbation leaves the oracle's per-pixel counts unchanged.  The
-    differenced forwards run with depth-sorted lists (deterministic mode), so
-    that both see one summation order and the difference holds no rounding
-    noise from the sort-free lists' varying order."""
+    differenced forwards run with deterministic mode's fixed-order lists
+    (ascending index), so that both see one summation order and the
+    difference holds no rounding noise from the sort-free lists' varying
+    order."""
     w = workload("small")
     f = w.frames[0]
     H, W = f.cam.height, f.cam.width

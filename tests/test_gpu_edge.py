@@ -138,20 +138,25 @@ def test_one_gaussian_covering_the_whole_image():
         np.testing.assert_allclose(g[k], ref[k], rtol=2e-3, atol=1e-4 * np.abs(ref[k]).max())
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (16, 8), (8, 8), (32, 8)])
-def test_sort_free_default_equals_depth_sorted_order(tile):
-    """The OIT blend is order-independent: the sort-free default and the
-    depth-sorted (deterministic) lists give the same images up to FP32
-    summation order, the same loss, and gradients that agree under the same
-    upstream gradients."""
-    w = workload("grad")
+@pytest.mark.parametrize("tile,size", [((16, 16), None), ((16, 8), None), ((8, 8), None),
+                                       ((32, 8), None), ((8, 8), (1280, 720))])
+def test_sort_free_default_equals_deterministic_order(tile, size):
+    """The OIT blend is order-independent: the sort-free default and
+    deterministic mode's lists (ascending index, fixed-order emission; at
+    1280x720 with 8x8 tiles, 14,400 tiles, depth-sorted super-tile lists
+    with the forward's depth cut) give the same images up to FP32 summation
+    order, the same loss, and gradients that agree under the same upstream
+    gradients."""
+    w = workload("grad") if size is None else workload("grad", width=size[0], height=size[1])
     f = w.frames[0]
     H, W = f.cam.height, f.cam.width
     Ct, Dt, _, _ = oracle_sdf_images(w)
     up = np.sign(np.random.default_rng(2).normal(size=(3, H, W))).astype(np.float32) * 1e-3
     outs = []
     for det in (False, True):
-        s = gps.settings(eps_depth=w.eps_depth, tile=tile, deterministic=det)
+        # the 1280x720 view's Gaussians cover many tiles each: room for all entries
+        s = gps.settings(eps_depth=w.eps_depth, tile=tile, deterministic=det,
+                         pair_capacity=0 if size is None else 64 * w.gaussians.M)
         r = gps.Renderer(w.gaussians.M, [f.cam], s)
         g = gps.Gaussians.from_numpy(w.gaussians)
         v = gps.View(f.cam, cuda(Ct), cuda(Dt), grad_rgb=cuda(up),

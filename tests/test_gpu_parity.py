@@ -171,49 +171,67 @@ def test_projection_matches_oracle():
 
 
 # --------------------------------------------------------------- binning
-_BIN_CASES = [(tile, det, 3000, (150, 100)) for det in (True, False)
+# list orders: "depth" (the with-sort blend: sorted by (depth, index)),
+# "index" (deterministic mode with the OIT blend: ascending Gaussian index,
+# placed without atomics where the tile grid allows), "emission" (the
+# sort-free default: the same entries in the order the atomics ran)
+_BIN_CASES = [(tile, order, 3000, (150, 100)) for order in ("depth", "index", "emission")
               for tile in ((16, 16), (16, 8), (8, 8), (32, 8))]
 # 320k and 1.3M Gaussians: 2 and 8 chunks of 256 Gaussians per binning block
 # (tile lists beyond the sort's shared buffers merge through its scratch)
-_BIN_CASES += [((16, 8), True, 320000, (150, 100)), ((16, 8), False, 320000, (150, 100)),
-               ((16, 8), False, 1300000, (150, 100))]
+_BIN_CASES += [((16, 8), "depth", 320000, (150, 100)), ((16, 8), "index", 320000, (150, 100)),
+               ((16, 8), "emission", 320000, (150, 100)), ((16, 8), "emission", 1300000, (150, 100)),
+               ((16, 8), "index", 1300000, (150, 100))]
 # tile grids beyond the shared-memory histogram (257 x 129 tiles of 8 x 8):
-# super-tile bins, sorted and split, or split in emission order
-_BIN_CASES += [((8, 8), True, 3000, (2050, 1030)), ((8, 8), False, 3000, (2050, 1030))]
+# super-tile bins, sorted and split (deterministic mode sorts by depth there),
+# or split in emission order
+_BIN_CASES += [((8, 8), "depth", 3000, (2050, 1030)), ((8, 8), "emission", 3000, (2050, 1030)),
+               ((8, 8), "depth-det", 3000, (2050, 1030))]
 
 
-@pytest.mark.parametrize("tile,det,M,size", _BIN_CASES)
-def test_binning_bit_exact(tile, det, M, size):
-    """Identical FP32 records in, identical sorted (tile, depth, index) lists out
-    (deterministic mode); the sort-free default gives every tile the same
-    entries in emission order."""
+@pytest.mark.parametrize("tile,order,M,size", _BIN_CASES)
+def test_binning_bit_exact(tile, order, M, size):
+    """Identical FP32 records in, identical lists out: sorted (tile, depth,
+    index) lists bit for bit where depth-sorted; each tile's entries in
+    ascending index, bit for bit, in deterministic mode's fixed order; the
+    same entries per tile in the sort-free default."""
     w = workload("small", M=M, width=size[0], height=size[1])  # ragged tiles
     f = w.frames[0]
     rec_o, _ = oracle.project(w.gaussians.astype(np.float64), f.cam)
     r32 = oracle.records_f32(rec_o)
     keys_o, vals_o, ranges_o = oracle.bin_records(r32, f.cam.width, f.cam.height, *tile)
+    kw = dict(stages=gps.STAGE_BIN, tile=tile)
+    if order == "depth":
+        kw["blend_mode"] = gps.BLEND_ALPHA
+    elif order in ("index", "depth-det"):
+        kw["deterministic"] = True
     # the large view's Gaussians span tens of bins each: room for all entries
-    r = _renderer(w, [f.cam], stages=gps.STAGE_BIN, tile=tile, deterministic=det,
-                  pair_capacity=64 * M if size[0] > 1000 else 0)
+    r = _renderer(w, [f.cam], pair_capacity=64 * M if size[0] > 1000 else 0, **kw)
     r.region(0, "records", torch.float32, r.M * 16).copy_(torch.from_numpy(r32.reshape(-1)).cuda())
     g = gps.Gaussians.from_numpy(w.gaussians)
     Ct, Dt = np.zeros((3, f.cam.height, f.cam.width), np.float32), np.zeros((f.cam.height, f.cam.width), np.float32)
     r.forward(g, [gps.View(f.cam, cuda(Ct), cuda(Dt))])
     L = r.layout(0)
+    # tile bins for the fixed and the emission order on the small view; super-tiles otherwise
+    assert L.tile_bins == int(order in ("index", "emission") and size[0] < 1000)
     nt = L.tiles_x * L.tiles_y
     ranges = r.region(0, "tile_ranges", torch.int32, nt * 2).view(nt, 2).cpu().numpy().astype(np.int64)
     allkeys = r.region(0, "pair_keys", torch.int64, int(ranges[:, 1].max())).cpu().numpy().view(np.uint64)
     total = 0
     for t in range(nt):
         seg = allkeys[ranges[t, 0]:ranges[t, 1]]
-        if not det:
-            seg = np.sort(seg)  # (depth bits, index) order, as the oracle's values
         lo, hi = int(ranges_o[t, 0]), int(ranges_o[t, 1])
+        ko, vo = keys_o[lo:hi], vals_o[lo:hi]
+        if order == "emission":
+            seg = np.sort(seg)  # (depth bits, index) order, as the oracle's values
+        elif order == "index":
+            o = np.argsort(vo, kind="stable")  # the oracle's entries in ascending index
+            ko, vo = ko[o], vo[o]
         total += len(seg)
         # device key = bits(d) << 32 | index; oracle key = tile << 32 | bits(d), value = index
         assert len(seg) == hi - lo, (t, len(seg), hi - lo)
-        np.testing.assert_array_equal(seg >> np.uint64(32), keys_o[lo:hi] & np.uint64(0xffffffff))
-        np.testing.assert_array_equal((seg & np.uint64(0xffffffff)).astype(np.uint32), vals_o[lo:hi])
+        np.testing.assert_array_equal(seg >> np.uint64(32), ko & np.uint64(0xffffffff))
+        np.testing.assert_array_equal((seg & np.uint64(0xffffffff)).astype(np.uint32), vo)
     assert total == len(keys_o) > M // 3
     assert r.status() == gps.GPS_OK
 
