@@ -241,8 +241,10 @@ typedef struct GpsWorkspaceLayout {
   size_t tile_partials; /* float [tiles][4] loss partial sums                 */
   size_t view_scalars;  /* float [8]: loss, colour sum, depth sum, N_valid,
                            (bin, Gaussian) entries, the deterministic pair
-                           counter, then the upstream maxima max|h|, max|sv|
-                           of the fixed-point backward; then uint64 [4] evaluation
+                           counter, then the upstream bounds max|h|, max|sv|
+                           of the fixed-point backward (from the forward's
+                           loss with the fused loss, per unit dL/dloss; from
+                           the upstream images otherwise); then uint64 [4] evaluation
                            counters: forward tested, forward counted, backward
                            tested, backward counted (instrument = 1)          */
   size_t grad2d;        /* float [M][12]                                      */
@@ -266,14 +268,12 @@ typedef struct GpsWorkspaceLayout {
                            super-tile), in buckets of half an octave; the
                            composites take their tiles in this order, longest
                            lists first                                        */
-  size_t grad_fixed;    /* int64 [M][10], then uint8 [M][16] (deterministic
-                           mode, OIT blend, tile schedule): each Gaussian's 2D
-                           gradient summed as integers in units of a
-                           power-of-two quantum from a bound on every addend
-                           (see composite.cu), so the sum is the same in any
-                           order; then each component's quantum exponent
-                           (+128); pair_grads and pair_base are empty in that
-                           mode                                              */
+  size_t grad_fixed;    /* int64 [M][10] (deterministic mode, OIT blend,
+                           tile schedule): each Gaussian's 2D gradient summed
+                           as integers in units of a power-of-two quantum
+                           from a bound on every addend (see composite.cu),
+                           so the sum is the same in any order; pair_grads
+                           and pair_base are empty in that mode              */
 } GpsWorkspaceLayout;
 
 /* ---------------------------------------------------------------- calls */

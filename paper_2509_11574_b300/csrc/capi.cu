@@ -34,8 +34,7 @@ cudaError_t launch_composite_bwd(const ViewBatch&, int, int, float, float, const
 cudaError_t launch_finalize_loss(const ViewBatch&, float, float*, int, cudaStream_t);
 cudaError_t launch_gather_pair_grads(const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_upstream_max(const ViewBatch&, float, float, const float*, cudaStream_t);
-cudaError_t launch_fixed_scale(const ViewBatch&, int, cudaStream_t);
-cudaError_t launch_fixed_to_grad2d(const ViewBatch&, int, cudaStream_t);
+cudaError_t launch_fixed_to_grad2d(const ViewBatch&, int, const float*, cudaStream_t);
 cudaError_t launch_pair_base(const ViewBatch&, int, const int*, cudaStream_t);
 cudaError_t launch_adam(const GpsGaussians&, const GpsGaussians&, const GpsGaussians&,
                         const GpsGaussians&, const GpsAdamHyper&, int, int*, cudaStream_t);
@@ -206,7 +205,7 @@ int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRender
     L.tile_order = off;
     off = align256(off + ntiles * 4);
     L.grad_fixed = off;
-    off = align256(off + (fixed ? (size_t)M * 96 : 0));
+    off = align256(off + (fixed ? (size_t)M * 80 : 0));
     L.tiles_x = tx;
     L.tiles_y = ty;
     L.tile_w = tc.tw;
@@ -293,7 +292,6 @@ ViewDev make_view(const GpsView& vw, char* ws, const GpsWorkspaceLayout& L, int 
   v.tile_bin = L.tile_bins;
   v.sorted = sorted ? 1 : 0;
   v.grad_fixed = fixed ? reinterpret_cast<long long*>(ws + L.grad_fixed) : nullptr;
-  v.fixed_exp = fixed ? reinterpret_cast<uint4*>(ws + L.grad_fixed + (size_t)M * 80) : nullptr;
   {
     const int sp = 1 << super_shift_for(L.tile_w);
     v.pair_slots = L.pair_capacity * ((sp / L.tile_w) * (sp / L.tile_h));
@@ -384,15 +382,24 @@ cudaError_t composite_backward(const ViewBatch& vb, int M, const GpsRenderSettin
     e = launch_composite_bwd_per_gaussian(vb, M, s->eps_depth, s->lambda_depth, dloss,
                                           s->instrument ? 1 : 0, st);
   } else if ((stages & GPS_STAGE_COMPOSITE_BWD) && fixed_point_grads(*s)) {
-    // deterministic, OIT: the carry-over walk with fixed-point sums
-    for (int j = 0; j < vb.n && e == cudaSuccess; ++j)
-      e = cudaMemsetAsync(vb.v[j].scalars + 6, 0, 2 * sizeof(float), st);
-    if (e == cudaSuccess) e = launch_upstream_max(vb, s->eps_depth, s->lambda_depth, dloss, st);
-    if (e == cudaSuccess && M > 0) e = launch_fixed_scale(vb, M, st);
+    // deterministic, OIT: the carry-over walk with fixed-point sums.  The
+    // quanta need bounds on the upstream terms: the forward's loss left them
+    // for views with the fused loss; the others take the maxima of their
+    // upstream images.
+    bool any_explicit = false;
+    for (int j = 0; j < vb.n && e == cudaSuccess; ++j) {
+      e = cudaMemsetAsync(vb.v[j].grad_fixed, 0, (size_t)M * 80, st);
+      if (e == cudaSuccess && !vb.v[j].fused) {
+        e = cudaMemsetAsync(vb.v[j].scalars + 6, 0, 2 * sizeof(float), st);
+        any_explicit = true;
+      }
+    }
+    if (e == cudaSuccess && any_explicit)
+      e = launch_upstream_max(vb, s->eps_depth, s->lambda_depth, dloss, st);
     if (e == cudaSuccess)
       e = launch_composite_bwd(vb, vb.v[0].tw, vb.v[0].th, s->eps_depth, s->lambda_depth, dloss,
                                s->blend_mode, 1, s->instrument ? 1 : 0, batch_sorted(vb), st);
-    if (e == cudaSuccess && M > 0) e = launch_fixed_to_grad2d(vb, M, st);
+    if (e == cudaSuccess && M > 0) e = launch_fixed_to_grad2d(vb, M, dloss, st);
   } else if (stages & GPS_STAGE_COMPOSITE_BWD) {
     for (int j = 0; j < vb.n && e == cudaSuccess; ++j)
       e = s->deterministic ? cudaMemsetAsync(vb.v[j].scalars + 5, 0, sizeof(float), st)

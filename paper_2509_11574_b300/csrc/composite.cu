@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
   __shared__ float4 s_a[NB], s_b[NB], s_c[NB];
   __shared__ float2 s_e[NB];
   __shared__ uint8_t s_list[NW][NB];
-  __shared__ float s_tmp[NW * 3];
+  __shared__ float s_tmp[NW * 4];
   const int slot = batch_slot(vb.tile_start, vb.n, blockIdx.x);
   const ViewDev& v = vb.v[vb.order[slot]];
   const int tile = tile_of(v, blockIdx.x - vb.tile_start[slot]);
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
     }
   }
   if (INSTR) add_counters(v, 0, n_tested, n_counted);
-  float lr = 0.f, ld = 0.f, nv = 0.f;
+  float lr = 0.f, ld = 0.f, nv = 0.f, um = 0.f;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const bool in = h ? in1 : in0;
@@ -345,6 +345,10 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
                 fabsf(o2 - ld_col(v.Ctgt, 2 * npx + pix, v.prec));
           ld += fabsf(od - dk);
           nv += 1.0f;
+          // for the deterministic backward's quanta: the fused loss's
+          // |dL/dalpha| term of this pixel is at most this x max(1/3, |lambda|)
+          // x |dL/dloss| / N_valid
+          um = fmaxf(um, (fabsf(o0) + fabsf(o1) + fabsf(o2) + fabsf(od)) * iN);
         }
       }
     }
@@ -353,21 +357,24 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_oit2_kernel(
     lr = warp_sum(lr);
     ld = warp_sum(ld);
     nv = warp_sum(nv);
+    um = warp_max(um);
     __syncthreads();
     if (lane == 0) {
-      s_tmp[warp * 3 + 0] = lr;
-      s_tmp[warp * 3 + 1] = ld;
-      s_tmp[warp * 3 + 2] = nv;
+      s_tmp[warp * 4 + 0] = lr;
+      s_tmp[warp * 4 + 1] = ld;
+      s_tmp[warp * 4 + 2] = nv;
+      s_tmp[warp * 4 + 3] = um;
     }
     __syncthreads();
     if (tid == 0) {
-      float a = 0.f, bsum = 0.f, c = 0.f;
+      float a = 0.f, bsum = 0.f, c = 0.f, w = 0.f;
       for (int k = 0; k < NW; ++k) {
-        a += s_tmp[k * 3];
-        bsum += s_tmp[k * 3 + 1];
-        c += s_tmp[k * 3 + 2];
+        a += s_tmp[k * 4];
+        bsum += s_tmp[k * 4 + 1];
+        c += s_tmp[k * 4 + 2];
+        w = fmaxf(w, s_tmp[k * 4 + 3]);
       }
-      v.tile_partials[tile] = make_float4(a, bsum, c, 0.f);
+      v.tile_partials[tile] = make_float4(a, bsum, c, w);
     }
   }
 }
@@ -573,48 +580,61 @@ __global__ void __launch_bounds__(TW* TH / 2) composite_fwd_alpha2_kernel(
 
 // Per-view loss from the tile partial sums, summed in a fixed order: each
 // thread adds a strided subset, then a fixed shuffle tree and warp order.
-// scalars: [0] view loss, [1] sum |C* - C|, [2] sum |D* - D|, [3] N_valid.
-// The views' losses are summed in view order into *loss (overwritten when
-// `first`, else added).
+// scalars: [0] view loss, [1] sum |C* - C|, [2] sum |D* - D|, [3] N_valid,
+// and for the deterministic OIT backward's quanta, bounds per unit
+// |dL/dloss| on the fused loss's upstream terms: [6] >= |dL/dC*| / (1 + W),
+// |dL/dD*| / (1 + W) = max(1/3, |lambda|) / N_valid, [7] >= |dL/dalpha|'s
+// sum term (max(1/3, |lambda|) / N_valid x the forward's per-pixel maximum
+// of (|C*| + |D*|) / (1 + W)); both carry a factor 1 + 2^-10 for the FP32
+// rounding of the backward's products.  The views' losses are summed in view
+// order into *loss (overwritten when `first`, else added).
 __global__ void __launch_bounds__(256) finalize_loss_kernel(const __grid_constant__ ViewBatch vb,
                                                             float lambda_depth, float* loss,
                                                             int first) {
   chain_wait();
-  __shared__ float s[3][8];
+  __shared__ float s[4][8];
   float total = 0.f;
   for (int k = 0; k < vb.n; ++k) {
     const ViewDev& v = vb.v[k];
     const int ntiles = v.tiles_x * v.tiles_y;
-    float a = 0.f, b = 0.f, c = 0.f;
+    float a = 0.f, b = 0.f, c = 0.f, u = 0.f;
     for (int t = threadIdx.x; t < ntiles; t += 256) {
       const float4 p = v.tile_partials[t];
       a += p.x;
       b += p.y;
       c += p.z;
+      u = fmaxf(u, p.w);
     }
     a = warp_sum(a);
     b = warp_sum(b);
     c = warp_sum(c);
+    u = warp_max(u);
     const int w = threadIdx.x >> 5;
     __syncthreads();
     if ((threadIdx.x & 31) == 0) {
       s[0][w] = a;
       s[1][w] = b;
       s[2][w] = c;
+      s[3][w] = u;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      float sa = 0.f, sb = 0.f, n = 0.f;
+      float sa = 0.f, sb = 0.f, n = 0.f, um = 0.f;
       for (int q = 0; q < 8; ++q) {
         sa += s[0][q];
         sb += s[1][q];
         n += s[2][q];
+        um = fmaxf(um, s[3][q]);
       }
       const float L = n > 0.f ? sa / (3.0f * n) + lambda_depth * sb / n : 0.0f;
+      const float hb = n > 0.f ? fmaxf(1.0f / 3.0f, fabsf(lambda_depth)) / n * (1.0f + 0x1p-10f)
+                               : 0.0f;
       v.scalars[0] = L;
       v.scalars[1] = sa;
       v.scalars[2] = sb;
       v.scalars[3] = n;
+      v.scalars[6] = hb;
+      v.scalars[7] = hb * um;
       total = k == 0 ? L : total + L;
     }
   }
@@ -681,113 +701,107 @@ __device__ __forceinline__ void zero_slot(const ViewDev& v, long long slot) {
 // integer in units of 2^e[k] for component k: integer addition is
 // associative, so the sum is the same whatever the order, and converting
 // back to float is one rounding.  e[k] comes from a bound b_k on the
-// magnitude of any partial of that component of that Gaussian, computed once
-// per Gaussian (fixed_scale_kernel) from its record and the view's upstream
-// maxima (hmax >= |h| of every pixel's dL/dC* / N, dL/dD* / N; smax >= |sv|):
+// magnitude of any partial of that component of that Gaussian, from its
+// record and the view's upstream bounds (hmax >= |h| of every pixel's
+// dL/dC* / N, dL/dD* / N; smax >= |sv|):
 //   a counted pixel has alpha <= sigma <= 1, |dx| <= ext_x, |dy| <= ext_y;
 //   with V = hmax (|r| + |g| + |b| + |d|) + smax >= |dL/dalpha|, over a warp
 //   block's 32 pixels |m_0..3| <= 32 hmax, |m4| <= 32 V sigma,
 //   |m5| <= 32 V ext_x, |m6| <= 32 V ext_y, |m7| <= 32 V ext_x^2,
 //   |m8| <= 32 V ext_x ext_y, |m9| <= 32 V ext_y^2, and grad2d_of's
-//   combinations follow; the bounds below carry a factor 2 for the FP32
-//   rounding of the partial and of the bound itself.
-// With at most n = (tiles of the Gaussian's rectangle) x (warps per tile)
-// partials, 2^e[k] >= b_k 2^-(62 - ceil(log2 n)) keeps every partial below
-// 2^(62 - ceil(log2 n)) quanta and every sum below 2^62: no overflow.  The
-// quantum is about 2^-56 of the bound at the room workload's sizes.  e is
-// clamped to [-120, 126] so that 2^-e and 2^e are normal floats (raising e
-// only coarsens the quantum; a bound above 2^(188 - ceil(log2 n)) is not met
-// by finite FP32 gradients).
+//   combinations follow; the bounds carry a factor 2 for the FP32 rounding
+//   of the partial and of the bound itself.
+// The bounds factor as (record term c_k) x (V or hmax); the projection
+// stores the record terms' exponents with the partial count in the record
+// (fixed_pre_exponents), and the walk and the conversion back add the
+// exponent of V or hmax.  With at most n = (tiles of the Gaussian's
+// rectangle) x (warps per tile) partials, 2^e[k] > b_k 2^-(62 - ceil(log2 n))
+// keeps every partial below 2^(62 - ceil(log2 n)) quanta and every sum below
+// 2^62: no overflow.  The quantum is about 2^-56 of the bound at the room
+// workload's sizes.  e is clamped to [-120, 126] so that 2^-e and 2^e are
+// normal floats (raising e only coarsens the quantum; lowering it to 126
+// happens only for bounds above 2^(188 - ceil(log2 n)), where any finite
+// FP32 partial is still below 2^2 quanta).
 constexpr int kFixedEMin = -120, kFixedEMax = 126;
 
-__device__ __forceinline__ void fixed_exponents(float ca, float cb, float cc, float cr, float cg,
-                                                float cbl, float d, float ex, float ey, float hmax,
-                                                float smax, int n_part, int (&e)[10]) {
-  const float V = hmax * (fabsf(cr) + fabsf(cg) + fabsf(cbl) + fabsf(d)) + smax;
-  float b[10];
-  b[0] = 64.0f * V * (fabsf(ca) * ex + fabsf(cb) * ey);
-  b[1] = 64.0f * V * (fabsf(cb) * ex + fabsf(cc) * ey);
-  b[2] = 32.0f * V * ex * ex;
-  b[3] = 64.0f * V * ex * ey;
-  b[4] = 32.0f * V * ey * ey;
-  b[5] = 64.0f * V;
-  b[6] = b[7] = b[8] = b[9] = 64.0f * hmax;
-  const int ln = n_part > 1 ? 32 - __clz(n_part - 1) : 0;  // ceil(log2 n)
+__device__ __forceinline__ int fixed_clamp_e(int e) { return min(max(e, kFixedEMin), kFixedEMax); }
+
+// The quantum exponents of a Gaussian's ten components from its packed
+// pre-exponents and the bounds V (components 0-5) and hmax (6-9).
+__device__ __forceinline__ void fixed_exponents(uint2 pre, float V, float hm, int (&e)[10]) {
+  const int xv = fixed_expo_above(V) - 128, xh = fixed_expo_above(hm) - 128;
 #pragma unroll
-  for (int k = 0; k < 10; ++k) {
-    int x = 0;
-    frexpf(fminf(b[k], 3.0e38f), &x);  // b < 2^x (NaN -> 3e38)
-    e[k] = min(max(x - (62 - ln), kFixedEMin), kFixedEMax);
-  }
+  for (int k = 0; k < 4; ++k) e[k] = fixed_clamp_e((int)((pre.x >> (8 * k)) & 0xffu) + xv);
+  e[4] = fixed_clamp_e((int)(pre.y & 0xffu) + xv);
+  const int p5 = (int)((pre.y >> 8) & 0xffu);
+  e[5] = fixed_clamp_e(p5 + xv);
+  e[6] = e[7] = e[8] = e[9] = fixed_clamp_e(p5 + xh);
 }
 
-// Exponent k of a Gaussian's packed exponents (byte k, biased by 128).
-__device__ __forceinline__ int fixed_e(const uint4& p, int k) {
-  const uint32_t w = k < 4 ? p.x : (k < 8 ? p.y : p.z);
-  return (int)((w >> (8 * (k & 3))) & 0xffu) - 128;
+// The view's upstream bounds: with the fused L1 loss the forward's loss
+// finalisation left them per unit dL/dloss in scalars[6..7] (scaled here by
+// |dL/dloss|), with explicit upstream images upstream_max_kernel left the
+// maxima themselves.
+__device__ __forceinline__ void fixed_maxima(const ViewDev& v, const float* dloss, float& hm,
+                                             float& sm) {
+  const float f = v.fused && dloss ? fabsf(*dloss) : 1.0f;
+  hm = __fmul_rn(v.scalars[6], f);
+  sm = __fmul_rn(v.scalars[7], f);
+}
+
+// V = hmax (|r| + |g| + |b| + |d|) + smax, explicitly rounded (the walk and
+// the conversion back compute it from the same record values).
+__device__ __forceinline__ float fixed_v(float hm, float sm, float cr, float cg, float cb,
+                                         float d) {
+  return __fmaf_rn(hm, __fadd_rn(__fadd_rn(fabsf(cr), fabsf(cg)), __fadd_rn(fabsf(cb), fabsf(d))),
+                   sm);
+}
+
+// A Gaussian's packed pre-exponents: from the record's words 13-14 where the
+// projection wrote them, else recomputed from the record.
+__device__ __forceinline__ uint2 fixed_pre(const ViewDev& v, const float4& E, float mx, float my,
+                                           float ca, float cb, float cc, const float* ex_p) {
+  const uint2 pre = make_uint2(__float_as_uint(E.y), __float_as_uint(E.z));
+  if (fixed_pre_tagged(pre.y)) return pre;
+  return fixed_pre_exponents(mx, my, ca, cb, cc, __ldg(ex_p), E.x, v.cam.W, v.cam.H, v.tw, v.th);
 }
 
 // Add a (warp block, Gaussian gi) partial g to gi's fixed-point sums.  The
-// integer q = g 2^-e, rounded half away from zero, is formed from the
-// float's fields: g = +-m 2^(E - 150) with the 24-bit significand m, so
-// q = m 2^(E - 150 - e) (an exact left shift: the bound keeps it below
-// 2^62; or a right shift with rounding).  Subnormal g (below 2^-126, under
-// the smallest quantum 2^-120) adds nothing.  (Integer shifts: a float to
-// 64-bit integer conversion per component measured 3.7 us slower per
-// backward on the room workload.)
-__device__ __forceinline__ void fixed_add(const ViewDev& v, uint32_t gi, const float (&g)[10]) {
-  const uint4 p = __ldg(v.fixed_exp + gi);
+// integer q = g 2^-e, truncated toward zero, is formed from the float's
+// fields: g = +-m 2^(E - 150) with the 24-bit significand m, so
+// q = m 2^(E - 150 - e): an exact left shift (the bound keeps it below 2^62)
+// or a right shift (an error below one quantum, the same in every run).  A
+// subnormal g (E = 0, below 2^-126) reads as m 2^-150 with the implicit bit
+// set; as the quantum is at least 2^-120, its shift is to the right by 30 or
+// more and it adds nothing.  (Integer shifts: a float to 64-bit integer
+// conversion per component measured 3.7 us slower per backward.)
+__device__ __forceinline__ void fixed_add(const ViewDev& v, uint32_t gi, const float (&g)[10],
+                                          const int (&e)[10]) {
   unsigned long long* o = reinterpret_cast<unsigned long long*>(v.grad_fixed + 10 * (size_t)gi);
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
     const int bits = __float_as_int(g[k]);
-    const int E = (bits >> 23) & 0xff;
-    const int sh = E - 150 - fixed_e(p, k);
+    const int sh = ((bits >> 23) & 0xff) - 150 - e[k];
     const unsigned long long m = (unsigned long long)((bits & 0x7fffff) | 0x800000);
-    unsigned long long q =
-        sh >= 0 ? m << min(sh, 63) : (sh > -25 ? (m + (1ull << (-sh - 1))) >> (-sh) : 0ull);
-    if (E == 0) q = 0ull;
-    if (bits < 0) q = 0ull - q;
-    if (q != 0ull) atomicAdd(o + k, q);
+    const unsigned long long q = sh >= 0 ? m << min(sh, 63) : m >> min(-sh, 63);
+    if (q != 0ull) atomicAdd(o + k, bits < 0 ? 0ull - q : q);
   }
 }
 
-// Per Gaussian, after the upstream maxima: its packed exponents, and zeroed
-// sums.  Block row blockIdx.y: view.
-__global__ void __launch_bounds__(256) fixed_scale_kernel(const __grid_constant__ ViewBatch vb,
-                                                          int M) {
-  chain_wait();
-  const ViewDev& v = vb.v[blockIdx.y];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  const float4 A = v.rec[4 * (size_t)i], B = v.rec[4 * (size_t)i + 1], C = v.rec[4 * (size_t)i + 2];
-  const float ey = v.rec[4 * (size_t)i + 3].x;
-  int n_part = 1, x0, x1, y0, y1;
-  if (record_rect(A.x, A.y, C.w, ey, v.cam.W, v.cam.H, x0, x1, y0, y1))
-    n_part = (x1 / v.tw - x0 / v.tw + 1) * (y1 / v.th - y0 / v.th + 1) * (v.tw * v.th / 32);
-  int e[10];
-  fixed_exponents(B.x, B.y, B.z, C.x, C.y, C.z, A.z, C.w, ey, v.scalars[6], v.scalars[7], n_part,
-                  e);
-  uint32_t w[3] = {0u, 0u, 0u};
-#pragma unroll
-  for (int k = 0; k < 10; ++k) w[k >> 2] |= (uint32_t)(e[k] + 128) << (8 * (k & 3));
-  v.fixed_exp[i] = make_uint4(w[0], w[1], w[2], 0u);
-  longlong2* o = reinterpret_cast<longlong2*>(v.grad_fixed + 10 * (size_t)i);
-#pragma unroll
-  for (int k = 0; k < 5; ++k) o[k] = make_longlong2(0, 0);
-}
-
-// The views' upstream maxima (scalars[6] = hmax, scalars[7] = smax, zero on
-// entry), from the same per-pixel terms the backward stages.  Block row
-// blockIdx.y: view; the blocks stride over the pixels, reduce in shared
-// memory and add one atomic maximum per block (one atomic per warp, all on
-// the same two words, took 19 us at 640 x 480).
+// The upstream maxima of the views with explicit upstream images
+// (scalars[6] = hmax, scalars[7] = smax, zero on entry), from the same
+// per-pixel terms the backward stages; views with the fused loss have their
+// bounds from the forward.  Block row blockIdx.y: view; the blocks stride
+// over the pixels, reduce in shared memory and add one atomic maximum per
+// block (one atomic per warp, all on the same two words, took 19 us at
+// 640 x 480).
 __global__ void __launch_bounds__(256) upstream_max_kernel(const __grid_constant__ ViewBatch vb,
                                                            float eps, float lambda,
                                                            const float* dloss) {
   chain_wait();
   __shared__ float s_m[2][8];
   const ViewDev& v = vb.v[blockIdx.y];
+  if (v.fused) return;
   const long long npx = (long long)v.cam.W * v.cam.H;
   const float scale = loss_scale(v, v.fused, dloss);
   float hm = 0.f, sm = 0.f;
@@ -821,22 +835,28 @@ __global__ void __launch_bounds__(256) upstream_max_kernel(const __grid_constant
 }
 
 // Fixed-point sums -> grad2d (float): one rounding of the integer sum, then
-// the exact power-of-two scale 2^e.  Block row blockIdx.y: view.
+// the exact power-of-two scale 2^e (the exponents recomputed from the
+// record, as the walk computed them).  Block row blockIdx.y: view.
 __global__ void __launch_bounds__(256) fixed_to_grad2d_kernel(const __grid_constant__ ViewBatch vb,
-                                                              int M) {
+                                                              int M, const float* dloss) {
   chain_wait();
   const ViewDev& v = vb.v[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
-  const uint4 p = v.fixed_exp[i];
+  const float4* rr = v.rec + 4 * (size_t)i;
+  const float4 A = rr[0], C = rr[2];
+  const uint2 pre = fixed_pre(v, rr[3], A.x, A.y, rr[1].x, rr[1].y, rr[1].z, &rr[2].w);
+  float hm, sm;
+  fixed_maxima(v, dloss, hm, sm);
+  int e[10];
+  fixed_exponents(pre, fixed_v(hm, sm, C.x, C.y, C.z, A.z), hm, e);
   const longlong2* s = reinterpret_cast<const longlong2*>(v.grad_fixed + 10 * (size_t)i);
   float g[12];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const longlong2 t = s[k];
-    g[2 * k] = __fmul_rn(__ll2float_rn(t.x), __int_as_float((127 + fixed_e(p, 2 * k)) << 23));
-    g[2 * k + 1] =
-        __fmul_rn(__ll2float_rn(t.y), __int_as_float((127 + fixed_e(p, 2 * k + 1)) << 23));
+    g[2 * k] = __fmul_rn(__ll2float_rn(t.x), __int_as_float((127 + e[2 * k]) << 23));
+    g[2 * k + 1] = __fmul_rn(__ll2float_rn(t.y), __int_as_float((127 + e[2 * k + 1]) << 23));
   }
   g[10] = g[11] = 0.f;
   float4* o = v.grad2d + 3 * (size_t)i;
@@ -1157,23 +1177,34 @@ struct BwdCarryBatch {
   static constexpr int value = NT >= 128 ? 256 : 128;
 };
 
-template <bool INSTR>
+template <bool INSTR, bool FIXED>
 __device__ __forceinline__ void bwd_flush(const ViewDev& v, const BwdGauss& G, bool has, int blk,
                                           float bx0, float by0, const float4* s_h,
-                                          const float2* s_s, unsigned& n_tested,
-                                          unsigned& n_counted) {
+                                          const float2* s_s, const float* dloss,
+                                          unsigned& n_tested, unsigned& n_counted) {
   float m[10], g[10];
   bwd_walk<INSTR>(G, has, blk, bx0, by0, s_h, s_s, m, n_tested, n_counted);
   if (has) {
     grad2d_of(m, G.ca, 0.5f * G.b2, G.cc, G.sig, g);
-    if (v.grad_fixed)
-      fixed_add(v, G.gi, g);
-    else
+    if constexpr (FIXED) {
+      // the pre-exponents are read back here (an L2 hit: the batch staged
+      // the record) rather than carried through the walk in registers
+      const float4* rr = v.rec + 4 * (size_t)G.gi;
+      const uint2 pre = fixed_pre(v, __ldg(rr + 3), G.mx, G.my, G.ca, 0.5f * G.b2, G.cc, &rr[2].w);
+      float hm, sm;
+      fixed_maxima(v, dloss, hm, sm);
+      int e[10];
+      fixed_exponents(pre, fixed_v(hm, sm, G.cr, G.cg, G.cb, G.d), hm, e);
+      fixed_add(v, G.gi, g, e);
+    } else {
       store_grad2d(v, 0, 0u, G.gi, g);
+    }
   }
 }
 
-template <int TW, int TH, bool INSTR>
+// FIXED: deterministic mode's fixed-point sums (a separate instantiation, so
+// that the default walk carries none of their code).
+template <int TW, int TH, bool INSTR, bool FIXED>
 __global__ void __launch_bounds__(TW* TH)
     composite_bwd_oit_carry_kernel(const __grid_constant__ ViewBatch vb, float eps, float lambda,
                                    const float* dloss) {
@@ -1278,7 +1309,7 @@ __global__ void __launch_bounds__(TW* TH)
         const int j = s_list[warp][t0 + lane - pend];
         G = bwd_gauss<INSTR>(s_a[j], s_b[j], s_c[j], s_e[j], s_gi[j], bx0, by0);
       }
-      bwd_flush<INSTR>(v, G, true, blk, bx0, by0, s_h, s_s, n_tested, n_counted);
+      bwd_flush<INSTR, FIXED>(v, G, true, blk, bx0, by0, s_h, s_s, dloss, n_tested, n_counted);
       t0 += 32 - pend;
       pend = 0;
     }
@@ -1292,7 +1323,7 @@ __global__ void __launch_bounds__(TW* TH)
   if (pend > 0) {
     const bool has = lane < pend;
     if (!has) G = bwd_idle();
-    bwd_flush<INSTR>(v, G, has, blk, bx0, by0, s_h, s_s, n_tested, n_counted);
+    bwd_flush<INSTR, FIXED>(v, G, has, blk, bx0, by0, s_h, s_s, dloss, n_tested, n_counted);
   }
   if (INSTR) add_counters(v, 2, n_tested, n_counted);
 }
@@ -1980,12 +2011,19 @@ static cudaError_t bwd_tw(const ViewBatch& vb, float eps, float lambda, const fl
   if (items <= 0) return cudaSuccess;
   // the carry-over walk: sort-free lists, or deterministic mode's fixed-point sums
   if (mode == GPS_BLEND_OIT && ((!det && !sorted) || vb.v[0].grad_fixed)) {
-    if (instr)
-      launch_chained(composite_bwd_oit_carry_kernel<TW, TH, true>, dim3(items), dim3(TW * TH), 0, st,
-          vb, eps, lambda, dloss);
+    const bool fixed = vb.v[0].grad_fixed != nullptr;
+    if (instr && fixed)
+      launch_chained(composite_bwd_oit_carry_kernel<TW, TH, true, true>, dim3(items), dim3(TW * TH),
+          0, st, vb, eps, lambda, dloss);
+    else if (instr)
+      launch_chained(composite_bwd_oit_carry_kernel<TW, TH, true, false>, dim3(items), dim3(TW * TH),
+          0, st, vb, eps, lambda, dloss);
+    else if (fixed)
+      launch_chained(composite_bwd_oit_carry_kernel<TW, TH, false, true>, dim3(items), dim3(TW * TH),
+          0, st, vb, eps, lambda, dloss);
     else
-      launch_chained(composite_bwd_oit_carry_kernel<TW, TH, false>, dim3(items), dim3(TW * TH), 0, st,
-          vb, eps, lambda, dloss);
+      launch_chained(composite_bwd_oit_carry_kernel<TW, TH, false, false>, dim3(items), dim3(TW * TH),
+          0, st, vb, eps, lambda, dloss);
   } else if (mode == GPS_BLEND_OIT) {
     if (instr)
       launch_chained(composite_bwd_oit_kernel<TW, TH, true>, dim3(items), dim3(TW * TH), 0, st,
@@ -2043,13 +2081,10 @@ cudaError_t launch_upstream_max(const ViewBatch& vb, float eps, float lambda, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_fixed_scale(const ViewBatch& vb, int M, cudaStream_t st) {
-  launch_chained(fixed_scale_kernel, dim3((M + 255) / 256, vb.n), dim3(256), 0, st, vb, M);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fixed_to_grad2d(const ViewBatch& vb, int M, cudaStream_t st) {
-  launch_chained(fixed_to_grad2d_kernel, dim3((M + 255) / 256, vb.n), dim3(256), 0, st, vb, M);
+cudaError_t launch_fixed_to_grad2d(const ViewBatch& vb, int M, const float* dloss,
+                                   cudaStream_t st) {
+  launch_chained(fixed_to_grad2d_kernel, dim3((M + 255) / 256, vb.n), dim3(256), 0, st, vb, M,
+                 dloss);
   return cudaGetLastError();
 }
 

@@ -73,7 +73,6 @@ struct ViewDev {
   float4* pix_g;          // [npx][2] per-Gaussian backward: (h), (sv, thr, -, -)
   int* tile_order;        // [tiles] longest lists first (by their bin's entry count)
   long long* grad_fixed;  // [M][10] fixed-point 2D gradient sums (deterministic OIT), else null
-  uint4* fixed_exp;       // [M] their quantum exponents, 10 bytes biased by 128 (same mode)
   int tiles_x, tiles_y, tw, th;
   // bins of the binning pass (sup_x * sup_y of them, 2^bin_sx x 2^bin_sy
   // pixels each): square super-tiles, or the tiles themselves
@@ -150,6 +149,55 @@ __device__ __forceinline__ bool record_rect(float mx, float my, float ex, float 
   y1 = min(H - 1, (int)floorf(fminf(hy, (float)H)));
   return x0 <= x1 && y0 <= y1;
 }
+
+// Deterministic OIT backward (fixed-point gradient sums, composite.cu): the
+// part of a Gaussian's quantum exponents that depends on its record alone,
+// written by the projection into the record's spare words 13 and 14 (float
+// 12 is ey).  The bounds on a (warp block, Gaussian) partial of each
+// component k factor as c_k x V (k < 6; V the view's bound on |dL/dalpha|
+// terms) or c_k x hmax (k >= 6) with
+//   c_0 = 64 (|a| ex + |b| ey), c_1 = 64 (|b| ex + |c| ey), c_2 = 32 ex^2,
+//   c_3 = 64 ex ey, c_4 = 32 ey^2, c_5 = c_6.. = 64
+// (conic a, b, c; extents ex, ey).  With n partials at most (tiles of the
+// rectangle x warp blocks per tile), the quantum exponent is
+// x(c_k) + x(V or hmax) - (62 - ceil(log2 n)), x(b) = the least integer
+// with b < 2^x (fixed_expo_above); the first and last terms are the
+// pre-exponent p_k, stored as p_k + 128 in a byte (clamped to [0, 255]:
+// raising p only coarsens the quantum).  Word 13: p_0..p_3; word 14: p_4,
+// p_5 (= p_6..p_9), 0, kFixedPreTag (records written otherwise lack the tag
+// and have the pre-exponents recomputed by whoever reads them).
+constexpr uint32_t kFixedPreTag = 0x5Au;
+
+// The least x >= -126 with b < 2^x, for b >= 0 (b >= 2^128, inf or NaN -> 129).
+__device__ __forceinline__ int fixed_expo_above(float b) {
+  const int E = (int)((__float_as_uint(b) >> 23) & 0xffu);
+  return E == 0 ? -126 : E - 126;
+}
+
+__device__ __forceinline__ uint2 fixed_pre_exponents(float mx, float my, float ca, float cb,
+                                                     float cc, float ex, float ey, int W, int H,
+                                                     int tw, int th) {
+  int n = 1, x0, x1, y0, y1;
+  if (record_rect(mx, my, ex, ey, W, H, x0, x1, y0, y1))
+    n = (x1 / tw - x0 / tw + 1) * (y1 / th - y0 / th + 1) * (tw * th / 32);
+  const int off = (n > 1 ? 32 - __clz(n - 1) : 0) - 62 + 128;  // ceil(log2 n) - 62, biased
+  // explicit roundings: every reader of an untagged record gets the same bits
+  const float ax = fabsf(ex), ay = fabsf(ey);
+  float c[5];
+  c[0] = __fmul_rn(64.0f, __fmaf_rn(fabsf(ca), ax, __fmul_rn(fabsf(cb), ay)));
+  c[1] = __fmul_rn(64.0f, __fmaf_rn(fabsf(cb), ax, __fmul_rn(fabsf(cc), ay)));
+  c[2] = __fmul_rn(__fmul_rn(32.0f, ax), ax);
+  c[3] = __fmul_rn(__fmul_rn(64.0f, ax), ay);
+  c[4] = __fmul_rn(__fmul_rn(32.0f, ay), ay);
+  uint32_t b[6];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) b[k] = (uint32_t)min(max(fixed_expo_above(c[k]) + off, 0), 255);
+  b[5] = (uint32_t)min(max(7 + off, 0), 255);  // x(64) = 7
+  return make_uint2(b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24),
+                    b[4] | (b[5] << 8) | (kFixedPreTag << 24));
+}
+
+__device__ __forceinline__ bool fixed_pre_tagged(uint32_t w14) { return (w14 >> 24) == kFixedPreTag; }
 
 // q = dx (a dx + 2b dy) + (c dy) dy with explicit roundings (identical on the
 // oracle's FP32 decision path).  b2 = 2 b.

@@ -223,17 +223,23 @@ __device__ __forceinline__ void project_one(const Params& P, int i, float near_,
   project_gaussian(P, i, cam, near_, o);
   float4* r = v.rec + 4 * (size_t)i;
   if (!o.vis) {
+    // (a culled Gaussian adds no partials: its fixed-point quanta are moot)
+    const uint2 pre = v.grad_fixed ? make_uint2(0u, kFixedPreTag << 24) : make_uint2(0u, 0u);
     r[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     r[1] = make_float4(0.f, 0.f, 0.f, 0.f);
     r[2] = make_float4(0.f, 0.f, 0.f, -1.0f);
-    r[3] = make_float4(-1.0f, 0.f, 0.f, 0.f);
+    r[3] = make_float4(-1.0f, __uint_as_float(pre.x), __uint_as_float(pre.y), 0.f);
     return;
   }
   const float3 col = view_colour<DEG>(P, i, cam, s_row);
+  // deterministic OIT backward: the record's part of the fixed-point quanta
+  const uint2 pre = v.grad_fixed ? fixed_pre_exponents(o.mx, o.my, o.ca, o.cb, o.cc, o.ex, o.ey,
+                                                       cam.W, cam.H, v.tw, v.th)
+                                 : make_uint2(0u, 0u);
   r[0] = make_float4(o.mx, o.my, o.tc[2], o.sig);
   r[1] = make_float4(o.ca, o.cb, o.cc, o.qmax);
   r[2] = make_float4(col.x, col.y, col.z, o.ex);
-  r[3] = make_float4(o.ey, 0.f, 0.f, 0.f);
+  r[3] = make_float4(o.ey, __uint_as_float(pre.x), __uint_as_float(pre.y), 0.f);
   int x0, x1, y0, y1;
   record_rect(o.mx, o.my, o.ex, o.ey, cam.W, cam.H, x0, x1, y0, y1);
   for (int sy = y0 >> v.bin_sy; sy <= (y1 >> v.bin_sy); ++sy)

@@ -490,6 +490,37 @@ def test_deterministic_mode_is_bitwise_reproducible_and_matches():
     np.testing.assert_allclose(outs[0], outs[2], atol=1e-6 * np.abs(outs[2]).max())
 
 
+def test_deterministic_quanta_from_records_without_the_projection_tag():
+    """The fixed-point sums' quanta: the projection writes each record's part
+    of them (words 13-14, tagged); records written by anyone else carry no
+    tag and have them recomputed from the record by the backward walk and by
+    the conversion back.  Same records either way, so the same gradients,
+    bit for bit."""
+    w = workload("small")
+    f = w.frames[0]
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    s = gps.settings(eps_depth=w.eps_depth, lambda_depth=0.5, tile=(16, 8), deterministic=True)
+    r = gps.Renderer(w.gaussians.M, [f.cam], s)
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    v = gps.View(f.cam, cuda(Ct), cuda(Dt), cuda(f.rgb), cuda(f.depth))
+    out = []
+    for untagged in (False, True):
+        if untagged:
+            rec = r.region(0, "records", torch.float32, r.M * 16).view(r.M, 16)
+            tag = rec[:, 14].contiguous().view(torch.int32).cpu().numpy() >> 24
+            assert np.all(tag == 0x5A)
+            rec[:, 13:15] = 0.0
+            r.s.stages = (gps.STAGE_BIN | gps.STAGE_COMPOSITE | gps.STAGE_COMPOSITE_BWD
+                          | gps.STAGE_PROJECT_BWD)
+        loss = torch.zeros(1, device="cuda")
+        r.forward(g, [v], loss)
+        grads = g.zeros_like()
+        r.backward(g, [v], grads)
+        out.append(grads.flat().cpu().numpy())
+    assert np.abs(out[0]).max() > 0
+    np.testing.assert_array_equal(out[0], out[1])
+
+
 # ------------------------------------------------------------------ Adam
 def test_adam_matches_oracle():
     rng = np.random.default_rng(0)
