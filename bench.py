@@ -550,7 +550,7 @@ def kernels_per_step(mode, tile, schedule="tiles", deterministic=False, fused=Tr
     # lists are depth-sorted, or where a view's tile grid exceeds what the
     # binning histogram holds (then the unsorted lists go through super-tiles
     # and a split)], composite, finalize, composite_bwd [deterministic: + the
-    # upstream maxima, the fixed-point exponents and the conversion (OIT; its
+    # conversion of the fixed-point sums (OIT, with the fused loss; its
     # fixed-order lists add the block prefix where the tile grid allows, else
     # they are depth-sorted), or the pair-slot placement and gather (alpha);
     # per-Gaussian schedule: pixel terms + per-Gaussian], projection adjoint +
@@ -564,7 +564,7 @@ def kernels_per_step(mode, tile, schedule="tiles", deterministic=False, fused=Tr
     if not tiles:
         extra = 1
     elif deterministic:
-        extra = 3 if mode == "oit" else 2
+        extra = 1 if mode == "oit" else 2
     else:
         extra = 0
     return 2 + ITERS_PER_FRAME * (8 + split + prefix + extra + (0 if fused else 1))

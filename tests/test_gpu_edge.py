@@ -174,3 +174,35 @@ def test_sort_free_default_equals_deterministic_order(tile, size):
     np.testing.assert_allclose(w0, w1, rtol=2e-6, atol=2e-6)
     scale = np.abs(g1).max()
     assert np.all(np.abs(g0 - g1) <= 1e-4 * scale + 1e-4 * np.abs(g1))
+
+
+@pytest.mark.parametrize("mode,tile,size", [(gps.BLEND_OIT, (16, 8), (320, 240)),
+                                            (gps.BLEND_ALPHA, (16, 8), (320, 240)),
+                                            (gps.BLEND_ALPHA, (8, 8), (150, 100)),
+                                            (gps.BLEND_OIT, (32, 8), (150, 100))])
+def test_tile_order_is_a_permutation(mode, tile, size):
+    """The composites take their tiles in the order the scan writes
+    (decreasing list length, in half-octave buckets): every tile exactly once,
+    with bins that are the tiles themselves or super-tiles of several tiles
+    (partial ones at the image edge), and bucket by bucket non-increasing in
+    list length."""
+    w = workload("small", M=4000, width=size[0], height=size[1])
+    f = w.frames[0]
+    Ct, Dt, _, _ = oracle_sdf_images(w)
+    s = gps.settings(eps_depth=w.eps_depth, blend_mode=mode, tile=tile)
+    r = gps.Renderer(w.gaussians.M, [f.cam], s)
+    g = gps.Gaussians.from_numpy(w.gaussians)
+    r.forward(g, [gps.View(f.cam, cuda(Ct), cuda(Dt), cuda(f.rgb), cuda(f.depth))])
+    torch.cuda.synchronize()
+    assert r.status() == gps.GPS_OK
+    L = r.layout(0)
+    n = L.tiles_x * L.tiles_y
+    order = r.region(0, "tile_order", torch.int32, n).cpu().numpy()
+    np.testing.assert_array_equal(np.sort(order), np.arange(n))
+    ranges = r.region(0, "tile_ranges", torch.int32, 2 * n).view(n, 2).cpu().numpy()
+    if L.tile_bins:
+        length = (ranges[:, 1] - ranges[:, 0]).astype(np.int64)
+        # the buckets are half octaves: a later tile is at most ~1.5x longer
+        lo = length[order]
+        for a in range(n - 1):
+            assert lo[a + 1] <= max(1, 2 * lo[a]), (a, lo[a], lo[a + 1])
