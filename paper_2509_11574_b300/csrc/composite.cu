@@ -728,12 +728,15 @@ __device__ __forceinline__ int fixed_clamp_e(int e) { return min(max(e, kFixedEM
 
 // The quantum exponents of a Gaussian's ten components from its packed
 // pre-exponents and the bounds V (components 0-5) and hmax (6-9).
+__device__ __forceinline__ int fixed_pre_byte(uint32_t w, int k) {
+  return (int)__byte_perm(w, 0u, 0x4440u + (uint32_t)k);  // byte k, zero-extended
+}
 __device__ __forceinline__ void fixed_exponents(uint2 pre, float V, float hm, int (&e)[10]) {
   const int xv = fixed_expo_above(V) - 128, xh = fixed_expo_above(hm) - 128;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) e[k] = fixed_clamp_e((int)((pre.x >> (8 * k)) & 0xffu) + xv);
-  e[4] = fixed_clamp_e((int)(pre.y & 0xffu) + xv);
-  const int p5 = (int)((pre.y >> 8) & 0xffu);
+  for (int k = 0; k < 4; ++k) e[k] = fixed_clamp_e(fixed_pre_byte(pre.x, k) + xv);
+  e[4] = fixed_clamp_e(fixed_pre_byte(pre.y, 0) + xv);
+  const int p5 = fixed_pre_byte(pre.y, 1);
   e[5] = fixed_clamp_e(p5 + xv);
   e[6] = e[7] = e[8] = e[9] = fixed_clamp_e(p5 + xh);
 }
@@ -767,24 +770,29 @@ __device__ __forceinline__ uint2 fixed_pre(const ViewDev& v, const float4& E, fl
 }
 
 // Add a (warp block, Gaussian gi) partial g to gi's fixed-point sums.  The
-// integer q = g 2^-e, truncated toward zero, is formed from the float's
-// fields: g = +-m 2^(E - 150) with the 24-bit significand m, so
-// q = m 2^(E - 150 - e): an exact left shift (the bound keeps it below 2^62)
-// or a right shift (an error below one quantum, the same in every run).  A
-// subnormal g (E = 0, below 2^-126) reads as m 2^-150 with the implicit bit
-// set; as the quantum is at least 2^-120, its shift is to the right by 30 or
-// more and it adds nothing.  (Integer shifts: a float to 64-bit integer
-// conversion per component measured 3.7 us slower per backward.)
+// integer q = floor(g 2^-e) is formed from the float's fields: g = s m
+// 2^(E - 150) with the sign s and the 24-bit significand m, so q =
+// floor(s m 2^39 / 2^(189 + e - E)), one arithmetic right shift of s m 2^39
+// (the bound keeps E - 150 - e <= 38, so the shift is at least 1; an error
+// below one quantum, the same in every run; shifts past 63 leave the sign).
+// A component that is zero adds nothing and issues no atomic.  (Integer
+// shifts: a float to 64-bit integer conversion per component measured
+// 3.7 us slower per backward.)
+__device__ __forceinline__ long long fixed_shr(long long x, int n) {
+  long long r;
+  asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(n));  // n > 63 acts as 64
+  return r;
+}
 __device__ __forceinline__ void fixed_add(const ViewDev& v, uint32_t gi, const float (&g)[10],
                                           const int (&e)[10]) {
   unsigned long long* o = reinterpret_cast<unsigned long long*>(v.grad_fixed + 10 * (size_t)gi);
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
     const int bits = __float_as_int(g[k]);
-    const int sh = ((bits >> 23) & 0xff) - 150 - e[k];
-    const unsigned long long m = (unsigned long long)((bits & 0x7fffff) | 0x800000);
-    const unsigned long long q = sh >= 0 ? m << min(sh, 63) : m >> min(-sh, 63);
-    if (q != 0ull) atomicAdd(o + k, bits < 0 ? 0ull - q : q);
+    const int amt = e[k] + 189 - (int)(((unsigned)bits >> 23) & 0xffu);
+    const int sm = (bits < 0 ? -1 : 1) * ((bits & 0x7fffff) | 0x800000);
+    const long long q = fixed_shr((long long)((unsigned long long)((unsigned)sm << 7) << 32), amt);
+    if (g[k] != 0.0f) atomicAdd(o + k, (unsigned long long)q);
   }
 }
 
