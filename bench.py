@@ -549,10 +549,11 @@ def kernels_per_step(mode, tile, schedule="tiles", deterministic=False, fused=Tr
     # fuse, raycast + per iteration: project, scan, emit, [sort + split where the
     # lists are depth-sorted, or where a view's tile grid exceeds what the
     # binning histogram holds (then the unsorted lists go through super-tiles
-    # and a split)], composite, finalize, composite_bwd [deterministic: + the
-    # conversion of the fixed-point sums (OIT, with the fused loss; its
-    # fixed-order lists add the block prefix where the tile grid allows, else
-    # they are depth-sorted), or the pair-slot placement and gather (alpha);
+    # and a split)], composite, finalize, composite_bwd [deterministic, OIT:
+    # nothing more (the fused loss's bounds come from the forward, the
+    # projection adjoint converts the fixed-point sums; the fixed-order lists
+    # add the block prefix where the tile grid allows, else they are
+    # depth-sorted); alpha: the pair-slot placement and gather;
     # per-Gaussian schedule: pixel terms + per-Gaussian], projection adjoint +
     # Adam (fused: one kernel, else two), step counter
     tiles = schedule != "per-gaussian"
@@ -564,7 +565,7 @@ def kernels_per_step(mode, tile, schedule="tiles", deterministic=False, fused=Tr
     if not tiles:
         extra = 1
     elif deterministic:
-        extra = 1 if mode == "oit" else 2
+        extra = 0 if mode == "oit" else 2
     else:
         extra = 0
     return 2 + ITERS_PER_FRAME * (8 + split + prefix + extra + (0 if fused else 1))

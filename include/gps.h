@@ -247,7 +247,11 @@ typedef struct GpsWorkspaceLayout {
                            the upstream images otherwise); then uint64 [4] evaluation
                            counters: forward tested, forward counted, backward
                            tested, backward counted (instrument = 1)          */
-  size_t grad2d;        /* float [M][12]                                      */
+  size_t grad2d;        /* float [M][12]: the composite adjoint's 2D gradients
+                           per Gaussian; in deterministic mode with the OIT
+                           blend they are written only by a backward call
+                           without GPS_STAGE_PROJECT_BWD (with it, the
+                           projection adjoint reads grad_fixed directly)      */
   size_t pair_grads;    /* float [tiles per super-tile * pair_capacity][12]
                            (deterministic mode): one slot per (tile,
                            Gaussian) pair, Gaussian-major (see pair_base)     */

@@ -20,7 +20,7 @@ cudaError_t launch_raycast(const GpsTsdf&, const Cam&, float, float, void*, int,
                            cudaStream_t);
 cudaError_t launch_project(const GpsGaussians&, float, const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_project_backward(const GpsGaussians&, float, const ViewBatch&,
-                                    const GpsGaussians&, cudaStream_t);
+                                    const GpsGaussians&, bool, const float*, cudaStream_t);
 cudaError_t launch_bin_histogram(int, const ViewBatch&, int, cudaStream_t);
 cudaError_t launch_scan_super(const ViewBatch&, int*, cudaStream_t);
 cudaError_t launch_emit_super(int, const ViewBatch&, int, cudaStream_t);
@@ -40,7 +40,8 @@ cudaError_t launch_adam(const GpsGaussians&, const GpsGaussians&, const GpsGauss
                         const GpsGaussians&, const GpsAdamHyper&, int, int*, cudaStream_t);
 cudaError_t launch_project_backward_adam(const GpsGaussians&, float, const ViewBatch&,
                                          const GpsGaussians&, const GpsGaussians&,
-                                         const GpsAdamHyper&, int, int*, cudaStream_t);
+                                         const GpsAdamHyper&, int, int*, bool, const float*,
+                                         cudaStream_t);
 }  // namespace gps
 
 using namespace gps;
@@ -137,6 +138,14 @@ bool view_tile_bins(const GpsView& vw, const GpsRenderSettings& s, const TileCfg
 // order of the carry-over backward's additions gives the same bits).
 bool fixed_point_grads(const GpsRenderSettings& s) {
   return s.deterministic && s.blend_mode == GPS_BLEND_OIT && s.schedule == GPS_SCHEDULE_TILES;
+}
+
+// A backward call that runs both the composite and the projection adjoint
+// of deterministic OIT lets the projection adjoint convert the fixed-point
+// sums as it reads them (grad2d is then not written).
+bool folds_fixed_sums(const GpsRenderSettings& s, int stages) {
+  return fixed_point_grads(s) && (stages & GPS_STAGE_COMPOSITE_BWD) &&
+         (stages & GPS_STAGE_PROJECT_BWD);
 }
 
 int32_t layout(int32_t M, const GpsView* views, int32_t n_views, const GpsRenderSettings* s,
@@ -374,9 +383,12 @@ int32_t check_render_args(const GpsGaussians* g, const GpsView* views, int32_t n
 // The composite adjoint of one batch of views, into the views' grad2d.
 // Deterministic mode first places each Gaussian's pair slots (pair_base),
 // writes every pair's gradient into its slot and sums each Gaussian's slots
-// in order.
+// in order; with the OIT blend it sums into fixed-point integers instead,
+// left unconverted when `fold` (the projection adjoint of the same call
+// reads them).
 cudaError_t composite_backward(const ViewBatch& vb, int M, const GpsRenderSettings* s, int stages,
-                               const float* dloss, const int* status, cudaStream_t st) {
+                               const float* dloss, const int* status, bool fold,
+                               cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if ((stages & GPS_STAGE_COMPOSITE_BWD) && s->schedule == GPS_SCHEDULE_PER_GAUSSIAN) {
     e = launch_composite_bwd_per_gaussian(vb, M, s->eps_depth, s->lambda_depth, dloss,
@@ -399,7 +411,7 @@ cudaError_t composite_backward(const ViewBatch& vb, int M, const GpsRenderSettin
     if (e == cudaSuccess)
       e = launch_composite_bwd(vb, vb.v[0].tw, vb.v[0].th, s->eps_depth, s->lambda_depth, dloss,
                                s->blend_mode, 1, s->instrument ? 1 : 0, batch_sorted(vb), st);
-    if (e == cudaSuccess && M > 0) e = launch_fixed_to_grad2d(vb, M, dloss, st);
+    if (e == cudaSuccess && M > 0 && !fold) e = launch_fixed_to_grad2d(vb, M, dloss, st);
   } else if (stages & GPS_STAGE_COMPOSITE_BWD) {
     for (int j = 0; j < vb.n && e == cudaSuccess; ++j)
       e = s->deterministic ? cudaMemsetAsync(vb.v[j].scalars + 5, 0, sizeof(float), st)
@@ -589,9 +601,11 @@ int32_t render_backward(const GpsGaussians* g, const GpsView* views, int32_t n_v
     ViewBatch vb;
     int max_nsup = 0;
     make_batch(g->M, views, n_views, s, base, b0, vb, max_nsup);
-    e = composite_backward(vb, g->M, s, stages, dloss, reinterpret_cast<const int*>(base), st);
+    const bool fold = folds_fixed_sums(*s, stages);
+    e = composite_backward(vb, g->M, s, stages, dloss, reinterpret_cast<const int*>(base), fold,
+                           st);
     if (e == cudaSuccess && (stages & GPS_STAGE_PROJECT_BWD) && g->M > 0)
-      e = launch_project_backward(*g, s->near_plane, vb, *grads, st);
+      e = launch_project_backward(*g, s->near_plane, vb, *grads, fold, dloss, st);
   }
   return e == cudaSuccess ? GPS_OK : cuda_fail(e, "render_backward");
 }
@@ -613,9 +627,12 @@ int32_t render_backward_adam(GpsGaussians* g, const GpsView* views, int32_t n_vi
   ViewBatch vb;
   int max_nsup = 0;
   make_batch(g->M, views, n_views, s, static_cast<char*>(ws), 0, vb, max_nsup);
-  cudaError_t e = composite_backward(vb, g->M, s, stages, dloss, static_cast<const int*>(ws), st);
+  const bool fold = folds_fixed_sums(*s, stages);
+  cudaError_t e =
+      composite_backward(vb, g->M, s, stages, dloss, static_cast<const int*>(ws), fold, st);
   if (e == cudaSuccess && g->M > 0)
-    e = launch_project_backward_adam(*g, s->near_plane, vb, *m, *v, *hyper, step, device_step, st);
+    e = launch_project_backward_adam(*g, s->near_plane, vb, *m, *v, *hyper, step, device_step,
+                                     fold, dloss, st);
   return e == cudaSuccess ? GPS_OK : cuda_fail(e, "render_backward_adam");
 }
 

@@ -722,53 +722,6 @@ __device__ __forceinline__ void zero_slot(const ViewDev& v, long long slot) {
 // normal floats (raising e only coarsens the quantum; lowering it to 126
 // happens only for bounds above 2^(188 - ceil(log2 n)), where any finite
 // FP32 partial is still below 2^2 quanta).
-constexpr int kFixedEMin = -120, kFixedEMax = 126;
-
-__device__ __forceinline__ int fixed_clamp_e(int e) { return min(max(e, kFixedEMin), kFixedEMax); }
-
-// The quantum exponents of a Gaussian's ten components from its packed
-// pre-exponents and the bounds V (components 0-5) and hmax (6-9).
-__device__ __forceinline__ int fixed_pre_byte(uint32_t w, int k) {
-  return (int)__byte_perm(w, 0u, 0x4440u + (uint32_t)k);  // byte k, zero-extended
-}
-__device__ __forceinline__ void fixed_exponents(uint2 pre, float V, float hm, int (&e)[10]) {
-  const int xv = fixed_expo_above(V) - 128, xh = fixed_expo_above(hm) - 128;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) e[k] = fixed_clamp_e(fixed_pre_byte(pre.x, k) + xv);
-  e[4] = fixed_clamp_e(fixed_pre_byte(pre.y, 0) + xv);
-  const int p5 = fixed_pre_byte(pre.y, 1);
-  e[5] = fixed_clamp_e(p5 + xv);
-  e[6] = e[7] = e[8] = e[9] = fixed_clamp_e(p5 + xh);
-}
-
-// The view's upstream bounds: with the fused L1 loss the forward's loss
-// finalisation left them per unit dL/dloss in scalars[6..7] (scaled here by
-// |dL/dloss|), with explicit upstream images upstream_max_kernel left the
-// maxima themselves.
-__device__ __forceinline__ void fixed_maxima(const ViewDev& v, const float* dloss, float& hm,
-                                             float& sm) {
-  const float f = v.fused && dloss ? fabsf(*dloss) : 1.0f;
-  hm = __fmul_rn(v.scalars[6], f);
-  sm = __fmul_rn(v.scalars[7], f);
-}
-
-// V = hmax (|r| + |g| + |b| + |d|) + smax, explicitly rounded (the walk and
-// the conversion back compute it from the same record values).
-__device__ __forceinline__ float fixed_v(float hm, float sm, float cr, float cg, float cb,
-                                         float d) {
-  return __fmaf_rn(hm, __fadd_rn(__fadd_rn(fabsf(cr), fabsf(cg)), __fadd_rn(fabsf(cb), fabsf(d))),
-                   sm);
-}
-
-// A Gaussian's packed pre-exponents: from the record's words 13-14 where the
-// projection wrote them, else recomputed from the record.
-__device__ __forceinline__ uint2 fixed_pre(const ViewDev& v, const float4& E, float mx, float my,
-                                           float ca, float cb, float cc, const float* ex_p) {
-  const uint2 pre = make_uint2(__float_as_uint(E.y), __float_as_uint(E.z));
-  if (fixed_pre_tagged(pre.y)) return pre;
-  return fixed_pre_exponents(mx, my, ca, cb, cc, __ldg(ex_p), E.x, v.cam.W, v.cam.H, v.tw, v.th);
-}
-
 // Add a (warp block, Gaussian gi) partial g to gi's fixed-point sums.  The
 // integer q = floor(g 2^-e) is formed from the float's fields: g = s m
 // 2^(E - 150) with the sign s and the 24-bit significand m, so q =
@@ -842,35 +795,20 @@ __global__ void __launch_bounds__(256) upstream_max_kernel(const __grid_constant
   }
 }
 
-// Fixed-point sums -> grad2d (float): one rounding of the integer sum, then
-// the exact power-of-two scale 2^e (the exponents recomputed from the
-// record, as the walk computed them).  Block row blockIdx.y: view.
+// Fixed-point sums -> grad2d (float) for calls whose projection adjoint
+// does not read the sums itself.  Block row blockIdx.y: view.
 __global__ void __launch_bounds__(256) fixed_to_grad2d_kernel(const __grid_constant__ ViewBatch vb,
                                                               int M, const float* dloss) {
   chain_wait();
   const ViewDev& v = vb.v[blockIdx.y];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
-  const float4* rr = v.rec + 4 * (size_t)i;
-  const float4 A = rr[0], C = rr[2];
-  const uint2 pre = fixed_pre(v, rr[3], A.x, A.y, rr[1].x, rr[1].y, rr[1].z, &rr[2].w);
-  float hm, sm;
-  fixed_maxima(v, dloss, hm, sm);
-  int e[10];
-  fixed_exponents(pre, fixed_v(hm, sm, C.x, C.y, C.z, A.z), hm, e);
-  const longlong2* s = reinterpret_cast<const longlong2*>(v.grad_fixed + 10 * (size_t)i);
-  float g[12];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const longlong2 t = s[k];
-    g[2 * k] = __fmul_rn(__ll2float_rn(t.x), __int_as_float((127 + e[2 * k]) << 23));
-    g[2 * k + 1] = __fmul_rn(__ll2float_rn(t.y), __int_as_float((127 + e[2 * k + 1]) << 23));
-  }
-  g[10] = g[11] = 0.f;
+  float4 ga, gb, gc;
+  fixed_grad2d(v, i, dloss, ga, gb, gc);
   float4* o = v.grad2d + 3 * (size_t)i;
-  o[0] = make_float4(g[0], g[1], g[2], g[3]);
-  o[1] = make_float4(g[4], g[5], g[6], g[7]);
-  o[2] = make_float4(g[8], g[9], g[10], g[11]);
+  o[0] = ga;
+  o[1] = gb;
+  o[2] = gc;
 }
 
 // 2D gradient g of a (tile, Gaussian gi) pair: deterministic mode writes it

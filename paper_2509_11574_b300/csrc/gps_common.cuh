@@ -199,6 +199,82 @@ __device__ __forceinline__ uint2 fixed_pre_exponents(float mx, float my, float c
 
 __device__ __forceinline__ bool fixed_pre_tagged(uint32_t w14) { return (w14 >> 24) == kFixedPreTag; }
 
+// Quantum exponents are clamped to [-120, 126] so that 2^-e and 2^e are
+// normal floats (composite.cu derives the bounds behind them).
+constexpr int kFixedEMin = -120, kFixedEMax = 126;
+
+__device__ __forceinline__ int fixed_clamp_e(int e) { return min(max(e, kFixedEMin), kFixedEMax); }
+
+// The quantum exponents of a Gaussian's ten components from its packed
+// pre-exponents and the bounds V (components 0-5) and hmax (6-9).
+__device__ __forceinline__ int fixed_pre_byte(uint32_t w, int k) {
+  return (int)__byte_perm(w, 0u, 0x4440u + (uint32_t)k);  // byte k, zero-extended
+}
+__device__ __forceinline__ void fixed_exponents(uint2 pre, float V, float hm, int (&e)[10]) {
+  const int xv = fixed_expo_above(V) - 128, xh = fixed_expo_above(hm) - 128;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) e[k] = fixed_clamp_e(fixed_pre_byte(pre.x, k) + xv);
+  e[4] = fixed_clamp_e(fixed_pre_byte(pre.y, 0) + xv);
+  const int p5 = fixed_pre_byte(pre.y, 1);
+  e[5] = fixed_clamp_e(p5 + xv);
+  e[6] = e[7] = e[8] = e[9] = fixed_clamp_e(p5 + xh);
+}
+
+// The view's upstream bounds: with the fused L1 loss the forward's loss
+// finalisation left them per unit dL/dloss in scalars[6..7] (scaled here by
+// |dL/dloss|), with explicit upstream images upstream_max_kernel left the
+// maxima themselves.
+__device__ __forceinline__ void fixed_maxima(const ViewDev& v, const float* dloss, float& hm,
+                                             float& sm) {
+  const float f = v.fused && dloss ? fabsf(*dloss) : 1.0f;
+  hm = __fmul_rn(v.scalars[6], f);
+  sm = __fmul_rn(v.scalars[7], f);
+}
+
+// V = hmax (|r| + |g| + |b| + |d|) + smax, explicitly rounded (the walk and
+// the conversion back compute it from the same record values).
+__device__ __forceinline__ float fixed_v(float hm, float sm, float cr, float cg, float cb,
+                                         float d) {
+  return __fmaf_rn(hm, __fadd_rn(__fadd_rn(fabsf(cr), fabsf(cg)), __fadd_rn(fabsf(cb), fabsf(d))),
+                   sm);
+}
+
+// A Gaussian's packed pre-exponents: from the record's words 13-14 where the
+// projection wrote them, else recomputed from the record.
+__device__ __forceinline__ uint2 fixed_pre(const ViewDev& v, const float4& E, float mx, float my,
+                                           float ca, float cb, float cc, const float* ex_p) {
+  const uint2 pre = make_uint2(__float_as_uint(E.y), __float_as_uint(E.z));
+  if (fixed_pre_tagged(pre.y)) return pre;
+  return fixed_pre_exponents(mx, my, ca, cb, cc, __ldg(ex_p), E.x, v.cam.W, v.cam.H, v.tw, v.th);
+}
+
+// A Gaussian's 2D gradient from its fixed-point sums: one rounding of each
+// integer sum, then the exact power-of-two scale 2^e (the exponents
+// recomputed from the record, as the backward walk computed them).
+// ga = d/d(mx, my, conic a, conic b), gb = (conic c, sigma, r, g),
+// gc = (b, depth, 0, 0), the layout of grad2d.
+__device__ __forceinline__ void fixed_grad2d(const ViewDev& v, int i, const float* dloss,
+                                             float4& ga, float4& gb, float4& gc) {
+  const float4* rr = v.rec + 4 * (size_t)i;
+  const float4 A = rr[0], C = rr[2];
+  const uint2 pre = fixed_pre(v, rr[3], A.x, A.y, rr[1].x, rr[1].y, rr[1].z, &rr[2].w);
+  float hm, sm;
+  fixed_maxima(v, dloss, hm, sm);
+  int e[10];
+  fixed_exponents(pre, fixed_v(hm, sm, C.x, C.y, C.z, A.z), hm, e);
+  const longlong2* s = reinterpret_cast<const longlong2*>(v.grad_fixed + 10 * (size_t)i);
+  float g[10];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const longlong2 t = s[k];
+    g[2 * k] = __fmul_rn(__ll2float_rn(t.x), __int_as_float((127 + e[2 * k]) << 23));
+    g[2 * k + 1] = __fmul_rn(__ll2float_rn(t.y), __int_as_float((127 + e[2 * k + 1]) << 23));
+  }
+  ga = make_float4(g[0], g[1], g[2], g[3]);
+  gb = make_float4(g[4], g[5], g[6], g[7]);
+  gc = make_float4(g[8], g[9], 0.f, 0.f);
+}
+
 // q = dx (a dx + 2b dy) + (c dy) dy with explicit roundings (identical on the
 // oracle's FP32 decision path).  b2 = 2 b.
 __device__ __forceinline__ float quad_form(float a, float b2, float c, float dx, float dy) {

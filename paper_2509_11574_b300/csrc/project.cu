@@ -383,11 +383,14 @@ __device__ __forceinline__ void project_adjoint(const ProjState& o, const Cam& c
 // K8: adjoint of the projection, summed over the batch's views in view order
 // and accumulated (+=) into the parameter gradients once per Gaussian.  With
 // DEG > 0 the block stages its Gaussians' SH rows and their gradient rows in
-// shared memory (2 x 256 x STRIDE floats).
-template <int DEG>
+// shared memory (2 x 256 x STRIDE floats).  FIXED: the 2D gradients are
+// read from deterministic mode's fixed-point sums (converted here, in the
+// same arithmetic as fixed_to_grad2d_kernel) instead of grad2d.
+template <int DEG, bool FIXED>
 __global__ void __launch_bounds__(256, DEG == 0 ? 3 : 2) project_backward_kernel(Params P, int M, float near_,
                                                                const __grid_constant__ ViewBatch vb,
-                                                               GpsGaussians grads) {
+                                                               GpsGaussians grads,
+                                                               const float* dloss) {
   chain_wait();
   extern __shared__ float s_sh[];
   using R = ShRows<DEG>;
@@ -408,8 +411,15 @@ __global__ void __launch_bounds__(256, DEG == 0 ? 3 : 2) project_backward_kernel
     ProjState o;
     project_gaussian(P, i, cam, near_, o);
     if (!o.vis) continue;
-    const float4* g2 = vb.v[k].grad2d + 3 * (size_t)i;
-    const float4 ga = g2[0], gb = g2[1], gc = g2[2];
+    float4 ga, gb, gc;
+    if constexpr (FIXED) {
+      fixed_grad2d(vb.v[k], i, dloss, ga, gb, gc);  // deterministic mode's sums
+    } else {
+      const float4* g2 = vb.v[k].grad2d + 3 * (size_t)i;
+      ga = g2[0];
+      gb = g2[1];
+      gc = g2[2];
+    }
     project_adjoint(o, cam, ga, gb, gc, a);
     if constexpr (DEG > 0) {
       const float3 gm = view_colour_adjoint<DEG>(P, i, cam, make_float3(gb.z, gb.w, gc.x),
@@ -478,10 +488,12 @@ struct AdamFused {
 // parameter gradient (summed over the batch's views, zero if no view sees
 // it) feeds adam_update directly instead of being added to a gradient array.
 // With the gradient array zeroed before render_backward, the same FP32
-// operations as render_backward followed by adam_step.
-template <int DEG>
+// operations as render_backward followed by adam_step.  FIXED: as in
+// project_backward_kernel.
+template <int DEG, bool FIXED>
 __global__ void __launch_bounds__(256, DEG == 0 ? 3 : 2) project_backward_adam_kernel(
-    Params P, int M, float near_, const __grid_constant__ ViewBatch vb, AdamFused A) {
+    Params P, int M, float near_, const __grid_constant__ ViewBatch vb, AdamFused A,
+    const float* dloss) {
   chain_wait();
   extern __shared__ float s_sh[];
   using R = ShRows<DEG>;
@@ -502,8 +514,15 @@ __global__ void __launch_bounds__(256, DEG == 0 ? 3 : 2) project_backward_adam_k
     ProjState o;
     project_gaussian(P, i, cam, near_, o);
     if (!o.vis) continue;
-    const float4* g2 = vb.v[k].grad2d + 3 * (size_t)i;
-    const float4 ga = g2[0], gb = g2[1], gc = g2[2];
+    float4 ga, gb, gc;
+    if constexpr (FIXED) {
+      fixed_grad2d(vb.v[k], i, dloss, ga, gb, gc);  // deterministic mode's sums
+    } else {
+      const float4* g2 = vb.v[k].grad2d + 3 * (size_t)i;
+      ga = g2[0];
+      gb = g2[1];
+      gc = g2[2];
+    }
     project_adjoint(o, cam, ga, gb, gc, a);
     if constexpr (DEG > 0) {
       const float3 gm = view_colour_adjoint<DEG>(P, i, cam, make_float3(gb.z, gb.w, gc.x),
@@ -624,34 +643,61 @@ cudaError_t launch_project_t(const Params& P, int M, float near_, const ViewBatc
   return cudaGetLastError();
 }
 
-template <int DEG>
+template <int DEG, bool FIXED>
 cudaError_t launch_project_backward_t(const Params& P, int M, float near_, const ViewBatch& vb,
-                                      const GpsGaussians& grads, cudaStream_t st) {
+                                      const GpsGaussians& grads, const float* dloss,
+                                      cudaStream_t st) {
   const size_t smem = DEG > 0 ? 2 * kProjThreads * ShRows<DEG>::STRIDE * 4 : 0;
   if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        project_backward_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  launch_chained(project_backward_kernel<DEG>, dim3((M + kProjThreads - 1) / kProjThreads), dim3(kProjThreads), smem, st,
-      P, M, near_, vb, grads);
-  return cudaGetLastError();
-}
-
-template <int DEG>
-cudaError_t launch_project_backward_adam_t(const Params& P, int M, float near_,
-                                           const ViewBatch& vb, const AdamFused& A,
-                                           cudaStream_t st) {
-  const size_t smem = DEG > 0 ? 2 * kProjThreads * ShRows<DEG>::STRIDE * 4 : 0;
-  if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(project_backward_adam_kernel<DEG>,
+    const cudaError_t e = cudaFuncSetAttribute(project_backward_kernel<DEG, FIXED>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
     if (e != cudaSuccess) return e;
   }
-  launch_chained(project_backward_adam_kernel<DEG>, dim3((M + kProjThreads - 1) / kProjThreads),
-                 dim3(kProjThreads), smem, st, P, M, near_, vb, A);
+  launch_chained(project_backward_kernel<DEG, FIXED>, dim3((M + kProjThreads - 1) / kProjThreads),
+                 dim3(kProjThreads), smem, st, P, M, near_, vb, grads, dloss);
   return cudaGetLastError();
+}
+
+template <int DEG, bool FIXED>
+cudaError_t launch_project_backward_adam_t(const Params& P, int M, float near_,
+                                           const ViewBatch& vb, const AdamFused& A,
+                                           const float* dloss, cudaStream_t st) {
+  const size_t smem = DEG > 0 ? 2 * kProjThreads * ShRows<DEG>::STRIDE * 4 : 0;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(project_backward_adam_kernel<DEG, FIXED>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  launch_chained(project_backward_adam_kernel<DEG, FIXED>,
+                 dim3((M + kProjThreads - 1) / kProjThreads), dim3(kProjThreads), smem, st, P, M,
+                 near_, vb, A, dloss);
+  return cudaGetLastError();
+}
+
+template <bool FIXED>
+cudaError_t launch_project_backward_adam_deg(const Params& P, int M, float near_,
+                                             const ViewBatch& vb, const AdamFused& A,
+                                             const float* dloss, cudaStream_t st) {
+  switch (P.sh_degree) {
+    case 1: return launch_project_backward_adam_t<1, FIXED>(P, M, near_, vb, A, dloss, st);
+    case 2: return launch_project_backward_adam_t<2, FIXED>(P, M, near_, vb, A, dloss, st);
+    case 3: return launch_project_backward_adam_t<3, FIXED>(P, M, near_, vb, A, dloss, st);
+    default: return launch_project_backward_adam_t<0, FIXED>(P, M, near_, vb, A, dloss, st);
+  }
+}
+
+template <bool FIXED>
+cudaError_t launch_project_backward_deg(const Params& P, int M, float near_, const ViewBatch& vb,
+                                        const GpsGaussians& grads, const float* dloss,
+                                        cudaStream_t st) {
+  switch (P.sh_degree) {
+    case 1: return launch_project_backward_t<1, FIXED>(P, M, near_, vb, grads, dloss, st);
+    case 2: return launch_project_backward_t<2, FIXED>(P, M, near_, vb, grads, dloss, st);
+    case 3: return launch_project_backward_t<3, FIXED>(P, M, near_, vb, grads, dloss, st);
+    default: return launch_project_backward_t<0, FIXED>(P, M, near_, vb, grads, dloss, st);
+  }
 }
 
 // Fused projection adjoint + Adam (one batch of views); afterwards the device
@@ -659,7 +705,7 @@ cudaError_t launch_project_backward_adam_t(const Params& P, int M, float near_,
 cudaError_t launch_project_backward_adam(const GpsGaussians& g, float near_, const ViewBatch& vb,
                                          const GpsGaussians& Mo, const GpsGaussians& Vo,
                                          const GpsAdamHyper& h, int step, int* device_step,
-                                         cudaStream_t st) {
+                                         bool fixed_in, const float* dloss, cudaStream_t st) {
   const Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb, g.sh_rest, g.sh_degree};
   AdamFused A{};
   float* const pp[6] = {g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb, g.sh_rest};
@@ -681,13 +727,9 @@ cudaError_t launch_project_backward_adam(const GpsGaussians& g, float near_, con
   } else {
     A.device_step = device_step;
   }
-  cudaError_t e = cudaSuccess;
-  switch (g.sh_degree) {
-    case 1: e = launch_project_backward_adam_t<1>(P, g.M, near_, vb, A, st); break;
-    case 2: e = launch_project_backward_adam_t<2>(P, g.M, near_, vb, A, st); break;
-    case 3: e = launch_project_backward_adam_t<3>(P, g.M, near_, vb, A, st); break;
-    default: e = launch_project_backward_adam_t<0>(P, g.M, near_, vb, A, st); break;
-  }
+  cudaError_t e = fixed_in
+                      ? launch_project_backward_adam_deg<true>(P, g.M, near_, vb, A, dloss, st)
+                      : launch_project_backward_adam_deg<false>(P, g.M, near_, vb, A, dloss, st);
   if (e == cudaSuccess && step <= 0) e = launch_adam_step_advance(device_step, st);
   return e;
 }
@@ -703,15 +745,14 @@ cudaError_t launch_project(const GpsGaussians& g, float near_, const ViewBatch& 
   }
 }
 
+// fixed_in: the views' 2D gradients are deterministic mode's fixed-point
+// sums, not yet converted into grad2d.
 cudaError_t launch_project_backward(const GpsGaussians& g, float near_, const ViewBatch& vb,
-                                    const GpsGaussians& grads, cudaStream_t st) {
+                                    const GpsGaussians& grads, bool fixed_in, const float* dloss,
+                                    cudaStream_t st) {
   const Params P{g.means, g.log_scales, g.quats, g.opacity_logits, g.rgb, g.sh_rest, g.sh_degree};
-  switch (g.sh_degree) {
-    case 1: return launch_project_backward_t<1>(P, g.M, near_, vb, grads, st);
-    case 2: return launch_project_backward_t<2>(P, g.M, near_, vb, grads, st);
-    case 3: return launch_project_backward_t<3>(P, g.M, near_, vb, grads, st);
-    default: return launch_project_backward_t<0>(P, g.M, near_, vb, grads, st);
-  }
+  return fixed_in ? launch_project_backward_deg<true>(P, g.M, near_, vb, grads, dloss, st)
+                  : launch_project_backward_deg<false>(P, g.M, near_, vb, grads, dloss, st);
 }
 
 }  // namespace gps

@@ -12,15 +12,15 @@ def test_kernels_per_step_counts_each_form():
     assert bench.kernels_per_step("oit", (16, 8)) == per_frame + it * 8
     # the two-call backward + Adam adds the separate Adam kernel
     assert bench.kernels_per_step("oit", (16, 8), fused=False) == per_frame + it * 9
-    # depth-sorted lists add the sort + split; deterministic mode also
-    # converts the fixed-point sums (OIT, whose fixed-order lists need the
-    # block prefix and no sort up to 6144 tiles; the fused loss's bounds come
-    # from the forward and the sums are zeroed by a memset), or places and
-    # gathers pair slots (alpha)
+    # depth-sorted lists add the sort + split; deterministic mode with OIT
+    # needs the block prefix for its fixed-order lists up to 6144 tiles (no
+    # sort) and nothing more in the backward (the fused loss's bounds come
+    # from the forward, a memset zeroes the fixed-point sums, the projection
+    # adjoint converts them); with alpha it places and gathers pair slots
     assert bench.kernels_per_step("alpha", (16, 8)) == per_frame + it * 9
-    assert bench.kernels_per_step("oit", (16, 8), deterministic=True) == per_frame + it * 10
+    assert bench.kernels_per_step("oit", (16, 8), deterministic=True) == per_frame + it * 9
     assert bench.kernels_per_step("oit", (8, 8), deterministic=True,
-                                  size=(1280, 720)) == per_frame + it * 10
+                                  size=(1280, 720)) == per_frame + it * 9
     assert bench.kernels_per_step("alpha", (16, 8), deterministic=True) == per_frame + it * 11
     # the per-Gaussian schedule: pixel terms + per-Gaussian backward, no sort
     assert bench.kernels_per_step("oit", (16, 8), schedule="per-gaussian") == per_frame + it * 9

@@ -494,8 +494,11 @@ def test_deterministic_quanta_from_records_without_the_projection_tag():
     """The fixed-point sums' quanta: the projection writes each record's part
     of them (words 13-14, tagged); records written by anyone else carry no
     tag and have them recomputed from the record by the backward walk and by
-    the conversion back.  Same records either way, so the same gradients,
-    bit for bit."""
+    the conversion back.  And the conversion: a backward call with both
+    backward stages converts the sums inside the projection adjoint, one
+    with the composite adjoint alone converts them into grad2d for a later
+    projection-adjoint call.  Same records, same arithmetic, so the same
+    gradients, bit for bit, all three ways."""
     w = workload("small")
     f = w.frames[0]
     Ct, Dt, _, _ = oracle_sdf_images(w)
@@ -503,22 +506,32 @@ def test_deterministic_quanta_from_records_without_the_projection_tag():
     r = gps.Renderer(w.gaussians.M, [f.cam], s)
     g = gps.Gaussians.from_numpy(w.gaussians)
     v = gps.View(f.cam, cuda(Ct), cuda(Dt), cuda(f.rgb), cuda(f.depth))
+    bwd = gps.STAGE_COMPOSITE_BWD | gps.STAGE_PROJECT_BWD
     out = []
-    for untagged in (False, True):
-        if untagged:
+    for form in ("tagged", "untagged", "two calls"):
+        r.s.stages = 0
+        if form == "untagged":
             rec = r.region(0, "records", torch.float32, r.M * 16).view(r.M, 16)
             tag = rec[:, 14].contiguous().view(torch.int32).cpu().numpy() >> 24
             assert np.all(tag == 0x5A)
             rec[:, 13:15] = 0.0
-            r.s.stages = (gps.STAGE_BIN | gps.STAGE_COMPOSITE | gps.STAGE_COMPOSITE_BWD
-                          | gps.STAGE_PROJECT_BWD)
+            r.s.stages = gps.STAGE_BIN | gps.STAGE_COMPOSITE | bwd
         loss = torch.zeros(1, device="cuda")
         r.forward(g, [v], loss)
         grads = g.zeros_like()
-        r.backward(g, [v], grads)
+        if form == "two calls":
+            r.s.stages = gps.STAGE_COMPOSITE_BWD
+            r.backward(g, [v], grads)
+            r.s.stages = gps.STAGE_PROJECT_BWD
+            r.backward(g, [v], grads)
+        else:
+            r.backward(g, [v], grads)
+        torch.cuda.synchronize()
+        assert r.status() == gps.GPS_OK
         out.append(grads.flat().cpu().numpy())
     assert np.abs(out[0]).max() > 0
     np.testing.assert_array_equal(out[0], out[1])
+    np.testing.assert_array_equal(out[0], out[2])
 
 
 # ------------------------------------------------------------------ Adam
